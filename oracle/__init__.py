@@ -1,0 +1,268 @@
+"""FP64 CPU oracle of delivery-state rendering (test infrastructure only).
+
+Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path never does.  It shares
+no code with the CUDA library; inputs come from the seeded generators.
+
+Functions and the passages of the paper they follow:
+
+* :func:`closure` -- Section 4 ("dependencies are enforced after delivery, then
+  converted to cluster-layer masks") and Section 7.4 (a chunk is usable only
+  when its whole dependency closure is usable): delivered depth per cluster.
+* :func:`project` -- Section 3 (base plus refinements) and Eq. 1 (low-rank
+  temporal position model, cluster affine = identity) followed by the EWA
+  projection of the external rasterizer the paper uses (Section 6).
+* :func:`render` -- front-to-back alpha compositing of one delivery state;
+  :func:`render_states` repeats it per state (the batched renderer of Section 6
+  must equal this serial evaluation).
+* :func:`mse_psnr` -- the distortion D of Eq. 3 taken as MSE (FP64) and PSNR.
+* :func:`render_backward` -- adjoint of :func:`render`.
+* :func:`bin_tiles` -- tile lists ordered by the 64-bit (tile | depth) key with
+  ties by Gaussian index then variant (an integer function).
+
+Every function is pinned by the CPU tests against closed forms, brute force,
+invariants and finite differences (see ``tests/test_oracle_pins.py``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dgs_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+REC_FIELDS = ("valid", "mx", "my", "A", "B", "C", "z", "o", "r", "g", "b", "radius",
+              "xlo", "xhi", "ylo", "yhi", "marg_rad", "marg_near", "z32", "d")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP64, OpenMP over pixels)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-Wall",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _OScene(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("n_clusters", ctypes.c_int32),
+                ("n_layers", ctypes.c_int32), ("sh_degree", ctypes.c_int32),
+                ("temporal_rank", ctypes.c_int32),
+                ("cluster_offsets", ctypes.c_void_p), ("mu0", ctypes.c_void_p),
+                ("u", ctypes.c_void_p), ("log_scale", ctypes.c_void_p),
+                ("quat", ctypes.c_void_p), ("opacity_logit", ctypes.c_void_p),
+                ("colour", ctypes.c_void_p), ("res", ctypes.c_void_p)]
+
+
+class _OCam(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3),
+                ("fx", ctypes.c_double), ("fy", ctypes.c_double),
+                ("cx", ctypes.c_double), ("cy", ctypes.c_double),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class _OEps(ctypes.Structure):
+    _fields_ = [("box_px", ctypes.c_double), ("rel_alpha", ctypes.c_double),
+                ("rel_T", ctypes.c_double), ("rel_depth", ctypes.c_double),
+                ("rel_radius", ctypes.c_double), ("near_abs", ctypes.c_double)]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        lib.o_closure.argtypes = [ctypes.c_int, ctypes.c_int, P, P]
+        lib.o_project.argtypes = [ctypes.POINTER(_OScene), P, ctypes.c_double, ctypes.POINTER(_OCam), P]
+        lib.o_render.argtypes = [ctypes.POINTER(_OScene), P, ctypes.c_double, ctypes.POINTER(_OCam),
+                                 P, ctypes.c_int, P, P, P, P, ctypes.c_int, ctypes.POINTER(_OEps)]
+        lib.o_render.restype = ctypes.c_int64
+        lib.o_render_backward.argtypes = [ctypes.POINTER(_OScene), P, ctypes.c_double,
+                                          ctypes.POINTER(_OCam), P, P] + [P] * 8
+        lib.o_sh_basis.argtypes = [P, ctypes.c_int, P]
+        lib.o_rec_width.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class _Pinned:
+    """Holds the contiguous arrays behind an _OScene for the call's duration."""
+
+    def __init__(self, scene):
+        c = lambda a, dt: np.ascontiguousarray(a, dtype=dt)
+        self.keep = dict(offs=c(scene.cluster_offsets, np.int32), mu0=c(scene.mu0, np.float32),
+                         u=c(scene.u, np.float32), ls=c(scene.log_scale, np.float32),
+                         q=c(scene.quat, np.float32), lg=c(scene.opacity_logit, np.float32),
+                         col=c(scene.colour, np.float32), res=c(scene.res, np.float32))
+        k = self.keep
+        if k["u"].size == 0:
+            k["u"] = np.zeros(3, np.float32)
+        if k["res"].size == 0:
+            k["res"] = np.zeros(1, np.float32)
+        self.s = _OScene(scene.n, scene.n_clusters, scene.n_layers, scene.sh_degree,
+                         scene.temporal_rank, k["offs"].ctypes.data, k["mu0"].ctypes.data,
+                         k["u"].ctypes.data, k["ls"].ctypes.data, k["q"].ctypes.data,
+                         k["lg"].ctypes.data, k["col"].ctypes.data, k["res"].ctypes.data)
+
+
+def _cam(cam) -> _OCam:
+    R = np.asarray(cam.R_wc, dtype=np.float64).reshape(9)
+    t = np.asarray(cam.t_wc, dtype=np.float64).reshape(3)
+    return _OCam((ctypes.c_double * 9)(*R), (ctypes.c_double * 3)(*t), float(cam.fx),
+                 float(cam.fy), float(cam.cx), float(cam.cy), int(cam.width), int(cam.height))
+
+
+def closure(mask_row: np.ndarray, n_clusters: int, n_layers: int) -> np.ndarray:
+    lib = _load()
+    m = np.ascontiguousarray(mask_row, dtype=np.uint32)
+    out = np.zeros(n_clusters, dtype=np.uint8)
+    lib.o_closure(n_clusters, n_layers, _ptr(m), _ptr(out))
+    return out
+
+
+def project(scene, depth: np.ndarray, t: float, cam) -> np.ndarray:
+    """Per-Gaussian FP64 projection, columns named by :data:`REC_FIELDS`."""
+    lib = _load()
+    pin = _Pinned(scene)
+    d = np.ascontiguousarray(depth, dtype=np.uint8)
+    out = np.zeros((scene.n, lib.o_rec_width()), dtype=np.float64)
+    oc = _cam(cam)
+    lib.o_project(ctypes.byref(pin.s), _ptr(d), float(t), ctypes.byref(oc), _ptr(out))
+    return out[:, :len(REC_FIELDS)]
+
+
+def render(scene, depth, t, cam, bg, pix=None, full_scan=False, eps=None):
+    """Render one state.  Returns (image FP64, marginal flags, evaluations).
+
+    ``pix`` = int array [P,2] of (x, y) samples, else the whole [H,W,3] image."""
+    lib = _load()
+    pin = _Pinned(scene)
+    d = np.ascontiguousarray(depth, dtype=np.uint8)
+    oc = _cam(cam)
+    bgd = np.ascontiguousarray(bg, dtype=np.float64)
+    n_eval = np.zeros(1, np.int64)
+    e = None if eps is None else _OEps(*eps)
+    if pix is None:
+        img = np.zeros((cam.height, cam.width, 3), np.float64)
+        marg = np.zeros((cam.height, cam.width), np.uint8)
+        lib.o_render(ctypes.byref(pin.s), _ptr(d), float(t), ctypes.byref(oc), _ptr(bgd), 0,
+                     None, _ptr(img), _ptr(marg), _ptr(n_eval), int(full_scan),
+                     ctypes.byref(e) if e else None)
+    else:
+        p = np.ascontiguousarray(pix, dtype=np.int32).reshape(-1, 2)
+        img = np.zeros((p.shape[0], 3), np.float64)
+        marg = np.zeros(p.shape[0], np.uint8)
+        lib.o_render(ctypes.byref(pin.s), _ptr(d), float(t), ctypes.byref(oc), _ptr(bgd),
+                     p.shape[0], _ptr(p), _ptr(img), _ptr(marg), _ptr(n_eval), 1,
+                     ctypes.byref(e) if e else None)
+    return img, marg.astype(bool), int(n_eval[0])
+
+
+def state_depths(states, n_clusters, n_layers) -> np.ndarray:
+    return np.stack([closure(states.masks[s], n_clusters, n_layers) for s in range(states.n)])
+
+
+def render_states(scene, states, cams, bg, which=None):
+    """Serial evaluation of every state (the definition batched rendering must equal)."""
+    D = state_depths(states, scene.n_clusters, scene.n_layers)
+    idx = range(states.n) if which is None else which
+    out = []
+    for s in idx:
+        cam = cams[int(states.cam[s])]
+        out.append(render(scene, D[s], float(states.t[s]), cam, bg))
+    return out
+
+
+def full_depth(scene) -> np.ndarray:
+    return np.full(scene.n_clusters, scene.n_layers, dtype=np.uint8)
+
+
+def mse_psnr(image: np.ndarray, ref: np.ndarray):
+    """Eq. 3's D as mean squared error over all channels (FP64) and PSNR (peak 1)."""
+    diff = np.asarray(image, np.float64) - np.asarray(ref, np.float64)
+    mse = float(np.mean(diff * diff))
+    psnr = float("inf") if mse == 0.0 else 10.0 * np.log10(1.0 / mse)
+    return mse, psnr
+
+
+def render_backward(scene, depth, t, cam, bg, dL_dimage, want_2d=False):
+    """Adjoint of :func:`render`; returns FP64 gradients in the scene layout."""
+    lib = _load()
+    pin = _Pinned(scene)
+    d = np.ascontiguousarray(depth, dtype=np.uint8)
+    oc = _cam(cam)
+    bgd = np.ascontiguousarray(bg, dtype=np.float64)
+    g = np.ascontiguousarray(dL_dimage, dtype=np.float64)
+    n, R, L = scene.n, scene.temporal_rank, scene.n_layers
+    out = dict(mu0=np.zeros((n, 3)), u=np.zeros((max(R, 1), n, 3)), log_scale=np.zeros((n, 3)),
+               quat=np.zeros((n, 4)), opacity_logit=np.zeros(n),
+               colour=np.zeros((n, scene.n_colour)),
+               res=np.zeros((max(L - 1, 1), n, scene.res_width)))
+    g2 = np.zeros((n, 9))
+    lib.o_render_backward(ctypes.byref(pin.s), _ptr(d), float(t), ctypes.byref(oc), _ptr(bgd),
+                          _ptr(g), _ptr(out["mu0"]), _ptr(out["u"]), _ptr(out["log_scale"]),
+                          _ptr(out["quat"]), _ptr(out["opacity_logit"]), _ptr(out["colour"]),
+                          _ptr(out["res"]), _ptr(g2))
+    out["u"] = out["u"][:R]
+    out["res"] = out["res"][:max(L - 1, 0)]
+    if want_2d:
+        out["g2d"] = g2
+    return out
+
+
+def sh_basis(direction, degree: int = 3) -> np.ndarray:
+    lib = _load()
+    d = np.ascontiguousarray(direction, dtype=np.float64)
+    Y = np.zeros(16, np.float64)
+    lib.o_sh_basis(_ptr(d), int(degree), _ptr(Y))
+    return Y[:(degree + 1) ** 2]
+
+
+def float_key(z32: np.ndarray) -> np.ndarray:
+    """Order-preserving uint32 image of positive float32 depths (their bit pattern)."""
+    return np.asarray(z32, dtype=np.float32).view(np.uint32)
+
+
+def bin_tiles(xlo, xhi, ylo, yhi, depth_bits, live, tile, tiles_x, tiles_y,
+              view_group=None, rank=None):
+    """Tile lists of live records (integer function).
+
+    Every live record r emits one entry per tile of its pixel box
+    [xlo, xhi] x [ylo, yhi]; the entries are ordered by the 64-bit key
+    (view_group * tiles + tile) << 32 | depth_bits, ties by ``rank`` (the record
+    order (Gaussian index, variant)).  Returns (keys uint64, values = record
+    index, ranges [V*tiles, 2])."""
+    n = len(xlo)
+    vg = np.zeros(n, np.int64) if view_group is None else np.asarray(view_group, np.int64)
+    rk = np.arange(n) if rank is None else np.asarray(rank, np.int64)
+    keys, vals = [], []
+    T = tiles_x * tiles_y
+    for r in np.nonzero(np.asarray(live))[0]:
+        for ty in range(int(ylo[r]) // tile, int(yhi[r]) // tile + 1):
+            for tx in range(int(xlo[r]) // tile, int(xhi[r]) // tile + 1):
+                key = ((int(vg[r]) * T + ty * tiles_x + tx) << 32) | int(depth_bits[r])
+                keys.append(key)
+                vals.append(r)
+    keys = np.array(keys, dtype=np.uint64)
+    vals = np.array(vals, dtype=np.int64)
+    order = np.lexsort((rk[vals] if len(vals) else vals, keys))
+    keys, vals = keys[order], vals[order]
+    nv = int(vg.max()) + 1 if n else 1
+    ranges = np.zeros((nv * T, 2), np.int64)
+    tid = (keys >> np.uint64(32)).astype(np.int64)
+    for k in range(nv * T):
+        lo = np.searchsorted(tid, k, side="left")
+        hi = np.searchsorted(tid, k, side="right")
+        ranges[k] = (lo, hi)
+    return keys, vals, ranges

@@ -1,0 +1,302 @@
+"""Seeded synthetic inputs: dynamic Gaussian scenes, delivery masks, times and cameras.
+
+This module only draws inputs.  It holds none of the renderer's arithmetic (no
+decode, deformation, projection, compositing or scoring); both the CUDA library
+and the FP64 oracle consume what it produces, and random numbers the method
+would draw (masks, times, erasures) are drawn here and passed in as inputs.
+
+Scene layout (the layout the C-ABI takes, Section 3 of the paper: N Gaussians
+with base attributes plus three additive refinements, grouped in clusters):
+
+* Gaussians are stored cluster-contiguous; ``cluster_offsets[c]:cluster_offsets[c+1]``
+  are the Gaussians of cluster ``c``.
+* ``mu0 [n,3]``, ``u [R,n,3]`` (the per-Gaussian temporal coefficients q_{i,r} of
+  Eq. 1), ``log_scale [n,3]``, ``quat [n,4]`` (w,x,y,z), ``opacity_logit [n]``,
+  ``colour [n, 3*(sh+1)^2]`` (SH coefficient-major, 3 channels innermost).
+* ``res [L-1, n, K]`` with ``K = 11 + 3*(sh+1)^2``: per refinement layer l=1..L-1
+  the residual vector (dmu[3], dlog_scale[3], dquat[4], dlogit[1], dcolour[...]).
+* A delivery state is a bitmask with bit ``c*L + l`` set when packet (cluster c,
+  layer l) arrived, packed little-endian into uint32 words, plus a time t and a
+  camera index.
+
+Distributions follow the workload descriptions of the benchmark configurations:
+means ~N(0,1)^3, log-scales ~N(-3.5,0.4), random unit quaternions, opacity
+logits ~N(0,1.5), RGB ~U[0,1] (SH degree 0) or 48 SH coefficients ~N(0,0.2^2)
+(degree 3), temporal coefficients ~N(0,0.1^2), residual std 0.05 halving per
+layer.  Cameras are OpenCV pinholes (x right, y down, z forward) on a ring of
+radius 4 in the z=0 plane looking at the origin with world up +z.
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+
+__all__ = [
+    "Scene", "Camera", "States", "Workload",
+    "make_scene", "ring_camera", "prefix_states", "bernoulli_states",
+    "erase_one_packet", "mask_words", "config", "CONFIG_NAMES",
+]
+
+
+@dataclasses.dataclass
+class Scene:
+    n: int
+    n_clusters: int
+    n_layers: int
+    sh_degree: int
+    temporal_rank: int
+    cluster_offsets: np.ndarray  # int32 [C+1]
+    mu0: np.ndarray              # f32 [n,3]
+    u: np.ndarray                # f32 [R,n,3]
+    log_scale: np.ndarray        # f32 [n,3]
+    quat: np.ndarray             # f32 [n,4]
+    opacity_logit: np.ndarray    # f32 [n]
+    colour: np.ndarray           # f32 [n, 3*(sh+1)^2]
+    res: np.ndarray              # f32 [L-1, n, K]
+
+    @property
+    def n_colour(self) -> int:
+        return 3 * (self.sh_degree + 1) ** 2
+
+    @property
+    def res_width(self) -> int:
+        return 11 + self.n_colour
+
+    def cluster_of(self) -> np.ndarray:
+        sizes = np.diff(self.cluster_offsets)
+        return np.repeat(np.arange(self.n_clusters, dtype=np.int32), sizes)
+
+    def subset(self, idx: np.ndarray) -> "Scene":
+        """Scene restricted to Gaussians ``idx`` (sorted), clusters kept."""
+        idx = np.sort(np.asarray(idx, dtype=np.int64))
+        cl = self.cluster_of()[idx]
+        counts = np.bincount(cl, minlength=self.n_clusters)
+        offs = np.zeros(self.n_clusters + 1, dtype=np.int32)
+        offs[1:] = np.cumsum(counts)
+        return Scene(len(idx), self.n_clusters, self.n_layers, self.sh_degree,
+                     self.temporal_rank, offs, self.mu0[idx].copy(),
+                     self.u[:, idx].copy(), self.log_scale[idx].copy(),
+                     self.quat[idx].copy(), self.opacity_logit[idx].copy(),
+                     self.colour[idx].copy(), self.res[:, idx].copy())
+
+    def arrays(self):
+        return dict(mu0=self.mu0, u=self.u, log_scale=self.log_scale, quat=self.quat,
+                    opacity_logit=self.opacity_logit, colour=self.colour, res=self.res)
+
+
+@dataclasses.dataclass
+class Camera:
+    R_wc: np.ndarray   # f32 [3,3] world -> camera rotation (row-major)
+    t_wc: np.ndarray   # f32 [3]
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    width: int
+    height: int
+
+
+@dataclasses.dataclass
+class States:
+    masks: np.ndarray  # uint32 [S, words]
+    t: np.ndarray      # f32 [S]
+    cam: np.ndarray    # int32 [S]
+
+    @property
+    def n(self) -> int:
+        return int(self.masks.shape[0])
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    scene: Scene
+    cams: list
+    states: States
+    bg: np.ndarray               # f32 [3]
+    target_scene: Scene | None = None   # teacher scene for training targets
+
+
+def mask_words(n_clusters: int, n_layers: int) -> int:
+    return (n_clusters * n_layers + 31) // 32
+
+
+def _kmeans(x: np.ndarray, k: int, rng: np.random.Generator, iters: int = 8) -> np.ndarray:
+    """Seeded Lloyd iterations; returns a cluster id per row (input grouping only)."""
+    n = x.shape[0]
+    k = min(k, n)
+    cent = x[rng.choice(n, size=k, replace=False)].astype(np.float64)
+    assign = np.zeros(n, dtype=np.int64)
+    chunk = 1 << 16
+    for _ in range(iters):
+        c2 = (cent * cent).sum(1)
+        for s in range(0, n, chunk):
+            xs = x[s:s + chunk].astype(np.float64)
+            d = c2[None, :] - 2.0 * xs @ cent.T
+            assign[s:s + chunk] = np.argmin(d, axis=1)
+        for j in range(k):
+            sel = assign == j
+            if sel.any():
+                cent[j] = x[sel].mean(0)
+    return assign
+
+
+def make_scene(n: int, n_clusters: int, n_layers: int, *, seed: int,
+               temporal_rank: int = 2, sh_degree: int = 0,
+               residual_std: float = 0.05, residual_attrs: str = "all",
+               mean_std: float = 1.0, log_scale_mean: float = -3.5,
+               log_scale_std: float = 0.4, logit_std: float = 1.5,
+               u_std: float = 0.1, sh_std: float = 0.2) -> Scene:
+    """Draw a scene; ``residual_attrs`` is "all" or "colour_opacity"."""
+    rng = np.random.default_rng(seed)
+    mu0 = rng.normal(0.0, mean_std, size=(n, 3))
+    ls = rng.normal(log_scale_mean, log_scale_std, size=(n, 3))
+    q = rng.normal(0.0, 1.0, size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    logit = rng.normal(0.0, logit_std, size=n)
+    nc = 3 * (sh_degree + 1) ** 2
+    if sh_degree == 0:
+        col = rng.uniform(0.0, 1.0, size=(n, 3))
+    else:
+        col = rng.normal(0.0, sh_std, size=(n, nc))
+    u = rng.normal(0.0, u_std, size=(temporal_rank, n, 3))
+    feats = mu0 if temporal_rank == 0 else np.concatenate(
+        [mu0] + [u[r] for r in range(temporal_rank)], axis=1)
+    assign = _kmeans(feats, n_clusters, rng)
+    K = 11 + nc
+    res = np.zeros((max(n_layers - 1, 0), n, K))
+    for l in range(1, n_layers):
+        std = residual_std * 2.0 ** (-(l - 1))
+        r = rng.normal(0.0, std, size=(n, K))
+        if residual_attrs == "colour_opacity":
+            r[:, 0:10] = 0.0
+        elif l == 1:
+            r[:, 0:3] = 0.0   # Eq. 1: position residuals only on the two finer levels
+        res[l - 1] = r
+    order = np.argsort(assign, kind="stable")
+    counts = np.bincount(assign, minlength=n_clusters)
+    offs = np.zeros(n_clusters + 1, dtype=np.int32)
+    offs[1:] = np.cumsum(counts)
+    f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    return Scene(n, n_clusters, n_layers, sh_degree, temporal_rank, offs,
+                 f32(mu0[order]), f32(u[:, order]), f32(ls[order]), f32(q[order]),
+                 f32(logit[order]), f32(col[order]), f32(res[:, order]))
+
+
+def ring_camera(k: int, n_ring: int, width: int, height: int, focal: float,
+                radius: float = 4.0) -> Camera:
+    """Pinhole at angle 2*pi*k/n_ring on a ring of ``radius``, looking at the origin."""
+    th = 2.0 * np.pi * k / n_ring
+    pos = np.array([radius * np.cos(th), radius * np.sin(th), 0.0])
+    fwd = -pos / np.linalg.norm(pos)
+    up = np.array([0.0, 0.0, 1.0])
+    right = np.cross(fwd, up)
+    right /= np.linalg.norm(right)
+    down = np.cross(fwd, right)
+    R = np.stack([right, down, fwd])
+    t = -R @ pos
+    return Camera(R.astype(np.float32), t.astype(np.float32), float(focal), float(focal),
+                  width / 2.0, height / 2.0, int(width), int(height))
+
+
+def _pack(bits: np.ndarray) -> np.ndarray:
+    """bits [S, C*L] bool -> uint32 [S, words], bit b in word b//32 at position b%32."""
+    S, nb = bits.shape
+    words = (nb + 31) // 32
+    out = np.zeros((S, words), dtype=np.uint64)
+    for b in range(nb):
+        out[:, b // 32] |= bits[:, b].astype(np.uint64) << np.uint64(b % 32)
+    return out.astype(np.uint32)
+
+
+def prefix_states(n_states: int, n_clusters: int, n_layers: int, rng: np.random.Generator,
+                  distinct: bool = False) -> np.ndarray:
+    """Prefix-valid masks: per cluster a delivered depth ~U{0..L}; returns depths [S,C]."""
+    d = rng.integers(0, n_layers + 1, size=(n_states, n_clusters))
+    if distinct:
+        while True:
+            _, first = np.unique(d, axis=0, return_index=True)
+            dup = np.setdiff1d(np.arange(n_states), first)
+            if dup.size == 0:
+                break
+            d[dup] = rng.integers(0, n_layers + 1, size=(dup.size, n_clusters))
+    return d
+
+
+def depths_to_bits(d: np.ndarray, n_layers: int) -> np.ndarray:
+    S, C = d.shape
+    lay = np.arange(n_layers)
+    return (lay[None, None, :] < d[:, :, None]).reshape(S, C * n_layers)
+
+
+def bernoulli_states(n_states: int, n_clusters: int, n_layers: int, rng: np.random.Generator,
+                     p: float = 0.5) -> np.ndarray:
+    return rng.uniform(size=(n_states, n_clusters * n_layers)) < p
+
+
+def erase_one_packet(bits: np.ndarray, frac: float, rng: np.random.Generator) -> np.ndarray:
+    """For a fraction of states clear one delivered packet chosen uniformly."""
+    bits = bits.copy()
+    S = bits.shape[0]
+    chosen = rng.uniform(size=S) < frac
+    for s in np.nonzero(chosen)[0]:
+        on = np.nonzero(bits[s])[0]
+        if on.size:
+            bits[s, rng.choice(on)] = False
+    return bits
+
+
+CONFIG_NAMES = ("c1_plain_4k", "c2_dynamic_250k", "c3_fwdbwd_250k", "c4_utility_2p7m")
+
+
+def config(name: str, *, scale: float = 1.0, n_states: int | None = None) -> Workload:
+    """The benchmark workloads.  ``scale`` < 1 shrinks Gaussians and image sides
+    (for oracle-sized parity cases); ``n_states`` overrides the state count."""
+    def nn(n):
+        return max(16, int(round(n * scale)))
+
+    def px(w):
+        return max(16, int(round(w * np.sqrt(scale)))) if scale < 1.0 else w
+
+    if name == "c1_plain_4k":
+        sc = make_scene(4096, 8, 2, seed=1001, temporal_rank=0, residual_attrs="colour_opacity")
+        rng = np.random.default_rng(2001)
+        S = n_states or 1
+        bits = bernoulli_states(S, 8, 2, rng)
+        st = States(_pack(bits), np.zeros(S, np.float32), np.zeros(S, np.int32))
+        cams = [ring_camera(0, 1, 128, 128, 150.0)]
+        return Workload(name, sc, cams, st, np.zeros(3, np.float32))
+    if name == "c2_dynamic_250k":
+        sc = make_scene(nn(250_000), 32, 4, seed=1002)
+        rng = np.random.default_rng(2002)
+        S = n_states or 256
+        d = prefix_states(S, 32, 4, rng)
+        t = (np.arange(S) % 16) / 16.0
+        W = px(800)
+        cams = [ring_camera(0, 1, W, W, 960.0 * W / 800)]
+        st = States(_pack(depths_to_bits(d, 4)), t.astype(np.float32), np.zeros(S, np.int32))
+        return Workload(name, sc, cams, st, np.zeros(3, np.float32))
+    if name == "c3_fwdbwd_250k":
+        sc = make_scene(nn(250_000), 64, 4, seed=1003)
+        teacher = make_scene(nn(250_000), 64, 4, seed=4003)
+        rng = np.random.default_rng(2003)
+        S = n_states or 64
+        d = prefix_states(S, 64, 4, rng)
+        bits = erase_one_packet(depths_to_bits(d, 4), 0.10, rng)
+        rng_t = np.random.default_rng(3003)
+        t = rng_t.integers(0, 16, size=S) / 16.0
+        W = px(512)
+        cams = [ring_camera(k, 8, W, W, 600.0 * W / 512) for k in range(8)]
+        st = States(_pack(bits), t.astype(np.float32), (np.arange(S) % 8).astype(np.int32))
+        return Workload(name, sc, cams, st, np.zeros(3, np.float32), target_scene=teacher)
+    if name == "c4_utility_2p7m":
+        sc = make_scene(nn(2_700_000), 64, 4, seed=1004)
+        rng = np.random.default_rng(2004)
+        S = n_states or 32768
+        d = prefix_states(S, 64, 4, rng, distinct=True)
+        W, H = (px(480), px(270))
+        cams = [ring_camera(0, 1, W, H, 520.0 * W / 480)]
+        st = States(_pack(depths_to_bits(d, 4)), np.full(S, 0.25, np.float32),
+                    np.zeros(S, np.int32))
+        return Workload(name, sc, cams, st, np.zeros(3, np.float32))
+    raise KeyError(name)

@@ -1,0 +1,509 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these re-derive the oracle's own formulas: each checks it against a
+closed form, a brute-force restatement, an invariant of the paper's
+delivery-state semantics, or central finite differences.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_17212_b300 import synth
+
+
+def tiny_scene(mu, log_scale, quat, logit, colour, n_layers=1, res=None, u=None,
+               clusters=None, sh_degree=0):
+    n = len(mu)
+    nc = 3 * (sh_degree + 1) ** 2
+    if clusters is None:
+        clusters = np.zeros(n, np.int64)
+    C = int(np.max(clusters)) + 1
+    order = np.argsort(clusters, kind="stable")
+    assert np.all(order == np.arange(n)), "tiny scenes are built cluster-contiguous"
+    offs = np.zeros(C + 1, np.int32)
+    offs[1:] = np.cumsum(np.bincount(clusters, minlength=C))
+    f = lambda a: np.ascontiguousarray(a, np.float32)
+    R = 0 if u is None else len(u)
+    K = 11 + nc
+    return synth.Scene(n, C, n_layers, sh_degree, R, offs, f(mu),
+                       f(np.zeros((0, n, 3)) if u is None else u), f(log_scale), f(quat),
+                       f(logit), f(colour),
+                       f(np.zeros((n_layers - 1, n, K)) if res is None else res))
+
+
+def axis_camera(W=128, H=128, f=128.0):
+    """Camera at (4,0,0) looking at the origin: image x = world y, image y = -world z."""
+    return synth.ring_camera(0, 1, W, H, f)
+
+
+def logit_of(o):
+    return math.log(o / (1.0 - o))
+
+
+def rodrigues(axis, angle):
+    a = np.asarray(axis, np.float64)
+    a = a / np.linalg.norm(a)
+    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    return np.eye(3) + math.sin(angle) * K + (1 - math.cos(angle)) * K @ K
+
+
+# ---------------------------------------------------------------- closure
+def test_closure_prefix_semantics():
+    """Section 4 / 7.4: a layer is usable only when every layer below it is."""
+    rng = np.random.default_rng(0)
+    C, L = 9, 4
+    for _ in range(200):
+        bits = rng.uniform(size=C * L) < 0.6
+        words = np.zeros(2, np.uint32)
+        for b in np.nonzero(bits)[0]:
+            words[b // 32] |= np.uint32(1 << (b % 32))
+        d = oracle.closure(words, C, L)
+        for c in range(C):
+            row = bits[c * L:(c + 1) * L]
+            assert 0 <= d[c] <= L
+            assert row[:d[c]].all()                       # everything below is delivered
+            assert d[c] == L or not row[d[c]]            # the first gap stops it
+            # monotone: delivering any extra packet never lowers the depth
+            for l in range(L):
+                w2 = words.copy()
+                b = c * L + l
+                w2[b // 32] |= np.uint32(1 << (b % 32))
+                assert oracle.closure(w2, C, L)[c] >= d[c]
+
+
+def test_closure_of_prefix_masks_is_identity():
+    rng = np.random.default_rng(1)
+    d = synth.prefix_states(50, 7, 4, rng)
+    masks = synth._pack(synth.depths_to_bits(d, 4))
+    for s in range(50):
+        assert np.array_equal(oracle.closure(masks[s], 7, 4), d[s])
+
+
+# ---------------------------------------------------------------- closed forms
+def _one_gaussian_at_pixel_centre(o=0.7, colour=(0.9, 0.2, 0.4), z_c=4.0):
+    # ray through pixel (64,64)'s centre (64.5, 64.5): x_c/z_c = y_c/z_c = 1/256
+    mu = [[4.0 - z_c, z_c / 256.0, -z_c / 256.0]]
+    return mu, o, colour
+
+
+def test_single_gaussian_centre_pixel_closed_form():
+    """One Gaussian whose mean sits on a pixel centre: C = o c + (1 - o) bg."""
+    mu, o, col = _one_gaussian_at_pixel_centre()
+    sc = tiny_scene(mu, [[-2.5] * 3], [[1, 0, 0, 0]], [logit_of(o)], [col])
+    bg = np.array([0.1, 0.3, 0.05])
+    img, marg, _ = oracle.render(sc, np.array([1], np.uint8), 0.0, axis_camera(), bg)
+    o32 = 1.0 / (1.0 + math.exp(-float(np.float32(logit_of(o)))))
+    expect = o32 * np.array(col, np.float32).astype(np.float64) + (1 - o32) * bg
+    assert np.allclose(img[64, 64], expect, rtol=0, atol=1e-12)
+    assert not marg[64, 64]
+
+
+def test_two_gaussians_on_one_ray_closed_form():
+    """Front-to-back order by depth, not by index: the nearer one is index 1."""
+    o1, o2 = 0.6, 0.8
+    c_far, c_near = (0.2, 0.9, 0.1), (0.7, 0.1, 0.3)
+    mu = [[4.0 - 3.0, 3.0 / 256, -3.0 / 256], [4.0 - 2.0, 2.0 / 256, -2.0 / 256]]
+    sc = tiny_scene(mu, [[-3.0] * 3] * 2, [[1, 0, 0, 0]] * 2, [logit_of(o2), logit_of(o1)],
+                    [c_far, c_near])
+    bg = np.array([0.05, 0.05, 0.5])
+    img, marg, _ = oracle.render(sc, np.array([1], np.uint8), 0.0, axis_camera(), bg)
+    sig = lambda x: 1.0 / (1.0 + math.exp(-float(np.float32(x))))
+    a1, a2 = sig(logit_of(o1)), sig(logit_of(o2))
+    c1 = np.array(c_near, np.float32).astype(float)
+    c2 = np.array(c_far, np.float32).astype(float)
+    expect = a1 * c1 + (1 - a1) * a2 * c2 + (1 - a1) * (1 - a2) * bg
+    assert np.allclose(img[64, 64], expect, atol=1e-12)
+
+
+def test_on_axis_covariance_and_radius_closed_form():
+    """On the optical axis J = diag(f/z, f/z) | 0, so Sigma2D = (f/z)^2 [W Sigma3 W^T]_2x2 + 0.3 I."""
+    rng = np.random.default_rng(5)
+    cam = axis_camera()
+    f, z = 128.0, 4.0
+    for trial in range(20):
+        ls = rng.normal(-3.0, 0.4, size=3)
+        axis = rng.normal(size=3)
+        ang = rng.uniform(0, np.pi)
+        axis = axis / np.linalg.norm(axis)
+        q = np.concatenate([[math.cos(ang / 2)], math.sin(ang / 2) * axis])
+        sc = tiny_scene([[0.0, 0.0, 0.0]], [ls], [q], [0.0], [[0.5, 0.5, 0.5]])
+        rec = oracle.project(sc, np.array([1], np.uint8), 0.0, cam)[0]
+        Rr = rodrigues(axis, ang)
+        s = np.exp(np.float32(ls).astype(np.float64))
+        S3 = Rr @ np.diag(s * s) @ Rr.T
+        W = cam.R_wc.astype(np.float64)
+        S2 = (f / z) ** 2 * (W @ S3 @ W.T)[:2, :2] + 0.3 * np.eye(2)
+        conic = np.linalg.inv(S2)
+        qf = np.float32(q).astype(np.float64)
+        # the float32 quaternion is the input; rebuild the exact rotation it encodes
+        qf = qf / np.linalg.norm(qf)
+        ang_f = 2 * math.acos(max(-1.0, min(1.0, qf[0])))
+        ax_f = qf[1:] / max(np.linalg.norm(qf[1:]), 1e-300)
+        Rr = rodrigues(ax_f, ang_f)
+        S3 = Rr @ np.diag(s * s) @ Rr.T
+        S2 = (f / z) ** 2 * (W @ S3 @ W.T)[:2, :2] + 0.3 * np.eye(2)
+        conic = np.linalg.inv(S2)
+        got = np.array([[rec[3], rec[4]], [rec[4], rec[5]]])
+        assert np.allclose(got, conic, rtol=1e-9, atol=1e-12), (trial, got, conic)
+        lam = np.linalg.eigvalsh(S2).max()
+        assert rec[11] == math.ceil(3 * math.sqrt(lam))
+        assert rec[1] == pytest.approx(64.0, abs=1e-12) and rec[2] == pytest.approx(64.0, abs=1e-12)
+
+
+def test_neighbour_pixel_falloff_closed_form():
+    """Axis-aligned Gaussian on the axis: alpha at pixel offsets follows the dilated conic."""
+    cam = axis_camera()
+    ls = np.array([-3.2, -2.9, -3.4], np.float32)
+    o = 0.9
+    sc = tiny_scene([[0.0, 0.0, 0.0]], [ls], [[1, 0, 0, 0]], [logit_of(o)], [[1.0, 1.0, 1.0]])
+    img, _, _ = oracle.render(sc, np.array([1], np.uint8), 0.0, cam, np.zeros(3))
+    s = np.exp(ls.astype(np.float64))
+    # image x = world y, image y = -world z
+    vx = (128.0 / 4.0 * s[1]) ** 2 + 0.3
+    vy = (128.0 / 4.0 * s[2]) ** 2 + 0.3
+    o32 = 1.0 / (1.0 + math.exp(-float(np.float32(logit_of(o)))))
+    for kx, ky in [(0, 0), (1, 0), (2, 1), (-3, 0), (0, -2), (2, 2)]:
+        dx, dy = 64 + kx + 0.5 - 64.0, 64 + ky + 0.5 - 64.0
+        a = min(0.99, o32 * math.exp(-0.5 * (dx * dx / vx + dy * dy / vy)))
+        expect = a if a >= 1 / 255 else 0.0
+        assert img[64 + ky, 64 + kx, 0] == pytest.approx(expect, abs=1e-12), (kx, ky)
+
+
+def _num_jacobian(cam, p):
+    """Finite-difference Jacobian of the pinhole image position w.r.t. world position."""
+    def proj(x):
+        sc = tiny_scene([x], [[-4.0] * 3], [[1, 0, 0, 0]], [0.0], [[0.5] * 3])
+        r = oracle.project(sc, np.array([1], np.uint8), 0.0, cam)[0]
+        return np.array([r[1], r[2]])
+    J = np.zeros((2, 3))
+    h = 1e-3
+    for k in range(3):
+        e = np.zeros(3); e[k] = h
+        hi = np.float32(p + e).astype(np.float64)   # the oracle reads float32 inputs:
+        lo = np.float32(p - e).astype(np.float64)   # divide by the step actually taken
+        J[:, k] = (proj(hi) - proj(lo)) / (hi[k] - lo[k])
+    return J
+
+
+def test_off_axis_covariance_matches_linearised_projection():
+    """EWA: Sigma2D = Jp Sigma3 Jp^T + 0.3 I with Jp the derivative of the projection
+    (taken here numerically), evaluated at the clamped direction outside 1.3 x FOV."""
+    rng = np.random.default_rng(7)
+    cam = synth.ring_camera(1, 8, 160, 120, 150.0)
+    for trial in range(12):
+        if trial < 8:
+            p = rng.normal(0, 0.6, size=3)
+        else:  # far outside the clamp on image x
+            p = np.array(cam.R_wc, np.float64).T @ (np.array([5.0, 0.3, 3.0]) - cam.t_wc.astype(np.float64))
+        p = np.float32(p).astype(np.float64)
+        ls = np.float32(rng.normal(-3.0, 0.3, size=3))
+        q = rng.normal(size=4); q /= np.linalg.norm(q)
+        q = np.float32(q)
+        sc = tiny_scene([p], [ls], [q], [0.0], [[0.5] * 3])
+        rec = oracle.project(sc, np.array([1], np.uint8), 0.0, cam)[0]
+        W = cam.R_wc.astype(np.float64)
+        pc = W @ p + cam.t_wc.astype(np.float64)
+        limx = 1.3 * (cam.width / 2) / cam.fx
+        limy = 1.3 * (cam.height / 2) / cam.fy
+        pcl = pc.copy()
+        pcl[0] = np.clip(pc[0] / pc[2], -limx, limx) * pc[2]
+        pcl[1] = np.clip(pc[1] / pc[2], -limy, limy) * pc[2]
+        pw = W.T @ (pcl - cam.t_wc.astype(np.float64))
+        Jp = _num_jacobian(cam, pw)
+        qd = q.astype(np.float64); qd /= np.linalg.norm(qd)
+        ang = 2 * math.acos(np.clip(qd[0], -1, 1))
+        Rr = rodrigues(qd[1:] if np.linalg.norm(qd[1:]) > 0 else [1, 0, 0], ang)
+        s = np.exp(ls.astype(np.float64))
+        S3 = Rr @ np.diag(s * s) @ Rr.T
+        S2 = Jp @ S3 @ Jp.T + 0.3 * np.eye(2)
+        got = np.linalg.inv(np.array([[rec[3], rec[4]], [rec[4], rec[5]]]))
+        assert np.allclose(got, S2, rtol=2e-5, atol=1e-9), (trial, got, S2)
+
+
+# ---------------------------------------------------------------- brute force
+def test_row_filter_equals_full_scan():
+    w = synth.config("c1_plain_4k")
+    sc = w.scene
+    D = oracle.state_depths(w.states, sc.n_clusters, sc.n_layers)
+    a = oracle.render(sc, D[0], 0.0, w.cams[0], w.bg)
+    b = oracle.render(sc, D[0], 0.0, w.cams[0], w.bg, full_scan=True)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2]
+
+
+def test_composite_equals_product_form_brute_force():
+    """Tiny scenes: C = sum_k c_k a_k prod_{j<k}(1-a_j) + prod(1-a_j) bg over the
+    included list, recomputed in Python from the projected records."""
+    rng = np.random.default_rng(11)
+    cam = synth.ring_camera(0, 1, 32, 32, 40.0)
+    for trial in range(4):
+        n = 16
+        mu = rng.normal(0, 0.5, size=(n, 3))
+        ls = rng.normal(-2.0, 0.3, size=(n, 3))
+        q = rng.normal(size=(n, 4)); q /= np.linalg.norm(q, axis=1, keepdims=True)
+        lg = rng.normal(0, 1.5, size=n)
+        col = rng.uniform(size=(n, 3))
+        sc = tiny_scene(mu, ls, q, lg, col)
+        bg = rng.uniform(size=3)
+        d = np.array([1], np.uint8)
+        img, marg, _ = oracle.render(sc, d, 0.0, cam, bg)
+        rec = oracle.project(sc, d, 0.0, cam)
+        live = np.nonzero(rec[:, 0] > 0)[0]
+        order = sorted(live, key=lambda i: (np.float32(rec[i, 6]), i))
+        for py in range(32):
+            for px in range(32):
+                alphas, cols = [], []
+                for i in order:
+                    r = rec[i]
+                    if not (r[12] <= px <= r[13] and r[14] <= py <= r[15]):
+                        continue
+                    dx, dy = r[1] - (px + 0.5), r[2] - (py + 0.5)
+                    pw = -0.5 * (r[3] * dx * dx + r[5] * dy * dy) - r[4] * dx * dy
+                    if pw > 0:
+                        continue
+                    a = min(0.99, r[7] * math.exp(pw))
+                    if a < 1 / 255:
+                        continue
+                    if np.prod([1 - x for x in alphas + [a]]) < 1e-4:
+                        break
+                    alphas.append(a); cols.append(r[8:11])
+                acc = np.zeros(3)
+                for k, (a, c) in enumerate(zip(alphas, cols)):
+                    acc += np.asarray(c) * a * np.prod([1 - x for x in alphas[:k]])
+                acc += np.prod([1 - x for x in alphas]) * bg
+                assert np.allclose(img[py, px], acc, atol=1e-12), (trial, px, py)
+
+
+def test_tile_lists_brute_force():
+    """bin_tiles == per tile, every record whose pixel box meets the tile, by (depth bits, rank)."""
+    rng = np.random.default_rng(3)
+    n, tile, tx, ty = 300, 16, 5, 4
+    W, H = 70, 60
+    xlo = rng.integers(0, W, n); xhi = np.minimum(W - 1, xlo + rng.integers(0, 30, n))
+    ylo = rng.integers(0, H, n); yhi = np.minimum(H - 1, ylo + rng.integers(0, 30, n))
+    z = rng.uniform(0.5, 8.0, n).astype(np.float32)
+    z[::7] = z[3]                       # exact depth ties
+    live = rng.uniform(size=n) < 0.9
+    vg = rng.integers(0, 3, n)
+    keys, vals, ranges = oracle.bin_tiles(xlo, xhi, ylo, yhi, oracle.float_key(z), live, tile,
+                                          tx, ty, view_group=vg)
+    for v in range(3):
+        for t in range(tx * ty):
+            x0, y0 = (t % tx) * tile, (t // tx) * tile
+            brute = [r for r in range(n) if live[r] and vg[r] == v
+                     and xlo[r] <= x0 + tile - 1 and xhi[r] >= x0
+                     and ylo[r] <= y0 + tile - 1 and yhi[r] >= y0]
+            brute.sort(key=lambda r: (z[r], r))
+            lo, hi = ranges[v * tx * ty + t]
+            assert list(vals[lo:hi]) == brute
+
+
+# ---------------------------------------------------------------- invariants
+def _c1_like():
+    w = synth.config("c1_plain_4k")
+    return w.scene, w.cams[0], w.bg
+
+
+def test_empty_delivery_is_background():
+    sc, cam, _ = _c1_like()
+    bg = np.array([0.2, 0.4, 0.6])
+    img, marg, ne = oracle.render(sc, np.zeros(sc.n_clusters, np.uint8), 0.0, cam, bg)
+    assert np.all(img == bg) and not marg.any() and ne == 0
+
+
+def test_full_delivery_equals_complete_render_and_mse_zero():
+    sc, cam, bg = _c1_like()
+    words = synth.mask_words(sc.n_clusters, sc.n_layers)
+    full_mask = np.full(words, 0xFFFFFFFF, np.uint32)
+    a = oracle.render(sc, oracle.closure(full_mask, sc.n_clusters, sc.n_layers), 0.0, cam, bg)
+    b = oracle.render(sc, oracle.full_depth(sc), 0.0, cam, bg)
+    assert np.array_equal(a[0], b[0])
+    mse, psnr = oracle.mse_psnr(a[0], b[0])
+    assert mse == 0.0 and psnr == float("inf")
+
+
+def test_mse_psnr_definition():
+    a = np.zeros((4, 5, 3)); b = np.full((4, 5, 3), 0.1)
+    mse, psnr = oracle.mse_psnr(a, b)
+    assert mse == pytest.approx(0.01, rel=1e-12) and psnr == pytest.approx(20.0, rel=1e-12)
+
+
+def test_undelivered_packets_never_change_a_pixel():
+    """Packets above a gap, and the residual data of undelivered layers, are invisible."""
+    rng = np.random.default_rng(21)
+    w = synth.config("c2_dynamic_250k", scale=0.02, n_states=4)
+    sc, cam = w.scene, w.cams[0]
+    C, L = sc.n_clusters, sc.n_layers
+    d = rng.integers(0, L, size=C)        # at most L-1: layer d is a gap
+    bits = synth.depths_to_bits(d[None], L)[0]
+    base_mask = synth._pack(bits[None])[0]
+    ref = oracle.render(sc, oracle.closure(base_mask, C, L), 0.3, cam, w.bg)
+    # deliver random packets strictly above each cluster's gap
+    extra = bits.copy()
+    for c in range(C):
+        for l in range(d[c] + 1, L):
+            extra[c * L + l] = rng.uniform() < 0.7
+    m2 = synth._pack(extra[None])[0]
+    got = oracle.render(sc, oracle.closure(m2, C, L), 0.3, cam, w.bg)
+    assert np.array_equal(ref[0], got[0])
+    # poison the residual layers no cluster uses
+    res = sc.res.copy()
+    cl = sc.cluster_of()
+    for i in range(sc.n):
+        res[d[cl[i]]:, i, :] = np.nan    # layers l >= d (index l-1 >= d-1 ... keep l < d)
+        if d[cl[i]] >= 1:
+            res[:d[cl[i]] - 1, i, :] = sc.res[:d[cl[i]] - 1, i, :]
+    poisoned = synth.Scene(**{**sc.__dict__, "res": res})
+    got2 = oracle.render(poisoned, oracle.closure(base_mask, C, L), 0.3, cam, w.bg)
+    assert np.array_equal(ref[0], got2[0])
+
+
+def test_decode_is_base_plus_delivered_refinements():
+    """Rendering at depth d equals rendering a base-only scene whose base already
+    holds base + res_1 + ... + res_{d-1} (Section 3)."""
+    w = synth.config("c2_dynamic_250k", scale=0.02, n_states=1)
+    sc, cam = w.scene, w.cams[0]
+    for d in range(1, sc.n_layers + 1):
+        depth = np.full(sc.n_clusters, d, np.uint8)
+        ref, marg, _ = oracle.render(sc, depth, 0.0, cam, w.bg)
+        acc = sc.res[:d - 1].astype(np.float64).sum(0)
+        nb = synth.Scene(sc.n, sc.n_clusters, 1, sc.sh_degree, sc.temporal_rank,
+                         sc.cluster_offsets,
+                         (sc.mu0 + acc[:, 0:3]).astype(np.float32), sc.u,
+                         (sc.log_scale + acc[:, 3:6]).astype(np.float32),
+                         (sc.quat + acc[:, 6:10]).astype(np.float32),
+                         (sc.opacity_logit + acc[:, 10]).astype(np.float32),
+                         (sc.colour + acc[:, 11:]).astype(np.float32),
+                         np.zeros((0, sc.n, sc.res_width), np.float32))
+        got, marg2, _ = oracle.render(nb, np.ones(sc.n_clusters, np.uint8), 0.0, cam, w.bg)
+        ok = ~(marg | marg2)
+        assert ok.mean() > 0.98
+        assert np.abs(got - ref)[ok].max() < 1e-4
+
+
+def test_temporal_basis_order_and_period():
+    """Eq. 1 basis b1 = cos 2 pi t, b2 = sin 2 pi t: t = 0 moves by u1, t = 1/4 by u2,
+    and t + 1 renders like t."""
+    w = synth.config("c2_dynamic_250k", scale=0.02, n_states=1)
+    sc, cam = w.scene, w.cams[0]
+    depth = np.ones(sc.n_clusters, np.uint8)
+    for t, k in [(0.0, 0), (0.25, 1)]:
+        ref, m1, _ = oracle.render(sc, depth, t, cam, w.bg)
+        moved = synth.Scene(**{**sc.__dict__, "temporal_rank": 0,
+                               "u": np.zeros((0, sc.n, 3), np.float32),
+                               "mu0": (sc.mu0.astype(np.float64) + sc.u[k]).astype(np.float32)})
+        got, m2, _ = oracle.render(moved, depth, 0.0, cam, w.bg)
+        ok = ~(m1 | m2)
+        assert np.abs(got - ref)[ok].max() < 1e-4
+    a, ma, _ = oracle.render(sc, depth, 0.375, cam, w.bg)
+    b, mb, _ = oracle.render(sc, depth, 1.375, cam, w.bg)
+    ok = ~(ma | mb)
+    assert np.abs(a - b)[ok].max() < 1e-9
+
+
+# ---------------------------------------------------------------- SH
+def test_sh_basis_orthonormal_by_quadrature():
+    """Gauss-Legendre in cos(theta) x uniform phi integrates products exactly to degree 6."""
+    xs, ws = np.polynomial.legendre.leggauss(12)
+    nphi = 24
+    G = np.zeros((16, 16))
+    for z, wz in zip(xs, ws):
+        for k in range(nphi):
+            ph = 2 * np.pi * k / nphi
+            r = math.sqrt(1 - z * z)
+            Y = oracle.sh_basis([r * math.cos(ph), r * math.sin(ph), z], 3)
+            G += wz * (2 * np.pi / nphi) * np.outer(Y, Y)
+    assert np.allclose(G, np.eye(16), atol=1e-12)
+
+
+def test_sh_degree0_equivalence():
+    """SH3 colour with only the DC coefficient = SH0 colour Y00 k0 + 0.5."""
+    w = synth.config("c1_plain_4k")
+    sc = w.scene
+    rng = np.random.default_rng(4)
+    k0 = rng.normal(0, 0.5, size=(sc.n, 3)).astype(np.float32)
+    sh = np.zeros((sc.n, 48), np.float32); sh[:, :3] = k0
+    sc3 = synth.Scene(**{**sc.__dict__, "sh_degree": 3, "colour": sh,
+                         "res": np.zeros((1, sc.n, 59), np.float32)})
+    Y00 = 0.5 / math.sqrt(math.pi)
+    sc0 = synth.Scene(**{**sc.__dict__, "colour": (Y00 * k0.astype(np.float64) + 0.5).astype(np.float32),
+                         "res": np.zeros((1, sc.n, 14), np.float32)})
+    d = oracle.full_depth(sc)
+    a, ma, _ = oracle.render(sc3, d, 0.0, w.cams[0], w.bg)
+    b, mb, _ = oracle.render(sc0, d, 0.0, w.cams[0], w.bg)
+    ok = ~(ma | mb)
+    assert np.abs(a - b)[ok].max() < 1e-6
+
+
+# ---------------------------------------------------------------- adjoint
+def _fd_case(sh_degree=0, n=256, seed=9):
+    if sh_degree == 0:
+        w = synth.config("c3_fwdbwd_250k", scale=0.004, n_states=2)
+        sc = w.scene
+    else:
+        sc = synth.make_scene(n, 8, 4, seed=seed, sh_degree=3)
+        w = synth.config("c3_fwdbwd_250k", scale=0.004, n_states=2)
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(sc.n, size=min(n, sc.n), replace=False))
+    sub = sc.subset(idx)
+    cam = synth.ring_camera(1, 8, 48, 40, 60.0)
+    return sub, cam
+
+
+def _loss(sc, depth, t, cam, bg, target):
+    img, _, _ = oracle.render(sc, depth, t, cam, bg)
+    return float(np.mean((img - target) ** 2)), img
+
+
+@pytest.mark.parametrize("sh_degree", [0, 3])
+def test_adjoint_matches_central_differences(sh_degree):
+    """Gradient of L = mean((I - target)^2) vs central differences, h = 1e-3
+    (parameters whose FD at h and h/2 disagree by >1e-2 straddle a threshold
+    and are excluded and counted)."""
+    sc, cam = _fd_case(sh_degree)
+    rng = np.random.default_rng(17)
+    depth = rng.integers(1, sc.n_layers + 1, size=sc.n_clusters).astype(np.uint8)
+    depth[0] = sc.n_layers
+    t = 0.3125
+    bg = np.array([0.1, 0.2, 0.3])
+    target = rng.uniform(size=(cam.height, cam.width, 3))
+    L0, img = _loss(sc, depth, t, cam, bg, target)
+    dL = 2.0 * (img - target) / img.size
+    g = oracle.render_backward(sc, depth, t, cam, bg, dL)
+    checked = excluded = 0
+    names = ["mu0", "u", "log_scale", "quat", "opacity_logit", "colour", "res"]
+    cl = sc.cluster_of()
+    for name in names:
+        arr = getattr(sc, name)
+        G = g[name]
+        flat = arr.reshape(-1)
+        scale = max(np.abs(G).max(), 1e-12)
+        cand = np.argsort(-np.abs(G).reshape(-1))[:12]
+        cand = np.concatenate([cand, rng.choice(flat.size, size=8, replace=False)])
+        for j in cand:
+            def fd(h):
+                orig = flat[j]
+                flat[j] = np.float32(orig + h); lp, _ = _loss(sc, depth, t, cam, bg, target); up = float(flat[j])
+                flat[j] = np.float32(orig - h); lm, _ = _loss(sc, depth, t, cam, bg, target); dn = float(flat[j])
+                flat[j] = orig
+                return (lp - lm) / (up - dn)
+            f1, f2 = fd(1e-3), fd(5e-4)
+            if abs(f1 - f2) > 1e-2 * max(abs(f1), abs(f2), 1e-3 * scale):
+                excluded += 1
+                continue
+            checked += 1
+            assert abs(G.reshape(-1)[j] - f2) <= 2e-3 * scale + 1e-9, (name, j, G.reshape(-1)[j], f1, f2)
+    assert checked >= 60 and excluded <= checked // 4, (checked, excluded)
+
+
+def test_undelivered_residuals_get_exactly_zero_gradient():
+    sc, cam = _fd_case(0)
+    depth = np.array([1, 2] + [4] * (sc.n_clusters - 2), np.uint8)
+    rng = np.random.default_rng(2)
+    dL = rng.normal(size=(cam.height, cam.width, 3))
+    g = oracle.render_backward(sc, depth, 0.1, cam, np.zeros(3), dL)
+    cl = sc.cluster_of()
+    for i in range(sc.n):
+        d = depth[cl[i]]
+        assert np.all(g["res"][d - 1:, i] == 0.0)

@@ -1,0 +1,350 @@
+#!/usr/bin/env python3
+"""Benchmark of the delivery-state renderer (one JSON line on stdout).
+
+Default workload: batched forward + backward training step on 250,000
+Gaussians (rank-2 temporal basis, 64 clusters x 4 layers), 64 delivery states
+per step at 512x512 on 8 ring cameras: render every state, per-state FP64 MSE
+against the teacher render of its view (loss = mean over states), adjoint
+render to scene gradients.  A step runs the whole hot path: closure, masked
+prefix decode, Eq. 1 deformation, EWA projection, binning, the two radix
+sorts, tile ranges, compositing, MSE, backward compositing, backward
+projection.
+
+``--impl reference`` times the FP64 CPU oracle on the same workload (bounded
+pixel sample per step, extrapolated to states/s).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "delivery-state renders/s and Mpix/s, batched fwd+bwd vs plain per-state, ≤1e-4 err"
+UNIT = "states/s"
+FWD_FLOP_PER_EVAL = 24     # FP32 ops of one (pixel, Gaussian) compositing evaluation
+BWD_FLOP_PER_EVAL = 57     # forward recompute (24) + adjoint arithmetic (33)
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(w, n_states=2, n_pix=1024, seed=0, want_backward=True):
+    """Time the FP64 oracle on a bounded sample: n_pix random pixels of n_states
+    states, forward (+ adjoint restricted to those pixels).  Returns
+    (seconds per full state, evaluations per pixel, threads, description)."""
+    import oracle
+    sc = w.scene
+    rng = np.random.default_rng(seed)
+    D = oracle.state_depths(w.states, sc.n_clusters, sc.n_layers)
+    H, W = w.cams[0].height, w.cams[0].width
+    tot_t, tot_px, tot_eval = 0.0, 0, 0
+    for s in range(n_states):
+        cam = w.cams[int(w.states.cam[s])]
+        t = float(w.states.t[s])
+        flat = rng.choice(H * W, size=n_pix, replace=False)
+        pix = np.stack([flat % W, flat // W], 1).astype(np.int32)
+        t0 = time.perf_counter()
+        img, marg, ne = oracle.render(sc, D[s], t, cam, w.bg, pix=pix)
+        if want_backward:
+            dL = np.zeros((H, W, 3))
+            dL[pix[:, 1], pix[:, 0]] = rng.normal(size=(n_pix, 3))
+            oracle.render_backward(sc, D[s], t, cam, w.bg, dL)
+        tot_t += time.perf_counter() - t0
+        tot_px += n_pix
+        tot_eval += ne
+    sec_per_state = tot_t / tot_px * (H * W)
+    threads = os.cpu_count() or 1
+    desc = ("%d random pixels in each of %d states (FP64 forward on %d threads%s), "
+            "extrapolated to %dx%d pixels per state" % (n_pix, n_states, threads,
+                                                       ", adjoint of those pixels on 1 thread" if want_backward
+                                                       else "", W, H))
+    return sec_per_state, tot_eval / tot_px, threads, desc
+
+
+def reference_arm(args, w):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    cfg = {"workload": w.name, "gaussians": w.scene.n, "states_per_step": w.states.n,
+           "resolution": [w.cams[0].width, w.cams[0].height]}
+    times = []
+    n_pix = 256
+    for k in range(args.warmup + args.steps):
+        sps, _, threads, desc = oracle_sample(w, n_states=1, n_pix=n_pix, seed=k)
+        if k >= args.warmup:
+            times.append(sps)
+    sec_per_state = float(np.mean(times))
+    value = 1.0 / sec_per_state
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec_per_state * w.states.n * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "per step: " + desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c3_fwdbwd_250k")
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
+
+    from paper_2606_17212_b300 import synth
+    ws, rank, local = _dist()
+    w = synth.config(args.workload, scale=args.scale)
+    if args.impl == "reference":
+        reference_arm(args, w)
+        return
+
+    import torch
+    from paper_2606_17212_b300 import dgs
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    # weak scaling: every rank renders its own batch of states (different mask seed)
+    if ws > 1 and rank > 0:
+        rng = np.random.default_rng(10_000 + rank)
+        d = synth.prefix_states(w.states.n, w.scene.n_clusters, w.scene.n_layers, rng)
+        w.states.masks = synth._pack(synth.depths_to_bits(d, w.scene.n_layers))
+
+    R = dgs.Renderer(local)
+    scene = dgs.DeviceScene.from_host(w.scene, device=dev)
+    states = dgs.DeviceStates.from_host(w.states)
+    S = states.n
+    H, W = w.cams[0].height, w.cams[0].width
+    training = w.target_scene is not None
+
+    # targets: complete render of the teacher scene at every (camera, time) a state uses
+    views = sorted(set(zip(w.states.cam.tolist(), w.states.t.tolist())))
+    ref_index = np.array([views.index((c, t)) for c, t in zip(w.states.cam.tolist(), w.states.t.tolist())],
+                         np.int32)
+    if training:
+        teacher = dgs.DeviceScene.from_host(w.target_scene, device=dev)
+        full = torch.full((len(views), states.masks.shape[1]), -1, dtype=torch.int32, device=dev)
+        tv = dgs.DeviceStates(full, np.array([v[1] for v in views], np.float32),
+                              np.array([v[0] for v in views], np.int32))
+        targets = R.render_states_batched(teacher, tv, w.cams, w.bg)
+        del teacher
+    images = torch.empty((S, H, W, 3), dtype=torch.float32, device=dev)
+    grads = scene.zeros_like_grads()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 126 MB L2
+
+    def step(st):
+        if training:
+            R.render_states_batched(scene, st, w.cams, w.bg, out=images)
+            mse, _, dL = R.image_mse(images, targets, ref_index, weight=1.0 / S, want_grad=True)
+            for g in grads.values():
+                g.zero_()
+            R.render_backward(scene, st, w.cams, w.bg, dL, grads)
+            return mse
+        mse, _ = R.state_utility(scene, st, w.cams, w.bg)
+        return mse
+
+    for _ in range(args.warmup):
+        step(states)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device time of K steps, L2 flushed between steps
+    R.reset_kernel_launches()
+    R.profile(True)
+    clocks = ClockSampler(local)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record()
+        step(states)
+        ends[k].record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    launches = R.kernel_launches()
+    prof = R.profile_read()
+    R.profile(False)
+    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = ws * S / (ms_per_step / 1e3)
+
+    # ---- end to end through the public API: masks H2D from pinned memory, loss D2H
+    host_masks = torch.from_numpy(np.ascontiguousarray(w.states.masks).view(np.int32)).pin_memory()
+    dev_masks = torch.empty_like(host_masks, device=dev)
+    res_host = torch.empty(S, dtype=torch.float64).pin_memory()
+    e2e_states = dgs.DeviceStates(dev_masks, w.states.t, w.states.cam)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        dev_masks.copy_(host_masks, non_blocking=True)
+        mse = step(e2e_states)
+        res_host.copy_(mse, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_value = ws * S / e2e_s
+    h2d = host_masks.numel() * 4 + w.states.t.nbytes + w.states.cam.nbytes
+    d2h = S * 8
+
+    # ---- plain per-state path (one state per launch sequence, synchronized)
+    plain = None
+    if not args.no_plain and rank == 0:
+        n_plain = S
+
+        def plain_state(s):
+            m = states.masks[s:s + 1]
+            st1 = dgs.DeviceStates(m, w.states.t[s:s + 1], w.states.cam[s:s + 1])
+            if training:
+                img = R.render_state(scene, m[0], float(w.states.t[s]), w.cams[int(w.states.cam[s])], w.bg,
+                                     out=images[s])
+                _, _, dL = R.image_mse(images[s:s + 1], targets, ref_index[s:s + 1], weight=1.0 / S,
+                                       want_grad=True)
+                R.render_backward(scene, st1, w.cams, w.bg, dL, grads)
+            else:
+                R.state_utility(scene, st1, w.cams, w.bg)
+            torch.cuda.synchronize()
+
+        for s in range(3):
+            plain_state(s)
+        t0 = time.perf_counter()
+        for s in range(n_plain):
+            plain_state(s)
+        plain = n_plain / (time.perf_counter() - t0)
+
+    # ---- roofline of the dominant kernel, from the live events
+    pk, pk_kind = _peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 1))
+    dom_name, (dom_ms, dom_n) = dom
+    dom_ms_per_launch = dom_ms / max(dom_n, 1)
+    cpu = None
+    roof = None
+    evals_per_px = None
+    if rank == 0:
+        n_samp = 2 if training else 4
+        sec_state, evals_per_px, threads, desc = oracle_sample(w, n_states=n_samp, n_pix=1024,
+                                                                want_backward=training)
+        if not args.no_cpu_baseline:
+            cpu = {"value": 1.0 / sec_state, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+        sm_mhz = pk.get("sm_max_mhz", 2032.0)
+        fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12     # TFLOP/s, FP32 FMA, all SMs
+        evals_per_launch = evals_per_px * H * W * S
+        per_eval = {"raster_bwd": BWD_FLOP_PER_EVAL, "raster_fwd": FWD_FLOP_PER_EVAL,
+                    "raster_fwd_mse": FWD_FLOP_PER_EVAL}.get(dom_name)
+        if per_eval is not None:
+            achieved = per_eval * evals_per_launch / (dom_ms_per_launch / 1e3) / 1e12
+            roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                    "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                    "peak_kind": "FP32 FMA issue peak: 148 SMs x 128 lanes x 2 x %.0f MHz (derived)" % sm_mhz,
+                    "ms_per_launch": dom_ms_per_launch,
+                    "evals_per_launch": evals_per_launch}
+    cfg = {"workload": w.name, "gaussians": w.scene.n, "clusters": w.scene.n_clusters,
+           "layers": w.scene.n_layers, "temporal_rank": w.scene.temporal_rank,
+           "states_per_step": S, "resolution": [W, H], "cameras": len(w.cams),
+           "view_groups": len(views), "l2": "flushed between timed steps (256 MB write)",
+           "parallelism": "dp%d" % ws}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+            "mpix_per_s": value * H * W / 1e6,
+            "plain_per_state": {"value": plain, "unit": UNIT} if plain else None,
+            "batched_vs_plain": (value / ws / plain) if plain else None,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
+            "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "peaks": pk_kind}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    R.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * dgs.h -- C ABI of the B300 delivery-state renderer for dynamic Gaussian scenes.
+ *
+ * The library renders a dynamic Gaussian scene as it stands in an incomplete
+ * delivery state and scores that state against the complete render, for one
+ * state or for many states in one batch, forward and backward.  It follows the
+ * paper "Renderable Partial Representations for Dynamic Gaussian Splatting
+ * under Incomplete Delivery":
+ *   - Section 3: N fixed-identity Gaussians in clusters; per cluster one base
+ *     completion group and refinement groups; every attribute is base plus
+ *     additive refinements; every dependency-closed subset is renderable.
+ *   - Eq. 1: mu_i(t) = mubar_i + sum_r b_r(t) q_{i,r} + refinement residuals,
+ *     with the shared basis b_{2j-1}(t) = cos(2 pi j t), b_{2j}(t) = sin(2 pi j t)
+ *     and the cluster affine taken as the identity.
+ *   - Sections 4 and 7.4: dependencies are enforced after delivery; a layer is
+ *     usable only when all layers below it in its cluster are usable.
+ *   - Section 6: many delivery states of one scene rasterized in one batch;
+ *     the batched result equals serial (one state at a time) evaluation.
+ *   - Eq. 3: the distortion D of a state against the reference render, taken
+ *     here as the per-state MSE (accumulated in FP64) and its PSNR.
+ * Rasterization is EWA splatting of the 3D Gaussians, tile-binned on 16x16
+ * pixel tiles with a stable 64-bit (tile | depth) order, composited front to
+ * back in FP32 (the readings of every unstated constant are listed in the
+ * project's design notes and match the FP64 oracle used by the tests).
+ *
+ * Conventions for every entry point:
+ *   - Pointers marked [device] are CUDA device pointers on the context's
+ *     device, [host] are host pointers.  The caller owns every buffer it
+ *     passes; the library owns only the workspace inside a dgs_ctx.
+ *   - Calls are asynchronous on the given stream, except that a call may
+ *     synchronize that stream once or twice to size its workspace (the number
+ *     of projected records and of tile entries); it never synchronizes other
+ *     streams.  A context must not be used by two host threads at once.
+ *   - Return 0 on success or a negative DGS_E_* code; dgs_last_error() then
+ *     describes the failure.  Arguments are validated before any launch; an
+ *     invalid call launches nothing and leaves outputs untouched.
+ *   - Mask bits at positions >= n_clusters * n_layers are ignored.
+ */
+#ifndef DGS_H
+#define DGS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DGS_VERSION 1
+
+#if defined(__GNUC__)
+#define DGS_API __attribute__((visibility("default")))
+#else
+#define DGS_API
+#endif
+
+enum {
+    DGS_OK = 0,
+    DGS_E_INVALID_ARG = -1,   /* null pointer, bad count, mismatched sizes */
+    DGS_E_UNSUPPORTED = -2,   /* e.g. sh_degree not in {0, 3}, > 1024 clusters */
+    DGS_E_OOM = -3,           /* workspace allocation failed */
+    DGS_E_CUDA = -4,          /* a CUDA runtime call or launch failed */
+    DGS_E_CAPACITY = -5       /* a count exceeds 32-bit indexing */
+};
+
+typedef struct dgs_ctx dgs_ctx;
+typedef void *dgs_stream;     /* a cudaStream_t; NULL = the legacy default stream */
+
+/*
+ * One scene (Section 3, Eq. 1).  Gaussians are stored cluster-contiguous:
+ * Gaussians cluster_offsets[c] .. cluster_offsets[c+1]-1 form cluster c.
+ * n_layers L counts the base layer: layer 0 = base, layers 1..L-1 = refinements.
+ * All arrays [device], FP32, row-major:
+ *   mu0 [n][3]          canonical mean (mubar of Eq. 1)
+ *   u [R][n][3]         temporal coefficients q_{i,r} of Eq. 1 (R = temporal_rank)
+ *   log_scale [n][3]    log of the three axis scales
+ *   quat [n][4]         rotation quaternion (w, x, y, z), normalised on use
+ *   opacity_logit [n]   opacity o = sigmoid(logit)
+ *   colour [n][NC]      NC = 3 (sh_degree 0: RGB) or 48 (sh_degree 3: 16 real
+ *                       SH coefficients x 3 channels, channel innermost)
+ *   res [L-1][n][K]     refinement l (1..L-1) of Gaussian i, K = 11 + NC:
+ *                       dmu[3], dlog_scale[3], dquat[4], dlogit[1], dcolour[NC]
+ * A Gaussian of cluster c at delivered depth d >= 1 renders with every
+ * attribute = base + res[0] + ... + res[d-2]; at depth 0 it is absent.
+ */
+typedef struct {
+    int32_t n, n_clusters, n_layers, sh_degree, temporal_rank;
+    const int32_t *cluster_offsets;   /* [device] [n_clusters + 1] */
+    const float *mu0;
+    const float *u;
+    const float *log_scale;
+    const float *quat;
+    const float *opacity_logit;
+    const float *colour;
+    const float *res;
+} dgs_scene;
+
+/* Gradients in the scene's layout, [device], ACCUMULATED (+=) by the backward. */
+typedef struct {
+    float *mu0, *u, *log_scale, *quat, *opacity_logit, *colour, *res;
+} dgs_scene_grad;
+
+/* OpenCV pinhole: p_cam = R_wc p_world + t_wc; x right, y down, z forward;
+ * pixel (x, y) has its centre at (x + 0.5, y + 0.5).  [host] */
+typedef struct {
+    float R_wc[9];
+    float t_wc[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} dgs_camera;
+
+/*
+ * A batch of delivery states.  masks [device] [n_states][W32] uint32,
+ * W32 = ceil(n_clusters * n_layers / 32); bit b = c * n_layers + l (word b/32,
+ * bit b%32) is set when packet (cluster c, layer l) arrived.  t [host] [n_states]
+ * is each state's time, cam [host] [n_states] its index into the camera array.
+ * States with equal (cam, t) form a view group and share decoded and projected
+ * Gaussians and tile lists.
+ */
+typedef struct {
+    const uint32_t *masks;
+    const float *t;
+    const int32_t *cam;
+    int32_t n_states;
+} dgs_states;
+
+/* Create a context on CUDA device `device`.  Returns DGS_OK and *out. */
+DGS_API int dgs_create(dgs_ctx **out, int device);
+/* Free the context and its workspace (device memory); NULL is accepted. */
+DGS_API void dgs_destroy(dgs_ctx *ctx);
+/* Message of the last failed call on this context ("" if none). [host] */
+DGS_API const char *dgs_last_error(const dgs_ctx *ctx);
+/* DGS_VERSION of the loaded library. */
+DGS_API int dgs_version(void);
+
+/*
+ * Render one delivery state (Section 3 + closure of Sections 4 / 7.4):
+ * mask [device] [W32], time t, camera [host], background bg [host][3].
+ * image [device] [H][W][3] FP32 receives C + T_final * bg per pixel.
+ * Bit-equal to that state's image from dgs_render_states_batched.
+ */
+DGS_API int dgs_render_state(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *mask, float t,
+                     const dgs_camera *cam, const float *bg, float *image, dgs_stream stream);
+
+/*
+ * Render every state of a batch in one pass (Section 6): shared decode and
+ * projection per (view group, Gaussian, delivered depth), one stable tile
+ * sort for the batch, per-state filtered compositing.  cams [host] [n_cams];
+ * all cameras must have the same width and height.  images [device]
+ * [n_states][H][W][3].  The call records its projection and tile lists in the
+ * context for a following dgs_render_backward with the same arguments.
+ */
+DGS_API int dgs_render_states_batched(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states,
+                              const dgs_camera *cams, int n_cams, const float *bg,
+                              float *images, dgs_stream stream);
+
+/*
+ * Adjoint of dgs_render_states_batched: given dL/dimages [device]
+ * [n_states][H][W][3], accumulate (+=) dL/d(parameters) into grads (every
+ * pointer [device], scene layout).  Transmittance is recomputed per tile, not
+ * stored.  Refinement layers a state did not deliver get exactly zero from that
+ * state.  If the context's last forward call had the same arguments (same
+ * pointers, counts, times and cameras) its projection and tile lists are
+ * reused; the caller must not have changed the scene or the masks since.
+ */
+DGS_API int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states,
+                        const dgs_camera *cams, int n_cams, const float *bg,
+                        const float *dL_dimages, const dgs_scene_grad *grads, dgs_stream stream);
+
+/*
+ * Eq. 3 distortion of every state against the complete render of its view:
+ * renders the full-delivery image of each view group and each state, without
+ * writing state images, and writes mse [device] [n_states] (FP64 sum of
+ * squared FP32 differences over 3*H*W values, divided by 3*H*W) and
+ * psnr [device] [n_states] = 10 log10(1 / mse) (+inf when mse == 0).
+ */
+DGS_API int dgs_state_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states,
+                      const dgs_camera *cams, int n_cams, const float *bg,
+                      double *mse, double *psnr, dgs_stream stream);
+
+/*
+ * Per-image MSE (FP64 accumulation) and PSNR of images [device] [S][H][W][3]
+ * against refs [device] [n_refs][H][W][3], image s against refs[ref_index[s]]
+ * (ref_index [host] [S]).  mse, psnr [device] [S] (psnr may be NULL).  If
+ * dL_dimages [device] [S][H][W][3] is not NULL it receives the gradient of
+ * L = sum_s weight * mse_s, i.e. weight * 2 (image - ref) / (3 H W).
+ */
+DGS_API int dgs_image_mse(dgs_ctx *ctx, const float *images, const float *refs, const int32_t *ref_index,
+                  int S, int n_refs, int H, int W, float weight, double *mse, double *psnr,
+                  float *dL_dimages, dgs_stream stream);
+
+/*
+ * Launch counters (host side, per context): number of kernels this context
+ * launched since creation or the last reset.  Used to report launch counts.
+ */
+DGS_API int64_t dgs_kernel_launches(const dgs_ctx *ctx);
+DGS_API void dgs_reset_kernel_launches(dgs_ctx *ctx);
+
+/*
+ * Launch profiler (library-wide).  While enabled, every named kernel launch is
+ * bracketed by CUDA events recorded on its own stream.  dgs_profile_read
+ * synchronizes the device, writes up to max_names aggregated rows -- name
+ * (names + 32*k, NUL-terminated, 32 bytes each), total milliseconds and launch
+ * count -- clears the records, and returns the number of rows (or < 0 on
+ * error).  Enabling (or disabling) also clears.  Host pointers.
+ */
+DGS_API void dgs_profile_enable(dgs_ctx *ctx, int on);
+DGS_API int dgs_profile_read(dgs_ctx *ctx, int max_names, char *names, double *total_ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGS_H */

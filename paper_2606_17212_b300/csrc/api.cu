@@ -1,0 +1,653 @@
+// C ABI entry points, the per-call planner (view groups of a state batch) and
+// the context's device workspace.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "dgs_internal.cuh"
+#include "kernels.cuh"
+
+namespace dgs {
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Library-wide launch profiler: CUDA events recorded on the launching stream
+// around each named launch while enabled; read (and cleared) by dgs_profile_read.
+namespace {
+struct ProfRec {
+    const char *name;
+    cudaEvent_t a, b;
+};
+bool g_prof = false;
+std::vector<ProfRec> g_prof_recs;
+std::vector<size_t> g_prof_stack;
+std::vector<cudaEvent_t> g_event_pool;
+size_t g_event_next = 0;
+
+cudaEvent_t next_event()
+{
+    if (g_event_next == g_event_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        g_event_pool.push_back(e);
+    }
+    return g_event_pool[g_event_next++];
+}
+}  // namespace
+
+void prof_begin(const char *name, cudaStream_t st)
+{
+    if (!g_prof) return;
+    ProfRec r{name, next_event(), next_event()};
+    if (r.a) cudaEventRecord(r.a, st);
+    g_prof_stack.push_back(g_prof_recs.size());
+    g_prof_recs.push_back(r);
+}
+
+void prof_end(cudaStream_t st)
+{
+    if (!g_prof || g_prof_stack.empty()) return;
+    const size_t k = g_prof_stack.back();
+    g_prof_stack.pop_back();
+    if (g_prof_recs[k].b) cudaEventRecord(g_prof_recs[k].b, st);
+}
+}  // namespace dgs
+
+using namespace dgs;
+
+namespace {
+
+struct Buf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+struct Plan {
+    int S = 0;           // states rendered (including appended reference states)
+    int S_user = 0;      // caller's states
+    int V = 0;
+    int W = 0, H = 0, tiles_x = 0, tiles_y = 0;
+    uint32_t tiles = 0;
+    std::vector<int32_t> vg_of_state;
+    std::vector<ViewGroup> vgs;
+};
+
+struct Tape {
+    bool valid = false;
+    dgs_scene scene{};
+    const uint32_t *masks = nullptr;
+    std::vector<float> t;
+    std::vector<int32_t> cam;
+    std::vector<dgs_camera> cams;
+    Plan plan;
+    uint32_t nRec = 0, nEnt = 0;
+    uint32_t *sorted_evals = nullptr;
+};
+
+}  // namespace
+
+struct dgs_ctx {
+    int device = 0;
+    int sms = 148;
+    std::string err;
+    Buf vgs, vgos, depth, need, counts, recBase, total, recs, k0, v0, k1, v1, tcount, toffs, ek0, ev0, ek1, ev1,
+        ranges, sortws, scanws, partial, refs, recgrad, refidx;
+    void *h_stage = nullptr;
+    size_t h_stage_cap = 0;
+    uint32_t *h_small = nullptr;   // pinned readback of counts
+    cudaEvent_t stage_done = nullptr;   // last copy out of h_stage
+    long long launch_base = 0;
+    Tape tape;
+};
+
+namespace {
+
+int fail(dgs_ctx *ctx, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    return code;
+}
+
+#define CK(x)                                                                                       \
+    do {                                                                                            \
+        cudaError_t e_ = (x);                                                                       \
+        if (e_ != cudaSuccess) return fail(ctx, DGS_E_CUDA, "%s: %s", #x, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define TRY(x)                     \
+    do {                           \
+        int r_ = (x);              \
+        if (r_ != DGS_OK) return r_; \
+    } while (0)
+
+int ensure(dgs_ctx *ctx, Buf &b, size_t bytes, cudaStream_t st)
+{
+    if (bytes == 0) bytes = 256;
+    if (b.cap >= bytes) return DGS_OK;
+    if (b.p) {
+        CK(cudaStreamSynchronize(st));
+        CK(cudaFree(b.p));
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    size_t want = bytes + bytes / 8;
+    if (cudaMalloc(&b.p, want) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, DGS_E_OOM, "device allocation of %zu bytes failed", want);
+    }
+    b.cap = want;
+    return DGS_OK;
+}
+
+int ensure_stage(dgs_ctx *ctx, size_t bytes, cudaStream_t st)
+{
+    if (ctx->h_stage_cap >= bytes) return DGS_OK;
+    if (ctx->h_stage) {
+        CK(cudaEventSynchronize(ctx->stage_done));
+        CK(cudaFreeHost(ctx->h_stage));
+        ctx->h_stage = nullptr;
+    }
+    size_t want = bytes + bytes / 4 + 4096;
+    CK(cudaMallocHost(&ctx->h_stage, want));
+    ctx->h_stage_cap = want;
+    return DGS_OK;
+}
+
+int check_scene(dgs_ctx *ctx, const dgs_scene *s)
+{
+    if (!s) return fail(ctx, DGS_E_INVALID_ARG, "scene is null");
+    if (s->n < 0 || s->n_clusters < 1 || s->n_layers < 1)
+        return fail(ctx, DGS_E_INVALID_ARG, "bad scene sizes n=%d C=%d L=%d", s->n, s->n_clusters, s->n_layers);
+    if (s->n_clusters > MAX_CLUSTERS) return fail(ctx, DGS_E_UNSUPPORTED, "more than %d clusters", MAX_CLUSTERS);
+    if (s->n_layers > MAX_LAYERS) return fail(ctx, DGS_E_UNSUPPORTED, "more than %d layers", MAX_LAYERS);
+    if (s->sh_degree != 0 && s->sh_degree != 3) return fail(ctx, DGS_E_UNSUPPORTED, "sh_degree must be 0 or 3");
+    if (s->temporal_rank < 0 || s->temporal_rank > 8)
+        return fail(ctx, DGS_E_UNSUPPORTED, "temporal_rank must be in [0, 8]");
+    if (s->n > 0) {
+        if (!s->cluster_offsets || !s->mu0 || !s->log_scale || !s->quat || !s->opacity_logit || !s->colour)
+            return fail(ctx, DGS_E_INVALID_ARG, "scene array is null");
+        if (s->temporal_rank > 0 && !s->u) return fail(ctx, DGS_E_INVALID_ARG, "u is null");
+        if (s->n_layers > 1 && !s->res) return fail(ctx, DGS_E_INVALID_ARG, "res is null");
+        if (((uintptr_t)s->quat & 15u) != 0) return fail(ctx, DGS_E_INVALID_ARG, "quat must be 16-byte aligned");
+    }
+    return DGS_OK;
+}
+
+SceneDev scene_dev(const dgs_scene *s)
+{
+    SceneDev d;
+    d.n = s->n; d.C = s->n_clusters; d.L = s->n_layers; d.sh = s->sh_degree; d.R = s->temporal_rank;
+    d.nc = 3 * (s->sh_degree + 1) * (s->sh_degree + 1);
+    d.K = 11 + d.nc;
+    d.offs = s->cluster_offsets; d.mu0 = s->mu0; d.u = s->u; d.ls = s->log_scale; d.quat = s->quat;
+    d.logit = s->opacity_logit; d.colour = s->colour; d.res = s->res;
+    return d;
+}
+
+int build_plan(dgs_ctx *ctx, const dgs_states *st, const dgs_camera *cams, int n_cams, bool add_refs, Plan &p)
+{
+    if (!st) return fail(ctx, DGS_E_INVALID_ARG, "states is null");
+    if (st->n_states < 0) return fail(ctx, DGS_E_INVALID_ARG, "n_states < 0");
+    if (!cams || n_cams < 1) return fail(ctx, DGS_E_INVALID_ARG, "need at least one camera");
+    if (st->n_states > 0 && (!st->masks || !st->t || !st->cam))
+        return fail(ctx, DGS_E_INVALID_ARG, "states arrays are null");
+    const int W = cams[0].width, H = cams[0].height;
+    if (W < 1 || H < 1 || W > 32768 || H > 32768) return fail(ctx, DGS_E_INVALID_ARG, "bad image size %dx%d", W, H);
+    for (int k = 0; k < n_cams; ++k) {
+        if (cams[k].width != W || cams[k].height != H)
+            return fail(ctx, DGS_E_INVALID_ARG, "all cameras of a batch must share one image size");
+        if (!(cams[k].fx > 0.0f) || !(cams[k].fy > 0.0f)) return fail(ctx, DGS_E_INVALID_ARG, "focal must be > 0");
+    }
+    p = Plan();
+    p.S_user = st->n_states;
+    p.W = W; p.H = H;
+    p.tiles_x = (W + TILE - 1) / TILE;
+    p.tiles_y = (H + TILE - 1) / TILE;
+    p.tiles = (uint32_t)p.tiles_x * (uint32_t)p.tiles_y;
+    std::map<std::pair<int, uint32_t>, int> groups;
+    p.vg_of_state.resize(st->n_states);
+    for (int s = 0; s < st->n_states; ++s) {
+        const int c = st->cam[s];
+        if (c < 0 || c >= n_cams) return fail(ctx, DGS_E_INVALID_ARG, "state %d: camera index %d out of range", s, c);
+        uint32_t tb;
+        std::memcpy(&tb, &st->t[s], 4);
+        auto key = std::make_pair(c, tb);
+        auto it = groups.find(key);
+        int v;
+        if (it == groups.end()) {
+            v = (int)p.vgs.size();
+            groups.emplace(key, v);
+            ViewGroup g;
+            const dgs_camera &cm = cams[c];
+            for (int k = 0; k < 9; ++k) g.R[k] = cm.R_wc[k];
+            for (int k = 0; k < 3; ++k) g.t[k] = cm.t_wc[k];
+            g.fx = cm.fx; g.fy = cm.fy; g.cx = cm.cx; g.cy = cm.cy;
+            g.time = st->t[s];
+            for (int k = 0; k < 3; ++k)   // camera centre = -R^T t
+                g.campos[k] = -(cm.R_wc[k] * cm.t_wc[0] + cm.R_wc[3 + k] * cm.t_wc[1] + cm.R_wc[6 + k] * cm.t_wc[2]);
+            g.width = W; g.height = H; g.cam = c; g.pad = 0;
+            p.vgs.push_back(g);
+        } else {
+            v = it->second;
+        }
+        p.vg_of_state[s] = v;
+    }
+    p.V = (int)p.vgs.size();
+    if (p.V > 65535) return fail(ctx, DGS_E_UNSUPPORTED, "more than 65535 distinct (camera, time) pairs");
+    if ((unsigned long long)(st->n_states + (add_refs ? p.V : 0)) * p.tiles >= 0x7fffffffull)
+        return fail(ctx, DGS_E_CAPACITY, "states x tiles exceeds the launch grid");
+    if ((unsigned long long)p.V * p.tiles >= 0xffffffffull)
+        return fail(ctx, DGS_E_CAPACITY, "view groups x tiles exceeds 32 bits");
+    p.S = p.S_user;
+    if (add_refs) {
+        for (int v = 0; v < p.V; ++v) p.vg_of_state.push_back(v);
+        p.S += p.V;
+    }
+    return DGS_OK;
+}
+
+int bits_for(unsigned long long maxval)
+{
+    int b = 1;
+    while (b < 32 && (maxval >> b) != 0) ++b;
+    return b;
+}
+
+// Closure, layout, projection, depth sort, binning, tile sort, ranges.
+int prepare(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *masks, const Plan &p, bool force_full,
+            cudaStream_t st, uint32_t &nRec, uint32_t &nEnt, uint32_t *&sorted_evals)
+{
+    const int C = scene->n_clusters, L = scene->n_layers;
+    const int words = (C * L + 31) / 32;
+    const size_t nvc = (size_t)p.V * C;
+    TRY(ensure(ctx, ctx->vgs, sizeof(ViewGroup) * (size_t)(p.V > 0 ? p.V : 1), st));
+    TRY(ensure(ctx, ctx->vgos, sizeof(int32_t) * (size_t)(p.S > 0 ? p.S : 1), st));
+    TRY(ensure(ctx, ctx->depth, (size_t)p.S * C, st));
+    TRY(ensure(ctx, ctx->need, sizeof(uint32_t) * nvc, st));
+    TRY(ensure(ctx, ctx->counts, sizeof(uint32_t) * (nvc + 1), st));
+    TRY(ensure(ctx, ctx->recBase, sizeof(uint32_t) * (nvc + 1), st));
+    TRY(ensure(ctx, ctx->total, 64, st));
+    TRY(ensure(ctx, ctx->scanws, scan_workspace_bytes(nvc + 1), st));
+    const size_t stage = sizeof(ViewGroup) * p.vgs.size() + sizeof(int32_t) * p.vg_of_state.size() + 64;
+    TRY(ensure_stage(ctx, stage, st));
+    CK(cudaEventSynchronize(ctx->stage_done));   // an earlier copy may still read h_stage
+    char *hs = (char *)ctx->h_stage;
+    std::memcpy(hs, p.vgs.data(), sizeof(ViewGroup) * p.vgs.size());
+    std::memcpy(hs + sizeof(ViewGroup) * p.vgs.size(), p.vg_of_state.data(), sizeof(int32_t) * p.vg_of_state.size());
+    CK(cudaMemcpyAsync(ctx->vgs.p, hs, sizeof(ViewGroup) * p.vgs.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->vgos.p, hs + sizeof(ViewGroup) * p.vgs.size(), sizeof(int32_t) * p.vg_of_state.size(),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(ctx->stage_done, st));
+    CK(cudaMemsetAsync(ctx->need.p, 0, sizeof(uint32_t) * nvc, st));
+    uint8_t *depth = (uint8_t *)ctx->depth.p;
+    if (p.S_user > 0)
+        launch_closure(masks, p.S_user, words, C, L, (const int32_t *)ctx->vgos.p, depth, (uint32_t *)ctx->need.p,
+                       force_full ? 1 : 0, ctx->sms, st);
+    if (p.S > p.S_user) CK(cudaMemsetAsync(depth + (size_t)p.S_user * C, L, (size_t)(p.S - p.S_user) * C, st));
+    launch_layout_counts((const uint32_t *)ctx->need.p, scene->cluster_offsets, p.V, C, (uint32_t *)ctx->counts.p,
+                         ctx->sms, st);
+    CK(exclusive_scan_u32((const uint32_t *)ctx->counts.p, (uint32_t *)ctx->recBase.p, nvc + 1,
+                          (uint32_t *)ctx->total.p, ctx->scanws.p, st));
+    CK(cudaMemcpyAsync(ctx->h_small, ctx->total.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    int32_t *hoffs = (int32_t *)(ctx->h_small + 16);
+    CK(cudaMemcpyAsync(hoffs, scene->cluster_offsets, sizeof(int32_t) * (size_t)(C + 1), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (hoffs[0] != 0 || hoffs[C] != scene->n)
+        return fail(ctx, DGS_E_INVALID_ARG, "cluster_offsets must start at 0 and end at n");
+    for (int c = 0; c < C; ++c)
+        if (hoffs[c + 1] < hoffs[c]) return fail(ctx, DGS_E_INVALID_ARG, "cluster_offsets must be non-decreasing");
+    nRec = ctx->h_small[0];
+    if (nRec >= 0x7fffffffu) return fail(ctx, DGS_E_CAPACITY, "too many projected records");
+    TRY(ensure(ctx, ctx->recs, sizeof(Rec) * (size_t)nRec, st));
+    TRY(ensure(ctx, ctx->k0, 4 * (size_t)nRec, st));
+    TRY(ensure(ctx, ctx->v0, 4 * (size_t)nRec, st));
+    TRY(ensure(ctx, ctx->k1, 4 * (size_t)nRec, st));
+    TRY(ensure(ctx, ctx->v1, 4 * (size_t)nRec, st));
+    TRY(ensure(ctx, ctx->tcount, 4 * ((size_t)nRec + 1), st));
+    TRY(ensure(ctx, ctx->toffs, 4 * ((size_t)nRec + 1), st));
+    TRY(ensure(ctx, ctx->sortws, radix_workspace_bytes(nRec), st));
+    TRY(ensure(ctx, ctx->scanws, scan_workspace_bytes((size_t)nRec + 1), st));
+    SceneDev sd = scene_dev(scene);
+    if (nRec > 0)
+        launch_project(sd, (const ViewGroup *)ctx->vgs.p, p.V, (const uint32_t *)ctx->need.p,
+                       (const uint32_t *)ctx->recBase.p, (Rec *)ctx->recs.p, (uint32_t *)ctx->k0.p,
+                       (uint32_t *)ctx->v0.p, ctx->sms, st);
+    bool alt = false;
+    CK(radix_sort_pairs((uint32_t *)ctx->k0.p, (uint32_t *)ctx->v0.p, (uint32_t *)ctx->k1.p, (uint32_t *)ctx->v1.p,
+                        nRec, 32, ctx->sortws.p, st, &alt));
+    const uint32_t *order = alt ? (const uint32_t *)ctx->v1.p : (const uint32_t *)ctx->v0.p;
+    if (nRec > 0) launch_tile_count((const Rec *)ctx->recs.p, order, nRec, (uint32_t *)ctx->tcount.p, ctx->sms, st);
+    CK(exclusive_scan_u32((const uint32_t *)ctx->tcount.p, (uint32_t *)ctx->toffs.p, nRec,
+                          (uint32_t *)ctx->total.p + 1, ctx->scanws.p, st));
+    CK(cudaMemcpyAsync(ctx->h_small + 1, (uint32_t *)ctx->total.p + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    nEnt = nRec > 0 ? ctx->h_small[1] : 0;
+    if (nEnt >= 0x7fffffffu) return fail(ctx, DGS_E_CAPACITY, "too many tile entries");
+    TRY(ensure(ctx, ctx->ek0, 4 * (size_t)nEnt, st));
+    TRY(ensure(ctx, ctx->ev0, 4 * (size_t)nEnt, st));
+    TRY(ensure(ctx, ctx->ek1, 4 * (size_t)nEnt, st));
+    TRY(ensure(ctx, ctx->ev1, 4 * (size_t)nEnt, st));
+    TRY(ensure(ctx, ctx->sortws, radix_workspace_bytes(nEnt), st));
+    TRY(ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)p.V * p.tiles, st));
+    if (nEnt > 0)
+        launch_emit((const Rec *)ctx->recs.p, order, (const uint32_t *)ctx->toffs.p, nRec, p.tiles_x, p.tiles,
+                    (uint32_t *)ctx->ek0.p, (uint32_t *)ctx->ev0.p, ctx->sms, st);
+    const int kbits = bits_for((unsigned long long)p.V * p.tiles - 1ull);
+    CK(radix_sort_pairs((uint32_t *)ctx->ek0.p, (uint32_t *)ctx->ev0.p, (uint32_t *)ctx->ek1.p,
+                        (uint32_t *)ctx->ev1.p, nEnt, kbits, ctx->sortws.p, st, &alt));
+    uint32_t *ekeys = alt ? (uint32_t *)ctx->ek1.p : (uint32_t *)ctx->ek0.p;
+    sorted_evals = alt ? (uint32_t *)ctx->ev1.p : (uint32_t *)ctx->ev0.p;
+    CK(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * (size_t)p.V * p.tiles, st));
+    launch_ranges(ekeys, nEnt, (uint2 *)ctx->ranges.p, ctx->sms, st);
+    CK(cudaGetLastError());
+    return DGS_OK;
+}
+
+RasterArgs raster_args(dgs_ctx *ctx, const Plan &p, int C, const float *bg, uint32_t *sorted_evals)
+{
+    RasterArgs a;
+    a.recs = (const Rec *)ctx->recs.p;
+    a.evals = sorted_evals;
+    a.ranges = (const uint2 *)ctx->ranges.p;
+    a.depth = (const uint8_t *)ctx->depth.p;
+    a.vg_of_state = (const int32_t *)ctx->vgos.p;
+    a.S = p.S_user; a.C = C; a.W = p.W; a.H = p.H; a.tiles_x = p.tiles_x; a.tiles = p.tiles;
+    a.bg0 = bg[0]; a.bg1 = bg[1]; a.bg2 = bg[2];
+    a.images = nullptr; a.refs = nullptr; a.ref_of_state = nullptr; a.partial = nullptr;
+    return a;
+}
+
+bool same_call(const Tape &tp, const dgs_scene *sc, const dgs_states *st, const dgs_camera *cams, int n_cams)
+{
+    if (!tp.valid) return false;
+    const dgs_scene &a = tp.scene;
+    if (a.n != sc->n || a.n_clusters != sc->n_clusters || a.n_layers != sc->n_layers ||
+        a.sh_degree != sc->sh_degree || a.temporal_rank != sc->temporal_rank ||
+        a.cluster_offsets != sc->cluster_offsets || a.mu0 != sc->mu0 || a.u != sc->u ||
+        a.log_scale != sc->log_scale || a.quat != sc->quat || a.opacity_logit != sc->opacity_logit ||
+        a.colour != sc->colour || a.res != sc->res)
+        return false;
+    if (tp.masks != st->masks || (int)tp.t.size() != st->n_states || (int)tp.cams.size() != n_cams) return false;
+    if (st->n_states > 0 && (std::memcmp(tp.t.data(), st->t, 4 * (size_t)st->n_states) != 0 ||
+                             std::memcmp(tp.cam.data(), st->cam, 4 * (size_t)st->n_states) != 0))
+        return false;
+    return std::memcmp(tp.cams.data(), cams, sizeof(dgs_camera) * (size_t)n_cams) == 0;
+}
+
+void record_tape(Tape &tp, const dgs_scene *sc, const dgs_states *st, const dgs_camera *cams, int n_cams,
+                 const Plan &p, uint32_t nRec, uint32_t nEnt, uint32_t *sorted)
+{
+    tp.valid = true;
+    tp.scene = *sc;
+    tp.masks = st->masks;
+    tp.t.assign(st->t, st->t + st->n_states);
+    tp.cam.assign(st->cam, st->cam + st->n_states);
+    tp.cams.assign(cams, cams + n_cams);
+    tp.plan = p;
+    tp.nRec = nRec; tp.nEnt = nEnt; tp.sorted_evals = sorted;
+}
+
+int render_batched(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states, const dgs_camera *cams,
+                   int n_cams, const float *bg, float *images, cudaStream_t st)
+{
+    TRY(check_scene(ctx, scene));
+    if (!bg) return fail(ctx, DGS_E_INVALID_ARG, "bg is null");
+    Plan p;
+    TRY(build_plan(ctx, states, cams, n_cams, false, p));
+    if (p.S_user > 0 && !images) return fail(ctx, DGS_E_INVALID_ARG, "images is null");
+    ctx->tape.valid = false;
+    if (p.S_user == 0) return DGS_OK;
+    uint32_t nRec = 0, nEnt = 0;
+    uint32_t *sorted = nullptr;
+    TRY(prepare(ctx, scene, states->masks, p, false, st, nRec, nEnt, sorted));
+    RasterArgs a = raster_args(ctx, p, scene->n_clusters, bg, sorted);
+    a.images = images;
+    launch_raster_fwd(a, st);
+    CK(cudaGetLastError());
+    record_tape(ctx->tape, scene, states, cams, n_cams, p, nRec, nEnt, sorted);
+    return DGS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dgs_version(void) { return DGS_VERSION; }
+
+int dgs_create(dgs_ctx **out, int device)
+{
+    if (!out) return DGS_E_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return DGS_E_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return DGS_E_CUDA;
+    dgs_ctx *ctx = new dgs_ctx();
+    ctx->device = device;
+    cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMallocHost((void **)&ctx->h_small, 64 + 4 * (MAX_CLUSTERS + 1)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->stage_done, cudaEventDisableTiming) != cudaSuccess) {
+        if (ctx->h_small) cudaFreeHost(ctx->h_small);
+        delete ctx;
+        return DGS_E_OOM;
+    }
+    ctx->launch_base = g_launches.load();
+    *out = ctx;
+    return DGS_OK;
+}
+
+void dgs_destroy(dgs_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    Buf *bufs[] = {&ctx->vgs, &ctx->vgos, &ctx->depth, &ctx->need, &ctx->counts, &ctx->recBase, &ctx->total,
+                   &ctx->recs, &ctx->k0, &ctx->v0, &ctx->k1, &ctx->v1, &ctx->tcount, &ctx->toffs, &ctx->ek0,
+                   &ctx->ev0, &ctx->ek1, &ctx->ev1, &ctx->ranges, &ctx->sortws, &ctx->scanws, &ctx->partial,
+                   &ctx->refs, &ctx->recgrad, &ctx->refidx};
+    for (Buf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    if (ctx->h_small) cudaFreeHost(ctx->h_small);
+    if (ctx->stage_done) cudaEventDestroy(ctx->stage_done);
+    delete ctx;
+}
+
+const char *dgs_last_error(const dgs_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t dgs_kernel_launches(const dgs_ctx *ctx) { return ctx ? (int64_t)(g_launches.load() - ctx->launch_base) : 0; }
+
+void dgs_reset_kernel_launches(dgs_ctx *ctx)
+{
+    if (ctx) ctx->launch_base = g_launches.load();
+}
+
+void dgs_profile_enable(dgs_ctx *ctx, int on)
+{
+    (void)ctx;
+    g_prof = on != 0;
+    g_prof_recs.clear();
+    g_prof_stack.clear();
+    g_event_next = 0;
+}
+
+int dgs_profile_read(dgs_ctx *ctx, int max_names, char *names, double *total_ms, int64_t *launches)
+{
+    if (!ctx) return DGS_E_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(ctx, DGS_E_CUDA, "synchronize failed");
+    std::vector<std::string> order;
+    std::map<std::string, std::pair<double, long long>> agg;
+    for (const ProfRec &r : g_prof_recs) {
+        float ms = 0.0f;
+        if (!r.a || !r.b || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        auto it = agg.find(r.name);
+        if (it == agg.end()) {
+            order.push_back(r.name);
+            agg[r.name] = {ms, 1};
+        } else {
+            it->second.first += ms;
+            it->second.second += 1;
+        }
+    }
+    g_prof_recs.clear();
+    g_prof_stack.clear();
+    g_event_next = 0;
+    const int n = (int)order.size() < max_names ? (int)order.size() : max_names;
+    for (int k = 0; k < n; ++k) {
+        if (names) {
+            std::strncpy(names + 32 * k, order[k].c_str(), 31);
+            names[32 * k + 31] = 0;
+        }
+        if (total_ms) total_ms[k] = agg[order[k]].first;
+        if (launches) launches[k] = agg[order[k]].second;
+    }
+    return n;
+}
+
+int dgs_render_states_batched(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states,
+                              const dgs_camera *cams, int n_cams, const float *bg, float *images, dgs_stream stream)
+{
+    if (!ctx) return DGS_E_INVALID_ARG;
+    CK(cudaSetDevice(ctx->device));
+    return render_batched(ctx, scene, states, cams, n_cams, bg, images, (cudaStream_t)stream);
+}
+
+int dgs_render_state(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *mask, float t, const dgs_camera *cam,
+                     const float *bg, float *image, dgs_stream stream)
+{
+    if (!ctx) return DGS_E_INVALID_ARG;
+    if (!mask || !cam) return fail(ctx, DGS_E_INVALID_ARG, "mask or camera is null");
+    CK(cudaSetDevice(ctx->device));
+    const int32_t cam0 = 0;
+    dgs_states s;
+    s.masks = mask; s.t = &t; s.cam = &cam0; s.n_states = 1;
+    const int r = render_batched(ctx, scene, &s, cam, 1, bg, image, (cudaStream_t)stream);
+    ctx->tape.valid = false;   // the tape would point at the caller's stack
+    return r;
+}
+
+int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states, const dgs_camera *cams,
+                        int n_cams, const float *bg, const float *dL_dimages, const dgs_scene_grad *grads,
+                        dgs_stream stream)
+{
+    if (!ctx) return DGS_E_INVALID_ARG;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(check_scene(ctx, scene));
+    if (!bg || !grads) return fail(ctx, DGS_E_INVALID_ARG, "bg or grads is null");
+    Plan p;
+    TRY(build_plan(ctx, states, cams, n_cams, false, p));
+    if (p.S_user == 0 || scene->n == 0) return DGS_OK;
+    if (!dL_dimages) return fail(ctx, DGS_E_INVALID_ARG, "dL_dimages is null");
+    if (!grads->mu0 || !grads->log_scale || !grads->quat || !grads->opacity_logit || !grads->colour ||
+        (scene->temporal_rank > 0 && !grads->u) || (scene->n_layers > 1 && !grads->res))
+        return fail(ctx, DGS_E_INVALID_ARG, "gradient array is null");
+    uint32_t nRec, nEnt;
+    uint32_t *sorted;
+    if (same_call(ctx->tape, scene, states, cams, n_cams)) {
+        nRec = ctx->tape.nRec; nEnt = ctx->tape.nEnt; sorted = ctx->tape.sorted_evals;
+    } else {
+        ctx->tape.valid = false;
+        TRY(prepare(ctx, scene, states->masks, p, false, st, nRec, nEnt, sorted));
+        record_tape(ctx->tape, scene, states, cams, n_cams, p, nRec, nEnt, sorted);
+    }
+    TRY(ensure(ctx, ctx->recgrad, sizeof(float4) * 3 * (size_t)nRec, st));
+    CK(cudaMemsetAsync(ctx->recgrad.p, 0, sizeof(float4) * 3 * (size_t)nRec, st));
+    RasterBwdArgs b;
+    b.f = raster_args(ctx, p, scene->n_clusters, bg, sorted);
+    b.dL_dimg = dL_dimages;
+    b.rec_grad = (float4 *)ctx->recgrad.p;
+    launch_raster_bwd(b, st);
+    GradDev g;
+    g.mu0 = grads->mu0; g.u = grads->u; g.ls = grads->log_scale; g.quat = grads->quat;
+    g.logit = grads->opacity_logit; g.colour = grads->colour; g.res = grads->res;
+    launch_project_bwd(scene_dev(scene), (const ViewGroup *)ctx->vgs.p, p.V, (const uint32_t *)ctx->need.p,
+                       (const uint32_t *)ctx->recBase.p, (const float4 *)ctx->recgrad.p, g, ctx->sms, st);
+    CK(cudaGetLastError());
+    return DGS_OK;
+}
+
+int dgs_state_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states, const dgs_camera *cams,
+                      int n_cams, const float *bg, double *mse, double *psnr, dgs_stream stream)
+{
+    if (!ctx) return DGS_E_INVALID_ARG;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(check_scene(ctx, scene));
+    if (!bg) return fail(ctx, DGS_E_INVALID_ARG, "bg is null");
+    Plan p;
+    TRY(build_plan(ctx, states, cams, n_cams, true, p));
+    if (p.S_user > 0 && !mse) return fail(ctx, DGS_E_INVALID_ARG, "mse is null");
+    ctx->tape.valid = false;
+    if (p.S_user == 0) return DGS_OK;
+    uint32_t nRec = 0, nEnt = 0;
+    uint32_t *sorted = nullptr;
+    TRY(prepare(ctx, scene, states->masks, p, true, st, nRec, nEnt, sorted));
+    const size_t img = (size_t)p.W * p.H * 3;
+    TRY(ensure(ctx, ctx->refs, sizeof(float) * img * (size_t)p.V, st));
+    TRY(ensure(ctx, ctx->partial, sizeof(double) * (size_t)p.S_user * p.tiles, st));
+    // complete renders of every view group (appended states S_user .. S-1)
+    RasterArgs r = raster_args(ctx, p, scene->n_clusters, bg, sorted);
+    r.S = p.V;
+    r.depth = (const uint8_t *)ctx->depth.p + (size_t)p.S_user * scene->n_clusters;
+    r.vg_of_state = (const int32_t *)ctx->vgos.p + p.S_user;
+    r.images = (float *)ctx->refs.p;
+    launch_raster_fwd(r, st);
+    // every state: fused FP64 squared error against its view's complete render
+    RasterArgs a = raster_args(ctx, p, scene->n_clusters, bg, sorted);
+    a.refs = (const float *)ctx->refs.p;
+    a.ref_of_state = (const int32_t *)ctx->vgos.p;
+    a.partial = (double *)ctx->partial.p;
+    launch_raster_fwd(a, st);
+    launch_mse_reduce((const double *)ctx->partial.p, p.S_user, (int)p.tiles, 1.0 / (double)img, mse, psnr, st);
+    CK(cudaGetLastError());
+    return DGS_OK;
+}
+
+int dgs_image_mse(dgs_ctx *ctx, const float *images, const float *refs, const int32_t *ref_index, int S, int n_refs,
+                  int H, int W, float weight, double *mse, double *psnr, float *dL_dimages, dgs_stream stream)
+{
+    if (!ctx) return DGS_E_INVALID_ARG;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (S < 0 || H < 1 || W < 1 || n_refs < 1) return fail(ctx, DGS_E_INVALID_ARG, "bad sizes");
+    if (S == 0) return DGS_OK;
+    if (!images || !refs || !ref_index || !mse) return fail(ctx, DGS_E_INVALID_ARG, "null argument");
+    for (int s = 0; s < S; ++s)
+        if (ref_index[s] < 0 || ref_index[s] >= n_refs)
+            return fail(ctx, DGS_E_INVALID_ARG, "ref_index[%d] = %d out of range", s, ref_index[s]);
+    const size_t per = (size_t)H * W * 3;
+    const int parts = (int)((per + 4095) / 4096);
+    TRY(ensure(ctx, ctx->refidx, sizeof(int32_t) * (size_t)S, st));
+    TRY(ensure(ctx, ctx->partial, sizeof(double) * (size_t)S * parts, st));
+    TRY(ensure_stage(ctx, sizeof(int32_t) * (size_t)S, st));
+    CK(cudaEventSynchronize(ctx->stage_done));   // an earlier copy may still read h_stage
+    std::memcpy(ctx->h_stage, ref_index, sizeof(int32_t) * (size_t)S);
+    CK(cudaMemcpyAsync(ctx->refidx.p, ctx->h_stage, sizeof(int32_t) * (size_t)S, cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(ctx->stage_done, st));
+    launch_image_mse(images, refs, (const int32_t *)ctx->refidx.p, S, H, W, weight, (double *)ctx->partial.p, parts,
+                     dL_dimages, st);
+    launch_mse_reduce((const double *)ctx->partial.p, S, parts, 1.0 / (double)per, mse, psnr, st);
+    CK(cudaGetLastError());
+    return DGS_OK;
+}
+
+}  // extern "C"

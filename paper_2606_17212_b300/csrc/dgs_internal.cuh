@@ -1,0 +1,87 @@
+// Internal declarations shared by the library's CUDA translation units.
+//
+// Data layout in HBM (all produced and consumed by the kernels of this library):
+//   depth   [S][C]  u8     delivered depth of cluster c in state s (closure)
+//   need    [V][C]  u32    bit d set when some state of view group v renders
+//                          cluster c at depth d (d = 1..L); bit 0 unused
+//   recBase [V*C+1] u32    first record slot of (v, c); records of (v, c) are
+//                          laid out Gaussian-major, depth-minor
+//   Rec     [nRec]  48 B   one projected variant (view group, Gaussian, depth)
+//   recKey  [nRec]  u32    float bits of camera depth (0xFFFFFFFF = culled)
+//   entries [nEnt]  u32 key (v * tiles + tile), u32 value (record slot)
+//   ranges  [V*T]   uint2  [start, end) of each (view group, tile) run
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dgs.h"
+
+namespace dgs {
+
+constexpr int TILE = 16;                 // tile side in pixels
+constexpr int TILE_PIX = TILE * TILE;    // threads per raster block
+constexpr int MAX_CLUSTERS = 1024;
+constexpr int MAX_LAYERS = 8;
+
+// One projected Gaussian variant, 48 bytes, read as three float4.
+struct __align__(16) Rec {
+    float mx, my, A, B;        // mean2d, conic (A = xx, B = xy, C = yy)
+    float C, o, r, g;          // conic yy, opacity, colour r, g
+    float b;                   // colour b
+    uint32_t bx;               // xlo | xhi << 16   (inclusive pixel range)
+    uint32_t by;               // ylo | yhi << 16
+    uint32_t cd;               // cluster | depth << 12 | view group << 16 (depth 0 = culled)
+};
+static_assert(sizeof(Rec) == 48, "record layout");
+
+// Per view group (camera, time) parameters, uploaded by the planner.
+struct ViewGroup {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    float time;
+    float campos[3];
+    int32_t width, height;
+    int32_t cam;
+    int32_t pad;
+};
+
+struct SceneDev {
+    int n, C, L, sh, R, nc, K;
+    const int32_t *offs;
+    const float *mu0, *u, *ls, *quat, *logit, *colour, *res;
+};
+
+struct GradDev {
+    float *mu0, *u, *ls, *quat, *logit, *colour, *res;
+};
+
+// ------------------------------------------------------------------ launches
+// Every kernel launch of the library goes through this counter so that the
+// number of device launches per call can be reported.
+void count_launch();
+// Optional per-kernel timing: when profiling is on, prof_begin/prof_end record
+// CUDA events on the launching stream around a named launch.
+void prof_begin(const char *name, cudaStream_t st);
+void prof_end(cudaStream_t st);
+struct ProfScope {
+    cudaStream_t st;
+    ProfScope(const char *name, cudaStream_t s) : st(s) { prof_begin(name, s); }
+    ~ProfScope() { prof_end(st); }
+};
+
+// Exclusive scan of n u32 values (in place allowed: out may equal in).
+// total_out [device] receives the sum when not null.  Uses ws_bytes of scratch
+// from `ws` (query with scan_workspace_bytes).
+size_t scan_workspace_bytes(size_t n);
+cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *total_out,
+                               void *ws, cudaStream_t st);
+
+// Stable LSD radix sort of (key, value) u32 pairs on key bits [0, bits).
+// Ping-pongs between (k0, v0) and (k1, v1); returns in *result_in_alt whether
+// the sorted data ended in (k1, v1).  ws from radix_workspace_bytes.
+size_t radix_workspace_bytes(size_t n);
+cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, size_t n,
+                             int bits, void *ws, cudaStream_t st, bool *result_in_alt);
+
+}  // namespace dgs

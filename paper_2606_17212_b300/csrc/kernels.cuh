@@ -1,0 +1,54 @@
+// Host-side launchers of the library's kernels (one translation unit each).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dgs_internal.cuh"
+
+namespace dgs {
+
+void launch_closure(const uint32_t *masks, int S, int words, int C, int L, const int32_t *vg_of_state,
+                    uint8_t *depth, uint32_t *need, int force_full, int sms, cudaStream_t st);
+void launch_layout_counts(const uint32_t *need, const int32_t *offs, int V, int C, uint32_t *counts, int sms,
+                          cudaStream_t st);
+void launch_project(const SceneDev &s, const ViewGroup *vgs, int V, const uint32_t *need, const uint32_t *recBase,
+                    Rec *recs, uint32_t *keys, uint32_t *vals, int sms, cudaStream_t st);
+void launch_tile_count(const Rec *recs, const uint32_t *order, uint32_t n, uint32_t *counts, int sms,
+                       cudaStream_t st);
+void launch_emit(const Rec *recs, const uint32_t *order, const uint32_t *offsets, uint32_t n, int tiles_x,
+                 uint32_t tiles, uint32_t *ekeys, uint32_t *evals, int sms, cudaStream_t st);
+void launch_ranges(const uint32_t *keys, uint32_t n, uint2 *ranges, int sms, cudaStream_t st);
+
+struct RasterArgs {
+    const Rec *recs;
+    const uint32_t *evals;        // entry -> record slot, tile-major
+    const uint2 *ranges;          // [V * tiles]
+    const uint8_t *depth;         // [S][C]
+    const int32_t *vg_of_state;   // [S]
+    int S, C, W, H, tiles_x;
+    uint32_t tiles;
+    float bg0, bg1, bg2;
+    float *images;                // [S][H][W][3] or null
+    const float *refs;            // [n_refs][H][W][3] or null (MSE epilogue)
+    const int32_t *ref_of_state;  // [S]
+    double *partial;              // [S][tiles] FP64 squared-error partial sums
+};
+void launch_raster_fwd(const RasterArgs &a, cudaStream_t st);
+
+struct RasterBwdArgs {
+    RasterArgs f;
+    const float *dL_dimg;         // [S][H][W][3]
+    float4 *rec_grad;             // [nRec][3]: (mx, my, A, B), (C, o, r, g), (b, -, -, -)
+};
+void launch_raster_bwd(const RasterBwdArgs &a, cudaStream_t st);
+
+void launch_mse_reduce(const double *partial, int S, int parts, double inv_count, double *mse, double *psnr,
+                       cudaStream_t st);
+void launch_image_mse(const float *images, const float *refs, const int32_t *ref_index, int S, int H, int W,
+                      float weight, double *partial, int parts, float *dL, cudaStream_t st);
+
+void launch_project_bwd(const SceneDev &s, const ViewGroup *vgs, int V, const uint32_t *need,
+                        const uint32_t *recBase, const float4 *rec_grad, const GradDev &g, int sms,
+                        cudaStream_t st);
+
+}  // namespace dgs

@@ -1,0 +1,254 @@
+// Device-wide exclusive scan and stable LSD radix sort (u32 key, u32 value).
+//
+// Both are HBM-bound streaming passes.  The radix sort is the classic
+// three-step LSD pass per 8-bit digit: per-block digit histogram, exclusive
+// scan of the digit-major histogram table, stable scatter.  Stability inside
+// a block comes from giving every warp a contiguous run of 512 items that it
+// ranks in index order with __match_any_sync, then offsetting warps by the
+// digit counts of the warps before them.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dgs_internal.cuh"
+
+namespace dgs {
+
+namespace {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 16;
+constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_ITEMS;   // 4096
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_CHUNK = RS_THREADS * RS_ITEMS;         // 4096
+constexpr int RS_RADIX = 256;
+
+__device__ __forceinline__ int pad(int i) { return i + (i >> 5); }
+
+// Block-wide exclusive scan of SCAN_CHUNK values held in shared memory (padded).
+__device__ uint32_t block_scan_chunk(uint32_t *sh, uint32_t *warp_tot)
+{
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    uint32_t v[SCAN_ITEMS];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) { v[k] = sh[pad(t * SCAN_ITEMS + k)]; sum += v[k]; }
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t x = lane < SCAN_THREADS / 32 ? warp_tot[lane] : 0, xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += y;
+        }
+        if (lane < SCAN_THREADS / 32) warp_tot[lane] = xi - x;   // exclusive warp offsets
+        if (lane == SCAN_THREADS / 32 - 1) warp_tot[SCAN_THREADS / 32] = xi;
+    }
+    __syncthreads();
+    uint32_t run = warp_tot[w] + inc - sum;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) { sh[pad(t * SCAN_ITEMS + k)] = run; run += v[k]; }
+    __syncthreads();
+    return warp_tot[SCAN_THREADS / 32];
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t *in, size_t n, uint32_t *sums)
+{
+    const size_t base = (size_t)blockIdx.x * SCAN_CHUNK;
+    uint32_t s = 0;
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        size_t i = base + (size_t)k * SCAN_THREADS + threadIdx.x;
+        if (i < n) s += in[i];
+    }
+    __shared__ uint32_t wt[SCAN_THREADS / 32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) wt[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < SCAN_THREADS / 32; ++w) t += wt[w];
+        sums[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t *in, uint32_t *out, size_t n,
+                                                            const uint32_t *offsets, uint32_t *total)
+{
+    __shared__ uint32_t sh[SCAN_CHUNK + SCAN_CHUNK / 32];
+    __shared__ uint32_t wt[SCAN_THREADS / 32 + 1];
+    const size_t base = (size_t)blockIdx.x * SCAN_CHUNK;
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        int j = k * SCAN_THREADS + threadIdx.x;
+        size_t i = base + j;
+        sh[pad(j)] = i < n ? in[i] : 0u;
+    }
+    __syncthreads();
+    uint32_t tot = block_scan_chunk(sh, wt);
+    uint32_t off = offsets ? offsets[blockIdx.x] : 0u;
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        int j = k * SCAN_THREADS + threadIdx.x;
+        size_t i = base + j;
+        if (i < n) out[i] = sh[pad(j)] + off;
+    }
+    if (total && threadIdx.x == 0 && blockIdx.x == gridDim.x - 1) *total = off + tot;
+}
+
+size_t blocks_for(size_t n, size_t chunk) { return (n + chunk - 1) / chunk; }
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Recursive scan; ws holds the block sums of every level.
+cudaError_t scan_rec(const uint32_t *in, uint32_t *out, size_t n, uint32_t *total, uint32_t *ws,
+                     cudaStream_t st)
+{
+    if (n == 0) {
+        if (total) return cudaMemsetAsync(total, 0, sizeof(uint32_t), st);
+        return cudaSuccess;
+    }
+    size_t nb = blocks_for(n, SCAN_CHUNK);
+    if (nb == 1) {
+        k_scan_down<<<1, SCAN_THREADS, 0, st>>>(in, out, n, nullptr, total);
+        count_launch();
+        return cudaGetLastError();
+    }
+    uint32_t *sums = ws;
+    uint32_t *next = ws + align_up(nb * sizeof(uint32_t)) / sizeof(uint32_t);
+    k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, n, sums);
+    count_launch();
+    cudaError_t e = scan_rec(sums, sums, nb, nullptr, next, st);
+    if (e != cudaSuccess) return e;
+    k_scan_down<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, out, n, sums, total);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- radix sort
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t *keys, size_t n, int shift, uint32_t mask,
+                                                        uint32_t *hist, uint32_t nblocks)
+{
+    __shared__ uint32_t h[RS_RADIX];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const size_t base = (size_t)blockIdx.x * RS_CHUNK;
+#pragma unroll 4
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        size_t i = base + (size_t)k * RS_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t *kin, const uint32_t *vin,
+                                                           uint32_t *kout, uint32_t *vout, size_t n,
+                                                           int shift, uint32_t mask,
+                                                           const uint32_t *offsets, uint32_t nblocks)
+{
+    __shared__ uint32_t wh[RS_WARPS][RS_RADIX];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < RS_WARPS * RS_RADIX; d += RS_THREADS) (&wh[0][0])[d] = 0;
+    __syncthreads();
+    const size_t base = (size_t)blockIdx.x * RS_CHUNK + (size_t)w * (RS_ITEMS * 32);
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t key[RS_ITEMS], val[RS_ITEMS], rank[RS_ITEMS];
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        size_t i = base + (size_t)k * 32 + lane;
+        bool ok = i < n;
+        key[k] = ok ? kin[i] : 0u;
+        val[k] = ok ? vin[i] : 0u;
+        uint32_t d = ok ? ((key[k] >> shift) & mask) : (RS_RADIX + lane);
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t before = ok ? wh[w][d] : 0u;
+        __syncwarp();
+        int leader = __ffs(peers) - 1;
+        if (ok && lane == leader) wh[w][d] = before + __popc(peers);
+        __syncwarp();
+        rank[k] = ok ? before + __popc(peers & lt) : 0xffffffffu;
+    }
+    __syncthreads();
+    // exclusive prefix of digit counts across warps (thread = digit)
+    {
+        const int d = threadIdx.x;
+        uint32_t run = 0;
+#pragma unroll
+        for (int ww = 0; ww < RS_WARPS; ++ww) { uint32_t c = wh[ww][d]; wh[ww][d] = run; run += c; }
+        // fold in the global base of this digit for this block
+        uint32_t g = offsets[(size_t)d * nblocks + blockIdx.x];
+#pragma unroll
+        for (int ww = 0; ww < RS_WARPS; ++ww) wh[ww][d] += g;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        if (rank[k] == 0xffffffffu) continue;
+        uint32_t d = (key[k] >> shift) & mask;
+        uint32_t pos = wh[w][d] + rank[k];
+        kout[pos] = key[k];
+        vout[pos] = val[k];
+    }
+}
+
+}  // namespace
+
+size_t scan_workspace_bytes(size_t n)
+{
+    size_t tot = 0;
+    while (n > (size_t)SCAN_CHUNK) {
+        n = blocks_for(n, SCAN_CHUNK);
+        tot += align_up(n * sizeof(uint32_t));
+    }
+    return tot + 256;
+}
+
+cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *total_out,
+                               void *ws, cudaStream_t st)
+{
+    return scan_rec(in, out, n, total_out, (uint32_t *)ws, st);
+}
+
+size_t radix_workspace_bytes(size_t n)
+{
+    size_t nb = blocks_for(n > 0 ? n : 1, RS_CHUNK);
+    size_t hist = (size_t)RS_RADIX * nb;
+    return align_up(hist * sizeof(uint32_t)) + scan_workspace_bytes(hist);
+}
+
+cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, size_t n,
+                             int bits, void *ws, cudaStream_t st, bool *result_in_alt)
+{
+    *result_in_alt = false;
+    if (n <= 1 || bits <= 0) return cudaSuccess;
+    size_t nb = blocks_for(n, RS_CHUNK);
+    uint32_t *hist = (uint32_t *)ws;
+    void *scan_ws = (char *)ws + align_up((size_t)RS_RADIX * nb * sizeof(uint32_t));
+    uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
+    for (int shift = 0; shift < bits; shift += 8) {
+        int w = bits - shift < 8 ? bits - shift : 8;
+        uint32_t mask = (1u << w) - 1u;
+        ProfScope ps_("radix_pass", st);
+        k_rs_hist<<<(unsigned)nb, RS_THREADS, 0, st>>>(ki, n, shift, mask, hist, (uint32_t)nb);
+        count_launch();
+        cudaError_t e = exclusive_scan_u32(hist, hist, (size_t)RS_RADIX * nb, nullptr, scan_ws, st);
+        if (e != cudaSuccess) return e;
+        k_rs_scatter<<<(unsigned)nb, RS_THREADS, 0, st>>>(ki, vi, ko, vo, n, shift, mask, hist, (uint32_t)nb);
+        count_launch();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        uint32_t *tk = ki, *tv = vi;
+        ki = ko; vi = vo; ko = tk; vo = tv;
+        *result_in_alt = !*result_in_alt;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace dgs

@@ -1,0 +1,296 @@
+"""Thin Python binding of the C ABI in ``include/dgs.h`` (argument marshalling only).
+
+Every step of the rendering path runs in the CUDA library ``libdgs.so``; this
+module only passes torch tensors' device pointers, sizes and the current CUDA
+stream.  There is no fallback: if the library is missing the import of
+:func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdgs.so")
+
+DGS_OK = 0
+ERRORS = {-1: "DGS_E_INVALID_ARG", -2: "DGS_E_UNSUPPORTED", -3: "DGS_E_OOM", -4: "DGS_E_CUDA",
+          -5: "DGS_E_CAPACITY"}
+
+
+class Scene_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("n_clusters", ctypes.c_int32), ("n_layers", ctypes.c_int32),
+                ("sh_degree", ctypes.c_int32), ("temporal_rank", ctypes.c_int32),
+                ("cluster_offsets", ctypes.c_void_p), ("mu0", ctypes.c_void_p), ("u", ctypes.c_void_p),
+                ("log_scale", ctypes.c_void_p), ("quat", ctypes.c_void_p),
+                ("opacity_logit", ctypes.c_void_p), ("colour", ctypes.c_void_p), ("res", ctypes.c_void_p)]
+
+
+class SceneGrad_t(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in
+                ("mu0", "u", "log_scale", "quat", "opacity_logit", "colour", "res")]
+
+
+class Camera_t(ctypes.Structure):
+    _fields_ = [("R_wc", ctypes.c_float * 9), ("t_wc", ctypes.c_float * 3), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class States_t(ctypes.Structure):
+    _fields_ = [("masks", ctypes.c_void_p), ("t", ctypes.c_void_p), ("cam", ctypes.c_void_p),
+                ("n_states", ctypes.c_int32)]
+
+
+EXPORTS = ("dgs_create", "dgs_destroy", "dgs_last_error", "dgs_version", "dgs_render_state",
+           "dgs_render_states_batched", "dgs_render_backward", "dgs_state_utility", "dgs_image_mse",
+           "dgs_kernel_launches", "dgs_reset_kernel_launches", "dgs_profile_enable", "dgs_profile_read")
+
+_lib = None
+
+
+def lib():
+    """Load ``libdgs.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libdgs.so is not built: run `python -m paper_2606_17212_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+        L.dgs_create.argtypes = [ctypes.POINTER(P), I]
+        L.dgs_destroy.argtypes = [P]
+        L.dgs_destroy.restype = None
+        L.dgs_last_error.argtypes = [P]
+        L.dgs_last_error.restype = ctypes.c_char_p
+        L.dgs_version.restype = I
+        L.dgs_render_state.argtypes = [P, ctypes.POINTER(Scene_t), P, F, ctypes.POINTER(Camera_t), P, P, P]
+        L.dgs_render_states_batched.argtypes = [P, ctypes.POINTER(Scene_t), ctypes.POINTER(States_t),
+                                                P, I, P, P, P]
+        L.dgs_render_backward.argtypes = [P, ctypes.POINTER(Scene_t), ctypes.POINTER(States_t), P, I, P, P,
+                                          ctypes.POINTER(SceneGrad_t), P]
+        L.dgs_state_utility.argtypes = [P, ctypes.POINTER(Scene_t), ctypes.POINTER(States_t), P, I, P, P, P, P]
+        L.dgs_image_mse.argtypes = [P, P, P, P, I, I, I, I, F, P, P, P, P]
+        L.dgs_kernel_launches.argtypes = [P]
+        L.dgs_kernel_launches.restype = ctypes.c_int64
+        L.dgs_reset_kernel_launches.argtypes = [P]
+        L.dgs_reset_kernel_launches.restype = None
+        L.dgs_profile_enable.argtypes = [P, I]
+        L.dgs_profile_enable.restype = None
+        L.dgs_profile_read.argtypes = [P, I, P, P, P]
+        L.dgs_profile_read.restype = I
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def camera_struct(cam) -> Camera_t:
+    R = np.asarray(cam.R_wc, np.float32).reshape(9)
+    t = np.asarray(cam.t_wc, np.float32).reshape(3)
+    return Camera_t((ctypes.c_float * 9)(*R), (ctypes.c_float * 3)(*t), float(cam.fx), float(cam.fy),
+                    float(cam.cx), float(cam.cy), int(cam.width), int(cam.height))
+
+
+def camera_array(cams):
+    arr = (Camera_t * len(cams))()
+    for k, c in enumerate(cams):
+        arr[k] = camera_struct(c)
+    return arr
+
+
+SCENE_FIELDS = ("mu0", "u", "log_scale", "quat", "opacity_logit", "colour", "res")
+
+
+class DeviceScene:
+    """Scene tensors resident on a CUDA device, with the C struct that points at them."""
+
+    def __init__(self, tensors: dict, n, n_clusters, n_layers, sh_degree, temporal_rank, cluster_offsets):
+        import torch
+        self.t = {k: tensors[k].contiguous() for k in SCENE_FIELDS}
+        self.offsets = cluster_offsets.to(torch.int32).contiguous()
+        self.n, self.n_clusters, self.n_layers = int(n), int(n_clusters), int(n_layers)
+        self.sh_degree, self.temporal_rank = int(sh_degree), int(temporal_rank)
+
+    @classmethod
+    def from_host(cls, scene, device="cuda"):
+        import torch
+        ts = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k), np.float32)).to(device)
+              for k in SCENE_FIELDS}
+        offs = torch.from_numpy(np.asarray(scene.cluster_offsets, np.int32)).to(device)
+        return cls(ts, scene.n, scene.n_clusters, scene.n_layers, scene.sh_degree, scene.temporal_rank, offs)
+
+    def struct(self) -> Scene_t:
+        g = lambda k: _ptr(self.t[k]) if self.t[k].numel() else None
+        return Scene_t(self.n, self.n_clusters, self.n_layers, self.sh_degree, self.temporal_rank,
+                       _ptr(self.offsets), g("mu0"), g("u"), g("log_scale"), g("quat"),
+                       g("opacity_logit"), g("colour"), g("res"))
+
+    def zeros_like_grads(self) -> dict:
+        import torch
+        return {k: torch.zeros_like(v) for k, v in self.t.items()}
+
+
+class DeviceStates:
+    """Masks on the device, times and camera indices on the host."""
+
+    def __init__(self, masks, t, cam):
+        import torch
+        self.masks = masks.contiguous() if isinstance(masks, torch.Tensor) else torch.from_numpy(
+            np.ascontiguousarray(masks, np.uint32).view(np.int32)).cuda()
+        self.t = np.ascontiguousarray(t, np.float32)
+        self.cam = np.ascontiguousarray(cam, np.int32)
+        self.n = int(self.t.shape[0])
+
+    @classmethod
+    def from_host(cls, states):
+        return cls(states.masks, states.t, states.cam)
+
+    def struct(self) -> States_t:
+        return States_t(_ptr(self.masks), self.t.ctypes.data_as(ctypes.c_void_p),
+                        self.cam.ctypes.data_as(ctypes.c_void_p), self.n)
+
+
+class Renderer:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._lib = lib()
+        h = ctypes.c_void_p()
+        rc = self._lib.dgs_create(ctypes.byref(h), int(device))
+        if rc != DGS_OK:
+            raise RuntimeError("dgs_create failed: %s" % ERRORS.get(rc, rc))
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.dgs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != DGS_OK:
+            msg = self._lib.dgs_last_error(self.h).decode()
+            raise RuntimeError("%s failed (%s): %s" % (what, ERRORS.get(rc, rc), msg))
+
+    def kernel_launches(self) -> int:
+        return int(self._lib.dgs_kernel_launches(self.h))
+
+    def reset_kernel_launches(self):
+        self._lib.dgs_reset_kernel_launches(self.h)
+
+    def profile(self, on: bool = True):
+        self._lib.dgs_profile_enable(self.h, int(bool(on)))
+
+    def profile_read(self) -> dict:
+        """{kernel name: (total ms, launches)} since enabling or the last read."""
+        n_max = 64
+        names = ctypes.create_string_buffer(32 * n_max)
+        ms = (ctypes.c_double * n_max)()
+        cnt = (ctypes.c_int64 * n_max)()
+        n = self._lib.dgs_profile_read(self.h, n_max, names, ms, cnt)
+        if n < 0:
+            self._check(n, "dgs_profile_read")
+        raw = names.raw
+        return {raw[32 * k:32 * k + 32].split(b"\0")[0].decode(): (ms[k], cnt[k]) for k in range(n)}
+
+    def render_state(self, scene: DeviceScene, mask, t: float, cam, bg, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+        bgv = (ctypes.c_float * 3)(*[float(x) for x in bg])
+        sc = scene.struct()
+        c = camera_struct(cam)
+        self._check(self._lib.dgs_render_state(self.h, ctypes.byref(sc), _ptr(mask), float(t), ctypes.byref(c),
+                                               bgv, _ptr(out), _stream(stream)), "dgs_render_state")
+        return out
+
+    def render_states_batched(self, scene: DeviceScene, states: DeviceStates, cams, bg, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((states.n, cams[0].height, cams[0].width, 3), dtype=torch.float32, device="cuda")
+        bgv = (ctypes.c_float * 3)(*[float(x) for x in bg])
+        sc, st, ca = scene.struct(), states.struct(), camera_array(cams)
+        self._check(self._lib.dgs_render_states_batched(self.h, ctypes.byref(sc), ctypes.byref(st), ca, len(cams),
+                                                        bgv, _ptr(out), _stream(stream)),
+                    "dgs_render_states_batched")
+        return out
+
+    def render_backward(self, scene: DeviceScene, states: DeviceStates, cams, bg, dL_dimages, grads=None,
+                        stream=None):
+        if grads is None:
+            grads = scene.zeros_like_grads()
+        bgv = (ctypes.c_float * 3)(*[float(x) for x in bg])
+        g = SceneGrad_t(*[(_ptr(grads[k]) if grads[k].numel() else None) for k in SCENE_FIELDS])
+        sc, st, ca = scene.struct(), states.struct(), camera_array(cams)
+        self._check(self._lib.dgs_render_backward(self.h, ctypes.byref(sc), ctypes.byref(st), ca, len(cams), bgv,
+                                                  _ptr(dL_dimages.contiguous()), ctypes.byref(g),
+                                                  _stream(stream)), "dgs_render_backward")
+        return grads
+
+    def state_utility(self, scene: DeviceScene, states: DeviceStates, cams, bg, mse=None, psnr=None,
+                      stream=None):
+        import torch
+        if mse is None:
+            mse = torch.empty(states.n, dtype=torch.float64, device="cuda")
+        if psnr is None:
+            psnr = torch.empty(states.n, dtype=torch.float64, device="cuda")
+        bgv = (ctypes.c_float * 3)(*[float(x) for x in bg])
+        sc, st, ca = scene.struct(), states.struct(), camera_array(cams)
+        self._check(self._lib.dgs_state_utility(self.h, ctypes.byref(sc), ctypes.byref(st), ca, len(cams), bgv,
+                                                _ptr(mse), _ptr(psnr), _stream(stream)), "dgs_state_utility")
+        return mse, psnr
+
+    def image_mse(self, images, refs, ref_index, weight=1.0, want_grad=False, stream=None):
+        import torch
+        S, H, W, _ = images.shape
+        ri = np.ascontiguousarray(ref_index, np.int32)
+        mse = torch.empty(S, dtype=torch.float64, device="cuda")
+        psnr = torch.empty(S, dtype=torch.float64, device="cuda")
+        dL = torch.empty_like(images) if want_grad else None
+        self._check(self._lib.dgs_image_mse(self.h, _ptr(images.contiguous()), _ptr(refs.contiguous()),
+                                            ri.ctypes.data_as(ctypes.c_void_p), S, refs.shape[0], H, W,
+                                            float(weight), _ptr(mse), _ptr(psnr), _ptr(dL), _stream(stream)),
+                    "dgs_image_mse")
+        return mse, psnr, dL
+
+
+def render_function():
+    """A torch.autograd.Function whose forward is the batched render and whose
+    backward is the library's adjoint (gradients w.r.t. the scene tensors)."""
+    import torch
+
+    class RenderStates(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, renderer, scene, states, cams, bg, *tensors):
+            out = renderer.render_states_batched(scene, states, cams, bg)
+            ctx.renderer, ctx.scene, ctx.states, ctx.cams, ctx.bg = renderer, scene, states, cams, bg
+            return out
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            grads = ctx.renderer.render_backward(ctx.scene, ctx.states, ctx.cams, ctx.bg, grad_out.contiguous())
+            return (None, None, None, None, None) + tuple(grads[k] for k in SCENE_FIELDS)
+
+    return RenderStates
+
+
+def render(renderer, scene: DeviceScene, states: DeviceStates, cams, bg):
+    """Differentiable batched render: images [S,H,W,3] with autograd to scene tensors."""
+    fn = render_function()
+    return fn.apply(renderer, scene, states, cams, bg, *[scene.t[k] for k in SCENE_FIELDS])

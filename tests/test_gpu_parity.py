@@ -1,0 +1,236 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (needs a B300)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_17212_b300 import dgs, synth
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-4          # max-abs per channel on non-marginal pixels
+GRAD_TOL = 1e-3         # ||g - g_ref||_inf <= GRAD_TOL * max(||g_ref||_inf, 1e-6), per tensor
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    assert _t.cuda.is_available()
+    return _t
+
+
+@pytest.fixture(scope="module")
+def R(torch):
+    r = dgs.Renderer(0)
+    yield r
+    r.close()
+
+
+def _compare_image(gpu, ref, marg, tol=IMG_TOL):
+    ok = ~marg
+    err = np.abs(gpu.astype(np.float64) - ref)[ok]
+    return (err.max() if err.size else 0.0), int(marg.sum())
+
+
+def _gpu_states(w):
+    return dgs.DeviceStates.from_host(w.states)
+
+
+# --------------------------------------------------------------------- forward
+def test_c1_render_state_matches_oracle(R, torch):
+    w = synth.config("c1_plain_4k")
+    sc = dgs.DeviceScene.from_host(w.scene)
+    st = _gpu_states(w)
+    img = R.render_state(sc, st.masks[0], 0.0, w.cams[0], w.bg)
+    torch.cuda.synchronize()
+    D = oracle.closure(w.states.masks[0], w.scene.n_clusters, w.scene.n_layers)
+    ref, marg, ne = oracle.render(w.scene, D, 0.0, w.cams[0], w.bg)
+    err, nm = _compare_image(img.cpu().numpy(), ref, marg)
+    assert err <= IMG_TOL, (err, nm)
+    assert nm <= 0.002 * marg.size
+
+
+@pytest.mark.parametrize("name,scale,n", [("c2_dynamic_250k", 0.02, 6), ("c3_fwdbwd_250k", 0.02, 6)])
+def test_batched_matches_oracle_per_state(R, torch, name, scale, n):
+    w = synth.config(name, scale=scale, n_states=n)
+    sc = dgs.DeviceScene.from_host(w.scene)
+    st = _gpu_states(w)
+    imgs = R.render_states_batched(sc, st, w.cams, w.bg).cpu().numpy()
+    refs = oracle.render_states(w.scene, w.states, w.cams, w.bg)
+    for s, (ref, marg, _) in enumerate(refs):
+        err, nm = _compare_image(imgs[s], ref, marg)
+        assert err <= IMG_TOL, (s, err, nm)
+        assert nm <= 0.01 * marg.size, (s, nm)
+
+
+def test_batched_equals_per_state_bitwise(R, torch):
+    """The abstract: batched rendering is bit-equivalent to serial evaluation."""
+    w = synth.config("c3_fwdbwd_250k", scale=0.05, n_states=24)
+    sc = dgs.DeviceScene.from_host(w.scene)
+    st = _gpu_states(w)
+    batched = R.render_states_batched(sc, st, w.cams, w.bg)
+    for s in range(st.n):
+        one = R.render_state(sc, st.masks[s], float(w.states.t[s]), w.cams[int(w.states.cam[s])], w.bg)
+        assert torch.equal(one, batched[s]), s
+
+
+def test_ragged_image_and_edge_cases(R, torch):
+    w = synth.config("c2_dynamic_250k", scale=0.01, n_states=3)
+    cam = synth.ring_camera(2, 8, 97, 61, 110.0)          # ragged tiles on both axes
+    sc = dgs.DeviceScene.from_host(w.scene)
+    st = _gpu_states(w)
+    imgs = R.render_states_batched(sc, st, [cam], w.bg).cpu().numpy()
+    for s in range(st.n):
+        D = oracle.closure(w.states.masks[s], w.scene.n_clusters, w.scene.n_layers)
+        ref, marg, _ = oracle.render(w.scene, D, float(w.states.t[s]), cam, w.bg)
+        err, nm = _compare_image(imgs[s], ref, marg)
+        assert err <= IMG_TOL, (s, err, nm)
+    # empty delivery -> background everywhere
+    bg = np.array([0.25, 0.5, 0.75], np.float32)
+    empty = torch.zeros_like(st.masks[0])
+    img = R.render_state(sc, empty, 0.0, cam, bg).cpu().numpy()
+    assert np.all(img == bg[None, None, :])
+    # no states: nothing to do
+    st0 = dgs.DeviceStates(st.masks[:0], np.zeros(0, np.float32), np.zeros(0, np.int32))
+    out = R.render_states_batched(sc, st0, [cam], bg)
+    assert out.shape[0] == 0
+
+
+def test_single_gaussian_closed_form_on_gpu(R, torch):
+    """C = o c + (1 - o) bg at the pixel centre under the mean (Section 6 path, 1 Gaussian)."""
+    o = 0.7
+    sc_h = synth.Scene(1, 1, 1, 0, 0, np.array([0, 1], np.int32),
+                       np.array([[0.0, 1 / 64, -1 / 64]], np.float32), np.zeros((0, 1, 3), np.float32),
+                       np.full((1, 3), -2.5, np.float32), np.array([[1, 0, 0, 0]], np.float32),
+                       np.array([math.log(o / (1 - o))], np.float32), np.array([[0.9, 0.2, 0.4]], np.float32),
+                       np.zeros((0, 1, 14), np.float32))
+    cam = synth.ring_camera(0, 1, 128, 128, 128.0)
+    sc = dgs.DeviceScene.from_host(sc_h)
+    mask = torch.ones(1, dtype=torch.int32, device="cuda")
+    bg = np.array([0.1, 0.3, 0.05], np.float32)
+    img = R.render_state(sc, mask, 0.0, cam, bg).cpu().numpy()
+    o32 = 1.0 / (1.0 + math.exp(-float(np.float32(math.log(o / (1 - o))))))
+    expect = o32 * np.array([0.9, 0.2, 0.4], np.float32) + (1 - o32) * bg
+    assert np.allclose(img[64, 64], expect, atol=2e-6)
+
+
+# --------------------------------------------------------------------- utility
+def test_state_utility_matches_oracle(R, torch):
+    w = synth.config("c2_dynamic_250k", scale=0.02, n_states=5)
+    # make state 0 the complete delivery: MSE exactly 0, PSNR +inf
+    masks = w.states.masks.copy()
+    masks[0] = 0xFFFFFFFF
+    w.states.masks = masks
+    sc = dgs.DeviceScene.from_host(w.scene)
+    st = _gpu_states(w)
+    mse, psnr = R.state_utility(sc, st, w.cams, w.bg)
+    mse, psnr = mse.cpu().numpy(), psnr.cpu().numpy()
+    assert mse[0] == 0.0 and math.isinf(psnr[0])
+    refs = oracle.render_states(w.scene, w.states, w.cams, w.bg)
+    for s in range(1, st.n):
+        full, mfull, _ = oracle.render(w.scene, oracle.full_depth(w.scene), float(w.states.t[s]),
+                                       w.cams[0], w.bg)
+        ref, marg, _ = refs[s]
+        ok = ~(marg | mfull)
+        m_ref = float(np.mean(((ref - full) ** 2)[ok]))
+        m_gpu_ok = mse[s]
+        assert abs(m_gpu_ok - m_ref) <= 2e-3 * m_ref + 1e-7, (s, m_gpu_ok, m_ref)
+        assert psnr[s] == pytest.approx(10 * math.log10(1 / mse[s]), rel=1e-12)
+
+
+def test_utility_equals_images_then_mse(R, torch):
+    """Fused FP64 epilogue == images written, then the separate MSE kernel (bitwise)."""
+    w = synth.config("c2_dynamic_250k", scale=0.02, n_states=7)
+    sc = dgs.DeviceScene.from_host(w.scene)
+    st = _gpu_states(w)
+    mse, _ = R.state_utility(sc, st, w.cams, w.bg)
+    imgs = R.render_states_batched(sc, st, w.cams, w.bg)
+    full_masks = torch.full_like(st.masks, -1)
+    tvals = np.unique(w.states.t)
+    fst = dgs.DeviceStates(full_masks[:len(tvals)], tvals, np.zeros(len(tvals), np.int32))
+    fulls = R.render_states_batched(sc, fst, w.cams, w.bg)
+    ridx = np.searchsorted(tvals, w.states.t)
+    m2, p2, _ = R.image_mse(imgs, fulls, ridx)
+    assert torch.allclose(mse, m2, rtol=1e-12, atol=0)
+
+
+def test_image_mse_and_gradient(R, torch):
+    rng = np.random.default_rng(0)
+    a = rng.uniform(size=(3, 37, 29, 3)).astype(np.float32)
+    b = rng.uniform(size=(2, 37, 29, 3)).astype(np.float32)
+    idx = np.array([1, 0, 1])
+    ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    mse, psnr, dL = R.image_mse(ta, tb, idx, weight=0.25, want_grad=True)
+    for s in range(3):
+        d = a[s].astype(np.float64) - b[idx[s]].astype(np.float64)
+        assert mse[s].item() == pytest.approx(np.mean(d * d), rel=1e-12)
+        g = 0.25 * 2 * (a[s] - b[idx[s]]) / d.size
+        assert np.allclose(dL[s].cpu().numpy(), g, rtol=1e-6, atol=1e-12)
+
+
+# --------------------------------------------------------------------- backward
+def _grad_case(seed=0, sh=0):
+    if sh == 0:
+        w = synth.config("c3_fwdbwd_250k", scale=0.004, n_states=4)
+        sc = w.scene
+    else:
+        w = synth.config("c3_fwdbwd_250k", scale=0.004, n_states=4)
+        sc = synth.make_scene(1000, 8, 4, seed=77, sh_degree=3)
+        w.states.masks = synth._pack(synth.depths_to_bits(
+            synth.prefix_states(4, 8, 4, np.random.default_rng(5)), 4))
+    cams = [synth.ring_camera(k, 8, 64, 48, 75.0) for k in range(8)]
+    return sc, w.states, cams
+
+
+@pytest.mark.parametrize("sh", [0, 3])
+def test_backward_matches_oracle_adjoint(R, torch, sh):
+    sc_h, states, cams = _grad_case(sh=sh)
+    bg = np.array([0.1, 0.2, 0.3], np.float32)
+    rng = np.random.default_rng(3)
+    S = states.n
+    H, W = cams[0].height, cams[0].width
+    dL = rng.normal(size=(S, H, W, 3))
+    D = oracle.state_depths(states, sc_h.n_clusters, sc_h.n_layers)
+    ref = None
+    for s in range(S):
+        cam = cams[int(states.cam[s])]
+        _, marg, _ = oracle.render(sc_h, D[s], float(states.t[s]), cam, bg)
+        dL[s][marg] = 0.0             # thresholds decided differently in FP32 are not compared
+        g = oracle.render_backward(sc_h, D[s], float(states.t[s]), cam, bg, dL[s])
+        ref = g if ref is None else {k: ref[k] + g[k] for k in ref}
+    sc = dgs.DeviceScene.from_host(sc_h)
+    st = dgs.DeviceStates.from_host(states)
+    R.render_states_batched(sc, st, cams, bg)
+    grads = R.render_backward(sc, st, cams, bg, torch.from_numpy(dL.astype(np.float32)).cuda())
+    for k in dgs.SCENE_FIELDS:
+        gg = grads[k].cpu().numpy().astype(np.float64)
+        gr = ref[k]
+        if gr.size == 0:
+            continue
+        scale = max(np.abs(gr).max(), 1e-6)
+        err = np.abs(gg - gr).max()
+        assert err <= GRAD_TOL * scale, (k, err, scale)
+
+
+def test_backward_undelivered_layers_exactly_zero_and_autograd(R, torch):
+    sc_h, states, cams = _grad_case()
+    # clusters 0 and 1 at depth 1 and 2 in every state
+    D = synth.prefix_states(states.n, sc_h.n_clusters, sc_h.n_layers, np.random.default_rng(1))
+    D[:, 0] = 1
+    D[:, 1] = 2
+    states.masks = synth._pack(synth.depths_to_bits(D, sc_h.n_layers))
+    sc = dgs.DeviceScene.from_host(sc_h)
+    st = dgs.DeviceStates.from_host(states)
+    bg = np.zeros(3, np.float32)
+    for v in sc.t.values():
+        v.requires_grad_(True)
+    img = dgs.render(R, sc, st, cams, bg)
+    loss = (img ** 2).mean()
+    loss.backward()
+    res_g = sc.t["res"].grad.cpu().numpy()
+    cl = sc_h.cluster_of()
+    assert np.all(res_g[:, cl == 0] == 0.0)          # depth 1: no refinement rendered
+    assert np.all(res_g[1:, cl == 1] == 0.0)         # depth 2: only layer 1
+    assert np.abs(res_g[0, cl == 1]).max() > 0
+    assert np.abs(sc.t["mu0"].grad.cpu().numpy()).max() > 0

@@ -117,10 +117,12 @@ def test_single_gaussian_closed_form_on_gpu(R, torch):
 
 # --------------------------------------------------------------------- utility
 def test_state_utility_matches_oracle(R, torch):
-    w = synth.config("c2_dynamic_250k", scale=0.02, n_states=5)
-    # make state 0 the complete delivery: MSE exactly 0, PSNR +inf
+    """Eq. 3 D per state vs the oracle.  States whose oracle renders (state and
+    complete) have no marginal pixel are compared with the bound that a 1e-4
+    per-value image error allows: |dMSE| <= mean(4 eps |d| + 4 eps^2)."""
+    w = synth.config("c2_dynamic_250k", scale=0.004, n_states=8)
     masks = w.states.masks.copy()
-    masks[0] = 0xFFFFFFFF
+    masks[0] = 0xFFFFFFFF             # complete delivery: MSE exactly 0, PSNR +inf
     w.states.masks = masks
     sc = dgs.DeviceScene.from_host(w.scene)
     st = _gpu_states(w)
@@ -128,15 +130,20 @@ def test_state_utility_matches_oracle(R, torch):
     mse, psnr = mse.cpu().numpy(), psnr.cpu().numpy()
     assert mse[0] == 0.0 and math.isinf(psnr[0])
     refs = oracle.render_states(w.scene, w.states, w.cams, w.bg)
+    checked = 0
     for s in range(1, st.n):
         full, mfull, _ = oracle.render(w.scene, oracle.full_depth(w.scene), float(w.states.t[s]),
                                        w.cams[0], w.bg)
         ref, marg, _ = refs[s]
-        ok = ~(marg | mfull)
-        m_ref = float(np.mean(((ref - full) ** 2)[ok]))
-        m_gpu_ok = mse[s]
-        assert abs(m_gpu_ok - m_ref) <= 2e-3 * m_ref + 1e-7, (s, m_gpu_ok, m_ref)
+        if marg.any() or mfull.any():
+            continue
+        d = ref - full
+        m_ref = float(np.mean(d * d))
+        bound = float(np.mean(4 * IMG_TOL * np.abs(d) + 4 * IMG_TOL ** 2))
+        assert abs(mse[s] - m_ref) <= bound, (s, mse[s], m_ref, bound)
         assert psnr[s] == pytest.approx(10 * math.log10(1 / mse[s]), rel=1e-12)
+        checked += 1
+    assert checked >= 2
 
 
 def test_utility_equals_images_then_mse(R, torch):
@@ -215,10 +222,15 @@ def test_backward_matches_oracle_adjoint(R, torch, sh):
 
 def test_backward_undelivered_layers_exactly_zero_and_autograd(R, torch):
     sc_h, states, cams = _grad_case()
-    # clusters 0 and 1 at depth 1 and 2 in every state
+    # the two clusters with the most Gaussians in view of state 0 go to depth 1 and 2
+    full = oracle.full_depth(sc_h)
+    rec = oracle.project(sc_h, full, float(states.t[0]), cams[int(states.cam[0])])
+    cl = sc_h.cluster_of()
+    seen = np.bincount(cl, weights=rec[:, 0], minlength=sc_h.n_clusters)
+    c1, c2 = np.argsort(-seen)[:2]
     D = synth.prefix_states(states.n, sc_h.n_clusters, sc_h.n_layers, np.random.default_rng(1))
-    D[:, 0] = 1
-    D[:, 1] = 2
+    D[:, c1] = 1
+    D[:, c2] = 2
     states.masks = synth._pack(synth.depths_to_bits(D, sc_h.n_layers))
     sc = dgs.DeviceScene.from_host(sc_h)
     st = dgs.DeviceStates.from_host(states)
@@ -229,8 +241,7 @@ def test_backward_undelivered_layers_exactly_zero_and_autograd(R, torch):
     loss = (img ** 2).mean()
     loss.backward()
     res_g = sc.t["res"].grad.cpu().numpy()
-    cl = sc_h.cluster_of()
-    assert np.all(res_g[:, cl == 0] == 0.0)          # depth 1: no refinement rendered
-    assert np.all(res_g[1:, cl == 1] == 0.0)         # depth 2: only layer 1
-    assert np.abs(res_g[0, cl == 1]).max() > 0
+    assert np.all(res_g[:, cl == c1] == 0.0)         # depth 1: no refinement rendered
+    assert np.all(res_g[1:, cl == c2] == 0.0)        # depth 2: only layer 1
+    assert np.abs(res_g[0, cl == c2]).max() > 0
     assert np.abs(sc.t["mu0"].grad.cpu().numpy()).max() > 0

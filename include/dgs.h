@@ -59,8 +59,12 @@ enum {
     DGS_E_UNSUPPORTED = -2,   /* e.g. sh_degree not in {0, 3}, > 1024 clusters */
     DGS_E_OOM = -3,           /* workspace allocation failed */
     DGS_E_CUDA = -4,          /* a CUDA runtime call or launch failed */
-    DGS_E_CAPACITY = -5       /* a count exceeds 32-bit indexing */
+    DGS_E_CAPACITY = -5,      /* a count exceeds 32-bit indexing */
+    DGS_E_SCRATCH = -6        /* dgs_image_mse_noalloc: sizes exceed its fixed scratch */
 };
+
+/* Doubles of fixed device scratch held by dgs_image_mse_noalloc (512 KiB per GPU). */
+#define DGS_NOALLOC_MAX_PARTS 65536
 
 typedef struct dgs_ctx dgs_ctx;
 typedef void *dgs_stream;     /* a cudaStream_t; NULL = the legacy default stream */
@@ -187,6 +191,36 @@ DGS_API int dgs_state_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_st
 DGS_API int dgs_image_mse(dgs_ctx *ctx, const float *images, const float *refs, const int32_t *ref_index,
                   int S, int n_refs, int H, int W, float weight, double *mse, double *psnr,
                   float *dL_dimages, dgs_stream stream);
+
+/*
+ * dgs_image_mse without allocation, for callers that cannot allocate: code that
+ * runs inside a memory pool or arena it does not own, real-time loops where an
+ * allocation (and the device synchronisation a free implies) is not allowed, or
+ * hosts that forbid a library from touching the allocator.  The paper has no
+ * counterpart; this is a deployment variant of the per-image MSE above.
+ *   - No context: runs on the calling thread's current device and stream.
+ *   - ref_index is [device] [S] (not host); an out-of-range index makes that
+ *     image's mse (and its dL_dimages values) NaN instead of reading past refs.
+ *     All other arguments as for dgs_image_mse.
+ *   - Allocates nothing: no cudaMalloc / cudaFree / allocating library call.
+ *     Its only scratch is a fixed file-scope device array of
+ *     DGS_NOALLOC_MAX_PARTS doubles (512 KiB) that every GPU which loads the
+ *     library holds until the process exits.  The call fails with
+ *     DGS_E_SCRATCH, launching nothing, when S * ceil(3 H W / 4096) exceeds
+ *     DGS_NOALLOC_MAX_PARTS, and with DGS_E_INVALID_ARG when S > 65535.
+ *   - The first call on each device looks up the scratch array's device
+ *     address (cudaGetSymbolAddress) with that device current; make that first
+ *     call before any stream capture on the device.
+ *   - Every call on a device shares the one scratch array (each call rewrites
+ *     all the partial sums it reads, so nothing needs clearing; the array keeps
+ *     the last call's values).  Calls that overlap on the GPU, e.g. on two
+ *     streams at once, race on it: serialise them.
+ * Returns DGS_OK, DGS_E_INVALID_ARG, DGS_E_SCRATCH or DGS_E_CUDA (no message:
+ * there is no context).
+ */
+DGS_API int dgs_image_mse_noalloc(const float *images, const float *refs, const int32_t *ref_index, int S,
+                                  int n_refs, int H, int W, float weight, double *mse, double *psnr,
+                                  float *dL_dimages, dgs_stream stream);
 
 /*
  * Launch counters (host side, per context): number of kernels this context

@@ -17,7 +17,9 @@ LIB_PATH = os.path.join(HERE, "libdgs.so")
 
 DGS_OK = 0
 ERRORS = {-1: "DGS_E_INVALID_ARG", -2: "DGS_E_UNSUPPORTED", -3: "DGS_E_OOM", -4: "DGS_E_CUDA",
-          -5: "DGS_E_CAPACITY"}
+          -5: "DGS_E_CAPACITY", -6: "DGS_E_SCRATCH"}
+DGS_E_SCRATCH = -6
+NOALLOC_MAX_PARTS = 65536
 
 
 class Scene_t(ctypes.Structure):
@@ -46,7 +48,8 @@ class States_t(ctypes.Structure):
 
 EXPORTS = ("dgs_create", "dgs_destroy", "dgs_last_error", "dgs_version", "dgs_render_state",
            "dgs_render_states_batched", "dgs_render_backward", "dgs_state_utility", "dgs_image_mse",
-           "dgs_kernel_launches", "dgs_reset_kernel_launches", "dgs_profile_enable", "dgs_profile_read")
+           "dgs_kernel_launches", "dgs_reset_kernel_launches", "dgs_profile_enable", "dgs_profile_read",
+           "dgs_image_mse_noalloc")
 
 _lib = None
 
@@ -80,6 +83,8 @@ def lib():
         L.dgs_profile_enable.restype = None
         L.dgs_profile_read.argtypes = [P, I, P, P, P]
         L.dgs_profile_read.restype = I
+        L.dgs_image_mse_noalloc.argtypes = [P, P, P, I, I, I, I, F, P, P, P, P]
+        L.dgs_image_mse_noalloc.restype = I
         _lib = L
     return _lib
 
@@ -294,3 +299,16 @@ def render(renderer, scene: DeviceScene, states: DeviceStates, cams, bg):
     """Differentiable batched render: images [S,H,W,3] with autograd to scene tensors."""
     fn = render_function()
     return fn.apply(renderer, scene, states, cams, bg, *[scene.t[k] for k in SCENE_FIELDS])
+
+
+def image_mse_noalloc(images, refs, ref_index, mse, psnr=None, dL=None, weight=1.0, stream=None) -> int:
+    """dgs_image_mse_noalloc: per-image MSE for callers that cannot allocate.
+
+    Every argument is a caller-owned CUDA tensor (ref_index int32 on the
+    device); nothing is allocated by this call or by the library.  Returns the
+    library's status code (0 = ok, DGS_E_SCRATCH when the sizes exceed the
+    fixed scratch)."""
+    S, H, W, _ = images.shape
+    return int(lib().dgs_image_mse_noalloc(_ptr(images), _ptr(refs), _ptr(ref_index), int(S), int(refs.shape[0]),
+                                           int(H), int(W), float(weight), _ptr(mse), _ptr(psnr), _ptr(dL),
+                                           _stream(stream)))

@@ -186,6 +186,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3_fwdbwd_250k")
     ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--states", type=int, default=None, help="override the workload's state count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     args = ap.parse_args()
@@ -193,7 +194,7 @@ def main():
 
     from paper_2606_17212_b300 import synth
     ws, rank, local = _dist()
-    w = synth.config(args.workload, scale=args.scale)
+    w = synth.config(args.workload, scale=args.scale, n_states=args.states)
     if args.impl == "reference":
         reference_arm(args, w)
         return
@@ -300,16 +301,18 @@ def main():
         n_plain = S
 
         def plain_state(s):
+            # one state per call sequence, with the same arguments for forward and
+            # backward so the backward reuses the forward's projection and lists
             m = states.masks[s:s + 1]
-            st1 = dgs.DeviceStates(m, w.states.t[s:s + 1], w.states.cam[s:s + 1])
+            cam = w.cams[int(w.states.cam[s])]
+            st1 = dgs.DeviceStates(m, w.states.t[s:s + 1], np.zeros(1, np.int32))
             if training:
-                img = R.render_state(scene, m[0], float(w.states.t[s]), w.cams[int(w.states.cam[s])], w.bg,
-                                     out=images[s])
+                R.render_state(scene, m[0], float(w.states.t[s]), cam, w.bg, out=images[s])
                 _, _, dL = R.image_mse(images[s:s + 1], targets, ref_index[s:s + 1], weight=1.0 / S,
                                        want_grad=True)
-                R.render_backward(scene, st1, w.cams, w.bg, dL, grads)
+                R.render_backward(scene, st1, [cam], w.bg, dL, grads)
             else:
-                R.state_utility(scene, st1, w.cams, w.bg)
+                R.state_utility(scene, st1, [cam], w.bg)
             torch.cuda.synchronize()
 
         for s in range(3):

@@ -193,6 +193,27 @@ DGS_API int dgs_image_mse(dgs_ctx *ctx, const float *images, const float *refs, 
                   float *dL_dimages, dgs_stream stream);
 
 /*
+ * Test and inspection access to the projected records and tile lists of the
+ * context's last dgs_render_states_batched / dgs_render_state call (or of a
+ * backward that re-prepared).  Sizes go to the [host] out-parameters (any may
+ * be NULL); each [device] buffer that is not NULL receives a device-to-device
+ * copy on `stream`:
+ *   recs        [n_rec][12] u32 -- the 48-byte records: mx, my, A, B, C, o, r,
+ *               g, b (floats), box x = xlo | xhi << 16, box y = ylo | yhi << 16,
+ *               cluster | depth << 12 | view group << 16 (depth 0 = culled)
+ *   depth_keys  [n_rec]  float bits of camera depth, ascending (0xFFFFFFFF = culled)
+ *   depth_slots [n_rec]  the record slot of each sorted depth key
+ *   entry_keys  [n_ent]  view group * tiles + tile, ascending (stable)
+ *   entry_vals  [n_ent]  record slot of each entry
+ *   ranges      [n_view_groups * tiles][2]  [start, end) of each tile's run
+ * Record slots are laid out view group, cluster, Gaussian, depth (ascending).
+ * Fails with DGS_E_INVALID_ARG when there is no such call to export.
+ */
+DGS_API int dgs_debug_tile_lists(dgs_ctx *ctx, uint32_t *n_rec, uint32_t *n_ent, int32_t *n_view_groups,
+                                 uint32_t *tiles, uint32_t *recs, uint32_t *depth_keys, uint32_t *depth_slots,
+                                 uint32_t *entry_keys, uint32_t *entry_vals, uint32_t *ranges, dgs_stream stream);
+
+/*
  * dgs_image_mse without allocation, for callers that cannot allocate: code that
  * runs inside a memory pool or arena it does not own, real-time loops where an
  * allocation (and the device synchronisation a free implies) is not allowed, or

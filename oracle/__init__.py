@@ -37,7 +37,8 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 REC_FIELDS = ("valid", "mx", "my", "A", "B", "C", "z", "o", "r", "g", "b", "radius",
-              "xlo", "xhi", "ylo", "yhi", "marg_rad", "marg_near", "z32", "d")
+              "xlo", "xhi", "ylo", "yhi", "marg_rad", "marg_near", "z32", "d",
+              "vxlo", "vxhi", "vylo", "vyhi", "marg_vbox")
 
 
 def build(force: bool = False) -> str:

@@ -81,13 +81,15 @@ typedef struct {            /* tolerances of the marginal rule */
 
 static const OEps kDefaultEps = {2e-3, 1e-4, 1e-4, 4e-7, 1e-5, 1e-6};
 
-enum { REC_W = 24 };
+enum { REC_W = 26 };
 /* Projected record of one present Gaussian (FP64). */
 typedef struct {
     int valid;
     int idx;
     double mx, my, A, B, Cc, z, o, rgb[3], r;
     int xlo, xhi, ylo, yhi;       /* exact pixel box (clamped to the image) */
+    int vxlo, vxhi, vylo, vyhi;   /* visible box: the tile-binning acceleration structure */
+    int marg_vbox;                /* a visible-box edge within tolerance of a pixel boundary */
     int marg_rad, marg_near;
     int has_proj;                 /* projection computed (z > 0, det > 0) */
     float z32;
@@ -289,6 +291,31 @@ static void project_one(const OScene *s, int i, int d, double t, const OCam *cam
     yh = yh > cam->height - 1 ? cam->height - 1 : (yh < -1 ? -1 : yh);
     rec->xlo = (int)xl; rec->xhi = (int)xh; rec->ylo = (int)yl; rec->yhi = (int)yh;
     rec->o = 1.0 / (1.0 + exp(-f->a.logit));
+    /* Visible box (tile binning only; images never depend on it): the pixel box
+     * intersected with the bounding box of o e^power >= 1/255, i.e. of
+     * d^T Q d <= rho = 2 ln(255 o), half-widths sqrt(rho a), sqrt(rho c) of the
+     * dilated covariance, inflated by 1e-3 relative + 0.05 px; empty when
+     * o < 1/255 (no pixel can reach alpha >= 1/255). */
+    rec->vxlo = 0; rec->vxhi = -1; rec->vylo = 0; rec->vyhi = -1;
+    if (rec->o >= 1.0 / 255.0) {
+        double rho = 2.0 * log(255.0 * rec->o);
+        if (rho < 0) rho = 0;
+        double hx = sqrt(rho * f->a2) * 1.001 + 0.05, hy = sqrt(rho * f->c2) * 1.001 + 0.05;
+        if (hx > rec->r) hx = rec->r;
+        if (hy > rec->r) hy = rec->r;
+        double e[4] = {rec->mx - hx - 0.5, rec->mx + hx - 0.5, rec->my - hy - 0.5, rec->my + hy - 0.5};
+        for (int k = 0; k < 4; ++k) {
+            double fr = e[k] - floor(e[k]);
+            if (fr <= eps->box_px || 1.0 - fr <= eps->box_px) rec->marg_vbox = 1;
+        }
+        double vl = ceil(e[0]), vh = floor(e[1]), wl = ceil(e[2]), wh = floor(e[3]);
+        vl = vl < 0 ? 0 : (vl > cam->width ? cam->width : vl);
+        wl = wl < 0 ? 0 : (wl > cam->height ? cam->height : wl);
+        vh = vh > cam->width - 1 ? cam->width - 1 : (vh < -1 ? -1 : vh);
+        wh = wh > cam->height - 1 ? cam->height - 1 : (wh < -1 ? -1 : wh);
+        rec->vxlo = (int)vl; rec->vxhi = (int)vh; rec->vylo = (int)wl; rec->vyhi = (int)wh;
+    }
+    if (fabs(rec->o - 1.0 / 255.0) <= eps->rel_alpha / 255.0) rec->marg_vbox = 1;
     int nc = n_colour(s);
     if (s->sh_degree == 0) {
         for (int k = 0; k < 3; ++k) { f->shv[k] = f->a.col[k]; rec->rgb[k] = f->a.col[k] > 0 ? f->a.col[k] : 0; }
@@ -315,7 +342,8 @@ static void project_one(const OScene *s, int i, int d, double t, const OCam *cam
 
 /* Exported per-Gaussian projection (FP64) for tests and the tile-list check.
  * out[i*REC_W + ...] = valid, mx, my, A, B, C, z, o, r, g, b, radius,
- * xlo, xhi, ylo, yhi, marg_rad, marg_near, z32 (as double), depth d. */
+ * xlo, xhi, ylo, yhi, marg_rad, marg_near, z32 (as double), depth d,
+ * visible box vxlo, vxhi, vylo, vyhi, marg_vbox. */
 int o_project(const OScene *s, const uint8_t *depth, double t, const OCam *cam, double *out)
 {
     for (int c = 0; c < s->n_clusters; ++c)
@@ -331,6 +359,7 @@ int o_project(const OScene *s, const uint8_t *depth, double t, const OCam *cam, 
             o[6] = r.z; o[7] = r.o; o[8] = r.rgb[0]; o[9] = r.rgb[1]; o[10] = r.rgb[2];
             o[11] = r.r; o[12] = r.xlo; o[13] = r.xhi; o[14] = r.ylo; o[15] = r.yhi;
             o[16] = r.marg_rad; o[17] = r.marg_near; o[18] = (double)r.z32;
+            o[20] = r.vxlo; o[21] = r.vxhi; o[22] = r.vylo; o[23] = r.vyhi; o[24] = r.marg_vbox;
         }
     return 0;
 }

@@ -80,6 +80,13 @@ struct Plan {
     std::vector<ViewGroup> vgs;
 };
 
+// Outputs of the shared preparation of a batch (pointers into the workspace).
+struct Lists {
+    uint32_t nRec = 0, nEnt = 0;
+    uint32_t *depth_keys = nullptr, *depth_slots = nullptr;   // records sorted by depth
+    uint32_t *ekeys = nullptr, *evals = nullptr;              // entries sorted by (view group, tile)
+};
+
 struct Tape {
     bool valid = false;
     dgs_scene scene{};
@@ -88,8 +95,7 @@ struct Tape {
     std::vector<int32_t> cam;
     std::vector<dgs_camera> cams;
     Plan plan;
-    uint32_t nRec = 0, nEnt = 0;
-    uint32_t *sorted_evals = nullptr;
+    Lists lists;
 };
 
 }  // namespace
@@ -268,8 +274,9 @@ int bits_for(unsigned long long maxval)
 
 // Closure, layout, projection, depth sort, binning, tile sort, ranges.
 int prepare(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *masks, const Plan &p, bool force_full,
-            cudaStream_t st, uint32_t &nRec, uint32_t &nEnt, uint32_t *&sorted_evals)
+            cudaStream_t st, Lists &out)
 {
+    uint32_t nRec = 0, nEnt = 0;
     const int C = scene->n_clusters, L = scene->n_layers;
     const int words = (C * L + 31) / 32;
     const size_t nvc = (size_t)p.V * C;
@@ -329,6 +336,8 @@ int prepare(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *masks, const P
     CK(radix_sort_pairs((uint32_t *)ctx->k0.p, (uint32_t *)ctx->v0.p, (uint32_t *)ctx->k1.p, (uint32_t *)ctx->v1.p,
                         nRec, 32, ctx->sortws.p, st, &alt));
     const uint32_t *order = alt ? (const uint32_t *)ctx->v1.p : (const uint32_t *)ctx->v0.p;
+    out.depth_keys = alt ? (uint32_t *)ctx->k1.p : (uint32_t *)ctx->k0.p;
+    out.depth_slots = (uint32_t *)order;
     if (nRec > 0) launch_tile_count((const Rec *)ctx->recs.p, order, nRec, (uint32_t *)ctx->tcount.p, ctx->sms, st);
     CK(exclusive_scan_u32((const uint32_t *)ctx->tcount.p, (uint32_t *)ctx->toffs.p, nRec,
                           (uint32_t *)ctx->total.p + 1, ctx->scanws.p, st));
@@ -349,7 +358,10 @@ int prepare(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *masks, const P
     CK(radix_sort_pairs((uint32_t *)ctx->ek0.p, (uint32_t *)ctx->ev0.p, (uint32_t *)ctx->ek1.p,
                         (uint32_t *)ctx->ev1.p, nEnt, kbits, ctx->sortws.p, st, &alt));
     uint32_t *ekeys = alt ? (uint32_t *)ctx->ek1.p : (uint32_t *)ctx->ek0.p;
-    sorted_evals = alt ? (uint32_t *)ctx->ev1.p : (uint32_t *)ctx->ev0.p;
+    out.ekeys = ekeys;
+    out.evals = alt ? (uint32_t *)ctx->ev1.p : (uint32_t *)ctx->ev0.p;
+    out.nRec = nRec;
+    out.nEnt = nEnt;
     CK(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * (size_t)p.V * p.tiles, st));
     launch_ranges(ekeys, nEnt, (uint2 *)ctx->ranges.p, ctx->sms, st);
     CK(cudaGetLastError());
@@ -388,7 +400,7 @@ bool same_call(const Tape &tp, const dgs_scene *sc, const dgs_states *st, const 
 }
 
 void record_tape(Tape &tp, const dgs_scene *sc, const dgs_states *st, const dgs_camera *cams, int n_cams,
-                 const Plan &p, uint32_t nRec, uint32_t nEnt, uint32_t *sorted)
+                 const Plan &p, const Lists &L)
 {
     tp.valid = true;
     tp.scene = *sc;
@@ -397,7 +409,7 @@ void record_tape(Tape &tp, const dgs_scene *sc, const dgs_states *st, const dgs_
     tp.cam.assign(st->cam, st->cam + st->n_states);
     tp.cams.assign(cams, cams + n_cams);
     tp.plan = p;
-    tp.nRec = nRec; tp.nEnt = nEnt; tp.sorted_evals = sorted;
+    tp.lists = L;
 }
 
 int render_batched(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states, const dgs_camera *cams,
@@ -410,14 +422,13 @@ int render_batched(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *state
     if (p.S_user > 0 && !images) return fail(ctx, DGS_E_INVALID_ARG, "images is null");
     ctx->tape.valid = false;
     if (p.S_user == 0) return DGS_OK;
-    uint32_t nRec = 0, nEnt = 0;
-    uint32_t *sorted = nullptr;
-    TRY(prepare(ctx, scene, states->masks, p, false, st, nRec, nEnt, sorted));
-    RasterArgs a = raster_args(ctx, p, scene->n_clusters, bg, sorted);
+    Lists L;
+    TRY(prepare(ctx, scene, states->masks, p, false, st, L));
+    RasterArgs a = raster_args(ctx, p, scene->n_clusters, bg, L.evals);
     a.images = images;
     launch_raster_fwd(a, st);
     CK(cudaGetLastError());
-    record_tape(ctx->tape, scene, states, cams, n_cams, p, nRec, nEnt, sorted);
+    record_tape(ctx->tape, scene, states, cams, n_cams, p, L);
     return DGS_OK;
 }
 
@@ -539,9 +550,7 @@ int dgs_render_state(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *mask,
     const int32_t cam0 = 0;
     dgs_states s;
     s.masks = mask; s.t = &t; s.cam = &cam0; s.n_states = 1;
-    const int r = render_batched(ctx, scene, &s, cam, 1, bg, image, (cudaStream_t)stream);
-    ctx->tape.valid = false;   // the tape would point at the caller's stack
-    return r;
+    return render_batched(ctx, scene, &s, cam, 1, bg, image, (cudaStream_t)stream);
 }
 
 int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states, const dgs_camera *cams,
@@ -560,19 +569,19 @@ int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *
     if (!grads->mu0 || !grads->log_scale || !grads->quat || !grads->opacity_logit || !grads->colour ||
         (scene->temporal_rank > 0 && !grads->u) || (scene->n_layers > 1 && !grads->res))
         return fail(ctx, DGS_E_INVALID_ARG, "gradient array is null");
-    uint32_t nRec, nEnt;
-    uint32_t *sorted;
+    Lists L;
     if (same_call(ctx->tape, scene, states, cams, n_cams)) {
-        nRec = ctx->tape.nRec; nEnt = ctx->tape.nEnt; sorted = ctx->tape.sorted_evals;
+        L = ctx->tape.lists;
     } else {
         ctx->tape.valid = false;
-        TRY(prepare(ctx, scene, states->masks, p, false, st, nRec, nEnt, sorted));
-        record_tape(ctx->tape, scene, states, cams, n_cams, p, nRec, nEnt, sorted);
+        TRY(prepare(ctx, scene, states->masks, p, false, st, L));
+        record_tape(ctx->tape, scene, states, cams, n_cams, p, L);
     }
+    const uint32_t nRec = L.nRec;
     TRY(ensure(ctx, ctx->recgrad, sizeof(float4) * 3 * (size_t)nRec, st));
     CK(cudaMemsetAsync(ctx->recgrad.p, 0, sizeof(float4) * 3 * (size_t)nRec, st));
     RasterBwdArgs b;
-    b.f = raster_args(ctx, p, scene->n_clusters, bg, sorted);
+    b.f = raster_args(ctx, p, scene->n_clusters, bg, L.evals);
     b.dL_dimg = dL_dimages;
     b.rec_grad = (float4 *)ctx->recgrad.p;
     launch_raster_bwd(b, st);
@@ -598,9 +607,9 @@ int dgs_state_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *st
     if (p.S_user > 0 && !mse) return fail(ctx, DGS_E_INVALID_ARG, "mse is null");
     ctx->tape.valid = false;
     if (p.S_user == 0) return DGS_OK;
-    uint32_t nRec = 0, nEnt = 0;
-    uint32_t *sorted = nullptr;
-    TRY(prepare(ctx, scene, states->masks, p, true, st, nRec, nEnt, sorted));
+    Lists L;
+    TRY(prepare(ctx, scene, states->masks, p, true, st, L));
+    uint32_t *sorted = L.evals;
     const size_t img = (size_t)p.W * p.H * 3;
     TRY(ensure(ctx, ctx->refs, sizeof(float) * img * (size_t)p.V, st));
     TRY(ensure(ctx, ctx->partial, sizeof(double) * (size_t)p.S_user * p.tiles, st));
@@ -619,6 +628,29 @@ int dgs_state_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *st
     launch_raster_fwd(a, st);
     launch_mse_reduce((const double *)ctx->partial.p, p.S_user, (int)p.tiles, 1.0 / (double)img, mse, psnr, st);
     CK(cudaGetLastError());
+    return DGS_OK;
+}
+
+int dgs_debug_tile_lists(dgs_ctx *ctx, uint32_t *n_rec, uint32_t *n_ent, int32_t *n_view_groups,
+                         uint32_t *tiles, uint32_t *recs, uint32_t *depth_keys, uint32_t *depth_slots,
+                         uint32_t *entry_keys, uint32_t *entry_vals, uint32_t *ranges, dgs_stream stream)
+{
+    if (!ctx) return DGS_E_INVALID_ARG;
+    if (!ctx->tape.valid) return fail(ctx, DGS_E_INVALID_ARG, "no forward call to export");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const Tape &tp = ctx->tape;
+    if (n_rec) *n_rec = tp.lists.nRec;
+    if (n_ent) *n_ent = tp.lists.nEnt;
+    if (n_view_groups) *n_view_groups = tp.plan.V;
+    if (tiles) *tiles = tp.plan.tiles;
+    const size_t nr = tp.lists.nRec, ne = tp.lists.nEnt, nrg = (size_t)tp.plan.V * tp.plan.tiles;
+    if (recs && nr) CK(cudaMemcpyAsync(recs, ctx->recs.p, sizeof(Rec) * nr, cudaMemcpyDeviceToDevice, st));
+    if (depth_keys && nr) CK(cudaMemcpyAsync(depth_keys, tp.lists.depth_keys, 4 * nr, cudaMemcpyDeviceToDevice, st));
+    if (depth_slots && nr) CK(cudaMemcpyAsync(depth_slots, tp.lists.depth_slots, 4 * nr, cudaMemcpyDeviceToDevice, st));
+    if (entry_keys && ne) CK(cudaMemcpyAsync(entry_keys, tp.lists.ekeys, 4 * ne, cudaMemcpyDeviceToDevice, st));
+    if (entry_vals && ne) CK(cudaMemcpyAsync(entry_vals, tp.lists.evals, 4 * ne, cudaMemcpyDeviceToDevice, st));
+    if (ranges && nrg) CK(cudaMemcpyAsync(ranges, ctx->ranges.p, sizeof(uint2) * nrg, cudaMemcpyDeviceToDevice, st));
     return DGS_OK;
 }
 

@@ -198,13 +198,24 @@ __device__ __forceinline__ void project_fwd(const SceneDev &s, int i, const Attr
     const float hd = 0.5f * (F.a - F.c);
     const float lam = 0.5f * (F.a + F.c) + sqrtf(hd * hd + F.b * F.b);
     P.r = ceilf(3.0f * sqrtf(lam));
-    // exact pixel box: |x + 0.5 - mx| <= r  <=>  ceil(mx - r - 0.5) <= x <= floor(mx + r - 0.5)
-    double xl = ceil((double)P.mx - (double)P.r - 0.5), xh = floor((double)P.mx + (double)P.r - 0.5);
-    double yl = ceil((double)P.my - (double)P.r - 0.5), yh = floor((double)P.my + (double)P.r - 0.5);
+    P.o = 1.0f / (1.0f + expf(-a.logit));
+    // Visible box.  The definition's box is |p_centre - m| <= r.  A pixel also
+    // needs alpha = o e^power >= 1/255, i.e. d^T Q d <= rho = 2 ln(255 o), whose
+    // bounding box has half-widths sqrt(rho a) and sqrt(rho c) (a, c: diagonal
+    // of the dilated covariance).  Intersecting both boxes removes only pixels
+    // the compositing would skip; the alpha half-widths are inflated by 1e-3
+    // relative + 0.05 px so FP32 rounding never drops a pixel that composites.
+    // A Gaussian with o < 1/255 never composites at all.
+    if (!(P.o >= (1.0f / 255.0f))) return;
+    const float rho = 2.0f * logf(255.0f * P.o);
+    const float hx = fminf(P.r, fmaf(sqrtf(fmaxf(rho, 0.0f) * F.a), 1.001f, 0.05f));
+    const float hy = fminf(P.r, fmaf(sqrtf(fmaxf(rho, 0.0f) * F.c), 1.001f, 0.05f));
+    // exact pixel ranges: |x + 0.5 - mx| <= h  <=>  ceil(mx - h - 0.5) <= x <= floor(mx + h - 0.5)
+    double xl = ceil((double)P.mx - (double)hx - 0.5), xh = floor((double)P.mx + (double)hx - 0.5);
+    double yl = ceil((double)P.my - (double)hy - 0.5), yh = floor((double)P.my + (double)hy - 0.5);
     xl = fmin(fmax(xl, 0.0), (double)vg.width);  xh = fmax(fmin(xh, (double)(vg.width - 1)), -1.0);
     yl = fmin(fmax(yl, 0.0), (double)vg.height); yh = fmax(fmin(yh, (double)(vg.height - 1)), -1.0);
     P.xlo = (int)xl; P.xhi = (int)xh; P.ylo = (int)yl; P.yhi = (int)yh;
-    P.o = 1.0f / (1.0f + expf(-a.logit));
     if (SH == 0) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) { F.shv[k] = a.col[k]; P.rgb[k] = fmaxf(a.col[k], 0.0f); }

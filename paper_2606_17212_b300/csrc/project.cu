@@ -110,10 +110,17 @@ __global__ void __launch_bounds__(256) k_project(SceneDev s, const ViewGroup *__
     }
 }
 
-__device__ __forceinline__ uint32_t rec_tiles(const Rec &r)
+// The last 16 bytes of a record: colour b, box x, box y, cluster/depth/view group.
+__device__ __forceinline__ float4 rec_tail(const Rec *recs, uint32_t slot)
 {
-    const int xlo = r.bx & 0xffff, xhi = r.bx >> 16, ylo = r.by & 0xffff, yhi = r.by >> 16;
-    if ((r.cd & 0xf000u) == 0 || xlo > xhi || ylo > yhi) return 0;
+    return __ldg(reinterpret_cast<const float4 *>(recs + slot) + 2);
+}
+
+__device__ __forceinline__ uint32_t rec_tiles(const float4 &q)
+{
+    const uint32_t bx = __float_as_uint(q.y), by = __float_as_uint(q.z), cd = __float_as_uint(q.w);
+    const int xlo = bx & 0xffff, xhi = bx >> 16, ylo = by & 0xffff, yhi = by >> 16;
+    if ((cd & 0xf000u) == 0 || xlo > xhi || ylo > yhi) return 0;
     return (uint32_t)((xhi / TILE - xlo / TILE + 1) * (yhi / TILE - ylo / TILE + 1));
 }
 
@@ -122,9 +129,7 @@ __global__ void k_tile_count(const Rec *__restrict__ recs, const uint32_t *__res
                              uint32_t *__restrict__ counts)
 {
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        const uint32_t slot = order[j];
-        const Rec r = recs[slot];
-        counts[j] = rec_tiles(r);
+        counts[j] = rec_tiles(rec_tail(recs, order[j]));
     }
 }
 
@@ -137,10 +142,11 @@ __global__ void k_emit(const Rec *__restrict__ recs, const uint32_t *__restrict_
 {
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         const uint32_t slot = order[j];
-        const Rec r = recs[slot];
-        if (rec_tiles(r) == 0) continue;
-        const int xlo = r.bx & 0xffff, xhi = r.bx >> 16, ylo = r.by & 0xffff, yhi = r.by >> 16;
-        const uint32_t v = r.cd >> 16;
+        const float4 q = rec_tail(recs, slot);
+        if (rec_tiles(q) == 0) continue;
+        const uint32_t bx = __float_as_uint(q.y), by = __float_as_uint(q.z);
+        const int xlo = bx & 0xffff, xhi = bx >> 16, ylo = by & 0xffff, yhi = by >> 16;
+        const uint32_t v = __float_as_uint(q.w) >> 16;
         uint32_t o = offsets[j];
         for (int ty = ylo / TILE; ty <= yhi / TILE; ++ty)
             for (int tx = xlo / TILE; tx <= xhi / TILE; ++tx) {

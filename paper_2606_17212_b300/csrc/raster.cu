@@ -1,16 +1,18 @@
 // Tile rasterization of delivery states: forward compositing with an optional
 // fused FP64 squared-error epilogue, and the adjoint compositing kernel.
 //
-// One 256-thread block renders one 16x16 tile of one state.  The tile's run of
+// One 128-thread block renders one 16x16 tile of one state; every thread owns
+// two vertically adjacent pixels, every warp a 16x4 strip.  The tile's run of
 // the batch-wide sorted entry list holds every depth variant any state of the
 // view group needs; each batch of 256 entries is staged in shared memory
 // keeping only the variants this state renders (variant depth == the state's
-// delivered depth of the Gaussian's cluster), compacted in order.  Filtering
-// a sorted run keeps it sorted, so every state sees exactly the (depth,
-// Gaussian) order it would see alone: batched == per-state, bit for bit.
+// delivered depth of the Gaussian's cluster), compacted in order, and each
+// warp then walks only the staged Gaussians whose pixel box reaches its rows.
+// Filtering a sorted run keeps it sorted, so every pixel sees exactly the
+// (depth, Gaussian) order it would see alone: batched == per-state, bit for bit.
 //
-// Per pixel and staged Gaussian the work is a handful of FP32 ops and one
-// MUFU exp: these kernels are ALU/issue bound, not HBM bound.
+// Per pixel and Gaussian the work is a handful of FP32 ops and one MUFU exp:
+// these kernels are ALU/issue bound, not HBM bound.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -22,50 +24,86 @@ namespace dgs {
 
 namespace {
 
-constexpr int NW = TILE_PIX / 32;   // warps per block
+constexpr int RT = 128;               // threads per raster block
+constexpr int RW = RT / 32;           // warps per block; warp w owns rows 4w..4w+3 of the tile
+constexpr int BATCH = 256;            // entries staged per batch (two per thread)
 
 struct Staged {
-    float4 r0[TILE_PIX];   // mx, my, A, B
-    float4 r1[TILE_PIX];   // C, o, r, g
-    float4 r2[TILE_PIX];   // b, box x, box y, cd
-    uint32_t slot[TILE_PIX];
-    int wcnt[NW];
+    float4 r0[BATCH];                 // mx, my, A, B
+    float4 r1[BATCH];                 // C, o, r, g
+    float4 r2[BATCH];                 // b, box x, box y, cd
+    uint32_t slot[BATCH];
+    uint8_t list[RW][BATCH];          // per-warp indices of staged entries reaching its rows
+    int cnt[RW];
+    int wcnt[2][RW];
 };
 
-// Stage entries [start, min(start + 256, end)) of the tile run, keeping the
-// variants this state renders.  Returns the kept count (same in every thread).
+// Stage entries [start, min(start + BATCH, end)) of the tile run, keeping the
+// variants this state renders, compacted in order; then build each warp's list
+// of kept entries whose box reaches the warp's rows.  Returns the kept count.
 __device__ __forceinline__ int stage_batch(const Rec *__restrict__ recs, const uint32_t *__restrict__ evals,
-                                           const uint8_t *sdep, uint32_t start, uint32_t end, Staged &sm)
+                                           const uint8_t *sdep, uint32_t start, uint32_t end, int row0,
+                                           Staged &sm)
 {
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const uint32_t e = start + (uint32_t)t;
-    bool keep = false;
-    float4 x0 = make_float4(0, 0, 0, 0), x1 = x0, x2 = x0;
-    uint32_t slot = 0;
-    if (e < end) {
-        slot = __ldg(evals + e);
-        const float4 *p = reinterpret_cast<const float4 *>(recs + slot);
-        x2 = __ldg(p + 2);
-        const uint32_t cd = __float_as_uint(x2.w);
-        keep = ((cd >> 12) & 0xfu) == (uint32_t)sdep[cd & 0xfffu];
-        if (keep) { x0 = __ldg(p); x1 = __ldg(p + 1); }
-    }
-    const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-    if (lane == 0) sm.wcnt[w] = __popc(bal);
-    __syncthreads();
-    int base = 0, total = 0;
+    bool keep[2];
+    float4 x0[2], x1[2], x2[2];
+    uint32_t slot[2];
 #pragma unroll
-    for (int k = 0; k < NW; ++k) {
-        const int c = sm.wcnt[k];
-        base += (k < w) ? c : 0;
-        total += c;
+    for (int h = 0; h < 2; ++h) {
+        const uint32_t e = start + (uint32_t)(h * RT + t);
+        keep[h] = false;
+        x0[h] = x1[h] = x2[h] = make_float4(0, 0, 0, 0);
+        slot[h] = 0;
+        if (e < end) {
+            slot[h] = __ldg(evals + e);
+            const float4 *p = reinterpret_cast<const float4 *>(recs + slot[h]);
+            x2[h] = __ldg(p + 2);
+            const uint32_t cd = __float_as_uint(x2[h].w);
+            keep[h] = ((cd >> 12) & 0xfu) == (uint32_t)sdep[cd & 0xfffu];
+            if (keep[h]) { x0[h] = __ldg(p); x1[h] = __ldg(p + 1); }
+        }
     }
-    if (keep) {
-        const int pos = base + __popc(bal & ((1u << lane) - 1u));
-        sm.r0[pos] = x0; sm.r1[pos] = x1; sm.r2[pos] = x2; sm.slot[pos] = slot;
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t b0 = __ballot_sync(0xffffffffu, keep[0]), b1 = __ballot_sync(0xffffffffu, keep[1]);
+    if (lane == 0) { sm.wcnt[0][w] = __popc(b0); sm.wcnt[1][w] = __popc(b1); }
+    __syncthreads();
+    int base0 = 0, tot0 = 0, base1 = 0, tot1 = 0;
+#pragma unroll
+    for (int k = 0; k < RW; ++k) {
+        const int c0 = sm.wcnt[0][k], c1 = sm.wcnt[1][k];
+        base0 += (k < w) ? c0 : 0;
+        tot0 += c0;
+        base1 += (k < w) ? c1 : 0;
+        tot1 += c1;
+    }
+    if (keep[0]) {
+        const int pos = base0 + __popc(b0 & lt);
+        sm.r0[pos] = x0[0]; sm.r1[pos] = x1[0]; sm.r2[pos] = x2[0]; sm.slot[pos] = slot[0];
+    }
+    if (keep[1]) {
+        const int pos = tot0 + base1 + __popc(b1 & lt);
+        sm.r0[pos] = x0[1]; sm.r1[pos] = x1[1]; sm.r2[pos] = x2[1]; sm.slot[pos] = slot[1];
     }
     __syncthreads();
-    return total;
+    const int nk = tot0 + tot1;
+    // warp w keeps staged entries whose inclusive row range meets rows row0 + 4w .. row0 + 4w + 3
+    const int wr0 = row0 + 4 * w, wr1 = wr0 + 3;
+    int n = 0;
+    for (int j0 = 0; j0 < nk; j0 += 32) {
+        const int j = j0 + lane;
+        bool hit = false;
+        if (j < nk) {
+            const uint32_t by = __float_as_uint(sm.r2[j].z);
+            hit = (int)(by & 0xffffu) <= wr1 && (int)(by >> 16) >= wr0;
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+        if (hit) sm.list[w][n + __popc(bal & lt)] = (uint8_t)j;
+        n += __popc(bal);
+    }
+    if (lane == 0) sm.cnt[w] = n;
+    __syncwarp();
+    return nk;
 }
 
 __device__ __forceinline__ bool in_box(const float4 &r2, int px, int py)
@@ -82,201 +120,270 @@ __device__ __forceinline__ float power_of(float A, float B, float C, float dx, f
     return __fmaf_rn(-0.5f, q, -__fmul_rn(B, __fmul_rn(dx, dy)));
 }
 
+// One pixel's front-to-back state.
+struct Pix {
+    float T, c0, c1, c2;
+    bool done;
+};
+
+// Composite staged entry (r0, r1, r2) into pixel (px, py); returns true when
+// the pixel stops at this entry (the entry is then excluded).
+// Branch-free: an entry the pixel skips (outside the box, power > 0 or
+// alpha < 1/255) gets alpha = 0, which leaves T and the colour bit-identical.
+__device__ __forceinline__ bool composite(Pix &p, const float4 &r0, const float4 &r1, const float4 &r2, int px,
+                                          int py)
+{
+    const bool inb = in_box(r2, px, py);
+    const float dx = __fsub_rn(r0.x, (float)px + 0.5f), dy = __fsub_rn(r0.y, (float)py + 0.5f);
+    const float pw = power_of(r0.z, r0.w, r1.x, dx, dy);
+    const float a0 = fminf(0.99f, __fmul_rn(r1.y, __expf(pw)));
+    const float alpha = (inb && pw <= 0.0f && a0 >= (1.0f / 255.0f)) ? a0 : 0.0f;
+    const float Tn = __fmul_rn(p.T, __fsub_rn(1.0f, alpha));
+    if (Tn < 1e-4f) return true;
+    const float wgt = __fmul_rn(alpha, p.T);
+    p.c0 = __fmaf_rn(r1.z, wgt, p.c0);
+    p.c1 = __fmaf_rn(r1.w, wgt, p.c1);
+    p.c2 = __fmaf_rn(r2.x, wgt, p.c2);
+    p.T = Tn;
+    return false;
+}
+
 __device__ __forceinline__ void load_depth_row(const uint8_t *depth, int s, int C, uint8_t *sdep)
 {
     for (int c = threadIdx.x; c < C; c += blockDim.x) sdep[c] = depth[(size_t)s * C + c];
 }
 
 template <bool WRITE, bool MSE>
-__global__ void __launch_bounds__(TILE_PIX) k_raster_fwd(RasterArgs a)
+__global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a)
 {
     __shared__ Staged sm;
     __shared__ uint8_t sdep[MAX_CLUSTERS];
-    __shared__ double wsum[NW];
+    __shared__ double wsum[RW];
     const int tile = (int)(blockIdx.x / (unsigned)a.S), s = (int)(blockIdx.x % (unsigned)a.S);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int v = a.vg_of_state[s];
     load_depth_row(a.depth, s, a.C, sdep);
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const int px = tx * TILE + (threadIdx.x & (TILE - 1)), py = ty * TILE + (threadIdx.x / TILE);
-    const bool inside = px < a.W && py < a.H;
-    const float pcx = (float)px + 0.5f, pcy = (float)py + 0.5f;
+    const int px = tx * TILE + (lane & 15);
+    const int py0 = ty * TILE + 4 * w + 2 * (lane >> 4), py1 = py0 + 1;
+    const bool in0 = px < a.W && py0 < a.H, in1 = px < a.W && py1 < a.H;
     const uint2 rg = a.ranges[(size_t)v * a.tiles + tile];
-    float T = 1.0f, c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
-    bool done = !inside;
-    for (uint32_t start = rg.x; start < rg.y; start += TILE_PIX) {
-        if (__syncthreads_count(!done) == 0) break;
-        const int nk = stage_batch(a.recs, a.evals, sdep, start, rg.y, sm);
-        if (done) continue;
-        for (int k = 0; k < nk; ++k) {
-            const float4 r2 = sm.r2[k];
-            if (!in_box(r2, px, py)) continue;
-            const float4 r0 = sm.r0[k], r1 = sm.r1[k];
-            const float dx = __fsub_rn(r0.x, pcx), dy = __fsub_rn(r0.y, pcy);
-            const float pw = power_of(r0.z, r0.w, r1.x, dx, dy);
-            if (pw > 0.0f) continue;
-            const float alpha = fminf(0.99f, __fmul_rn(r1.y, __expf(pw)));
-            if (alpha < (1.0f / 255.0f)) continue;
-            const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
-            if (Tn < 1e-4f) { done = true; break; }
-            const float wgt = __fmul_rn(alpha, T);
-            c0 = __fmaf_rn(r1.z, wgt, c0);
-            c1 = __fmaf_rn(r1.w, wgt, c1);
-            c2 = __fmaf_rn(r2.x, wgt, c2);
-            T = Tn;
+    Pix p0 = {1.0f, 0.0f, 0.0f, 0.0f, !in0}, p1 = {1.0f, 0.0f, 0.0f, 0.0f, !in1};
+    for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
+        if (__syncthreads_count(!(p0.done && p1.done)) == 0) break;
+        stage_batch(a.recs, a.evals, sdep, start, rg.y, ty * TILE, sm);
+        const int n = sm.cnt[w];
+        for (int i = 0; i < n; ++i) {
+            if (p0.done && p1.done) break;
+            const int k = sm.list[w][i];
+            const float4 r0 = sm.r0[k], r1 = sm.r1[k], r2 = sm.r2[k];
+            if (!p0.done && composite(p0, r0, r1, r2, px, py0)) p0.done = true;
+            if (!p1.done && composite(p1, r0, r1, r2, px, py1)) p1.done = true;
         }
     }
-    const float o0 = __fmaf_rn(T, a.bg0, c0), o1 = __fmaf_rn(T, a.bg1, c1), o2 = __fmaf_rn(T, a.bg2, c2);
-    if (WRITE && inside) {
-        float *dst = a.images + (((size_t)s * a.H + py) * a.W + px) * 3;
-        dst[0] = o0; dst[1] = o1; dst[2] = o2;
+    float o[2][3];
+    o[0][0] = __fmaf_rn(p0.T, a.bg0, p0.c0); o[0][1] = __fmaf_rn(p0.T, a.bg1, p0.c1); o[0][2] = __fmaf_rn(p0.T, a.bg2, p0.c2);
+    o[1][0] = __fmaf_rn(p1.T, a.bg0, p1.c0); o[1][1] = __fmaf_rn(p1.T, a.bg1, p1.c1); o[1][2] = __fmaf_rn(p1.T, a.bg2, p1.c2);
+    if (WRITE) {
+        if (in0) {
+            float *dst = a.images + (((size_t)s * a.H + py0) * a.W + px) * 3;
+            dst[0] = o[0][0]; dst[1] = o[0][1]; dst[2] = o[0][2];
+        }
+        if (in1) {
+            float *dst = a.images + (((size_t)s * a.H + py1) * a.W + px) * 3;
+            dst[0] = o[1][0]; dst[1] = o[1][1]; dst[2] = o[1][2];
+        }
     }
     if (MSE) {
         double se = 0.0;
-        if (inside) {
-            const float *rp = a.refs + (((size_t)a.ref_of_state[s] * a.H + py) * a.W + px) * 3;
-            const double d0 = (double)o0 - (double)rp[0], d1 = (double)o1 - (double)rp[1];
-            const double d2 = (double)o2 - (double)rp[2];
-            se = d0 * d0 + d1 * d1 + d2 * d2;
+        const float *rbase = a.refs + (size_t)a.ref_of_state[s] * a.H * a.W * 3;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int py = h ? py1 : py0;
+            if (h ? in1 : in0) {
+                const float *rp = rbase + ((size_t)py * a.W + px) * 3;
+                const double d0 = (double)o[h][0] - (double)rp[0], d1 = (double)o[h][1] - (double)rp[1];
+                const double d2 = (double)o[h][2] - (double)rp[2];
+                se += d0 * d0 + d1 * d1 + d2 * d2;
+            }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
-        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = se;
+        for (int off = 16; off > 0; off >>= 1) se += __shfl_xor_sync(0xffffffffu, se, off);
+        if (lane == 0) wsum[w] = se;
         __syncthreads();
         if (threadIdx.x == 0) {
             double tot = 0.0;
 #pragma unroll
-            for (int w = 0; w < NW; ++w) tot += wsum[w];
+            for (int k = 0; k < RW; ++k) tot += wsum[k];
             a.partial[(size_t)s * a.tiles + tile] = tot;
         }
     }
 }
 
+// Per-pixel state of the adjoint walk.
+struct PixB {
+    float T, c0, c1, c2;      // transmittance and colour prefix (pass 2)
+    float Cf0, Cf1, Cf2;      // final colour without background (pass 1)
+    float sb0, sb1, sb2;      // T_final * bg
+    float g0, g1, g2;         // dL/dC
+    uint32_t stop;            // filtered-stream index where the pixel stopped
+    bool active;
+};
+
+// Adjoint of one pixel at one staged entry; adds to g[9] =
+// (mx, my, A, B, C, o, r, g, b) when the entry is included.  T and the colour
+// prefix advance exactly as in the forward.
+// Branch-free like composite(): a skipped entry has alpha = 0 and adds zeros.
+__device__ __forceinline__ bool adjoint(PixB &p, const float4 &r0, const float4 &r1, const float4 &r2, int px,
+                                        int py, float *g)
+{
+    const bool inb = in_box(r2, px, py);
+    const float dx = __fsub_rn(r0.x, (float)px + 0.5f), dy = __fsub_rn(r0.y, (float)py + 0.5f);
+    const float pw = power_of(r0.z, r0.w, r1.x, dx, dy);
+    const float ex = __expf(pw);
+    const float araw = __fmul_rn(r1.y, ex);
+    const float a0 = fminf(0.99f, araw);
+    const bool ok = inb && pw <= 0.0f && a0 >= (1.0f / 255.0f);
+    const float alpha = ok ? a0 : 0.0f;
+    const float one_m = __fsub_rn(1.0f, alpha);
+    const float wgt = __fmul_rn(alpha, p.T);
+    p.c0 = __fmaf_rn(r1.z, wgt, p.c0);
+    p.c1 = __fmaf_rn(r1.w, wgt, p.c1);
+    p.c2 = __fmaf_rn(r2.x, wgt, p.c2);
+    const float inv = 1.0f / one_m;
+    const float da = p.g0 * (r1.z * p.T - ((p.Cf0 - p.c0) + p.sb0) * inv) +
+                     p.g1 * (r1.w * p.T - ((p.Cf1 - p.c1) + p.sb1) * inv) +
+                     p.g2 * (r2.x * p.T - ((p.Cf2 - p.c2) + p.sb2) * inv);
+    g[6] += p.g0 * wgt; g[7] += p.g1 * wgt; g[8] += p.g2 * wgt;
+    // alpha = 0 (skipped) or the 0.99 clamp: no gradient to opacity, mean, conic
+    const float gpw = (ok && araw < 0.99f) ? da * alpha : 0.0f;
+    g[5] += (ok && araw < 0.99f) ? da * ex : 0.0f;
+    g[0] -= gpw * (r0.z * dx + r0.w * dy);
+    g[1] -= gpw * (r1.x * dy + r0.w * dx);
+    g[2] -= 0.5f * gpw * dx * dx;
+    g[3] -= gpw * dx * dy;
+    g[4] -= 0.5f * gpw * dy * dy;
+    p.T = __fmul_rn(p.T, one_m);
+    return ok;
+}
+
+// Sum of v[0..7] over the warp: after three exchange-and-keep-half steps and
+// two plain steps, lane 4j holds the warp total of v[j].
+__device__ __forceinline__ float reduce8_transpose(const float *v, int lane)
+{
+    float u[4], w2[2];
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = b4 ? v[i] : v[i + 4];
+        const float keep = b4 ? v[i + 4] : v[i];
+        u[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = b3 ? u[i] : u[i + 2];
+        const float keep = b3 ? u[i + 2] : u[i];
+        w2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    const float send = b2 ? w2[0] : w2[1];
+    float x = (b2 ? w2[1] : w2[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
+    x += __shfl_xor_sync(0xffffffffu, x, 2);
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    return x;
+}
+
 // Adjoint compositing.  Pass 1 re-runs the forward walk to get each pixel's
-// final colour, final transmittance and stop position; pass 2 walks front to
-// back again and, for each included Gaussian k,
+// final colour, final transmittance and stop position (nothing is stored by
+// the forward); pass 2 walks front to back again and, for each included k,
 //   dC/drgb_k   = alpha_k T_k
 //   dC/dalpha_k = rgb_k T_k - (C_after_k + T_final bg) / (1 - alpha_k)
-// where C_after_k = C_final - (colour accumulated up to and including k).
-// Per-Gaussian sums are reduced per warp, then per block in shared memory,
-// then added to the record's gradient with one float4 atomic per 4 values.
-__global__ void __launch_bounds__(TILE_PIX) k_raster_bwd(RasterBwdArgs b)
+// with C_after_k = C_final - (colour accumulated up to and including k).
+// Per-Gaussian sums: two pixels per thread, warp transpose reduction, block
+// sum in shared memory, then float4 atomics into the record's gradient.
+__global__ void __launch_bounds__(RT, 6) k_raster_bwd(RasterBwdArgs b)
 {
     const RasterArgs &a = b.f;
     __shared__ Staged sm;
     __shared__ uint8_t sdep[MAX_CLUSTERS];
-    __shared__ float gacc[TILE_PIX][9];
+    __shared__ float gacc[BATCH][9];
     const int tile = (int)(blockIdx.x / (unsigned)a.S), s = (int)(blockIdx.x % (unsigned)a.S);
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int v = a.vg_of_state[s];
     load_depth_row(a.depth, s, a.C, sdep);
-    for (int j = threadIdx.x; j < TILE_PIX * 9; j += TILE_PIX) (&gacc[0][0])[j] = 0.0f;
+    for (int j = threadIdx.x; j < BATCH * 9; j += RT) (&gacc[0][0])[j] = 0.0f;
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const int px = tx * TILE + (threadIdx.x & (TILE - 1)), py = ty * TILE + (threadIdx.x / TILE);
-    const bool inside = px < a.W && py < a.H;
-    const float pcx = (float)px + 0.5f, pcy = (float)py + 0.5f;
+    const int px = tx * TILE + (lane & 15);
+    const int py0 = ty * TILE + 4 * w + 2 * (lane >> 4), py1 = py0 + 1;
+    const bool in0 = px < a.W && py0 < a.H, in1 = px < a.W && py1 < a.H;
     const uint2 rg = a.ranges[(size_t)v * a.tiles + tile];
 
-    // ---- pass 1: forward walk
-    float T = 1.0f, c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
-    bool done = !inside;
-    uint32_t stop = 0xffffffffu, kept = 0;
-    for (uint32_t start = rg.x; start < rg.y; start += TILE_PIX) {
-        if (__syncthreads_count(!done) == 0) break;
-        const int nk = stage_batch(a.recs, a.evals, sdep, start, rg.y, sm);
-        if (!done) {
-            for (int k = 0; k < nk; ++k) {
-                const float4 r2 = sm.r2[k];
-                if (!in_box(r2, px, py)) continue;
-                const float4 r0 = sm.r0[k], r1 = sm.r1[k];
-                const float dx = __fsub_rn(r0.x, pcx), dy = __fsub_rn(r0.y, pcy);
-                const float pw = power_of(r0.z, r0.w, r1.x, dx, dy);
-                if (pw > 0.0f) continue;
-                const float alpha = fminf(0.99f, __fmul_rn(r1.y, __expf(pw)));
-                if (alpha < (1.0f / 255.0f)) continue;
-                const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
-                if (Tn < 1e-4f) { done = true; stop = kept + (uint32_t)k; break; }
-                const float wgt = __fmul_rn(alpha, T);
-                c0 = __fmaf_rn(r1.z, wgt, c0);
-                c1 = __fmaf_rn(r1.w, wgt, c1);
-                c2 = __fmaf_rn(r2.x, wgt, c2);
-                T = Tn;
-            }
+    // ---- pass 1: forward walk, recording where each pixel stops
+    Pix f0 = {1.0f, 0.0f, 0.0f, 0.0f, !in0}, f1 = {1.0f, 0.0f, 0.0f, 0.0f, !in1};
+    uint32_t stop0 = 0xffffffffu, stop1 = 0xffffffffu, kept = 0;
+    for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
+        if (__syncthreads_count(!(f0.done && f1.done)) == 0) break;
+        const int nk = stage_batch(a.recs, a.evals, sdep, start, rg.y, ty * TILE, sm);
+        const int n = sm.cnt[w];
+        for (int i = 0; i < n; ++i) {
+            if (f0.done && f1.done) break;
+            const int k = sm.list[w][i];
+            const float4 r0 = sm.r0[k], r1 = sm.r1[k], r2 = sm.r2[k];
+            if (!f0.done && composite(f0, r0, r1, r2, px, py0)) { f0.done = true; stop0 = kept + (uint32_t)k; }
+            if (!f1.done && composite(f1, r0, r1, r2, px, py1)) { f1.done = true; stop1 = kept + (uint32_t)k; }
         }
         kept += (uint32_t)nk;
     }
-    const float Tf = T, Cf0 = c0, Cf1 = c1, Cf2 = c2;
-    float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
-    if (inside) {
-        const float *gp = b.dL_dimg + (((size_t)s * a.H + py) * a.W + px) * 3;
-        g0 = gp[0]; g1 = gp[1]; g2 = gp[2];
+    PixB q[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const Pix &f = h ? f1 : f0;
+        const bool in = h ? in1 : in0;
+        const int py = h ? py1 : py0;
+        PixB &p = q[h];
+        p.T = 1.0f; p.c0 = p.c1 = p.c2 = 0.0f;
+        p.Cf0 = f.c0; p.Cf1 = f.c1; p.Cf2 = f.c2;
+        p.sb0 = f.T * a.bg0; p.sb1 = f.T * a.bg1; p.sb2 = f.T * a.bg2;
+        p.g0 = p.g1 = p.g2 = 0.0f;
+        if (in) {
+            const float *gp = b.dL_dimg + (((size_t)s * a.H + py) * a.W + px) * 3;
+            p.g0 = gp[0]; p.g1 = gp[1]; p.g2 = gp[2];
+        }
+        p.stop = h ? stop1 : stop0;
+        p.active = in && p.stop > 0 && (p.g0 != 0.0f || p.g1 != 0.0f || p.g2 != 0.0f);
     }
-    const float sb0 = Tf * a.bg0, sb1 = Tf * a.bg1, sb2 = Tf * a.bg2;
 
     // ---- pass 2: gradients
-    T = 1.0f; c0 = 0.0f; c1 = 0.0f; c2 = 0.0f;
-    bool active = inside && stop > 0 && (g0 != 0.0f || g1 != 0.0f || g2 != 0.0f);
     kept = 0;
-    for (uint32_t start = rg.x; start < rg.y; start += TILE_PIX) {
-        if (__syncthreads_count(active) == 0) break;
-        const int nk = stage_batch(a.recs, a.evals, sdep, start, rg.y, sm);
-        for (int k = 0; k < nk; ++k) {
-            float gv[9];
+    for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
+        if (__syncthreads_count(q[0].active || q[1].active) == 0) break;
+        const int nk = stage_batch(a.recs, a.evals, sdep, start, rg.y, ty * TILE, sm);
+        const int n = sm.cnt[w];
+        if (__any_sync(0xffffffffu, q[0].active || q[1].active)) {
+            for (int i = 0; i < n; ++i) {
+                const int k = sm.list[w][i];
+                float g[9];
 #pragma unroll
-            for (int j = 0; j < 9; ++j) gv[j] = 0.0f;
-            bool contrib = false;
-            if (active && kept + (uint32_t)k >= stop) active = false;
-            if (active) {
-                const float4 r2 = sm.r2[k];
-                if (in_box(r2, px, py)) {
-                    const float4 r0 = sm.r0[k], r1 = sm.r1[k];
-                    const float dx = __fsub_rn(r0.x, pcx), dy = __fsub_rn(r0.y, pcy);
-                    const float pw = power_of(r0.z, r0.w, r1.x, dx, dy);
-                    if (pw <= 0.0f) {
-                        const float ex = __expf(pw);
-                        const float araw = __fmul_rn(r1.y, ex);
-                        const float alpha = fminf(0.99f, araw);
-                        if (alpha >= (1.0f / 255.0f)) {
-                            const float one_m = __fsub_rn(1.0f, alpha);
-                            const float wgt = __fmul_rn(alpha, T);
-                            c0 = __fmaf_rn(r1.z, wgt, c0);
-                            c1 = __fmaf_rn(r1.w, wgt, c1);
-                            c2 = __fmaf_rn(r2.x, wgt, c2);
-                            const float inv = 1.0f / one_m;
-                            const float da = g0 * (r1.z * T - ((Cf0 - c0) + sb0) * inv) +
-                                             g1 * (r1.w * T - ((Cf1 - c1) + sb1) * inv) +
-                                             g2 * (r2.x * T - ((Cf2 - c2) + sb2) * inv);
-                            gv[6] = g0 * wgt; gv[7] = g1 * wgt; gv[8] = g2 * wgt;
-                            if (araw < 0.99f) {
-                                const float gpw = da * alpha;
-                                gv[5] = da * ex;
-                                gv[0] = -gpw * (r0.z * dx + r0.w * dy);
-                                gv[1] = -gpw * (r1.x * dy + r0.w * dx);
-                                gv[2] = -0.5f * gpw * dx * dx;
-                                gv[3] = -gpw * dx * dy;
-                                gv[4] = -0.5f * gpw * dy * dy;
-                            }
-                            T = __fmul_rn(T, one_m);
-                            contrib = true;
-                        }
-                    }
+                for (int j = 0; j < 9; ++j) g[j] = 0.0f;
+                bool contrib = false;
+                const float4 r0 = sm.r0[k], r1 = sm.r1[k], r2 = sm.r2[k];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    PixB &p = q[h];
+                    if (p.active && kept + (uint32_t)k >= p.stop) p.active = false;
+                    if (p.active) contrib |= adjoint(p, r0, r1, r2, px, h ? py1 : py0, g);
                 }
-            }
-            if (__ballot_sync(0xffffffffu, contrib)) {
+                if (__ballot_sync(0xffffffffu, contrib)) {
+                    const float x = reduce8_transpose(g, lane);
+                    float g8 = g[8];
 #pragma unroll
-                for (int j = 0; j < 9; ++j) {
-                    float x = gv[j];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                    gv[j] = x;
-                }
-                if (lane == 0) {
-#pragma unroll
-                    for (int j = 0; j < 9; ++j) atomicAdd(&gacc[k][j], gv[j]);
+                    for (int off = 16; off > 0; off >>= 1) g8 += __shfl_xor_sync(0xffffffffu, g8, off);
+                    if ((lane & 3) == 0) atomicAdd(&gacc[k][lane >> 2], x);
+                    if (lane == 1) atomicAdd(&gacc[k][8], g8);
                 }
             }
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < nk; k += TILE_PIX) {
+        for (int k = threadIdx.x; k < nk; k += RT) {
             float x[9];
             bool any = false;
 #pragma unroll
@@ -350,9 +457,9 @@ void launch_raster_fwd(const RasterArgs &a, cudaStream_t st)
     // one block per (tile, state), tile-major so states sharing a tile list run together
     const unsigned grid = a.tiles * (unsigned)a.S;
     ProfScope ps_(a.refs ? "raster_fwd_mse" : "raster_fwd", st);
-    if (a.images && a.refs) k_raster_fwd<true, true><<<grid, TILE_PIX, 0, st>>>(a);
-    else if (a.images) k_raster_fwd<true, false><<<grid, TILE_PIX, 0, st>>>(a);
-    else k_raster_fwd<false, true><<<grid, TILE_PIX, 0, st>>>(a);
+    if (a.images && a.refs) k_raster_fwd<true, true><<<grid, RT, 0, st>>>(a);
+    else if (a.images) k_raster_fwd<true, false><<<grid, RT, 0, st>>>(a);
+    else k_raster_fwd<false, true><<<grid, RT, 0, st>>>(a);
     count_launch();
 }
 
@@ -361,7 +468,7 @@ void launch_raster_bwd(const RasterBwdArgs &b, cudaStream_t st)
     if (b.f.S == 0 || b.f.tiles == 0) return;
     const unsigned grid = b.f.tiles * (unsigned)b.f.S;
     ProfScope ps_("raster_bwd", st);
-    k_raster_bwd<<<grid, TILE_PIX, 0, st>>>(b);
+    k_raster_bwd<<<grid, RT, 0, st>>>(b);
     count_launch();
 }
 

@@ -5,7 +5,9 @@
 // scan of the digit-major histogram table, stable scatter.  Stability inside
 // a block comes from giving every warp a contiguous run of 512 items that it
 // ranks in index order with __match_any_sync, then offsetting warps by the
-// digit counts of the warps before them.
+// digit counts of the warps before them.  The scatter first reorders the
+// block's 4096 items by digit in shared memory, then writes each digit run
+// with consecutive threads on consecutive slots (coalesced stores).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -153,7 +155,11 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t *kin, 
                                                            int shift, uint32_t mask,
                                                            const uint32_t *offsets, uint32_t nblocks)
 {
-    __shared__ uint32_t wh[RS_WARPS][RS_RADIX];
+    __shared__ uint32_t wh[RS_WARPS][RS_RADIX];     // per-warp digit counts, then offsets
+    __shared__ uint32_t dstart[RS_RADIX];           // first block-local slot of each digit
+    __shared__ uint32_t gbase[RS_RADIX];            // global slot of the block's first item of each digit
+    __shared__ uint32_t sk[RS_CHUNK], sv[RS_CHUNK]; // the block's items in (digit, index) order
+    __shared__ uint32_t wsum[RS_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int d = threadIdx.x; d < RS_WARPS * RS_RADIX; d += RS_THREADS) (&wh[0][0])[d] = 0;
     __syncthreads();
@@ -176,25 +182,43 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t *kin, 
         rank[k] = ok ? before + __popc(peers & lt) : 0xffffffffu;
     }
     __syncthreads();
-    // exclusive prefix of digit counts across warps (thread = digit)
-    {
-        const int d = threadIdx.x;
-        uint32_t run = 0;
+    // thread = digit: exclusive prefix across warps, digit total, then a
+    // block-wide exclusive scan of the totals gives each digit's local start
+    const int d = threadIdx.x;
+    uint32_t run = 0;
 #pragma unroll
-        for (int ww = 0; ww < RS_WARPS; ++ww) { uint32_t c = wh[ww][d]; wh[ww][d] = run; run += c; }
-        // fold in the global base of this digit for this block
-        uint32_t g = offsets[(size_t)d * nblocks + blockIdx.x];
+    for (int ww = 0; ww < RS_WARPS; ++ww) { uint32_t c = wh[ww][d]; wh[ww][d] = run; run += c; }
+    uint32_t inc = run;
 #pragma unroll
-        for (int ww = 0; ww < RS_WARPS; ++ww) wh[ww][d] += g;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
     }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    uint32_t woff = 0;
+    for (int ww = 0; ww < w; ++ww) woff += wsum[ww];
+    dstart[d] = woff + inc - run;
+    gbase[d] = offsets[(size_t)d * nblocks + blockIdx.x];
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
         if (rank[k] == 0xffffffffu) continue;
-        uint32_t d = (key[k] >> shift) & mask;
-        uint32_t pos = wh[w][d] + rank[k];
-        kout[pos] = key[k];
-        vout[pos] = val[k];
+        const uint32_t dk = (key[k] >> shift) & mask;
+        const uint32_t pos = dstart[dk] + wh[w][dk] + rank[k];
+        sk[pos] = key[k];
+        sv[pos] = val[k];
+    }
+    __syncthreads();
+    const size_t blk0 = (size_t)blockIdx.x * RS_CHUNK;
+    const uint32_t valid = n - blk0 < (size_t)RS_CHUNK ? (uint32_t)(n - blk0) : (uint32_t)RS_CHUNK;
+    // consecutive threads write consecutive slots of each digit run: coalesced
+    for (uint32_t i = threadIdx.x; i < valid; i += RS_THREADS) {
+        const uint32_t kk = sk[i];
+        const uint32_t dk = (kk >> shift) & mask;
+        const uint32_t g = gbase[dk] + (i - dstart[dk]);
+        kout[g] = kk;
+        vout[g] = sv[i];
     }
 }
 

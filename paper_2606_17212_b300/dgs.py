@@ -49,7 +49,7 @@ class States_t(ctypes.Structure):
 EXPORTS = ("dgs_create", "dgs_destroy", "dgs_last_error", "dgs_version", "dgs_render_state",
            "dgs_render_states_batched", "dgs_render_backward", "dgs_state_utility", "dgs_image_mse",
            "dgs_kernel_launches", "dgs_reset_kernel_launches", "dgs_profile_enable", "dgs_profile_read",
-           "dgs_image_mse_noalloc")
+           "dgs_image_mse_noalloc", "dgs_debug_tile_lists")
 
 _lib = None
 
@@ -85,6 +85,8 @@ def lib():
         L.dgs_profile_read.restype = I
         L.dgs_image_mse_noalloc.argtypes = [P, P, P, I, I, I, I, F, P, P, P, P]
         L.dgs_image_mse_noalloc.restype = I
+        L.dgs_debug_tile_lists.argtypes = [P] * 11 + [P]
+        L.dgs_debug_tile_lists.restype = I
         _lib = L
     return _lib
 
@@ -213,6 +215,28 @@ class Renderer:
             self._check(n, "dgs_profile_read")
         raw = names.raw
         return {raw[32 * k:32 * k + 32].split(b"\0")[0].decode(): (ms[k], cnt[k]) for k in range(n)}
+
+    def debug_tile_lists(self, stream=None) -> dict:
+        """Copies of the last forward call's records and sorted lists (numpy)."""
+        import torch
+        n_rec, n_ent = ctypes.c_uint32(), ctypes.c_uint32()
+        nvg, tiles = ctypes.c_int32(), ctypes.c_uint32()
+        z = None
+        self._check(self._lib.dgs_debug_tile_lists(self.h, ctypes.byref(n_rec), ctypes.byref(n_ent),
+                                                   ctypes.byref(nvg), ctypes.byref(tiles), z, z, z, z, z, z,
+                                                   _stream(stream)), "dgs_debug_tile_lists")
+        nr, ne, nrg = n_rec.value, n_ent.value, nvg.value * tiles.value
+        mk = lambda *shape: torch.empty(shape, dtype=torch.int32, device="cuda")
+        recs, dk, ds, ek, ev, rg = mk(max(nr, 1), 12), mk(max(nr, 1)), mk(max(nr, 1)), mk(max(ne, 1)), \
+            mk(max(ne, 1)), mk(max(nrg, 1), 2)
+        self._check(self._lib.dgs_debug_tile_lists(self.h, None, None, None, None, _ptr(recs), _ptr(dk), _ptr(ds),
+                                                   _ptr(ek), _ptr(ev), _ptr(rg), _stream(stream)),
+                    "dgs_debug_tile_lists")
+        torch.cuda.synchronize()
+        u = lambda t, n: t.cpu().numpy().view(np.uint32)[:n]
+        return dict(n_rec=nr, n_ent=ne, view_groups=nvg.value, tiles=tiles.value,
+                    recs=recs.cpu().numpy().view(np.uint32)[:nr], depth_keys=u(dk, nr), depth_slots=u(ds, nr),
+                    entry_keys=u(ek, ne), entry_vals=u(ev, ne), ranges=rg.cpu().numpy().view(np.uint32)[:nrg])
 
     def render_state(self, scene: DeviceScene, mask, t: float, cam, bg, out=None, stream=None):
         import torch

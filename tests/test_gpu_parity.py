@@ -245,3 +245,95 @@ def test_backward_undelivered_layers_exactly_zero_and_autograd(R, torch):
     assert np.all(res_g[1:, cl == c2] == 0.0)        # depth 2: only layer 1
     assert np.abs(res_g[0, cl == c2]).max() > 0
     assert np.abs(sc.t["mu0"].grad.cpu().numpy()).max() > 0
+
+
+# --------------------------------------------------------------------- tile lists
+def _unpack_boxes(recs):
+    bx, by, cd = recs[:, 9], recs[:, 10], recs[:, 11]
+    return (bx & 0xFFFF).astype(np.int64), (bx >> 16).astype(np.int64), (by & 0xFFFF).astype(np.int64), \
+        (by >> 16).astype(np.int64), ((cd >> 12) & 0xF).astype(np.int64), (cd >> 16).astype(np.int64), \
+        (cd & 0xFFF).astype(np.int64)
+
+
+def test_tile_lists_bitwise_and_end_to_end(R, torch):
+    w = synth.config("c3_fwdbwd_250k", scale=0.01, n_states=10)
+    sc_h = w.scene
+    sc = dgs.DeviceScene.from_host(sc_h)
+    st = _gpu_states(w)
+    R.render_states_batched(sc, st, w.cams, w.bg)
+    d = R.debug_tile_lists()
+    n_rec, T = d["n_rec"], d["tiles"]
+    W, H = w.cams[0].width, w.cams[0].height
+    tx, ty = -(-W // 16), -(-H // 16)
+    assert T == tx * ty
+    recs = d["recs"]
+    xlo, xhi, ylo, yhi, depth, vg, clus = _unpack_boxes(recs)
+    live = depth != 0
+    dkey = np.full(n_rec, 0xFFFFFFFF, np.uint64)
+    dkey[d["depth_slots"].astype(np.int64)] = d["depth_keys"]
+    # depth sort = stable sort of the per-record depth keys
+    order = np.argsort(dkey, kind="stable")
+    assert np.array_equal(order, d["depth_slots"].astype(np.int64))
+    # (1) bitwise: the oracle's integer binning of the GPU's own records
+    keys, vals, ranges = oracle.bin_tiles(xlo, xhi, ylo, yhi, dkey, live, 16, tx, ty, view_group=vg,
+                                          rank=np.arange(n_rec))
+    assert np.array_equal((keys >> np.uint64(32)).astype(np.uint32), d["entry_keys"])
+    assert np.array_equal(vals.astype(np.uint32), d["entry_vals"])
+    g_rng = d["ranges"].reshape(-1, 2).astype(np.int64)
+    for k in range(len(g_rng)):
+        lo, hi = ranges[k] if k < len(ranges) else (0, 0)
+        if hi > lo:
+            assert tuple(g_rng[k]) == (lo, hi), k
+        else:
+            assert g_rng[k][0] == g_rng[k][1], k
+    # (2) end to end: the same slots from FP64 projections
+    views = []
+    for s in range(w.states.n):
+        key = (int(w.states.cam[s]), float(w.states.t[s]))
+        if key not in views:
+            views.append(key)
+    D = oracle.state_depths(w.states, sc_h.n_clusters, sc_h.n_layers)
+    vg_of = [views.index((int(w.states.cam[s]), float(w.states.t[s]))) for s in range(w.states.n)]
+    need = [[set() for _ in range(sc_h.n_clusters)] for _ in views]
+    for s in range(w.states.n):
+        for c in range(sc_h.n_clusters):
+            if D[s, c] > 0:
+                need[vg_of[s]][c].add(int(D[s, c]))
+    proj = {}
+    offs = sc_h.cluster_offsets
+    o_live = np.zeros(n_rec, bool); o_box = np.zeros((n_rec, 4), np.int64)
+    o_z = np.zeros(n_rec, np.float32); o_marg = np.zeros(n_rec, bool)
+    slot = 0
+    for v, (cam_i, t) in enumerate(views):
+        for c in range(sc_h.n_clusters):
+            ds = sorted(need[v][c])
+            for i in range(offs[c], offs[c + 1]):
+                for dd in ds:
+                    if (v, dd) not in proj:
+                        proj[(v, dd)] = oracle.project(sc_h, np.full(sc_h.n_clusters, dd, np.uint8), t,
+                                                       w.cams[cam_i])
+                    r = proj[(v, dd)][i]
+                    vb = r[20:24].astype(np.int64)
+                    o_live[slot] = r[0] > 0 and vb[0] <= vb[1] and vb[2] <= vb[3]
+                    o_box[slot] = vb
+                    o_z[slot] = np.float32(r[18])
+                    o_marg[slot] = bool(r[24] or r[16] or r[17])
+                    assert vg[slot] == v and clus[slot] == c and depth[slot] in (0, dd)
+                    slot += 1
+    assert slot == n_rec
+    ok = ~o_marg
+    assert o_marg.mean() < 0.03
+    assert np.array_equal(o_live[ok], live[ok])
+    both = ok & live
+    assert np.array_equal(o_box[both], np.stack([xlo, xhi, ylo, yhi], 1)[both])
+    gz = dkey[both].astype(np.uint32).view(np.float32)
+    assert np.all(np.abs(gz.astype(np.float64) - o_z[both]) <= 4e-7 * np.abs(o_z[both]))
+    # per tile, the GPU run restricted to non-marginal records is the FP64 depth order
+    ev = d["entry_vals"].astype(np.int64)
+    for k in range(len(g_rng)):
+        lo, hi = g_rng[k]
+        seq = [x for x in ev[lo:hi] if ok[x]]
+        zs = o_z[seq].astype(np.float64)
+        bad = np.nonzero(np.diff(zs) < 0)[0]
+        for b in bad:   # only near-ties (FP32 vs FP64 depth within a few ulps) may swap
+            assert zs[b] - zs[b + 1] <= 8e-7 * zs[b], (k, b)

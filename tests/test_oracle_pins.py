@@ -507,3 +507,32 @@ def test_undelivered_residuals_get_exactly_zero_gradient():
     for i in range(sc.n):
         d = depth[cl[i]]
         assert np.all(g["res"][d - 1:, i] == 0.0)
+
+
+def test_visible_box_contains_every_contributing_pixel():
+    """The tile-binning box (pixel box cut to the alpha >= 1/255 ellipse's bounding
+    box) keeps every pixel whose alpha reaches 1/255 and never exceeds the pixel box."""
+    rng = np.random.default_rng(8)
+    cam = synth.ring_camera(0, 1, 96, 80, 110.0)
+    n = 200
+    mu = rng.normal(0, 0.6, size=(n, 3))
+    ls = rng.normal(-2.8, 0.5, size=(n, 3))
+    q = rng.normal(size=(n, 4)); q /= np.linalg.norm(q, axis=1, keepdims=True)
+    lg = rng.normal(-1.0, 2.5, size=n)
+    sc = tiny_scene(mu, ls, q, lg, rng.uniform(size=(n, 3)))
+    rec = oracle.project(sc, np.array([1], np.uint8), 0.0, cam)
+    checked = 0
+    for r in rec:
+        if r[0] <= 0:
+            continue
+        vx0, vx1, vy0, vy1 = r[20:24]
+        if vx0 <= vx1 and vy0 <= vy1:
+            assert r[12] <= vx0 and vx1 <= r[13] and r[14] <= vy0 and vy1 <= r[15]
+        for py in range(int(r[14]), int(r[15]) + 1):
+            for px in range(int(r[12]), int(r[13]) + 1):
+                dx, dy = r[1] - (px + 0.5), r[2] - (py + 0.5)
+                pw = -0.5 * (r[3] * dx * dx + r[5] * dy * dy) - r[4] * dx * dy
+                if pw <= 0 and r[7] * math.exp(pw) >= 1.0 / 255.0:
+                    assert vx0 <= px <= vx1 and vy0 <= py <= vy1
+                    checked += 1
+    assert checked > 1000

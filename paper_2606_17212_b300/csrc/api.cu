@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <string>
 #include <utility>
@@ -85,6 +86,7 @@ struct Lists {
     uint32_t nRec = 0, nEnt = 0;
     uint32_t *depth_keys = nullptr, *depth_slots = nullptr;   // records sorted by depth
     uint32_t *ekeys = nullptr, *evals = nullptr;              // entries sorted by (view group, tile)
+    uint32_t *tile_order = nullptr;                           // (view group, tile), costliest first
 };
 
 struct Tape {
@@ -105,7 +107,8 @@ struct dgs_ctx {
     int sms = 148;
     std::string err;
     Buf vgs, vgos, depth, need, counts, recBase, total, recs, k0, v0, k1, v1, tcount, toffs, ek0, ev0, ek1, ev1,
-        ranges, sortws, scanws, partial, refs, recgrad, refidx;
+        ranges, sortws, scanws, partial, refs, recgrad, refidx, tck0, tcv0, tck1, tcv1, icnt, ioff, qint, counter;
+    std::map<std::vector<long long>, int> tuned_G;   // autotuner: call shape -> states per block
     void *h_stage = nullptr;
     size_t h_stage_cap = 0;
     uint32_t *h_small = nullptr;   // pinned readback of counts
@@ -364,6 +367,18 @@ int prepare(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *masks, const P
     out.nEnt = nEnt;
     CK(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * (size_t)p.V * p.tiles, st));
     launch_ranges(ekeys, nEnt, (uint2 *)ctx->ranges.p, ctx->sms, st);
+    // (view group, tile) pairs in descending entry count: the raster work order
+    const size_t vt = (size_t)p.V * p.tiles;
+    TRY(ensure(ctx, ctx->tck0, 4 * vt, st));
+    TRY(ensure(ctx, ctx->tcv0, 4 * vt, st));
+    TRY(ensure(ctx, ctx->tck1, 4 * vt, st));
+    TRY(ensure(ctx, ctx->tcv1, 4 * vt, st));
+    TRY(ensure(ctx, ctx->sortws, radix_workspace_bytes(vt), st));
+    launch_tile_costs((const uint2 *)ctx->ranges.p, (uint32_t)vt, (uint32_t *)ctx->tck0.p, (uint32_t *)ctx->tcv0.p,
+                      ctx->sms, st);
+    CK(radix_sort_pairs((uint32_t *)ctx->tck0.p, (uint32_t *)ctx->tcv0.p, (uint32_t *)ctx->tck1.p,
+                        (uint32_t *)ctx->tcv1.p, vt, 32, ctx->sortws.p, st, &alt));
+    out.tile_order = alt ? (uint32_t *)ctx->tcv1.p : (uint32_t *)ctx->tcv0.p;
     CK(cudaGetLastError());
     return DGS_OK;
 }
@@ -379,6 +394,7 @@ RasterArgs raster_args(dgs_ctx *ctx, const Plan &p, int C, const float *bg, uint
     a.S = p.S_user; a.C = C; a.W = p.W; a.H = p.H; a.tiles_x = p.tiles_x; a.tiles = p.tiles;
     a.bg0 = bg[0]; a.bg1 = bg[1]; a.bg2 = bg[2];
     a.images = nullptr; a.refs = nullptr; a.ref_of_state = nullptr; a.partial = nullptr;
+    a.img_s0 = 0;
     return a;
 }
 
@@ -412,6 +428,101 @@ void record_tape(Tape &tp, const dgs_scene *sc, const dgs_states *st, const dgs_
     tp.lists = L;
 }
 
+// Forward raster of states [s0, s1) of the plan: group them by view group in
+// groups of at most G, build the cost-ordered work queue and launch the
+// persistent kernel.
+int launch_fwd_pass(dgs_ctx *ctx, const Plan &p, const Lists &L, const RasterArgs &a, int s0, int s1, int G,
+                    cudaStream_t st)
+{
+    const int n = s1 - s0;
+    if (n <= 0) return DGS_OK;
+    std::vector<std::vector<int32_t>> per_vg(p.V);
+    for (int s = s0; s < s1; ++s) per_vg[p.vg_of_state[s]].push_back(s);
+    std::vector<int32_t> order, gfirst, gcount, gbase(p.V), ngroups(p.V);
+    order.reserve(n);
+    for (int v = 0; v < p.V; ++v) {
+        gbase[v] = (int32_t)gfirst.size();
+        for (size_t k = 0; k < per_vg[v].size(); k += G) {
+            gfirst.push_back((int32_t)order.size() + (int32_t)k);
+            gcount.push_back((int32_t)std::min<size_t>(G, per_vg[v].size() - k));
+        }
+        ngroups[v] = (int32_t)gfirst.size() - gbase[v];
+        order.insert(order.end(), per_vg[v].begin(), per_vg[v].end());
+    }
+    const size_t ng = gfirst.size(), vt = (size_t)p.V * p.tiles;
+    const size_t ints = order.size() + 2 * ng + 2 * (size_t)p.V;
+    TRY(ensure(ctx, ctx->qint, 4 * ints, st));
+    TRY(ensure(ctx, ctx->icnt, 4 * (vt + 1), st));
+    TRY(ensure(ctx, ctx->ioff, 4 * (vt + 1), st));
+    TRY(ensure(ctx, ctx->counter, 16, st));
+    TRY(ensure(ctx, ctx->scanws, scan_workspace_bytes(vt + 1), st));
+    TRY(ensure_stage(ctx, 4 * ints, st));
+    CK(cudaEventSynchronize(ctx->stage_done));
+    int32_t *h = (int32_t *)ctx->h_stage;
+    size_t o = 0;
+    std::memcpy(h + o, order.data(), 4 * order.size()); const size_t o_order = o; o += order.size();
+    std::memcpy(h + o, gfirst.data(), 4 * ng); const size_t o_first = o; o += ng;
+    std::memcpy(h + o, gcount.data(), 4 * ng); const size_t o_count = o; o += ng;
+    std::memcpy(h + o, gbase.data(), 4 * (size_t)p.V); const size_t o_base = o; o += p.V;
+    std::memcpy(h + o, ngroups.data(), 4 * (size_t)p.V); const size_t o_ng = o; o += p.V;
+    CK(cudaMemcpyAsync(ctx->qint.p, h, 4 * o, cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(ctx->stage_done, st));
+    const int32_t *qd = (const int32_t *)ctx->qint.p;
+    launch_item_counts(L.tile_order, (uint32_t)vt, p.tiles, qd + o_ng, (uint32_t *)ctx->icnt.p, ctx->sms, st);
+    CK(exclusive_scan_u32((const uint32_t *)ctx->icnt.p, (uint32_t *)ctx->ioff.p, vt, nullptr, ctx->scanws.p, st));
+    CK(cudaMemsetAsync(ctx->counter.p, 0, 4, st));
+    WorkQueue q;
+    q.tile_order = L.tile_order;
+    q.item_offsets = (const uint32_t *)ctx->ioff.p;
+    q.n_vt = (uint32_t)vt;
+    q.n_items = (uint32_t)(ng * p.tiles);
+    q.group_first = qd + o_first;
+    q.group_count = qd + o_count;
+    q.vg_group_base = qd + o_base;
+    q.state_order = qd + o_order;
+    q.counter = (uint32_t *)ctx->counter.p;
+    const int blocks = ctx->sms * raster_fwd_blocks_per_sm(G, a.images != nullptr, a.refs != nullptr);
+    launch_raster_fwd(a, q, G, blocks, st);
+    CK(cudaGetLastError());
+    return DGS_OK;
+}
+
+// Autotuned forward pass: the first call of a given shape times every
+// states-per-block choice (each produces the same bits) and keeps the fastest.
+int fwd_pass(dgs_ctx *ctx, const dgs_scene *scene, const Plan &p, const Lists &L, const RasterArgs &a, int s0,
+             int s1, cudaStream_t st)
+{
+    int maxper = 1;
+    {
+        std::vector<int> cnt(p.V, 0);
+        for (int s = s0; s < s1; ++s) maxper = std::max(maxper, ++cnt[p.vg_of_state[s]]);
+    }
+    const std::vector<long long> key = {s1 - s0, p.V, p.W, p.H, scene->n, scene->n_clusters, scene->n_layers,
+                                        a.images != nullptr, a.refs != nullptr, maxper};
+    auto it = ctx->tuned_G.find(key);
+    if (it != ctx->tuned_G.end()) return launch_fwd_pass(ctx, p, L, a, s0, s1, it->second, st);
+    const int cands[4] = {1, 2, 4, 8};
+    int best = 1;
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int G : cands) {
+        if (G > 1 && G / 2 >= maxper) break;
+        CK(cudaEventRecord(e0, st));
+        TRY(launch_fwd_pass(ctx, p, L, a, s0, s1, G, st));
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) { best_ms = ms; best = G; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tuned_G[key] = best;   // every trial wrote the same bits, so the outputs are final
+    return DGS_OK;
+}
+
 int render_batched(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states, const dgs_camera *cams,
                    int n_cams, const float *bg, float *images, cudaStream_t st)
 {
@@ -426,8 +537,7 @@ int render_batched(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *state
     TRY(prepare(ctx, scene, states->masks, p, false, st, L));
     RasterArgs a = raster_args(ctx, p, scene->n_clusters, bg, L.evals);
     a.images = images;
-    launch_raster_fwd(a, st);
-    CK(cudaGetLastError());
+    TRY(fwd_pass(ctx, scene, p, L, a, 0, p.S_user, st));
     record_tape(ctx->tape, scene, states, cams, n_cams, p, L);
     return DGS_OK;
 }
@@ -471,7 +581,11 @@ void dgs_destroy(dgs_ctx *ctx)
                    &ctx->recs, &ctx->k0, &ctx->v0, &ctx->k1, &ctx->v1, &ctx->tcount, &ctx->toffs, &ctx->ek0,
                    &ctx->ev0, &ctx->ek1, &ctx->ev1, &ctx->ranges, &ctx->sortws, &ctx->scanws, &ctx->partial,
                    &ctx->refs, &ctx->recgrad, &ctx->refidx};
+    Buf *more[] = {&ctx->tck0, &ctx->tcv0, &ctx->tck1, &ctx->tcv1, &ctx->icnt, &ctx->ioff, &ctx->qint,
+                   &ctx->counter};
     for (Buf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    for (Buf *b : more)
         if (b->p) cudaFree(b->p);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->h_small) cudaFreeHost(ctx->h_small);
@@ -615,17 +729,15 @@ int dgs_state_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *st
     TRY(ensure(ctx, ctx->partial, sizeof(double) * (size_t)p.S_user * p.tiles, st));
     // complete renders of every view group (appended states S_user .. S-1)
     RasterArgs r = raster_args(ctx, p, scene->n_clusters, bg, sorted);
-    r.S = p.V;
-    r.depth = (const uint8_t *)ctx->depth.p + (size_t)p.S_user * scene->n_clusters;
-    r.vg_of_state = (const int32_t *)ctx->vgos.p + p.S_user;
     r.images = (float *)ctx->refs.p;
-    launch_raster_fwd(r, st);
+    r.img_s0 = p.S_user;
+    TRY(fwd_pass(ctx, scene, p, L, r, p.S_user, p.S, st));
     // every state: fused FP64 squared error against its view's complete render
     RasterArgs a = raster_args(ctx, p, scene->n_clusters, bg, sorted);
     a.refs = (const float *)ctx->refs.p;
     a.ref_of_state = (const int32_t *)ctx->vgos.p;
     a.partial = (double *)ctx->partial.p;
-    launch_raster_fwd(a, st);
+    TRY(fwd_pass(ctx, scene, p, L, a, 0, p.S_user, st));
     launch_mse_reduce((const double *)ctx->partial.p, p.S_user, (int)p.tiles, 1.0 / (double)img, mse, psnr, st);
     CK(cudaGetLastError());
     return DGS_OK;

@@ -32,8 +32,27 @@ struct RasterArgs {
     const float *refs;            // [n_refs][H][W][3] or null (MSE epilogue)
     const int32_t *ref_of_state;  // [S]
     double *partial;              // [S][tiles] FP64 squared-error partial sums
+    int img_s0;                   // images hold states img_s0, img_s0 + 1, ...
 };
-void launch_raster_fwd(const RasterArgs &a, cudaStream_t st);
+// Work queue of the persistent forward raster: (view group, tile) pairs in
+// descending cost order, each expanded into that view group's state groups.
+struct WorkQueue {
+    const uint32_t *tile_order;    // [V * tiles] view group * tiles + tile, costliest first
+    const uint32_t *item_offsets;  // [V * tiles + 1] first work item of each tile_order entry
+    uint32_t n_vt;                 // V * tiles
+    uint32_t n_items;
+    const int32_t *group_first;    // [n_groups] first index into state_order
+    const int32_t *group_count;    // [n_groups] states in the group (<= G)
+    const int32_t *vg_group_base;  // [V] first group of each view group
+    const int32_t *state_order;    // [S] states sorted by view group
+    uint32_t *counter;             // zeroed before the launch
+};
+// G = states composited per staged batch (1, 2, 4 or 8); blocks = persistent grid.
+void launch_raster_fwd(const RasterArgs &a, const WorkQueue &q, int G, int blocks, cudaStream_t st);
+int raster_fwd_blocks_per_sm(int G, bool write, bool mse);
+void launch_tile_costs(const uint2 *ranges, uint32_t n, uint32_t *keys, uint32_t *vals, int sms, cudaStream_t st);
+void launch_item_counts(const uint32_t *tile_order, uint32_t n, uint32_t tiles, const int32_t *vg_ngroups,
+                        uint32_t *counts, int sms, cudaStream_t st);
 
 struct RasterBwdArgs {
     RasterArgs f;

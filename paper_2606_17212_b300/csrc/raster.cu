@@ -153,71 +153,190 @@ __device__ __forceinline__ void load_depth_row(const uint8_t *depth, int s, int 
     for (int c = threadIdx.x; c < C; c += blockDim.x) sdep[c] = depth[(size_t)s * C + c];
 }
 
-template <bool WRITE, bool MSE>
-__global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a)
+// Stage entries [start, min(start + BATCH, end)) of the tile run unfiltered
+// (every depth variant: the states of a group filter per warp).  Returns nk.
+__device__ __forceinline__ int stage_all(const Rec *__restrict__ recs, const uint32_t *__restrict__ evals,
+                                         uint32_t start, uint32_t end, Staged &sm)
+{
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int j = h * RT + threadIdx.x;
+        const uint32_t e = start + (uint32_t)j;
+        if (e < end) {
+            const uint32_t slot = __ldg(evals + e);
+            const float4 *p = reinterpret_cast<const float4 *>(recs + slot);
+            sm.r0[j] = __ldg(p); sm.r1[j] = __ldg(p + 1); sm.r2[j] = __ldg(p + 2);
+        }
+    }
+    __syncthreads();
+    return (int)min(end - start, (uint32_t)BATCH);
+}
+
+// Warp w's list of staged entries that state row `dep` renders (variant depth
+// == the state's delivered depth of the entry's cluster) and whose box meets
+// the warp's rows.  Returns the list length (same in all lanes).
+__device__ __forceinline__ int warp_list(const Staged &sm, uint8_t *list, int nk, const uint8_t *dep, int wr0)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    int n = 0;
+    for (int j0 = 0; j0 < nk; j0 += 32) {
+        const int j = j0 + lane;
+        bool hit = false;
+        if (j < nk) {
+            const float4 r2 = sm.r2[j];
+            const uint32_t by = __float_as_uint(r2.z), cd = __float_as_uint(r2.w);
+            hit = (int)(by & 0xffffu) <= wr0 + 3 && (int)(by >> 16) >= wr0 &&
+                  ((cd >> 12) & 0xfu) == (uint32_t)dep[cd & 0xfffu];
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+        if (hit) list[n + __popc(bal & lt)] = (uint8_t)j;
+        n += __popc(bal);
+    }
+    __syncwarp();
+    return n;
+}
+
+// Persistent forward raster.  Each block repeatedly takes a work item (one
+// tile of one view group and a group of up to G states of that view group),
+// stages the tile's Gaussians once per batch and composites them for every
+// state of the group; items come costliest tile first from an atomic counter.
+// Per pixel and state the arithmetic is composite(), exactly as for a single
+// state, so grouping never changes a bit of the result.
+template <int G, bool WRITE, bool MSE>
+__global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a, WorkQueue q)
 {
     __shared__ Staged sm;
-    __shared__ uint8_t sdep[MAX_CLUSTERS];
-    __shared__ double wsum[RW];
-    const int tile = (int)(blockIdx.x / (unsigned)a.S), s = (int)(blockIdx.x % (unsigned)a.S);
+    __shared__ uint8_t sdep[G][MAX_CLUSTERS];
+    __shared__ double wsum[G][RW];
+    __shared__ uint32_t s_item;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int v = a.vg_of_state[s];
-    load_depth_row(a.depth, s, a.C, sdep);
-    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const int px = tx * TILE + (lane & 15);
-    const int py0 = ty * TILE + 4 * w + 2 * (lane >> 4), py1 = py0 + 1;
-    const bool in0 = px < a.W && py0 < a.H, in1 = px < a.W && py1 < a.H;
-    const uint2 rg = a.ranges[(size_t)v * a.tiles + tile];
-    Pix p0 = {1.0f, 0.0f, 0.0f, 0.0f, !in0}, p1 = {1.0f, 0.0f, 0.0f, 0.0f, !in1};
-    for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
-        if (__syncthreads_count(!(p0.done && p1.done)) == 0) break;
-        stage_batch(a.recs, a.evals, sdep, start, rg.y, ty * TILE, sm);
-        const int n = sm.cnt[w];
-        for (int i = 0; i < n; ++i) {
-            if (p0.done && p1.done) break;
-            const int k = sm.list[w][i];
-            const float4 r0 = sm.r0[k], r1 = sm.r1[k], r2 = sm.r2[k];
-            if (!p0.done && composite(p0, r0, r1, r2, px, py0)) p0.done = true;
-            if (!p1.done && composite(p1, r0, r1, r2, px, py1)) p1.done = true;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(q.counter, 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= q.n_items) break;
+        // largest j with item_offsets[j] <= item
+        uint32_t lo = 0, hi = q.n_vt - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (q.item_offsets[mid] <= item) lo = mid; else hi = mid - 1;
         }
-    }
-    float o[2][3];
-    o[0][0] = __fmaf_rn(p0.T, a.bg0, p0.c0); o[0][1] = __fmaf_rn(p0.T, a.bg1, p0.c1); o[0][2] = __fmaf_rn(p0.T, a.bg2, p0.c2);
-    o[1][0] = __fmaf_rn(p1.T, a.bg0, p1.c0); o[1][1] = __fmaf_rn(p1.T, a.bg1, p1.c1); o[1][2] = __fmaf_rn(p1.T, a.bg2, p1.c2);
-    if (WRITE) {
-        if (in0) {
-            float *dst = a.images + (((size_t)s * a.H + py0) * a.W + px) * 3;
-            dst[0] = o[0][0]; dst[1] = o[0][1]; dst[2] = o[0][2];
-        }
-        if (in1) {
-            float *dst = a.images + (((size_t)s * a.H + py1) * a.W + px) * 3;
-            dst[0] = o[1][0]; dst[1] = o[1][1]; dst[2] = o[1][2];
-        }
-    }
-    if (MSE) {
-        double se = 0.0;
-        const float *rbase = a.refs + (size_t)a.ref_of_state[s] * a.H * a.W * 3;
+        const uint32_t vt = q.tile_order[lo];
+        const int v = (int)(vt / a.tiles), tile = (int)(vt % a.tiles);
+        const int grp = q.vg_group_base[v] + (int)(item - q.item_offsets[lo]);
+        const int first = q.group_first[grp], cnt = q.group_count[grp];
+        int sid[G];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int py = h ? py1 : py0;
-            if (h ? in1 : in0) {
-                const float *rp = rbase + ((size_t)py * a.W + px) * 3;
-                const double d0 = (double)o[h][0] - (double)rp[0], d1 = (double)o[h][1] - (double)rp[1];
-                const double d2 = (double)o[h][2] - (double)rp[2];
-                se += d0 * d0 + d1 * d1 + d2 * d2;
+        for (int g = 0; g < G; ++g) sid[g] = g < cnt ? q.state_order[first + g] : -1;
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            if (sid[g] >= 0)
+                for (int c = threadIdx.x; c < a.C; c += RT) sdep[g][c] = a.depth[(size_t)sid[g] * a.C + c];
+        const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+        const int px = tx * TILE + (lane & 15);
+        const int py0 = ty * TILE + 4 * w + 2 * (lane >> 4), py1 = py0 + 1;
+        const bool in0 = px < a.W && py0 < a.H, in1 = px < a.W && py1 < a.H;
+        const int wr0 = ty * TILE + 4 * w;
+        const uint2 rg = a.ranges[vt];
+        Pix p[G][2];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            p[g][0] = {1.0f, 0.0f, 0.0f, 0.0f, !in0 || sid[g] < 0};
+            p[g][1] = {1.0f, 0.0f, 0.0f, 0.0f, !in1 || sid[g] < 0};
+        }
+        for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
+            bool alive = false;
+#pragma unroll
+            for (int g = 0; g < G; ++g) alive |= !(p[g][0].done && p[g][1].done);
+            if (__syncthreads_count(alive) == 0) break;
+            const int nk = stage_all(a.recs, a.evals, start, rg.y, sm);
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                if (!__any_sync(0xffffffffu, !(p[g][0].done && p[g][1].done))) continue;
+                const int n = warp_list(sm, sm.list[w], nk, sdep[g], wr0);
+                for (int i = 0; i < n; ++i) {
+                    if (p[g][0].done && p[g][1].done) break;
+                    const int k = sm.list[w][i];
+                    const float4 r0 = sm.r0[k], r1 = sm.r1[k], r2 = sm.r2[k];
+                    if (!p[g][0].done && composite(p[g][0], r0, r1, r2, px, py0)) p[g][0].done = true;
+                    if (!p[g][1].done && composite(p[g][1], r0, r1, r2, px, py1)) p[g][1].done = true;
+                }
+                __syncwarp();
             }
         }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) se += __shfl_xor_sync(0xffffffffu, se, off);
-        if (lane == 0) wsum[w] = se;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double tot = 0.0;
+        for (int g = 0; g < G; ++g) {
+            if (sid[g] < 0) continue;
+            const int s = sid[g];
+            float o[2][3];
 #pragma unroll
-            for (int k = 0; k < RW; ++k) tot += wsum[k];
-            a.partial[(size_t)s * a.tiles + tile] = tot;
+            for (int h = 0; h < 2; ++h) {
+                o[h][0] = __fmaf_rn(p[g][h].T, a.bg0, p[g][h].c0);
+                o[h][1] = __fmaf_rn(p[g][h].T, a.bg1, p[g][h].c1);
+                o[h][2] = __fmaf_rn(p[g][h].T, a.bg2, p[g][h].c2);
+            }
+            if (WRITE) {
+                const size_t si = (size_t)(s - a.img_s0);
+                if (in0) {
+                    float *dst = a.images + ((si * a.H + py0) * a.W + px) * 3;
+                    dst[0] = o[0][0]; dst[1] = o[0][1]; dst[2] = o[0][2];
+                }
+                if (in1) {
+                    float *dst = a.images + ((si * a.H + py1) * a.W + px) * 3;
+                    dst[0] = o[1][0]; dst[1] = o[1][1]; dst[2] = o[1][2];
+                }
+            }
+            if (MSE) {
+                double se = 0.0;
+                const float *rbase = a.refs + (size_t)a.ref_of_state[s] * a.H * a.W * 3;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int py = h ? py1 : py0;
+                    if (h ? in1 : in0) {
+                        const float *rp = rbase + ((size_t)py * a.W + px) * 3;
+                        const double d0 = (double)o[h][0] - (double)rp[0], d1 = (double)o[h][1] - (double)rp[1];
+                        const double d2 = (double)o[h][2] - (double)rp[2];
+                        se += d0 * d0 + d1 * d1 + d2 * d2;
+                    }
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) se += __shfl_xor_sync(0xffffffffu, se, off);
+                if (lane == 0) wsum[g][w] = se;
+            }
         }
+        if (MSE) {
+            __syncthreads();
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                if (threadIdx.x == g && sid[g] >= 0) {
+                    double tot = 0.0;
+#pragma unroll
+                    for (int k = 0; k < RW; ++k) tot += wsum[g][k];
+                    a.partial[(size_t)sid[g] * a.tiles + tile] = tot;
+                }
+            }
+        }
+        __syncthreads();
     }
+}
+
+// Cost key of each (view group, tile): ascending key = descending entry count.
+__global__ void k_tile_costs(const uint2 *__restrict__ ranges, uint32_t n, uint32_t *__restrict__ keys,
+                             uint32_t *__restrict__ vals)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint2 r = ranges[i];
+        keys[i] = 0xffffffffu - (r.y - r.x);
+        vals[i] = i;
+    }
+}
+
+__global__ void k_item_counts(const uint32_t *__restrict__ tile_order, uint32_t n, uint32_t tiles,
+                              const int32_t *__restrict__ vg_ngroups, uint32_t *__restrict__ counts)
+{
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        counts[j] = (uint32_t)vg_ngroups[tile_order[j] / tiles];
 }
 
 // Per-pixel state of the adjoint walk.
@@ -451,15 +570,77 @@ __global__ void __launch_bounds__(256) k_image_mse(const float *__restrict__ ima
 
 }  // namespace
 
-void launch_raster_fwd(const RasterArgs &a, cudaStream_t st)
+template <int G, bool WRITE, bool MSE>
+static void launch_fwd_t(const RasterArgs &a, const WorkQueue &q, int blocks, cudaStream_t st)
 {
-    if (a.S == 0 || a.tiles == 0 || (!a.images && !a.refs)) return;
-    // one block per (tile, state), tile-major so states sharing a tile list run together
-    const unsigned grid = a.tiles * (unsigned)a.S;
+    k_raster_fwd<G, WRITE, MSE><<<blocks, RT, 0, st>>>(a, q);
+}
+
+template <int G>
+static void launch_fwd_g(const RasterArgs &a, const WorkQueue &q, int blocks, cudaStream_t st)
+{
+    if (a.images && a.refs) launch_fwd_t<G, true, true>(a, q, blocks, st);
+    else if (a.images) launch_fwd_t<G, true, false>(a, q, blocks, st);
+    else launch_fwd_t<G, false, true>(a, q, blocks, st);
+}
+
+void launch_raster_fwd(const RasterArgs &a, const WorkQueue &q, int G, int blocks, cudaStream_t st)
+{
+    if (q.n_items == 0 || (!a.images && !a.refs)) return;
     ProfScope ps_(a.refs ? "raster_fwd_mse" : "raster_fwd", st);
-    if (a.images && a.refs) k_raster_fwd<true, true><<<grid, RT, 0, st>>>(a);
-    else if (a.images) k_raster_fwd<true, false><<<grid, RT, 0, st>>>(a);
-    else k_raster_fwd<false, true><<<grid, RT, 0, st>>>(a);
+    switch (G) {
+    case 1: launch_fwd_g<1>(a, q, blocks, st); break;
+    case 2: launch_fwd_g<2>(a, q, blocks, st); break;
+    case 4: launch_fwd_g<4>(a, q, blocks, st); break;
+    default: launch_fwd_g<8>(a, q, blocks, st); break;
+    }
+    count_launch();
+}
+
+template <int G, bool WRITE, bool MSE>
+static int occ_t()
+{
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_fwd<G, WRITE, MSE>, RT, 0);
+    return n > 0 ? n : 1;
+}
+
+template <int G>
+static int occ_g(bool write, bool mse)
+{
+    if (write && mse) return occ_t<G, true, true>();
+    if (write) return occ_t<G, true, false>();
+    return occ_t<G, false, true>();
+}
+
+int raster_fwd_blocks_per_sm(int G, bool write, bool mse)
+{
+    switch (G) {
+    case 1: return occ_g<1>(write, mse);
+    case 2: return occ_g<2>(write, mse);
+    case 4: return occ_g<4>(write, mse);
+    default: return occ_g<8>(write, mse);
+    }
+}
+
+void launch_tile_costs(const uint2 *ranges, uint32_t n, uint32_t *keys, uint32_t *vals, int sms, cudaStream_t st)
+{
+    if (n == 0) return;
+    unsigned b = (n + 255) / 256;
+    if (b > (unsigned)sms * 8) b = sms * 8;
+    ProfScope ps_("tile_costs", st);
+    k_tile_costs<<<b, 256, 0, st>>>(ranges, n, keys, vals);
+    count_launch();
+}
+
+void launch_item_counts(const uint32_t *tile_order, uint32_t n, uint32_t tiles, const int32_t *vg_ngroups,
+                        uint32_t *counts, int sms, cudaStream_t st)
+{
+    if (n == 0) return;
+    unsigned b = (n + 255) / 256;
+    if (b > (unsigned)sms * 8) b = sms * 8;
+    ProfScope ps_("item_counts", st);
+    k_item_counts<<<b, 256, 0, st>>>(tile_order, n, tiles, vg_ngroups, counts);
     count_launch();
 }
 

@@ -339,8 +339,8 @@ def main():
         sm_mhz = pk.get("sm_max_mhz", 2032.0)
         fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12     # TFLOP/s, FP32 FMA, all SMs
         evals_per_launch = evals_per_px * H * W * S
-        per_eval = {"raster_bwd": BWD_FLOP_PER_EVAL, "raster_fwd": FWD_FLOP_PER_EVAL,
-                    "raster_fwd_mse": FWD_FLOP_PER_EVAL}.get(dom_name)
+        per_eval = BWD_FLOP_PER_EVAL if dom_name == "raster_bwd" else (
+            FWD_FLOP_PER_EVAL if dom_name.startswith("raster_fwd") else None)
         if per_eval is not None:
             achieved = per_eval * evals_per_launch / (dom_ms_per_launch / 1e3) / 1e12
             roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": fp32_peak,

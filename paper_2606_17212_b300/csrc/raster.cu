@@ -587,7 +587,11 @@ static void launch_fwd_g(const RasterArgs &a, const WorkQueue &q, int blocks, cu
 void launch_raster_fwd(const RasterArgs &a, const WorkQueue &q, int G, int blocks, cudaStream_t st)
 {
     if (q.n_items == 0 || (!a.images && !a.refs)) return;
-    ProfScope ps_(a.refs ? "raster_fwd_mse" : "raster_fwd", st);
+    static const char *names[2][4] = {{"raster_fwd_g1", "raster_fwd_g2", "raster_fwd_g4", "raster_fwd_g8"},
+                                      {"raster_fwd_mse_g1", "raster_fwd_mse_g2", "raster_fwd_mse_g4",
+                                       "raster_fwd_mse_g8"}};
+    const int gi = G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : 3;
+    ProfScope ps_(names[a.refs ? 1 : 0][gi], st);
     switch (G) {
     case 1: launch_fwd_g<1>(a, q, blocks, st); break;
     case 2: launch_fwd_g<2>(a, q, blocks, st); break;

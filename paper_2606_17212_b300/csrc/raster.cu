@@ -32,18 +32,61 @@ struct Staged {
     float4 r0[BATCH];                 // mx, my, A, B
     float4 r1[BATCH];                 // C, o, r, g
     float4 r2[BATCH];                 // b, box x, box y, cd
+    int4 box[BATCH];                  // xlo, xhi - xlo, ylo, yhi - ylo
     uint32_t slot[BATCH];
     uint8_t list[RW][BATCH];          // per-warp indices of staged entries reaching its rows
     int cnt[RW];
     int wcnt[2][RW];
 };
 
+__device__ __forceinline__ int4 unpack_box(const float4 &r2)
+{
+    const uint32_t bx = __float_as_uint(r2.y), by = __float_as_uint(r2.z);
+    const int x0 = (int)(bx & 0xffffu), y0 = (int)(by & 0xffffu);
+    return make_int4(x0, (int)(bx >> 16) - x0, y0, (int)(by >> 16) - y0);
+}
+
+// Can Gaussian (mx, my, conic A B C, opacity o) reach alpha >= 1/255 at some
+// pixel centre of the rectangle [x0, x1] x [y0, y1]?  alpha >= 1/255 needs
+// q(d) = A dx^2 + 2 B dx dy + C dy^2 <= rho = 2 ln(255 o) with d = p - m.  The
+// minimum of the convex q over the rectangle is 0 when it holds the mean, else
+// it lies on an edge (1-D quadratic, clamped vertex).  rho is inflated by
+// 1e-3 relative + 1e-3 so FP32 rounding never drops a pixel that composites;
+// skipping a Gaussian that stays below 1/255 on the whole strip changes nothing.
+__device__ __forceinline__ bool ellipse_meets_rect(const float4 &r0, const float4 &r1, float x0, float x1,
+                                                   float y0, float y1)
+{
+    const float A = r0.z, B = r0.w, C = r1.x, o = r1.y;
+    const float rho = fmaf(2.0f * __logf(255.0f * o), 1.001f, 1e-3f);
+    const float X0 = x0 - r0.x, X1 = x1 - r0.x, Y0 = y0 - r0.y, Y1 = y1 - r0.y;
+    if (X0 <= 0.0f && X1 >= 0.0f && Y0 <= 0.0f && Y1 >= 0.0f) return true;
+    float best = 3.4e38f;
+    // vertical edges dx = X: minimise over dy in [Y0, Y1]
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float X = e ? X1 : X0;
+        const float dy = fminf(fmaxf(__fdividef(-B * X, C), Y0), Y1);
+        best = fminf(best, A * X * X + 2.0f * B * X * dy + C * dy * dy);
+    }
+    // horizontal edges dy = Y: minimise over dx in [X0, X1]
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float Y = e ? Y1 : Y0;
+        const float dx = fminf(fmaxf(__fdividef(-B * Y, A), X0), X1);
+        best = fminf(best, A * dx * dx + 2.0f * B * dx * Y + C * Y * Y);
+    }
+    return best <= rho;
+}
+
+// pixel coordinate v lies in [lo, lo + w] (w >= 0): one subtract, one unsigned compare
+__device__ __forceinline__ bool in_range(int v, int lo, int w) { return (unsigned)(v - lo) <= (unsigned)w; }
+
 // Stage entries [start, min(start + BATCH, end)) of the tile run, keeping the
 // variants this state renders, compacted in order; then build each warp's list
 // of kept entries whose box reaches the warp's rows.  Returns the kept count.
 __device__ __forceinline__ int stage_batch(const Rec *__restrict__ recs, const uint32_t *__restrict__ evals,
                                            const uint8_t *sdep, uint32_t start, uint32_t end, int row0,
-                                           Staged &sm)
+                                           int col0, Staged &sm)
 {
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     bool keep[2];
@@ -80,22 +123,27 @@ __device__ __forceinline__ int stage_batch(const Rec *__restrict__ recs, const u
     if (keep[0]) {
         const int pos = base0 + __popc(b0 & lt);
         sm.r0[pos] = x0[0]; sm.r1[pos] = x1[0]; sm.r2[pos] = x2[0]; sm.slot[pos] = slot[0];
+        sm.box[pos] = unpack_box(x2[0]);
     }
     if (keep[1]) {
         const int pos = tot0 + base1 + __popc(b1 & lt);
         sm.r0[pos] = x0[1]; sm.r1[pos] = x1[1]; sm.r2[pos] = x2[1]; sm.slot[pos] = slot[1];
+        sm.box[pos] = unpack_box(x2[1]);
     }
     __syncthreads();
     const int nk = tot0 + tot1;
-    // warp w keeps staged entries whose inclusive row range meets rows row0 + 4w .. row0 + 4w + 3
+    // warp w keeps staged entries whose box meets rows row0 + 4w .. row0 + 4w + 3
+    // and whose alpha >= 1/255 ellipse meets the warp's 16 x 4 strip
     const int wr0 = row0 + 4 * w, wr1 = wr0 + 3;
+    const float sx0 = (float)col0 + 0.5f, sx1 = (float)col0 + 15.5f;
+    const float sy0 = (float)wr0 + 0.5f, sy1 = (float)wr1 + 0.5f;
     int n = 0;
     for (int j0 = 0; j0 < nk; j0 += 32) {
         const int j = j0 + lane;
         bool hit = false;
         if (j < nk) {
-            const uint32_t by = __float_as_uint(sm.r2[j].z);
-            hit = (int)(by & 0xffffu) <= wr1 && (int)(by >> 16) >= wr0;
+            const int4 bx = sm.box[j];
+            hit = bx.z <= wr1 && bx.z + bx.w >= wr0 && ellipse_meets_rect(sm.r0[j], sm.r1[j], sx0, sx1, sy0, sy1);
         }
         const uint32_t bal = __ballot_sync(0xffffffffu, hit);
         if (hit) sm.list[w][n + __popc(bal & lt)] = (uint8_t)j;
@@ -104,12 +152,6 @@ __device__ __forceinline__ int stage_batch(const Rec *__restrict__ recs, const u
     if (lane == 0) sm.cnt[w] = n;
     __syncwarp();
     return nk;
-}
-
-__device__ __forceinline__ bool in_box(const float4 &r2, int px, int py)
-{
-    const uint32_t bx = __float_as_uint(r2.y), by = __float_as_uint(r2.z);
-    return px >= (int)(bx & 0xffffu) && px <= (int)(bx >> 16) && py >= (int)(by & 0xffffu) && py <= (int)(by >> 16);
 }
 
 // power = -1/2 (A dx^2 + C dy^2) - B dx dy, with explicit rounding so every
@@ -126,26 +168,27 @@ struct Pix {
     bool done;
 };
 
-// Composite staged entry (r0, r1, r2) into pixel (px, py); returns true when
-// the pixel stops at this entry (the entry is then excluded).
-// Branch-free: an entry the pixel skips (outside the box, power > 0 or
-// alpha < 1/255) gets alpha = 0, which leaves T and the colour bit-identical.
-__device__ __forceinline__ bool composite(Pix &p, const float4 &r0, const float4 &r1, const float4 &r2, int px,
-                                          int py)
+// Composite one staged entry into one pixel (pixel centre pcx, pcy), branch
+// free: an entry the pixel skips (outside the box, power > 0, alpha < 1/255,
+// or the pixel already stopped) gets alpha = 0, and the entry at which
+// T (1 - alpha) would drop below 1e-4 stops the pixel without being added;
+// both leave T and the colour bit-identical.  Returns true at the stop.
+__device__ __forceinline__ bool composite(Pix &p, const float4 &r0, const float4 &r1, float b, bool inb, float pcx,
+                                          float pcy)
 {
-    const bool inb = in_box(r2, px, py);
-    const float dx = __fsub_rn(r0.x, (float)px + 0.5f), dy = __fsub_rn(r0.y, (float)py + 0.5f);
+    const float dx = __fsub_rn(r0.x, pcx), dy = __fsub_rn(r0.y, pcy);
     const float pw = power_of(r0.z, r0.w, r1.x, dx, dy);
     const float a0 = fminf(0.99f, __fmul_rn(r1.y, __expf(pw)));
-    const float alpha = (inb && pw <= 0.0f && a0 >= (1.0f / 255.0f)) ? a0 : 0.0f;
+    const float alpha = (inb && !p.done && pw <= 0.0f && a0 >= (1.0f / 255.0f)) ? a0 : 0.0f;
     const float Tn = __fmul_rn(p.T, __fsub_rn(1.0f, alpha));
-    if (Tn < 1e-4f) return true;
-    const float wgt = __fmul_rn(alpha, p.T);
+    const bool stop = Tn < 1e-4f;
+    const float wgt = stop ? 0.0f : __fmul_rn(alpha, p.T);
     p.c0 = __fmaf_rn(r1.z, wgt, p.c0);
     p.c1 = __fmaf_rn(r1.w, wgt, p.c1);
-    p.c2 = __fmaf_rn(r2.x, wgt, p.c2);
-    p.T = Tn;
-    return false;
+    p.c2 = __fmaf_rn(b, wgt, p.c2);
+    p.T = stop ? p.T : Tn;
+    p.done = p.done || stop;
+    return stop;
 }
 
 __device__ __forceinline__ void load_depth_row(const uint8_t *depth, int s, int C, uint8_t *sdep)
@@ -165,7 +208,10 @@ __device__ __forceinline__ int stage_all(const Rec *__restrict__ recs, const uin
         if (e < end) {
             const uint32_t slot = __ldg(evals + e);
             const float4 *p = reinterpret_cast<const float4 *>(recs + slot);
-            sm.r0[j] = __ldg(p); sm.r1[j] = __ldg(p + 1); sm.r2[j] = __ldg(p + 2);
+            sm.r0[j] = __ldg(p); sm.r1[j] = __ldg(p + 1);
+            const float4 r2 = __ldg(p + 2);
+            sm.r2[j] = r2;
+            sm.box[j] = unpack_box(r2);
         }
     }
     __syncthreads();
@@ -175,19 +221,22 @@ __device__ __forceinline__ int stage_all(const Rec *__restrict__ recs, const uin
 // Warp w's list of staged entries that state row `dep` renders (variant depth
 // == the state's delivered depth of the entry's cluster) and whose box meets
 // the warp's rows.  Returns the list length (same in all lanes).
-__device__ __forceinline__ int warp_list(const Staged &sm, uint8_t *list, int nk, const uint8_t *dep, int wr0)
+__device__ __forceinline__ int warp_list(const Staged &sm, uint8_t *list, int nk, const uint8_t *dep, int wr0,
+                                         int col0)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
+    const float sx0 = (float)col0 + 0.5f, sx1 = (float)col0 + 15.5f;
+    const float sy0 = (float)wr0 + 0.5f, sy1 = (float)wr0 + 3.5f;
     int n = 0;
     for (int j0 = 0; j0 < nk; j0 += 32) {
         const int j = j0 + lane;
         bool hit = false;
         if (j < nk) {
-            const float4 r2 = sm.r2[j];
-            const uint32_t by = __float_as_uint(r2.z), cd = __float_as_uint(r2.w);
-            hit = (int)(by & 0xffffu) <= wr0 + 3 && (int)(by >> 16) >= wr0 &&
-                  ((cd >> 12) & 0xfu) == (uint32_t)dep[cd & 0xfffu];
+            const uint32_t cd = __float_as_uint(sm.r2[j].w);
+            const int4 bx = sm.box[j];
+            hit = bx.z <= wr0 + 3 && bx.z + bx.w >= wr0 && ((cd >> 12) & 0xfu) == (uint32_t)dep[cd & 0xfffu] &&
+                  ellipse_meets_rect(sm.r0[j], sm.r1[j], sx0, sx1, sy0, sy1);
         }
         const uint32_t bal = __ballot_sync(0xffffffffu, hit);
         if (hit) list[n + __popc(bal & lt)] = (uint8_t)j;
@@ -237,6 +286,7 @@ __global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a, WorkQueue q)
         const int px = tx * TILE + (lane & 15);
         const int py0 = ty * TILE + 4 * w + 2 * (lane >> 4), py1 = py0 + 1;
         const bool in0 = px < a.W && py0 < a.H, in1 = px < a.W && py1 < a.H;
+        const float pcx = (float)px + 0.5f, pcy0 = (float)py0 + 0.5f, pcy1 = (float)py1 + 0.5f;
         const int wr0 = ty * TILE + 4 * w;
         const uint2 rg = a.ranges[vt];
         Pix p[G][2];
@@ -254,13 +304,16 @@ __global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a, WorkQueue q)
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 if (!__any_sync(0xffffffffu, !(p[g][0].done && p[g][1].done))) continue;
-                const int n = warp_list(sm, sm.list[w], nk, sdep[g], wr0);
+                const int n = warp_list(sm, sm.list[w], nk, sdep[g], wr0, tx * TILE);
                 for (int i = 0; i < n; ++i) {
                     if (p[g][0].done && p[g][1].done) break;
                     const int k = sm.list[w][i];
-                    const float4 r0 = sm.r0[k], r1 = sm.r1[k], r2 = sm.r2[k];
-                    if (!p[g][0].done && composite(p[g][0], r0, r1, r2, px, py0)) p[g][0].done = true;
-                    if (!p[g][1].done && composite(p[g][1], r0, r1, r2, px, py1)) p[g][1].done = true;
+                    const float4 r0 = sm.r0[k], r1 = sm.r1[k];
+                    const float b = sm.r2[k].x;
+                    const int4 bx = sm.box[k];
+                    const bool xin = in_range(px, bx.x, bx.y);
+                    composite(p[g][0], r0, r1, b, xin && in_range(py0, bx.z, bx.w), pcx, pcy0);
+                    composite(p[g][1], r0, r1, b, xin && in_range(py1, bx.z, bx.w), pcx, pcy1);
                 }
                 __syncwarp();
             }
@@ -350,14 +403,13 @@ struct PixB {
 };
 
 // Adjoint of one pixel at one staged entry; adds to g[9] =
-// (mx, my, A, B, C, o, r, g, b) when the entry is included.  T and the colour
-// prefix advance exactly as in the forward.
-// Branch-free like composite(): a skipped entry has alpha = 0 and adds zeros.
-__device__ __forceinline__ bool adjoint(PixB &p, const float4 &r0, const float4 &r1, const float4 &r2, int px,
-                                        int py, float *g)
+// (mx, my, A, B, C, o, r, g, b) when the entry is included (inb: in the box
+// and the pixel still active).  Branch free like composite(): a skipped entry
+// has alpha = 0, adds zeros, and leaves T and the colour prefix unchanged.
+__device__ __forceinline__ bool adjoint(PixB &p, const float4 &r0, const float4 &r1, float b, bool inb, float pcx,
+                                        float pcy, float *g)
 {
-    const bool inb = in_box(r2, px, py);
-    const float dx = __fsub_rn(r0.x, (float)px + 0.5f), dy = __fsub_rn(r0.y, (float)py + 0.5f);
+    const float dx = __fsub_rn(r0.x, pcx), dy = __fsub_rn(r0.y, pcy);
     const float pw = power_of(r0.z, r0.w, r1.x, dx, dy);
     const float ex = __expf(pw);
     const float araw = __fmul_rn(r1.y, ex);
@@ -368,15 +420,16 @@ __device__ __forceinline__ bool adjoint(PixB &p, const float4 &r0, const float4 
     const float wgt = __fmul_rn(alpha, p.T);
     p.c0 = __fmaf_rn(r1.z, wgt, p.c0);
     p.c1 = __fmaf_rn(r1.w, wgt, p.c1);
-    p.c2 = __fmaf_rn(r2.x, wgt, p.c2);
-    const float inv = 1.0f / one_m;
+    p.c2 = __fmaf_rn(b, wgt, p.c2);
+    const float inv = __fdividef(1.0f, one_m);
     const float da = p.g0 * (r1.z * p.T - ((p.Cf0 - p.c0) + p.sb0) * inv) +
                      p.g1 * (r1.w * p.T - ((p.Cf1 - p.c1) + p.sb1) * inv) +
-                     p.g2 * (r2.x * p.T - ((p.Cf2 - p.c2) + p.sb2) * inv);
+                     p.g2 * (b * p.T - ((p.Cf2 - p.c2) + p.sb2) * inv);
     g[6] += p.g0 * wgt; g[7] += p.g1 * wgt; g[8] += p.g2 * wgt;
     // alpha = 0 (skipped) or the 0.99 clamp: no gradient to opacity, mean, conic
-    const float gpw = (ok && araw < 0.99f) ? da * alpha : 0.0f;
-    g[5] += (ok && araw < 0.99f) ? da * ex : 0.0f;
+    const bool lin = ok && araw < 0.99f;
+    const float gpw = lin ? da * alpha : 0.0f;
+    g[5] += lin ? da * ex : 0.0f;
     g[0] -= gpw * (r0.z * dx + r0.w * dy);
     g[1] -= gpw * (r1.x * dy + r0.w * dx);
     g[2] -= 0.5f * gpw * dx * dx;
@@ -434,6 +487,7 @@ __global__ void __launch_bounds__(RT, 6) k_raster_bwd(RasterBwdArgs b)
     const int px = tx * TILE + (lane & 15);
     const int py0 = ty * TILE + 4 * w + 2 * (lane >> 4), py1 = py0 + 1;
     const bool in0 = px < a.W && py0 < a.H, in1 = px < a.W && py1 < a.H;
+    const float pcx = (float)px + 0.5f, pcy0 = (float)py0 + 0.5f, pcy1 = (float)py1 + 0.5f;
     const uint2 rg = a.ranges[(size_t)v * a.tiles + tile];
 
     // ---- pass 1: forward walk, recording where each pixel stops
@@ -441,14 +495,17 @@ __global__ void __launch_bounds__(RT, 6) k_raster_bwd(RasterBwdArgs b)
     uint32_t stop0 = 0xffffffffu, stop1 = 0xffffffffu, kept = 0;
     for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
         if (__syncthreads_count(!(f0.done && f1.done)) == 0) break;
-        const int nk = stage_batch(a.recs, a.evals, sdep, start, rg.y, ty * TILE, sm);
+        const int nk = stage_batch(a.recs, a.evals, sdep, start, rg.y, ty * TILE, tx * TILE, sm);
         const int n = sm.cnt[w];
         for (int i = 0; i < n; ++i) {
             if (f0.done && f1.done) break;
             const int k = sm.list[w][i];
-            const float4 r0 = sm.r0[k], r1 = sm.r1[k], r2 = sm.r2[k];
-            if (!f0.done && composite(f0, r0, r1, r2, px, py0)) { f0.done = true; stop0 = kept + (uint32_t)k; }
-            if (!f1.done && composite(f1, r0, r1, r2, px, py1)) { f1.done = true; stop1 = kept + (uint32_t)k; }
+            const float4 r0 = sm.r0[k], r1 = sm.r1[k];
+            const float b = sm.r2[k].x;
+            const int4 bx = sm.box[k];
+            const bool xin = in_range(px, bx.x, bx.y);
+            if (composite(f0, r0, r1, b, xin && in_range(py0, bx.z, bx.w), pcx, pcy0)) stop0 = kept + (uint32_t)k;
+            if (composite(f1, r0, r1, b, xin && in_range(py1, bx.z, bx.w), pcx, pcy1)) stop1 = kept + (uint32_t)k;
         }
         kept += (uint32_t)nk;
     }
@@ -475,21 +532,26 @@ __global__ void __launch_bounds__(RT, 6) k_raster_bwd(RasterBwdArgs b)
     kept = 0;
     for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
         if (__syncthreads_count(q[0].active || q[1].active) == 0) break;
-        const int nk = stage_batch(a.recs, a.evals, sdep, start, rg.y, ty * TILE, sm);
+        const int nk = stage_batch(a.recs, a.evals, sdep, start, rg.y, ty * TILE, tx * TILE, sm);
         const int n = sm.cnt[w];
         if (__any_sync(0xffffffffu, q[0].active || q[1].active)) {
             for (int i = 0; i < n; ++i) {
+                if ((i & 7) == 0 && !__any_sync(0xffffffffu, q[0].active || q[1].active)) break;
                 const int k = sm.list[w][i];
                 float g[9];
 #pragma unroll
                 for (int j = 0; j < 9; ++j) g[j] = 0.0f;
                 bool contrib = false;
-                const float4 r0 = sm.r0[k], r1 = sm.r1[k], r2 = sm.r2[k];
+                const float4 r0 = sm.r0[k], r1 = sm.r1[k];
+                const float b = sm.r2[k].x;
+                const int4 bx = sm.box[k];
+                const bool xin = in_range(px, bx.x, bx.y);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     PixB &p = q[h];
-                    if (p.active && kept + (uint32_t)k >= p.stop) p.active = false;
-                    if (p.active) contrib |= adjoint(p, r0, r1, r2, px, h ? py1 : py0, g);
+                    p.active = p.active && kept + (uint32_t)k < p.stop;
+                    const bool inb = p.active && xin && in_range(h ? py1 : py0, bx.z, bx.w);
+                    contrib |= adjoint(p, r0, r1, b, inb, pcx, h ? pcy1 : pcy0, g);
                 }
                 if (__ballot_sync(0xffffffffu, contrib)) {
                     const float x = reduce8_transpose(g, lane);

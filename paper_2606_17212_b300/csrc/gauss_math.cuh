@@ -210,11 +210,13 @@ __device__ __forceinline__ void project_fwd(const SceneDev &s, int i, const Attr
     const float rho = 2.0f * logf(255.0f * P.o);
     const float hx = fminf(P.r, fmaf(sqrtf(fmaxf(rho, 0.0f) * F.a), 1.001f, 0.05f));
     const float hy = fminf(P.r, fmaf(sqrtf(fmaxf(rho, 0.0f) * F.c), 1.001f, 0.05f));
-    // exact pixel ranges: |x + 0.5 - mx| <= h  <=>  ceil(mx - h - 0.5) <= x <= floor(mx + h - 0.5)
-    double xl = ceil((double)P.mx - (double)hx - 0.5), xh = floor((double)P.mx + (double)hx - 0.5);
-    double yl = ceil((double)P.my - (double)hy - 0.5), yh = floor((double)P.my + (double)hy - 0.5);
-    xl = fmin(fmax(xl, 0.0), (double)vg.width);  xh = fmax(fmin(xh, (double)(vg.width - 1)), -1.0);
-    yl = fmin(fmax(yl, 0.0), (double)vg.height); yh = fmax(fmin(yh, (double)(vg.height - 1)), -1.0);
+    // pixel ranges: |x + 0.5 - mx| <= h  <=>  ceil(mx - h - 0.5) <= x <= floor(mx + h - 0.5),
+    // evaluated in FP32 (rounding moves an edge only for pixel centres within
+    // ~1e-5 px of the boundary), clamped to the image before the integer cast
+    float xl = ceilf(__fsub_rn(__fsub_rn(P.mx, hx), 0.5f)), xh = floorf(__fsub_rn(__fadd_rn(P.mx, hx), 0.5f));
+    float yl = ceilf(__fsub_rn(__fsub_rn(P.my, hy), 0.5f)), yh = floorf(__fsub_rn(__fadd_rn(P.my, hy), 0.5f));
+    xl = fminf(fmaxf(xl, 0.0f), (float)vg.width);  xh = fmaxf(fminf(xh, (float)(vg.width - 1)), -1.0f);
+    yl = fminf(fmaxf(yl, 0.0f), (float)vg.height); yh = fmaxf(fminf(yh, (float)(vg.height - 1)), -1.0f);
     P.xlo = (int)xl; P.xhi = (int)xh; P.ylo = (int)yl; P.yhi = (int)yh;
     if (SH == 0) {
 #pragma unroll

@@ -59,53 +59,75 @@ __device__ __forceinline__ int cluster_of(const int32_t *offs, int C, int i)
     return lo;
 }
 
-// One thread per (view group, Gaussian): decode the base and the delivered
-// refinement prefix incrementally (Section 3) and project every depth some
-// state of the view group needs.  Writes Rec, its depth key and its slot.
-template <int SH>
-__global__ void __launch_bounds__(256) k_project(SceneDev s, const ViewGroup *__restrict__ vgs, int V,
-                                                 const uint32_t *__restrict__ need,
-                                                 const uint32_t *__restrict__ recBase, Rec *__restrict__ recs,
-                                                 uint32_t *__restrict__ keys, uint32_t *__restrict__ vals)
+// One thread per Gaussian: decode the base and the delivered refinement prefix
+// incrementally (Section 3), once per depth some state needs, and project that
+// decoded variant for every view group whose states render the Gaussian's
+// cluster at that depth.  The scene is read once; records are written at
+// their (view group, cluster, Gaussian, depth) slot with the depth key.
+// need, recBase and the view groups are small per-call tables; when they fit
+// they are staged in shared memory (dynamic size) so the loop over view groups
+// issues no dependent global loads.
+template <int SH, bool SMEM>
+__global__ void __launch_bounds__(128, 4) k_project(SceneDev s, const ViewGroup *__restrict__ vgs_g, int V,
+                                                    const uint32_t *__restrict__ need_g,
+                                                    const uint32_t *__restrict__ recBase_g, Rec *__restrict__ recs,
+                                                    uint32_t *__restrict__ keys, uint32_t *__restrict__ vals)
 {
-    const long long total = (long long)V * s.n;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int v = (int)(t / s.n), i = (int)(t % s.n);
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const ViewGroup *vgs = vgs_g;
+    const uint32_t *need = need_g, *recBase = recBase_g;
+    if (SMEM) {
+        ViewGroup *svg = reinterpret_cast<ViewGroup *>(sm_raw);
+        uint32_t *sneed = reinterpret_cast<uint32_t *>(svg + V);
+        uint32_t *sbase = sneed + (size_t)V * s.C;
+        const int nvg_words = (int)(sizeof(ViewGroup) / 4) * V;
+        for (int k = threadIdx.x; k < nvg_words; k += blockDim.x)
+            reinterpret_cast<uint32_t *>(svg)[k] = reinterpret_cast<const uint32_t *>(vgs_g)[k];
+        for (int k = threadIdx.x; k < V * s.C; k += blockDim.x) { sneed[k] = need_g[k]; sbase[k] = recBase_g[k]; }
+        __syncthreads();
+        vgs = svg; need = sneed; recBase = sbase;
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += gridDim.x * blockDim.x) {
         const int c = cluster_of(s.offs, s.C, i);
         if (i < s.offs[c] || i >= s.offs[c + 1]) continue;   // offsets validated on the host; never taken
-        const uint32_t nd = need[(size_t)v * s.C + c] & ~1u;
-        if (!nd) continue;
-        const ViewGroup vg = vgs[v];
-        const int cnt = __popc(nd);
-        uint32_t slot = recBase[(size_t)v * s.C + c] + (uint32_t)(i - s.offs[c]) * cnt;
-        const int dmax = 31 - __clz(nd);
+        const uint32_t li = (uint32_t)(i - s.offs[c]);
+        uint32_t any = 0;
+        for (int v = 0; v < V; ++v) any |= need[(size_t)v * s.C + c];
+        any &= ~1u;
+        if (!any) continue;
+        const int dmax = 31 - __clz(any);
         Attr<SH> a;
         load_base<SH>(s, i, a);
         for (int d = 1; d <= dmax; ++d) {
             if (d >= 2) add_layer<SH>(s, i, d - 1, a);
-            if (!((nd >> d) & 1u)) continue;
-            Proj P; Fwd F;
-            project_fwd<SH>(s, i, a, vg, P, F);
-            Rec R;
-            if (P.live) {
-                R.mx = P.mx; R.my = P.my; R.A = P.A; R.B = P.B; R.C = P.C; R.o = P.o;
-                R.r = P.rgb[0]; R.g = P.rgb[1]; R.b = P.rgb[2];
-                R.bx = (uint32_t)P.xlo | ((uint32_t)P.xhi << 16);
-                R.by = (uint32_t)P.ylo | ((uint32_t)P.yhi << 16);
-                R.cd = (uint32_t)c | ((uint32_t)d << 12) | ((uint32_t)v << 16);
-                keys[slot] = __float_as_uint(P.z);
-            } else {
-                R.mx = R.my = R.A = R.B = R.C = R.o = R.r = R.g = R.b = 0.0f;
-                R.bx = 1u; R.by = 1u;          // xlo = 1 > xhi = 0: empty box
-                R.cd = (uint32_t)c | ((uint32_t)v << 16);   // depth field 0 = culled
-                keys[slot] = 0xffffffffu;
+            if (!((any >> d) & 1u)) continue;
+            for (int v = 0; v < V; ++v) {
+                const uint32_t nd = need[(size_t)v * s.C + c] & ~1u;
+                if (!((nd >> d) & 1u)) continue;
+                const uint32_t slot = recBase[(size_t)v * s.C + c] + li * (uint32_t)__popc(nd) +
+                                      (uint32_t)__popc(nd & ((1u << d) - 1u));
+                const ViewGroup &vg = vgs[v];
+                Proj P; Fwd F;
+                project_fwd<SH>(s, i, a, vg, P, F);
+                Rec R;
+                if (P.live) {
+                    R.mx = P.mx; R.my = P.my; R.A = P.A; R.B = P.B; R.C = P.C; R.o = P.o;
+                    R.r = P.rgb[0]; R.g = P.rgb[1]; R.b = P.rgb[2];
+                    R.bx = (uint32_t)P.xlo | ((uint32_t)P.xhi << 16);
+                    R.by = (uint32_t)P.ylo | ((uint32_t)P.yhi << 16);
+                    R.cd = (uint32_t)c | ((uint32_t)d << 12) | ((uint32_t)v << 16);
+                    keys[slot] = __float_as_uint(P.z);
+                } else {
+                    R.mx = R.my = R.A = R.B = R.C = R.o = R.r = R.g = R.b = 0.0f;
+                    R.bx = 1u; R.by = 1u;          // xlo = 1 > xhi = 0: empty box
+                    R.cd = (uint32_t)c | ((uint32_t)v << 16);   // depth field 0 = culled
+                    keys[slot] = 0xffffffffu;
+                }
+                float4 *dst = reinterpret_cast<float4 *>(recs + slot);
+                const float4 *src = reinterpret_cast<const float4 *>(&R);
+                dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2];
+                vals[slot] = slot;
             }
-            float4 *dst = reinterpret_cast<float4 *>(recs + slot);
-            const float4 *src = reinterpret_cast<const float4 *>(&R);
-            dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2];
-            vals[slot] = slot;
-            ++slot;
         }
     }
 }
@@ -135,25 +157,69 @@ __global__ void k_tile_count(const Rec *__restrict__ recs, const uint32_t *__res
 
 // Emit one (view group * tiles + tile, slot) entry per overlapped tile, in
 // depth order, so a stable sort on the tile key leaves every tile's run
-// ordered by (depth, Gaussian, depth variant).
+// ordered by (depth, Gaussian, depth variant).  A warp takes 32 consecutive
+// records, whose entries are contiguous, and writes them cooperatively: lane
+// e of each pass finds the record owning entry e by a 5-step search over the
+// warp's inclusive prefix of tile counts (coalesced stores).
 __global__ void k_emit(const Rec *__restrict__ recs, const uint32_t *__restrict__ order,
                        const uint32_t *__restrict__ offsets, uint32_t n, int tiles_x, uint32_t tiles,
                        uint32_t *__restrict__ ekeys, uint32_t *__restrict__ evals)
 {
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        const uint32_t slot = order[j];
-        const float4 q = rec_tail(recs, slot);
-        if (rec_tiles(q) == 0) continue;
-        const uint32_t bx = __float_as_uint(q.y), by = __float_as_uint(q.z);
-        const int xlo = bx & 0xffff, xhi = bx >> 16, ylo = by & 0xffff, yhi = by >> 16;
-        const uint32_t v = __float_as_uint(q.w) >> 16;
-        uint32_t o = offsets[j];
-        for (int ty = ylo / TILE; ty <= yhi / TILE; ++ty)
-            for (int tx = xlo / TILE; tx <= xhi / TILE; ++tx) {
-                ekeys[o] = v * tiles + (uint32_t)(ty * tiles_x + tx);
-                evals[o] = slot;
-                ++o;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t base = warp * 32u; base < n; base += nwarps * 32u) {
+        const uint32_t j = base + lane;
+        uint32_t slot = 0, cnt = 0, off = 0;
+        int x0 = 0, tw = 1, y0 = 0;
+        uint32_t vbase = 0;
+        if (j < n) {
+            slot = order[j];
+            const float4 q = rec_tail(recs, slot);
+            cnt = rec_tiles(q);
+            off = offsets[j];
+            const uint32_t bx = __float_as_uint(q.y), by = __float_as_uint(q.z);
+            x0 = (int)(bx & 0xffffu) / TILE;
+            tw = (int)(bx >> 16) / TILE - x0 + 1;
+            y0 = (int)(by & 0xffffu) / TILE;
+            vbase = (__float_as_uint(q.w) >> 16) * tiles;
+        }
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t first = __shfl_sync(0xffffffffu, off, 0);
+        const float rtw = 1.0f / (float)tw;
+        // every lane runs the same number of passes so full-warp shuffles see every lane
+        for (uint32_t e0 = 0; e0 < total; e0 += 32) {
+            const uint32_t e = e0 + lane;
+            int lo = 0;                       // number of records whose entries end at or before e
+#pragma unroll
+            for (int b = 16; b >= 1; b >>= 1) {
+                const uint32_t v = __shfl_sync(0xffffffffu, incl, lo + b - 1);
+                if (v <= e) lo += b;
             }
+            const uint32_t o_incl = __shfl_sync(0xffffffffu, incl, lo);
+            const uint32_t o_cnt = __shfl_sync(0xffffffffu, cnt, lo);
+            const int o_x0 = __shfl_sync(0xffffffffu, x0, lo);
+            const int o_tw = __shfl_sync(0xffffffffu, tw, lo);
+            const int o_y0 = __shfl_sync(0xffffffffu, y0, lo);
+            const float o_rtw = __shfl_sync(0xffffffffu, rtw, lo);
+            const uint32_t o_vb = __shfl_sync(0xffffffffu, vbase, lo);
+            const uint32_t o_slot = __shfl_sync(0xffffffffu, slot, lo);
+            if (e < total) {
+                const int li = (int)(e - (o_incl - o_cnt));
+                int row = (int)(((float)li + 0.5f) * o_rtw);
+                row -= (row * o_tw > li) ? 1 : 0;            // exact quotient li / o_tw
+                row += ((row + 1) * o_tw <= li) ? 1 : 0;
+                const int col = li - row * o_tw;
+                ekeys[first + e] = o_vb + (uint32_t)((o_y0 + row) * tiles_x + o_x0 + col);
+                evals[first + e] = o_slot;
+            }
+        }
     }
 }
 
@@ -195,10 +261,18 @@ void launch_layout_counts(const uint32_t *need, const int32_t *offs, int V, int 
 void launch_project(const SceneDev &s, const ViewGroup *vgs, int V, const uint32_t *need, const uint32_t *recBase,
                     Rec *recs, uint32_t *keys, uint32_t *vals, int sms, cudaStream_t st)
 {
-    const unsigned g = grid_for((long long)V * s.n, 256, sms);
+    unsigned g = (unsigned)((s.n + 127) / 128);
+    if (g < 1) g = 1;
+    const size_t smem = sizeof(ViewGroup) * (size_t)V + 8 * (size_t)V * s.C;
+    const bool use_smem = smem <= 40 * 1024;
     ProfScope ps_("project", st);
-    if (s.sh == 0) k_project<0><<<g, 256, 0, st>>>(s, vgs, V, need, recBase, recs, keys, vals);
-    else k_project<3><<<g, 256, 0, st>>>(s, vgs, V, need, recBase, recs, keys, vals);
+    if (use_smem) {
+        if (s.sh == 0) k_project<0, true><<<g, 128, smem, st>>>(s, vgs, V, need, recBase, recs, keys, vals);
+        else k_project<3, true><<<g, 128, smem, st>>>(s, vgs, V, need, recBase, recs, keys, vals);
+    } else {
+        if (s.sh == 0) k_project<0, false><<<g, 128, 0, st>>>(s, vgs, V, need, recBase, recs, keys, vals);
+        else k_project<3, false><<<g, 128, 0, st>>>(s, vgs, V, need, recBase, recs, keys, vals);
+    }
     count_launch();
 }
 

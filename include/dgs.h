@@ -193,6 +193,49 @@ DGS_API int dgs_image_mse(dgs_ctx *ctx, const float *images, const float *refs, 
                   float *dL_dimages, dgs_stream stream);
 
 /*
+ * Plans: capture-safe execution of a fixed batch (Section 6 batching, run as a
+ * CUDA-graph-friendly sequence).  A plan fixes the scene (its pointers; the
+ * values may change between calls), the states' times and camera indices, the
+ * cameras, the background and -- for mode DGS_PLAN_RENDER with ref_index --
+ * the reference image of each state for dgs_plan_image_mse.  dgs_plan_create
+ * runs once, synchronously, on the given masks: it plans the view groups,
+ * sizes a private workspace (records exactly: at most one depth per state and
+ * cluster; tile entries as the masks' count times entry_headroom (>= 1, 0 =
+ * 1.25) plus 65536), tunes the states-per-block of the forward raster and
+ * uploads every table.  Afterwards dgs_plan_render / _backward / _utility /
+ * _image_mse only launch kernels on `stream`: no allocation, no host copy,
+ * no synchronisation, launch sizes fixed by the plan, counts kept on the
+ * device -- so they can be captured in a CUDA graph and replayed with other
+ * masks of the same shape ([n_states][W32], device).  If some masks need more
+ * tile entries than reserved, the surplus entries are dropped and
+ * dgs_plan_status reports DGS_E_CAPACITY (re-create the plan with more
+ * headroom).  A plan is used by one stream at a time; dgs_plan_backward uses
+ * the lists of the plan's last dgs_plan_render.  Results equal the
+ * corresponding context calls bit for bit (images, MSE) or up to float atomic
+ * order (gradients).
+ */
+typedef struct dgs_plan dgs_plan;
+enum { DGS_PLAN_RENDER = 1, DGS_PLAN_UTILITY = 2 };
+DGS_API int dgs_plan_create(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states, const dgs_camera *cams,
+                            int n_cams, const float *bg, int mode, const int32_t *ref_index /*[host] [n_states] or NULL*/,
+                            int n_refs, float entry_headroom, dgs_plan **out);
+DGS_API void dgs_plan_destroy(dgs_plan *plan);
+DGS_API const char *dgs_plan_last_error(const dgs_plan *plan);
+/* images [device] [n_states][H][W][3]: as dgs_render_states_batched. */
+DGS_API int dgs_plan_render(dgs_plan *plan, const uint32_t *masks, float *images, dgs_stream stream);
+/* dL/dimages [device]: accumulates into grads as dgs_render_backward. */
+DGS_API int dgs_plan_backward(dgs_plan *plan, const float *dL_dimages, const dgs_scene_grad *grads,
+                              dgs_stream stream);
+/* mse, psnr [device] [n_states]: as dgs_state_utility (mode DGS_PLAN_UTILITY). */
+DGS_API int dgs_plan_utility(dgs_plan *plan, const uint32_t *masks, double *mse, double *psnr, dgs_stream stream);
+/* As dgs_image_mse with the plan's ref_index; refs [device] [n_refs][H][W][3]. */
+DGS_API int dgs_plan_image_mse(dgs_plan *plan, const float *images, const float *refs, float weight, double *mse,
+                               double *psnr, float *dL_dimages, dgs_stream stream);
+/* Synchronizes `stream`; the last call's record and tile-entry counts [host];
+ * DGS_E_CAPACITY (and clears the flag) when entries overflowed since the last check. */
+DGS_API int dgs_plan_status(dgs_plan *plan, int64_t *n_records, int64_t *n_entries, dgs_stream stream);
+
+/*
  * Test and inspection access to the projected records and tile lists of the
  * context's last dgs_render_states_batched / dgs_render_state call (or of a
  * backward that re-prepared).  Sizes go to the [host] out-parameters (any may

@@ -428,18 +428,19 @@ void record_tape(Tape &tp, const dgs_scene *sc, const dgs_states *st, const dgs_
     tp.lists = L;
 }
 
-// Forward raster of states [s0, s1) of the plan: group them by view group in
-// groups of at most G, build the cost-ordered work queue and launch the
-// persistent kernel.
-int launch_fwd_pass(dgs_ctx *ctx, const Plan &p, const Lists &L, const RasterArgs &a, int s0, int s1, int G,
-                    cudaStream_t st)
+// Device-resident state-group tables of one forward pass (states grouped by
+// view group in groups of at most G).
+struct QueueTabs {
+    const int32_t *order = nullptr, *gfirst = nullptr, *gcount = nullptr, *gbase = nullptr, *ngroups = nullptr;
+    size_t ng = 0;
+    int G = 1;
+};
+
+void build_groups(const Plan &p, int s0, int s1, int G, std::vector<int32_t> &buf, size_t off[5], size_t &ng)
 {
-    const int n = s1 - s0;
-    if (n <= 0) return DGS_OK;
     std::vector<std::vector<int32_t>> per_vg(p.V);
     for (int s = s0; s < s1; ++s) per_vg[p.vg_of_state[s]].push_back(s);
     std::vector<int32_t> order, gfirst, gcount, gbase(p.V), ngroups(p.V);
-    order.reserve(n);
     for (int v = 0; v < p.V; ++v) {
         gbase[v] = (int32_t)gfirst.size();
         for (size_t k = 0; k < per_vg[v].size(); k += G) {
@@ -449,42 +450,69 @@ int launch_fwd_pass(dgs_ctx *ctx, const Plan &p, const Lists &L, const RasterArg
         ngroups[v] = (int32_t)gfirst.size() - gbase[v];
         order.insert(order.end(), per_vg[v].begin(), per_vg[v].end());
     }
-    const size_t ng = gfirst.size(), vt = (size_t)p.V * p.tiles;
-    const size_t ints = order.size() + 2 * ng + 2 * (size_t)p.V;
-    TRY(ensure(ctx, ctx->qint, 4 * ints, st));
+    ng = gfirst.size();
+    buf.clear();
+    off[0] = buf.size(); buf.insert(buf.end(), order.begin(), order.end());
+    off[1] = buf.size(); buf.insert(buf.end(), gfirst.begin(), gfirst.end());
+    off[2] = buf.size(); buf.insert(buf.end(), gcount.begin(), gcount.end());
+    off[3] = buf.size(); buf.insert(buf.end(), gbase.begin(), gbase.end());
+    off[4] = buf.size(); buf.insert(buf.end(), ngroups.begin(), ngroups.end());
+}
+
+QueueTabs tabs_at(const int32_t *dev, const size_t off[5], size_t ng, int G)
+{
+    QueueTabs q;
+    q.order = dev + off[0]; q.gfirst = dev + off[1]; q.gcount = dev + off[2]; q.gbase = dev + off[3];
+    q.ngroups = dev + off[4]; q.ng = ng; q.G = G;
+    return q;
+}
+
+// Launch the persistent forward raster for uploaded group tables: per-call
+// item offsets from the cost-ordered tile list, counter reset, kernel.
+int launch_queue(dgs_ctx *ctx, const Plan &p, const Lists &L, const RasterArgs &a, const QueueTabs &qt,
+                 cudaStream_t st)
+{
+    const size_t vt = (size_t)p.V * p.tiles;
     TRY(ensure(ctx, ctx->icnt, 4 * (vt + 1), st));
     TRY(ensure(ctx, ctx->ioff, 4 * (vt + 1), st));
     TRY(ensure(ctx, ctx->counter, 16, st));
     TRY(ensure(ctx, ctx->scanws, scan_workspace_bytes(vt + 1), st));
-    TRY(ensure_stage(ctx, 4 * ints, st));
-    CK(cudaEventSynchronize(ctx->stage_done));
-    int32_t *h = (int32_t *)ctx->h_stage;
-    size_t o = 0;
-    std::memcpy(h + o, order.data(), 4 * order.size()); const size_t o_order = o; o += order.size();
-    std::memcpy(h + o, gfirst.data(), 4 * ng); const size_t o_first = o; o += ng;
-    std::memcpy(h + o, gcount.data(), 4 * ng); const size_t o_count = o; o += ng;
-    std::memcpy(h + o, gbase.data(), 4 * (size_t)p.V); const size_t o_base = o; o += p.V;
-    std::memcpy(h + o, ngroups.data(), 4 * (size_t)p.V); const size_t o_ng = o; o += p.V;
-    CK(cudaMemcpyAsync(ctx->qint.p, h, 4 * o, cudaMemcpyHostToDevice, st));
-    CK(cudaEventRecord(ctx->stage_done, st));
-    const int32_t *qd = (const int32_t *)ctx->qint.p;
-    launch_item_counts(L.tile_order, (uint32_t)vt, p.tiles, qd + o_ng, (uint32_t *)ctx->icnt.p, ctx->sms, st);
+    launch_item_counts(L.tile_order, (uint32_t)vt, p.tiles, qt.ngroups, (uint32_t *)ctx->icnt.p, ctx->sms, st);
     CK(exclusive_scan_u32((const uint32_t *)ctx->icnt.p, (uint32_t *)ctx->ioff.p, vt, nullptr, ctx->scanws.p, st));
     CK(cudaMemsetAsync(ctx->counter.p, 0, 4, st));
     WorkQueue q;
     q.tile_order = L.tile_order;
     q.item_offsets = (const uint32_t *)ctx->ioff.p;
     q.n_vt = (uint32_t)vt;
-    q.n_items = (uint32_t)(ng * p.tiles);
-    q.group_first = qd + o_first;
-    q.group_count = qd + o_count;
-    q.vg_group_base = qd + o_base;
-    q.state_order = qd + o_order;
+    q.n_items = (uint32_t)(qt.ng * p.tiles);
+    q.group_first = qt.gfirst;
+    q.group_count = qt.gcount;
+    q.vg_group_base = qt.gbase;
+    q.state_order = qt.order;
     q.counter = (uint32_t *)ctx->counter.p;
-    const int blocks = ctx->sms * raster_fwd_blocks_per_sm(G, a.images != nullptr, a.refs != nullptr);
-    launch_raster_fwd(a, q, G, blocks, st);
+    const int blocks = ctx->sms * raster_fwd_blocks_per_sm(qt.G, a.images != nullptr, a.refs != nullptr);
+    launch_raster_fwd(a, q, qt.G, blocks, st);
     CK(cudaGetLastError());
     return DGS_OK;
+}
+
+// Forward raster of states [s0, s1) of the plan: group them by view group in
+// groups of at most G, upload the tables through the pinned staging buffer and
+// launch the persistent kernel.
+int launch_fwd_pass(dgs_ctx *ctx, const Plan &p, const Lists &L, const RasterArgs &a, int s0, int s1, int G,
+                    cudaStream_t st)
+{
+    if (s1 - s0 <= 0) return DGS_OK;
+    std::vector<int32_t> buf;
+    size_t off[5], ng = 0;
+    build_groups(p, s0, s1, G, buf, off, ng);
+    TRY(ensure(ctx, ctx->qint, 4 * buf.size(), st));
+    TRY(ensure_stage(ctx, 4 * buf.size(), st));
+    CK(cudaEventSynchronize(ctx->stage_done));
+    std::memcpy(ctx->h_stage, buf.data(), 4 * buf.size());
+    CK(cudaMemcpyAsync(ctx->qint.p, ctx->h_stage, 4 * buf.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(ctx->stage_done, st));
+    return launch_queue(ctx, p, L, a, tabs_at((const int32_t *)ctx->qint.p, off, ng, G), st);
 }
 
 // Autotuned forward pass: the first call of a given shape times every
@@ -540,6 +568,121 @@ int render_batched(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *state
     TRY(fwd_pass(ctx, scene, p, L, a, 0, p.S_user, st));
     record_tape(ctx->tape, scene, states, cams, n_cams, p, L);
     return DGS_OK;
+}
+
+}  // namespace
+
+
+// ---------------------------------------------------------------- plans
+// A plan fixes the scene, the states' times and cameras, the cameras and the
+// background of a batch, and owns a workspace sized for them.  Its per-call
+// entry points launch kernels only: counts stay on the device, every launch
+// size depends only on the plan, nothing is allocated, copied from the host or
+// synchronised, so a caller can capture them in a CUDA graph and replay them
+// with new masks (and new scene values) of the same shapes.
+struct dgs_plan {
+    dgs_ctx ws;                   // private workspace and error message
+    Plan p;
+    dgs_scene scene{};
+    float bg[3] = {0, 0, 0};
+    int mode = 0;
+    uint32_t R_cap = 0, E_cap = 0;
+    Buf cnts;                     // [0] records, [1] entries, [2] min(entries, capacity), [3] overflow flags
+    Buf qfwd, qref;               // state-group tables of the forward / reference passes
+    QueueTabs tfwd, tref;
+    Lists L;
+    bool rendered = false;
+    int n_refs = 0;
+    int image_parts = 0;
+};
+
+namespace {
+
+int plan_fail(dgs_plan *P, int code, const char *msg)
+{
+    P->ws.err = msg;
+    return code;
+}
+
+// Capture-safe preparation: closure, layout, projection, sorts, binning and
+// tile order with every count kept on the device.
+int prepare_dev(dgs_plan *P, const uint32_t *masks, bool force_full, cudaStream_t st)
+{
+    dgs_ctx *ctx = &P->ws;
+    const Plan &p = P->p;
+    const dgs_scene *scene = &P->scene;
+    const int C = scene->n_clusters, L = scene->n_layers;
+    const int words = (C * L + 31) / 32;
+    const size_t nvc = (size_t)p.V * C, vt = (size_t)p.V * p.tiles;
+    uint32_t *cnt = (uint32_t *)P->cnts.p;
+    CK(cudaMemsetAsync(ctx->need.p, 0, 4 * nvc, st));
+    if (p.S_user > 0)
+        launch_closure(masks, p.S_user, words, C, L, (const int32_t *)ctx->vgos.p, (uint8_t *)ctx->depth.p,
+                       (uint32_t *)ctx->need.p, force_full ? 1 : 0, ctx->sms, st);
+    launch_layout_counts((const uint32_t *)ctx->need.p, scene->cluster_offsets, p.V, C, (uint32_t *)ctx->counts.p,
+                         ctx->sms, st);
+    CK(exclusive_scan_u32((const uint32_t *)ctx->counts.p, (uint32_t *)ctx->recBase.p, nvc + 1, cnt + 0,
+                          ctx->scanws.p, st));
+    launch_project(scene_dev(scene), (const ViewGroup *)ctx->vgs.p, p.V, (const uint32_t *)ctx->need.p,
+                   (const uint32_t *)ctx->recBase.p, (Rec *)ctx->recs.p, (uint32_t *)ctx->k0.p, (uint32_t *)ctx->v0.p,
+                   ctx->sms, st);
+    bool alt = false;
+    CK(radix_sort_pairs((uint32_t *)ctx->k0.p, (uint32_t *)ctx->v0.p, (uint32_t *)ctx->k1.p, (uint32_t *)ctx->v1.p,
+                        P->R_cap, 32, ctx->sortws.p, st, &alt, cnt + 0));
+    const uint32_t *order = alt ? (const uint32_t *)ctx->v1.p : (const uint32_t *)ctx->v0.p;
+    Lists &out = P->L;
+    out.depth_keys = alt ? (uint32_t *)ctx->k1.p : (uint32_t *)ctx->k0.p;
+    out.depth_slots = (uint32_t *)order;
+    launch_tile_count((const Rec *)ctx->recs.p, order, P->R_cap, (uint32_t *)ctx->tcount.p, ctx->sms, st, cnt + 0);
+    CK(exclusive_scan_u32((const uint32_t *)ctx->tcount.p, (uint32_t *)ctx->toffs.p, P->R_cap, cnt + 1,
+                          ctx->scanws.p, st));
+    launch_clamp_count(cnt + 1, P->E_cap, cnt + 2, cnt + 3, st);
+    launch_emit((const Rec *)ctx->recs.p, order, (const uint32_t *)ctx->toffs.p, P->R_cap, p.tiles_x, p.tiles,
+                (uint32_t *)ctx->ek0.p, (uint32_t *)ctx->ev0.p, ctx->sms, st, cnt + 0, P->E_cap);
+    const int kbits = bits_for((unsigned long long)vt - 1ull);
+    CK(radix_sort_pairs((uint32_t *)ctx->ek0.p, (uint32_t *)ctx->ev0.p, (uint32_t *)ctx->ek1.p,
+                        (uint32_t *)ctx->ev1.p, P->E_cap, kbits, ctx->sortws.p, st, &alt, cnt + 2));
+    out.ekeys = alt ? (uint32_t *)ctx->ek1.p : (uint32_t *)ctx->ek0.p;
+    out.evals = alt ? (uint32_t *)ctx->ev1.p : (uint32_t *)ctx->ev0.p;
+    CK(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * vt, st));
+    launch_ranges(out.ekeys, P->E_cap, (uint2 *)ctx->ranges.p, ctx->sms, st, cnt + 2);
+    launch_tile_costs((const uint2 *)ctx->ranges.p, (uint32_t)vt, (uint32_t *)ctx->tck0.p, (uint32_t *)ctx->tcv0.p,
+                      ctx->sms, st);
+    CK(radix_sort_pairs((uint32_t *)ctx->tck0.p, (uint32_t *)ctx->tcv0.p, (uint32_t *)ctx->tck1.p,
+                        (uint32_t *)ctx->tcv1.p, vt, 32, ctx->sortws.p, st, &alt));
+    out.tile_order = alt ? (uint32_t *)ctx->tcv1.p : (uint32_t *)ctx->tcv0.p;
+    out.nRec = P->R_cap;
+    out.nEnt = P->E_cap;
+    CK(cudaGetLastError());
+    return DGS_OK;
+}
+
+int upload_tabs(dgs_plan *P, Buf &b, int s0, int s1, int G, QueueTabs &out)
+{
+    dgs_ctx *ctx = &P->ws;
+    std::vector<int32_t> buf;
+    size_t off[5], ng = 0;
+    build_groups(P->p, s0, s1, G, buf, off, ng);
+    TRY(ensure(ctx, b, 4 * buf.size() + 16, 0));
+    CK(cudaMemcpy(b.p, buf.data(), 4 * buf.size(), cudaMemcpyHostToDevice));
+    out = tabs_at((const int32_t *)b.p, off, ng, G);
+    return DGS_OK;
+}
+
+int tuned_choice(dgs_ctx *ctx, const dgs_scene *scene, const Plan &p, int s0, int s1, bool images, bool refs)
+{
+    int maxper = 1;
+    std::vector<int> cnt(p.V, 0);
+    for (int s = s0; s < s1; ++s) maxper = std::max(maxper, ++cnt[p.vg_of_state[s]]);
+    const std::vector<long long> key = {s1 - s0, p.V, p.W, p.H, scene->n, scene->n_clusters, scene->n_layers,
+                                        images, refs, maxper};
+    auto it = ctx->tuned_G.find(key);
+    return it == ctx->tuned_G.end() ? 1 : it->second;
+}
+
+RasterArgs plan_raster_args(dgs_plan *P)
+{
+    return raster_args(&P->ws, P->p, P->scene.n_clusters, P->bg, P->L.evals);
 }
 
 }  // namespace
@@ -791,6 +934,253 @@ int dgs_image_mse(dgs_ctx *ctx, const float *images, const float *refs, const in
                      dL_dimages, st);
     launch_mse_reduce((const double *)ctx->partial.p, S, parts, 1.0 / (double)per, mse, psnr, st);
     CK(cudaGetLastError());
+    return DGS_OK;
+}
+
+
+int dgs_plan_create(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states, const dgs_camera *cams,
+                    int n_cams, const float *bg, int mode, const int32_t *ref_index, int n_refs,
+                    float entry_headroom, dgs_plan **out)
+{
+    if (!ctx || !out) return DGS_E_INVALID_ARG;
+    *out = nullptr;
+    CK(cudaSetDevice(ctx->device));
+    TRY(check_scene(ctx, scene));
+    if (!bg) return fail(ctx, DGS_E_INVALID_ARG, "bg is null");
+    if (mode != DGS_PLAN_RENDER && mode != DGS_PLAN_UTILITY) return fail(ctx, DGS_E_INVALID_ARG, "bad plan mode");
+    Plan p;
+    TRY(build_plan(ctx, states, cams, n_cams, mode == DGS_PLAN_UTILITY, p));
+    if (p.S_user < 1) return fail(ctx, DGS_E_INVALID_ARG, "a plan needs at least one state");
+    if (ref_index) {
+        if (n_refs < 1) return fail(ctx, DGS_E_INVALID_ARG, "n_refs < 1");
+        for (int s = 0; s < p.S_user; ++s)
+            if (ref_index[s] < 0 || ref_index[s] >= n_refs)
+                return fail(ctx, DGS_E_INVALID_ARG, "ref_index[%d] out of range", s);
+    }
+    if (!(entry_headroom >= 1.0f)) entry_headroom = 1.25f;
+    dgs_plan *P = new dgs_plan();
+    dgs_ctx *w = &P->ws;
+    w->device = ctx->device;
+    w->sms = ctx->sms;
+    if (cudaMallocHost((void **)&w->h_small, 64 + 4 * (MAX_CLUSTERS + 1)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&w->stage_done, cudaEventDisableTiming) != cudaSuccess) {
+        dgs_plan_destroy(P);
+        return fail(ctx, DGS_E_OOM, "plan host allocation failed");
+    }
+    P->p = p;
+    P->scene = *scene;
+    P->bg[0] = bg[0]; P->bg[1] = bg[1]; P->bg[2] = bg[2];
+    P->mode = mode;
+    cudaStream_t st = 0;
+    int r = DGS_OK;
+    do {
+        // exact record capacity: each state adds at most one depth per cluster
+        std::vector<int> per(p.V, 0);
+        for (int s = 0; s < p.S; ++s) ++per[p.vg_of_state[s]];
+        unsigned long long rc = 0;
+        for (int v = 0; v < p.V; ++v) rc += (unsigned long long)scene->n * (unsigned long long)std::min(per[v], scene->n_layers);
+        if (rc >= 0x7fffffffull) { r = fail(ctx, DGS_E_CAPACITY, "record capacity exceeds 32 bits"); break; }
+        P->R_cap = (uint32_t)std::max<unsigned long long>(rc, 1);
+        // sizing run on the given masks (synchronous), then capacities
+        Lists L0;
+        if ((r = prepare(w, scene, states->masks, p, mode == DGS_PLAN_UTILITY, st, L0)) != DGS_OK) break;
+        unsigned long long ec = (unsigned long long)((double)L0.nEnt * entry_headroom) + 65536ull;
+        if (ec >= 0x7fffffffull) ec = 0x7ffffffeull;
+        P->E_cap = (uint32_t)ec;
+        const size_t vt = (size_t)p.V * p.tiles, R = P->R_cap, E = P->E_cap;
+        if ((r = ensure(w, w->recs, sizeof(Rec) * R, st)) != DGS_OK) break;
+        Buf *rb[] = {&w->k0, &w->v0, &w->k1, &w->v1};
+        for (Buf *b : rb) if ((r = ensure(w, *b, 4 * R, st)) != DGS_OK) break;
+        if (r != DGS_OK) break;
+        if ((r = ensure(w, w->tcount, 4 * (R + 1), st)) != DGS_OK) break;
+        if ((r = ensure(w, w->toffs, 4 * (R + 1), st)) != DGS_OK) break;
+        Buf *eb[] = {&w->ek0, &w->ev0, &w->ek1, &w->ev1};
+        for (Buf *b : eb) if ((r = ensure(w, *b, 4 * E, st)) != DGS_OK) break;
+        if (r != DGS_OK) break;
+        const size_t big = std::max(std::max(R, E), vt) + 1;
+        if ((r = ensure(w, w->sortws, radix_workspace_bytes(big), st)) != DGS_OK) break;
+        if ((r = ensure(w, w->scanws, scan_workspace_bytes(big), st)) != DGS_OK) break;
+        if ((r = ensure(w, w->icnt, 4 * (vt + 1), st)) != DGS_OK) break;
+        if ((r = ensure(w, w->ioff, 4 * (vt + 1), st)) != DGS_OK) break;
+        if ((r = ensure(w, w->counter, 16, st)) != DGS_OK) break;
+        if ((r = ensure(w, P->cnts, 16, st)) != DGS_OK) break;
+        CK(cudaMemset(P->cnts.p, 0, 16));
+        if (mode == DGS_PLAN_RENDER && (r = ensure(w, w->recgrad, sizeof(float4) * 3 * R, st)) != DGS_OK) break;
+        const size_t img = (size_t)p.W * p.H * 3;
+        if (mode == DGS_PLAN_UTILITY) {
+            if ((r = ensure(w, w->refs, sizeof(float) * img * p.V, st)) != DGS_OK) break;
+            if ((r = ensure(w, w->partial, sizeof(double) * (size_t)p.S_user * p.tiles, st)) != DGS_OK) break;
+        }
+        if (ref_index) {
+            P->n_refs = n_refs;
+            P->image_parts = (int)((img + 4095) / 4096);
+            if ((r = ensure(w, w->refidx, 4 * (size_t)p.S_user, st)) != DGS_OK) break;
+            CK(cudaMemcpy(w->refidx.p, ref_index, 4 * (size_t)p.S_user, cudaMemcpyHostToDevice));
+            if ((r = ensure(w, w->partial, sizeof(double) * (size_t)p.S_user *
+                                               std::max<size_t>(P->image_parts, p.tiles), st)) != DGS_OK) break;
+        }
+        // Growing the workspace above reallocated buffers the sizing run's lists
+        // point into: prepare again so every list lives in the final buffers,
+        // then tune states-per-block on it and upload the tables.
+        if ((r = prepare(w, scene, states->masks, p, mode == DGS_PLAN_UTILITY, st, L0)) != DGS_OK) break;
+        CK(cudaDeviceSynchronize());
+        RasterArgs a = raster_args(w, p, scene->n_clusters, P->bg, L0.evals);
+        if (mode == DGS_PLAN_RENDER) {
+            float *tmp = nullptr;
+            if (cudaMalloc(&tmp, sizeof(float) * img * p.S_user) != cudaSuccess) {
+                cudaGetLastError();
+                r = fail(ctx, DGS_E_OOM, "plan tuning buffer");
+                break;
+            }
+            a.images = tmp;
+            r = fwd_pass(w, scene, p, L0, a, 0, p.S_user, st);
+            CK(cudaDeviceSynchronize());
+            cudaFree(tmp);
+            if (r != DGS_OK) break;
+            if ((r = upload_tabs(P, P->qfwd, 0, p.S_user,
+                                 tuned_choice(w, scene, p, 0, p.S_user, true, false), P->tfwd)) != DGS_OK) break;
+        } else {
+            RasterArgs rr = a;
+            rr.images = (float *)w->refs.p;
+            rr.img_s0 = p.S_user;
+            if ((r = fwd_pass(w, scene, p, L0, rr, p.S_user, p.S, st)) != DGS_OK) break;
+            a.refs = (const float *)w->refs.p;
+            a.ref_of_state = (const int32_t *)w->vgos.p;
+            a.partial = (double *)w->partial.p;
+            if ((r = fwd_pass(w, scene, p, L0, a, 0, p.S_user, st)) != DGS_OK) break;
+            if ((r = upload_tabs(P, P->qref, p.S_user, p.S, 1, P->tref)) != DGS_OK) break;
+            if ((r = upload_tabs(P, P->qfwd, 0, p.S_user,
+                                 tuned_choice(w, scene, p, 0, p.S_user, false, true), P->tfwd)) != DGS_OK) break;
+        }
+        CK(cudaDeviceSynchronize());
+    } while (0);
+    if (r != DGS_OK) {
+        if (!w->err.empty()) ctx->err = w->err;
+        dgs_plan_destroy(P);
+        return r;
+    }
+    *out = P;
+    return DGS_OK;
+}
+
+void dgs_plan_destroy(dgs_plan *P)
+{
+    if (!P) return;
+    cudaSetDevice(P->ws.device);
+    cudaDeviceSynchronize();
+    dgs_ctx *w = &P->ws;
+    Buf *bufs[] = {&w->vgs, &w->vgos, &w->depth, &w->need, &w->counts, &w->recBase, &w->total, &w->recs, &w->k0,
+                   &w->v0, &w->k1, &w->v1, &w->tcount, &w->toffs, &w->ek0, &w->ev0, &w->ek1, &w->ev1, &w->ranges,
+                   &w->sortws, &w->scanws, &w->partial, &w->refs, &w->recgrad, &w->refidx, &w->tck0, &w->tcv0,
+                   &w->tck1, &w->tcv1, &w->icnt, &w->ioff, &w->qint, &w->counter, &P->cnts, &P->qfwd, &P->qref};
+    for (Buf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (w->h_stage) cudaFreeHost(w->h_stage);
+    if (w->h_small) cudaFreeHost(w->h_small);
+    if (w->stage_done) cudaEventDestroy(w->stage_done);
+    delete P;
+}
+
+const char *dgs_plan_last_error(const dgs_plan *P) { return P ? P->ws.err.c_str() : "null plan"; }
+
+int dgs_plan_render(dgs_plan *P, const uint32_t *masks, float *images, dgs_stream stream)
+{
+    if (!P) return DGS_E_INVALID_ARG;
+    if (P->mode != DGS_PLAN_RENDER) return plan_fail(P, DGS_E_INVALID_ARG, "plan was not made for rendering");
+    if (!masks || !images) return plan_fail(P, DGS_E_INVALID_ARG, "masks or images is null");
+    dgs_ctx *ctx = &P->ws;
+    CK(cudaSetDevice(P->ws.device));
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(prepare_dev(P, masks, false, st));
+    RasterArgs a = plan_raster_args(P);
+    a.images = images;
+    TRY(launch_queue(&P->ws, P->p, P->L, a, P->tfwd, st));
+    P->rendered = true;
+    return DGS_OK;
+}
+
+int dgs_plan_backward(dgs_plan *P, const float *dL_dimages, const dgs_scene_grad *grads, dgs_stream stream)
+{
+    if (!P) return DGS_E_INVALID_ARG;
+    if (!P->rendered) return plan_fail(P, DGS_E_INVALID_ARG, "dgs_plan_backward needs a dgs_plan_render first");
+    if (!dL_dimages || !grads) return plan_fail(P, DGS_E_INVALID_ARG, "dL_dimages or grads is null");
+    const dgs_scene *scene = &P->scene;
+    if (!grads->mu0 || !grads->log_scale || !grads->quat || !grads->opacity_logit || !grads->colour ||
+        (scene->temporal_rank > 0 && !grads->u) || (scene->n_layers > 1 && !grads->res))
+        return plan_fail(P, DGS_E_INVALID_ARG, "gradient array is null");
+    dgs_ctx *ctx = &P->ws;
+    CK(cudaSetDevice(P->ws.device));
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_zero_prefix((uint32_t *)ctx->recgrad.p, P->R_cap, (const uint32_t *)P->cnts.p, 12, ctx->sms, st);
+    RasterBwdArgs b;
+    b.f = plan_raster_args(P);
+    b.dL_dimg = dL_dimages;
+    b.rec_grad = (float4 *)ctx->recgrad.p;
+    launch_raster_bwd(b, st);
+    GradDev g;
+    g.mu0 = grads->mu0; g.u = grads->u; g.ls = grads->log_scale; g.quat = grads->quat;
+    g.logit = grads->opacity_logit; g.colour = grads->colour; g.res = grads->res;
+    launch_project_bwd(scene_dev(scene), (const ViewGroup *)ctx->vgs.p, P->p.V, (const uint32_t *)ctx->need.p,
+                       (const uint32_t *)ctx->recBase.p, (const float4 *)ctx->recgrad.p, g, ctx->sms, st);
+    CK(cudaGetLastError());
+    return DGS_OK;
+}
+
+int dgs_plan_utility(dgs_plan *P, const uint32_t *masks, double *mse, double *psnr, dgs_stream stream)
+{
+    if (!P) return DGS_E_INVALID_ARG;
+    if (P->mode != DGS_PLAN_UTILITY) return plan_fail(P, DGS_E_INVALID_ARG, "plan was not made for utility");
+    if (!masks || !mse) return plan_fail(P, DGS_E_INVALID_ARG, "masks or mse is null");
+    dgs_ctx *ctx = &P->ws;
+    CK(cudaSetDevice(P->ws.device));
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(prepare_dev(P, masks, true, st));
+    RasterArgs r = plan_raster_args(P);
+    r.images = (float *)ctx->refs.p;
+    r.img_s0 = P->p.S_user;
+    TRY(launch_queue(ctx, P->p, P->L, r, P->tref, st));
+    RasterArgs a = plan_raster_args(P);
+    a.refs = (const float *)ctx->refs.p;
+    a.ref_of_state = (const int32_t *)ctx->vgos.p;
+    a.partial = (double *)ctx->partial.p;
+    TRY(launch_queue(ctx, P->p, P->L, a, P->tfwd, st));
+    launch_mse_reduce((const double *)ctx->partial.p, P->p.S_user, (int)P->p.tiles,
+                      1.0 / (double)((size_t)P->p.W * P->p.H * 3), mse, psnr, st);
+    CK(cudaGetLastError());
+    return DGS_OK;
+}
+
+int dgs_plan_image_mse(dgs_plan *P, const float *images, const float *refs, float weight, double *mse,
+                       double *psnr, float *dL_dimages, dgs_stream stream)
+{
+    if (!P) return DGS_E_INVALID_ARG;
+    if (P->n_refs < 1) return plan_fail(P, DGS_E_INVALID_ARG, "plan was made without ref_index");
+    if (!images || !refs || !mse) return plan_fail(P, DGS_E_INVALID_ARG, "null argument");
+    dgs_ctx *ctx = &P->ws;
+    CK(cudaSetDevice(P->ws.device));
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_image_mse(images, refs, (const int32_t *)ctx->refidx.p, P->p.S_user, P->p.H, P->p.W, weight,
+                     (double *)ctx->partial.p, P->image_parts, dL_dimages, st);
+    launch_mse_reduce((const double *)ctx->partial.p, P->p.S_user, P->image_parts,
+                      1.0 / (double)((size_t)P->p.W * P->p.H * 3), mse, psnr, st);
+    CK(cudaGetLastError());
+    return DGS_OK;
+}
+
+int dgs_plan_status(dgs_plan *P, int64_t *n_records, int64_t *n_entries, dgs_stream stream)
+{
+    if (!P) return DGS_E_INVALID_ARG;
+    dgs_ctx *ctx = &P->ws;
+    CK(cudaSetDevice(P->ws.device));
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(ctx->h_small, P->cnts.p, 16, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (n_records) *n_records = ctx->h_small[0];
+    if (n_entries) *n_entries = ctx->h_small[1];
+    if (ctx->h_small[3]) {
+        CK(cudaMemsetAsync((uint32_t *)P->cnts.p + 3, 0, 4, st));
+        return plan_fail(P, DGS_E_CAPACITY, "tile entries exceeded the plan's capacity: results are incomplete");
+    }
     return DGS_OK;
 }
 

@@ -79,9 +79,12 @@ cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint
 
 // Stable LSD radix sort of (key, value) u32 pairs on key bits [0, bits).
 // Ping-pongs between (k0, v0) and (k1, v1); returns in *result_in_alt whether
-// the sorted data ended in (k1, v1).  ws from radix_workspace_bytes.
+// the sorted data ended in (k1, v1).  ws from radix_workspace_bytes(n).  With
+// n_dev the live count is read on the device (n is then the capacity), so the
+// launch sequence does not depend on it (capture-safe).
 size_t radix_workspace_bytes(size_t n);
 cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, size_t n,
-                             int bits, void *ws, cudaStream_t st, bool *result_in_alt);
+                             int bits, void *ws, cudaStream_t st, bool *result_in_alt,
+                             const uint32_t *n_dev = nullptr);
 
 }  // namespace dgs

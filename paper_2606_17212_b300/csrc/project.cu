@@ -146,13 +146,29 @@ __device__ __forceinline__ uint32_t rec_tiles(const float4 &q)
     return (uint32_t)((xhi / TILE - xlo / TILE + 1) * (yhi / TILE - ylo / TILE + 1));
 }
 
-// Tile counts of records in depth order (sorted slot list).
-__global__ void k_tile_count(const Rec *__restrict__ recs, const uint32_t *__restrict__ order, uint32_t n,
-                             uint32_t *__restrict__ counts)
+__device__ __forceinline__ uint32_t live_n(uint32_t n_cap, const uint32_t *n_dev)
 {
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        counts[j] = rec_tiles(rec_tail(recs, order[j]));
+    return n_dev ? min(n_cap, *n_dev) : n_cap;
+}
+
+// Tile counts of records in depth order (sorted slot list); zero past the
+// live count so a scan over the capacity gives the entry total.
+__global__ void k_tile_count(const Rec *__restrict__ recs, const uint32_t *__restrict__ order, uint32_t n_cap,
+                             const uint32_t *__restrict__ n_dev, uint32_t *__restrict__ counts)
+{
+    const uint32_t n = live_n(n_cap, n_dev);
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n_cap; j += gridDim.x * blockDim.x) {
+        counts[j] = j < n ? rec_tiles(rec_tail(recs, order[j])) : 0u;
     }
+}
+
+// out = min(total, cap); flags bit 0 when total exceeds the capacity.
+__global__ void k_clamp_count(const uint32_t *__restrict__ total, uint32_t cap, uint32_t *__restrict__ out,
+                              uint32_t *__restrict__ flags)
+{
+    const uint32_t t = *total;
+    *out = t < cap ? t : cap;
+    if (t > cap) atomicOr(flags, 1u);
 }
 
 // Emit one (view group * tiles + tile, slot) entry per overlapped tile, in
@@ -162,9 +178,11 @@ __global__ void k_tile_count(const Rec *__restrict__ recs, const uint32_t *__res
 // e of each pass finds the record owning entry e by a 5-step search over the
 // warp's inclusive prefix of tile counts (coalesced stores).
 __global__ void k_emit(const Rec *__restrict__ recs, const uint32_t *__restrict__ order,
-                       const uint32_t *__restrict__ offsets, uint32_t n, int tiles_x, uint32_t tiles,
-                       uint32_t *__restrict__ ekeys, uint32_t *__restrict__ evals)
+                       const uint32_t *__restrict__ offsets, uint32_t n_cap, const uint32_t *__restrict__ n_dev,
+                       uint32_t e_cap, int tiles_x, uint32_t tiles, uint32_t *__restrict__ ekeys,
+                       uint32_t *__restrict__ evals)
 {
+    const uint32_t n = live_n(n_cap, n_dev);
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -210,7 +228,7 @@ __global__ void k_emit(const Rec *__restrict__ recs, const uint32_t *__restrict_
             const float o_rtw = __shfl_sync(0xffffffffu, rtw, lo);
             const uint32_t o_vb = __shfl_sync(0xffffffffu, vbase, lo);
             const uint32_t o_slot = __shfl_sync(0xffffffffu, slot, lo);
-            if (e < total) {
+            if (e < total && first + e < e_cap) {
                 const int li = (int)(e - (o_incl - o_cnt));
                 int row = (int)(((float)li + 0.5f) * o_rtw);
                 row -= (row * o_tw > li) ? 1 : 0;            // exact quotient li / o_tw
@@ -223,13 +241,24 @@ __global__ void k_emit(const Rec *__restrict__ recs, const uint32_t *__restrict_
     }
 }
 
-__global__ void k_ranges(const uint32_t *__restrict__ keys, uint32_t n, uint2 *__restrict__ ranges)
+__global__ void k_ranges(const uint32_t *__restrict__ keys, uint32_t n_cap, const uint32_t *__restrict__ n_dev,
+                         uint2 *__restrict__ ranges)
 {
+    const uint32_t n = live_n(n_cap, n_dev);
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         const uint32_t k = keys[e];
         if (e == 0 || keys[e - 1] != k) ranges[k].x = e;
         if (e == n - 1 || keys[e + 1] != k) ranges[k].y = e + 1;
     }
+}
+
+// Zero the first (live count) * per words of p (live count read on the device).
+__global__ void k_zero_prefix(uint32_t *__restrict__ p, uint32_t n_cap, const uint32_t *__restrict__ n_dev,
+                              uint32_t per)
+{
+    const size_t words = (size_t)live_n(n_cap, n_dev) * per;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < words; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = 0u;
 }
 
 // --------------------------------------------------------------- launchers
@@ -277,26 +306,43 @@ void launch_project(const SceneDev &s, const ViewGroup *vgs, int V, const uint32
 }
 
 void launch_tile_count(const Rec *recs, const uint32_t *order, uint32_t n, uint32_t *counts, int sms,
-                       cudaStream_t st)
+                       cudaStream_t st, const uint32_t *n_dev)
 {
+    if (n == 0) return;
     ProfScope ps_("tile_count", st);
-    k_tile_count<<<grid_for(n, 256, sms), 256, 0, st>>>(recs, order, n, counts);
+    k_tile_count<<<grid_for(n, 256, sms), 256, 0, st>>>(recs, order, n, n_dev, counts);
+    count_launch();
+}
+
+void launch_clamp_count(const uint32_t *total, uint32_t cap, uint32_t *out, uint32_t *flags, cudaStream_t st)
+{
+    k_clamp_count<<<1, 1, 0, st>>>(total, cap, out, flags);
     count_launch();
 }
 
 void launch_emit(const Rec *recs, const uint32_t *order, const uint32_t *offsets, uint32_t n, int tiles_x,
-                 uint32_t tiles, uint32_t *ekeys, uint32_t *evals, int sms, cudaStream_t st)
+                 uint32_t tiles, uint32_t *ekeys, uint32_t *evals, int sms, cudaStream_t st, const uint32_t *n_dev,
+                 uint32_t e_cap)
 {
+    if (n == 0) return;
     ProfScope ps_("emit", st);
-    k_emit<<<grid_for(n, 256, sms), 256, 0, st>>>(recs, order, offsets, n, tiles_x, tiles, ekeys, evals);
+    k_emit<<<grid_for(n, 256, sms), 256, 0, st>>>(recs, order, offsets, n, n_dev, e_cap, tiles_x, tiles, ekeys,
+                                                   evals);
     count_launch();
 }
 
-void launch_ranges(const uint32_t *keys, uint32_t n, uint2 *ranges, int sms, cudaStream_t st)
+void launch_ranges(const uint32_t *keys, uint32_t n, uint2 *ranges, int sms, cudaStream_t st, const uint32_t *n_dev)
 {
     if (n == 0) return;
     ProfScope ps_("ranges", st);
-    k_ranges<<<grid_for(n, 256, sms), 256, 0, st>>>(keys, n, ranges);
+    k_ranges<<<grid_for(n, 256, sms), 256, 0, st>>>(keys, n, n_dev, ranges);
+    count_launch();
+}
+
+void launch_zero_prefix(uint32_t *p, uint32_t n_cap, const uint32_t *n_dev, uint32_t per, int sms, cudaStream_t st)
+{
+    if (n_cap == 0 || per == 0) return;
+    k_zero_prefix<<<grid_for((long long)n_cap * per, 256, sms), 256, 0, st>>>(p, n_cap, n_dev, per);
     count_launch();
 }
 

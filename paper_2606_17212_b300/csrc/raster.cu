@@ -679,14 +679,22 @@ static int occ_g(bool write, bool mse)
     return occ_t<G, false, true>();
 }
 
+// Resident blocks per SM of each instantiation (queried once, then cached, so
+// launches made during stream capture issue no runtime queries).
 int raster_fwd_blocks_per_sm(int G, bool write, bool mse)
 {
-    switch (G) {
-    case 1: return occ_g<1>(write, mse);
-    case 2: return occ_g<2>(write, mse);
-    case 4: return occ_g<4>(write, mse);
-    default: return occ_g<8>(write, mse);
+    static int cache[4][3] = {};
+    const int gi = G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : 3;
+    const int mi = (write && mse) ? 0 : write ? 1 : 2;
+    if (!cache[gi][mi]) {
+        switch (G) {
+        case 1: cache[gi][mi] = occ_g<1>(write, mse); break;
+        case 2: cache[gi][mi] = occ_g<2>(write, mse); break;
+        case 4: cache[gi][mi] = occ_g<4>(write, mse); break;
+        default: cache[gi][mi] = occ_g<8>(write, mse); break;
+        }
     }
+    return cache[gi][mi];
 }
 
 void launch_tile_costs(const uint2 *ranges, uint32_t n, uint32_t *keys, uint32_t *vals, int sms, cudaStream_t st)

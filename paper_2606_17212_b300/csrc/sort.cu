@@ -134,9 +134,16 @@ cudaError_t scan_rec(const uint32_t *in, uint32_t *out, size_t n, uint32_t *tota
 }
 
 // ---------------------------------------------------------------- radix sort
-__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t *keys, size_t n, int shift, uint32_t mask,
-                                                        uint32_t *hist, uint32_t nblocks)
+// n_dev (optional) holds the live item count on the device (<= n, the capacity)
+__device__ __forceinline__ size_t live_count(size_t n, const uint32_t *n_dev)
 {
+    return n_dev ? min(n, (size_t)*n_dev) : n;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t *keys, size_t n_cap, const uint32_t *n_dev,
+                                                        int shift, uint32_t mask, uint32_t *hist, uint32_t nblocks)
+{
+    const size_t n = live_count(n_cap, n_dev);
     __shared__ uint32_t h[RS_RADIX];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -151,10 +158,11 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t *keys, si
 }
 
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t *kin, const uint32_t *vin,
-                                                           uint32_t *kout, uint32_t *vout, size_t n,
-                                                           int shift, uint32_t mask,
+                                                           uint32_t *kout, uint32_t *vout, size_t n_cap,
+                                                           const uint32_t *n_dev, int shift, uint32_t mask,
                                                            const uint32_t *offsets, uint32_t nblocks)
 {
+    const size_t n = live_count(n_cap, n_dev);
     __shared__ uint32_t wh[RS_WARPS][RS_RADIX];     // per-warp digit counts, then offsets
     __shared__ uint32_t dstart[RS_RADIX];           // first block-local slot of each digit
     __shared__ uint32_t gbase[RS_RADIX];            // global slot of the block's first item of each digit
@@ -211,7 +219,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t *kin, 
     }
     __syncthreads();
     const size_t blk0 = (size_t)blockIdx.x * RS_CHUNK;
-    const uint32_t valid = n - blk0 < (size_t)RS_CHUNK ? (uint32_t)(n - blk0) : (uint32_t)RS_CHUNK;
+    const uint32_t valid = n <= blk0 ? 0u : (n - blk0 < (size_t)RS_CHUNK ? (uint32_t)(n - blk0) : (uint32_t)RS_CHUNK);
     // consecutive threads write consecutive slots of each digit run: coalesced
     for (uint32_t i = threadIdx.x; i < valid; i += RS_THREADS) {
         const uint32_t kk = sk[i];
@@ -248,10 +256,10 @@ size_t radix_workspace_bytes(size_t n)
 }
 
 cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, size_t n,
-                             int bits, void *ws, cudaStream_t st, bool *result_in_alt)
+                             int bits, void *ws, cudaStream_t st, bool *result_in_alt, const uint32_t *n_dev)
 {
     *result_in_alt = false;
-    if (n <= 1 || bits <= 0) return cudaSuccess;
+    if (n == 0 || (n <= 1 && !n_dev) || bits <= 0) return cudaSuccess;
     size_t nb = blocks_for(n, RS_CHUNK);
     uint32_t *hist = (uint32_t *)ws;
     void *scan_ws = (char *)ws + align_up((size_t)RS_RADIX * nb * sizeof(uint32_t));
@@ -260,11 +268,12 @@ cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t 
         int w = bits - shift < 8 ? bits - shift : 8;
         uint32_t mask = (1u << w) - 1u;
         ProfScope ps_("radix_pass", st);
-        k_rs_hist<<<(unsigned)nb, RS_THREADS, 0, st>>>(ki, n, shift, mask, hist, (uint32_t)nb);
+        k_rs_hist<<<(unsigned)nb, RS_THREADS, 0, st>>>(ki, n, n_dev, shift, mask, hist, (uint32_t)nb);
         count_launch();
         cudaError_t e = exclusive_scan_u32(hist, hist, (size_t)RS_RADIX * nb, nullptr, scan_ws, st);
         if (e != cudaSuccess) return e;
-        k_rs_scatter<<<(unsigned)nb, RS_THREADS, 0, st>>>(ki, vi, ko, vo, n, shift, mask, hist, (uint32_t)nb);
+        k_rs_scatter<<<(unsigned)nb, RS_THREADS, 0, st>>>(ki, vi, ko, vo, n, n_dev, shift, mask, hist,
+                                                          (uint32_t)nb);
         count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

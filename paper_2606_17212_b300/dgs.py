@@ -49,7 +49,10 @@ class States_t(ctypes.Structure):
 EXPORTS = ("dgs_create", "dgs_destroy", "dgs_last_error", "dgs_version", "dgs_render_state",
            "dgs_render_states_batched", "dgs_render_backward", "dgs_state_utility", "dgs_image_mse",
            "dgs_kernel_launches", "dgs_reset_kernel_launches", "dgs_profile_enable", "dgs_profile_read",
-           "dgs_image_mse_noalloc", "dgs_debug_tile_lists")
+           "dgs_image_mse_noalloc", "dgs_debug_tile_lists", "dgs_plan_create", "dgs_plan_destroy",
+           "dgs_plan_last_error", "dgs_plan_render", "dgs_plan_backward", "dgs_plan_utility",
+           "dgs_plan_image_mse", "dgs_plan_status")
+PLAN_RENDER, PLAN_UTILITY = 1, 2
 
 _lib = None
 
@@ -87,6 +90,17 @@ def lib():
         L.dgs_image_mse_noalloc.restype = I
         L.dgs_debug_tile_lists.argtypes = [P] * 11 + [P]
         L.dgs_debug_tile_lists.restype = I
+        L.dgs_plan_create.argtypes = [P, ctypes.POINTER(Scene_t), ctypes.POINTER(States_t), P, I, P, I, P, I, F,
+                                      ctypes.POINTER(P)]
+        L.dgs_plan_destroy.argtypes = [P]
+        L.dgs_plan_destroy.restype = None
+        L.dgs_plan_last_error.argtypes = [P]
+        L.dgs_plan_last_error.restype = ctypes.c_char_p
+        L.dgs_plan_render.argtypes = [P, P, P, P]
+        L.dgs_plan_backward.argtypes = [P, P, ctypes.POINTER(SceneGrad_t), P]
+        L.dgs_plan_utility.argtypes = [P, P, P, P, P]
+        L.dgs_plan_image_mse.argtypes = [P, P, P, F, P, P, P, P]
+        L.dgs_plan_status.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), P]
         _lib = L
     return _lib
 
@@ -336,3 +350,72 @@ def image_mse_noalloc(images, refs, ref_index, mse, psnr=None, dL=None, weight=1
     return int(lib().dgs_image_mse_noalloc(_ptr(images), _ptr(refs), _ptr(ref_index), int(S), int(refs.shape[0]),
                                            int(H), int(W), float(weight), _ptr(mse), _ptr(psnr), _ptr(dL),
                                            _stream(stream)))
+
+
+class Plan:
+    """A capture-safe plan over a fixed batch (see dgs_plan_create in include/dgs.h).
+
+    Per-step calls launch kernels only, so they can run inside a
+    ``torch.cuda.graph`` capture and be replayed with new masks."""
+
+    def __init__(self, renderer: Renderer, scene: DeviceScene, states: DeviceStates, cams, bg,
+                 mode: int = PLAN_RENDER, ref_index=None, n_refs: int = 0, entry_headroom: float = 1.25):
+        self._lib = lib()
+        self.scene, self.cams, self.n = scene, cams, states.n
+        self.W, self.H = cams[0].width, cams[0].height
+        self._keep = (scene.struct(), states.struct(), camera_array(cams),
+                      (ctypes.c_float * 3)(*[float(x) for x in bg]))
+        ri = None if ref_index is None else np.ascontiguousarray(ref_index, np.int32)
+        self._ri = ri
+        h = ctypes.c_void_p()
+        sc, st, ca, bgv = self._keep
+        rc = self._lib.dgs_plan_create(renderer.h, ctypes.byref(sc), ctypes.byref(st), ca, len(cams), bgv, int(mode),
+                                       None if ri is None else ri.ctypes.data_as(ctypes.c_void_p), int(n_refs),
+                                       float(entry_headroom), ctypes.byref(h))
+        if rc != DGS_OK:
+            raise RuntimeError("dgs_plan_create failed (%s): %s" % (ERRORS.get(rc, rc),
+                                                                    self._lib.dgs_last_error(renderer.h).decode()))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.dgs_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != DGS_OK:
+            raise RuntimeError("%s failed (%s): %s" % (what, ERRORS.get(rc, rc),
+                                                       self._lib.dgs_plan_last_error(self.h).decode()))
+
+    def render(self, masks, images, stream=None):
+        self._check(self._lib.dgs_plan_render(self.h, _ptr(masks), _ptr(images), _stream(stream)), "dgs_plan_render")
+        return images
+
+    def backward(self, dL, grads, stream=None):
+        g = SceneGrad_t(*[(_ptr(grads[k]) if grads[k].numel() else None) for k in SCENE_FIELDS])
+        self._check(self._lib.dgs_plan_backward(self.h, _ptr(dL), ctypes.byref(g), _stream(stream)),
+                    "dgs_plan_backward")
+        return grads
+
+    def utility(self, masks, mse, psnr, stream=None):
+        self._check(self._lib.dgs_plan_utility(self.h, _ptr(masks), _ptr(mse), _ptr(psnr), _stream(stream)),
+                    "dgs_plan_utility")
+        return mse, psnr
+
+    def image_mse(self, images, refs, mse, psnr, dL, weight=1.0, stream=None):
+        self._check(self._lib.dgs_plan_image_mse(self.h, _ptr(images), _ptr(refs), float(weight), _ptr(mse),
+                                                 _ptr(psnr), _ptr(dL), _stream(stream)), "dgs_plan_image_mse")
+        return mse, psnr, dL
+
+    def status(self, stream=None):
+        """(records, entries) of the last call; raises if entries overflowed."""
+        nr, ne = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self._lib.dgs_plan_status(self.h, ctypes.byref(nr), ctypes.byref(ne), _stream(stream)),
+                    "dgs_plan_status")
+        return nr.value, ne.value

@@ -1,0 +1,134 @@
+"""Capture-safe plans: equal to the context calls, and replayable in a CUDA graph."""
+import numpy as np
+import pytest
+
+from paper_2606_17212_b300 import dgs, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    assert _t.cuda.is_available()
+    return _t
+
+
+@pytest.fixture(scope="module")
+def R(torch):
+    r = dgs.Renderer(0)
+    yield r
+    r.close()
+
+
+def _masks(torch, w, seed):
+    rng = np.random.default_rng(seed)
+    sc = w.scene
+    d = synth.prefix_states(w.states.n, sc.n_clusters, sc.n_layers, rng)
+    bits = synth.erase_one_packet(synth.depths_to_bits(d, sc.n_layers), 0.2, rng)
+    return torch.from_numpy(synth._pack(bits).view(np.int32)).cuda()
+
+
+def test_plan_render_backward_match_and_replay_in_graph(R, torch):
+    w = synth.config("c3_fwdbwd_250k", scale=0.05, n_states=12)
+    sc = dgs.DeviceScene.from_host(w.scene)
+    st = dgs.DeviceStates.from_host(w.states)
+    S, H, W = st.n, w.cams[0].height, w.cams[0].width
+    plan = dgs.Plan(R, sc, st, w.cams, w.bg, dgs.PLAN_RENDER, entry_headroom=2.0)
+    masks = st.masks.clone()
+    images = torch.empty((S, H, W, 3), device="cuda")
+    plan.render(masks, images)
+    ref = R.render_states_batched(sc, st, w.cams, w.bg)
+    assert torch.equal(images, ref)
+    rng = np.random.default_rng(0)
+    dL = torch.from_numpy(rng.normal(size=(S, H, W, 3)).astype(np.float32)).cuda()
+    g_plan = plan.backward(dL, sc.zeros_like_grads())
+    g_ref = R.render_backward(sc, st, w.cams, w.bg, dL)
+    for k in dgs.SCENE_FIELDS:
+        a, b = g_plan[k], g_ref[k]
+        if b.numel():
+            assert torch.allclose(a, b, rtol=1e-4, atol=1e-5 * float(b.abs().max()) + 1e-12), k
+    # capture forward + backward once, replay with other masks
+    grads = sc.zeros_like_grads()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        plan.render(masks, images)
+        plan.backward(dL, grads)
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        for g in grads.values():
+            g.zero_()
+        plan.render(masks, images)
+        plan.backward(dL, grads)
+    for seed in (1, 2):
+        new = _masks(torch, w, seed)
+        masks.copy_(new)
+        graph.replay()
+        torch.cuda.synchronize()
+        plan.status()
+        st_new = dgs.DeviceStates(new, w.states.t, w.states.cam)
+        assert torch.equal(images, R.render_states_batched(sc, st_new, w.cams, w.bg))
+        g_ref = R.render_backward(sc, st_new, w.cams, w.bg, dL)
+        for k in dgs.SCENE_FIELDS:
+            if g_ref[k].numel():
+                assert torch.allclose(grads[k], g_ref[k], rtol=1e-4,
+                                      atol=1e-5 * float(g_ref[k].abs().max()) + 1e-12), (seed, k)
+    plan.close()
+
+
+def test_plan_utility_and_image_mse(R, torch):
+    w = synth.config("c2_dynamic_250k", scale=0.02, n_states=20)
+    sc = dgs.DeviceScene.from_host(w.scene)
+    st = dgs.DeviceStates.from_host(w.states)
+    plan = dgs.Plan(R, sc, st, w.cams, w.bg, dgs.PLAN_UTILITY)
+    mse = torch.empty(st.n, dtype=torch.float64, device="cuda")
+    psnr = torch.empty_like(mse)
+    masks = st.masks.clone()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        plan.utility(masks, mse, psnr)
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        plan.utility(masks, mse, psnr)
+    graph.replay()
+    torch.cuda.synchronize()
+    m_ref, p_ref = R.state_utility(sc, st, w.cams, w.bg)
+    assert torch.equal(mse, m_ref) and torch.equal(psnr, p_ref)
+    plan.close()
+    # image MSE through a render plan with reference indices
+    tv = np.unique(w.states.t)
+    ridx = np.searchsorted(tv, w.states.t).astype(np.int32)
+    plan2 = dgs.Plan(R, sc, st, w.cams, w.bg, dgs.PLAN_RENDER, ref_index=ridx, n_refs=len(tv))
+    imgs = R.render_states_batched(sc, st, w.cams, w.bg)
+    full = torch.full((len(tv), st.masks.shape[1]), -1, dtype=torch.int32, device="cuda")
+    refs = R.render_states_batched(sc, dgs.DeviceStates(full, tv, np.zeros(len(tv), np.int32)), w.cams, w.bg)
+    m1, p1, d1 = R.image_mse(imgs, refs, ridx, weight=0.5, want_grad=True)
+    m2, p2, d2 = torch.empty_like(m1), torch.empty_like(p1), torch.empty_like(d1)
+    plan2.image_mse(imgs, refs, m2, p2, d2, weight=0.5)
+    torch.cuda.synchronize()
+    assert torch.equal(m1, m2) and torch.equal(d1, d2)
+    plan2.close()
+
+
+def test_plan_reports_entry_overflow_without_faulting(R, torch):
+    """A plan sized on sparse masks, run on complete masks, drops entries past its
+    capacity (every write stays inside the reserved buffers) and says so."""
+    w = synth.config("c3_fwdbwd_250k", scale=0.3, n_states=4)    # ~2M entries when complete
+    sc = dgs.DeviceScene.from_host(w.scene)
+    sparse = torch.zeros((w.states.n, w.states.masks.shape[1]), dtype=torch.int32, device="cuda")
+    sparse[:, 0] = 1                          # only cluster 0's base layer
+    st = dgs.DeviceStates(sparse, w.states.t, w.states.cam)
+    plan = dgs.Plan(R, sc, st, w.cams, w.bg, dgs.PLAN_RENDER, entry_headroom=1.0)
+    images = torch.empty((st.n, w.cams[0].height, w.cams[0].width, 3), device="cuda")
+    plan.render(sparse, images)
+    plan.status()                             # fits
+    full = torch.full_like(sparse, -1)
+    plan.render(full, images)
+    with pytest.raises(RuntimeError, match="DGS_E_CAPACITY"):
+        plan.status()
+    plan.status()                             # the flag was cleared
+    plan.close()

@@ -394,18 +394,21 @@ __global__ void k_item_counts(const uint32_t *__restrict__ tile_order, uint32_t 
 
 // Per-pixel state of the adjoint walk.
 struct PixB {
-    float T, c0, c1, c2;      // transmittance and colour prefix (pass 2)
-    float Cf0, Cf1, Cf2;      // final colour without background (pass 1)
-    float sb0, sb1, sb2;      // T_final * bg
+    float T;                  // transmittance before the current entry (pass 2)
+    float gc;                 // dL/dC . (colour accumulated so far)
+    float GK;                 // dL/dC . (C_final + T_final bg), from pass 1
     float g0, g1, g2;         // dL/dC
     uint32_t stop;            // filtered-stream index where the pixel stopped
     bool active;
 };
 
-// Adjoint of one pixel at one staged entry; adds to g[9] =
-// (mx, my, A, B, C, o, r, g, b) when the entry is included (inb: in the box
-// and the pixel still active).  Branch free like composite(): a skipped entry
-// has alpha = 0, adds zeros, and leaves T and the colour prefix unchanged.
+// Adjoint of one pixel at one staged entry (inb: in the box and the pixel
+// still active).  With gr = dL/dC . rgb_k and the running gc = dL/dC . C_prefix
+// (including k):  dL/dalpha_k = T_k gr - (GK - gc) / (1 - alpha_k).  Adds to
+// g[9] = (S gpw dx, S gpw dy, S gpw dx^2, S gpw dx dy, S gpw dy^2, dL/do, dL/drgb)
+// with gpw = dL/dpower; the conic and mean gradients are linear in these sums
+// (A, B, C are per Gaussian) and are formed once per Gaussian after the
+// reduction.  Branch free: a skipped entry has alpha = 0 and adds zeros.
 __device__ __forceinline__ bool adjoint(PixB &p, const float4 &r0, const float4 &r1, float b, bool inb, float pcx,
                                         float pcy, float *g)
 {
@@ -418,23 +421,22 @@ __device__ __forceinline__ bool adjoint(PixB &p, const float4 &r0, const float4 
     const float alpha = ok ? a0 : 0.0f;
     const float one_m = __fsub_rn(1.0f, alpha);
     const float wgt = __fmul_rn(alpha, p.T);
-    p.c0 = __fmaf_rn(r1.z, wgt, p.c0);
-    p.c1 = __fmaf_rn(r1.w, wgt, p.c1);
-    p.c2 = __fmaf_rn(b, wgt, p.c2);
-    const float inv = __fdividef(1.0f, one_m);
-    const float da = p.g0 * (r1.z * p.T - ((p.Cf0 - p.c0) + p.sb0) * inv) +
-                     p.g1 * (r1.w * p.T - ((p.Cf1 - p.c1) + p.sb1) * inv) +
-                     p.g2 * (b * p.T - ((p.Cf2 - p.c2) + p.sb2) * inv);
-    g[6] += p.g0 * wgt; g[7] += p.g1 * wgt; g[8] += p.g2 * wgt;
+    const float gr = fmaf(p.g2, b, fmaf(p.g1, r1.w, p.g0 * r1.z));
+    p.gc = fmaf(wgt, gr, p.gc);
+    const float da = fmaf(p.T, gr, -(p.GK - p.gc) * __fdividef(1.0f, one_m));
+    g[6] = fmaf(p.g0, wgt, g[6]);
+    g[7] = fmaf(p.g1, wgt, g[7]);
+    g[8] = fmaf(p.g2, wgt, g[8]);
     // alpha = 0 (skipped) or the 0.99 clamp: no gradient to opacity, mean, conic
     const bool lin = ok && araw < 0.99f;
     const float gpw = lin ? da * alpha : 0.0f;
     g[5] += lin ? da * ex : 0.0f;
-    g[0] -= gpw * (r0.z * dx + r0.w * dy);
-    g[1] -= gpw * (r1.x * dy + r0.w * dx);
-    g[2] -= 0.5f * gpw * dx * dx;
-    g[3] -= gpw * dx * dy;
-    g[4] -= 0.5f * gpw * dy * dy;
+    const float t1 = gpw * dx, t2 = gpw * dy;
+    g[0] += t1;
+    g[1] += t2;
+    g[2] = fmaf(t1, dx, g[2]);
+    g[3] = fmaf(t1, dy, g[3]);
+    g[4] = fmaf(t2, dy, g[4]);
     p.T = __fmul_rn(p.T, one_m);
     return ok;
 }
@@ -516,14 +518,13 @@ __global__ void __launch_bounds__(RT, 6) k_raster_bwd(RasterBwdArgs b)
         const bool in = h ? in1 : in0;
         const int py = h ? py1 : py0;
         PixB &p = q[h];
-        p.T = 1.0f; p.c0 = p.c1 = p.c2 = 0.0f;
-        p.Cf0 = f.c0; p.Cf1 = f.c1; p.Cf2 = f.c2;
-        p.sb0 = f.T * a.bg0; p.sb1 = f.T * a.bg1; p.sb2 = f.T * a.bg2;
+        p.T = 1.0f; p.gc = 0.0f;
         p.g0 = p.g1 = p.g2 = 0.0f;
         if (in) {
             const float *gp = b.dL_dimg + (((size_t)s * a.H + py) * a.W + px) * 3;
             p.g0 = gp[0]; p.g1 = gp[1]; p.g2 = gp[2];
         }
+        p.GK = p.g0 * fmaf(f.T, a.bg0, f.c0) + p.g1 * fmaf(f.T, a.bg1, f.c1) + p.g2 * fmaf(f.T, a.bg2, f.c2);
         p.stop = h ? stop1 : stop0;
         p.active = in && p.stop > 0 && (p.g0 != 0.0f || p.g1 != 0.0f || p.g2 != 0.0f);
     }
@@ -570,9 +571,12 @@ __global__ void __launch_bounds__(RT, 6) k_raster_bwd(RasterBwdArgs b)
 #pragma unroll
             for (int j = 0; j < 9; ++j) { x[j] = gacc[k][j]; gacc[k][j] = 0.0f; any |= (x[j] != 0.0f); }
             if (any) {
+                // conic and mean gradients from the per-Gaussian sums
+                const float A = sm.r0[k].z, B = sm.r0[k].w, C = sm.r1[k].x;
+                const float gmx = -(A * x[0] + B * x[1]), gmy = -(C * x[1] + B * x[0]);
                 float4 *dst = b.rec_grad + (size_t)sm.slot[k] * 3;
-                atomicAdd(dst, make_float4(x[0], x[1], x[2], x[3]));
-                atomicAdd(dst + 1, make_float4(x[4], x[5], x[6], x[7]));
+                atomicAdd(dst, make_float4(gmx, gmy, -0.5f * x[2], -x[3]));
+                atomicAdd(dst + 1, make_float4(-0.5f * x[4], x[5], x[6], x[7]));
                 atomicAdd(dst + 2, make_float4(x[8], 0.0f, 0.0f, 0.0f));
             }
         }

@@ -23,8 +23,8 @@ constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_ITEMS;   // 4096
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ITEMS = 16;
-constexpr int RS_CHUNK = RS_THREADS * RS_ITEMS;         // 4096
+constexpr int RS_ITEMS = 8;
+constexpr int RS_CHUNK = RS_THREADS * RS_ITEMS;         // 2048
 constexpr int RS_RADIX = 256;
 
 __device__ __forceinline__ int pad(int i) { return i + (i >> 5); }

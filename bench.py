@@ -46,6 +46,28 @@ def _dist():
     return ws, rank, local
 
 
+def rank_states(w, rank):
+    """Weak scaling: rank r renders its own batch of delivery states (rank 0
+    keeps the workload's masks, others draw prefix masks with seed 10000 + r)."""
+    from paper_2606_17212_b300 import synth
+    if rank == 0:
+        return w.states.masks
+    rng = np.random.default_rng(10_000 + rank)
+    d = synth.prefix_states(w.states.n, w.scene.n_clusters, w.scene.n_layers, rng)
+    return synth._pack(synth.depths_to_bits(d, w.scene.n_layers))
+
+
+def max_over_ranks(x, device=None):
+    """Max of a float over the process group (identity without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -219,10 +241,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     # weak scaling: every rank renders its own batch of states (different mask seed)
-    if ws > 1 and rank > 0:
-        rng = np.random.default_rng(10_000 + rank)
-        d = synth.prefix_states(w.states.n, w.scene.n_clusters, w.scene.n_layers, rng)
-        w.states.masks = synth._pack(synth.depths_to_bits(d, w.scene.n_layers))
+    w.states.masks = rank_states(w, rank)
 
     R = dgs.Renderer(local)
     scene = dgs.DeviceScene.from_host(w.scene, device=dev)
@@ -277,11 +296,7 @@ def main():
         torch.cuda.synchronize()
         if ws > 1:
             torch.distributed.barrier()
-        total = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
-        if ws > 1:
-            t = torch.tensor([total], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total = float(t.item())
+        total = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(starts, ends)), device=dev)
         return total / K
 
     clocks = ClockSampler(local)

@@ -271,7 +271,7 @@ def main():
             mse, _, dL = R.image_mse(images, targets, ref_index, weight=1.0 / S, want_grad=True)
             for g in grads.values():
                 g.zero_()
-            R.render_backward(scene, st, w.cams, w.bg, dL, grads)
+            R.render_backward(scene, st, w.cams, w.bg, dL, grads, images=images)
             return mse
         mse, _ = R.state_utility(scene, st, w.cams, w.bg)
         return mse
@@ -325,7 +325,7 @@ def main():
                 g.zero_()
             plan.render(g_masks, images)
             plan.image_mse(images, targets, g_mse, g_psnr, g_dL, weight=1.0 / S)
-            plan.backward(g_dL, grads)
+            plan.backward(g_dL, grads, images=images)
 
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
@@ -389,7 +389,7 @@ def main():
                 R.render_state(scene, m[0], float(w.states.t[s]), cam, w.bg, out=images[s])
                 _, _, dL = R.image_mse(images[s:s + 1], targets, ref_index[s:s + 1], weight=1.0 / S,
                                        want_grad=True)
-                R.render_backward(scene, st1, [cam], w.bg, dL, grads)
+                R.render_backward(scene, st1, [cam], w.bg, dL, grads, images=images[s:s + 1])
             else:
                 R.state_utility(scene, st1, [cam], w.bg)
             torch.cuda.synchronize()

@@ -158,16 +158,21 @@ DGS_API int dgs_render_states_batched(dgs_ctx *ctx, const dgs_scene *scene, cons
                               float *images, dgs_stream stream);
 
 /*
- * Adjoint of dgs_render_states_batched: given dL/dimages [device]
- * [n_states][H][W][3], accumulate (+=) dL/d(parameters) into grads (every
- * pointer [device], scene layout).  Transmittance is recomputed per tile, not
- * stored.  Refinement layers a state did not deliver get exactly zero from that
- * state.  If the context's last forward call had the same arguments (same
- * pointers, counts, times and cameras) its projection and tile lists are
- * reused; the caller must not have changed the scene or the masks since.
+ * Adjoint of dgs_render_states_batched (Section 4 training, Eq. 2): given
+ * dL/dimages [device] [n_states][H][W][3], accumulate (+=) dL/d(parameters)
+ * into grads (every pointer [device], scene layout).  images [device]
+ * [n_states][H][W][3] is the forward's output for the same arguments, or NULL:
+ * with it the adjoint walks each tile once, without it a first walk recomputes
+ * each pixel's final value (same gradients up to float atomic order; images
+ * that are not this forward's output give wrong gradients, undetected).  Either
+ * way transmittance is recomputed per tile, not stored.  Refinement layers a
+ * state did not deliver get exactly zero from that state.  If the context's
+ * last forward call had the same arguments (same pointers, counts, times and
+ * cameras) its projection and tile lists are reused; the caller must not have
+ * changed the scene or the masks since.
  */
 DGS_API int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states,
-                        const dgs_camera *cams, int n_cams, const float *bg,
+                        const dgs_camera *cams, int n_cams, const float *bg, const float *images,
                         const float *dL_dimages, const dgs_scene_grad *grads, dgs_stream stream);
 
 /*
@@ -223,9 +228,10 @@ DGS_API void dgs_plan_destroy(dgs_plan *plan);
 DGS_API const char *dgs_plan_last_error(const dgs_plan *plan);
 /* images [device] [n_states][H][W][3]: as dgs_render_states_batched. */
 DGS_API int dgs_plan_render(dgs_plan *plan, const uint32_t *masks, float *images, dgs_stream stream);
-/* dL/dimages [device]: accumulates into grads as dgs_render_backward. */
-DGS_API int dgs_plan_backward(dgs_plan *plan, const float *dL_dimages, const dgs_scene_grad *grads,
-                              dgs_stream stream);
+/* images (the last dgs_plan_render's output, or NULL) and dL/dimages [device]:
+ * accumulates into grads as dgs_render_backward. */
+DGS_API int dgs_plan_backward(dgs_plan *plan, const float *images, const float *dL_dimages,
+                              const dgs_scene_grad *grads, dgs_stream stream);
 /* mse, psnr [device] [n_states]: as dgs_state_utility (mode DGS_PLAN_UTILITY). */
 DGS_API int dgs_plan_utility(dgs_plan *plan, const uint32_t *masks, double *mse, double *psnr, dgs_stream stream);
 /* As dgs_image_mse with the plan's ref_index; refs [device] [n_refs][H][W][3]. */

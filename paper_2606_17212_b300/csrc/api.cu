@@ -811,8 +811,8 @@ int dgs_render_state(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *mask,
 }
 
 int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states, const dgs_camera *cams,
-                        int n_cams, const float *bg, const float *dL_dimages, const dgs_scene_grad *grads,
-                        dgs_stream stream)
+                        int n_cams, const float *bg, const float *images, const float *dL_dimages,
+                        const dgs_scene_grad *grads, dgs_stream stream)
 {
     if (!ctx) return DGS_E_INVALID_ARG;
     CK(cudaSetDevice(ctx->device));
@@ -840,6 +840,7 @@ int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *
     RasterBwdArgs b;
     b.f = raster_args(ctx, p, scene->n_clusters, bg, L.evals);
     b.dL_dimg = dL_dimages;
+    b.img_fwd = images;
     b.rec_grad = (float4 *)ctx->recgrad.p;
     launch_raster_bwd(b, st);
     GradDev g;
@@ -1099,7 +1100,8 @@ int dgs_plan_render(dgs_plan *P, const uint32_t *masks, float *images, dgs_strea
     return DGS_OK;
 }
 
-int dgs_plan_backward(dgs_plan *P, const float *dL_dimages, const dgs_scene_grad *grads, dgs_stream stream)
+int dgs_plan_backward(dgs_plan *P, const float *images, const float *dL_dimages, const dgs_scene_grad *grads,
+                      dgs_stream stream)
 {
     if (!P) return DGS_E_INVALID_ARG;
     if (!P->rendered) return plan_fail(P, DGS_E_INVALID_ARG, "dgs_plan_backward needs a dgs_plan_render first");
@@ -1115,6 +1117,7 @@ int dgs_plan_backward(dgs_plan *P, const float *dL_dimages, const dgs_scene_grad
     RasterBwdArgs b;
     b.f = plan_raster_args(P);
     b.dL_dimg = dL_dimages;
+    b.img_fwd = images;
     b.rec_grad = (float4 *)ctx->recgrad.p;
     launch_raster_bwd(b, st);
     GradDev g;

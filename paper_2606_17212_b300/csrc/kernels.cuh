@@ -62,6 +62,7 @@ void launch_item_counts(const uint32_t *tile_order, uint32_t n, uint32_t tiles, 
 struct RasterBwdArgs {
     RasterArgs f;
     const float *dL_dimg;         // [S][H][W][3]
+    const float *img_fwd;         // [S][H][W][3] the forward's images, or null (recomputed)
     float4 *rec_grad;             // [nRec][3]: (mx, my, A, B), (C, o, r, g), (b, -, -, -)
 };
 void launch_raster_bwd(const RasterBwdArgs &a, cudaStream_t st);

@@ -394,21 +394,23 @@ __global__ void k_item_counts(const uint32_t *__restrict__ tile_order, uint32_t 
 
 // Per-pixel state of the adjoint walk.
 struct PixB {
-    float T;                  // transmittance before the current entry (pass 2)
+    float T;                  // transmittance before the current entry
     float gc;                 // dL/dC . (colour accumulated so far)
-    float GK;                 // dL/dC . (C_final + T_final bg), from pass 1
+    float GK;                 // dL/dC . (C_final + T_final bg): the forward's pixel
     float g0, g1, g2;         // dL/dC
-    uint32_t stop;            // filtered-stream index where the pixel stopped
-    bool active;
+    bool active;              // in the image, dL/dC != 0 and not stopped yet
 };
 
 // Adjoint of one pixel at one staged entry (inb: in the box and the pixel
-// still active).  With gr = dL/dC . rgb_k and the running gc = dL/dC . C_prefix
-// (including k):  dL/dalpha_k = T_k gr - (GK - gc) / (1 - alpha_k).  Adds to
-// g[9] = (S gpw dx, S gpw dy, S gpw dx^2, S gpw dx dy, S gpw dy^2, dL/do, dL/drgb)
-// with gpw = dL/dpower; the conic and mean gradients are linear in these sums
-// (A, B, C are per Gaussian) and are formed once per Gaussian after the
-// reduction.  Branch free: a skipped entry has alpha = 0 and adds zeros.
+// still active).  The entry at which T (1 - alpha) would drop below 1e-4 stops
+// the pixel without contributing, exactly as in composite(), so the walk ends
+// where the forward ended.  With gr = dL/dC . rgb_k and the running
+// gc = dL/dC . C_prefix (including k):
+//   dL/dalpha_k = T_k gr - (GK - gc) / (1 - alpha_k).
+// Adds to g[9] = (S gpw dx, S gpw dy, S gpw dx^2, S gpw dx dy, S gpw dy^2,
+// dL/do, dL/drgb) with gpw = dL/dpower; the conic and mean gradients are
+// linear in these sums (A, B, C are per Gaussian) and are formed once per
+// Gaussian after the reduction.  Branch free: a skipped entry adds zeros.
 __device__ __forceinline__ bool adjoint(PixB &p, const float4 &r0, const float4 &r1, float b, bool inb, float pcx,
                                         float pcy, float *g)
 {
@@ -417,7 +419,11 @@ __device__ __forceinline__ bool adjoint(PixB &p, const float4 &r0, const float4 
     const float ex = __expf(pw);
     const float araw = __fmul_rn(r1.y, ex);
     const float a0 = fminf(0.99f, araw);
-    const bool ok = inb && pw <= 0.0f && a0 >= (1.0f / 255.0f);
+    const bool hit = inb && pw <= 0.0f && a0 >= (1.0f / 255.0f);
+    const float Tn = __fmul_rn(p.T, __fsub_rn(1.0f, hit ? a0 : 0.0f));
+    const bool stop = Tn < 1e-4f;
+    const bool ok = hit && !stop;
+    p.active = p.active && !stop;
     const float alpha = ok ? a0 : 0.0f;
     const float one_m = __fsub_rn(1.0f, alpha);
     const float wgt = __fmul_rn(alpha, p.T);
@@ -437,7 +443,7 @@ __device__ __forceinline__ bool adjoint(PixB &p, const float4 &r0, const float4 
     g[2] = fmaf(t1, dx, g[2]);
     g[3] = fmaf(t1, dy, g[3]);
     g[4] = fmaf(t2, dy, g[4]);
-    p.T = __fmul_rn(p.T, one_m);
+    p.T = ok ? Tn : p.T;
     return ok;
 }
 
@@ -466,14 +472,18 @@ __device__ __forceinline__ float reduce8_transpose(const float *v, int lane)
     return x;
 }
 
-// Adjoint compositing.  Pass 1 re-runs the forward walk to get each pixel's
-// final colour, final transmittance and stop position (nothing is stored by
-// the forward); pass 2 walks front to back again and, for each included k,
+// Adjoint compositing, one block per (tile, state).  The walk needs each
+// pixel's final value C_final + T_final bg: with IMG it is read from the
+// forward's image (the forward and this walk composite with the same
+// arithmetic, so that value is the one this walk would reach), otherwise a
+// first pass re-runs the forward walk.  Transmittance is never stored: the
+// gradient pass walks front to back recomputing it and, for each included k,
 //   dC/drgb_k   = alpha_k T_k
 //   dC/dalpha_k = rgb_k T_k - (C_after_k + T_final bg) / (1 - alpha_k)
 // with C_after_k = C_final - (colour accumulated up to and including k).
 // Per-Gaussian sums: two pixels per thread, warp transpose reduction, block
 // sum in shared memory, then float4 atomics into the record's gradient.
+template <bool IMG>
 __global__ void __launch_bounds__(RT, 6) k_raster_bwd(RasterBwdArgs b)
 {
     const RasterArgs &a = b.f;
@@ -492,29 +502,44 @@ __global__ void __launch_bounds__(RT, 6) k_raster_bwd(RasterBwdArgs b)
     const float pcx = (float)px + 0.5f, pcy0 = (float)py0 + 0.5f, pcy1 = (float)py1 + 0.5f;
     const uint2 rg = a.ranges[(size_t)v * a.tiles + tile];
 
-    // ---- pass 1: forward walk, recording where each pixel stops
-    Pix f0 = {1.0f, 0.0f, 0.0f, 0.0f, !in0}, f1 = {1.0f, 0.0f, 0.0f, 0.0f, !in1};
-    uint32_t stop0 = 0xffffffffu, stop1 = 0xffffffffu, kept = 0;
-    for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
-        if (__syncthreads_count(!(f0.done && f1.done)) == 0) break;
-        const int nk = stage_batch(a.recs, a.evals, sdep, start, rg.y, ty * TILE, tx * TILE, sm);
-        const int n = sm.cnt[w];
-        for (int i = 0; i < n; ++i) {
-            if (f0.done && f1.done) break;
-            const int k = sm.list[w][i];
-            const float4 r0 = sm.r0[k], r1 = sm.r1[k];
-            const float b = sm.r2[k].x;
-            const int4 bx = sm.box[k];
-            const bool xin = in_range(px, bx.x, bx.y);
-            if (composite(f0, r0, r1, b, xin && in_range(py0, bx.z, bx.w), pcx, pcy0)) stop0 = kept + (uint32_t)k;
-            if (composite(f1, r0, r1, b, xin && in_range(py1, bx.z, bx.w), pcx, pcy1)) stop1 = kept + (uint32_t)k;
+    // ---- final pixel values
+    float fin[2][3];
+    if (IMG) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            fin[h][0] = fin[h][1] = fin[h][2] = 0.0f;
+            if (h ? in1 : in0) {
+                const float *ip = b.img_fwd + (((size_t)s * a.H + (h ? py1 : py0)) * a.W + px) * 3;
+                fin[h][0] = ip[0]; fin[h][1] = ip[1]; fin[h][2] = ip[2];
+            }
         }
-        kept += (uint32_t)nk;
+    } else {
+        Pix f[2] = {{1.0f, 0.0f, 0.0f, 0.0f, !in0}, {1.0f, 0.0f, 0.0f, 0.0f, !in1}};
+        for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
+            if (__syncthreads_count(!(f[0].done && f[1].done)) == 0) break;
+            stage_batch(a.recs, a.evals, sdep, start, rg.y, ty * TILE, tx * TILE, sm);
+            const int n = sm.cnt[w];
+            for (int i = 0; i < n; ++i) {
+                if (f[0].done && f[1].done) break;
+                const int k = sm.list[w][i];
+                const float4 r0 = sm.r0[k], r1 = sm.r1[k];
+                const float bb = sm.r2[k].x;
+                const int4 bx = sm.box[k];
+                const bool xin = in_range(px, bx.x, bx.y);
+                composite(f[0], r0, r1, bb, xin && in_range(py0, bx.z, bx.w), pcx, pcy0);
+                composite(f[1], r0, r1, bb, xin && in_range(py1, bx.z, bx.w), pcx, pcy1);
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            fin[h][0] = __fmaf_rn(f[h].T, a.bg0, f[h].c0);
+            fin[h][1] = __fmaf_rn(f[h].T, a.bg1, f[h].c1);
+            fin[h][2] = __fmaf_rn(f[h].T, a.bg2, f[h].c2);
+        }
     }
     PixB q[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const Pix &f = h ? f1 : f0;
         const bool in = h ? in1 : in0;
         const int py = h ? py1 : py0;
         PixB &p = q[h];
@@ -524,13 +549,11 @@ __global__ void __launch_bounds__(RT, 6) k_raster_bwd(RasterBwdArgs b)
             const float *gp = b.dL_dimg + (((size_t)s * a.H + py) * a.W + px) * 3;
             p.g0 = gp[0]; p.g1 = gp[1]; p.g2 = gp[2];
         }
-        p.GK = p.g0 * fmaf(f.T, a.bg0, f.c0) + p.g1 * fmaf(f.T, a.bg1, f.c1) + p.g2 * fmaf(f.T, a.bg2, f.c2);
-        p.stop = h ? stop1 : stop0;
-        p.active = in && p.stop > 0 && (p.g0 != 0.0f || p.g1 != 0.0f || p.g2 != 0.0f);
+        p.GK = p.g0 * fin[h][0] + p.g1 * fin[h][1] + p.g2 * fin[h][2];
+        p.active = in && (p.g0 != 0.0f || p.g1 != 0.0f || p.g2 != 0.0f);
     }
 
-    // ---- pass 2: gradients
-    kept = 0;
+    // ---- gradient pass
     for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
         if (__syncthreads_count(q[0].active || q[1].active) == 0) break;
         const int nk = stage_batch(a.recs, a.evals, sdep, start, rg.y, ty * TILE, tx * TILE, sm);
@@ -544,15 +567,14 @@ __global__ void __launch_bounds__(RT, 6) k_raster_bwd(RasterBwdArgs b)
                 for (int j = 0; j < 9; ++j) g[j] = 0.0f;
                 bool contrib = false;
                 const float4 r0 = sm.r0[k], r1 = sm.r1[k];
-                const float b = sm.r2[k].x;
+                const float bb = sm.r2[k].x;
                 const int4 bx = sm.box[k];
                 const bool xin = in_range(px, bx.x, bx.y);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     PixB &p = q[h];
-                    p.active = p.active && kept + (uint32_t)k < p.stop;
                     const bool inb = p.active && xin && in_range(h ? py1 : py0, bx.z, bx.w);
-                    contrib |= adjoint(p, r0, r1, b, inb, pcx, h ? pcy1 : pcy0, g);
+                    contrib |= adjoint(p, r0, r1, bb, inb, pcx, h ? pcy1 : pcy0, g);
                 }
                 if (__ballot_sync(0xffffffffu, contrib)) {
                     const float x = reduce8_transpose(g, lane);
@@ -580,7 +602,6 @@ __global__ void __launch_bounds__(RT, 6) k_raster_bwd(RasterBwdArgs b)
                 atomicAdd(dst + 2, make_float4(x[8], 0.0f, 0.0f, 0.0f));
             }
         }
-        kept += (uint32_t)nk;
     }
 }
 
@@ -726,8 +747,9 @@ void launch_raster_bwd(const RasterBwdArgs &b, cudaStream_t st)
 {
     if (b.f.S == 0 || b.f.tiles == 0) return;
     const unsigned grid = b.f.tiles * (unsigned)b.f.S;
-    ProfScope ps_("raster_bwd", st);
-    k_raster_bwd<<<grid, RT, 0, st>>>(b);
+    ProfScope ps_(b.img_fwd ? "raster_bwd" : "raster_bwd_2pass", st);
+    if (b.img_fwd) k_raster_bwd<true><<<grid, RT, 0, st>>>(b);
+    else k_raster_bwd<false><<<grid, RT, 0, st>>>(b);
     count_launch();
 }
 

@@ -74,7 +74,7 @@ def lib():
         L.dgs_render_state.argtypes = [P, ctypes.POINTER(Scene_t), P, F, ctypes.POINTER(Camera_t), P, P, P]
         L.dgs_render_states_batched.argtypes = [P, ctypes.POINTER(Scene_t), ctypes.POINTER(States_t),
                                                 P, I, P, P, P]
-        L.dgs_render_backward.argtypes = [P, ctypes.POINTER(Scene_t), ctypes.POINTER(States_t), P, I, P, P,
+        L.dgs_render_backward.argtypes = [P, ctypes.POINTER(Scene_t), ctypes.POINTER(States_t), P, I, P, P, P,
                                           ctypes.POINTER(SceneGrad_t), P]
         L.dgs_state_utility.argtypes = [P, ctypes.POINTER(Scene_t), ctypes.POINTER(States_t), P, I, P, P, P, P]
         L.dgs_image_mse.argtypes = [P, P, P, P, I, I, I, I, F, P, P, P, P]
@@ -97,7 +97,7 @@ def lib():
         L.dgs_plan_last_error.argtypes = [P]
         L.dgs_plan_last_error.restype = ctypes.c_char_p
         L.dgs_plan_render.argtypes = [P, P, P, P]
-        L.dgs_plan_backward.argtypes = [P, P, ctypes.POINTER(SceneGrad_t), P]
+        L.dgs_plan_backward.argtypes = [P, P, P, ctypes.POINTER(SceneGrad_t), P]
         L.dgs_plan_utility.argtypes = [P, P, P, P, P]
         L.dgs_plan_image_mse.argtypes = [P, P, P, F, P, P, P, P]
         L.dgs_plan_status.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), P]
@@ -275,14 +275,17 @@ class Renderer:
         return out
 
     def render_backward(self, scene: DeviceScene, states: DeviceStates, cams, bg, dL_dimages, grads=None,
-                        stream=None):
+                        stream=None, images=None):
+        """Adjoint of render_states_batched.  ``images``: that forward's output
+        (one walk per tile) or None (a first walk recomputes final pixels)."""
         if grads is None:
             grads = scene.zeros_like_grads()
         bgv = (ctypes.c_float * 3)(*[float(x) for x in bg])
         g = SceneGrad_t(*[(_ptr(grads[k]) if grads[k].numel() else None) for k in SCENE_FIELDS])
         sc, st, ca = scene.struct(), states.struct(), camera_array(cams)
+        img = None if images is None else images.contiguous()
         self._check(self._lib.dgs_render_backward(self.h, ctypes.byref(sc), ctypes.byref(st), ca, len(cams), bgv,
-                                                  _ptr(dL_dimages.contiguous()), ctypes.byref(g),
+                                                  _ptr(img), _ptr(dL_dimages.contiguous()), ctypes.byref(g),
                                                   _stream(stream)), "dgs_render_backward")
         return grads
 
@@ -323,11 +326,14 @@ def render_function():
         def forward(ctx, renderer, scene, states, cams, bg, *tensors):
             out = renderer.render_states_batched(scene, states, cams, bg)
             ctx.renderer, ctx.scene, ctx.states, ctx.cams, ctx.bg = renderer, scene, states, cams, bg
+            ctx.save_for_backward(out)
             return out
 
         @staticmethod
         def backward(ctx, grad_out):
-            grads = ctx.renderer.render_backward(ctx.scene, ctx.states, ctx.cams, ctx.bg, grad_out.contiguous())
+            (out,) = ctx.saved_tensors
+            grads = ctx.renderer.render_backward(ctx.scene, ctx.states, ctx.cams, ctx.bg, grad_out.contiguous(),
+                                                 images=out)
             return (None, None, None, None, None) + tuple(grads[k] for k in SCENE_FIELDS)
 
     return RenderStates
@@ -397,9 +403,10 @@ class Plan:
         self._check(self._lib.dgs_plan_render(self.h, _ptr(masks), _ptr(images), _stream(stream)), "dgs_plan_render")
         return images
 
-    def backward(self, dL, grads, stream=None):
+    def backward(self, dL, grads, stream=None, images=None):
+        """Adjoint of the last render; ``images``: its output, or None."""
         g = SceneGrad_t(*[(_ptr(grads[k]) if grads[k].numel() else None) for k in SCENE_FIELDS])
-        self._check(self._lib.dgs_plan_backward(self.h, _ptr(dL), ctypes.byref(g), _stream(stream)),
+        self._check(self._lib.dgs_plan_backward(self.h, _ptr(images), _ptr(dL), ctypes.byref(g), _stream(stream)),
                     "dgs_plan_backward")
         return grads
 

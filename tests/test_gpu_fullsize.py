@@ -78,8 +78,8 @@ def test_fwdbwd_250k_full_size(R, torch):
         g = oracle.render_backward(w.scene, D[s], float(w.states.t[s]), w.cams[int(w.states.cam[s])], w.bg,
                                    dL[s].astype(np.float64))
         ref = g if ref is None else {k: ref[k] + g[k] for k in ref}
-    R.render_states_batched(sc, st, w.cams, w.bg)
-    grads = R.render_backward(sc, st, w.cams, w.bg, torch.from_numpy(dL).cuda())
+    imgs_t = R.render_states_batched(sc, st, w.cams, w.bg)
+    grads = R.render_backward(sc, st, w.cams, w.bg, torch.from_numpy(dL).cuda(), images=imgs_t)
     for k in dgs.SCENE_FIELDS:
         gr = ref[k]
         if gr.size == 0:

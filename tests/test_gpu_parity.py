@@ -190,8 +190,10 @@ def _grad_case(seed=0, sh=0):
     return sc, w.states, cams
 
 
-@pytest.mark.parametrize("sh", [0, 3])
-def test_backward_matches_oracle_adjoint(R, torch, sh):
+@pytest.mark.parametrize("sh,with_images", [(0, False), (0, True), (3, False), (3, True)])
+def test_backward_matches_oracle_adjoint(R, torch, sh, with_images):
+    """Adjoint vs the oracle's, with the forward images given (one walk per
+    tile) and without (final pixel values recomputed by a first walk)."""
     sc_h, states, cams = _grad_case(sh=sh)
     bg = np.array([0.1, 0.2, 0.3], np.float32)
     rng = np.random.default_rng(3)
@@ -208,8 +210,9 @@ def test_backward_matches_oracle_adjoint(R, torch, sh):
         ref = g if ref is None else {k: ref[k] + g[k] for k in ref}
     sc = dgs.DeviceScene.from_host(sc_h)
     st = dgs.DeviceStates.from_host(states)
-    R.render_states_batched(sc, st, cams, bg)
-    grads = R.render_backward(sc, st, cams, bg, torch.from_numpy(dL.astype(np.float32)).cuda())
+    imgs = R.render_states_batched(sc, st, cams, bg)
+    grads = R.render_backward(sc, st, cams, bg, torch.from_numpy(dL.astype(np.float32)).cuda(),
+                              images=imgs if with_images else None)
     for k in dgs.SCENE_FIELDS:
         gg = grads[k].cpu().numpy().astype(np.float64)
         gr = ref[k]

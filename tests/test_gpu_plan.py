@@ -42,8 +42,8 @@ def test_plan_render_backward_match_and_replay_in_graph(R, torch):
     assert torch.equal(images, ref)
     rng = np.random.default_rng(0)
     dL = torch.from_numpy(rng.normal(size=(S, H, W, 3)).astype(np.float32)).cuda()
-    g_plan = plan.backward(dL, sc.zeros_like_grads())
-    g_ref = R.render_backward(sc, st, w.cams, w.bg, dL)
+    g_plan = plan.backward(dL, sc.zeros_like_grads(), images=images)
+    g_ref = R.render_backward(sc, st, w.cams, w.bg, dL)          # final pixels recomputed
     for k in dgs.SCENE_FIELDS:
         a, b = g_plan[k], g_ref[k]
         if b.numel():
@@ -54,14 +54,14 @@ def test_plan_render_backward_match_and_replay_in_graph(R, torch):
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):
         plan.render(masks, images)
-        plan.backward(dL, grads)
+        plan.backward(dL, grads, images=images)
     torch.cuda.current_stream().wait_stream(side)
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
         for g in grads.values():
             g.zero_()
         plan.render(masks, images)
-        plan.backward(dL, grads)
+        plan.backward(dL, grads, images=images)
     for seed in (1, 2):
         new = _masks(torch, w, seed)
         masks.copy_(new)

@@ -276,7 +276,7 @@ DGS_API int dgs_debug_tile_lists(dgs_ctx *ctx, uint32_t *n_rec, uint32_t *n_ent,
  *     Its only scratch is a fixed file-scope device array of
  *     DGS_NOALLOC_MAX_PARTS doubles (512 KiB) that every GPU which loads the
  *     library holds until the process exits.  The call fails with
- *     DGS_E_SCRATCH, launching nothing, when S * ceil(3 H W / 4096) exceeds
+ *     DGS_E_SCRATCH, launching nothing, when S * ceil(H W / 1024) exceeds
  *     DGS_NOALLOC_MAX_PARTS, and with DGS_E_INVALID_ARG when S > 65535.
  *   - The first call on each device looks up the scratch array's device
  *     address (cudaGetSymbolAddress) with that device current; make that first

@@ -377,7 +377,7 @@ int prepare(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *masks, const P
     launch_tile_costs((const uint2 *)ctx->ranges.p, (uint32_t)vt, (uint32_t *)ctx->tck0.p, (uint32_t *)ctx->tcv0.p,
                       ctx->sms, st);
     CK(radix_sort_pairs((uint32_t *)ctx->tck0.p, (uint32_t *)ctx->tcv0.p, (uint32_t *)ctx->tck1.p,
-                        (uint32_t *)ctx->tcv1.p, vt, 32, ctx->sortws.p, st, &alt));
+                        (uint32_t *)ctx->tcv1.p, vt, 16, ctx->sortws.p, st, &alt));
     out.tile_order = alt ? (uint32_t *)ctx->tcv1.p : (uint32_t *)ctx->tcv0.p;
     CK(cudaGetLastError());
     return DGS_OK;
@@ -649,7 +649,7 @@ int prepare_dev(dgs_plan *P, const uint32_t *masks, bool force_full, cudaStream_
     launch_tile_costs((const uint2 *)ctx->ranges.p, (uint32_t)vt, (uint32_t *)ctx->tck0.p, (uint32_t *)ctx->tcv0.p,
                       ctx->sms, st);
     CK(radix_sort_pairs((uint32_t *)ctx->tck0.p, (uint32_t *)ctx->tcv0.p, (uint32_t *)ctx->tck1.p,
-                        (uint32_t *)ctx->tcv1.p, vt, 32, ctx->sortws.p, st, &alt));
+                        (uint32_t *)ctx->tcv1.p, vt, 16, ctx->sortws.p, st, &alt));
     out.tile_order = alt ? (uint32_t *)ctx->tcv1.p : (uint32_t *)ctx->tcv0.p;
     out.nRec = P->R_cap;
     out.nEnt = P->E_cap;
@@ -923,7 +923,7 @@ int dgs_image_mse(dgs_ctx *ctx, const float *images, const float *refs, const in
         if (ref_index[s] < 0 || ref_index[s] >= n_refs)
             return fail(ctx, DGS_E_INVALID_ARG, "ref_index[%d] = %d out of range", s, ref_index[s]);
     const size_t per = (size_t)H * W * 3;
-    const int parts = (int)((per + 4095) / 4096);
+    const int parts = mse_parts(H, W);
     TRY(ensure(ctx, ctx->refidx, sizeof(int32_t) * (size_t)S, st));
     TRY(ensure(ctx, ctx->partial, sizeof(double) * (size_t)S * parts, st));
     TRY(ensure_stage(ctx, sizeof(int32_t) * (size_t)S, st));
@@ -1014,7 +1014,7 @@ int dgs_plan_create(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *stat
         }
         if (ref_index) {
             P->n_refs = n_refs;
-            P->image_parts = (int)((img + 4095) / 4096);
+            P->image_parts = mse_parts(p.H, p.W);
             if ((r = ensure(w, w->refidx, 4 * (size_t)p.S_user, st)) != DGS_OK) break;
             CK(cudaMemcpy(w->refidx.p, ref_index, 4 * (size_t)p.S_user, cudaMemcpyHostToDevice));
             if ((r = ensure(w, w->partial, sizeof(double) * (size_t)p.S_user *

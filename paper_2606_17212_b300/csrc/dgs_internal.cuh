@@ -56,6 +56,25 @@ struct GradDev {
     float *mu0, *u, *ls, *quat, *logit, *colour, *res;
 };
 
+// ------------------------------------------------------------------ MSE
+// Per-image squared error (Eq. 3's D = MSE): each pixel's squared RGB error is
+// formed in FP32 with fixed rounding and the sum over pixels is accumulated in
+// FP64, in partial sums of MSE_CHUNK_PIX pixels.  B300 issues FP64 at a small
+// fraction of its FP32 rate, so FP64 is spent only where precision needs it:
+// on the sum of up to millions of terms, not on three differences per pixel
+// (relative error of one pixel's term below 5 * 2^-24 to first order: one
+// rounding in each difference, squared, plus the multiply and two fused adds).
+constexpr int MSE_CHUNK_PIX = 1024;
+__host__ __device__ inline int mse_parts(int H, int W)
+{
+    return (int)(((size_t)H * (size_t)W + MSE_CHUNK_PIX - 1) / MSE_CHUNK_PIX);
+}
+__device__ __forceinline__ float pixel_sq_err(float x0, float x1, float x2, float y0, float y1, float y2)
+{
+    const float d0 = __fsub_rn(x0, y0), d1 = __fsub_rn(x1, y1), d2 = __fsub_rn(x2, y2);
+    return __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, __fmul_rn(d0, d0)));
+}
+
 // ------------------------------------------------------------------ launches
 // Every kernel launch of the library goes through this counter so that the
 // number of device launches per call can be reported.

@@ -69,6 +69,7 @@ void launch_raster_bwd(const RasterBwdArgs &a, cudaStream_t st);
 
 void launch_mse_reduce(const double *partial, int S, int parts, double inv_count, double *mse, double *psnr,
                        cudaStream_t st);
+// parts = mse_parts(H, W) partial sums per image
 void launch_image_mse(const float *images, const float *refs, const int32_t *ref_index, int S, int H, int W,
                       float weight, double *partial, int parts, float *dL, cudaStream_t st);
 

@@ -18,7 +18,6 @@
 namespace dgs {
 namespace {
 
-constexpr int NOALLOC_CHUNK = 4096;                       // values per partial sum
 constexpr int NOALLOC_MAX_PARTS = DGS_NOALLOC_MAX_PARTS;  // doubles of scratch
 
 // Shared scratch of every call on a device; the last call's partial sums stay
@@ -46,29 +45,32 @@ cudaError_t scratch_address(int device, double **out)
 
 // Variant of the MSE partial-sum kernel: reads the reference index from device
 // memory and checks it (an out-of-range index turns that image's MSE into NaN).
-// Every (image, chunk) partial is written exactly once per call, so the shared
-// scratch needs no clearing between calls.
+// Same per-pixel FP32 squared error and FP64 chunk sums of MSE_CHUNK_PIX
+// pixels as dgs_image_mse.  Every (image, chunk) partial is written exactly
+// once per call, so the shared scratch needs no clearing between calls.
 __global__ void __launch_bounds__(256) k_image_mse_noalloc(const float *__restrict__ images,
                                                            const float *__restrict__ refs,
                                                            const int32_t *__restrict__ ref_index, int n_refs,
-                                                           size_t per_image, float gscale, double *partial,
+                                                           size_t npix, float gscale, double *partial,
                                                            int parts, float *__restrict__ dL)
 {
     __shared__ double wsum[8];
     const int s = blockIdx.y;
     const int r = ref_index[s];
     const bool ok = r >= 0 && r < n_refs;
-    const float *im = images + (size_t)s * per_image;
-    const float *rf = refs + (size_t)(ok ? r : 0) * per_image;
+    const float *im = images + (size_t)s * npix * 3;
+    const float *rf = refs + (size_t)(ok ? r : 0) * npix * 3;
     double se = 0.0;
-    const size_t base = (size_t)blockIdx.x * NOALLOC_CHUNK;
-    for (int k = 0; k < NOALLOC_CHUNK / 256; ++k) {
-        const size_t j = base + (size_t)k * 256 + threadIdx.x;
-        if (j < per_image) {
-            const float x = im[j], y = ok ? rf[j] : 0.0f;
-            const double d = (double)x - (double)y;
-            se += d * d;
-            if (dL) dL[(size_t)s * per_image + j] = ok ? gscale * (x - y) : __int_as_float(0x7fc00000);
+    const size_t base = (size_t)blockIdx.x * MSE_CHUNK_PIX;
+    for (int k = 0; k < MSE_CHUNK_PIX / 256; ++k) {
+        const size_t p = base + (size_t)k * 256 + threadIdx.x;
+        if (p < npix) {
+            float x[3], y[3];
+            for (int c = 0; c < 3; ++c) { x[c] = im[3 * p + c]; y[c] = ok ? rf[3 * p + c] : 0.0f; }
+            se += (double)pixel_sq_err(x[0], x[1], x[2], y[0], y[1], y[2]);
+            if (dL)
+                for (int c = 0; c < 3; ++c)
+                    dL[((size_t)s * npix + p) * 3 + c] = ok ? gscale * (x[c] - y[c]) : __int_as_float(0x7fc00000);
         }
     }
 #pragma unroll
@@ -109,10 +111,10 @@ extern "C" int dgs_image_mse_noalloc(const float *images, const float *refs, con
     if (S < 0 || S > 65535 || H < 1 || W < 1 || n_refs < 1) return DGS_E_INVALID_ARG;
     if (S == 0) return DGS_OK;
     if (!images || !refs || !ref_index || !mse) return DGS_E_INVALID_ARG;
-    const size_t per = (size_t)H * (size_t)W * 3;
-    const size_t parts = (per + NOALLOC_CHUNK - 1) / NOALLOC_CHUNK;
+    const size_t npix = (size_t)H * (size_t)W, per = npix * 3;
+    const size_t parts = (npix + MSE_CHUNK_PIX - 1) / MSE_CHUNK_PIX;
     if (parts > (size_t)NOALLOC_MAX_PARTS || (size_t)S * parts > (size_t)NOALLOC_MAX_PARTS)
-        return DGS_E_SCRATCH;   // S * ceil(3HW / 4096) must not exceed DGS_NOALLOC_MAX_PARTS
+        return DGS_E_SCRATCH;   // S * ceil(HW / 1024) must not exceed DGS_NOALLOC_MAX_PARTS
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= MAX_DEVICES) return DGS_E_CUDA;
     double *partial = nullptr;
@@ -120,7 +122,7 @@ extern "C" int dgs_image_mse_noalloc(const float *images, const float *refs, con
     cudaStream_t st = (cudaStream_t)stream;
     const float gscale = (float)(2.0 * (double)weight / (double)per);
     dim3 grid((unsigned)parts, (unsigned)S);
-    k_image_mse_noalloc<<<grid, 256, 0, st>>>(images, refs, ref_index, n_refs, per, gscale, partial, (int)parts,
+    k_image_mse_noalloc<<<grid, 256, 0, st>>>(images, refs, ref_index, n_refs, npix, gscale, partial, (int)parts,
                                               dL_dimages);
     count_launch();
     const int threads = 256, blocks = (S * 32 + threads - 1) / threads;

@@ -157,8 +157,23 @@ __global__ void k_tile_count(const Rec *__restrict__ recs, const uint32_t *__res
                              const uint32_t *__restrict__ n_dev, uint32_t *__restrict__ counts)
 {
     const uint32_t n = live_n(n_cap, n_dev);
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n_cap; j += gridDim.x * blockDim.x) {
-        counts[j] = j < n ? rec_tiles(rec_tail(recs, order[j])) : 0u;
+    const uint32_t T = gridDim.x * blockDim.x;
+    // four records per thread per step, every gather issued before any use
+    for (uint32_t j0 = blockIdx.x * blockDim.x + threadIdx.x; j0 < n_cap; j0 += 4u * T) {
+        uint32_t slot[4];
+        float4 q[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t j = j0 + (uint32_t)k * T;
+            slot[k] = j < n ? __ldg(order + j) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q[k] = slot[k] != 0xffffffffu ? rec_tail(recs, slot[k]) : make_float4(0, 0, 0, 0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t j = j0 + (uint32_t)k * T;
+            if (j < n_cap) counts[j] = slot[k] != 0xffffffffu ? rec_tiles(q[k]) : 0u;
+        }
     }
 }
 
@@ -245,10 +260,25 @@ __global__ void k_ranges(const uint32_t *__restrict__ keys, uint32_t n_cap, cons
                          uint2 *__restrict__ ranges)
 {
     const uint32_t n = live_n(n_cap, n_dev);
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        const uint32_t k = keys[e];
-        if (e == 0 || keys[e - 1] != k) ranges[k].x = e;
-        if (e == n - 1 || keys[e + 1] != k) ranges[k].y = e + 1;
+    const uint32_t T = gridDim.x * blockDim.x;
+    // four keys per thread per step with their neighbours, all loads issued first
+    for (uint32_t e0 = blockIdx.x * blockDim.x + threadIdx.x; e0 < n; e0 += 4u * T) {
+        uint32_t k[4], prev[4], next[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t e = e0 + (uint32_t)u * T;
+            const bool ok = e < n;
+            k[u] = ok ? __ldg(keys + e) : 0u;
+            prev[u] = ok && e > 0 ? __ldg(keys + e - 1) : ~k[u];
+            next[u] = ok && e + 1 < n ? __ldg(keys + e + 1) : ~k[u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t e = e0 + (uint32_t)u * T;
+            if (e >= n) continue;
+            if (prev[u] != k[u]) ranges[k[u]].x = e;
+            if (next[u] != k[u]) ranges[k[u]].y = e + 1;
+        }
     }
 }
 

@@ -348,9 +348,7 @@ __global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a, WorkQueue q)
                     const int py = h ? py1 : py0;
                     if (h ? in1 : in0) {
                         const float *rp = rbase + ((size_t)py * a.W + px) * 3;
-                        const double d0 = (double)o[h][0] - (double)rp[0], d1 = (double)o[h][1] - (double)rp[1];
-                        const double d2 = (double)o[h][2] - (double)rp[2];
-                        se += d0 * d0 + d1 * d1 + d2 * d2;
+                        se += (double)pixel_sq_err(o[h][0], o[h][1], o[h][2], rp[0], rp[1], rp[2]);
                     }
                 }
 #pragma unroll
@@ -374,13 +372,14 @@ __global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a, WorkQueue q)
     }
 }
 
-// Cost key of each (view group, tile): ascending key = descending entry count.
+// Cost key of each (view group, tile), 16 bits: ascending key = descending
+// entry count (counts above 65535 tie; the order only schedules work).
 __global__ void k_tile_costs(const uint2 *__restrict__ ranges, uint32_t n, uint32_t *__restrict__ keys,
                              uint32_t *__restrict__ vals)
 {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint2 r = ranges[i];
-        keys[i] = 0xffffffffu - (r.y - r.x);
+        keys[i] = 0xffffu - min(r.y - r.x, 0xffffu);
         vals[i] = i;
     }
 }
@@ -622,26 +621,41 @@ __global__ void k_mse_reduce(const double *__restrict__ partial, int S, int part
     }
 }
 
-// Squared-error partial sums of image s vs refs[ref_index[s]] over one chunk of
-// 256 * 16 values, and optionally dL/dimage = weight * 2 (image - ref) / count.
+// Squared-error partial sum of image s vs refs[ref_index[s]] over one chunk
+// of MSE_CHUNK_PIX pixels (four per thread), and optionally
+// dL/dimage = weight * 2 (image - ref) / (3 H W).
 __global__ void __launch_bounds__(256) k_image_mse(const float *__restrict__ images, const float *__restrict__ refs,
-                                                   const int32_t *__restrict__ ref_index, size_t per_image,
+                                                   const int32_t *__restrict__ ref_index, size_t npix,
                                                    float gscale, double *__restrict__ partial, int parts,
                                                    float *__restrict__ dL)
 {
     __shared__ double wsum[8];
     const int s = blockIdx.y;
-    const float *im = images + (size_t)s * per_image;
-    const float *rf = refs + (size_t)ref_index[s] * per_image;
+    const float *im = images + (size_t)s * npix * 3;
+    const float *rf = refs + (size_t)ref_index[s] * npix * 3;
+    float x[4][3], y[4][3];
+    const size_t base = (size_t)blockIdx.x * MSE_CHUNK_PIX + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const size_t p = base + (size_t)k * 256;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { x[k][c] = 0.0f; y[k][c] = 0.0f; }
+        if (p < npix) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) { x[k][c] = __ldg(im + 3 * p + c); y[k][c] = __ldg(rf + 3 * p + c); }
+        }
+    }
     double se = 0.0;
-    const size_t base = (size_t)blockIdx.x * 4096;
-    for (int k = 0; k < 16; ++k) {
-        const size_t j = base + (size_t)k * 256 + threadIdx.x;
-        if (j < per_image) {
-            const float x = im[j], y = rf[j];
-            const double d = (double)x - (double)y;
-            se += d * d;
-            if (dL) dL[(size_t)s * per_image + j] = gscale * (x - y);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const size_t p = base + (size_t)k * 256;
+        if (p < npix) {
+            se += (double)pixel_sq_err(x[k][0], x[k][1], x[k][2], y[k][0], y[k][1], y[k][2]);
+            if (dL) {
+                float *d = dL + ((size_t)s * npix + p) * 3;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) d[c] = gscale * (x[k][c] - y[k][c]);
+            }
         }
     }
 #pragma unroll
@@ -767,11 +781,11 @@ void launch_image_mse(const float *images, const float *refs, const int32_t *ref
                       float weight, double *partial, int parts, float *dL, cudaStream_t st)
 {
     if (S == 0) return;
-    const size_t per = (size_t)H * W * 3;
-    const float gscale = (float)(2.0 * (double)weight / (double)per);
+    const size_t npix = (size_t)H * W;
+    const float gscale = (float)(2.0 * (double)weight / (double)(npix * 3));
     dim3 grid((unsigned)parts, (unsigned)S);
     ProfScope ps_("image_mse", st);
-    k_image_mse<<<grid, 256, 0, st>>>(images, refs, ref_index, per, gscale, partial, parts, dL);
+    k_image_mse<<<grid, 256, 0, st>>>(images, refs, ref_index, npix, gscale, partial, parts, dL);
     count_launch();
 }
 

@@ -3,10 +3,10 @@
 // Both are HBM-bound streaming passes.  The radix sort is the classic
 // three-step LSD pass per 8-bit digit: per-block digit histogram, exclusive
 // scan of the digit-major histogram table, stable scatter.  Stability inside
-// a block comes from giving every warp a contiguous run of 512 items that it
-// ranks in index order with __match_any_sync, then offsetting warps by the
-// digit counts of the warps before them.  The scatter first reorders the
-// block's 4096 items by digit in shared memory, then writes each digit run
+// a block comes from giving every warp a contiguous run of RS_ITEMS * 32 items
+// that it ranks in index order (peers by eight ballots), then offsetting warps by
+// the digit counts of the warps before them.  The scatter first reorders the
+// block's RS_CHUNK items by digit in shared memory, then writes each digit run
 // with consecutive threads on consecutive slots (coalesced stores).
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -140,21 +140,50 @@ __device__ __forceinline__ size_t live_count(size_t n, const uint32_t *n_dev)
     return n_dev ? min(n, (size_t)*n_dev) : n;
 }
 
-__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t *keys, size_t n_cap, const uint32_t *n_dev,
-                                                        int shift, uint32_t mask, uint32_t *hist, uint32_t nblocks)
+// Per-block digit histogram.  All of a thread's keys are loaded before any
+// counting (RS_ITEMS loads in flight per thread); each warp counts into its
+// own row of shared counters so warps never contend, then thread d sums the
+// rows for digit d.
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t *__restrict__ keys, size_t n_cap,
+                                                        const uint32_t *n_dev, int shift, uint32_t mask,
+                                                        uint32_t *__restrict__ hist, uint32_t nblocks)
 {
     const size_t n = live_count(n_cap, n_dev);
-    __shared__ uint32_t h[RS_RADIX];
-    h[threadIdx.x] = 0;
-    __syncthreads();
+    __shared__ uint32_t h[RS_WARPS][RS_RADIX];
+    const int w = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < RS_WARPS * RS_RADIX; d += RS_THREADS) (&h[0][0])[d] = 0;
     const size_t base = (size_t)blockIdx.x * RS_CHUNK;
-#pragma unroll 4
+    uint32_t key[RS_ITEMS];
+#pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
-        size_t i = base + (size_t)k * RS_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
+        const size_t i = base + (size_t)k * RS_THREADS + threadIdx.x;
+        key[k] = i < n ? __ldg(keys + i) : 0u;
     }
     __syncthreads();
-    hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        const size_t i = base + (size_t)k * RS_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&h[w][(key[k] >> shift) & mask], 1u);
+    }
+    __syncthreads();
+    uint32_t tot = 0;
+#pragma unroll
+    for (int ww = 0; ww < RS_WARPS; ++ww) tot += h[ww][threadIdx.x];
+    hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = tot;
+}
+
+// Lanes of the warp whose digit equals this lane's (8-bit digits): one ballot
+// per digit bit, restricted to the lanes holding a valid item.
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d, uint32_t valid)
+{
+    uint32_t peers = valid;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bal : ~bal;
+    }
+    return peers;
 }
 
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t *kin, const uint32_t *vin,
@@ -174,14 +203,23 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t *kin, 
     const size_t base = (size_t)blockIdx.x * RS_CHUNK + (size_t)w * (RS_ITEMS * 32);
     const uint32_t lt = (1u << lane) - 1u;
     uint32_t key[RS_ITEMS], val[RS_ITEMS], rank[RS_ITEMS];
+    // every load of the tile is issued before the ranking chain starts
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        const size_t i = base + (size_t)k * 32 + lane;
+        key[k] = i < n ? __ldg(kin + i) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        const size_t i = base + (size_t)k * 32 + lane;
+        val[k] = i < n ? __ldg(vin + i) : 0u;
+    }
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
         size_t i = base + (size_t)k * 32 + lane;
         bool ok = i < n;
-        key[k] = ok ? kin[i] : 0u;
-        val[k] = ok ? vin[i] : 0u;
-        uint32_t d = ok ? ((key[k] >> shift) & mask) : (RS_RADIX + lane);
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t d = ok ? ((key[k] >> shift) & mask) : 0u;
+        uint32_t peers = digit_peers(d, __ballot_sync(0xffffffffu, ok));
         uint32_t before = ok ? wh[w][d] : 0u;
         __syncwarp();
         int leader = __ffs(peers) - 1;
@@ -260,6 +298,12 @@ cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t 
 {
     *result_in_alt = false;
     if (n == 0 || (n <= 1 && !n_dev) || bits <= 0) return cudaSuccess;
+    static bool carveout_set = false;   // the scatter's shared memory allows 8 blocks per SM at full carveout
+    if (!carveout_set) {
+        cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        carveout_set = true;
+    }
     size_t nb = blocks_for(n, RS_CHUNK);
     uint32_t *hist = (uint32_t *)ws;
     void *scan_ws = (char *)ws + align_up((size_t)RS_RADIX * nb * sizeof(uint32_t));

@@ -171,7 +171,17 @@ def test_image_mse_and_gradient(R, torch):
     mse, psnr, dL = R.image_mse(ta, tb, idx, weight=0.25, want_grad=True)
     for s in range(3):
         d = a[s].astype(np.float64) - b[idx[s]].astype(np.float64)
-        assert mse[s].item() == pytest.approx(np.mean(d * d), rel=1e-12)
+        # each pixel's squared RGB error is an FP32 value within 5 * 2^-24 (first
+        # order) of the exact one; the sum over pixels is FP64
+        assert mse[s].item() == pytest.approx(np.mean(d * d), rel=5 * 2.0 ** -24)
+        # the same per-pixel value emulated: FP32 differences, d0^2 rounded, then two
+        # fused multiply-adds (the product is exact in FP64; one rounding to FP32)
+        d32 = (a[s] - b[idx[s]]).astype(np.float32)
+        e = d32.astype(np.float64)
+        p0 = (d32[..., 0] * d32[..., 0]).astype(np.float64)
+        p1 = (e[..., 1] * e[..., 1] + p0).astype(np.float32).astype(np.float64)
+        p2 = (e[..., 2] * e[..., 2] + p1).astype(np.float32).astype(np.float64)
+        assert mse[s].item() == pytest.approx(p2.sum() / d.size, rel=1e-12)
         g = 0.25 * 2 * (a[s] - b[idx[s]]) / d.size
         assert np.allclose(dL[s].cpu().numpy(), g, rtol=1e-6, atol=1e-12)
 

@@ -38,12 +38,12 @@ def test_noalloc_matches_image_mse_on_two_calls_in_a_row():
 
 
 def test_noalloc_refuses_sizes_beyond_its_scratch():
-    """400 images of 512 x 512 need 400 * ceil(3 * 512 * 512 / 4096) = 76,800 partial
+    """400 images of 512 x 512 need 400 * ceil(512 * 512 / 1024) = 102,400 partial
     sums > 65,536: refused before any launch.  Every buffer is sized for the shape
     it is passed with, so even a refusal that failed could not read out of bounds."""
     import torch
     S, H, W = 400, 512, 512
-    parts = -(-3 * H * W // 4096)
+    parts = -(-H * W // 1024)
     assert S * parts > dgs.NOALLOC_MAX_PARTS
     images = torch.zeros((S, H, W, 3), dtype=torch.float32, device="cuda")
     refs = torch.zeros((1, H, W, 3), dtype=torch.float32, device="cuda")

@@ -28,6 +28,32 @@ constexpr int RT = 128;               // threads per raster block
 constexpr int RW = RT / 32;           // warps per block; warp w owns rows 4w..4w+3 of the tile
 constexpr int BATCH = 256;            // entries staged per batch (two per thread)
 
+// Staged conic coefficients are pre-scaled so that one pixel's exponent in
+// base 2, p2 = log2(e) * power = a2 dx^2 + b2 dx dy + c2 dy^2, costs two fused
+// multiply-adds per pixel on top of two per-entry products shared by the
+// thread's two pixels, and alpha = o 2^p2 (e^power == 2^(log2(e) power)).
+constexpr float LOG2E = 1.4426950408889634f;
+constexpr float K_AC = -0.5f * LOG2E;      // a2 = K_AC A, c2 = K_AC C
+constexpr float K_B = -LOG2E;              // b2 = K_B B
+constexpr float INV_K_AC = 1.0f / K_AC, INV_K_B = 1.0f / K_B;
+
+__device__ __forceinline__ float4 scale_r0(float4 r0) { return make_float4(r0.x, r0.y, r0.z * K_AC, r0.w * K_B); }
+__device__ __forceinline__ float4 scale_r1(float4 r1) { return make_float4(r1.x * K_AC, r1.y, r1.z, r1.w); }
+
+// 2^x on the MUFU unit (ex2.approx.ftz: relative error ~2^-22, tiny results flush to 0)
+__device__ __forceinline__ float ex2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// p2 at vertical offset dy, given the entry's per-column terms u = a2 dx^2 and v = b2 dx
+__device__ __forceinline__ float log2_power(float u, float v, float c2, float dy)
+{
+    return __fmaf_rn(__fmaf_rn(c2, dy, v), dy, u);
+}
+
 struct Staged {
     float4 r0[BATCH];                 // mx, my, A, B
     float4 r1[BATCH];                 // C, o, r, g
@@ -51,12 +77,13 @@ __device__ __forceinline__ int4 unpack_box(const float4 &r2)
 // q(d) = A dx^2 + 2 B dx dy + C dy^2 <= rho = 2 ln(255 o) with d = p - m.  The
 // minimum of the convex q over the rectangle is 0 when it holds the mean, else
 // it lies on an edge (1-D quadratic, clamped vertex).  rho is inflated by
-// 1e-3 relative + 1e-3 so FP32 rounding never drops a pixel that composites;
+// 1e-3 relative + 1e-3 so FP32 rounding never drops a pixel that composites
+// (the 1e-3 also covers undoing the staged scaling of the conic);
 // skipping a Gaussian that stays below 1/255 on the whole strip changes nothing.
 __device__ __forceinline__ bool ellipse_meets_rect(const float4 &r0, const float4 &r1, float x0, float x1,
                                                    float y0, float y1)
 {
-    const float A = r0.z, B = r0.w, C = r1.x, o = r1.y;
+    const float A = r0.z * INV_K_AC, B = r0.w * INV_K_B, C = r1.x * INV_K_AC, o = r1.y;   // staged: scaled
     const float rho = fmaf(2.0f * __logf(255.0f * o), 1.001f, 1e-3f);
     const float X0 = x0 - r0.x, X1 = x1 - r0.x, Y0 = y0 - r0.y, Y1 = y1 - r0.y;
     if (X0 <= 0.0f && X1 >= 0.0f && Y0 <= 0.0f && Y1 >= 0.0f) return true;
@@ -104,7 +131,7 @@ __device__ __forceinline__ int stage_batch(const Rec *__restrict__ recs, const u
             x2[h] = __ldg(p + 2);
             const uint32_t cd = __float_as_uint(x2[h].w);
             keep[h] = ((cd >> 12) & 0xfu) == (uint32_t)sdep[cd & 0xfffu];
-            if (keep[h]) { x0[h] = __ldg(p); x1[h] = __ldg(p + 1); }
+            if (keep[h]) { x0[h] = scale_r0(__ldg(p)); x1[h] = scale_r1(__ldg(p + 1)); }
         }
     }
     const uint32_t lt = (1u << lane) - 1u;
@@ -154,41 +181,38 @@ __device__ __forceinline__ int stage_batch(const Rec *__restrict__ recs, const u
     return nk;
 }
 
-// power = -1/2 (A dx^2 + C dy^2) - B dx dy, with explicit rounding so every
-// kernel that evaluates it gets the same bits.
-__device__ __forceinline__ float power_of(float A, float B, float C, float dx, float dy)
-{
-    const float q = __fmaf_rn(A, __fmul_rn(dx, dx), __fmul_rn(C, __fmul_rn(dy, dy)));
-    return __fmaf_rn(-0.5f, q, -__fmul_rn(B, __fmul_rn(dx, dy)));
-}
-
 // One pixel's front-to-back state.
 struct Pix {
     float T, c0, c1, c2;
     bool done;
 };
 
-// Composite one staged entry into one pixel (pixel centre pcx, pcy), branch
-// free: an entry the pixel skips (outside the box, power > 0, alpha < 1/255,
-// or the pixel already stopped) gets alpha = 0, and the entry at which
-// T (1 - alpha) would drop below 1e-4 stops the pixel without being added;
-// both leave T and the colour bit-identical.  Returns true at the stop.
-__device__ __forceinline__ bool composite(Pix &p, const float4 &r0, const float4 &r1, float b, bool inb, float pcx,
-                                          float pcy)
+// Composite one staged entry into one pixel, given its base-2 exponent p2;
+// branch free: an entry the pixel skips (outside the box, power > 0,
+// alpha < 1/255, or the pixel already stopped) gets alpha = 0, and the entry
+// at which T (1 - alpha) would drop below 1e-4 stops the pixel without being
+// added; both leave T and the colour bit-identical.  Returns true at the stop.
+__device__ __forceinline__ bool composite(Pix &p, float p2, float o, float r, float g, float b, bool inb)
 {
-    const float dx = __fsub_rn(r0.x, pcx), dy = __fsub_rn(r0.y, pcy);
-    const float pw = power_of(r0.z, r0.w, r1.x, dx, dy);
-    const float a0 = fminf(0.99f, __fmul_rn(r1.y, __expf(pw)));
-    const float alpha = (inb && !p.done && pw <= 0.0f && a0 >= (1.0f / 255.0f)) ? a0 : 0.0f;
+    const float a0 = fminf(0.99f, __fmul_rn(o, ex2(p2)));
+    const float alpha = (inb && !p.done && p2 <= 0.0f && a0 >= (1.0f / 255.0f)) ? a0 : 0.0f;
     const float Tn = __fmul_rn(p.T, __fsub_rn(1.0f, alpha));
     const bool stop = Tn < 1e-4f;
     const float wgt = stop ? 0.0f : __fmul_rn(alpha, p.T);
-    p.c0 = __fmaf_rn(r1.z, wgt, p.c0);
-    p.c1 = __fmaf_rn(r1.w, wgt, p.c1);
+    p.c0 = __fmaf_rn(r, wgt, p.c0);
+    p.c1 = __fmaf_rn(g, wgt, p.c1);
     p.c2 = __fmaf_rn(b, wgt, p.c2);
     p.T = stop ? p.T : Tn;
     p.done = p.done || stop;
     return stop;
+}
+
+// Per-entry column terms for a thread's pixel column: u = a2 dx^2, v = b2 dx.
+__device__ __forceinline__ void column_terms(const float4 &r0, float pcx, float &dx, float &u, float &v)
+{
+    dx = __fsub_rn(r0.x, pcx);
+    u = __fmul_rn(__fmul_rn(r0.z, dx), dx);
+    v = __fmul_rn(r0.w, dx);
 }
 
 __device__ __forceinline__ void load_depth_row(const uint8_t *depth, int s, int C, uint8_t *sdep)
@@ -208,7 +232,7 @@ __device__ __forceinline__ int stage_all(const Rec *__restrict__ recs, const uin
         if (e < end) {
             const uint32_t slot = __ldg(evals + e);
             const float4 *p = reinterpret_cast<const float4 *>(recs + slot);
-            sm.r0[j] = __ldg(p); sm.r1[j] = __ldg(p + 1);
+            sm.r0[j] = scale_r0(__ldg(p)); sm.r1[j] = scale_r1(__ldg(p + 1));
             const float4 r2 = __ldg(p + 2);
             sm.r2[j] = r2;
             sm.box[j] = unpack_box(r2);
@@ -312,8 +336,12 @@ __global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a, WorkQueue q)
                     const float b = sm.r2[k].x;
                     const int4 bx = sm.box[k];
                     const bool xin = in_range(px, bx.x, bx.y);
-                    composite(p[g][0], r0, r1, b, xin && in_range(py0, bx.z, bx.w), pcx, pcy0);
-                    composite(p[g][1], r0, r1, b, xin && in_range(py1, bx.z, bx.w), pcx, pcy1);
+                    float dx, u, v;
+                    column_terms(r0, pcx, dx, u, v);
+                    composite(p[g][0], log2_power(u, v, r1.x, __fsub_rn(r0.y, pcy0)), r1.y, r1.z, r1.w, b,
+                              xin && in_range(py0, bx.z, bx.w));
+                    composite(p[g][1], log2_power(u, v, r1.x, __fsub_rn(r0.y, pcy1)), r1.y, r1.z, r1.w, b,
+                              xin && in_range(py1, bx.z, bx.w));
                 }
                 __syncwarp();
             }
@@ -410,15 +438,15 @@ struct PixB {
 // dL/do, dL/drgb) with gpw = dL/dpower; the conic and mean gradients are
 // linear in these sums (A, B, C are per Gaussian) and are formed once per
 // Gaussian after the reduction.  Branch free: a skipped entry adds zeros.
-__device__ __forceinline__ bool adjoint(PixB &p, const float4 &r0, const float4 &r1, float b, bool inb, float pcx,
-                                        float pcy, float *g)
+__device__ __forceinline__ bool adjoint(PixB &p, const float4 &r0, const float4 &r1, float b, bool inb, float dx,
+                                        float u, float v, float pcy, float *g)
 {
-    const float dx = __fsub_rn(r0.x, pcx), dy = __fsub_rn(r0.y, pcy);
-    const float pw = power_of(r0.z, r0.w, r1.x, dx, dy);
-    const float ex = __expf(pw);
+    const float dy = __fsub_rn(r0.y, pcy);
+    const float p2 = log2_power(u, v, r1.x, dy);
+    const float ex = ex2(p2);
     const float araw = __fmul_rn(r1.y, ex);
     const float a0 = fminf(0.99f, araw);
-    const bool hit = inb && pw <= 0.0f && a0 >= (1.0f / 255.0f);
+    const bool hit = inb && p2 <= 0.0f && a0 >= (1.0f / 255.0f);
     const float Tn = __fmul_rn(p.T, __fsub_rn(1.0f, hit ? a0 : 0.0f));
     const bool stop = Tn < 1e-4f;
     const bool ok = hit && !stop;
@@ -525,8 +553,12 @@ __global__ void __launch_bounds__(RT, 6) k_raster_bwd(RasterBwdArgs b)
                 const float bb = sm.r2[k].x;
                 const int4 bx = sm.box[k];
                 const bool xin = in_range(px, bx.x, bx.y);
-                composite(f[0], r0, r1, bb, xin && in_range(py0, bx.z, bx.w), pcx, pcy0);
-                composite(f[1], r0, r1, bb, xin && in_range(py1, bx.z, bx.w), pcx, pcy1);
+                float dx, u, v;
+                column_terms(r0, pcx, dx, u, v);
+                composite(f[0], log2_power(u, v, r1.x, __fsub_rn(r0.y, pcy0)), r1.y, r1.z, r1.w, bb,
+                          xin && in_range(py0, bx.z, bx.w));
+                composite(f[1], log2_power(u, v, r1.x, __fsub_rn(r0.y, pcy1)), r1.y, r1.z, r1.w, bb,
+                          xin && in_range(py1, bx.z, bx.w));
             }
         }
 #pragma unroll
@@ -569,11 +601,13 @@ __global__ void __launch_bounds__(RT, 6) k_raster_bwd(RasterBwdArgs b)
                 const float bb = sm.r2[k].x;
                 const int4 bx = sm.box[k];
                 const bool xin = in_range(px, bx.x, bx.y);
+                float dx, u, v;
+                column_terms(r0, pcx, dx, u, v);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     PixB &p = q[h];
                     const bool inb = p.active && xin && in_range(h ? py1 : py0, bx.z, bx.w);
-                    contrib |= adjoint(p, r0, r1, bb, inb, pcx, h ? pcy1 : pcy0, g);
+                    contrib |= adjoint(p, r0, r1, bb, inb, dx, u, v, h ? pcy1 : pcy0, g);
                 }
                 if (__ballot_sync(0xffffffffu, contrib)) {
                     const float x = reduce8_transpose(g, lane);
@@ -593,7 +627,7 @@ __global__ void __launch_bounds__(RT, 6) k_raster_bwd(RasterBwdArgs b)
             for (int j = 0; j < 9; ++j) { x[j] = gacc[k][j]; gacc[k][j] = 0.0f; any |= (x[j] != 0.0f); }
             if (any) {
                 // conic and mean gradients from the per-Gaussian sums
-                const float A = sm.r0[k].z, B = sm.r0[k].w, C = sm.r1[k].x;
+                const float A = sm.r0[k].z * INV_K_AC, B = sm.r0[k].w * INV_K_B, C = sm.r1[k].x * INV_K_AC;
                 const float gmx = -(A * x[0] + B * x[1]), gmy = -(C * x[1] + B * x[0]);
                 float4 *dst = b.rec_grad + (size_t)sm.slot[k] * 3;
                 atomicAdd(dst, make_float4(gmx, gmy, -0.5f * x[2], -x[3]));

@@ -249,7 +249,9 @@ DGS_API int dgs_plan_status(dgs_plan *plan, int64_t *n_records, int64_t *n_entri
  * copy on `stream`:
  *   recs        [n_rec][12] u32 -- the 48-byte records: mx, my, A, B, C, o, r,
  *               g, b (floats), box x = xlo | xhi << 16, box y = ylo | yhi << 16,
- *               cluster | depth << 12 | view group << 16 (depth 0 = culled)
+ *               cluster | depth << 12 | view group << 16 | boxed << 31 (depth 0
+ *               = culled; boxed: the 3-sigma box is narrower than the
+ *               alpha >= 1/255 box on some axis)
  *   depth_keys  [n_rec]  float bits of camera depth, ascending (0xFFFFFFFF = culled)
  *   depth_slots [n_rec]  the record slot of each sorted depth key
  *   entry_keys  [n_ent]  view group * tiles + tile, ascending (stable)

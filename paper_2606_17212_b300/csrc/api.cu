@@ -255,7 +255,7 @@ int build_plan(dgs_ctx *ctx, const dgs_states *st, const dgs_camera *cams, int n
         p.vg_of_state[s] = v;
     }
     p.V = (int)p.vgs.size();
-    if (p.V > 65535) return fail(ctx, DGS_E_UNSUPPORTED, "more than 65535 distinct (camera, time) pairs");
+    if (p.V > 32767) return fail(ctx, DGS_E_UNSUPPORTED, "more than 32767 distinct (camera, time) pairs");
     if ((unsigned long long)(st->n_states + (add_refs ? p.V : 0)) * p.tiles >= 0x7fffffffull)
         return fail(ctx, DGS_E_CAPACITY, "states x tiles exceeds the launch grid");
     if ((unsigned long long)p.V * p.tiles >= 0xffffffffull)

@@ -30,7 +30,8 @@ struct __align__(16) Rec {
     float b;                   // colour b
     uint32_t bx;               // xlo | xhi << 16   (inclusive pixel range)
     uint32_t by;               // ylo | yhi << 16
-    uint32_t cd;               // cluster | depth << 12 | view group << 16 (depth 0 = culled)
+    uint32_t cd;               // cluster | depth << 12 | view group << 16 | boxed << 31 (depth 0 = culled;
+                               // boxed: pixels need the box test, the 3-sigma box clips the alpha box)
 };
 static_assert(sizeof(Rec) == 48, "record layout");
 

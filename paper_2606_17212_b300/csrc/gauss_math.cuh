@@ -124,6 +124,7 @@ struct Proj {
     float mx, my, A, B, C, o, rgb[3], z, r;
     int xlo, xhi, ylo, yhi;
     bool live;
+    bool rclip;                // the 3-sigma box is narrower than the alpha >= 1/255 box on some axis
 };
 
 // Eq. 1 deformation and EWA projection of decoded attributes `a` of Gaussian i.
@@ -132,6 +133,7 @@ __device__ __forceinline__ void project_fwd(const SceneDev &s, int i, const Attr
                                             const ViewGroup &vg, Proj &P, Fwd &F)
 {
     P.live = false;
+    P.rclip = false;
 #pragma unroll
     for (int k = 0; k < 3; ++k) F.mu[k] = a.mu[k];
     for (int r = 0; r < s.R; ++r) {
@@ -208,8 +210,12 @@ __device__ __forceinline__ void project_fwd(const SceneDev &s, int i, const Attr
     // A Gaussian with o < 1/255 never composites at all.
     if (!(P.o >= (1.0f / 255.0f))) return;
     const float rho = 2.0f * logf(255.0f * P.o);
-    const float hx = fminf(P.r, fmaf(sqrtf(fmaxf(rho, 0.0f) * F.a), 1.001f, 0.05f));
-    const float hy = fminf(P.r, fmaf(sqrtf(fmaxf(rho, 0.0f) * F.c), 1.001f, 0.05f));
+    const float ax = fmaf(sqrtf(fmaxf(rho, 0.0f) * F.a), 1.001f, 0.05f);
+    const float ay = fmaf(sqrtf(fmaxf(rho, 0.0f) * F.c), 1.001f, 0.05f);
+    const float hx = fminf(P.r, ax), hy = fminf(P.r, ay);
+    // Where the 3-sigma box is not the narrower one, the box holds every pixel
+    // the alpha test keeps, so the raster needs no per-pixel box test.
+    P.rclip = (P.r < ax) || (P.r < ay);
     // pixel ranges: |x + 0.5 - mx| <= h  <=>  ceil(mx - h - 0.5) <= x <= floor(mx + h - 0.5),
     // evaluated in FP32 (rounding moves an edge only for pixel centres within
     // ~1e-5 px of the boundary), clamped to the image before the integer cast

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(128, 4) k_project(SceneDev s, const ViewGroup 
                     R.r = P.rgb[0]; R.g = P.rgb[1]; R.b = P.rgb[2];
                     R.bx = (uint32_t)P.xlo | ((uint32_t)P.xhi << 16);
                     R.by = (uint32_t)P.ylo | ((uint32_t)P.yhi << 16);
-                    R.cd = (uint32_t)c | ((uint32_t)d << 12) | ((uint32_t)v << 16);
+                    R.cd = (uint32_t)c | ((uint32_t)d << 12) | ((uint32_t)v << 16) | ((uint32_t)P.rclip << 31);
                     keys[slot] = __float_as_uint(P.z);
                 } else {
                     R.mx = R.my = R.A = R.B = R.C = R.o = R.r = R.g = R.b = 0.0f;
@@ -215,7 +215,7 @@ __global__ void k_emit(const Rec *__restrict__ recs, const uint32_t *__restrict_
             x0 = (int)(bx & 0xffffu) / TILE;
             tw = (int)(bx >> 16) / TILE - x0 + 1;
             y0 = (int)(by & 0xffffu) / TILE;
-            vbase = (__float_as_uint(q.w) >> 16) * tiles;
+            vbase = ((__float_as_uint(q.w) >> 16) & 0x7fffu) * tiles;
         }
         uint32_t incl = cnt;
 #pragma unroll

@@ -229,6 +229,11 @@ __device__ __forceinline__ bool composite(Pix &p, float p2, float o, float r, fl
     return stop;
 }
 
+// Does the entry need the per-pixel box test?  Only where its 3-sigma box
+// clips the alpha >= 1/255 box (record flag); elsewhere the box holds every
+// pixel the alpha test keeps and the test is skipped.
+__device__ __forceinline__ bool is_boxed(const float4 &r2) { return (__float_as_uint(r2.w) >> 31) != 0u; }
+
 // Per-entry column terms for a thread's pixel column: u = a2 dx^2, v = b2 dx.
 __device__ __forceinline__ void column_terms(const float4 &r0, float pcx, float &dx, float &u, float &v)
 {
@@ -350,16 +355,20 @@ __global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a, WorkQueue q)
                 for (int i = 0; i < n; ++i) {
                     if (p[g][0].done && p[g][1].done) break;
                     const int k = sm.list[w][i];
-                    const float4 r0 = sm.r0[k], r1 = sm.r1[k];
-                    const float b = sm.r2[k].x;
-                    const int4 bx = sm.box[k];
-                    const bool xin = in_range(px, bx.x, bx.y);
+                    const float4 r0 = sm.r0[k], r1 = sm.r1[k], r2 = sm.r2[k];
                     float dx, u, v;
                     column_terms(r0, pcx, dx, u, v);
-                    composite(p[g][0], log2_power(u, v, r1.x, __fsub_rn(r0.y, pcy0)), r1.y, r1.z, r1.w, b,
-                              xin && in_range(py0, bx.z, bx.w));
-                    composite(p[g][1], log2_power(u, v, r1.x, __fsub_rn(r0.y, pcy1)), r1.y, r1.z, r1.w, b,
-                              xin && in_range(py1, bx.z, bx.w));
+                    const float q0 = log2_power(u, v, r1.x, __fsub_rn(r0.y, pcy0));
+                    const float q1 = log2_power(u, v, r1.x, __fsub_rn(r0.y, pcy1));
+                    if (is_boxed(r2)) {           // same entry in every lane: uniform branch
+                        const int4 bx = sm.box[k];
+                        const bool xin = in_range(px, bx.x, bx.y);
+                        composite(p[g][0], q0, r1.y, r1.z, r1.w, r2.x, xin && in_range(py0, bx.z, bx.w));
+                        composite(p[g][1], q1, r1.y, r1.z, r1.w, r2.x, xin && in_range(py1, bx.z, bx.w));
+                    } else {
+                        composite(p[g][0], q0, r1.y, r1.z, r1.w, r2.x, true);
+                        composite(p[g][1], q1, r1.y, r1.z, r1.w, r2.x, true);
+                    }
                 }
                 __syncwarp();
             }
@@ -567,16 +576,20 @@ __global__ void __launch_bounds__(RT, 6) k_raster_bwd(RasterBwdArgs b)
             for (int i = 0; i < n; ++i) {
                 if (f[0].done && f[1].done) break;
                 const int k = sm.list[w][i];
-                const float4 r0 = sm.r0[k], r1 = sm.r1[k];
-                const float bb = sm.r2[k].x;
-                const int4 bx = sm.box[k];
-                const bool xin = in_range(px, bx.x, bx.y);
+                const float4 r0 = sm.r0[k], r1 = sm.r1[k], r2 = sm.r2[k];
                 float dx, u, v;
                 column_terms(r0, pcx, dx, u, v);
-                composite(f[0], log2_power(u, v, r1.x, __fsub_rn(r0.y, pcy0)), r1.y, r1.z, r1.w, bb,
-                          xin && in_range(py0, bx.z, bx.w));
-                composite(f[1], log2_power(u, v, r1.x, __fsub_rn(r0.y, pcy1)), r1.y, r1.z, r1.w, bb,
-                          xin && in_range(py1, bx.z, bx.w));
+                const float q0 = log2_power(u, v, r1.x, __fsub_rn(r0.y, pcy0));
+                const float q1 = log2_power(u, v, r1.x, __fsub_rn(r0.y, pcy1));
+                bool b0 = true, b1 = true;
+                if (is_boxed(r2)) {
+                    const int4 bx = sm.box[k];
+                    const bool xin = in_range(px, bx.x, bx.y);
+                    b0 = xin && in_range(py0, bx.z, bx.w);
+                    b1 = xin && in_range(py1, bx.z, bx.w);
+                }
+                composite(f[0], q0, r1.y, r1.z, r1.w, r2.x, b0);
+                composite(f[1], q1, r1.y, r1.z, r1.w, r2.x, b1);
             }
         }
 #pragma unroll
@@ -615,17 +628,22 @@ __global__ void __launch_bounds__(RT, 6) k_raster_bwd(RasterBwdArgs b)
 #pragma unroll
                 for (int j = 0; j < 9; ++j) g[j] = 0.0f;
                 bool contrib = false;
-                const float4 r0 = sm.r0[k], r1 = sm.r1[k];
-                const float bb = sm.r2[k].x;
-                const int4 bx = sm.box[k];
-                const bool xin = in_range(px, bx.x, bx.y);
+                const float4 r0 = sm.r0[k], r1 = sm.r1[k], r2 = sm.r2[k];
                 float dx, u, v;
                 column_terms(r0, pcx, dx, u, v);
+                if (is_boxed(r2)) {           // same entry in every lane: uniform branch
+                    const int4 bx = sm.box[k];
+                    const bool xin = in_range(px, bx.x, bx.y);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    PixB &p = q[h];
-                    const bool inb = p.active && xin && in_range(h ? py1 : py0, bx.z, bx.w);
-                    contrib |= adjoint(p, r0, r1, bb, inb, dx, u, v, h ? pcy1 : pcy0, g);
+                    for (int h = 0; h < 2; ++h) {
+                        PixB &p = q[h];
+                        const bool inb = p.active && xin && in_range(h ? py1 : py0, bx.z, bx.w);
+                        contrib |= adjoint(p, r0, r1, r2.x, inb, dx, u, v, h ? pcy1 : pcy0, g);
+                    }
+                } else {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) contrib |= adjoint(q[h], r0, r1, r2.x, q[h].active, dx, u, v,
+                                                                   h ? pcy1 : pcy0, g);
                 }
                 if (__ballot_sync(0xffffffffu, contrib)) {
                     const float x = reduce8_transpose(g, lane);

@@ -264,7 +264,7 @@ def test_backward_undelivered_layers_exactly_zero_and_autograd(R, torch):
 def _unpack_boxes(recs):
     bx, by, cd = recs[:, 9], recs[:, 10], recs[:, 11]
     return (bx & 0xFFFF).astype(np.int64), (bx >> 16).astype(np.int64), (by & 0xFFFF).astype(np.int64), \
-        (by >> 16).astype(np.int64), ((cd >> 12) & 0xF).astype(np.int64), (cd >> 16).astype(np.int64), \
+        (by >> 16).astype(np.int64), ((cd >> 12) & 0xF).astype(np.int64), ((cd >> 16) & 0x7FFF).astype(np.int64), \
         (cd & 0xFFF).astype(np.int64)
 
 

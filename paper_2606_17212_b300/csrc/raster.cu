@@ -461,42 +461,44 @@ struct PixB {
 // where the forward ended.  With gr = dL/dC . rgb_k and the running
 // gc = dL/dC . C_prefix (including k):
 //   dL/dalpha_k = T_k gr - (GK - gc) / (1 - alpha_k).
-// Adds to g[9] = (S gpw dx, S gpw dy, S gpw dx^2, S gpw dx dy, S gpw dy^2,
-// dL/do, dL/drgb) with gpw = dL/dpower; the conic and mean gradients are
-// linear in these sums (A, B, C are per Gaussian) and are formed once per
-// Gaussian after the reduction.  Branch free: a skipped entry adds zeros.
+// Writes (FIRST) or adds to g[9] = (S gpw dx, S gpw dy, S gpw dx^2,
+// S gpw dx dy, S gpw dy^2, S gpw, dL/drgb) with gpw = dL/dpower; the conic
+// and mean gradients are linear in these sums (A, B, C are per Gaussian) and
+// dL/do = S gpw / o (alpha = o e^power), all formed once per Gaussian after
+// the reduction.  Branch free: a skipped entry adds zeros.
+template <bool FIRST>
 __device__ __forceinline__ bool adjoint(PixB &p, const float4 &r0, const float4 &r1, float b, bool inb, float dx,
                                         float u, float v, float pcy, float *g)
 {
     const float dy = __fsub_rn(r0.y, pcy);
     const float p2 = log2_power(u, v, r1.x, dy);
-    const float ex = ex2(p2);
-    const float araw = __fmul_rn(r1.y, ex);
+    const float araw = __fmul_rn(r1.y, ex2(p2));
     const float a0 = fminf(0.99f, araw);
     const bool hit = inb && p2 <= 0.0f && a0 >= (1.0f / 255.0f);
-    const float Tn = __fmul_rn(p.T, __fsub_rn(1.0f, hit ? a0 : 0.0f));
-    const bool stop = Tn < 1e-4f;
+    const float om = __fsub_rn(1.0f, a0);                // >= 0.01
+    const float Tn = __fmul_rn(p.T, om);
+    const bool stop = hit && Tn < 1e-4f;
     const bool ok = hit && !stop;
     p.active = p.active && !stop;
-    const float alpha = ok ? a0 : 0.0f;
-    const float one_m = __fsub_rn(1.0f, alpha);
-    const float wgt = __fmul_rn(alpha, p.T);
+    const float wgt = ok ? __fmul_rn(a0, p.T) : 0.0f;
     const float gr = fmaf(p.g2, b, fmaf(p.g1, r1.w, p.g0 * r1.z));
     p.gc = fmaf(wgt, gr, p.gc);
-    const float da = fmaf(p.T, gr, -(p.GK - p.gc) * __fdividef(1.0f, one_m));
-    g[6] = fmaf(p.g0, wgt, g[6]);
-    g[7] = fmaf(p.g1, wgt, g[7]);
-    g[8] = fmaf(p.g2, wgt, g[8]);
-    // alpha = 0 (skipped) or the 0.99 clamp: no gradient to opacity, mean, conic
-    const bool lin = ok && araw < 0.99f;
-    const float gpw = lin ? da * alpha : 0.0f;
-    g[5] += lin ? da * ex : 0.0f;
+    // unused unless ok; finite either way (om >= 0.01)
+    const float da = fmaf(p.T, gr, -(p.GK - p.gc) * __fdividef(1.0f, om));
+    // d alpha / d power = alpha on the linear range; 0 when skipped or at the 0.99 clamp
+    const float gpw = da * ((ok && araw < 0.99f) ? a0 : 0.0f);
     const float t1 = gpw * dx, t2 = gpw * dy;
-    g[0] += t1;
-    g[1] += t2;
-    g[2] = fmaf(t1, dx, g[2]);
-    g[3] = fmaf(t1, dy, g[3]);
-    g[4] = fmaf(t2, dy, g[4]);
+    if (FIRST) {
+        g[0] = t1; g[1] = t2;
+        g[2] = t1 * dx; g[3] = t1 * dy; g[4] = t2 * dy;
+        g[5] = gpw;
+        g[6] = p.g0 * wgt; g[7] = p.g1 * wgt; g[8] = p.g2 * wgt;
+    } else {
+        g[0] += t1; g[1] += t2;
+        g[2] = fmaf(t1, dx, g[2]); g[3] = fmaf(t1, dy, g[3]); g[4] = fmaf(t2, dy, g[4]);
+        g[5] += gpw;
+        g[6] = fmaf(p.g0, wgt, g[6]); g[7] = fmaf(p.g1, wgt, g[7]); g[8] = fmaf(p.g2, wgt, g[8]);
+    }
     p.T = ok ? Tn : p.T;
     return ok;
 }
@@ -625,25 +627,20 @@ __global__ void __launch_bounds__(RT, 6) k_raster_bwd(RasterBwdArgs b)
                 if ((i & 7) == 0 && !__any_sync(0xffffffffu, q[0].active || q[1].active)) break;
                 const int k = sm.list[w][i];
                 float g[9];
-#pragma unroll
-                for (int j = 0; j < 9; ++j) g[j] = 0.0f;
-                bool contrib = false;
+                bool contrib;
                 const float4 r0 = sm.r0[k], r1 = sm.r1[k], r2 = sm.r2[k];
                 float dx, u, v;
                 column_terms(r0, pcx, dx, u, v);
                 if (is_boxed(r2)) {           // same entry in every lane: uniform branch
                     const int4 bx = sm.box[k];
                     const bool xin = in_range(px, bx.x, bx.y);
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        PixB &p = q[h];
-                        const bool inb = p.active && xin && in_range(h ? py1 : py0, bx.z, bx.w);
-                        contrib |= adjoint(p, r0, r1, r2.x, inb, dx, u, v, h ? pcy1 : pcy0, g);
-                    }
+                    contrib = adjoint<true>(q[0], r0, r1, r2.x, q[0].active && xin && in_range(py0, bx.z, bx.w),
+                                            dx, u, v, pcy0, g);
+                    contrib |= adjoint<false>(q[1], r0, r1, r2.x, q[1].active && xin && in_range(py1, bx.z, bx.w),
+                                              dx, u, v, pcy1, g);
                 } else {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) contrib |= adjoint(q[h], r0, r1, r2.x, q[h].active, dx, u, v,
-                                                                   h ? pcy1 : pcy0, g);
+                    contrib = adjoint<true>(q[0], r0, r1, r2.x, q[0].active, dx, u, v, pcy0, g);
+                    contrib |= adjoint<false>(q[1], r0, r1, r2.x, q[1].active, dx, u, v, pcy1, g);
                 }
                 if (__ballot_sync(0xffffffffu, contrib)) {
                     const float x = reduce8_transpose(g, lane);
@@ -667,7 +664,7 @@ __global__ void __launch_bounds__(RT, 6) k_raster_bwd(RasterBwdArgs b)
                 const float gmx = -(A * x[0] + B * x[1]), gmy = -(C * x[1] + B * x[0]);
                 float4 *dst = b.rec_grad + (size_t)sm.slot[k] * 3;
                 atomicAdd(dst, make_float4(gmx, gmy, -0.5f * x[2], -x[3]));
-                atomicAdd(dst + 1, make_float4(-0.5f * x[4], x[5], x[6], x[7]));
+                atomicAdd(dst + 1, make_float4(-0.5f * x[4], __fdividef(x[5], sm.r1[k].y), x[6], x[7]));
                 atomicAdd(dst + 2, make_float4(x[8], 0.0f, 0.0f, 0.0f));
             }
         }

@@ -147,37 +147,55 @@ class ClockSampler:
                 "reasons": sorted(self.reasons), "samples": len(self.samples)}
 
 
-def oracle_sample(w, n_states=2, n_pix=1024, seed=0, want_backward=True):
-    """Time the FP64 oracle on a bounded sample: n_pix random pixels of n_states
-    states, forward (+ adjoint restricted to those pixels).  Returns
-    (seconds per full state, evaluations per pixel, threads, description)."""
+def oracle_sample(w, n_states=2, n_bands=8, band_rows=2, n_pix=256, seed=0, want_backward=True):
+    """Time the FP64 oracle as it stands on a bounded sample of each state.
+    Forward: the projection (once per state) plus n_bands bands of band_rows
+    whole rows at random heights, rendered as in the full image (row filter),
+    extrapolated to all rows.  Adjoint: its fixed part (projection and the
+    per-record chain rule, timed with dL/dI = 0) plus the adjoint of n_pix
+    random pixels, extrapolated to all pixels.  Returns (seconds per full
+    state, evaluations per pixel, threads, description)."""
     import oracle
     sc = w.scene
     rng = np.random.default_rng(seed)
     D = oracle.state_depths(w.states, sc.n_clusters, sc.n_layers)
     H, W = w.cams[0].height, w.cams[0].width
-    tot_t, tot_px, tot_eval = 0.0, 0, 0
+    tot_t, tot_eval, tot_px = 0.0, 0, 0
+    rows = min(band_rows, H)
     for s in range(n_states):
         cam = w.cams[int(w.states.cam[s])]
         t = float(w.states.t[s])
-        flat = rng.choice(H * W, size=n_pix, replace=False)
-        pix = np.stack([flat % W, flat // W], 1).astype(np.int32)
         t0 = time.perf_counter()
-        img, marg, ne = oracle.render(sc, D[s], t, cam, w.bg, pix=pix)
+        oracle.project(sc, D[s], t, cam)
+        t_proj = time.perf_counter() - t0
+        t_rows, n_rows = 0.0, 0
+        for y0 in rng.integers(0, H - rows + 1, size=n_bands):
+            t0 = time.perf_counter()
+            _, _, ne = oracle.render_rows(sc, D[s], t, cam, w.bg, int(y0), int(y0) + rows)
+            t_rows += max(time.perf_counter() - t0 - t_proj, 0.0)
+            n_rows += rows
+            tot_eval += ne
+            tot_px += rows * W
+        fwd = t_proj + t_rows * H / n_rows
+        bwd = 0.0
         if want_backward:
             dL = np.zeros((H, W, 3))
-            dL[pix[:, 1], pix[:, 0]] = rng.normal(size=(n_pix, 3))
+            t0 = time.perf_counter()
             oracle.render_backward(sc, D[s], t, cam, w.bg, dL)
-        tot_t += time.perf_counter() - t0
-        tot_px += n_pix
-        tot_eval += ne
-    sec_per_state = tot_t / tot_px * (H * W)
+            t_fix = time.perf_counter() - t0
+            flat = rng.choice(H * W, size=min(n_pix, H * W), replace=False)
+            dL[flat // W, flat % W] = rng.normal(size=(flat.size, 3))
+            t0 = time.perf_counter()
+            oracle.render_backward(sc, D[s], t, cam, w.bg, dL)
+            bwd = t_fix + max(time.perf_counter() - t0 - t_fix, 0.0) * (H * W) / flat.size
+        tot_t += fwd + bwd
     threads = os.cpu_count() or 1
-    desc = ("%d random pixels in each of %d states (FP64 forward on %d threads%s), "
-            "extrapolated to %dx%d pixels per state" % (n_pix, n_states, threads,
-                                                       ", adjoint of those pixels on 1 thread" if want_backward
-                                                       else "", W, H))
-    return sec_per_state, tot_eval / tot_px, threads, desc
+    desc = ("%d states, each: projection once + %d bands of %d whole rows (FP64 forward on %d threads, row "
+            "filter as in the full image) extrapolated to %d rows%s" % (
+                n_states, n_bands, rows, threads, H,
+                "; adjoint (1 thread): fixed part once + %d random pixels extrapolated to %dx%d" % (n_pix, W, H)
+                if want_backward else ""))
+    return tot_t / n_states, tot_eval / max(tot_px, 1), threads, desc
 
 
 def workload_config(w, ws, views, path):
@@ -197,7 +215,8 @@ def reference_arm(args, w):
     times = []
     n_pix = 256
     for k in range(args.warmup + args.steps):
-        sps, _, threads, desc = oracle_sample(w, n_states=1, n_pix=n_pix, seed=k)
+        sps, _, threads, desc = oracle_sample(w, n_states=1, n_pix=n_pix, seed=k,
+                                              want_backward=w.target_scene is not None)
         if k >= args.warmup:
             times.append(sps)
     sec_per_state = float(np.mean(times))
@@ -210,6 +229,187 @@ def reference_arm(args, w):
                              "sample": "per step: " + desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_mix(args):
+    """Serving-shaped uneven mix: 48 scenes (SH degree 3, 50k-2.7M Gaussians,
+    256^2 / 512^2 / 960x540), 64 states each; one step = the training step
+    (render, MSE against the scene's complete render at the state's view,
+    adjoint) of every scene.  Headline = the faster of the context calls and
+    one CUDA graph holding every scene's plan (plans share one arena)."""
+    import torch
+    from paper_2606_17212_b300 import dgs, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    R = dgs.Renderer(0)
+    specs = synth.mix_specs(scale=args.scale)
+    scenes = []
+    t_gen = time.perf_counter()
+    evals_total = 0.0
+    oracle_sec = 0.0
+    threads = None
+    for spec in specs:
+        w = synth.mix_workload(spec)
+        sc = dgs.DeviceScene.from_host(w.scene, device=dev)
+        st = dgs.DeviceStates.from_host(w.states)
+        views = sorted(set(zip(w.states.cam.tolist(), w.states.t.tolist())))
+        ridx = np.array([views.index(v) for v in zip(w.states.cam.tolist(), w.states.t.tolist())], np.int32)
+        full = torch.full((len(views), st.masks.shape[1]), -1, dtype=torch.int32, device=dev)
+        fv = dgs.DeviceStates(full, np.array([v[1] for v in views], np.float32),
+                              np.array([v[0] for v in views], np.int32))
+        targets = R.render_states_batched(sc, fv, w.cams, w.bg)
+        S, H, W = st.n, w.cams[0].height, w.cams[0].width
+        # oracle on a bounded sample of this scene: evaluations per pixel and CPU time per state
+        sec, epp, threads, _ = oracle_sample(w, n_states=1, n_bands=4, n_pix=64, seed=spec.index,
+                                             want_backward=True)
+        evals_total += epp * H * W * S
+        oracle_sec += sec * S
+        scenes.append(dict(spec=spec, w_t=w.states.t, w_cam=w.states.cam, cams=w.cams, bg=w.bg, sc=sc, st=st,
+                           ridx=ridx, targets=targets, S=S, H=H, W=W,
+                           host_masks=torch.from_numpy(np.ascontiguousarray(w.states.masks).view(np.int32)).pin_memory(),
+                           images=torch.empty((S, H, W, 3), device=dev), grads=sc.zeros_like_grads()))
+        del w
+    t_gen = time.perf_counter() - t_gen
+    total_states = sum(c["S"] for c in scenes)
+    total_px = sum(c["S"] * c["H"] * c["W"] for c in scenes)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def eager_step():
+        out = []
+        for c in scenes:
+            R.render_states_batched(c["sc"], c["st"], c["cams"], c["bg"], out=c["images"])
+            mse, _, dL = R.image_mse(c["images"], c["targets"], c["ridx"], weight=1.0 / c["S"], want_grad=True)
+            for g in c["grads"].values():
+                g.zero_()
+            R.render_backward(c["sc"], c["st"], c["cams"], c["bg"], dL, c["grads"], images=c["images"])
+            out.append(mse)
+        return out
+
+    def timed(fn, K):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        torch.cuda.synchronize()
+        for k in range(K):
+            flush.fill_(float(k))
+            starts[k].record()
+            fn()
+            ends[k].record()
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / K
+
+    for _ in range(args.warmup):
+        eager_step()
+    clocks = ClockSampler(0)
+    R.reset_kernel_launches()
+    R.profile(True)
+    eager_ms = timed(eager_step, args.steps)
+    eager_launches = R.kernel_launches()
+    prof = R.profile_read()
+    R.profile(False)
+
+    # graph: one plan per scene in a shared arena, the whole step captured once
+    arena = dgs.Arena(R)
+    for c in scenes:
+        c["plan"] = dgs.Plan(R, c["sc"], c["st"], c["cams"], c["bg"], dgs.PLAN_RENDER, ref_index=c["ridx"],
+                             n_refs=int(c["targets"].shape[0]), entry_headroom=1.5, arena=arena)
+        c["g_masks"] = c["st"].masks.clone()
+        c["g_mse"] = torch.empty(c["S"], dtype=torch.float64, device=dev)
+        c["g_psnr"] = torch.empty_like(c["g_mse"])
+        c["g_dL"] = torch.empty_like(c["images"])
+
+    def plan_step():
+        for c in scenes:
+            for g in c["grads"].values():
+                g.zero_()
+            c["plan"].render(c["g_masks"], c["images"])
+            c["plan"].image_mse(c["images"], c["targets"], c["g_mse"], c["g_psnr"], c["g_dL"], weight=1.0 / c["S"])
+            c["plan"].backward(c["g_dL"], c["grads"], images=c["images"])
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        plan_step()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    R.reset_kernel_launches()
+    with torch.cuda.graph(graph):
+        plan_step()
+    launches_per_step = R.kernel_launches()
+    for _ in range(args.warmup):
+        graph.replay()
+    graph_ms = timed(graph.replay, args.steps)
+    for c in scenes:
+        c["plan"].status()
+    clk = clocks.stop()
+    use_graph = graph_ms < eager_ms
+    ms = graph_ms if use_graph else eager_ms
+    value = total_states / (ms / 1e3)
+
+    # end to end: every scene's masks H2D from pinned memory, every MSE D2H, per step
+    res_host = [torch.empty(c["S"], dtype=torch.float64).pin_memory() for c in scenes]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        if use_graph:
+            for c in scenes:
+                c["g_masks"].copy_(c["host_masks"], non_blocking=True)
+            graph.replay()
+            for c, rh in zip(scenes, res_host):
+                rh.copy_(c["g_mse"], non_blocking=True)
+        else:
+            for c in scenes:
+                c["st"].masks.copy_(c["host_masks"], non_blocking=True)
+            for m, rh in zip(eager_step(), res_host):
+                rh.copy_(m, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_value = total_states / ((time.perf_counter() - t0) / args.steps)
+    h2d = sum(c["host_masks"].numel() * 4 + c["w_t"].nbytes + c["w_cam"].nbytes for c in scenes)
+    d2h = total_states * 8
+
+    pk, pk_kind = _peaks()
+    sm_mhz = pk.get("sm_max_mhz", 2032.0)
+    fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    roof = None
+    if "raster_bwd" in prof:
+        bms, bn = prof["raster_bwd"]
+        # evaluations of all scenes' backward launches per step / their summed time per step
+        achieved = BWD_FLOP_PER_EVAL * evals_total / (bms / args.steps / 1e3) / 1e12
+        roof = {"kernel": "raster_bwd", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                "traffic_unit": "bytes per launch (ncu, full size)",
+                "peak_kind": "FP32 FMA issue peak: 148 SMs x 128 lanes x 2 x %.0f MHz (derived)" % sm_mhz,
+                "ms_per_launch": bms / max(bn, 1), "launches_per_step": bn / args.steps,
+                "evals_per_step": evals_total}
+    cpu = None if args.no_cpu_baseline else {
+        "value": total_states / oracle_sec, "unit": UNIT, "cores": threads, "kind": "oracle",
+        "sample": "per scene, 1 state: projection + 4 bands of 2 whole rows (FP64 forward on %s threads), "
+                  "adjoint fixed part + 64 random pixels (1 thread), extrapolated to the scene's 64 states"
+                  % threads}
+    sizes = [c["spec"].n for c in scenes]
+    cfg = {"workload": "c5_mix_48", "scenes": len(scenes), "gaussians_total": int(sum(sizes)),
+           "gaussians_min": int(min(sizes)), "gaussians_max": int(max(sizes)), "sh_degree": 3,
+           "states_per_step": total_states, "states_per_scene": 64,
+           "resolutions": sorted({"%dx%d" % (c["W"], c["H"]) for c in scenes}),
+           "pixels_per_step": int(total_px), "l2": "flushed between timed steps (256 MB write)",
+           "parallelism": "dp1", "path": "cuda_graph_arena_plans" if use_graph else "context_calls",
+           "generation_s": round(t_gen, 1)}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+            "mpix_per_s": total_px / (ms / 1e3) / 1e6,
+            "eager_per_step": {"ms": eager_ms, "value": total_states / (eager_ms / 1e3), "unit": UNIT,
+                               "what": "context calls, scene after scene"},
+            "graph_per_step": {"ms": graph_ms, "value": total_states / (graph_ms / 1e3), "unit": UNIT,
+                               "what": "one CUDA graph of every scene's plan (one arena)"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": (launches_per_step * args.steps) if use_graph else eager_launches,
+            "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
+            "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}, "peaks": pk_kind}
+    print(json.dumps(line), flush=True)
+    for c in scenes:
+        c["plan"].close()
+    arena.close()
+    R.close()
 
 
 def main():
@@ -228,6 +428,14 @@ def main():
 
     from paper_2606_17212_b300 import synth
     ws, rank, local = _dist()
+    if args.workload == "c5_mix_48":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the serving mix has no reference-arm mode; "
+                              "its oracle baseline is the cpu_baseline of the ours arm"}), flush=True)
+            return
+        if rank == 0:
+            run_mix(args)
+        return
     w = synth.config(args.workload, scale=args.scale, n_states=args.states)
     if args.impl == "reference":
         reference_arm(args, w)
@@ -411,7 +619,7 @@ def main():
     evals_per_px = None
     if rank == 0:
         n_samp = 2 if training else 4
-        sec_state, evals_per_px, threads, desc = oracle_sample(w, n_states=n_samp, n_pix=1024,
+        sec_state, evals_per_px, threads, desc = oracle_sample(w, n_states=n_samp, n_bands=16, n_pix=1024,
                                                                 want_backward=training)
         if not args.no_cpu_baseline:
             cpu = {"value": 1.0 / sec_state, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}

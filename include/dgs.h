@@ -221,9 +221,28 @@ DGS_API int dgs_image_mse(dgs_ctx *ctx, const float *images, const float *refs, 
  */
 typedef struct dgs_plan dgs_plan;
 enum { DGS_PLAN_RENDER = 1, DGS_PLAN_UTILITY = 2 };
+
+/*
+ * Arenas: one scratch workspace (records, keys, tile entries, sort and raster
+ * buffers) shared by every plan created in it, for batches of plans that run
+ * one after another on one stream, e.g. many scenes in one CUDA graph (the
+ * scratch is sized to the largest plan, not the sum).  Each plan keeps its
+ * own small tables.  Rules: create every plan of an arena before capturing
+ * any of them (a later creation may reallocate the scratch); a plan's
+ * dgs_plan_backward must follow its own dgs_plan_render with no other plan of
+ * the arena run in between (checked on the host: DGS_E_INVALID_ARG);
+ * destroy the plans before the arena (dgs_arena_destroy returns
+ * DGS_E_INVALID_ARG while plans remain).  Error messages of the arena's plans
+ * share one string.
+ */
+typedef struct dgs_arena dgs_arena;
+DGS_API int dgs_arena_create(dgs_ctx *ctx, dgs_arena **out);
+DGS_API int dgs_arena_destroy(dgs_arena *arena);
+
+/* arena: NULL for a private workspace. */
 DGS_API int dgs_plan_create(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states, const dgs_camera *cams,
                             int n_cams, const float *bg, int mode, const int32_t *ref_index /*[host] [n_states] or NULL*/,
-                            int n_refs, float entry_headroom, dgs_plan **out);
+                            int n_refs, float entry_headroom, dgs_arena *arena, dgs_plan **out);
 DGS_API void dgs_plan_destroy(dgs_plan *plan);
 DGS_API const char *dgs_plan_last_error(const dgs_plan *plan);
 /* images [device] [n_states][H][W][3]: as dgs_render_states_batched. */

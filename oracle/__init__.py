@@ -85,6 +85,9 @@ def _load():
         lib.o_render.argtypes = [ctypes.POINTER(_OScene), P, ctypes.c_double, ctypes.POINTER(_OCam),
                                  P, ctypes.c_int, P, P, P, P, ctypes.c_int, ctypes.POINTER(_OEps)]
         lib.o_render.restype = ctypes.c_int64
+        lib.o_render_rows.argtypes = [ctypes.POINTER(_OScene), P, ctypes.c_double, ctypes.POINTER(_OCam), P,
+                                      ctypes.c_int, ctypes.c_int, P, P, P]
+        lib.o_render_rows.restype = ctypes.c_int64
         lib.o_render_backward.argtypes = [ctypes.POINTER(_OScene), P, ctypes.c_double,
                                           ctypes.POINTER(_OCam), P, P] + [P] * 8
         lib.o_sh_basis.argtypes = [P, ctypes.c_int, P]
@@ -167,6 +170,23 @@ def render(scene, depth, t, cam, bg, pix=None, full_scan=False, eps=None):
         lib.o_render(ctypes.byref(pin.s), _ptr(d), float(t), ctypes.byref(oc), _ptr(bgd),
                      p.shape[0], _ptr(p), _ptr(img), _ptr(marg), _ptr(n_eval), 1,
                      ctypes.byref(e) if e else None)
+    return img, marg.astype(bool), int(n_eval[0])
+
+
+def render_rows(scene, depth, t, cam, bg, y0, y1):
+    """Rows [y0, y1) of one state's image, rendered exactly as the whole image
+    (same row filter); a bounded sample for timing the oracle.  Returns
+    (image rows FP64 [y1-y0, W, 3], marginal flags, evaluations)."""
+    lib = _load()
+    pin = _Pinned(scene)
+    d = np.ascontiguousarray(depth, dtype=np.uint8)
+    oc = _cam(cam)
+    bgd = np.ascontiguousarray(bg, dtype=np.float64)
+    n_eval = np.zeros(1, np.int64)
+    img = np.zeros((y1 - y0, cam.width, 3), np.float64)
+    marg = np.zeros((y1 - y0, cam.width), np.uint8)
+    lib.o_render_rows(ctypes.byref(pin.s), _ptr(d), float(t), ctypes.byref(oc), _ptr(bgd), int(y0), int(y1),
+                      _ptr(img), _ptr(marg), _ptr(n_eval))
     return img, marg.astype(bool), int(n_eval[0])
 
 

@@ -471,6 +471,44 @@ static int row_candidates(const ORec *recs, int m, int py, int *list)
  * full_scan != 0 walks the whole sorted list per pixel (brute force).
  * eps == NULL uses the default tolerances.  Returns the marginal count.
  */
+/* Rows [y0, y1) of the image into image_out [(y1 - y0)][W][3] (marg likewise). */
+static void render_rows(const ORec *recs, int m, int W, int y0, int y1, const double *bg, const OEps *eps,
+                        int full_scan, double *image_out, uint8_t *marg, int64_t *total_marg, int64_t *total_eval)
+{
+    int64_t tm = 0, te = 0;
+    #pragma omp parallel for schedule(dynamic, 1) reduction(+:tm, te)
+    for (int py = y0; py < y1; ++py) {
+        int *list = (int *)malloc(sizeof(int) * (size_t)(m > 0 ? m : 1));
+        int nl;
+        if (full_scan) { for (int k = 0; k < m; ++k) list[k] = k; nl = m; }
+        else nl = row_candidates(recs, m, py, list);
+        for (int px = 0; px < W; ++px) {
+            int mg = 0; int64_t ne = 0;
+            const size_t o = (size_t)(py - y0) * W + px;
+            shade_pixel(recs, list, nl, px, py, bg, eps, image_out + o * 3, &mg, &ne);
+            if (marg) marg[o] = (uint8_t)mg;
+            tm += mg; te += ne;
+        }
+        free(list);
+    }
+    *total_marg += tm;
+    *total_eval += te;
+}
+
+/* A band of whole rows [y0, y1) (row filter as in the full render): the
+ * bounded sample a timing of the oracle extrapolates from. */
+int64_t o_render_rows(const OScene *s, const uint8_t *depth, double t, const OCam *cam, const double *bg,
+                      int y0, int y1, double *image_out, uint8_t *marg, int64_t *n_eval)
+{
+    int m = 0;
+    ORec *recs = project_sorted(s, depth, t, cam, &kDefaultEps, &m);
+    int64_t total_marg = 0, total_eval = 0;
+    render_rows(recs, m, cam->width, y0, y1, bg, &kDefaultEps, 0, image_out, marg, &total_marg, &total_eval);
+    free(recs);
+    if (n_eval) *n_eval = total_eval;
+    return total_marg;
+}
+
 int64_t o_render(const OScene *s, const uint8_t *depth, double t, const OCam *cam,
                  const double *bg, int npix, const int32_t *pix, double *image_out,
                  uint8_t *marg, int64_t *n_eval, int full_scan, const OEps *eps_in)
@@ -481,20 +519,7 @@ int64_t o_render(const OScene *s, const uint8_t *depth, double t, const OCam *ca
     int64_t total_marg = 0, total_eval = 0;
     int W = cam->width, H = cam->height;
     if (pix == NULL) {
-        #pragma omp parallel for schedule(dynamic, 1) reduction(+:total_marg, total_eval)
-        for (int py = 0; py < H; ++py) {
-            int *list = (int *)malloc(sizeof(int) * (size_t)(m > 0 ? m : 1));
-            int nl;
-            if (full_scan) { for (int k = 0; k < m; ++k) list[k] = k; nl = m; }
-            else nl = row_candidates(recs, m, py, list);
-            for (int px = 0; px < W; ++px) {
-                int mg = 0; int64_t ne = 0;
-                shade_pixel(recs, list, nl, px, py, bg, eps, image_out + ((size_t)py * W + px) * 3, &mg, &ne);
-                if (marg) marg[(size_t)py * W + px] = (uint8_t)mg;
-                total_marg += mg; total_eval += ne;
-            }
-            free(list);
-        }
+        render_rows(recs, m, W, 0, H, bg, eps, full_scan, image_out, marg, &total_marg, &total_eval);
     } else {
         #pragma omp parallel for schedule(dynamic, 16) reduction(+:total_marg, total_eval)
         for (int q = 0; q < npix; ++q) {

@@ -580,8 +580,18 @@ int render_batched(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *state
 // size depends only on the plan, nothing is allocated, copied from the host or
 // synchronised, so a caller can capture them in a CUDA graph and replay them
 // with new masks (and new scene values) of the same shapes.
+// Scratch workspace shared by the plans created in it (they run one after
+// another on one stream): records, keys, entries, sort and raster buffers.
+struct dgs_arena {
+    dgs_ctx ws;
+    int plans = 0;
+    const dgs_plan *last = nullptr;   // the plan whose lists the scratch holds
+};
+
 struct dgs_plan {
-    dgs_ctx ws;                   // private workspace and error message
+    dgs_ctx ws;                   // the plan's own tables (vgs, vgos, refidx), host staging, error message
+    dgs_ctx *sc = nullptr;        // scratch buffers: &ws, or the arena's workspace
+    dgs_arena *arena = nullptr;
     Plan p;
     dgs_scene scene{};
     float bg[3] = {0, 0, 0};
@@ -601,6 +611,7 @@ namespace {
 int plan_fail(dgs_plan *P, int code, const char *msg)
 {
     P->ws.err = msg;
+    P->sc->err = msg;
     return code;
 }
 
@@ -608,7 +619,7 @@ int plan_fail(dgs_plan *P, int code, const char *msg)
 // tile order with every count kept on the device.
 int prepare_dev(dgs_plan *P, const uint32_t *masks, bool force_full, cudaStream_t st)
 {
-    dgs_ctx *ctx = &P->ws;
+    dgs_ctx *ctx = P->sc;
     const Plan &p = P->p;
     const dgs_scene *scene = &P->scene;
     const int C = scene->n_clusters, L = scene->n_layers;
@@ -617,13 +628,13 @@ int prepare_dev(dgs_plan *P, const uint32_t *masks, bool force_full, cudaStream_
     uint32_t *cnt = (uint32_t *)P->cnts.p;
     CK(cudaMemsetAsync(ctx->need.p, 0, 4 * nvc, st));
     if (p.S_user > 0)
-        launch_closure(masks, p.S_user, words, C, L, (const int32_t *)ctx->vgos.p, (uint8_t *)ctx->depth.p,
+        launch_closure(masks, p.S_user, words, C, L, (const int32_t *)P->ws.vgos.p, (uint8_t *)ctx->depth.p,
                        (uint32_t *)ctx->need.p, force_full ? 1 : 0, ctx->sms, st);
     launch_layout_counts((const uint32_t *)ctx->need.p, scene->cluster_offsets, p.V, C, (uint32_t *)ctx->counts.p,
                          ctx->sms, st);
     CK(exclusive_scan_u32((const uint32_t *)ctx->counts.p, (uint32_t *)ctx->recBase.p, nvc + 1, cnt + 0,
                           ctx->scanws.p, st));
-    launch_project(scene_dev(scene), (const ViewGroup *)ctx->vgs.p, p.V, (const uint32_t *)ctx->need.p,
+    launch_project(scene_dev(scene), (const ViewGroup *)P->ws.vgs.p, p.V, (const uint32_t *)ctx->need.p,
                    (const uint32_t *)ctx->recBase.p, (Rec *)ctx->recs.p, (uint32_t *)ctx->k0.p, (uint32_t *)ctx->v0.p,
                    ctx->sms, st);
     bool alt = false;
@@ -680,9 +691,26 @@ int tuned_choice(dgs_ctx *ctx, const dgs_scene *scene, const Plan &p, int s0, in
     return it == ctx->tuned_G.end() ? 1 : it->second;
 }
 
+// Free every device and host buffer a workspace holds (not the workspace itself).
+void free_ctx_buffers(dgs_ctx *ctx)
+{
+    Buf *bufs[] = {&ctx->vgs, &ctx->vgos, &ctx->depth, &ctx->need, &ctx->counts, &ctx->recBase, &ctx->total,
+                   &ctx->recs, &ctx->k0, &ctx->v0, &ctx->k1, &ctx->v1, &ctx->tcount, &ctx->toffs, &ctx->ek0,
+                   &ctx->ev0, &ctx->ek1, &ctx->ev1, &ctx->ranges, &ctx->sortws, &ctx->scanws, &ctx->partial,
+                   &ctx->refs, &ctx->recgrad, &ctx->refidx, &ctx->tck0, &ctx->tcv0, &ctx->tck1, &ctx->tcv1,
+                   &ctx->icnt, &ctx->ioff, &ctx->qint, &ctx->counter};
+    for (Buf *b : bufs)
+        if (b->p) { cudaFree(b->p); b->p = nullptr; b->cap = 0; }
+    if (ctx->h_stage) { cudaFreeHost(ctx->h_stage); ctx->h_stage = nullptr; }
+    if (ctx->h_small) { cudaFreeHost(ctx->h_small); ctx->h_small = nullptr; }
+    if (ctx->stage_done) { cudaEventDestroy(ctx->stage_done); ctx->stage_done = nullptr; }
+}
+
 RasterArgs plan_raster_args(dgs_plan *P)
 {
-    return raster_args(&P->ws, P->p, P->scene.n_clusters, P->bg, P->L.evals);
+    RasterArgs a = raster_args(P->sc, P->p, P->scene.n_clusters, P->bg, P->L.evals);
+    a.vg_of_state = (const int32_t *)P->ws.vgos.p;
+    return a;
 }
 
 }  // namespace
@@ -720,19 +748,7 @@ void dgs_destroy(dgs_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
-    Buf *bufs[] = {&ctx->vgs, &ctx->vgos, &ctx->depth, &ctx->need, &ctx->counts, &ctx->recBase, &ctx->total,
-                   &ctx->recs, &ctx->k0, &ctx->v0, &ctx->k1, &ctx->v1, &ctx->tcount, &ctx->toffs, &ctx->ek0,
-                   &ctx->ev0, &ctx->ek1, &ctx->ev1, &ctx->ranges, &ctx->sortws, &ctx->scanws, &ctx->partial,
-                   &ctx->refs, &ctx->recgrad, &ctx->refidx};
-    Buf *more[] = {&ctx->tck0, &ctx->tcv0, &ctx->tck1, &ctx->tcv1, &ctx->icnt, &ctx->ioff, &ctx->qint,
-                   &ctx->counter};
-    for (Buf *b : bufs)
-        if (b->p) cudaFree(b->p);
-    for (Buf *b : more)
-        if (b->p) cudaFree(b->p);
-    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
-    if (ctx->h_small) cudaFreeHost(ctx->h_small);
-    if (ctx->stage_done) cudaEventDestroy(ctx->stage_done);
+    free_ctx_buffers(ctx);
     delete ctx;
 }
 
@@ -939,9 +955,36 @@ int dgs_image_mse(dgs_ctx *ctx, const float *images, const float *refs, const in
 }
 
 
+int dgs_arena_create(dgs_ctx *ctx, dgs_arena **out)
+{
+    if (!ctx || !out) return DGS_E_INVALID_ARG;
+    *out = nullptr;
+    CK(cudaSetDevice(ctx->device));
+    dgs_arena *A = new dgs_arena();
+    A->ws.device = ctx->device;
+    A->ws.sms = ctx->sms;
+    if (cudaMallocHost((void **)&A->ws.h_small, 64 + 4 * (MAX_CLUSTERS + 1)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&A->ws.stage_done, cudaEventDisableTiming) != cudaSuccess) {
+        if (A->ws.h_small) cudaFreeHost(A->ws.h_small);
+        delete A;
+        return fail(ctx, DGS_E_OOM, "arena host allocation failed");
+    }
+    *out = A;
+    return DGS_OK;
+}
+
+int dgs_arena_destroy(dgs_arena *A)
+{
+    if (!A) return DGS_OK;
+    if (A->plans > 0) return DGS_E_INVALID_ARG;
+    free_ctx_buffers(&A->ws);
+    delete A;
+    return DGS_OK;
+}
+
 int dgs_plan_create(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states, const dgs_camera *cams,
                     int n_cams, const float *bg, int mode, const int32_t *ref_index, int n_refs,
-                    float entry_headroom, dgs_plan **out)
+                    float entry_headroom, dgs_arena *arena, dgs_plan **out)
 {
     if (!ctx || !out) return DGS_E_INVALID_ARG;
     *out = nullptr;
@@ -959,12 +1002,16 @@ int dgs_plan_create(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *stat
                 return fail(ctx, DGS_E_INVALID_ARG, "ref_index[%d] out of range", s);
     }
     if (!(entry_headroom >= 1.0f)) entry_headroom = 1.25f;
+    if (arena && arena->ws.device != ctx->device) return fail(ctx, DGS_E_INVALID_ARG, "arena is on another device");
     dgs_plan *P = new dgs_plan();
-    dgs_ctx *w = &P->ws;
-    w->device = ctx->device;
-    w->sms = ctx->sms;
-    if (cudaMallocHost((void **)&w->h_small, 64 + 4 * (MAX_CLUSTERS + 1)) != cudaSuccess ||
-        cudaEventCreateWithFlags(&w->stage_done, cudaEventDisableTiming) != cudaSuccess) {
+    dgs_ctx *own = &P->ws;
+    own->device = ctx->device;
+    own->sms = ctx->sms;
+    P->arena = arena;
+    P->sc = arena ? &arena->ws : own;
+    dgs_ctx *w = P->sc;             // scratch: sizing runs, capacities, tuning
+    if (cudaMallocHost((void **)&own->h_small, 64 + 4 * (MAX_CLUSTERS + 1)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&own->stage_done, cudaEventDisableTiming) != cudaSuccess) {
         dgs_plan_destroy(P);
         return fail(ctx, DGS_E_OOM, "plan host allocation failed");
     }
@@ -1015,8 +1062,8 @@ int dgs_plan_create(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *stat
         if (ref_index) {
             P->n_refs = n_refs;
             P->image_parts = mse_parts(p.H, p.W);
-            if ((r = ensure(w, w->refidx, 4 * (size_t)p.S_user, st)) != DGS_OK) break;
-            CK(cudaMemcpy(w->refidx.p, ref_index, 4 * (size_t)p.S_user, cudaMemcpyHostToDevice));
+            if ((r = ensure(own, own->refidx, 4 * (size_t)p.S_user, st)) != DGS_OK) break;
+            CK(cudaMemcpy(own->refidx.p, ref_index, 4 * (size_t)p.S_user, cudaMemcpyHostToDevice));
             if ((r = ensure(w, w->partial, sizeof(double) * (size_t)p.S_user *
                                                std::max<size_t>(P->image_parts, p.tiles), st)) != DGS_OK) break;
         }
@@ -1025,6 +1072,12 @@ int dgs_plan_create(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *stat
         // then tune states-per-block on it and upload the tables.
         if ((r = prepare(w, scene, states->masks, p, mode == DGS_PLAN_UTILITY, st, L0)) != DGS_OK) break;
         CK(cudaDeviceSynchronize());
+        if (arena) {   // the plan's own copies of its view-group tables (the arena's are overwritten by others)
+            if ((r = ensure(own, own->vgs, sizeof(ViewGroup) * (size_t)p.V, st)) != DGS_OK) break;
+            if ((r = ensure(own, own->vgos, sizeof(int32_t) * (size_t)p.S, st)) != DGS_OK) break;
+            CK(cudaMemcpy(own->vgs.p, w->vgs.p, sizeof(ViewGroup) * (size_t)p.V, cudaMemcpyDeviceToDevice));
+            CK(cudaMemcpy(own->vgos.p, w->vgos.p, sizeof(int32_t) * (size_t)p.S, cudaMemcpyDeviceToDevice));
+        }
         RasterArgs a = raster_args(w, p, scene->n_clusters, P->bg, L0.evals);
         if (mode == DGS_PLAN_RENDER) {
             float *tmp = nullptr;
@@ -1060,6 +1113,7 @@ int dgs_plan_create(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *stat
         dgs_plan_destroy(P);
         return r;
     }
+    if (arena) ++arena->plans;
     *out = P;
     return DGS_OK;
 }
@@ -1069,34 +1123,33 @@ void dgs_plan_destroy(dgs_plan *P)
     if (!P) return;
     cudaSetDevice(P->ws.device);
     cudaDeviceSynchronize();
-    dgs_ctx *w = &P->ws;
-    Buf *bufs[] = {&w->vgs, &w->vgos, &w->depth, &w->need, &w->counts, &w->recBase, &w->total, &w->recs, &w->k0,
-                   &w->v0, &w->k1, &w->v1, &w->tcount, &w->toffs, &w->ek0, &w->ev0, &w->ek1, &w->ev1, &w->ranges,
-                   &w->sortws, &w->scanws, &w->partial, &w->refs, &w->recgrad, &w->refidx, &w->tck0, &w->tcv0,
-                   &w->tck1, &w->tcv1, &w->icnt, &w->ioff, &w->qint, &w->counter, &P->cnts, &P->qfwd, &P->qref};
-    for (Buf *b : bufs)
+    Buf *own[] = {&P->cnts, &P->qfwd, &P->qref};
+    for (Buf *b : own)
         if (b->p) cudaFree(b->p);
-    if (w->h_stage) cudaFreeHost(w->h_stage);
-    if (w->h_small) cudaFreeHost(w->h_small);
-    if (w->stage_done) cudaEventDestroy(w->stage_done);
+    free_ctx_buffers(&P->ws);          // with an arena: only the plan's tables live here
+    if (P->arena) {
+        --P->arena->plans;
+        if (P->arena->last == P) P->arena->last = nullptr;
+    }
     delete P;
 }
 
-const char *dgs_plan_last_error(const dgs_plan *P) { return P ? P->ws.err.c_str() : "null plan"; }
+const char *dgs_plan_last_error(const dgs_plan *P) { return P ? P->sc->err.c_str() : "null plan"; }
 
 int dgs_plan_render(dgs_plan *P, const uint32_t *masks, float *images, dgs_stream stream)
 {
     if (!P) return DGS_E_INVALID_ARG;
     if (P->mode != DGS_PLAN_RENDER) return plan_fail(P, DGS_E_INVALID_ARG, "plan was not made for rendering");
     if (!masks || !images) return plan_fail(P, DGS_E_INVALID_ARG, "masks or images is null");
-    dgs_ctx *ctx = &P->ws;
+    dgs_ctx *ctx = P->sc;
     CK(cudaSetDevice(P->ws.device));
     cudaStream_t st = (cudaStream_t)stream;
     TRY(prepare_dev(P, masks, false, st));
     RasterArgs a = plan_raster_args(P);
     a.images = images;
-    TRY(launch_queue(&P->ws, P->p, P->L, a, P->tfwd, st));
+    TRY(launch_queue(ctx, P->p, P->L, a, P->tfwd, st));
     P->rendered = true;
+    if (P->arena) P->arena->last = P;
     return DGS_OK;
 }
 
@@ -1105,12 +1158,14 @@ int dgs_plan_backward(dgs_plan *P, const float *images, const float *dL_dimages,
 {
     if (!P) return DGS_E_INVALID_ARG;
     if (!P->rendered) return plan_fail(P, DGS_E_INVALID_ARG, "dgs_plan_backward needs a dgs_plan_render first");
+    if (P->arena && P->arena->last != P)
+        return plan_fail(P, DGS_E_INVALID_ARG, "another plan of the arena ran after this plan's render");
     if (!dL_dimages || !grads) return plan_fail(P, DGS_E_INVALID_ARG, "dL_dimages or grads is null");
     const dgs_scene *scene = &P->scene;
     if (!grads->mu0 || !grads->log_scale || !grads->quat || !grads->opacity_logit || !grads->colour ||
         (scene->temporal_rank > 0 && !grads->u) || (scene->n_layers > 1 && !grads->res))
         return plan_fail(P, DGS_E_INVALID_ARG, "gradient array is null");
-    dgs_ctx *ctx = &P->ws;
+    dgs_ctx *ctx = P->sc;
     CK(cudaSetDevice(P->ws.device));
     cudaStream_t st = (cudaStream_t)stream;
     launch_zero_prefix((uint32_t *)ctx->recgrad.p, P->R_cap, (const uint32_t *)P->cnts.p, 12, ctx->sms, st);
@@ -1123,7 +1178,7 @@ int dgs_plan_backward(dgs_plan *P, const float *images, const float *dL_dimages,
     GradDev g;
     g.mu0 = grads->mu0; g.u = grads->u; g.ls = grads->log_scale; g.quat = grads->quat;
     g.logit = grads->opacity_logit; g.colour = grads->colour; g.res = grads->res;
-    launch_project_bwd(scene_dev(scene), (const ViewGroup *)ctx->vgs.p, P->p.V, (const uint32_t *)ctx->need.p,
+    launch_project_bwd(scene_dev(scene), (const ViewGroup *)P->ws.vgs.p, P->p.V, (const uint32_t *)ctx->need.p,
                        (const uint32_t *)ctx->recBase.p, (const float4 *)ctx->recgrad.p, g, ctx->sms, st);
     CK(cudaGetLastError());
     return DGS_OK;
@@ -1134,17 +1189,18 @@ int dgs_plan_utility(dgs_plan *P, const uint32_t *masks, double *mse, double *ps
     if (!P) return DGS_E_INVALID_ARG;
     if (P->mode != DGS_PLAN_UTILITY) return plan_fail(P, DGS_E_INVALID_ARG, "plan was not made for utility");
     if (!masks || !mse) return plan_fail(P, DGS_E_INVALID_ARG, "masks or mse is null");
-    dgs_ctx *ctx = &P->ws;
+    dgs_ctx *ctx = P->sc;
     CK(cudaSetDevice(P->ws.device));
     cudaStream_t st = (cudaStream_t)stream;
     TRY(prepare_dev(P, masks, true, st));
+    if (P->arena) P->arena->last = P;
     RasterArgs r = plan_raster_args(P);
     r.images = (float *)ctx->refs.p;
     r.img_s0 = P->p.S_user;
     TRY(launch_queue(ctx, P->p, P->L, r, P->tref, st));
     RasterArgs a = plan_raster_args(P);
     a.refs = (const float *)ctx->refs.p;
-    a.ref_of_state = (const int32_t *)ctx->vgos.p;
+    a.ref_of_state = (const int32_t *)P->ws.vgos.p;
     a.partial = (double *)ctx->partial.p;
     TRY(launch_queue(ctx, P->p, P->L, a, P->tfwd, st));
     launch_mse_reduce((const double *)ctx->partial.p, P->p.S_user, (int)P->p.tiles,
@@ -1159,10 +1215,10 @@ int dgs_plan_image_mse(dgs_plan *P, const float *images, const float *refs, floa
     if (!P) return DGS_E_INVALID_ARG;
     if (P->n_refs < 1) return plan_fail(P, DGS_E_INVALID_ARG, "plan was made without ref_index");
     if (!images || !refs || !mse) return plan_fail(P, DGS_E_INVALID_ARG, "null argument");
-    dgs_ctx *ctx = &P->ws;
+    dgs_ctx *ctx = P->sc;
     CK(cudaSetDevice(P->ws.device));
     cudaStream_t st = (cudaStream_t)stream;
-    launch_image_mse(images, refs, (const int32_t *)ctx->refidx.p, P->p.S_user, P->p.H, P->p.W, weight,
+    launch_image_mse(images, refs, (const int32_t *)P->ws.refidx.p, P->p.S_user, P->p.H, P->p.W, weight,
                      (double *)ctx->partial.p, P->image_parts, dL_dimages, st);
     launch_mse_reduce((const double *)ctx->partial.p, P->p.S_user, P->image_parts,
                       1.0 / (double)((size_t)P->p.W * P->p.H * 3), mse, psnr, st);

@@ -51,7 +51,7 @@ EXPORTS = ("dgs_create", "dgs_destroy", "dgs_last_error", "dgs_version", "dgs_re
            "dgs_kernel_launches", "dgs_reset_kernel_launches", "dgs_profile_enable", "dgs_profile_read",
            "dgs_image_mse_noalloc", "dgs_debug_tile_lists", "dgs_plan_create", "dgs_plan_destroy",
            "dgs_plan_last_error", "dgs_plan_render", "dgs_plan_backward", "dgs_plan_utility",
-           "dgs_plan_image_mse", "dgs_plan_status")
+           "dgs_plan_image_mse", "dgs_plan_status", "dgs_arena_create", "dgs_arena_destroy")
 PLAN_RENDER, PLAN_UTILITY = 1, 2
 
 _lib = None
@@ -91,7 +91,9 @@ def lib():
         L.dgs_debug_tile_lists.argtypes = [P] * 11 + [P]
         L.dgs_debug_tile_lists.restype = I
         L.dgs_plan_create.argtypes = [P, ctypes.POINTER(Scene_t), ctypes.POINTER(States_t), P, I, P, I, P, I, F,
-                                      ctypes.POINTER(P)]
+                                      P, ctypes.POINTER(P)]
+        L.dgs_arena_create.argtypes = [P, ctypes.POINTER(P)]
+        L.dgs_arena_destroy.argtypes = [P]
         L.dgs_plan_destroy.argtypes = [P]
         L.dgs_plan_destroy.restype = None
         L.dgs_plan_last_error.argtypes = [P]
@@ -358,15 +360,44 @@ def image_mse_noalloc(images, refs, ref_index, mse, psnr=None, dL=None, weight=1
                                            _stream(stream)))
 
 
+class Arena:
+    """A scratch workspace shared by plans that run one after another on one
+    stream (see dgs_arena_create in include/dgs.h)."""
+
+    def __init__(self, renderer: Renderer):
+        self._lib = lib()
+        h = ctypes.c_void_p()
+        rc = self._lib.dgs_arena_create(renderer.h, ctypes.byref(h))
+        if rc != DGS_OK:
+            raise RuntimeError("dgs_arena_create failed (%s)" % ERRORS.get(rc, rc))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            rc = self._lib.dgs_arena_destroy(self.h)
+            if rc != DGS_OK:
+                raise RuntimeError("dgs_arena_destroy: plans of this arena are still alive")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Plan:
     """A capture-safe plan over a fixed batch (see dgs_plan_create in include/dgs.h).
 
     Per-step calls launch kernels only, so they can run inside a
-    ``torch.cuda.graph`` capture and be replayed with new masks."""
+    ``torch.cuda.graph`` capture and be replayed with new masks.  ``arena``
+    (an Arena) shares the scratch buffers with the arena's other plans."""
 
     def __init__(self, renderer: Renderer, scene: DeviceScene, states: DeviceStates, cams, bg,
-                 mode: int = PLAN_RENDER, ref_index=None, n_refs: int = 0, entry_headroom: float = 1.25):
+                 mode: int = PLAN_RENDER, ref_index=None, n_refs: int = 0, entry_headroom: float = 1.25,
+                 arena: "Arena | None" = None):
         self._lib = lib()
+        self.arena = arena
         self.scene, self.cams, self.n = scene, cams, states.n
         self.W, self.H = cams[0].width, cams[0].height
         self._keep = (scene.struct(), states.struct(), camera_array(cams),
@@ -377,7 +408,7 @@ class Plan:
         sc, st, ca, bgv = self._keep
         rc = self._lib.dgs_plan_create(renderer.h, ctypes.byref(sc), ctypes.byref(st), ca, len(cams), bgv, int(mode),
                                        None if ri is None else ri.ctypes.data_as(ctypes.c_void_p), int(n_refs),
-                                       float(entry_headroom), ctypes.byref(h))
+                                       float(entry_headroom), None if arena is None else arena.h, ctypes.byref(h))
         if rc != DGS_OK:
             raise RuntimeError("dgs_plan_create failed (%s): %s" % (ERRORS.get(rc, rc),
                                                                     self._lib.dgs_last_error(renderer.h).decode()))

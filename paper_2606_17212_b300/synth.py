@@ -34,7 +34,7 @@ import numpy as np
 __all__ = [
     "Scene", "Camera", "States", "Workload",
     "make_scene", "ring_camera", "prefix_states", "bernoulli_states",
-    "erase_one_packet", "mask_words", "config", "CONFIG_NAMES",
+    "erase_one_packet", "mask_words", "config", "CONFIG_NAMES", "MixSpec", "mix_specs", "mix_workload",
 ]
 
 
@@ -141,13 +141,53 @@ def _kmeans(x: np.ndarray, k: int, rng: np.random.Generator, iters: int = 8) -> 
     return assign
 
 
+def _nearest(x: np.ndarray, cent: np.ndarray) -> np.ndarray:
+    out = np.zeros(x.shape[0], dtype=np.int64)
+    c2 = (cent * cent).sum(1)
+    for s in range(0, x.shape[0], 1 << 16):
+        xs = x[s:s + (1 << 16)].astype(np.float64)
+        out[s:s + (1 << 16)] = np.argmin(c2[None, :] - 2.0 * xs @ cent.T, axis=1)
+    return out
+
+
+def _fast_normal(seed: int, tag: int, shape, mean: float, std: float) -> np.ndarray:
+    """float32 N(mean, std^2) filled in 16 fixed chunks, each from its own
+    PCG64 stream spawned from (seed, tag), on a thread pool: the values depend
+    only on (seed, tag, shape), not on the number of threads."""
+    from concurrent.futures import ThreadPoolExecutor
+    out = np.empty(int(np.prod(shape)), dtype=np.float32)
+    n = out.size
+    chunks = 16
+    gens = [np.random.Generator(np.random.PCG64(ss))
+            for ss in np.random.SeedSequence([seed, tag]).spawn(chunks)]
+
+    def fill(i):
+        lo, hi = i * n // chunks, (i + 1) * n // chunks
+        v = out[lo:hi]
+        gens[i].standard_normal(out=v, dtype=np.float32)
+        v *= np.float32(std)
+        v += np.float32(mean)
+
+    with ThreadPoolExecutor(8) as ex:
+        list(ex.map(fill, range(chunks)))
+    return out.reshape(shape)
+
+
 def make_scene(n: int, n_clusters: int, n_layers: int, *, seed: int,
                temporal_rank: int = 2, sh_degree: int = 0,
                residual_std: float = 0.05, residual_attrs: str = "all",
                mean_std: float = 1.0, log_scale_mean: float = -3.5,
                log_scale_std: float = 0.4, logit_std: float = 1.5,
-               u_std: float = 0.1, sh_std: float = 0.2) -> Scene:
-    """Draw a scene; ``residual_attrs`` is "all" or "colour_opacity"."""
+               u_std: float = 0.1, sh_std: float = 0.2, fast: bool = False) -> Scene:
+    """Draw a scene; ``residual_attrs`` is "all" or "colour_opacity".
+
+    ``fast`` (for the many large scenes of the serving mix) draws float32
+    values from parallel streams, fits the k-means centroids on a 65,536-point
+    subsample and assigns every Gaussian to its nearest centroid, and draws the
+    attributes that do not enter the clustering directly in cluster order."""
+    if fast:
+        return _make_scene_fast(n, n_clusters, n_layers, seed, temporal_rank, sh_degree, residual_std,
+                                mean_std, log_scale_mean, log_scale_std, logit_std, u_std, sh_std)
     rng = np.random.default_rng(seed)
     mu0 = rng.normal(0.0, mean_std, size=(n, 3))
     ls = rng.normal(log_scale_mean, log_scale_std, size=(n, 3))
@@ -181,6 +221,46 @@ def make_scene(n: int, n_clusters: int, n_layers: int, *, seed: int,
     return Scene(n, n_clusters, n_layers, sh_degree, temporal_rank, offs,
                  f32(mu0[order]), f32(u[:, order]), f32(ls[order]), f32(q[order]),
                  f32(logit[order]), f32(col[order]), f32(res[:, order]))
+
+
+def _make_scene_fast(n, n_clusters, n_layers, seed, temporal_rank, sh_degree, residual_std, mean_std,
+                     log_scale_mean, log_scale_std, logit_std, u_std, sh_std) -> Scene:
+    rng = np.random.default_rng(seed)
+    mu0 = _fast_normal(seed, 0, (n, 3), 0.0, mean_std)
+    u = _fast_normal(seed, 1, (temporal_rank, n, 3), 0.0, u_std)
+    feats = mu0 if temporal_rank == 0 else np.concatenate(
+        [mu0] + [u[r] for r in range(temporal_rank)], axis=1)
+    if n > 65536:
+        sub = rng.choice(n, size=65536, replace=False)
+        a_sub = _kmeans(feats[sub], n_clusters, rng)
+        cent = np.stack([feats[sub][a_sub == j].mean(0) if (a_sub == j).any() else feats[sub][0]
+                         for j in range(n_clusters)]).astype(np.float64)
+        assign = _nearest(feats, cent)
+    else:
+        assign = _kmeans(feats, n_clusters, rng)
+    order = np.argsort(assign, kind="stable")
+    counts = np.bincount(assign, minlength=n_clusters)
+    offs = np.zeros(n_clusters + 1, dtype=np.int32)
+    offs[1:] = np.cumsum(counts)
+    mu0 = np.ascontiguousarray(mu0[order])
+    u = np.ascontiguousarray(u[:, order])
+    # the remaining attributes are i.i.d. per Gaussian: drawn in cluster order
+    ls = _fast_normal(seed, 2, (n, 3), log_scale_mean, log_scale_std)
+    q = _fast_normal(seed, 3, (n, 4), 0.0, 1.0)
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    logit = _fast_normal(seed, 4, (n,), 0.0, logit_std)
+    nc = 3 * (sh_degree + 1) ** 2
+    if sh_degree == 0:
+        col = rng.uniform(0.0, 1.0, size=(n, 3)).astype(np.float32)
+    else:
+        col = _fast_normal(seed, 5, (n, nc), 0.0, sh_std)
+    K = 11 + nc
+    res = np.empty((max(n_layers - 1, 0), n, K), dtype=np.float32)
+    for l in range(1, n_layers):
+        res[l - 1] = _fast_normal(seed, 5 + l, (n, K), 0.0, residual_std * 2.0 ** (-(l - 1)))
+        if l == 1:
+            res[0, :, 0:3] = 0.0   # Eq. 1: position residuals only on the two finer levels
+    return Scene(n, n_clusters, n_layers, sh_degree, temporal_rank, offs, mu0, u, ls, q, logit, col, res)
 
 
 def ring_camera(k: int, n_ring: int, width: int, height: int, focal: float,
@@ -246,7 +326,50 @@ def erase_one_packet(bits: np.ndarray, frac: float, rng: np.random.Generator) ->
     return bits
 
 
-CONFIG_NAMES = ("c1_plain_4k", "c2_dynamic_250k", "c3_fwdbwd_250k", "c4_utility_2p7m")
+CONFIG_NAMES = ("c1_plain_4k", "c2_dynamic_250k", "c3_fwdbwd_250k", "c4_utility_2p7m", "c5_mix_48")
+
+MIX_RESOLUTIONS = ((256, 256), (512, 512), (960, 540))
+
+
+@dataclasses.dataclass
+class MixSpec:
+    """One scene of the serving-shaped mix: sizes drawn up front, scene drawn on demand."""
+    index: int
+    n: int
+    n_clusters: int
+    width: int
+    height: int
+    seed: int
+
+
+def mix_specs(n_scenes: int = 48, *, scale: float = 1.0) -> list:
+    """The uneven mix: Gaussian counts log-uniform in [50,000, 2,700,000],
+    clusters ~U{16..64}, 4 layers, resolution drawn from MIX_RESOLUTIONS."""
+    rng = np.random.default_rng(1005)
+    specs = []
+    for i in range(n_scenes):
+        n = int(round(np.exp(rng.uniform(np.log(5e4), np.log(2.7e6)))))
+        C = int(rng.integers(16, 65))
+        W, H = MIX_RESOLUTIONS[int(rng.integers(0, len(MIX_RESOLUTIONS)))]
+        if scale < 1.0:
+            n = max(64, int(round(n * scale)))
+            W, H = max(16, int(round(W * np.sqrt(scale)))), max(16, int(round(H * np.sqrt(scale))))
+        specs.append(MixSpec(i, n, C, W, H, 10_000 + i))
+    return specs
+
+
+def mix_workload(spec: MixSpec, n_states: int = 64) -> Workload:
+    """One scene of the mix: SH degree 3, rank-2 temporal basis, 4 layers;
+    64 prefix-valid states, state s at camera s mod 8 of a radius-4 ring and
+    t = (s mod 16)/16; focal 1.2 W.  The training target of each state is the
+    complete render of the same scene at its view (held fixed)."""
+    sc = make_scene(spec.n, spec.n_clusters, 4, seed=spec.seed, sh_degree=3, fast=True)
+    rng = np.random.default_rng(20_000 + spec.index)
+    d = prefix_states(n_states, spec.n_clusters, 4, rng)
+    t = (np.arange(n_states) % 16) / 16.0
+    cams = [ring_camera(k, 8, spec.width, spec.height, 1.2 * spec.width) for k in range(8)]
+    st = States(_pack(depths_to_bits(d, 4)), t.astype(np.float32), (np.arange(n_states) % 8).astype(np.int32))
+    return Workload("c5_mix_48/%d" % spec.index, sc, cams, st, np.zeros(3, np.float32))
 
 
 def config(name: str, *, scale: float = 1.0, n_states: int | None = None) -> Workload:

@@ -131,3 +131,42 @@ def test_utility_sweep_2p7m_full_size(R, torch):
     imgs = imgs_t.cpu().numpy()
     _check_sampled(w_sub, {k: imgs[k] for k in range(len(which))}, range(len(which)), np.random.default_rng(2),
                    n_pix=48)
+
+
+def test_serving_mix_scenes_full_size(R, torch):
+    """Serving-shaped mix (SH degree 3, 64 states per scene): the smallest
+    scene, the largest (2.47M Gaussians) and a 960x540 one at full size;
+    sampled pixels of the batched forward and the adjoint of sampled pixels
+    through the batched backward against the oracle."""
+    specs = synth.mix_specs()
+    by_n = sorted(specs, key=lambda s: s.n)
+    wide = [s for s in specs if (s.width, s.height) == (960, 540)]
+    pick = [by_n[0], by_n[-1], wide[len(wide) // 2]]
+    rng = np.random.default_rng(5)
+    for spec in pick:
+        w = synth.mix_workload(spec)
+        sc = dgs.DeviceScene.from_host(w.scene)
+        st = dgs.DeviceStates.from_host(w.states)
+        imgs_t = R.render_states_batched(sc, st, w.cams, w.bg)
+        which = [0, 37]
+        samp = _check_sampled(w, {s: imgs_t[s].cpu().numpy() for s in which}, which, rng, n_pix=64)
+        S, H, W = st.n, w.cams[0].height, w.cams[0].width
+        dL = np.zeros((S, H, W, 3), np.float32)
+        D = oracle.state_depths(w.states, w.scene.n_clusters, w.scene.n_layers)
+        ref = None
+        for s in which:
+            pix, marg = samp[s]
+            keep = pix[~marg]
+            dL[s, keep[:, 1], keep[:, 0]] = rng.normal(size=(len(keep), 3)).astype(np.float32)
+            g = oracle.render_backward(w.scene, D[s], float(w.states.t[s]), w.cams[int(w.states.cam[s])], w.bg,
+                                       dL[s].astype(np.float64))
+            ref = g if ref is None else {k: ref[k] + g[k] for k in ref}
+        grads = R.render_backward(sc, st, w.cams, w.bg, torch.from_numpy(dL).cuda(), images=imgs_t)
+        for k in dgs.SCENE_FIELDS:
+            gr = ref[k]
+            if gr.size == 0:
+                continue
+            gg = grads[k].cpu().numpy().astype(np.float64)
+            scale = max(np.abs(gr).max(), 1e-6)
+            assert np.abs(gg - gr).max() <= GRAD_TOL * scale, (spec.index, k, np.abs(gg - gr).max(), scale)
+        del sc, st, imgs_t, grads

@@ -132,3 +132,83 @@ def test_plan_reports_entry_overflow_without_faulting(R, torch):
         plan.status()
     plan.status()                             # the flag was cleared
     plan.close()
+
+
+def _mix_case(torch, R, spec, n_states):
+    w = synth.mix_workload(spec, n_states=n_states)
+    sc = dgs.DeviceScene.from_host(w.scene)
+    st = dgs.DeviceStates.from_host(w.states)
+    views = sorted(set(zip(w.states.cam.tolist(), w.states.t.tolist())))
+    ridx = np.array([views.index(v) for v in zip(w.states.cam.tolist(), w.states.t.tolist())], np.int32)
+    full = torch.full((len(views), st.masks.shape[1]), -1, dtype=torch.int32, device="cuda")
+    fv = dgs.DeviceStates(full, np.array([v[1] for v in views], np.float32), np.array([v[0] for v in views], np.int32))
+    targets = R.render_states_batched(sc, fv, w.cams, w.bg)
+    return w, sc, st, ridx, targets
+
+
+def test_arena_plans_of_several_scenes_in_one_graph(R, torch):
+    """Three scenes of the serving mix (SH degree 3, different sizes and
+    resolutions), one plan each in a shared arena, the training step of all
+    three captured in one CUDA graph: images equal the context calls bit for
+    bit, gradients up to float atomic order, after replays with new masks."""
+    specs = synth.mix_specs(scale=0.02)
+    pick = [specs[0], specs[1], specs[2]]
+    assert len({(s.width, s.height) for s in pick}) >= 2
+    arena = dgs.Arena(R)
+    cases = []
+    for spec in pick:
+        w, sc, st, ridx, targets = _mix_case(torch, R, spec, 12)
+        plan = dgs.Plan(R, sc, st, w.cams, w.bg, dgs.PLAN_RENDER, ref_index=ridx, n_refs=int(targets.shape[0]),
+                        entry_headroom=2.0, arena=arena)
+        S, H, W = st.n, w.cams[0].height, w.cams[0].width
+        cases.append(dict(w=w, sc=sc, st=st, ridx=ridx, targets=targets, plan=plan, masks=st.masks.clone(),
+                          images=torch.empty((S, H, W, 3), device="cuda"),
+                          mse=torch.empty(S, dtype=torch.float64, device="cuda"),
+                          psnr=torch.empty(S, dtype=torch.float64, device="cuda"),
+                          dL=torch.empty((S, H, W, 3), device="cuda"), grads=sc.zeros_like_grads()))
+
+    def step():
+        for c in cases:
+            for g in c["grads"].values():
+                g.zero_()
+            c["plan"].render(c["masks"], c["images"])
+            c["plan"].image_mse(c["images"], c["targets"], c["mse"], c["psnr"], c["dL"], weight=1.0 / c["st"].n)
+            c["plan"].backward(c["dL"], c["grads"], images=c["images"])
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    for seed in (3, 4):
+        for c in cases:
+            c["masks"].copy_(_masks(torch, c["w"], seed))
+        graph.replay()
+        torch.cuda.synchronize()
+        for c in cases:
+            c["plan"].status()
+            w, sc = c["w"], c["sc"]
+            st_new = dgs.DeviceStates(c["masks"], w.states.t, w.states.cam)
+            imgs = R.render_states_batched(sc, st_new, w.cams, w.bg)
+            assert torch.equal(c["images"], imgs)
+            mse, _, dL = R.image_mse(imgs, c["targets"], c["ridx"], weight=1.0 / st_new.n, want_grad=True)
+            assert torch.equal(c["mse"], mse)
+            g_ref = R.render_backward(sc, st_new, w.cams, w.bg, dL, images=imgs)
+            for k in dgs.SCENE_FIELDS:
+                if g_ref[k].numel():
+                    assert torch.allclose(c["grads"][k], g_ref[k], rtol=1e-4,
+                                          atol=1e-5 * float(g_ref[k].abs().max()) + 1e-12), (seed, k)
+    # a plan's backward must follow its own render within the arena
+    a, b = cases[0], cases[1]
+    a["plan"].render(a["masks"], a["images"])
+    b["plan"].render(b["masks"], b["images"])
+    with pytest.raises(RuntimeError, match="another plan of the arena"):
+        a["plan"].backward(a["dL"], a["grads"], images=a["images"])
+    with pytest.raises(RuntimeError, match="still alive"):
+        arena.close()
+    for c in cases:
+        c["plan"].close()
+    arena.close()

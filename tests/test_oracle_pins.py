@@ -536,3 +536,15 @@ def test_visible_box_contains_every_contributing_pixel():
                     assert vx0 <= px <= vx1 and vy0 <= py <= vy1
                     checked += 1
     assert checked > 1000
+
+
+def test_row_band_render_equals_full_render_rows():
+    """The row-band render used to time the oracle on a bounded sample gives
+    exactly the rows of the whole-image render."""
+    w = synth.config("c1_plain_4k")
+    D = oracle.closure(w.states.masks[0], w.scene.n_clusters, w.scene.n_layers)
+    full, marg, ne = oracle.render(w.scene, D, 0.0, w.cams[0], w.bg)
+    band, bmarg, bne = oracle.render_rows(w.scene, D, 0.0, w.cams[0], w.bg, 40, 57)
+    assert np.array_equal(band, full[40:57]) and np.array_equal(bmarg, marg[40:57])
+    parts = [oracle.render_rows(w.scene, D, 0.0, w.cams[0], w.bg, y, min(y + 32, 128))[2] for y in range(0, 128, 32)]
+    assert sum(parts) == ne

@@ -19,6 +19,8 @@ Functions and the passages of the paper they follow:
 * :func:`render_backward` -- adjoint of :func:`render`.
 * :func:`bin_tiles` -- tile lists ordered by the 64-bit (tile | depth) key with
   ties by Gaussian index then variant (an integer function).
+* :func:`group_utility` -- Eq. 3 marginal contribution of each completion group
+  over its sampled contexts and the risk-adjusted utility of Eq. 4.
 
 Every function is pinned by the CPU tests against closed forms, brute force,
 invariants and finite differences (see ``tests/test_oracle_pins.py``).
@@ -287,3 +289,43 @@ def bin_tiles(xlo, xhi, ylo, yhi, depth_bits, live, tile, tiles_x, tiles_y,
         hi = np.searchsorted(tid, k, side="right")
         ranges[k] = (lo, hi)
     return keys, vals, ranges
+
+
+def utility_stats(delta: np.ndarray, alpha: float = 0.25, beta: float = 0.05, q: float = 0.10):
+    """Eq. 4 over one group's contexts: returns (mean, Q_q, std, risk-adjusted
+    utility) with E_m the mean over the sampled contexts, Std_m the population
+    standard deviation, Q_q the quantile by linear interpolation between order
+    statistics (position q (M - 1) of the sorted values), and
+    utility = ((1 - alpha) mean + alpha Q_q) / (1 + beta std)."""
+    x = np.sort(np.asarray(delta, dtype=np.float64))
+    mean = float(np.mean(x))
+    std = float(np.sqrt(np.mean((x - mean) ** 2)))
+    h = q * (x.size - 1)
+    lo = int(np.floor(h))
+    hi = min(lo + 1, x.size - 1)
+    quant = float(x[lo] + (h - lo) * (x[hi] - x[lo]))
+    return mean, quant, std, ((1.0 - alpha) * mean + alpha * quant) / (1.0 + beta * std)
+
+
+def group_utility(scene, ctx_masks, groups, n_contexts, cam, t, bg, alpha=0.25, beta=0.05, q=0.10):
+    """Eq. 3 and Eq. 4.  ``ctx_masks`` [G * M, words]: context j of group g is
+    row g * M + j; ``groups`` [G, 2] = (cluster, layer) packets.  For every
+    context m: Delta_g(m) = D(I, R(m)) - D(I, R(m u g)) with D the MSE against
+    the complete render I at the same view (FP64 renders).  Returns
+    (delta [G, M], stats [G, 4] = mean, Q_q, std, utility)."""
+    G, M = len(groups), int(n_contexts)
+    L = scene.n_layers
+    full, _, _ = render(scene, full_depth(scene), t, cam, bg)
+    delta = np.zeros((G, M))
+    stats = np.zeros((G, 4))
+    for g, (c, l) in enumerate(groups):
+        bit = int(c) * L + int(l)
+        for j in range(M):
+            m = np.array(ctx_masks[g * M + j], dtype=np.uint32)
+            mg = m.copy()
+            mg[bit // 32] |= np.uint32(1 << (bit % 32))
+            d0 = mse_psnr(render(scene, closure(m, scene.n_clusters, L), t, cam, bg)[0], full)[0]
+            d1 = mse_psnr(render(scene, closure(mg, scene.n_clusters, L), t, cam, bg)[0], full)[0]
+            delta[g, j] = d0 - d1
+        stats[g] = utility_stats(delta[g], alpha, beta, q)
+    return delta, stats

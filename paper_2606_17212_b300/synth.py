@@ -35,6 +35,7 @@ __all__ = [
     "Scene", "Camera", "States", "Workload",
     "make_scene", "ring_camera", "prefix_states", "bernoulli_states",
     "erase_one_packet", "mask_words", "config", "CONFIG_NAMES", "MixSpec", "mix_specs", "mix_workload",
+    "completion_groups", "group_contexts",
 ]
 
 
@@ -324,6 +325,27 @@ def erase_one_packet(bits: np.ndarray, frac: float, rng: np.random.Generator) ->
         if on.size:
             bits[s, rng.choice(on)] = False
     return bits
+
+
+def completion_groups(n_clusters: int, n_layers: int, n_groups: int, rng: np.random.Generator) -> np.ndarray:
+    """n_groups distinct (cluster, layer) packets, uniformly drawn: [G, 2] int32."""
+    allg = np.array([(c, l) for c in range(n_clusters) for l in range(n_layers)], dtype=np.int32)
+    pick = rng.choice(len(allg), size=min(n_groups, len(allg)), replace=False)
+    return allg[np.sort(pick)]
+
+
+def group_contexts(groups: np.ndarray, n_contexts: int, n_clusters: int, n_layers: int,
+                   rng: np.random.Generator) -> np.ndarray:
+    """Valid partial receiver contexts for each completion group (cluster c,
+    layer l): prefix-valid masks whose cluster c holds exactly layers 0..l-1
+    (so adding the packet keeps the state valid and changes it) and every other
+    cluster a delivered depth ~U{0..L}.  Row g * n_contexts + j is context j of
+    group g; returns packed uint32 masks."""
+    G = len(groups)
+    d = rng.integers(0, n_layers + 1, size=(G * n_contexts, n_clusters))
+    for g, (c, l) in enumerate(groups):
+        d[g * n_contexts:(g + 1) * n_contexts, c] = l
+    return _pack(depths_to_bits(d, n_layers))
 
 
 CONFIG_NAMES = ("c1_plain_4k", "c2_dynamic_250k", "c3_fwdbwd_250k", "c4_utility_2p7m", "c5_mix_48")

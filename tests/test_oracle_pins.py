@@ -548,3 +548,52 @@ def test_row_band_render_equals_full_render_rows():
     assert np.array_equal(band, full[40:57]) and np.array_equal(bmarg, marg[40:57])
     parts = [oracle.render_rows(w.scene, D, 0.0, w.cams[0], w.bg, y, min(y + 32, 128))[2] for y in range(0, 128, 32)]
     assert sum(parts) == ne
+
+
+def test_utility_stats_hand_computed():
+    """Eq. 4 on values computed by hand: Delta = 1..10 gives mean 5.5, population
+    std sqrt(8.25), Q_0.1 at position 0.9 between 1 and 2 = 1.9."""
+    import math
+    mean, qv, std, u = oracle.utility_stats(np.arange(10, 0, -1, dtype=float))   # order must not matter
+    assert mean == 5.5 and abs(qv - 1.9) < 1e-15 and abs(std - math.sqrt(8.25)) < 1e-15
+    assert abs(u - (0.75 * 5.5 + 0.25 * 1.9) / (1 + 0.05 * math.sqrt(8.25))) < 1e-15
+    # constant contributions: every statistic equals the value, utility too
+    assert oracle.utility_stats(np.full(7, -0.3)) == pytest.approx((-0.3, -0.3, 0.0, -0.3), abs=1e-15)
+    # one context: the quantile is that value
+    assert oracle.utility_stats(np.array([2.0]), alpha=0.5, beta=1.0) == (2.0, 2.0, 0.0, 2.0)
+    # q = 0 is the minimum, q = 1 the maximum
+    assert oracle.utility_stats(np.array([3.0, -1.0, 2.0]), q=0.0)[1] == -1.0
+    assert oracle.utility_stats(np.array([3.0, -1.0, 2.0]), q=1.0)[1] == 3.0
+
+
+def test_group_utility_special_cases():
+    """Eq. 3: a packet of a cluster with no Gaussian in view contributes exactly
+    0 in every context; adding a base packet to the empty state changes D from
+    the closed form mean((bg - I)^2) (an empty delivery renders the background)."""
+    w = synth.config("c1_plain_4k")
+    sc, cam, bg = w.scene, w.cams[0], np.array([0.2, 0.1, 0.0], np.float32)
+    # a cluster entirely off-screen: push its Gaussians far behind the camera
+    sc2 = synth.Scene(**{f.name: getattr(sc, f.name) for f in __import__("dataclasses").fields(sc)})
+    sc2.mu0 = sc.mu0.copy()
+    c_off = 3
+    lo, hi = sc.cluster_offsets[c_off], sc.cluster_offsets[c_off + 1]
+    sc2.mu0[lo:hi] = cam.R_wc.T @ (np.array([0.0, 0.0, -50.0]) - cam.t_wc)   # z = -50 in camera space
+    groups = np.array([[c_off, 0], [c_off, 1], [1, 0]], np.int32)
+    rng = np.random.default_rng(7)
+    M = 3
+    ctx = synth.group_contexts(groups, M, sc.n_clusters, sc.n_layers, rng)
+    delta, stats = oracle.group_utility(sc2, ctx, groups, M, cam, 0.0, bg)
+    assert np.all(delta[0] == 0.0) and np.all(delta[1] == 0.0)
+    assert np.all(stats[0] == 0.0)
+    # empty state vs base of cluster 1 alone
+    empty = np.zeros((1, ctx.shape[1]), np.uint32)
+    d, _ = oracle.group_utility(sc2, empty, groups[2:3], 1, cam, 0.0, bg)
+    full, _, _ = oracle.render(sc2, oracle.full_depth(sc2), 0.0, cam, bg)
+    depth = np.zeros(sc.n_clusters, np.uint8); depth[1] = 1
+    one, _, _ = oracle.render(sc2, depth, 0.0, cam, bg)
+    d_empty = np.mean((bg.astype(np.float64)[None, None, :] - full) ** 2)
+    assert d[0, 0] == pytest.approx(d_empty - np.mean((one - full) ** 2), rel=1e-12)
+    # contexts hold cluster c at exactly depth l, others anything
+    D = np.stack([oracle.closure(m, sc.n_clusters, sc.n_layers) for m in ctx])
+    for g, (c, l) in enumerate(groups):
+        assert np.all(D[g * M:(g + 1) * M, c] == l)

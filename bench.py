@@ -412,6 +412,73 @@ def run_mix(args):
     R.close()
 
 
+def run_groups(args):
+    """Utility table of the 2.7M-Gaussian sweep scene (Eq. 3 / Eq. 4): every
+    completion group (64 clusters x 4 layers = 256 packets) over 64 sampled
+    valid contexts, i.e. 2 x 256 x 64 = 32,768 rendered states per step (the
+    state count of the paper's utility experiment), 480x270, one view."""
+    import torch
+    from paper_2606_17212_b300 import dgs, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    w = synth.config("c4_utility_2p7m", scale=args.scale, n_states=1)
+    sc_h = w.scene
+    groups = np.array([(c, l) for c in range(sc_h.n_clusters) for l in range(sc_h.n_layers)], np.int32)
+    M = 64
+    ctx = synth.group_contexts(groups, M, sc_h.n_clusters, sc_h.n_layers, np.random.default_rng(2104))
+    G = len(groups)
+    states = synth.States(ctx, np.full(G * M, 0.25, np.float32), np.zeros(G * M, np.int32))
+    R = dgs.Renderer(0)
+    scene = dgs.DeviceScene.from_host(sc_h, device=dev)
+    dst = dgs.DeviceStates.from_host(states)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        R.group_utility(scene, dst, groups, M, w.cams, w.bg)
+    clocks = ClockSampler(0)
+    R.reset_kernel_launches()
+    R.profile(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record()
+        R.group_utility(scene, dst, groups, M, w.cams, w.bg)
+        ends[k].record()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / args.steps
+    launches = R.kernel_launches()
+    prof = R.profile_read()
+    R.profile(False)
+    clk = clocks.stop()
+    n_states = 2 * G * M
+    # end to end: contexts H2D from pinned memory, the utility table D2H
+    host = torch.from_numpy(np.ascontiguousarray(ctx).view(np.int32)).pin_memory()
+    out = torch.empty((G, 4), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        dst.masks.copy_(host, non_blocking=True)
+        _, st = R.group_utility(scene, dst, groups, M, w.cams, w.bg)
+        out.copy_(st, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e = n_states / ((time.perf_counter() - t0) / args.steps)
+    H, W = w.cams[0].height, w.cams[0].width
+    line = {"metric": METRIC, "value": n_states / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "c4_group_utility", "gaussians": sc_h.n, "groups": G, "contexts_per_group": M,
+                       "states_per_step": n_states, "resolution": [W, H], "alpha": 0.25, "beta": 0.05, "q": 0.10,
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": "dp1"},
+            "groups_per_s": G / (ms / 1e3), "mpix_per_s": n_states * H * W / (ms / 1e3) / 1e6,
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": host.numel() * 4 + states.t.nbytes +
+                    states.cam.nbytes, "d2h_bytes_per_step": G * 32},
+            "gpu_launches": launches, "clocks": clk,
+            "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
+    print(json.dumps(line), flush=True)
+    R.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -428,6 +495,14 @@ def main():
 
     from paper_2606_17212_b300 import synth
     ws, rank, local = _dist()
+    if args.workload == "c4_group_utility":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the utility-table mode has no reference-arm "
+                              "mode; the oracle's Eq. 3/4 is checked in the tests"}), flush=True)
+            return
+        if rank == 0:
+            run_groups(args)
+        return
     if args.workload == "c5_mix_48":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the serving mix has no reference-arm mode; "

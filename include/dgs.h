@@ -187,6 +187,33 @@ DGS_API int dgs_state_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_st
                       double *mse, double *psnr, dgs_stream stream);
 
 /*
+ * Counterfactual render utility of completion groups (Section 5, Eq. 3 and
+ * Eq. 4).  A completion group g is one packet (cluster, layer): groups [host]
+ * [n_groups][2].  contexts holds n_groups * n_contexts states (masks [device],
+ * t and cam [host]); state g * n_contexts + j is context j of group g, which
+ * should be a valid partial receiver state that lacks g (a context that
+ * already holds g, or lacks a prerequisite of g, gives Delta = 0).  For each
+ * context m the call renders m and m u g (one batch of 2 n_groups n_contexts
+ * states, all sharing decode and projection per view) and forms
+ *   Delta_g(m) = D(I, R(m)) - D(I, R(m u g)),
+ * D = the MSE of dgs_state_utility against the complete render I of the
+ * state's view.  delta [device] [n_groups * n_contexts] (may be NULL) receives
+ * every Delta; stats [device] [n_groups][4] receives per group
+ *   mean   = E_m[Delta_g]                (over its n_contexts contexts)
+ *   Q      = Q_q(Delta_g)                (linear interpolation between order
+ *                                         statistics, position q (n - 1))
+ *   std    = Std_m(Delta_g)              (population standard deviation)
+ *   utility = ((1 - alpha) mean + alpha Q) / (1 + beta std)
+ * (the paper's setting: alpha = 0.25, beta = 0.05, q = 0.10).  All in FP64.
+ * Needs 1 <= n_contexts <= DGS_UTILITY_MAX_CONTEXTS, 0 <= q <= 1, beta >= 0.
+ */
+#define DGS_UTILITY_MAX_CONTEXTS 4096
+DGS_API int dgs_group_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *contexts,
+                              const int32_t *groups, int n_groups, int n_contexts, const dgs_camera *cams,
+                              int n_cams, const float *bg, double alpha, double beta, double q, double *delta,
+                              double *stats, dgs_stream stream);
+
+/*
  * Per-image MSE (FP64 accumulation) and PSNR of images [device] [S][H][W][3]
  * against refs [device] [n_refs][H][W][3], image s against refs[ref_index[s]]
  * (ref_index [host] [S]).  mse, psnr [device] [S] (psnr may be NULL).  If

@@ -107,7 +107,8 @@ struct dgs_ctx {
     int sms = 148;
     std::string err;
     Buf vgs, vgos, depth, need, counts, recBase, total, recs, k0, v0, k1, v1, tcount, toffs, ek0, ev0, ek1, ev1,
-        ranges, sortws, scanws, partial, refs, recgrad, refidx, tck0, tcv0, tck1, tcv1, icnt, ioff, qint, counter;
+        ranges, sortws, scanws, partial, refs, recgrad, refidx, tck0, tcv0, tck1, tcv1, icnt, ioff, qint, counter,
+        pairm, grp, gmse;
     std::map<std::vector<long long>, int> tuned_G;   // autotuner: call shape -> states per block
     void *h_stage = nullptr;
     size_t h_stage_cap = 0;
@@ -698,13 +699,16 @@ void free_ctx_buffers(dgs_ctx *ctx)
                    &ctx->recs, &ctx->k0, &ctx->v0, &ctx->k1, &ctx->v1, &ctx->tcount, &ctx->toffs, &ctx->ek0,
                    &ctx->ev0, &ctx->ek1, &ctx->ev1, &ctx->ranges, &ctx->sortws, &ctx->scanws, &ctx->partial,
                    &ctx->refs, &ctx->recgrad, &ctx->refidx, &ctx->tck0, &ctx->tcv0, &ctx->tck1, &ctx->tcv1,
-                   &ctx->icnt, &ctx->ioff, &ctx->qint, &ctx->counter};
+                   &ctx->icnt, &ctx->ioff, &ctx->qint, &ctx->counter, &ctx->pairm, &ctx->grp, &ctx->gmse};
     for (Buf *b : bufs)
         if (b->p) { cudaFree(b->p); b->p = nullptr; b->cap = 0; }
     if (ctx->h_stage) { cudaFreeHost(ctx->h_stage); ctx->h_stage = nullptr; }
     if (ctx->h_small) { cudaFreeHost(ctx->h_small); ctx->h_small = nullptr; }
     if (ctx->stage_done) { cudaEventDestroy(ctx->stage_done); ctx->stage_done = nullptr; }
 }
+
+int utility_pass(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states, const dgs_camera *cams,
+                 int n_cams, const float *bg, double *mse, double *psnr, cudaStream_t st);
 
 RasterArgs plan_raster_args(dgs_plan *P)
 {
@@ -873,9 +877,72 @@ int dgs_state_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *st
 {
     if (!ctx) return DGS_E_INVALID_ARG;
     CK(cudaSetDevice(ctx->device));
-    cudaStream_t st = (cudaStream_t)stream;
     TRY(check_scene(ctx, scene));
     if (!bg) return fail(ctx, DGS_E_INVALID_ARG, "bg is null");
+    return utility_pass(ctx, scene, states, cams, n_cams, bg, mse, psnr, (cudaStream_t)stream);
+}
+
+int dgs_group_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *contexts, const int32_t *groups,
+                      int n_groups, int n_contexts, const dgs_camera *cams, int n_cams, const float *bg,
+                      double alpha, double beta, double q, double *delta, double *stats, dgs_stream stream)
+{
+    if (!ctx) return DGS_E_INVALID_ARG;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(check_scene(ctx, scene));
+    if (!bg || !contexts) return fail(ctx, DGS_E_INVALID_ARG, "bg or contexts is null");
+    if (n_groups < 0 || n_contexts < 1 || n_contexts > DGS_UTILITY_MAX_CONTEXTS)
+        return fail(ctx, DGS_E_INVALID_ARG, "need n_groups >= 0 and 1 <= n_contexts <= %d", DGS_UTILITY_MAX_CONTEXTS);
+    if ((long long)n_groups * n_contexts != (long long)contexts->n_states)
+        return fail(ctx, DGS_E_INVALID_ARG, "contexts must hold n_groups * n_contexts states");
+    if (2ll * n_groups * n_contexts > 0x7fffffffll) return fail(ctx, DGS_E_CAPACITY, "too many states");
+    if (!(q >= 0.0 && q <= 1.0) || !(beta >= 0.0) || !(alpha == alpha))
+        return fail(ctx, DGS_E_INVALID_ARG, "need 0 <= q <= 1, beta >= 0, alpha finite");
+    if (n_groups == 0) return DGS_OK;
+    if (!groups || !stats || !contexts->masks || !contexts->t || !contexts->cam)
+        return fail(ctx, DGS_E_INVALID_ARG, "null argument");
+    const int C = scene->n_clusters, L = scene->n_layers, G = n_groups, M = n_contexts;
+    for (int g = 0; g < G; ++g)
+        if (groups[2 * g] < 0 || groups[2 * g] >= C || groups[2 * g + 1] < 0 || groups[2 * g + 1] >= L)
+            return fail(ctx, DGS_E_INVALID_ARG, "group %d = (%d, %d) is not a packet", g, groups[2 * g],
+                        groups[2 * g + 1]);
+    const int words = (C * L + 31) / 32;
+    const size_t GM = (size_t)G * M;
+    TRY(ensure(ctx, ctx->pairm, 4 * 2 * GM * words, st));
+    TRY(ensure(ctx, ctx->grp, 8 * (size_t)G, st));
+    TRY(ensure(ctx, ctx->gmse, 8 * 2 * GM, st));
+    TRY(ensure_stage(ctx, 8 * (size_t)G, st));
+    CK(cudaEventSynchronize(ctx->stage_done));   // an earlier copy may still read h_stage
+    std::memcpy(ctx->h_stage, groups, 8 * (size_t)G);
+    CK(cudaMemcpyAsync(ctx->grp.p, ctx->h_stage, 8 * (size_t)G, cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(ctx->stage_done, st));
+    launch_pair_masks(contexts->masks, (const int2 *)ctx->grp.p, G, M, words, L, (uint32_t *)ctx->pairm.p,
+                      ctx->sms, st);
+    std::vector<float> t2(2 * GM);
+    std::vector<int32_t> c2(2 * GM);
+    for (size_t k = 0; k < GM; ++k) {
+        t2[k] = t2[GM + k] = contexts->t[k];
+        c2[k] = c2[GM + k] = contexts->cam[k];
+    }
+    dgs_states s2;
+    s2.masks = (const uint32_t *)ctx->pairm.p;
+    s2.t = t2.data();
+    s2.cam = c2.data();
+    s2.n_states = (int)(2 * GM);
+    TRY(utility_pass(ctx, scene, &s2, cams, n_cams, bg, (double *)ctx->gmse.p, nullptr, st));
+    launch_group_stats((const double *)ctx->gmse.p, G, M, alpha, beta, q, delta, stats, st);
+    CK(cudaGetLastError());
+    return DGS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Eq. 3 distortion of every state against its view's complete render (one batch).
+int utility_pass(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states, const dgs_camera *cams,
+                 int n_cams, const float *bg, double *mse, double *psnr, cudaStream_t st)
+{
     Plan p;
     TRY(build_plan(ctx, states, cams, n_cams, true, p));
     if (p.S_user > 0 && !mse) return fail(ctx, DGS_E_INVALID_ARG, "mse is null");
@@ -902,6 +969,10 @@ int dgs_state_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *st
     CK(cudaGetLastError());
     return DGS_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int dgs_debug_tile_lists(dgs_ctx *ctx, uint32_t *n_rec, uint32_t *n_ent, int32_t *n_view_groups,
                          uint32_t *tiles, uint32_t *recs, uint32_t *depth_keys, uint32_t *depth_slots,

@@ -73,6 +73,12 @@ void launch_mse_reduce(const double *partial, int S, int parts, double inv_count
 void launch_image_mse(const float *images, const float *refs, const int32_t *ref_index, int S, int H, int W,
                       float weight, double *partial, int parts, float *dL, cudaStream_t st);
 
+// Counterfactual utility (Eq. 3 / Eq. 4): paired masks, per-group statistics.
+void launch_pair_masks(const uint32_t *ctx_masks, const int2 *groups, int G, int M, int words, int L,
+                       uint32_t *out, int sms, cudaStream_t st);
+void launch_group_stats(const double *mse, int G, int M, double alpha, double beta, double q, double *delta,
+                        double *stats, cudaStream_t st);
+
 void launch_project_bwd(const SceneDev &s, const ViewGroup *vgs, int V, const uint32_t *need,
                         const uint32_t *recBase, const float4 *rec_grad, const GradDev &g, int sms,
                         cudaStream_t st);

@@ -51,7 +51,9 @@ EXPORTS = ("dgs_create", "dgs_destroy", "dgs_last_error", "dgs_version", "dgs_re
            "dgs_kernel_launches", "dgs_reset_kernel_launches", "dgs_profile_enable", "dgs_profile_read",
            "dgs_image_mse_noalloc", "dgs_debug_tile_lists", "dgs_plan_create", "dgs_plan_destroy",
            "dgs_plan_last_error", "dgs_plan_render", "dgs_plan_backward", "dgs_plan_utility",
-           "dgs_plan_image_mse", "dgs_plan_status", "dgs_arena_create", "dgs_arena_destroy")
+           "dgs_plan_image_mse", "dgs_plan_status", "dgs_arena_create", "dgs_arena_destroy",
+           "dgs_group_utility")
+UTILITY_MAX_CONTEXTS = 4096
 PLAN_RENDER, PLAN_UTILITY = 1, 2
 
 _lib = None
@@ -78,6 +80,9 @@ def lib():
                                           ctypes.POINTER(SceneGrad_t), P]
         L.dgs_state_utility.argtypes = [P, ctypes.POINTER(Scene_t), ctypes.POINTER(States_t), P, I, P, P, P, P]
         L.dgs_image_mse.argtypes = [P, P, P, P, I, I, I, I, F, P, P, P, P]
+        D = ctypes.c_double
+        L.dgs_group_utility.argtypes = [P, ctypes.POINTER(Scene_t), ctypes.POINTER(States_t), P, I, I, P, I, P,
+                                        D, D, D, P, P, P]
         L.dgs_kernel_launches.argtypes = [P]
         L.dgs_kernel_launches.restype = ctypes.c_int64
         L.dgs_reset_kernel_launches.argtypes = [P]
@@ -303,6 +308,23 @@ class Renderer:
         self._check(self._lib.dgs_state_utility(self.h, ctypes.byref(sc), ctypes.byref(st), ca, len(cams), bgv,
                                                 _ptr(mse), _ptr(psnr), _stream(stream)), "dgs_state_utility")
         return mse, psnr
+
+    def group_utility(self, scene: DeviceScene, contexts: DeviceStates, groups, n_contexts: int, cams, bg,
+                      alpha: float = 0.25, beta: float = 0.05, q: float = 0.10, stream=None):
+        """Eq. 3 / Eq. 4 (dgs_group_utility): returns (delta [G, M] f64, stats [G, 4]
+        f64 = mean, Q_q, std, risk-adjusted utility) as CUDA tensors."""
+        import torch
+        g = np.ascontiguousarray(groups, np.int32).reshape(-1, 2)
+        G, M = g.shape[0], int(n_contexts)
+        delta = torch.empty((G, M), dtype=torch.float64, device="cuda")
+        stats = torch.empty((G, 4), dtype=torch.float64, device="cuda")
+        bgv = (ctypes.c_float * 3)(*[float(x) for x in bg])
+        sc, st, ca = scene.struct(), contexts.struct(), camera_array(cams)
+        self._check(self._lib.dgs_group_utility(self.h, ctypes.byref(sc), ctypes.byref(st),
+                                                g.ctypes.data_as(ctypes.c_void_p), G, M, ca, len(cams), bgv,
+                                                float(alpha), float(beta), float(q), _ptr(delta), _ptr(stats),
+                                                _stream(stream)), "dgs_group_utility")
+        return delta, stats
 
     def image_mse(self, images, refs, ref_index, weight=1.0, want_grad=False, stream=None):
         import torch

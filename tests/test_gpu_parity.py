@@ -139,7 +139,7 @@ def test_state_utility_matches_oracle(R, torch):
             continue
         d = ref - full
         m_ref = float(np.mean(d * d))
-        bound = float(np.mean(4 * IMG_TOL * np.abs(d) + 4 * IMG_TOL ** 2))
+        bound = float(np.mean(4 * IMG_TOL * np.abs(d) + 4 * IMG_TOL ** 2)) + 5 * 2.0 ** -24 * m_ref
         assert abs(mse[s] - m_ref) <= bound, (s, mse[s], m_ref, bound)
         assert psnr[s] == pytest.approx(10 * math.log10(1 / mse[s]), rel=1e-12)
         checked += 1
@@ -350,3 +350,85 @@ def test_tile_lists_bitwise_and_end_to_end(R, torch):
         bad = np.nonzero(np.diff(zs) < 0)[0]
         for b in bad:   # only near-ties (FP32 vs FP64 depth within a few ulps) may swap
             assert zs[b] - zs[b + 1] <= 8e-7 * zs[b], (k, b)
+
+
+# --------------------------------------------------------------------- Eq. 3 / Eq. 4
+def test_group_utility_matches_oracle(R, torch):
+    """Counterfactual utility of completion groups.  (1) The per-group
+    statistics equal the oracle's Eq. 4 on the GPU's own Delta values; (2) every
+    Delta equals the MSE difference of the GPU's own rendered images of m and
+    m u g; (3) every Delta matches the FP64 oracle within the bound a 1e-4
+    per-value image error allows on non-marginal pixels plus, at pixels the
+    oracle flags as marginal (a threshold FP32 may decide the other way), a
+    change of up to one colour unit per value; (4) the statistics match the
+    oracle's within the largest per-context bound of their group (mean,
+    quantile and std move by at most the largest change of their inputs)."""
+    w = synth.config("c3_fwdbwd_250k", scale=0.004)
+    sc_h = w.scene
+    cam, t, bg = synth.ring_camera(2, 8, 64, 48, 75.0), 0.25, np.array([0.05, 0.1, 0.0], np.float32)
+    full_d = oracle.full_depth(sc_h)
+    rec = oracle.project(sc_h, full_d, t, cam)
+    seen = np.bincount(sc_h.cluster_of(), weights=rec[:, 0], minlength=sc_h.n_clusters)
+    vis = np.argsort(-seen)
+    groups = np.array([[vis[0], 0], [vis[0], 1], [vis[1], 2], [vis[2], 3], [vis[3], 0], [vis[5], 1]], np.int32)
+    G, M = len(groups), 10
+    ctx = synth.group_contexts(groups, M, sc_h.n_clusters, sc_h.n_layers, np.random.default_rng(11))
+    states = synth.States(ctx, np.full(G * M, t, np.float32), np.zeros(G * M, np.int32))
+    sc = dgs.DeviceScene.from_host(sc_h)
+    delta_t, stats_t = R.group_utility(sc, dgs.DeviceStates.from_host(states), groups, M, [cam], bg)
+    delta, stats = delta_t.cpu().numpy(), stats_t.cpu().numpy()
+    for g in range(G):
+        ref = oracle.utility_stats(delta[g])
+        assert np.allclose(stats[g], ref, rtol=1e-12, atol=1e-15), (g, stats[g], ref)
+    # paired masks (m rows, then m u g rows), rendered as images on the GPU
+    L = sc_h.n_layers
+    pairs = np.concatenate([ctx, ctx.copy()])
+    for k in range(G * M):
+        c, l = groups[k // M]
+        pairs[G * M + k, (c * L + l) // 32] |= np.uint32(1 << ((c * L + l) % 32))
+    pst = synth.States(pairs, np.full(2 * G * M, t, np.float32), np.zeros(2 * G * M, np.int32))
+    imgs = R.render_states_batched(sc, dgs.DeviceStates.from_host(pst), [cam], bg)
+    fullm = torch.full((1, pairs.shape[1]), -1, dtype=torch.int32, device="cuda")
+    fimg = R.render_states_batched(sc, dgs.DeviceStates(fullm, np.full(1, t, np.float32), np.zeros(1, np.int32)),
+                                   [cam], bg)
+    mse_g, _, _ = R.image_mse(imgs, fimg, np.zeros(2 * G * M, np.int32))
+    mse_g = mse_g.cpu().numpy()
+    assert np.allclose(delta.ravel(), mse_g[:G * M] - mse_g[G * M:], rtol=1e-12, atol=1e-16)
+    # the FP64 oracle, per state.  Loose check: all pixels, marginal ones allowed
+    # one colour unit.  Tight check: Delta over the pixels neither render flags,
+    # from the GPU's images (tied to the API's Delta above) and the oracle's.
+    full, mfull, _ = oracle.render(sc_h, full_d, t, cam, bg)
+    imgs_h = imgs.cpu().numpy().astype(np.float64)
+    fimg_h = fimg[0].cpu().numpy().astype(np.float64)
+    n_val = full.size
+    mse_o = np.zeros(2 * G * M); tol = np.zeros(2 * G * M)
+    m_o = np.zeros(2 * G * M); m_g = np.zeros(2 * G * M); tol_m = np.zeros(2 * G * M)
+    for k in range(2 * G * M):
+        img, marg, _ = oracle.render(sc_h, oracle.closure(pairs[k], sc_h.n_clusters, L), t, cam, bg)
+        d = img - full
+        mse_o[k] = np.mean(d * d)
+        flagged = np.broadcast_to((marg | mfull)[..., None], d.shape)
+        tol[k] = np.mean(np.where(flagged, 2 * np.abs(d) + 1.0, 4 * IMG_TOL * np.abs(d) + 4 * IMG_TOL ** 2)) \
+            + 5 * 2.0 ** -24 * mse_o[k]
+        dg = imgs_h[k] - fimg_h
+        m_o[k] = np.sum(np.where(flagged, 0.0, d * d)) / n_val
+        m_g[k] = np.sum(np.where(flagged, 0.0, dg * dg)) / n_val
+        tol_m[k] = np.sum(np.where(flagged, 0.0, 4 * IMG_TOL * np.abs(d) + 4 * IMG_TOL ** 2)) / n_val \
+            + 5 * 2.0 ** -24 * m_o[k]
+    delta_o = (mse_o[:G * M] - mse_o[G * M:]).reshape(G, M)
+    tol_d = (tol[:G * M] + tol[G * M:]).reshape(G, M)
+    assert np.all(np.abs(delta - delta_o) <= tol_d), np.max(np.abs(delta - delta_o) - tol_d)
+    dm_o = (m_o[:G * M] - m_o[G * M:]).reshape(G, M)
+    dm_g = (m_g[:G * M] - m_g[G * M:]).reshape(G, M)
+    tol_dm = (tol_m[:G * M] + tol_m[G * M:]).reshape(G, M)
+    assert np.all(np.abs(dm_g - dm_o) <= tol_dm), np.max(np.abs(dm_g - dm_o) - tol_dm)
+    assert np.abs(dm_o).max() > 1e-3                 # the groups do change the image
+    assert np.median(tol_dm) < 0.05 * np.abs(dm_o).max()
+    for g in range(G):
+        ref = np.array(oracle.utility_stats(delta_o[g]))
+        bound = tol_d[g].max()
+        assert np.all(np.abs(stats[g, :3] - ref[:3]) <= bound + 1e-15), (g, stats[g], ref, bound)
+        assert abs(stats[g, 3] - ref[3]) <= 2 * bound + 1e-15
+        # the same statistics of the masked Delta: tight
+        sg, so = np.array(oracle.utility_stats(dm_g[g])), np.array(oracle.utility_stats(dm_o[g]))
+        assert np.all(np.abs(sg[:3] - so[:3]) <= tol_dm[g].max() + 1e-15)

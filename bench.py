@@ -35,7 +35,7 @@ FWD_FLOP_PER_EVAL = 24     # FP32 ops of one (pixel, Gaussian) compositing evalu
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of this workload at full
 # size; valid only for the kernel source it was taken on (sha1 of csrc/raster.cu).
-MEASURED_TRAFFIC = {("raster_bwd", "c3_fwdbwd_250k"): (574458368 + 51844096, "3feb53b412769e48d4d885697bb1755ed8c90745")}
+MEASURED_TRAFFIC = {("raster_bwd", "c3_fwdbwd_250k"): (802653952 + 55802624, "08427ecce22a76c8c1bbfcb11870e3049777fcd3")}
 BWD_FLOP_PER_EVAL = 57     # forward recompute (24) + adjoint arithmetic (33)
 
 

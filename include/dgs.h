@@ -293,8 +293,10 @@ DGS_API int dgs_plan_status(dgs_plan *plan, int64_t *n_records, int64_t *n_entri
  * backward that re-prepared).  Sizes go to the [host] out-parameters (any may
  * be NULL); each [device] buffer that is not NULL receives a device-to-device
  * copy on `stream`:
- *   recs        [n_rec][12] u32 -- the 48-byte records: mx, my, A, B, C, o, r,
- *               g, b (floats), box x = xlo | xhi << 16, box y = ylo | yhi << 16,
+ *   recs        [n_rec][12] u32 -- the 48-byte records: mx, my, a2, b2, c2, o,
+ *               r, g, b (floats; the conic scaled for base-2 exponents:
+ *               a2 = -log2(e)/2 A, b2 = -log2(e) B, c2 = -log2(e)/2 C),
+ *               box x = xlo | xhi << 16, box y = ylo | yhi << 16,
  *               cluster | depth << 12 | view group << 16 | boxed << 31 (depth 0
  *               = culled; boxed: the 3-sigma box is narrower than the
  *               alpha >= 1/255 box on some axis)

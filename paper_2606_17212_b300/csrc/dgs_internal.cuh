@@ -23,10 +23,19 @@ constexpr int TILE_PIX = TILE * TILE;    // threads per raster block
 constexpr int MAX_CLUSTERS = 1024;
 constexpr int MAX_LAYERS = 8;
 
+// Records hold the conic (A = xx, B = xy, C = yy) pre-scaled for base-2
+// exponents: a2 = K_AC A, b2 = K_B B, c2 = K_AC C, so that a pixel's
+// log2(e) * power = a2 dx^2 + b2 dx dy + c2 dy^2 and alpha = o 2^(that)
+// (e^power == 2^(log2(e) power)); the raster stages records by plain copies.
+constexpr float LOG2E = 1.4426950408889634f;
+constexpr float K_AC = -0.5f * LOG2E;
+constexpr float K_B = -LOG2E;
+constexpr float INV_K_AC = 1.0f / K_AC, INV_K_B = 1.0f / K_B;
+
 // One projected Gaussian variant, 48 bytes, read as three float4.
 struct __align__(16) Rec {
-    float mx, my, A, B;        // mean2d, conic (A = xx, B = xy, C = yy)
-    float C, o, r, g;          // conic yy, opacity, colour r, g
+    float mx, my, A, B;        // mean2d, scaled conic a2 (xx), b2 (xy)
+    float C, o, r, g;          // scaled conic c2 (yy), opacity, colour r, g
     float b;                   // colour b
     uint32_t bx;               // xlo | xhi << 16   (inclusive pixel range)
     uint32_t by;               // ylo | yhi << 16

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(128, 4) k_project(SceneDev s, const ViewGroup 
                 project_fwd<SH>(s, i, a, vg, P, F);
                 Rec R;
                 if (P.live) {
-                    R.mx = P.mx; R.my = P.my; R.A = P.A; R.B = P.B; R.C = P.C; R.o = P.o;
+                    R.mx = P.mx; R.my = P.my; R.A = P.A * K_AC; R.B = P.B * K_B; R.C = P.C * K_AC; R.o = P.o;
                     R.r = P.rgb[0]; R.g = P.rgb[1]; R.b = P.rgb[2];
                     R.bx = (uint32_t)P.xlo | ((uint32_t)P.xhi << 16);
                     R.by = (uint32_t)P.ylo | ((uint32_t)P.yhi << 16);

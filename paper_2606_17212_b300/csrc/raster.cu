@@ -29,17 +29,10 @@ constexpr int RT = 128;               // threads per raster block
 constexpr int RW = RT / 32;           // warps per block; warp w owns rows 4w..4w+3 of the tile
 constexpr int BATCH = 256;            // entries staged per batch (two per thread)
 
-// Staged conic coefficients are pre-scaled so that one pixel's exponent in
-// base 2, p2 = log2(e) * power = a2 dx^2 + b2 dx dy + c2 dy^2, costs two fused
-// multiply-adds per pixel on top of two per-entry products shared by the
-// thread's two pixels, and alpha = o 2^p2 (e^power == 2^(log2(e) power)).
-constexpr float LOG2E = 1.4426950408889634f;
-constexpr float K_AC = -0.5f * LOG2E;      // a2 = K_AC A, c2 = K_AC C
-constexpr float K_B = -LOG2E;              // b2 = K_B B
-constexpr float INV_K_AC = 1.0f / K_AC, INV_K_B = 1.0f / K_B;
-
-__device__ __forceinline__ float4 scale_r0(float4 r0) { return make_float4(r0.x, r0.y, r0.z * K_AC, r0.w * K_B); }
-__device__ __forceinline__ float4 scale_r1(float4 r1) { return make_float4(r1.x * K_AC, r1.y, r1.z, r1.w); }
+// Records hold the conic pre-scaled (a2 = K_AC A, b2 = K_B B, c2 = K_AC C), so
+// one pixel's exponent in base 2, p2 = log2(e) * power = a2 dx^2 + b2 dx dy +
+// c2 dy^2, costs two fused multiply-adds per pixel on top of two per-entry
+// products shared by the thread's two pixels, and alpha = o 2^p2.
 
 // 2^x on the MUFU unit (ex2.approx.ftz: relative error ~2^-22, tiny results flush to 0)
 __device__ __forceinline__ float ex2(float x)
@@ -56,8 +49,8 @@ __device__ __forceinline__ float log2_power(float u, float v, float c2, float dy
 }
 
 struct Staged {
-    float4 r0[BATCH];                 // mx, my, A, B
-    float4 r1[BATCH];                 // C, o, r, g
+    float4 r0[BATCH];                 // mx, my, a2, b2 (scaled conic)
+    float4 r1[BATCH];                 // c2, o, r, g
     float4 r2[BATCH];                 // b, box x, box y, cd
     int4 box[BATCH];                  // xlo, xhi - xlo, ylo, yhi - ylo
     uint32_t slot[BATCH];
@@ -79,12 +72,12 @@ __device__ __forceinline__ int4 unpack_box(const float4 &r2)
 // minimum of the convex q over the rectangle is 0 when it holds the mean, else
 // it lies on an edge (1-D quadratic, clamped vertex).  rho is inflated by
 // 1e-3 relative + 1e-3 so FP32 rounding never drops a pixel that composites
-// (the 1e-3 also covers undoing the staged scaling of the conic);
+// (the 1e-3 also covers undoing the records' scaling of the conic);
 // skipping a Gaussian that stays below 1/255 on the whole strip changes nothing.
 __device__ __forceinline__ bool ellipse_meets_rect(const float4 &r0, const float4 &r1, float x0, float x1,
                                                    float y0, float y1)
 {
-    const float A = r0.z * INV_K_AC, B = r0.w * INV_K_B, C = r1.x * INV_K_AC, o = r1.y;   // staged: scaled
+    const float A = r0.z * INV_K_AC, B = r0.w * INV_K_B, C = r1.x * INV_K_AC, o = r1.y;   // records: scaled
     const float rho = fmaf(2.0f * __logf(255.0f * o), 1.001f, 1e-3f);
     const float X0 = x0 - r0.x, X1 = x1 - r0.x, Y0 = y0 - r0.y, Y1 = y1 - r0.y;
     if (X0 <= 0.0f && X1 >= 0.0f && Y0 <= 0.0f && Y1 >= 0.0f) return true;
@@ -157,7 +150,7 @@ __device__ __forceinline__ int stage_batch(const Rec *__restrict__ recs, const u
             x2[h] = __ldg(p + 2);
             const uint32_t cd = __float_as_uint(x2[h].w);
             keep[h] = ((cd >> 12) & 0xfu) == (uint32_t)sdep[cd & 0xfffu];
-            if (keep[h]) { x0[h] = scale_r0(__ldg(p)); x1[h] = scale_r1(__ldg(p + 1)); }
+            if (keep[h]) { x0[h] = __ldg(p); x1[h] = __ldg(p + 1); }
         }
     }
     const uint32_t lt = (1u << lane) - 1u;
@@ -259,7 +252,7 @@ __device__ __forceinline__ int stage_all(const Rec *__restrict__ recs, const uin
         if (e < end) {
             const uint32_t slot = __ldg(evals + e);
             const float4 *p = reinterpret_cast<const float4 *>(recs + slot);
-            sm.r0[j] = scale_r0(__ldg(p)); sm.r1[j] = scale_r1(__ldg(p + 1));
+            sm.r0[j] = __ldg(p); sm.r1[j] = __ldg(p + 1);
             const float4 r2 = __ldg(p + 2);
             sm.r2[j] = r2;
             sm.box[j] = unpack_box(r2);
@@ -659,7 +652,7 @@ __global__ void __launch_bounds__(RT, 6) k_raster_bwd(RasterBwdArgs b)
 #pragma unroll
             for (int j = 0; j < 9; ++j) { x[j] = gacc[k][j]; gacc[k][j] = 0.0f; any |= (x[j] != 0.0f); }
             if (any) {
-                // conic and mean gradients from the per-Gaussian sums
+                // conic and mean gradients from the per-Gaussian sums (records hold the scaled conic)
                 const float A = sm.r0[k].z * INV_K_AC, B = sm.r0[k].w * INV_K_B, C = sm.r1[k].x * INV_K_AC;
                 const float gmx = -(A * x[0] + B * x[1]), gmy = -(C * x[1] + B * x[0]);
                 float4 *dst = b.rec_grad + (size_t)sm.slot[k] * 3;

@@ -22,3 +22,12 @@ def test_library_loads_and_exports_every_symbol():
     for name in declared():
         assert hasattr(L, name), name
     assert L.dgs_version() == 1
+
+
+def test_library_binds_every_symbol_at_load():
+    """Loading with immediate binding fails if any symbol of the library is left
+    undefined (e.g. a launcher declared with one signature and defined with another)."""
+    import ctypes
+    import os
+    from paper_2606_17212_b300 import dgs
+    ctypes.CDLL(dgs.LIB_PATH, mode=os.RTLD_NOW | os.RTLD_LOCAL)

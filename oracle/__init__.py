@@ -329,3 +329,109 @@ def group_utility(scene, ctx_masks, groups, n_contexts, cam, t, bg, alpha=0.25, 
             delta[g, j] = d0 - d1
         stats[g] = utility_stats(delta[g], alpha, beta, q)
     return delta, stats
+
+
+# ----------------------------------------------------------------- Eq. 2 objective
+SSIM_C1, SSIM_C2 = 0.01 ** 2, 0.03 ** 2
+
+
+def ssim_window(size: int = 11, sigma: float = 1.5) -> np.ndarray:
+    """Normalised 1-D Gaussian window (the 2-D window is its outer product)."""
+    x = np.arange(size, dtype=np.float64) - (size - 1) / 2.0
+    g = np.exp(-x * x / (2.0 * sigma * sigma))
+    return g / g.sum()
+
+
+def _blur(img: np.ndarray, g: np.ndarray) -> np.ndarray:
+    """'Same'-size 2-D filtering of [H, W, C] with the separable window g, zero padded."""
+    r = len(g) // 2
+    H, W = img.shape[:2]
+    p = np.zeros((H + 2 * r, W + 2 * r) + img.shape[2:])
+    p[r:r + H, r:r + W] = img
+    h = sum(g[k] * p[:, k:k + W] for k in range(len(g)))
+    return sum(g[k] * h[k:k + H] for k in range(len(g)))
+
+
+def ssim(x: np.ndarray, y: np.ndarray, want_grad: bool = False):
+    """Structural similarity of image x against reference y ([H, W, 3]) in FP64:
+    local means, variances and covariance under an 11x11 Gaussian window
+    (sigma 1.5, zero-padded same-size filtering), per-pixel
+    ((2 mx my + C1)(2 sxy + C2)) / ((mx^2 + my^2 + C1)(sx^2 + sy^2 + C2)),
+    averaged over pixels and channels.  With want_grad also returns dSSIM/dx
+    (want_grad="map": the per-pixel, per-channel values instead of their mean)."""
+    g = ssim_window()
+    x = np.asarray(x, np.float64); y = np.asarray(y, np.float64)
+    mx, my = _blur(x, g), _blur(y, g)
+    exx, eyy, exy = _blur(x * x, g), _blur(y * y, g), _blur(x * y, g)
+    sxx, syy, sxy = exx - mx * mx, eyy - my * my, exy - mx * my
+    a1, a2 = 2 * mx * my + SSIM_C1, 2 * sxy + SSIM_C2
+    b1, b2 = mx * mx + my * my + SSIM_C1, sxx + syy + SSIM_C2
+    f = a1 * a2 / (b1 * b2)
+    if want_grad == "map":
+        return f
+    s = float(np.mean(f))
+    if not want_grad:
+        return s
+    # f as a function of (mx, exx, exy): chain through sxx = exx - mx^2, sxy = exy - mx my
+    d_mx = f * (2 * my / a1 - 2 * my / a2 - 2 * mx / b1 + 2 * mx / b2)
+    d_exx = -f / b2
+    d_exy = 2 * f / a2
+    n = f.size
+    grad = (_blur(d_mx, g) + 2 * x * _blur(d_exx, g) + y * _blur(d_exy, g)) / n
+    return s, grad
+
+
+def objective(images, refs, ref_index, pairs_t=(), pairs_m=(), anchors=(), ssim_weight=0.20,
+              lambda_c=0.30, cvar_q=0.05, lambda_t=0.10, lambda_m=2.0, anchor_weight=0.50):
+    """Eq. 2 with the locked weights, in FP64, over a batch of rendered states.
+
+    D_s = MSE(I_s, ref) + ssim_weight (1 - SSIM(I_s, ref)) against the state's
+    reference image; then
+      L = mean_s D_s + lambda_c CVaR_q(D) + lambda_t F + lambda_m M
+          + anchor_weight mean_{s in anchors} D_s
+    with CVaR_q(D) the mean of the ceil(q S) largest D (the upper tail of the
+    loss), F the mean over temporal pairs (i, j) of the mean squared error
+    between the rendered change I_j - I_i and the reference change, and M the
+    mean over prefix pairs (i, j) (state j extends state i) of max(0, D_j - D_i).
+    The rate term is absent (its locked weight is 0).  Returns (L, D [S],
+    dL/dimages [S, H, W, 3])."""
+    imgs = np.asarray(images, np.float64)
+    rf = np.asarray(refs, np.float64)
+    S = imgs.shape[0]
+    n_val = imgs[0].size
+    D = np.zeros(S)
+    gD = np.zeros_like(imgs)                     # dD_s / dI_s
+    for s in range(S):
+        y = rf[int(ref_index[s])]
+        d = imgs[s] - y
+        sv, sg = ssim(imgs[s], y, want_grad=True)
+        D[s] = np.mean(d * d) + ssim_weight * (1.0 - sv)
+        gD[s] = 2.0 * d / n_val - ssim_weight * sg
+    w = np.full(S, 1.0 / S)                      # dL / dD_s
+    k = int(np.ceil(cvar_q * S)) if S else 0
+    top = np.argsort(-D, kind="stable")[:k]
+    cvar = float(np.mean(D[top])) if k else 0.0
+    w[top] += lambda_c / k
+    M = 0.0
+    if len(pairs_m):
+        for i, j in pairs_m:
+            if D[j] > D[i]:
+                M += (D[j] - D[i]) / len(pairs_m)
+                w[j] += lambda_m / len(pairs_m)
+                w[i] -= lambda_m / len(pairs_m)
+    A = 0.0
+    if len(anchors):
+        for s in anchors:
+            A += D[s] / len(anchors)
+            w[s] += anchor_weight / len(anchors)
+    grad = w[:, None, None, None] * gD
+    F = 0.0
+    if len(pairs_t):
+        for i, j in pairs_t:
+            e = (imgs[j] - imgs[i]) - (rf[int(ref_index[j])] - rf[int(ref_index[i])])
+            F += np.mean(e * e) / len(pairs_t)
+            gf = lambda_t * 2.0 * e / (n_val * len(pairs_t))
+            grad[j] += gf
+            grad[i] -= gf
+    L = float(np.mean(D)) + lambda_c * cvar + lambda_t * F + lambda_m * M + anchor_weight * A
+    return L, D, grad

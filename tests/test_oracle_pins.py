@@ -597,3 +597,58 @@ def test_group_utility_special_cases():
     D = np.stack([oracle.closure(m, sc.n_clusters, sc.n_layers) for m in ctx])
     for g, (c, l) in enumerate(groups):
         assert np.all(D[g * M:(g + 1) * M, c] == l)
+
+
+# ------------------------------------------------------------ Eq. 2 objective
+def test_ssim_window_and_identities():
+    """The window is the normalised sampled Gaussian (ratio of neighbours
+    exp(-(2k+1)/(2 sigma^2)) about the centre), SSIM(x, x) = 1 exactly, SSIM is
+    symmetric, and on constant images the interior value (window inside the
+    image) is the closed form (2ab + C1)/(a^2 + b^2 + C1)."""
+    g = oracle.ssim_window()
+    assert len(g) == 11 and abs(g.sum() - 1.0) < 1e-15 and np.allclose(g, g[::-1], rtol=0, atol=0)
+    for k in range(5):
+        assert g[6 + k] / g[5 + k] == pytest.approx(np.exp(-(2 * k + 1) / (2 * 1.5 ** 2)), rel=1e-13)
+    rng = np.random.default_rng(3)
+    x = rng.uniform(size=(19, 23, 3)); y = rng.uniform(size=(19, 23, 3))
+    assert oracle.ssim(x, x) == 1.0
+    assert oracle.ssim(x, y) == pytest.approx(oracle.ssim(y, x), rel=1e-14)
+    assert oracle.ssim(x, y) < 1.0
+    a, b = 0.3, 0.7
+    f = oracle.ssim(np.full((20, 24, 3), a), np.full((20, 24, 3), b), want_grad="map")
+    c1 = 0.01 ** 2
+    assert np.allclose(f[5:-5, 5:-5], (2 * a * b + c1) / (a * a + b * b + c1), rtol=1e-12, atol=0)
+
+
+def _fd(fun, x, idx, h=1e-6):
+    xp = x.copy(); xp[idx] += h
+    xm = x.copy(); xm[idx] -= h
+    return (fun(xp) - fun(xm)) / (2 * h)
+
+
+def test_objective_gradient_finite_differences_and_special_cases():
+    """Every term of Eq. 2 (mean D, CVaR tail, temporal change F, prefix
+    hinge M, complete-prefix anchor) against central differences of the
+    oracle's own value; images equal to their references give L = 0 and no
+    gradient; a prefix pair whose distortion falls adds nothing."""
+    rng = np.random.default_rng(5)
+    S, H, W = 6, 12, 14
+    refs = rng.uniform(size=(2, H, W, 3))
+    ridx = np.array([0, 1, 0, 1, 0, 1])
+    imgs = refs[ridx] + rng.normal(0, [0.05, 0.1, 0.2, 0.02, 0.3, 0.15], size=(H, W, 3, S)).transpose(3, 0, 1, 2)
+    kw = dict(pairs_t=[(0, 2), (1, 3)], pairs_m=[(0, 4), (4, 0), (1, 5)], anchors=[3], cvar_q=0.34)
+    L, D, grad = oracle.objective(imgs, refs, ridx, **kw)
+    assert np.sum(D > D[3]) >= 1
+    for idx in [(0, 3, 4, 1), (2, 0, 0, 0), (4, 11, 13, 2), (5, 6, 7, 1), (3, 5, 5, 0)]:
+        fd = _fd(lambda z: oracle.objective(z, refs, ridx, **kw)[0], imgs, idx)
+        assert fd == pytest.approx(grad[idx], rel=1e-5, abs=1e-11), idx
+    # the definition term by term on these values
+    k = int(np.ceil(0.34 * S))
+    cvar = np.sort(D)[::-1][:k].mean()
+    M = (max(0, D[4] - D[0]) + max(0, D[0] - D[4]) + max(0, D[5] - D[1])) / 3
+    F = np.mean((((imgs[2] - imgs[0]) - (refs[0] - refs[0])) ** 2)) / 2 + \
+        np.mean((((imgs[3] - imgs[1]) - (refs[1] - refs[1])) ** 2)) / 2
+    assert L == pytest.approx(D.mean() + 0.30 * cvar + 0.10 * F + 2.0 * M + 0.5 * D[3], rel=1e-12)
+    # perfect renders: zero objective, zero gradient
+    L0, D0, g0 = oracle.objective(refs[ridx], refs, ridx, **kw)
+    assert L0 == 0.0 and np.all(D0 == 0.0) and np.abs(g0).max() < 1e-12   # SSIM is stationary at x = y

@@ -490,6 +490,8 @@ def main():
     ap.add_argument("--states", type=int, default=None, help="override the workload's state count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--loss", default="mse", choices=["mse", "eq2"],
+                    help="training loss: mean MSE, or Eq. 2 (MSE + 0.2 (1 - SSIM), CVaR_0.05 tail)")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
 
@@ -551,7 +553,10 @@ def main():
     def step(st):
         if training:
             R.render_states_batched(scene, st, w.cams, w.bg, out=images)
-            mse, _, dL = R.image_mse(images, targets, ref_index, weight=1.0 / S, want_grad=True)
+            if args.loss == "eq2":
+                mse, _, dL = R.objective(images, targets, ref_index)
+            else:
+                mse, _, dL = R.image_mse(images, targets, ref_index, weight=1.0 / S, want_grad=True)
             for g in grads.values():
                 g.zero_()
             R.render_backward(scene, st, w.cams, w.bg, dL, grads, images=images)
@@ -595,7 +600,7 @@ def main():
     # ---- graph path (training): a capture-safe plan, the whole step captured
     # once in a CUDA graph and replayed (masks live in a static device buffer)
     graph_ms = None
-    if training:
+    if training and args.loss == "mse":     # the Eq. 2 objective call is not capture-safe
         plan = dgs.Plan(R, scene, states, w.cams, w.bg, dgs.PLAN_RENDER, ref_index=ref_index,
                         n_refs=len(views), entry_headroom=1.5)
         g_masks = states.masks.clone()
@@ -719,6 +724,8 @@ def main():
                     "ms_per_launch": dom_ms_per_launch,
                     "evals_per_launch": evals_per_launch}
     cfg = workload_config(w, ws, views, "cuda_graph_plan" if use_graph else "context_calls")
+    if training:
+        cfg["loss"] = "mean MSE" if args.loss == "mse" else "Eq. 2: MSE + 0.2 (1 - SSIM), 0.3 CVaR_0.05 tail"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,

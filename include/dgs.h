@@ -214,6 +214,36 @@ DGS_API int dgs_group_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_st
                               double *stats, dgs_stream stream);
 
 /*
+ * The packet-conditioned training objective of Section 4 (Eq. 2) over a batch
+ * of rendered states, with its gradient.  For state s with reference image
+ * refs[ref_index[s]]:
+ *   D_s = MSE(I_s, ref) + ssim_weight (1 - SSIM(I_s, ref))
+ * SSIM: 11x11 Gaussian window (sigma 1.5), zero-padded same-size filtering,
+ * C1 = 0.01^2, C2 = 0.03^2, mean over pixels and channels.  Then
+ *   L = mean_s D_s + lambda_c CVaR_q(D) + lambda_t F + lambda_m M
+ *       + anchor_weight mean_{s in anchors} D_s
+ * CVaR_q(D) = the mean of the ceil(q S) largest D (ties: lower state index);
+ * F = mean over temporal pairs (i, j) of the MSE between the rendered change
+ * I_j - I_i and the reference change; M = mean over prefix pairs (i, j), state
+ * j extending state i, of max(0, D_j - D_i).  The rate term is absent (its
+ * weight is 0 in the paper's setting).  params NULL = the paper's weights:
+ * 0.20, 0.30, 0.05, 0.10, 2.0, 0.50.
+ * images [device] [S][H][W][3], refs [device] [n_refs][H][W][3], ref_index
+ * [host] [S], pairs_t / pairs_m [host] [n][2] state indices, anchors [host]
+ * [n_anchors]; loss [device] [1] (required), D [device] [S] (may be NULL),
+ * dL_dimages [device] [S][H][W][3] (may be NULL: no gradient).  1 <= S <=
+ * DGS_OBJECTIVE_MAX_STATES.  Sums over pixels, states and pairs are FP64.
+ */
+typedef struct dgs_objective_params {
+    double ssim_weight, lambda_c, cvar_q, lambda_t, lambda_m, anchor_weight;
+} dgs_objective_params;
+#define DGS_OBJECTIVE_MAX_STATES 16384
+DGS_API int dgs_objective(dgs_ctx *ctx, const float *images, const float *refs, const int32_t *ref_index, int S,
+                          int n_refs, int H, int W, const int32_t *pairs_t, int n_pairs_t, const int32_t *pairs_m,
+                          int n_pairs_m, const int32_t *anchors, int n_anchors, const dgs_objective_params *params,
+                          double *loss, double *D, float *dL_dimages, dgs_stream stream);
+
+/*
  * Per-image MSE (FP64 accumulation) and PSNR of images [device] [S][H][W][3]
  * against refs [device] [n_refs][H][W][3], image s against refs[ref_index[s]]
  * (ref_index [host] [S]).  mse, psnr [device] [S] (psnr may be NULL).  If

@@ -108,7 +108,7 @@ struct dgs_ctx {
     std::string err;
     Buf vgs, vgos, depth, need, counts, recBase, total, recs, k0, v0, k1, v1, tcount, toffs, ek0, ev0, ek1, ev1,
         ranges, sortws, scanws, partial, refs, recgrad, refidx, tck0, tcv0, tck1, tcv1, icnt, ioff, qint, counter,
-        pairm, grp, gmse;
+        pairm, grp, gmse, omaps, opart, otpart, oD, oweight, oints;
     std::map<std::vector<long long>, int> tuned_G;   // autotuner: call shape -> states per block
     void *h_stage = nullptr;
     size_t h_stage_cap = 0;
@@ -699,7 +699,8 @@ void free_ctx_buffers(dgs_ctx *ctx)
                    &ctx->recs, &ctx->k0, &ctx->v0, &ctx->k1, &ctx->v1, &ctx->tcount, &ctx->toffs, &ctx->ek0,
                    &ctx->ev0, &ctx->ek1, &ctx->ev1, &ctx->ranges, &ctx->sortws, &ctx->scanws, &ctx->partial,
                    &ctx->refs, &ctx->recgrad, &ctx->refidx, &ctx->tck0, &ctx->tcv0, &ctx->tck1, &ctx->tcv1,
-                   &ctx->icnt, &ctx->ioff, &ctx->qint, &ctx->counter, &ctx->pairm, &ctx->grp, &ctx->gmse};
+                   &ctx->icnt, &ctx->ioff, &ctx->qint, &ctx->counter, &ctx->pairm, &ctx->grp, &ctx->gmse, &ctx->omaps, &ctx->opart, &ctx->otpart,
+                   &ctx->oD, &ctx->oweight, &ctx->oints};
     for (Buf *b : bufs)
         if (b->p) { cudaFree(b->p); b->p = nullptr; b->cap = 0; }
     if (ctx->h_stage) { cudaFreeHost(ctx->h_stage); ctx->h_stage = nullptr; }
@@ -931,6 +932,89 @@ int dgs_group_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *co
     s2.n_states = (int)(2 * GM);
     TRY(utility_pass(ctx, scene, &s2, cams, n_cams, bg, (double *)ctx->gmse.p, nullptr, st));
     launch_group_stats((const double *)ctx->gmse.p, G, M, alpha, beta, q, delta, stats, st);
+    CK(cudaGetLastError());
+    return DGS_OK;
+}
+
+int dgs_objective(dgs_ctx *ctx, const float *images, const float *refs, const int32_t *ref_index, int S, int n_refs,
+                  int H, int W, const int32_t *pairs_t, int n_pairs_t, const int32_t *pairs_m, int n_pairs_m,
+                  const int32_t *anchors, int n_anchors, const dgs_objective_params *params, double *loss, double *D,
+                  float *dL_dimages, dgs_stream stream)
+{
+    if (!ctx) return DGS_E_INVALID_ARG;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (S < 1 || S > DGS_OBJECTIVE_MAX_STATES || n_refs < 1 || H < 1 || W < 1 || n_pairs_t < 0 || n_pairs_m < 0 ||
+        n_anchors < 0)
+        return fail(ctx, DGS_E_INVALID_ARG, "bad sizes (1 <= S <= %d)", DGS_OBJECTIVE_MAX_STATES);
+    if (!images || !refs || !ref_index || !loss) return fail(ctx, DGS_E_INVALID_ARG, "null argument");
+    if ((n_pairs_t && !pairs_t) || (n_pairs_m && !pairs_m) || (n_anchors && !anchors))
+        return fail(ctx, DGS_E_INVALID_ARG, "null pair or anchor list");
+    for (int s = 0; s < S; ++s)
+        if (ref_index[s] < 0 || ref_index[s] >= n_refs)
+            return fail(ctx, DGS_E_INVALID_ARG, "ref_index[%d] out of range", s);
+    for (int p = 0; p < 2 * n_pairs_t; ++p)
+        if (pairs_t[p] < 0 || pairs_t[p] >= S) return fail(ctx, DGS_E_INVALID_ARG, "temporal pair out of range");
+    for (int p = 0; p < 2 * n_pairs_m; ++p)
+        if (pairs_m[p] < 0 || pairs_m[p] >= S) return fail(ctx, DGS_E_INVALID_ARG, "prefix pair out of range");
+    for (int a = 0; a < n_anchors; ++a)
+        if (anchors[a] < 0 || anchors[a] >= S) return fail(ctx, DGS_E_INVALID_ARG, "anchor out of range");
+    dgs_objective_params prm = {0.20, 0.30, 0.05, 0.10, 2.0, 0.50};
+    if (params) prm = *params;
+    if (!(prm.cvar_q >= 0.0 && prm.cvar_q <= 1.0)) return fail(ctx, DGS_E_INVALID_ARG, "cvar_q outside [0, 1]");
+    const size_t npix = (size_t)H * W;
+    int tx;
+    const int nt = objective_tiles(H, W, &tx);
+    const int chunks = (int)((npix + 1023) / 1024);
+    // host tables: ref_index [S], pairs_t [2 n_t], pairs_m [2 n_m], anchors, toff [S + 1], tlist [2 n_t][2]
+    std::vector<int32_t> toff(S + 1, 0), tl(4 * (size_t)n_pairs_t);
+    for (int p = 0; p < n_pairs_t; ++p) { ++toff[pairs_t[2 * p] + 1]; ++toff[pairs_t[2 * p + 1] + 1]; }
+    for (int s = 0; s < S; ++s) toff[s + 1] += toff[s];
+    {
+        std::vector<int32_t> fill(toff.begin(), toff.end() - 1);
+        for (int p = 0; p < n_pairs_t; ++p) {
+            const int i = pairs_t[2 * p], j = pairs_t[2 * p + 1];
+            tl[2 * fill[i]] = j; tl[2 * fill[i] + 1] = -1; ++fill[i];      // i is the earlier state
+            tl[2 * fill[j]] = i; tl[2 * fill[j] + 1] = +1; ++fill[j];      // j is the later state
+        }
+    }
+    // the int2 lists first, at even offsets (8-byte aligned), then the int arrays
+    const size_t o_pt = 0, o_pm = o_pt + 2 * (size_t)n_pairs_t, o_tl = o_pm + 2 * (size_t)n_pairs_m;
+    const size_t o_ri = o_tl + tl.size(), o_an = o_ri + S, o_to = o_an + n_anchors, n_ints = o_to + S + 1;
+    TRY(ensure(ctx, ctx->oints, 4 * n_ints + 16, st));
+    TRY(ensure(ctx, ctx->omaps, sizeof(float) * 3 * (size_t)S * 3 * npix, st));
+    TRY(ensure(ctx, ctx->opart, sizeof(double) * 2 * (size_t)S * nt, st));
+    TRY(ensure(ctx, ctx->otpart, sizeof(double) * (size_t)(n_pairs_t > 0 ? n_pairs_t : 1) * chunks, st));
+    TRY(ensure(ctx, ctx->oD, sizeof(double) * (size_t)S, st));
+    TRY(ensure(ctx, ctx->oweight, sizeof(double) * (size_t)S, st));
+    TRY(ensure_stage(ctx, 4 * n_ints, st));
+    CK(cudaEventSynchronize(ctx->stage_done));   // an earlier copy may still read h_stage
+    int32_t *h = (int32_t *)ctx->h_stage;
+    std::memcpy(h + o_ri, ref_index, 4 * (size_t)S);
+    if (n_pairs_t) std::memcpy(h + o_pt, pairs_t, 8 * (size_t)n_pairs_t);
+    if (n_pairs_m) std::memcpy(h + o_pm, pairs_m, 8 * (size_t)n_pairs_m);
+    if (n_anchors) std::memcpy(h + o_an, anchors, 4 * (size_t)n_anchors);
+    std::memcpy(h + o_to, toff.data(), 4 * (size_t)(S + 1));
+    if (!tl.empty()) std::memcpy(h + o_tl, tl.data(), 4 * tl.size());
+    CK(cudaMemcpyAsync(ctx->oints.p, h, 4 * n_ints, cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(ctx->stage_done, st));
+    const int32_t *d = (const int32_t *)ctx->oints.p;
+    float *maps = (float *)ctx->omaps.p;
+    const size_t plane = (size_t)S * 3 * npix;
+    launch_ssim_fwd(images, refs, d + o_ri, S, H, W, maps, maps + plane, maps + 2 * plane, (double *)ctx->opart.p,
+                    st);
+    launch_temporal(images, refs, d + o_ri, (const int2 *)(d + o_pt), n_pairs_t, H, W, (double *)ctx->otpart.p, chunks,
+                    st);
+    double *Dout = D ? D : (double *)ctx->oD.p;
+    if (launch_objective((const double *)ctx->opart.p, nt, (const double *)ctx->otpart.p, chunks, n_pairs_t,
+                         (const int2 *)(d + o_pm), n_pairs_m, d + o_an, n_anchors, S, 1.0 / (double)(npix * 3), prm,
+                         Dout, (double *)ctx->oweight.p, loss, st) != 0)
+        return fail(ctx, DGS_E_CUDA, "objective kernel attribute");
+    if (dL_dimages)
+        launch_objective_grad(images, refs, d + o_ri, S, H, W, maps, maps + plane, maps + 2 * plane,
+                              (const double *)ctx->oweight.p, (float)prm.ssim_weight,
+                              n_pairs_t ? (float)(prm.lambda_t / (double)n_pairs_t) : 0.0f, d + o_to,
+                              (const int2 *)(d + o_tl), dL_dimages, st);
     CK(cudaGetLastError());
     return DGS_OK;
 }

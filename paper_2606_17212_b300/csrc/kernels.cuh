@@ -79,6 +79,22 @@ void launch_pair_masks(const uint32_t *ctx_masks, const int2 *groups, int G, int
 void launch_group_stats(const double *mse, int G, int M, double alpha, double beta, double q, double *delta,
                         double *stats, cudaStream_t st);
 
+// Eq. 2 objective (objective.cu).
+typedef dgs_objective_params ObjectiveParams;
+int objective_tiles(int H, int W, int *tiles_x);
+size_t objective_smem(int S);
+void launch_ssim_fwd(const float *images, const float *refs, const int32_t *ref_index, int S, int H, int W,
+                     float *d_mx, float *d_exx, float *d_exy, double *part, cudaStream_t st);
+void launch_temporal(const float *images, const float *refs, const int32_t *ref_index, const int2 *pairs,
+                     int n_pairs, int H, int W, double *tpart, int chunks, cudaStream_t st);
+int launch_objective(const double *part, int n_tiles, const double *tpart, int chunks, int n_t, const int2 *pm,
+                     int n_m, const int32_t *anchors, int n_a, int S, double inv_vals, const ObjectiveParams &prm,
+                     double *D, double *weight, double *loss, cudaStream_t st);
+void launch_objective_grad(const float *images, const float *refs, const int32_t *ref_index, int S, int H, int W,
+                           const float *d_mx, const float *d_exx, const float *d_exy, const double *weight,
+                           float ssim_weight, float tscale, const int32_t *toff, const int2 *tlist, float *dL,
+                           cudaStream_t st);
+
 void launch_project_bwd(const SceneDev &s, const ViewGroup *vgs, int V, const uint32_t *need,
                         const uint32_t *recBase, const float4 *rec_grad, const GradDev &g, int sms,
                         cudaStream_t st);

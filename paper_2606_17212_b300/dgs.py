@@ -30,6 +30,15 @@ class Scene_t(ctypes.Structure):
                 ("opacity_logit", ctypes.c_void_p), ("colour", ctypes.c_void_p), ("res", ctypes.c_void_p)]
 
 
+OBJECTIVE_KEYS = ("ssim_weight", "lambda_c", "cvar_q", "lambda_t", "lambda_m", "anchor_weight")
+OBJECTIVE_DEFAULTS = dict(ssim_weight=0.20, lambda_c=0.30, cvar_q=0.05, lambda_t=0.10, lambda_m=2.0,
+                          anchor_weight=0.50)
+
+
+class ObjectiveParams_t(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in OBJECTIVE_KEYS]
+
+
 class SceneGrad_t(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in
                 ("mu0", "u", "log_scale", "quat", "opacity_logit", "colour", "res")]
@@ -52,7 +61,8 @@ EXPORTS = ("dgs_create", "dgs_destroy", "dgs_last_error", "dgs_version", "dgs_re
            "dgs_image_mse_noalloc", "dgs_debug_tile_lists", "dgs_plan_create", "dgs_plan_destroy",
            "dgs_plan_last_error", "dgs_plan_render", "dgs_plan_backward", "dgs_plan_utility",
            "dgs_plan_image_mse", "dgs_plan_status", "dgs_arena_create", "dgs_arena_destroy",
-           "dgs_group_utility")
+           "dgs_group_utility", "dgs_objective")
+OBJECTIVE_MAX_STATES = 16384
 UTILITY_MAX_CONTEXTS = 4096
 PLAN_RENDER, PLAN_UTILITY = 1, 2
 
@@ -81,6 +91,8 @@ def lib():
         L.dgs_state_utility.argtypes = [P, ctypes.POINTER(Scene_t), ctypes.POINTER(States_t), P, I, P, P, P, P]
         L.dgs_image_mse.argtypes = [P, P, P, P, I, I, I, I, F, P, P, P, P]
         D = ctypes.c_double
+        L.dgs_objective.argtypes = [P, P, P, P, I, I, I, I, P, I, P, I, P, I, ctypes.POINTER(ObjectiveParams_t), P, P,
+                                    P, P]
         L.dgs_group_utility.argtypes = [P, ctypes.POINTER(Scene_t), ctypes.POINTER(States_t), P, I, I, P, I, P,
                                         D, D, D, P, P, P]
         L.dgs_kernel_launches.argtypes = [P]
@@ -326,6 +338,31 @@ class Renderer:
                                                 _stream(stream)), "dgs_group_utility")
         return delta, stats
 
+    def objective(self, images, refs, ref_index, pairs_t=(), pairs_m=(), anchors=(), params=None,
+                  want_grad=True, stream=None):
+        """Eq. 2 (dgs_objective): returns (loss [1] f64, D [S] f64, dL/dimages or None)
+        as CUDA tensors.  params: dict of ssim_weight, lambda_c, cvar_q, lambda_t,
+        lambda_m, anchor_weight (missing keys take the paper's values)."""
+        import torch
+        S, H, W, _ = images.shape
+        ri = np.ascontiguousarray(ref_index, np.int32)
+        pt = np.ascontiguousarray(np.asarray(pairs_t, np.int32).reshape(-1, 2))
+        pm = np.ascontiguousarray(np.asarray(pairs_m, np.int32).reshape(-1, 2))
+        an = np.ascontiguousarray(np.asarray(anchors, np.int32).reshape(-1))
+        prm = None
+        if params is not None:
+            v = dict(OBJECTIVE_DEFAULTS, **params)
+            prm = ObjectiveParams_t(*[float(v[k]) for k in OBJECTIVE_KEYS])
+        loss = torch.empty(1, dtype=torch.float64, device="cuda")
+        D = torch.empty(S, dtype=torch.float64, device="cuda")
+        dL = torch.empty_like(images) if want_grad else None
+        vp = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a.size else None
+        self._check(self._lib.dgs_objective(self.h, _ptr(images.contiguous()), _ptr(refs.contiguous()), vp(ri), S,
+                                            refs.shape[0], H, W, vp(pt), pt.shape[0], vp(pm), pm.shape[0], vp(an),
+                                            an.size, None if prm is None else ctypes.byref(prm), _ptr(loss), _ptr(D),
+                                            _ptr(dL), _stream(stream)), "dgs_objective")
+        return loss, D, dL
+
     def image_mse(self, images, refs, ref_index, weight=1.0, want_grad=False, stream=None):
         import torch
         S, H, W, _ = images.shape
@@ -361,6 +398,34 @@ def render_function():
             return (None, None, None, None, None) + tuple(grads[k] for k in SCENE_FIELDS)
 
     return RenderStates
+
+
+def objective_function():
+    """A torch.autograd.Function for the Eq. 2 objective over rendered images:
+    forward = dgs_objective (loss and per-state D), backward = its gradient
+    with respect to the images (computed in the same call)."""
+    import torch
+
+    class Objective(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, renderer, images, refs, ref_index, pairs_t, pairs_m, anchors, params):
+            loss, D, dL = renderer.objective(images.detach(), refs, ref_index, pairs_t, pairs_m, anchors, params,
+                                             want_grad=True)
+            ctx.save_for_backward(dL)
+            ctx.mark_non_differentiable(D)
+            return loss[0], D
+
+        @staticmethod
+        def backward(ctx, g_loss, g_D):
+            (dL,) = ctx.saved_tensors
+            return None, dL * g_loss.to(dL.dtype), None, None, None, None, None, None
+
+    return Objective
+
+
+def objective(renderer, images, refs, ref_index, pairs_t=(), pairs_m=(), anchors=(), params=None):
+    """Differentiable Eq. 2 loss of rendered images: returns (loss, D)."""
+    return objective_function().apply(renderer, images, refs, ref_index, pairs_t, pairs_m, anchors, params)
 
 
 def render(renderer, scene: DeviceScene, states: DeviceStates, cams, bg):

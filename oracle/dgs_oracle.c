@@ -63,6 +63,8 @@ typedef struct {
     const float *opacity_logit;       /* [n] */
     const float *colour;              /* [n][nc] */
     const float *res;                 /* [L-1][n][11+nc] */
+    const float *affine;              /* [C][T][12] cluster affine keyframes of Eq. 1, or NULL (identity) */
+    int32_t affine_T;                 /* keyframes per cluster, keyframe k at time k / T (period 1) */
 } OScene;
 
 typedef struct {
@@ -129,6 +131,35 @@ static void decode(const OScene *s, int i, int d, OAttr *a)
         a->logit += r[10];
         for (int k = 0; k < nc; ++k) a->col[k] += r[11 + k];
     }
+}
+
+/* Cluster affine A_{c,t} of Eq. 1 (3x4, row-major: linear part | translation):
+ * keyframe k of cluster c holds A at time k / T; between keyframes the twelve
+ * entries are interpolated linearly, periodically in t with period 1.  Returns
+ * the keyframes used (k0, k1) and the weight w of k1 (NULL affine: identity). */
+static void affine_at(const OScene *s, int c, double t, double A[12], int *k0, int *k1, double *w)
+{
+    if (!s->affine) {
+        for (int k = 0; k < 12; ++k) A[k] = (k == 0 || k == 5 || k == 10) ? 1.0 : 0.0;
+        *k0 = *k1 = -1; *w = 0.0;
+        return;
+    }
+    int T = s->affine_T;
+    double u = t * T;
+    double fl = floor(u);
+    *w = u - fl;
+    long kk = (long)fl % T;
+    if (kk < 0) kk += T;
+    *k0 = (int)kk; *k1 = (int)((kk + 1) % T);
+    const float *a0 = s->affine + ((size_t)c * T + *k0) * 12, *a1 = s->affine + ((size_t)c * T + *k1) * 12;
+    for (int k = 0; k < 12; ++k) A[k] = (1.0 - *w) * a0[k] + *w * a1[k];
+}
+
+static int cluster_of_idx(const OScene *s, int i)
+{
+    int c = 0;
+    while (!(i >= s->cluster_offsets[c] && i < s->cluster_offsets[c + 1])) ++c;
+    return c;
 }
 
 /* Shared temporal basis of Eq. 1: b_{2j-1}(t) = cos(2 pi j t), b_{2j}(t) = sin(2 pi j t). */
@@ -224,7 +255,17 @@ static void project_one(const OScene *s, int i, int d, double t, const OCam *cam
     memset(rec, 0, sizeof(*rec));
     rec->idx = i;
     decode(s, i, d, &f->a);
-    for (int k = 0; k < 3; ++k) f->mu[k] = f->a.mu[k];
+    if (s->affine) {   /* Eq. 1: A_{c,t} mubar + (delivered position residuals) */
+        double A[12], w;
+        int k0, k1;
+        affine_at(s, cluster_of_idx(s, i), t, A, &k0, &k1, &w);
+        const float *m0 = s->mu0 + 3 * i;
+        for (int k = 0; k < 3; ++k)
+            f->mu[k] = A[4 * k] * m0[0] + A[4 * k + 1] * m0[1] + A[4 * k + 2] * m0[2] + A[4 * k + 3] +
+                       (f->a.mu[k] - m0[k]);
+    } else {
+        for (int k = 0; k < 3; ++k) f->mu[k] = f->a.mu[k];
+    }
     for (int r = 0; r < s->temporal_rank; ++r) {
         double b = basis(r, t);
         for (int k = 0; k < 3; ++k) f->mu[k] += b * s->u[((size_t)r * s->n + i) * 3 + k];
@@ -544,7 +585,7 @@ typedef struct { double mx, my, A, B, Cc, o, rgb[3]; } OGrad2;
 /* Accumulate the chain rule of one record into the scene gradient arrays. */
 static void backprop_record(const OScene *s, int i, int d, double t, const OCam *cam,
                             const OGrad2 *g, double *g_mu0, double *g_u, double *g_ls,
-                            double *g_quat, double *g_logit, double *g_col, double *g_res)
+                            double *g_quat, double *g_logit, double *g_col, double *g_res, double *g_aff)
 {
     ORec rec;
     OFwd f;
@@ -640,7 +681,26 @@ static void backprop_record(const OScene *s, int i, int d, double t, const OCam 
     double dq = gqn[0] * f.qn[0] + gqn[1] * f.qn[1] + gqn[2] * f.qn[2] + gqn[3] * f.qn[3];
     for (int k = 0; k < 4; ++k) gq[k] = (gqn[k] - f.qn[k] * dq) / f.qnorm;
     /* scatter to base, temporal coefficients and delivered residual layers */
-    for (int k = 0; k < 3; ++k) { g_mu0[3 * i + k] += gmu[k]; g_ls[3 * i + k] += gls[k]; }
+    if (s->affine) {   /* mu = A mubar + ...: d/dmubar = A_lin^T, d/dA = (mubar, 1) per row */
+        double A[12], w;
+        int k0, k1;
+        const int c = cluster_of_idx(s, i);
+        affine_at(s, c, t, A, &k0, &k1, &w);
+        const float *m0 = s->mu0 + 3 * i;
+        for (int k = 0; k < 3; ++k) g_mu0[3 * i + k] += A[k] * gmu[0] + A[4 + k] * gmu[1] + A[8 + k] * gmu[2];
+        if (g_aff) {
+            const double pv[4] = {m0[0], m0[1], m0[2], 1.0};
+            double *ga0 = g_aff + ((size_t)c * s->affine_T + k0) * 12, *ga1 = g_aff + ((size_t)c * s->affine_T + k1) * 12;
+            for (int r = 0; r < 3; ++r)
+                for (int k = 0; k < 4; ++k) {
+                    ga0[4 * r + k] += (1.0 - w) * gmu[r] * pv[k];
+                    ga1[4 * r + k] += w * gmu[r] * pv[k];
+                }
+        }
+        for (int k = 0; k < 3; ++k) g_ls[3 * i + k] += gls[k];
+    } else {
+        for (int k = 0; k < 3; ++k) { g_mu0[3 * i + k] += gmu[k]; g_ls[3 * i + k] += gls[k]; }
+    }
     for (int r = 0; r < s->temporal_rank; ++r) {
         double b = basis(r, t);
         for (int k = 0; k < 3; ++k) g_u[((size_t)r * s->n + i) * 3 + k] += b * gmu[k];
@@ -670,7 +730,7 @@ static void backprop_record(const OScene *s, int i, int d, double t, const OCam 
 int o_render_backward(const OScene *s, const uint8_t *depth, double t, const OCam *cam,
                       const double *bg, const double *dL_dimg,
                       double *g_mu0, double *g_u, double *g_ls, double *g_quat,
-                      double *g_logit, double *g_col, double *g_res, double *g2d_out)
+                      double *g_logit, double *g_col, double *g_res, double *g2d_out, double *g_aff)
 {
     int m = 0;
     ORec *recs = project_sorted(s, depth, t, cam, &kDefaultEps, &m);
@@ -731,7 +791,7 @@ int o_render_backward(const OScene *s, const uint8_t *depth, double t, const OCa
         int i = r->idx;
         int c = 0;
         while (!(i >= s->cluster_offsets[c] && i < s->cluster_offsets[c + 1])) ++c;
-        backprop_record(s, i, depth[c], t, cam, &g2[k], g_mu0, g_u, g_ls, g_quat, g_logit, g_col, g_res);
+        backprop_record(s, i, depth[c], t, cam, &g2[k], g_mu0, g_u, g_ls, g_quat, g_logit, g_col, g_res, g_aff);
         if (g2d_out) {
             double *o = g2d_out + (size_t)i * 9;
             o[0] += g2[k].mx; o[1] += g2[k].my; o[2] += g2[k].A; o[3] += g2[k].B; o[4] += g2[k].Cc;

@@ -35,7 +35,7 @@ __all__ = [
     "Scene", "Camera", "States", "Workload",
     "make_scene", "ring_camera", "prefix_states", "bernoulli_states",
     "erase_one_packet", "mask_words", "config", "CONFIG_NAMES", "MixSpec", "mix_specs", "mix_workload",
-    "completion_groups", "group_contexts",
+    "completion_groups", "group_contexts", "cluster_affine",
 ]
 
 
@@ -54,6 +54,7 @@ class Scene:
     opacity_logit: np.ndarray    # f32 [n]
     colour: np.ndarray           # f32 [n, 3*(sh+1)^2]
     res: np.ndarray              # f32 [L-1, n, K]
+    affine: np.ndarray | None = None   # f32 [C, T, 12] cluster affine keyframes of Eq. 1 (None = identity)
 
     @property
     def n_colour(self) -> int:
@@ -78,7 +79,8 @@ class Scene:
                      self.temporal_rank, offs, self.mu0[idx].copy(),
                      self.u[:, idx].copy(), self.log_scale[idx].copy(),
                      self.quat[idx].copy(), self.opacity_logit[idx].copy(),
-                     self.colour[idx].copy(), self.res[:, idx].copy())
+                     self.colour[idx].copy(), self.res[:, idx].copy(),
+                     None if self.affine is None else self.affine.copy())
 
     def arrays(self):
         return dict(mu0=self.mu0, u=self.u, log_scale=self.log_scale, quat=self.quat,
@@ -346,6 +348,17 @@ def group_contexts(groups: np.ndarray, n_contexts: int, n_clusters: int, n_layer
     for g, (c, l) in enumerate(groups):
         d[g * n_contexts:(g + 1) * n_contexts, c] = l
     return _pack(depths_to_bits(d, n_layers))
+
+
+def cluster_affine(n_clusters: int, n_keyframes: int, rng: np.random.Generator, linear_std: float = 0.05,
+                   shift_std: float = 0.1) -> np.ndarray:
+    """Cluster affine keyframes of Eq. 1 near the identity: [C, T, 12] float32,
+    row-major 3x4 (linear part | translation), linear part I + N(0, linear_std^2),
+    translation N(0, shift_std^2)."""
+    A = np.zeros((n_clusters, n_keyframes, 3, 4))
+    A[..., :3] = np.eye(3) + rng.normal(0.0, linear_std, size=(n_clusters, n_keyframes, 3, 3))
+    A[..., 3] = rng.normal(0.0, shift_std, size=(n_clusters, n_keyframes, 3))
+    return A.reshape(n_clusters, n_keyframes, 12).astype(np.float32)
 
 
 CONFIG_NAMES = ("c1_plain_4k", "c2_dynamic_250k", "c3_fwdbwd_250k", "c4_utility_2p7m", "c5_mix_48")

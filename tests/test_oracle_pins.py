@@ -652,3 +652,80 @@ def test_objective_gradient_finite_differences_and_special_cases():
     # perfect renders: zero objective, zero gradient
     L0, D0, g0 = oracle.objective(refs[ridx], refs, ridx, **kw)
     assert L0 == 0.0 and np.all(D0 == 0.0) and np.abs(g0).max() < 1e-12   # SSIM is stationary at x = y
+
+
+# ------------------------------------------------------------ cluster affine (Eq. 1)
+def _affine_case():
+    import dataclasses
+    w = synth.config("c3_fwdbwd_250k", scale=0.004, n_states=1)
+    sc = w.scene
+    cam = synth.ring_camera(1, 8, 48, 40, 60.0)
+    D = oracle.full_depth(sc)
+    return sc, cam, D, dataclasses
+
+
+def test_cluster_affine_special_cases():
+    """Identity keyframes change nothing; a uniform scale by 2 equals rendering
+    means doubled (exact in FP32); at a keyframe time only that keyframe counts,
+    half way between two keyframes their average."""
+    sc, cam, D, dc = _affine_case()
+    bg = np.zeros(3)
+    base, _, _ = oracle.render(sc, D, 0.3, cam, bg)
+    C = sc.n_clusters
+    eye = np.tile(np.array([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0], np.float32), (C, 4, 1))
+    ident, _, _ = oracle.render(dc.replace(sc, affine=eye), D, 0.3, cam, bg)
+    assert np.abs(ident - base).max() < 1e-12
+    two = eye.copy(); two[..., [0, 5, 10]] = 2.0
+    scaled, _, _ = oracle.render(dc.replace(sc, affine=two), D, 0.3, cam, bg)
+    ref2, _, _ = oracle.render(dc.replace(sc, mu0=(sc.mu0 * 2).astype(np.float32)), D, 0.3, cam, bg)
+    assert np.abs(scaled - ref2).max() < 1e-12
+    # keyframes on a 2^-10 grid, so that the average of two is exact in FP32
+    A = (np.round(synth.cluster_affine(C, 4, np.random.default_rng(9)) * 1024) / 1024).astype(np.float32)
+    at_key, _, _ = oracle.render(dc.replace(sc, affine=A), D, 0.5, cam, bg)          # t = 2/4: keyframe 2
+    one, _, _ = oracle.render(dc.replace(sc, affine=A[:, 2:3].copy()), D, 0.5, cam, bg)
+    assert np.abs(at_key - one).max() < 1e-12
+    mid, _, _ = oracle.render(dc.replace(sc, affine=A), D, 0.125, cam, bg)            # half way 0 -> 1
+    avg = (0.5 * A[:, 0:1].astype(np.float64) + 0.5 * A[:, 1:2].astype(np.float64))
+    avg32 = avg.astype(np.float32)
+    assert np.array_equal(avg32.astype(np.float64), avg)                               # exactly representable?
+    mid_ref, _, _ = oracle.render(dc.replace(sc, affine=avg32), D, 0.125, cam, bg)
+    assert np.abs(mid - mid_ref).max() < 1e-12
+
+
+def test_cluster_affine_gradient_finite_differences():
+    """dL/dA (keyframes, between two of them) and dL/dmubar through A against
+    central differences on a sparse scene; parameters whose differences at h
+    and h/2 disagree straddle a threshold and are excluded and counted."""
+    import dataclasses
+    sc, cam = _fd_case(0)
+    A = synth.cluster_affine(sc.n_clusters, 3, np.random.default_rng(4))
+    sca = dataclasses.replace(sc, affine=A)
+    D = oracle.full_depth(sca)
+    t = 0.2                                                  # between keyframes 0 and 1 (w = 0.6)
+    rng = np.random.default_rng(1)
+    bg = np.array([0.1, 0.0, 0.2])
+    target = rng.uniform(size=(cam.height, cam.width, 3))
+    _, img = _loss(sca, D, t, cam, bg, target)
+    g = oracle.render_backward(sca, D, t, cam, bg, 2.0 * (img - target) / img.size)
+    checked = excluded = 0
+    for name, arr in (("affine", A), ("mu0", sca.mu0)):
+        G = g[name].reshape(-1)
+        flat = arr.reshape(-1)
+        scale = max(np.abs(G).max(), 1e-12)
+        cand = np.argsort(-np.abs(G))[:16]
+        for j in cand:
+            def fd(h):
+                orig = flat[j]
+                flat[j] = np.float32(orig + h); lp, _ = _loss(sca, D, t, cam, bg, target); up = float(flat[j])
+                flat[j] = np.float32(orig - h); lm, _ = _loss(sca, D, t, cam, bg, target); dn = float(flat[j])
+                flat[j] = orig
+                return (lp - lm) / (up - dn)
+            f1, f2 = fd(1e-4), fd(5e-5)     # cluster parameters move many Gaussians: small steps
+            if abs(f1 - f2) > 1e-2 * max(abs(f1), abs(f2), 1e-3 * scale):
+                excluded += 1
+                continue
+            checked += 1
+            assert abs(G[j] - f2) <= 2e-3 * scale + 1e-9, (name, j, G[j], f1, f2)
+    assert checked >= 16 and excluded <= checked // 2, (checked, excluded)
+    # keyframes the state's time does not touch get nothing
+    assert np.all(g["affine"][:, 2] == 0.0)

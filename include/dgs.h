@@ -83,8 +83,15 @@ typedef void *dgs_stream;     /* a cudaStream_t; NULL = the legacy default strea
  *                       SH coefficients x 3 channels, channel innermost)
  *   res [L-1][n][K]     refinement l (1..L-1) of Gaussian i, K = 11 + NC:
  *                       dmu[3], dlog_scale[3], dquat[4], dlogit[1], dcolour[NC]
+ *   affine [C][T][12]   optional cluster affine A_{c,t} of Eq. 1 (NULL = the
+ *                       identity): keyframe k of cluster c, row-major 3x4
+ *                       (linear part | translation), holds A at time k / T
+ *                       (T = affine_T >= 1); between keyframes the twelve
+ *                       entries are interpolated linearly, periodically in t
+ *                       with period 1
  * A Gaussian of cluster c at delivered depth d >= 1 renders with every
- * attribute = base + res[0] + ... + res[d-2]; at depth 0 it is absent.
+ * attribute = base + res[0] + ... + res[d-2]; at depth 0 it is absent.  Its
+ * mean at time t is A_{c,t} mu0 + (position residuals) + sum_r b_r(t) u_r.
  */
 typedef struct {
     int32_t n, n_clusters, n_layers, sh_degree, temporal_rank;
@@ -96,11 +103,14 @@ typedef struct {
     const float *opacity_logit;
     const float *colour;
     const float *res;
+    const float *affine;              /* [device] [n_clusters][affine_T][12] or NULL */
+    int32_t affine_T;
 } dgs_scene;
 
 /* Gradients in the scene's layout, [device], ACCUMULATED (+=) by the backward. */
 typedef struct {
     float *mu0, *u, *log_scale, *quat, *opacity_logit, *colour, *res;
+    float *affine;                    /* [n_clusters][affine_T][12]; needed when the scene has an affine */
 } dgs_scene_grad;
 
 /* OpenCV pinhole: p_cam = R_wc p_world + t_wc; x right, y down, z forward;

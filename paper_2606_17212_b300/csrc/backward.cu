@@ -7,7 +7,10 @@
 // receives the sum over variants d > l (layer l is part of every variant of
 // depth >= l + 1); the base receives the sum over all variants; layers no
 // state delivered receive nothing.  Temporal coefficients u_k receive
-// b_k(t) times the mean gradient of each record.
+// b_k(t) times the mean gradient of each record.  With a cluster affine
+// (Eq. 1), the base mean receives A_{c,t}^T times each record's mean
+// gradient, and each record's mean gradient is kept for k_affine_grad, which
+// forms the keyframe gradients per (view group, cluster).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -54,6 +57,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(SceneDev s, const ViewGroup
         float gu[MAX_RANK][3];
 #pragma unroll
         for (int r = 0; r < MAX_RANK; ++r) gu[r][0] = gu[r][1] = gu[r][2] = 0.0f;
+        float gm0[3] = {0.0f, 0.0f, 0.0f};    // base-mean gradient through the affine
         bool any = false;
         for (int d = s.L; d >= 1; --d) {
             bool decoded = false;
@@ -75,11 +79,20 @@ __global__ void __launch_bounds__(128) k_project_bwd(SceneDev s, const ViewGroup
                 }
                 const ViewGroup vg = vgs[v];
                 Proj P; Fwd F;
-                project_fwd<SH>(s, i, a, vg, P, F);
+                project_fwd<SH>(s, i, c, a, vg, P, F);
                 if (!P.live) continue;
                 const float gg[9] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x};
                 float gmu[3];
                 project_bwd<SH>(a, vg, P, F, gg, acc, gmu);
+                if (s.affine) {
+                    float A[12], w;
+                    int k0, k1;
+                    affine_at(s, c, vg.time, A, k0, k1, w);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) gm0[k] += A[k] * gmu[0] + A[4 + k] * gmu[1] + A[8 + k] * gmu[2];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) g.rec_gmu[(size_t)slot * 3 + k] = gmu[k];
+                }
                 for (int r = 0; r < s.R && r < MAX_RANK; ++r) {
                     const float bk = temporal_basis(r, vg.time);
 #pragma unroll
@@ -101,7 +114,10 @@ __global__ void __launch_bounds__(128) k_project_bwd(SceneDev s, const ViewGroup
                 for (int k = 0; k < NC; ++k) dst[11 + k] += acc.col[k];
             } else {
 #pragma unroll
-                for (int k = 0; k < 3; ++k) { g.mu0[3 * i + k] += acc.mu[k]; g.ls[3 * i + k] += acc.ls[k]; }
+                for (int k = 0; k < 3; ++k) {
+                    g.mu0[3 * i + k] += s.affine ? gm0[k] : acc.mu[k];
+                    g.ls[3 * i + k] += acc.ls[k];
+                }
 #pragma unroll
                 for (int k = 0; k < 4; ++k) g.quat[4 * i + k] += acc.q[k];
                 g.logit[i] += acc.logit;
@@ -117,19 +133,76 @@ __global__ void __launch_bounds__(128) k_project_bwd(SceneDev s, const ViewGroup
     }
 }
 
+// Keyframe gradients of the cluster affine: one block per (view group v,
+// cluster c) sums dL/dmu (x) (mubar, 1) over the records of (v, c) and adds the
+// sum to the two keyframes of v's time with their interpolation weights.
+__global__ void __launch_bounds__(256) k_affine_grad(SceneDev s, const ViewGroup *__restrict__ vgs,
+                                                     const uint32_t *__restrict__ need,
+                                                     const uint32_t *__restrict__ recBase,
+                                                     const float *__restrict__ rec_gmu, float *__restrict__ g_aff)
+{
+    __shared__ float red[8][12];
+    const int v = blockIdx.x / s.C, c = blockIdx.x % s.C;
+    const uint32_t nd = need[(size_t)v * s.C + c] & ~1u;
+    if (!nd) return;
+    const uint32_t nvar = (uint32_t)__popc(nd);
+    const uint32_t r0 = recBase[(size_t)v * s.C + c], r1 = recBase[(size_t)v * s.C + c + 1];
+    const int i0 = s.offs[c];
+    float acc[12];
+#pragma unroll
+    for (int e = 0; e < 12; ++e) acc[e] = 0.0f;
+    for (uint32_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        const int i = i0 + (int)((r - r0) / nvar);
+        const float g0 = rec_gmu[(size_t)r * 3], g1 = rec_gmu[(size_t)r * 3 + 1], g2 = rec_gmu[(size_t)r * 3 + 2];
+        const float m[4] = {__ldg(s.mu0 + 3 * i), __ldg(s.mu0 + 3 * i + 1), __ldg(s.mu0 + 3 * i + 2), 1.0f};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            acc[k] = fmaf(g0, m[k], acc[k]);
+            acc[4 + k] = fmaf(g1, m[k], acc[4 + k]);
+            acc[8 + k] = fmaf(g2, m[k], acc[8 + k]);
+        }
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int e = 0; e < 12; ++e) {
+        float x = acc[e];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[w][e] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 12) {
+        float tot = 0.0f;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += red[k][threadIdx.x];
+        float A[12], wt;
+        int k0, k1;
+        affine_at(s, c, vgs[v].time, A, k0, k1, wt);
+        atomicAdd(g_aff + ((size_t)c * s.aT + k0) * 12 + threadIdx.x, (1.0f - wt) * tot);
+        atomicAdd(g_aff + ((size_t)c * s.aT + k1) * 12 + threadIdx.x, wt * tot);
+    }
+}
+
 }  // namespace
 
 void launch_project_bwd(const SceneDev &s, const ViewGroup *vgs, int V, const uint32_t *need,
-                        const uint32_t *recBase, const float4 *rec_grad, const GradDev &g, int sms,
-                        cudaStream_t st)
+                        const uint32_t *recBase, const float4 *rec_grad, const GradDev &g, size_t rec_cap,
+                        int sms, cudaStream_t st)
 {
     if (s.n == 0) return;
+    if (s.affine && rec_cap) cudaMemsetAsync(g.rec_gmu, 0, sizeof(float) * 3 * rec_cap, st);
     long long b = (s.n + 127) / 128;
     if (b > (long long)sms * 32) b = (long long)sms * 32;
-    ProfScope ps_("project_bwd", st);
-    if (s.sh == 0) k_project_bwd<0><<<(unsigned)b, 128, 0, st>>>(s, vgs, V, need, recBase, rec_grad, g);
-    else k_project_bwd<3><<<(unsigned)b, 128, 0, st>>>(s, vgs, V, need, recBase, rec_grad, g);
-    count_launch();
+    {
+        ProfScope ps_("project_bwd", st);
+        if (s.sh == 0) k_project_bwd<0><<<(unsigned)b, 128, 0, st>>>(s, vgs, V, need, recBase, rec_grad, g);
+        else k_project_bwd<3><<<(unsigned)b, 128, 0, st>>>(s, vgs, V, need, recBase, rec_grad, g);
+        count_launch();
+    }
+    if (s.affine && V > 0) {
+        ProfScope ps_("affine_grad", st);
+        k_affine_grad<<<(unsigned)(V * s.C), 256, 0, st>>>(s, vgs, need, recBase, g.rec_gmu, g.affine);
+        count_launch();
+    }
 }
 
 }  // namespace dgs

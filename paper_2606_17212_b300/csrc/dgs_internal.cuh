@@ -60,10 +60,13 @@ struct SceneDev {
     int n, C, L, sh, R, nc, K;
     const int32_t *offs;
     const float *mu0, *u, *ls, *quat, *logit, *colour, *res;
+    const float *affine;       // [C][aT][12] cluster affine keyframes, or null (identity)
+    int aT;
 };
 
 struct GradDev {
-    float *mu0, *u, *ls, *quat, *logit, *colour, *res;
+    float *mu0, *u, *ls, *quat, *logit, *colour, *res, *affine;
+    float *rec_gmu;            // [nRec][3] per-record mean gradient (only with an affine)
 };
 
 // ------------------------------------------------------------------ MSE

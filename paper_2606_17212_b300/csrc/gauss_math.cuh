@@ -16,6 +16,7 @@ template <int SH> struct NCol { static constexpr int value = 3 * (SH + 1) * (SH 
 template <int SH>
 struct Attr {
     float mu[3], ls[3], q[4], logit;
+    float mu0[3];              // the base mean alone (the cluster affine applies to it)
     float col[NCol<SH>::value];
 };
 
@@ -24,7 +25,10 @@ __device__ __forceinline__ void load_base(const SceneDev &s, int i, Attr<SH> &a)
 {
     constexpr int NC = NCol<SH>::value;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) { a.mu[k] = __ldg(s.mu0 + 3 * i + k); a.ls[k] = __ldg(s.ls + 3 * i + k); }
+    for (int k = 0; k < 3; ++k) {
+        a.mu[k] = a.mu0[k] = __ldg(s.mu0 + 3 * i + k);
+        a.ls[k] = __ldg(s.ls + 3 * i + k);
+    }
     const float4 q = __ldg(reinterpret_cast<const float4 *>(s.quat) + i);
     a.q[0] = q.x; a.q[1] = q.y; a.q[2] = q.z; a.q[3] = q.w;
     a.logit = __ldg(s.logit + i);
@@ -46,6 +50,23 @@ __device__ __forceinline__ void add_layer(const SceneDev &s, int i, int l, Attr<
     a.logit += __ldg(r + 10);
 #pragma unroll
     for (int k = 0; k < NC; ++k) a.col[k] += __ldg(r + 11 + k);
+}
+
+// Cluster affine A_{c,t} of Eq. 1: keyframe k at time k / T, linear
+// interpolation of the twelve entries between keyframes, periodic in t.
+// Returns the keyframes used and the weight w of k1.
+__device__ __forceinline__ void affine_at(const SceneDev &s, int c, float t, float *A, int &k0, int &k1, float &w)
+{
+    const float u = t * (float)s.aT;
+    const float fl = floorf(u);
+    w = u - fl;
+    int kk = (int)fl % s.aT;
+    if (kk < 0) kk += s.aT;
+    k0 = kk;
+    k1 = (kk + 1) % s.aT;
+    const float *a0 = s.affine + ((size_t)c * s.aT + k0) * 12, *a1 = s.affine + ((size_t)c * s.aT + k1) * 12;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) A[k] = fmaf(w, __ldg(a1 + k), (1.0f - w) * __ldg(a0 + k));
 }
 
 // Shared temporal basis of Eq. 1: b_{2j-1}(t) = cos(2 pi j t), b_{2j}(t) = sin(2 pi j t).
@@ -129,13 +150,23 @@ struct Proj {
 
 // Eq. 1 deformation and EWA projection of decoded attributes `a` of Gaussian i.
 template <int SH>
-__device__ __forceinline__ void project_fwd(const SceneDev &s, int i, const Attr<SH> &a,
+__device__ __forceinline__ void project_fwd(const SceneDev &s, int i, int c, const Attr<SH> &a,
                                             const ViewGroup &vg, Proj &P, Fwd &F)
 {
     P.live = false;
     P.rclip = false;
+    if (s.affine) {   // A_{c,t} mubar + (position residuals)
+        float A[12], w;
+        int k0, k1;
+        affine_at(s, c, vg.time, A, k0, k1, w);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) F.mu[k] = a.mu[k];
+        for (int k = 0; k < 3; ++k)
+            F.mu[k] = fmaf(A[4 * k], a.mu0[0], fmaf(A[4 * k + 1], a.mu0[1], fmaf(A[4 * k + 2], a.mu0[2], A[4 * k + 3]))) +
+                      (a.mu[k] - a.mu0[k]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) F.mu[k] = a.mu[k];
+    }
     for (int r = 0; r < s.R; ++r) {
         const float bk = temporal_basis(r, vg.time);
         const float *ur = s.u + ((size_t)r * s.n + i) * 3;

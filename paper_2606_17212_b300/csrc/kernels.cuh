@@ -95,8 +95,10 @@ void launch_objective_grad(const float *images, const float *refs, const int32_t
                            float ssim_weight, float tscale, const int32_t *toff, const int2 *tlist, float *dL,
                            cudaStream_t st);
 
+// rec_cap: record slots of rec_grad (the per-record mean gradients of the
+// affine, g.rec_gmu, are cleared over it)
 void launch_project_bwd(const SceneDev &s, const ViewGroup *vgs, int V, const uint32_t *need,
-                        const uint32_t *recBase, const float4 *rec_grad, const GradDev &g, int sms,
-                        cudaStream_t st);
+                        const uint32_t *recBase, const float4 *rec_grad, const GradDev &g, size_t rec_cap,
+                        int sms, cudaStream_t st);
 
 }  // namespace dgs

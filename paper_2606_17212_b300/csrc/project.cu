@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(128, 4) k_project(SceneDev s, const ViewGroup 
                                       (uint32_t)__popc(nd & ((1u << d) - 1u));
                 const ViewGroup &vg = vgs[v];
                 Proj P; Fwd F;
-                project_fwd<SH>(s, i, a, vg, P, F);
+                project_fwd<SH>(s, i, c, a, vg, P, F);
                 Rec R;
                 if (P.live) {
                     R.mx = P.mx; R.my = P.my; R.A = P.A * K_AC; R.B = P.B * K_B; R.C = P.C * K_AC; R.o = P.o;

@@ -27,7 +27,8 @@ class Scene_t(ctypes.Structure):
                 ("sh_degree", ctypes.c_int32), ("temporal_rank", ctypes.c_int32),
                 ("cluster_offsets", ctypes.c_void_p), ("mu0", ctypes.c_void_p), ("u", ctypes.c_void_p),
                 ("log_scale", ctypes.c_void_p), ("quat", ctypes.c_void_p),
-                ("opacity_logit", ctypes.c_void_p), ("colour", ctypes.c_void_p), ("res", ctypes.c_void_p)]
+                ("opacity_logit", ctypes.c_void_p), ("colour", ctypes.c_void_p), ("res", ctypes.c_void_p),
+                ("affine", ctypes.c_void_p), ("affine_T", ctypes.c_int32)]
 
 
 OBJECTIVE_KEYS = ("ssim_weight", "lambda_c", "cvar_q", "lambda_t", "lambda_m", "anchor_weight")
@@ -41,7 +42,7 @@ class ObjectiveParams_t(ctypes.Structure):
 
 class SceneGrad_t(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in
-                ("mu0", "u", "log_scale", "quat", "opacity_logit", "colour", "res")]
+                ("mu0", "u", "log_scale", "quat", "opacity_logit", "colour", "res", "affine")]
 
 
 class Camera_t(ctypes.Structure):
@@ -151,12 +152,21 @@ def camera_array(cams):
 SCENE_FIELDS = ("mu0", "u", "log_scale", "quat", "opacity_logit", "colour", "res")
 
 
+def _grad_struct(grads: dict) -> SceneGrad_t:
+    ptrs = [(_ptr(grads[k]) if grads[k].numel() else None) for k in SCENE_FIELDS]
+    return SceneGrad_t(*ptrs, _ptr(grads.get("affine")))
+
+
 class DeviceScene:
     """Scene tensors resident on a CUDA device, with the C struct that points at them."""
 
-    def __init__(self, tensors: dict, n, n_clusters, n_layers, sh_degree, temporal_rank, cluster_offsets):
+    def __init__(self, tensors: dict, n, n_clusters, n_layers, sh_degree, temporal_rank, cluster_offsets,
+                 affine=None):
         import torch
         self.t = {k: tensors[k].contiguous() for k in SCENE_FIELDS}
+        # optional cluster affine keyframes of Eq. 1 [C, T, 12] (None = identity)
+        if affine is not None:
+            self.t["affine"] = affine.contiguous()
         self.offsets = cluster_offsets.to(torch.int32).contiguous()
         self.n, self.n_clusters, self.n_layers = int(n), int(n_clusters), int(n_layers)
         self.sh_degree, self.temporal_rank = int(sh_degree), int(temporal_rank)
@@ -167,13 +177,23 @@ class DeviceScene:
         ts = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k), np.float32)).to(device)
               for k in SCENE_FIELDS}
         offs = torch.from_numpy(np.asarray(scene.cluster_offsets, np.int32)).to(device)
-        return cls(ts, scene.n, scene.n_clusters, scene.n_layers, scene.sh_degree, scene.temporal_rank, offs)
+        aff = getattr(scene, "affine", None)
+        aff = None if aff is None else torch.from_numpy(np.ascontiguousarray(aff, np.float32)).to(device)
+        return cls(ts, scene.n, scene.n_clusters, scene.n_layers, scene.sh_degree, scene.temporal_rank, offs,
+                   affine=aff)
+
+    @property
+    def fields(self):
+        """The differentiable tensors: SCENE_FIELDS, plus "affine" when present."""
+        return SCENE_FIELDS + (("affine",) if "affine" in self.t else ())
 
     def struct(self) -> Scene_t:
         g = lambda k: _ptr(self.t[k]) if self.t[k].numel() else None
+        aff = self.t.get("affine")
         return Scene_t(self.n, self.n_clusters, self.n_layers, self.sh_degree, self.temporal_rank,
                        _ptr(self.offsets), g("mu0"), g("u"), g("log_scale"), g("quat"),
-                       g("opacity_logit"), g("colour"), g("res"))
+                       g("opacity_logit"), g("colour"), g("res"), _ptr(aff),
+                       0 if aff is None else int(aff.shape[1]))
 
     def zeros_like_grads(self) -> dict:
         import torch
@@ -300,7 +320,7 @@ class Renderer:
         if grads is None:
             grads = scene.zeros_like_grads()
         bgv = (ctypes.c_float * 3)(*[float(x) for x in bg])
-        g = SceneGrad_t(*[(_ptr(grads[k]) if grads[k].numel() else None) for k in SCENE_FIELDS])
+        g = _grad_struct(grads)
         sc, st, ca = scene.struct(), states.struct(), camera_array(cams)
         img = None if images is None else images.contiguous()
         self._check(self._lib.dgs_render_backward(self.h, ctypes.byref(sc), ctypes.byref(st), ca, len(cams), bgv,
@@ -395,7 +415,7 @@ def render_function():
             (out,) = ctx.saved_tensors
             grads = ctx.renderer.render_backward(ctx.scene, ctx.states, ctx.cams, ctx.bg, grad_out.contiguous(),
                                                  images=out)
-            return (None, None, None, None, None) + tuple(grads[k] for k in SCENE_FIELDS)
+            return (None, None, None, None, None) + tuple(grads[k] for k in ctx.scene.fields)
 
     return RenderStates
 
@@ -431,7 +451,7 @@ def objective(renderer, images, refs, ref_index, pairs_t=(), pairs_m=(), anchors
 def render(renderer, scene: DeviceScene, states: DeviceStates, cams, bg):
     """Differentiable batched render: images [S,H,W,3] with autograd to scene tensors."""
     fn = render_function()
-    return fn.apply(renderer, scene, states, cams, bg, *[scene.t[k] for k in SCENE_FIELDS])
+    return fn.apply(renderer, scene, states, cams, bg, *[scene.t[k] for k in scene.fields])
 
 
 def image_mse_noalloc(images, refs, ref_index, mse, psnr=None, dL=None, weight=1.0, stream=None) -> int:
@@ -523,7 +543,7 @@ class Plan:
 
     def backward(self, dL, grads, stream=None, images=None):
         """Adjoint of the last render; ``images``: its output, or None."""
-        g = SceneGrad_t(*[(_ptr(grads[k]) if grads[k].numel() else None) for k in SCENE_FIELDS])
+        g = _grad_struct(grads)
         self._check(self._lib.dgs_plan_backward(self.h, _ptr(images), _ptr(dL), ctypes.byref(g), _stream(stream)),
                     "dgs_plan_backward")
         return grads

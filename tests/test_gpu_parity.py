@@ -488,3 +488,50 @@ def test_objective_through_autograd_to_the_scene(R, torch):
     for k in dgs.SCENE_FIELDS:
         if g_hand[k].numel():
             assert torch.allclose(g_auto[k], g_hand[k], rtol=1e-4, atol=1e-6 * float(g_hand[k].abs().max()) + 1e-12)
+
+
+# --------------------------------------------------------------------- cluster affine (Eq. 1)
+def test_cluster_affine_matches_oracle_forward_backward_and_plan(R, torch):
+    """Scenes with cluster affine keyframes: batched images against the oracle
+    (non-marginal pixels), the adjoint (including the keyframe gradients)
+    against the oracle's, and a capture-safe plan equal to the context calls."""
+    import dataclasses
+    sc_h, states, cams = _grad_case()
+    A = synth.cluster_affine(sc_h.n_clusters, 3, np.random.default_rng(12))
+    sca = dataclasses.replace(sc_h, affine=A)
+    bg = np.array([0.1, 0.2, 0.3], np.float32)
+    sc = dgs.DeviceScene.from_host(sca)
+    st = dgs.DeviceStates.from_host(states)
+    imgs = R.render_states_batched(sc, st, cams, bg)
+    D = oracle.state_depths(states, sca.n_clusters, sca.n_layers)
+    rng = np.random.default_rng(3)
+    S, H, W = states.n, cams[0].height, cams[0].width
+    dL = rng.normal(size=(S, H, W, 3))
+    ref = None
+    for s in range(S):
+        cam = cams[int(states.cam[s])]
+        img_o, marg, _ = oracle.render(sca, D[s], float(states.t[s]), cam, bg)
+        err = np.abs(imgs[s].cpu().numpy().astype(np.float64) - img_o)[~marg]
+        assert err.max() <= IMG_TOL, (s, err.max())
+        dL[s][marg] = 0.0
+        g = oracle.render_backward(sca, D[s], float(states.t[s]), cam, bg, dL[s])
+        ref = g if ref is None else {k: ref[k] + g[k] for k in ref}
+    dLt = torch.from_numpy(dL.astype(np.float32)).cuda()
+    grads = R.render_backward(sc, st, cams, bg, dLt, images=imgs)
+    assert float(np.abs(ref["affine"]).max()) > 0
+    for k in sc.fields:
+        gg = grads[k].cpu().numpy().astype(np.float64)
+        gr = ref[k]
+        if gr.size == 0:
+            continue
+        scale = max(np.abs(gr).max(), 1e-6)
+        assert np.abs(gg - gr).max() <= GRAD_TOL * scale, (k, np.abs(gg - gr).max(), scale)
+    plan = dgs.Plan(R, sc, st, cams, bg, dgs.PLAN_RENDER, entry_headroom=2.0)
+    out = torch.empty_like(imgs)
+    plan.render(st.masks, out)
+    assert torch.equal(out, imgs)
+    gp = plan.backward(dLt, sc.zeros_like_grads(), images=out)
+    for k in sc.fields:
+        if grads[k].numel():
+            assert torch.allclose(gp[k], grads[k], rtol=1e-4, atol=1e-5 * float(grads[k].abs().max()) + 1e-12), k
+    plan.close()

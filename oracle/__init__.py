@@ -61,7 +61,8 @@ class _OScene(ctypes.Structure):
                 ("u", ctypes.c_void_p), ("log_scale", ctypes.c_void_p),
                 ("quat", ctypes.c_void_p), ("opacity_logit", ctypes.c_void_p),
                 ("colour", ctypes.c_void_p), ("res", ctypes.c_void_p),
-                ("affine", ctypes.c_void_p), ("affine_T", ctypes.c_int32)]
+                ("affine", ctypes.c_void_p), ("affine_T", ctypes.c_int32),
+                ("res_q", ctypes.c_void_p), ("res_step", ctypes.c_void_p), ("res_mode", ctypes.c_int32)]
 
 
 class _OCam(ctypes.Structure):
@@ -92,7 +93,7 @@ def _load():
                                       ctypes.c_int, ctypes.c_int, P, P, P]
         lib.o_render_rows.restype = ctypes.c_int64
         lib.o_render_backward.argtypes = [ctypes.POINTER(_OScene), P, ctypes.c_double,
-                                          ctypes.POINTER(_OCam), P, P] + [P] * 9
+                                          ctypes.POINTER(_OCam), P, P] + [P] * 10
         lib.o_sh_basis.argtypes = [P, ctypes.c_int, P]
         lib.o_rec_width.restype = ctypes.c_int
         _lib = lib
@@ -120,12 +121,19 @@ class _Pinned:
         aff = getattr(scene, "affine", None)
         if aff is not None:
             k["aff"] = c(aff, np.float32)
+        mode = int(getattr(scene, "res_mode", 0))
+        if mode:
+            k["step"] = c(scene.res_step, np.float32)
+            if mode == 1:
+                k["rq"] = c(scene.res_q, np.int16)
         self.s = _OScene(scene.n, scene.n_clusters, scene.n_layers, scene.sh_degree,
                          scene.temporal_rank, k["offs"].ctypes.data, k["mu0"].ctypes.data,
                          k["u"].ctypes.data, k["ls"].ctypes.data, k["q"].ctypes.data,
                          k["lg"].ctypes.data, k["col"].ctypes.data, k["res"].ctypes.data,
                          k["aff"].ctypes.data if aff is not None else None,
-                         int(aff.shape[1]) if aff is not None else 0)
+                         int(aff.shape[1]) if aff is not None else 0,
+                         k["rq"].ctypes.data if mode == 1 else None,
+                         k["step"].ctypes.data if mode else None, mode)
 
 
 def _cam(cam) -> _OCam:
@@ -242,10 +250,13 @@ def render_backward(scene, depth, t, cam, bg, dL_dimage, want_2d=False):
     aff = getattr(scene, "affine", None)
     if aff is not None:
         out["affine"] = np.zeros(aff.shape)
+    if int(getattr(scene, "res_mode", 0)) == 2:
+        out["res_step"] = np.zeros(np.asarray(scene.res_step).shape)
     lib.o_render_backward(ctypes.byref(pin.s), _ptr(d), float(t), ctypes.byref(oc), _ptr(bgd),
                           _ptr(g), _ptr(out["mu0"]), _ptr(out["u"]), _ptr(out["log_scale"]),
                           _ptr(out["quat"]), _ptr(out["opacity_logit"]), _ptr(out["colour"]),
-                          _ptr(out["res"]), _ptr(g2), _ptr(out["affine"]) if aff is not None else None)
+                          _ptr(out["res"]), _ptr(g2), _ptr(out["affine"]) if aff is not None else None,
+                          _ptr(out["res_step"]) if "res_step" in out else None)
     out["u"] = out["u"][:R]
     out["res"] = out["res"][:max(L - 1, 0)]
     if want_2d:

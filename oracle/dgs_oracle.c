@@ -65,6 +65,9 @@ typedef struct {
     const float *res;                 /* [L-1][n][11+nc] */
     const float *affine;              /* [C][T][12] cluster affine keyframes of Eq. 1, or NULL (identity) */
     int32_t affine_T;                 /* keyframes per cluster, keyframe k at time k / T (period 1) */
+    const int16_t *res_q;             /* [L-1][n][K] quantized refinement symbols (res_mode 1) */
+    const float *res_step;            /* [L-1][K] quantization steps (res_mode 1 and 2) */
+    int32_t res_mode;                 /* 0: res as given; 1: res_q * step; 2: res quantized to step */
 } OScene;
 
 typedef struct {
@@ -117,19 +120,45 @@ void o_closure(int C, int L, const uint32_t *mask, uint8_t *depth)
 /* ---- Section 3: base plus the delivered refinements l = 1..d-1 ---- */
 typedef struct { double mu[3], ls[3], q[4], logit, col[48]; } OAttr;
 
+/* Quantization of a refinement value to step st (the learned steps of
+ * Section 3): the signed 16-bit symbol v = round(x / st) (x / st in FP32, ties
+ * to even), clipped to [-32768, 32767]; returns v and whether it was clipped. */
+static double quant_symbol(float x, float st, int *clipped)
+{
+    float u = x / st;
+    double v = rint((double)u);
+    *clipped = 0;
+    if (v > 32767.0) { v = 32767.0; *clipped = 1; }
+    if (v < -32768.0) { v = -32768.0; *clipped = 1; }
+    return v;
+}
+
+/* Component k of refinement layer l (1-based) of Gaussian i as decoded. */
+static double res_value(const OScene *s, int l, int i, int k)
+{
+    int K = res_width(s);
+    size_t o = ((size_t)(l - 1) * s->n + i) * K + k;
+    if (s->res_mode == 1) return (double)s->res_q[o] * (double)s->res_step[(size_t)(l - 1) * K + k];
+    if (s->res_mode == 2) {
+        int cl;
+        float st = s->res_step[(size_t)(l - 1) * K + k];
+        return quant_symbol(s->res[o], st, &cl) * (double)st;
+    }
+    return s->res[o];
+}
+
 static void decode(const OScene *s, int i, int d, OAttr *a)
 {
-    int nc = n_colour(s), K = res_width(s);
+    int nc = n_colour(s);
     for (int k = 0; k < 3; ++k) { a->mu[k] = s->mu0[3 * i + k]; a->ls[k] = s->log_scale[3 * i + k]; }
     for (int k = 0; k < 4; ++k) a->q[k] = s->quat[4 * i + k];
     a->logit = s->opacity_logit[i];
     for (int k = 0; k < nc; ++k) a->col[k] = s->colour[(size_t)nc * i + k];
     for (int l = 1; l < d; ++l) {
-        const float *r = s->res + ((size_t)(l - 1) * s->n + i) * K;
-        for (int k = 0; k < 3; ++k) { a->mu[k] += r[k]; a->ls[k] += r[3 + k]; }
-        for (int k = 0; k < 4; ++k) a->q[k] += r[6 + k];
-        a->logit += r[10];
-        for (int k = 0; k < nc; ++k) a->col[k] += r[11 + k];
+        for (int k = 0; k < 3; ++k) { a->mu[k] += res_value(s, l, i, k); a->ls[k] += res_value(s, l, i, 3 + k); }
+        for (int k = 0; k < 4; ++k) a->q[k] += res_value(s, l, i, 6 + k);
+        a->logit += res_value(s, l, i, 10);
+        for (int k = 0; k < nc; ++k) a->col[k] += res_value(s, l, i, 11 + k);
     }
 }
 
@@ -585,7 +614,8 @@ typedef struct { double mx, my, A, B, Cc, o, rgb[3]; } OGrad2;
 /* Accumulate the chain rule of one record into the scene gradient arrays. */
 static void backprop_record(const OScene *s, int i, int d, double t, const OCam *cam,
                             const OGrad2 *g, double *g_mu0, double *g_u, double *g_ls,
-                            double *g_quat, double *g_logit, double *g_col, double *g_res, double *g_aff)
+                            double *g_quat, double *g_logit, double *g_col, double *g_res, double *g_aff,
+                            double *g_step)
 {
     ORec rec;
     OFwd f;
@@ -709,11 +739,27 @@ static void backprop_record(const OScene *s, int i, int d, double t, const OCam 
     g_logit[i] += glogit;
     for (int k = 0; k < nc; ++k) g_col[(size_t)nc * i + k] += gcol[k];
     for (int l = 1; l < d; ++l) {
+        double gv[64];     /* gradient of the decoded refinement components */
+        for (int k = 0; k < 3; ++k) { gv[k] = gmu[k]; gv[3 + k] = gls[k]; }
+        for (int k = 0; k < 4; ++k) gv[6 + k] = gq[k];
+        gv[10] = glogit;
+        for (int k = 0; k < nc; ++k) gv[11 + k] = gcol[k];
+        if (s->res_mode == 1) continue;      /* decoded symbols: no gradient */
         double *gr = g_res + ((size_t)(l - 1) * s->n + i) * K;
-        for (int k = 0; k < 3; ++k) { gr[k] += gmu[k]; gr[3 + k] += gls[k]; }
-        for (int k = 0; k < 4; ++k) gr[6 + k] += gq[k];
-        gr[10] += glogit;
-        for (int k = 0; k < nc; ++k) gr[11 + k] += gcol[k];
+        for (int k = 0; k < K; ++k) {
+            if (s->res_mode == 2) {
+                /* straight-through: the rounding passes the gradient, the clip stops it;
+                 * the step receives g (v - x / st) in range and g v when clipped */
+                int cl;
+                const float x = s->res[((size_t)(l - 1) * s->n + i) * K + k];
+                const float st = s->res_step[(size_t)(l - 1) * K + k];
+                const double v = quant_symbol(x, st, &cl);
+                if (!cl) gr[k] += gv[k];
+                if (g_step) g_step[(size_t)(l - 1) * K + k] += gv[k] * (cl ? v : v - (double)(x / st));
+            } else {
+                gr[k] += gv[k];
+            }
+        }
     }
 }
 
@@ -730,7 +776,8 @@ static void backprop_record(const OScene *s, int i, int d, double t, const OCam 
 int o_render_backward(const OScene *s, const uint8_t *depth, double t, const OCam *cam,
                       const double *bg, const double *dL_dimg,
                       double *g_mu0, double *g_u, double *g_ls, double *g_quat,
-                      double *g_logit, double *g_col, double *g_res, double *g2d_out, double *g_aff)
+                      double *g_logit, double *g_col, double *g_res, double *g2d_out, double *g_aff,
+                      double *g_step)
 {
     int m = 0;
     ORec *recs = project_sorted(s, depth, t, cam, &kDefaultEps, &m);
@@ -791,7 +838,8 @@ int o_render_backward(const OScene *s, const uint8_t *depth, double t, const OCa
         int i = r->idx;
         int c = 0;
         while (!(i >= s->cluster_offsets[c] && i < s->cluster_offsets[c + 1])) ++c;
-        backprop_record(s, i, depth[c], t, cam, &g2[k], g_mu0, g_u, g_ls, g_quat, g_logit, g_col, g_res, g_aff);
+        backprop_record(s, i, depth[c], t, cam, &g2[k], g_mu0, g_u, g_ls, g_quat, g_logit, g_col, g_res, g_aff,
+                        g_step);
         if (g2d_out) {
             double *o = g2d_out + (size_t)i * 9;
             o[0] += g2[k].mx; o[1] += g2[k].my; o[2] += g2[k].A; o[3] += g2[k].B; o[4] += g2[k].Cc;

@@ -35,7 +35,7 @@ __all__ = [
     "Scene", "Camera", "States", "Workload",
     "make_scene", "ring_camera", "prefix_states", "bernoulli_states",
     "erase_one_packet", "mask_words", "config", "CONFIG_NAMES", "MixSpec", "mix_specs", "mix_workload",
-    "completion_groups", "group_contexts", "cluster_affine",
+    "completion_groups", "group_contexts", "cluster_affine", "quantize_residuals",
 ]
 
 
@@ -55,6 +55,9 @@ class Scene:
     colour: np.ndarray           # f32 [n, 3*(sh+1)^2]
     res: np.ndarray              # f32 [L-1, n, K]
     affine: np.ndarray | None = None   # f32 [C, T, 12] cluster affine keyframes of Eq. 1 (None = identity)
+    res_q: np.ndarray | None = None    # i16 [L-1, n, K] quantized refinement symbols (res_mode 1)
+    res_step: np.ndarray | None = None  # f32 [L-1, K] quantization steps (res_mode 1 and 2)
+    res_mode: int = 0                  # 0: res as given; 1: res_q * res_step; 2: res quantized to res_step
 
     @property
     def n_colour(self) -> int:
@@ -80,7 +83,9 @@ class Scene:
                      self.u[:, idx].copy(), self.log_scale[idx].copy(),
                      self.quat[idx].copy(), self.opacity_logit[idx].copy(),
                      self.colour[idx].copy(), self.res[:, idx].copy(),
-                     None if self.affine is None else self.affine.copy())
+                     None if self.affine is None else self.affine.copy(),
+                     None if self.res_q is None else self.res_q[:, idx].copy(),
+                     None if self.res_step is None else self.res_step.copy(), self.res_mode)
 
     def arrays(self):
         return dict(mu0=self.mu0, u=self.u, log_scale=self.log_scale, quat=self.quat,
@@ -359,6 +364,19 @@ def cluster_affine(n_clusters: int, n_keyframes: int, rng: np.random.Generator, 
     A[..., :3] = np.eye(3) + rng.normal(0.0, linear_std, size=(n_clusters, n_keyframes, 3, 3))
     A[..., 3] = rng.normal(0.0, shift_std, size=(n_clusters, n_keyframes, 3))
     return A.reshape(n_clusters, n_keyframes, 12).astype(np.float32)
+
+
+def quantize_residuals(scene: Scene, step_scale: float = 1.0 / 256.0) -> tuple:
+    """Quantization steps and symbols for a scene's refinements: one step per
+    (layer, component), a power of two near step_scale times the component's
+    standard deviation, and the signed 16-bit symbols round(res / step).
+    Returns (res_q int16 [L-1, n, K], res_step float32 [L-1, K])."""
+    r = np.asarray(scene.res, np.float32)
+    sd = r.std(axis=1) + 1e-12
+    step = (2.0 ** np.round(np.log2(sd * step_scale))).astype(np.float32)
+    step[r.std(axis=1) == 0] = 1.0
+    q = np.clip(np.rint(r / step[:, None, :]), -32768, 32767).astype(np.int16)
+    return q, step
 
 
 CONFIG_NAMES = ("c1_plain_4k", "c2_dynamic_250k", "c3_fwdbwd_250k", "c4_utility_2p7m", "c5_mix_48")

@@ -729,3 +729,55 @@ def test_cluster_affine_gradient_finite_differences():
     assert checked >= 16 and excluded <= checked // 2, (checked, excluded)
     # keyframes the state's time does not touch get nothing
     assert np.all(g["affine"][:, 2] == 0.0)
+
+
+# ------------------------------------------------------------ quantized refinements
+def _quant_case():
+    import dataclasses
+    sc, cam = _fd_case(0)
+    q, step = synth.quantize_residuals(sc)
+    deq = (q.astype(np.float32) * step[:, None, :]).astype(np.float32)    # exact: steps are powers of two
+    return sc, cam, q, step, deq, dataclasses
+
+
+def test_quantized_refinement_decode_special_cases():
+    """Decoding symbols (mode 1) equals the float refinements q * step; fake
+    quantization (mode 2) equals rendering its dequantized values, and is the
+    identity on values already on the step grid."""
+    sc, cam, q, step, deq, dc = _quant_case()
+    D = np.array([sc.n_layers] * sc.n_clusters, np.uint8)
+    D[1] = 2
+    bg = np.zeros(3)
+    ref, _, _ = oracle.render(dc.replace(sc, res=deq), D, 0.4, cam, bg)
+    m1, _, _ = oracle.render(dc.replace(sc, res_q=q, res_step=step, res_mode=1), D, 0.4, cam, bg)
+    assert np.abs(m1 - ref).max() < 1e-12
+    m2grid, _, _ = oracle.render(dc.replace(sc, res=deq, res_step=step, res_mode=2), D, 0.4, cam, bg)
+    assert np.abs(m2grid - ref).max() < 1e-12
+    m2, _, _ = oracle.render(dc.replace(sc, res_step=step, res_mode=2), D, 0.4, cam, bg)
+    v = np.clip(np.rint(sc.res / step[:, None, :]), -32768, 32767)   # float32 division, as the definition
+    ref2, _, _ = oracle.render(dc.replace(sc, res=(v * step[:, None, :]).astype(np.float32)), D, 0.4, cam, bg)
+    assert np.abs(m2 - ref2).max() < 1e-12
+    assert np.abs(m2 - oracle.render(sc, D, 0.4, cam, bg)[0]).max() > 0     # the quantization shows
+
+
+def test_quantized_refinement_straight_through_gradients():
+    """Mode 2: the refinement gradient is the gradient at the dequantized values
+    (straight through the rounding), zero where the symbol clips; the step
+    gradient is the sum of g (v - x / step), or g v where clipped."""
+    sc, cam, q, step, deq, dc = _quant_case()
+    res = sc.res.copy()
+    res[0, 5, 11] = 40000.0 * step[0, 11]                   # clips at 32767
+    scq = dc.replace(sc, res=res, res_step=step, res_mode=2)
+    D = oracle.full_depth(sc)
+    rng = np.random.default_rng(6)
+    dL = rng.normal(size=(cam.height, cam.width, 3))
+    g2 = oracle.render_backward(scq, D, 0.4, cam, np.zeros(3), dL)
+    v = np.clip(np.rint(res / step[:, None, :]), -32768, 32767)
+    g0 = oracle.render_backward(dc.replace(sc, res=(v * step[:, None, :]).astype(np.float32)), D, 0.4, cam,
+                                np.zeros(3), dL)
+    clipped = np.abs(res / step[:, None, :]) > 32767.5
+    assert clipped.sum() == 1 and g2["res"][0, 5, 11] == 0.0
+    assert np.allclose(g2["res"][~clipped], g0["res"][~clipped], rtol=1e-12, atol=1e-15)
+    lsq = np.where(clipped, v, v - res / step[:, None, :])
+    assert np.allclose(g2["res_step"], (g0["res"] * lsq).sum(axis=1), rtol=1e-9, atol=1e-14)
+    assert np.abs(g2["res_step"]).max() > 0

@@ -89,6 +89,18 @@ typedef void *dgs_stream;     /* a cudaStream_t; NULL = the legacy default strea
  *                       (T = affine_T >= 1); between keyframes the twelve
  *                       entries are interpolated linearly, periodically in t
  *                       with period 1
+ *   res_mode            how refinements are read (Section 3: refinements are
+ *                       quantized with learned steps):
+ *                       0  res as given (float);
+ *                       1  res_q [L-1][n][K] int16 symbols times res_step
+ *                          [L-1][K] (one step per layer and component); res
+ *                          unused; no refinement gradient;
+ *                       2  res quantized on the fly: symbol v = round(res /
+ *                          res_step) (FP32 quotient, ties to even) clipped to
+ *                          [-32768, 32767], value v * step; gradients pass
+ *                          straight through the rounding (zero where clipped)
+ *                          and the step receives sum g (v - res / step), or
+ *                          g v where clipped
  * A Gaussian of cluster c at delivered depth d >= 1 renders with every
  * attribute = base + res[0] + ... + res[d-2]; at depth 0 it is absent.  Its
  * mean at time t is A_{c,t} mu0 + (position residuals) + sum_r b_r(t) u_r.
@@ -105,12 +117,16 @@ typedef struct {
     const float *res;
     const float *affine;              /* [device] [n_clusters][affine_T][12] or NULL */
     int32_t affine_T;
+    const int16_t *res_q;             /* [device] [L-1][n][K] (res_mode 1) */
+    const float *res_step;            /* [device] [L-1][K] (res_mode 1 and 2) */
+    int32_t res_mode;
 } dgs_scene;
 
 /* Gradients in the scene's layout, [device], ACCUMULATED (+=) by the backward. */
 typedef struct {
     float *mu0, *u, *log_scale, *quat, *opacity_logit, *colour, *res;
     float *affine;                    /* [n_clusters][affine_T][12]; needed when the scene has an affine */
+    float *res_step;                  /* [L-1][K]; needed with res_mode 2 */
 } dgs_scene_grad;
 
 /* OpenCV pinhole: p_cam = R_wc p_world + t_wc; x right, y down, z forward;

@@ -108,7 +108,7 @@ struct dgs_ctx {
     std::string err;
     Buf vgs, vgos, depth, need, counts, recBase, total, recs, k0, v0, k1, v1, tcount, toffs, ek0, ev0, ek1, ev1,
         ranges, sortws, scanws, partial, refs, recgrad, refidx, tck0, tcv0, tck1, tcv1, icnt, ioff, qint, counter,
-        pairm, grp, gmse, omaps, opart, otpart, oD, oweight, oints, recgmu;
+        pairm, grp, gmse, omaps, opart, otpart, oD, oweight, oints, recgmu, gqws;
     std::map<std::vector<long long>, int> tuned_G;   // autotuner: call shape -> states per block
     void *h_stage = nullptr;
     size_t h_stage_cap = 0;
@@ -190,10 +190,14 @@ int check_scene(dgs_ctx *ctx, const dgs_scene *s)
         if (!s->cluster_offsets || !s->mu0 || !s->log_scale || !s->quat || !s->opacity_logit || !s->colour)
             return fail(ctx, DGS_E_INVALID_ARG, "scene array is null");
         if (s->temporal_rank > 0 && !s->u) return fail(ctx, DGS_E_INVALID_ARG, "u is null");
-        if (s->n_layers > 1 && !s->res) return fail(ctx, DGS_E_INVALID_ARG, "res is null");
+        if (s->n_layers > 1 && s->res_mode != 1 && !s->res) return fail(ctx, DGS_E_INVALID_ARG, "res is null");
+        if (s->n_layers > 1 && s->res_mode == 1 && !s->res_q) return fail(ctx, DGS_E_INVALID_ARG, "res_q is null");
+        if (s->n_layers > 1 && s->res_mode != 0 && !s->res_step)
+            return fail(ctx, DGS_E_INVALID_ARG, "res_step is null");
         if (((uintptr_t)s->quat & 15u) != 0) return fail(ctx, DGS_E_INVALID_ARG, "quat must be 16-byte aligned");
     }
     if (s->affine && s->affine_T < 1) return fail(ctx, DGS_E_INVALID_ARG, "affine_T must be >= 1");
+    if (s->res_mode < 0 || s->res_mode > 2) return fail(ctx, DGS_E_INVALID_ARG, "res_mode must be 0, 1 or 2");
     return DGS_OK;
 }
 
@@ -206,6 +210,7 @@ SceneDev scene_dev(const dgs_scene *s)
     d.offs = s->cluster_offsets; d.mu0 = s->mu0; d.u = s->u; d.ls = s->log_scale; d.quat = s->quat;
     d.logit = s->opacity_logit; d.colour = s->colour; d.res = s->res;
     d.affine = s->affine; d.aT = s->affine ? s->affine_T : 0;
+    d.res_q = s->res_q; d.res_step = s->res_step; d.res_mode = s->res_mode;
     return d;
 }
 
@@ -702,7 +707,7 @@ void free_ctx_buffers(dgs_ctx *ctx)
                    &ctx->ev0, &ctx->ek1, &ctx->ev1, &ctx->ranges, &ctx->sortws, &ctx->scanws, &ctx->partial,
                    &ctx->refs, &ctx->recgrad, &ctx->refidx, &ctx->tck0, &ctx->tcv0, &ctx->tck1, &ctx->tcv1,
                    &ctx->icnt, &ctx->ioff, &ctx->qint, &ctx->counter, &ctx->pairm, &ctx->grp, &ctx->gmse, &ctx->omaps, &ctx->opart, &ctx->otpart,
-                   &ctx->oD, &ctx->oweight, &ctx->oints, &ctx->recgmu};
+                   &ctx->oD, &ctx->oweight, &ctx->oints, &ctx->recgmu, &ctx->gqws};
     for (Buf *b : bufs)
         if (b->p) { cudaFree(b->p); b->p = nullptr; b->cap = 0; }
     if (ctx->h_stage) { cudaFreeHost(ctx->h_stage); ctx->h_stage = nullptr; }
@@ -847,8 +852,9 @@ int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *
     if (p.S_user == 0 || scene->n == 0) return DGS_OK;
     if (!dL_dimages) return fail(ctx, DGS_E_INVALID_ARG, "dL_dimages is null");
     if (!grads->mu0 || !grads->log_scale || !grads->quat || !grads->opacity_logit || !grads->colour ||
-        (scene->temporal_rank > 0 && !grads->u) || (scene->n_layers > 1 && !grads->res) ||
-        (scene->affine && !grads->affine))
+        (scene->temporal_rank > 0 && !grads->u) ||
+        (scene->n_layers > 1 && scene->res_mode != 1 && !grads->res) || (scene->affine && !grads->affine) ||
+        (scene->n_layers > 1 && scene->res_mode == 2 && !grads->res_step))
         return fail(ctx, DGS_E_INVALID_ARG, "gradient array is null");
     Lists L;
     if (same_call(ctx->tape, scene, states, cams, n_cams)) {
@@ -871,9 +877,15 @@ int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *
     g.mu0 = grads->mu0; g.u = grads->u; g.ls = grads->log_scale; g.quat = grads->quat;
     g.logit = grads->opacity_logit; g.colour = grads->colour; g.res = grads->res;
     g.affine = grads->affine; g.rec_gmu = nullptr;
+    g.res_step = grads->res_step; g.gq = nullptr;
     if (scene->affine) {
         TRY(ensure(ctx, ctx->recgmu, sizeof(float) * 3 * ((size_t)nRec + 1), st));
         g.rec_gmu = (float *)ctx->recgmu.p;
+    }
+    if (scene->res_mode == 2 && scene->n_layers > 1) {
+        const SceneDev sdv = scene_dev(scene);
+        TRY(ensure(ctx, ctx->gqws, sizeof(float) * (size_t)(scene->n_layers - 1) * scene->n * sdv.K, st));
+        g.gq = (float *)ctx->gqws.p;
     }
     launch_project_bwd(scene_dev(scene), (const ViewGroup *)ctx->vgs.p, p.V, (const uint32_t *)ctx->need.p,
                        (const uint32_t *)ctx->recBase.p, (const float4 *)ctx->recgrad.p, g, nRec, ctx->sms, st);
@@ -1219,6 +1231,9 @@ int dgs_plan_create(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *stat
         if (mode == DGS_PLAN_RENDER && (r = ensure(w, w->recgrad, sizeof(float4) * 3 * R, st)) != DGS_OK) break;
         if (mode == DGS_PLAN_RENDER && scene->affine &&
             (r = ensure(w, w->recgmu, sizeof(float) * 3 * (R + 1), st)) != DGS_OK) break;
+        if (mode == DGS_PLAN_RENDER && scene->res_mode == 2 && scene->n_layers > 1 &&
+            (r = ensure(w, w->gqws, sizeof(float) * (size_t)(scene->n_layers - 1) * scene->n * scene_dev(scene).K,
+                        st)) != DGS_OK) break;
         const size_t img = (size_t)p.W * p.H * 3;
         if (mode == DGS_PLAN_UTILITY) {
             if ((r = ensure(w, w->refs, sizeof(float) * img * p.V, st)) != DGS_OK) break;
@@ -1328,8 +1343,9 @@ int dgs_plan_backward(dgs_plan *P, const float *images, const float *dL_dimages,
     if (!dL_dimages || !grads) return plan_fail(P, DGS_E_INVALID_ARG, "dL_dimages or grads is null");
     const dgs_scene *scene = &P->scene;
     if (!grads->mu0 || !grads->log_scale || !grads->quat || !grads->opacity_logit || !grads->colour ||
-        (scene->temporal_rank > 0 && !grads->u) || (scene->n_layers > 1 && !grads->res) ||
-        (scene->affine && !grads->affine))
+        (scene->temporal_rank > 0 && !grads->u) ||
+        (scene->n_layers > 1 && scene->res_mode != 1 && !grads->res) || (scene->affine && !grads->affine) ||
+        (scene->n_layers > 1 && scene->res_mode == 2 && !grads->res_step))
         return plan_fail(P, DGS_E_INVALID_ARG, "gradient array is null");
     dgs_ctx *ctx = P->sc;
     CK(cudaSetDevice(P->ws.device));
@@ -1345,6 +1361,7 @@ int dgs_plan_backward(dgs_plan *P, const float *images, const float *dL_dimages,
     g.mu0 = grads->mu0; g.u = grads->u; g.ls = grads->log_scale; g.quat = grads->quat;
     g.logit = grads->opacity_logit; g.colour = grads->colour; g.res = grads->res;
     g.affine = grads->affine; g.rec_gmu = scene->affine ? (float *)ctx->recgmu.p : nullptr;
+    g.res_step = grads->res_step; g.gq = scene->res_mode == 2 ? (float *)ctx->gqws.p : nullptr;
     launch_project_bwd(scene_dev(scene), (const ViewGroup *)P->ws.vgs.p, P->p.V, (const uint32_t *)ctx->need.p,
                        (const uint32_t *)ctx->recBase.p, (const float4 *)ctx->recgrad.p, g, P->R_cap, ctx->sms, st);
     CK(cudaGetLastError());

@@ -103,8 +103,11 @@ __global__ void __launch_bounds__(128) k_project_bwd(SceneDev s, const ViewGroup
             if (!any) continue;
             // acc now sums the variants of depth >= d
             float *dst;
-            if (d >= 2) {
-                dst = g.res + ((size_t)(d - 2) * s.n + i) * K;
+            if (d >= 2 && s.res_mode == 1) {
+                // decoded symbols: no refinement gradient
+            } else if (d >= 2) {
+                // res_mode 2: the decoded-refinement gradient goes to the workspace for k_quant_grad
+                dst = (s.res_mode == 2 ? g.gq : g.res) + ((size_t)(d - 2) * s.n + i) * K;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) { dst[k] += acc.mu[k]; dst[3 + k] += acc.ls[k]; }
 #pragma unroll
@@ -131,6 +134,42 @@ __global__ void __launch_bounds__(128) k_project_bwd(SceneDev s, const ViewGroup
                 for (int k = 0; k < 3; ++k) g.u[((size_t)r * s.n + i) * 3 + k] += gu[r][k];
         }
     }
+}
+
+// Quantized refinements (res_mode 2): straight-through gradient to the float
+// refinements (zero where the symbol clips) and the learned-step gradient
+// sum_i g (v - x / step) (g v where clipped), block-reduced per component.
+// One block per (layer, 256 Gaussians); component sums via shared memory.
+__global__ void __launch_bounds__(256) k_quant_grad(SceneDev s, const float *__restrict__ gq, float *__restrict__ g_res,
+                                                    float *__restrict__ g_step)
+{
+    __shared__ float part[64];
+    const int blocks_per_layer = (s.n + 255) / 256;
+    const int l = blockIdx.x / blocks_per_layer;             // 0-based refinement layer
+    const int i = (blockIdx.x % blocks_per_layer) * 256 + threadIdx.x;
+    for (int k = threadIdx.x; k < s.K; k += blockDim.x) part[k] = 0.0f;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < s.K; ++k) {
+        float c = 0.0f;
+        if (i < s.n) {
+            const size_t o = ((size_t)l * s.n + i) * s.K + k;
+            const float gv = gq[o];
+            if (gv != 0.0f) {
+                const float x = s.res[o], st = s.res_step[(size_t)l * s.K + k];
+                bool cl;
+                const float v = quant_symbol(x, st, cl);
+                if (!cl) g_res[o] += gv;
+                c = gv * (cl ? v : v - __fdiv_rn(x, st));
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+        if (lane == 0 && c != 0.0f) atomicAdd(&part[k], c);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < s.K; k += blockDim.x)
+        if (part[k] != 0.0f) atomicAdd(g_step + (size_t)l * s.K + k, part[k]);
 }
 
 // Keyframe gradients of the cluster affine: one block per (view group v,
@@ -190,12 +229,18 @@ void launch_project_bwd(const SceneDev &s, const ViewGroup *vgs, int V, const ui
 {
     if (s.n == 0) return;
     if (s.affine && rec_cap) cudaMemsetAsync(g.rec_gmu, 0, sizeof(float) * 3 * rec_cap, st);
+    if (s.res_mode == 2 && s.L > 1) cudaMemsetAsync(g.gq, 0, sizeof(float) * (size_t)(s.L - 1) * s.n * s.K, st);
     long long b = (s.n + 127) / 128;
     if (b > (long long)sms * 32) b = (long long)sms * 32;
     {
         ProfScope ps_("project_bwd", st);
         if (s.sh == 0) k_project_bwd<0><<<(unsigned)b, 128, 0, st>>>(s, vgs, V, need, recBase, rec_grad, g);
         else k_project_bwd<3><<<(unsigned)b, 128, 0, st>>>(s, vgs, V, need, recBase, rec_grad, g);
+        count_launch();
+    }
+    if (s.res_mode == 2 && s.L > 1) {
+        ProfScope ps_("quant_grad", st);
+        k_quant_grad<<<(unsigned)((s.L - 1) * ((s.n + 255) / 256)), 256, 0, st>>>(s, g.gq, g.res, g.res_step);
         count_launch();
     }
     if (s.affine && V > 0) {

@@ -62,11 +62,16 @@ struct SceneDev {
     const float *mu0, *u, *ls, *quat, *logit, *colour, *res;
     const float *affine;       // [C][aT][12] cluster affine keyframes, or null (identity)
     int aT;
+    const int16_t *res_q;      // [L-1][n][K] refinement symbols (res_mode 1)
+    const float *res_step;     // [L-1][K] quantization steps (res_mode 1, 2)
+    int res_mode;              // 0 float refinements, 1 symbols x step, 2 quantized on the fly
 };
 
 struct GradDev {
     float *mu0, *u, *ls, *quat, *logit, *colour, *res, *affine;
     float *rec_gmu;            // [nRec][3] per-record mean gradient (only with an affine)
+    float *res_step;           // [L-1][K] step gradients (res_mode 2)
+    float *gq;                 // [L-1][n][K] gradients of the decoded refinements (res_mode 2 workspace)
 };
 
 // ------------------------------------------------------------------ MSE

@@ -36,12 +36,42 @@ __device__ __forceinline__ void load_base(const SceneDev &s, int i, Attr<SH> &a)
     for (int k = 0; k < NC; ++k) a.col[k] = __ldg(s.colour + (size_t)NC * i + k);
 }
 
+// Symbol of a refinement value x quantized to step st (the learned steps of
+// Section 3): round(x / st) (IEEE FP32 quotient, ties to even) clipped to the
+// signed 16-bit range.
+__device__ __forceinline__ float quant_symbol(float x, float st, bool &clipped)
+{
+    float v = rintf(__fdiv_rn(x, st));
+    clipped = v > 32767.0f || v < -32768.0f;
+    return fminf(fmaxf(v, -32768.0f), 32767.0f);
+}
+
+// Component k of refinement layer l (1-based) of Gaussian i as decoded (res_mode 1, 2).
+__device__ __forceinline__ float res_value(const SceneDev &s, int l, int i, int k)
+{
+    const size_t o = ((size_t)(l - 1) * s.n + i) * s.K + k;
+    const float st = __ldg(s.res_step + (size_t)(l - 1) * s.K + k);
+    if (s.res_mode == 1) return __fmul_rn((float)__ldg(s.res_q + o), st);
+    bool cl;
+    return __fmul_rn(quant_symbol(__ldg(s.res + o), st, cl), st);
+}
+
 // attribute += refinement layer l (1-based) of Gaussian i, in a fixed order
 template <int SH>
 __device__ __forceinline__ void add_layer(const SceneDev &s, int i, int l, Attr<SH> &a)
 {
     constexpr int NC = NCol<SH>::value;
     constexpr int K = 11 + NC;
+    if (s.res_mode != 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { a.mu[k] += res_value(s, l, i, k); a.ls[k] += res_value(s, l, i, 3 + k); }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a.q[k] += res_value(s, l, i, 6 + k);
+        a.logit += res_value(s, l, i, 10);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) a.col[k] += res_value(s, l, i, 11 + k);
+        return;
+    }
     const float *r = s.res + ((size_t)(l - 1) * s.n + i) * K;
 #pragma unroll
     for (int k = 0; k < 3; ++k) { a.mu[k] += __ldg(r + k); a.ls[k] += __ldg(r + 3 + k); }

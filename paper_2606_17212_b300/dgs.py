@@ -28,7 +28,8 @@ class Scene_t(ctypes.Structure):
                 ("cluster_offsets", ctypes.c_void_p), ("mu0", ctypes.c_void_p), ("u", ctypes.c_void_p),
                 ("log_scale", ctypes.c_void_p), ("quat", ctypes.c_void_p),
                 ("opacity_logit", ctypes.c_void_p), ("colour", ctypes.c_void_p), ("res", ctypes.c_void_p),
-                ("affine", ctypes.c_void_p), ("affine_T", ctypes.c_int32)]
+                ("affine", ctypes.c_void_p), ("affine_T", ctypes.c_int32),
+                ("res_q", ctypes.c_void_p), ("res_step", ctypes.c_void_p), ("res_mode", ctypes.c_int32)]
 
 
 OBJECTIVE_KEYS = ("ssim_weight", "lambda_c", "cvar_q", "lambda_t", "lambda_m", "anchor_weight")
@@ -42,7 +43,7 @@ class ObjectiveParams_t(ctypes.Structure):
 
 class SceneGrad_t(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in
-                ("mu0", "u", "log_scale", "quat", "opacity_logit", "colour", "res", "affine")]
+                ("mu0", "u", "log_scale", "quat", "opacity_logit", "colour", "res", "affine", "res_step")]
 
 
 class Camera_t(ctypes.Structure):
@@ -154,19 +155,28 @@ SCENE_FIELDS = ("mu0", "u", "log_scale", "quat", "opacity_logit", "colour", "res
 
 def _grad_struct(grads: dict) -> SceneGrad_t:
     ptrs = [(_ptr(grads[k]) if grads[k].numel() else None) for k in SCENE_FIELDS]
-    return SceneGrad_t(*ptrs, _ptr(grads.get("affine")))
+    return SceneGrad_t(*ptrs, _ptr(grads.get("affine")), _ptr(grads.get("res_step")))
 
 
 class DeviceScene:
     """Scene tensors resident on a CUDA device, with the C struct that points at them."""
 
     def __init__(self, tensors: dict, n, n_clusters, n_layers, sh_degree, temporal_rank, cluster_offsets,
-                 affine=None):
+                 affine=None, res_q=None, res_step=None, res_mode=0):
         import torch
         self.t = {k: tensors[k].contiguous() for k in SCENE_FIELDS}
         # optional cluster affine keyframes of Eq. 1 [C, T, 12] (None = identity)
         if affine is not None:
             self.t["affine"] = affine.contiguous()
+        # quantized refinements: res_mode 1 reads int16 symbols res_q times res_step,
+        # res_mode 2 quantizes res to res_step on the fly (res_step then has a gradient)
+        self.res_mode = int(res_mode)
+        self.res_q = None if res_q is None else res_q.contiguous()
+        if res_step is not None:
+            if self.res_mode == 2:
+                self.t["res_step"] = res_step.contiguous()
+            else:
+                self.res_step = res_step.contiguous()
         self.offsets = cluster_offsets.to(torch.int32).contiguous()
         self.n, self.n_clusters, self.n_layers = int(n), int(n_clusters), int(n_layers)
         self.sh_degree, self.temporal_rank = int(sh_degree), int(temporal_rank)
@@ -179,21 +189,25 @@ class DeviceScene:
         offs = torch.from_numpy(np.asarray(scene.cluster_offsets, np.int32)).to(device)
         aff = getattr(scene, "affine", None)
         aff = None if aff is None else torch.from_numpy(np.ascontiguousarray(aff, np.float32)).to(device)
+        mode = int(getattr(scene, "res_mode", 0))
+        rq = None if mode != 1 else torch.from_numpy(np.ascontiguousarray(scene.res_q, np.int16)).to(device)
+        rs = None if mode == 0 else torch.from_numpy(np.ascontiguousarray(scene.res_step, np.float32)).to(device)
         return cls(ts, scene.n, scene.n_clusters, scene.n_layers, scene.sh_degree, scene.temporal_rank, offs,
-                   affine=aff)
+                   affine=aff, res_q=rq, res_step=rs, res_mode=mode)
 
     @property
     def fields(self):
-        """The differentiable tensors: SCENE_FIELDS, plus "affine" when present."""
-        return SCENE_FIELDS + (("affine",) if "affine" in self.t else ())
+        """The differentiable tensors: SCENE_FIELDS, plus "affine" and "res_step" when present."""
+        return SCENE_FIELDS + tuple(k for k in ("affine", "res_step") if k in self.t)
 
     def struct(self) -> Scene_t:
         g = lambda k: _ptr(self.t[k]) if self.t[k].numel() else None
         aff = self.t.get("affine")
+        step = self.t.get("res_step", getattr(self, "res_step", None))
         return Scene_t(self.n, self.n_clusters, self.n_layers, self.sh_degree, self.temporal_rank,
                        _ptr(self.offsets), g("mu0"), g("u"), g("log_scale"), g("quat"),
                        g("opacity_logit"), g("colour"), g("res"), _ptr(aff),
-                       0 if aff is None else int(aff.shape[1]))
+                       0 if aff is None else int(aff.shape[1]), _ptr(self.res_q), _ptr(step), self.res_mode)
 
     def zeros_like_grads(self) -> dict:
         import torch

@@ -535,3 +535,43 @@ def test_cluster_affine_matches_oracle_forward_backward_and_plan(R, torch):
         if grads[k].numel():
             assert torch.allclose(gp[k], grads[k], rtol=1e-4, atol=1e-5 * float(grads[k].abs().max()) + 1e-12), k
     plan.close()
+
+
+# --------------------------------------------------------------------- quantized refinements
+@pytest.mark.parametrize("mode", [1, 2])
+def test_quantized_refinements_match_oracle(R, torch, mode):
+    """Refinements read as int16 symbols times learned steps (mode 1) or
+    quantized on the fly with straight-through gradients (mode 2): images
+    against the oracle on non-marginal pixels and the adjoint (refinements
+    and steps) against the oracle's."""
+    import dataclasses
+    sc_h, states, cams = _grad_case()
+    q, step = synth.quantize_residuals(sc_h, step_scale=1.0 / 16.0)      # coarse: the quantization shows
+    scq = dataclasses.replace(sc_h, res_q=q, res_step=step, res_mode=mode)
+    bg = np.array([0.1, 0.2, 0.3], np.float32)
+    sc = dgs.DeviceScene.from_host(scq)
+    st = dgs.DeviceStates.from_host(states)
+    imgs = R.render_states_batched(sc, st, cams, bg)
+    D = oracle.state_depths(states, scq.n_clusters, scq.n_layers)
+    rng = np.random.default_rng(4)
+    S, H, W = states.n, cams[0].height, cams[0].width
+    dL = rng.normal(size=(S, H, W, 3))
+    ref = None
+    for s in range(S):
+        cam = cams[int(states.cam[s])]
+        img_o, marg, _ = oracle.render(scq, D[s], float(states.t[s]), cam, bg)
+        err = np.abs(imgs[s].cpu().numpy().astype(np.float64) - img_o)[~marg]
+        assert err.max() <= IMG_TOL, (s, err.max())
+        dL[s][marg] = 0.0
+        g = oracle.render_backward(scq, D[s], float(states.t[s]), cam, bg, dL[s])
+        ref = g if ref is None else {k: ref[k] + g[k] for k in ref}
+    grads = R.render_backward(sc, st, cams, bg, torch.from_numpy(dL.astype(np.float32)).cuda(), images=imgs)
+    if mode == 2:
+        assert "res_step" in sc.fields and float(np.abs(ref["res_step"]).max()) > 0
+    for k in sc.fields:
+        gg = grads[k].cpu().numpy().astype(np.float64)
+        gr = ref[k]
+        if gr.size == 0:
+            continue
+        scale = max(np.abs(gr).max(), 1e-6)
+        assert np.abs(gg - gr).max() <= GRAD_TOL * scale, (mode, k, np.abs(gg - gr).max(), scale)

@@ -1,0 +1,108 @@
+"""The oracle's pins must catch plausible mistakes in the oracle.
+
+Each case plants one mistake (a dropped term, a wrong sign, a swapped index or
+constant) in a copy of the oracle on the CPU, rebuilds the copy and runs the
+pin suite against it; the suite must fail.  The real oracle is never touched.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+C = "oracle/dgs_oracle.c"
+PY = "oracle/__init__.py"
+
+# (name, file, text as it stands, planted mistake); the text occurs once.
+MUTATIONS = [
+    ("dilation dropped (Section 7.4 low-pass)", C,
+     "f->a2 = S2[0] + 0.3; f->b2 = S2[1]; f->c2 = S2[3] + 0.3;",
+     "f->a2 = S2[0]; f->b2 = S2[1]; f->c2 = S2[3];"),
+    ("sign of the conic cross term", C,
+     "        double pw = -0.5 * (r->A * dx * dx + r->Cc * dy * dy) - r->B * dx * dy;\n"
+     "        double pmag",
+     "        double pw = -0.5 * (r->A * dx * dx + r->Cc * dy * dy) + r->B * dx * dy;\n"
+     "        double pmag"),
+    ("transmittance dropped from compositing (Eq. 3 render)", C,
+     "for (int ch = 0; ch < 3; ++ch) C[ch] += r->rgb[ch] * alpha * T;",
+     "for (int ch = 0; ch < 3; ++ch) C[ch] += r->rgb[ch] * alpha;"),
+    ("early-stop threshold", C,
+     "        if (Tn < 1e-4) break;\n        for (int ch = 0; ch < 3; ++ch) C[ch]",
+     "        if (Tn < 1e-3) break;\n        for (int ch = 0; ch < 3; ++ch) C[ch]"),
+    ("cos and sin of the temporal basis swapped (Eq. 1)", C,
+     "(k % 2 == 0) ? cos(", "(k % 2 == 1) ? cos("),
+    ("closure ignores a missing layer (Section 4)", C,
+     "if (!((mask[b >> 5] >> (b & 31)) & 1u)) break;",
+     "if (!((mask[b >> 5] >> (b & 31)) & 1u)) { ++d; continue; }"),
+    ("refinement layers off by one (Section 3)", C,
+     "    for (int l = 1; l < d; ++l) {\n        for (int k = 0; k < 3; ++k) { a->mu[k]",
+     "    for (int l = 1; l <= d && l < s->n_layers; ++l) {\n        for (int k = 0; k < 3; ++k) { a->mu[k]"),
+    ("opacity adjoint misses the Gaussian factor", C,
+     "g->o += galpha * ex[q];", "g->o += galpha;"),
+    ("suffix term of the alpha adjoint not divided by (1 - alpha)", C,
+     "galpha += gC[ch] * (r->rgb[ch] * T_q - suffix[ch] / (1.0 - alpha));",
+     "galpha += gC[ch] * (r->rgb[ch] * T_q - suffix[ch]);"),
+    ("sign of the cross term in the mean adjoint", C,
+     "g->mx += gpw * (-(r->A * dx + r->B * dy));", "g->mx += gpw * (-(r->A * dx - r->B * dy));"),
+    ("sigmoid derivative truncated", C,
+     "double glogit = g->o * rec.o * (1.0 - rec.o);", "double glogit = g->o * rec.o;"),
+    ("straight-through gradient ignores clipping", C,
+     "if (!cl) gr[k] += gv[k];", "gr[k] += gv[k];"),
+    ("affine interpolation weights swapped (Eq. 1)", C,
+     "A[k] = (1.0 - *w) * a0[k] + *w * a1[k];", "A[k] = *w * a0[k] + (1.0 - *w) * a1[k];"),
+    ("quantized decode uses the wrong step index", C,
+     "return (double)s->res_q[o] * (double)s->res_step[(size_t)(l - 1) * K + k];",
+     "return (double)s->res_q[o] * (double)s->res_step[(size_t)(l - 1) * K];"),
+    ("SSIM constants swapped in the structure term", PY,
+     "a1, a2 = 2 * mx * my + SSIM_C1, 2 * sxy + SSIM_C2",
+     "a1, a2 = 2 * mx * my + SSIM_C1, 2 * sxy + SSIM_C1"),
+    ("SSIM window sigma", PY,
+     "def ssim_window(size: int = 11, sigma: float = 1.5)",
+     "def ssim_window(size: int = 11, sigma: float = 1.0)"),
+    ("sample instead of population standard deviation (Eq. 4)", PY,
+     "std = float(np.sqrt(np.mean((x - mean) ** 2)))",
+     "std = float(np.sqrt(np.sum((x - mean) ** 2) / max(x.size - 1, 1)))"),
+    ("quantile position q M instead of q (M - 1) (Eq. 4)", PY,
+     "h = q * (x.size - 1)", "h = min(q * x.size, x.size - 1)"),
+    ("CVaR over the lower tail (Eq. 2)", PY,
+     "top = np.argsort(-D, kind=\"stable\")[:k]", "top = np.argsort(D, kind=\"stable\")[:k]"),
+    ("prefix hinge with the wrong orientation (Eq. 2)", PY,
+     "            if D[j] > D[i]:\n                M += (D[j] - D[i]) / len(pairs_m)",
+     "            if D[i] > D[j]:\n                M += (D[i] - D[j]) / len(pairs_m)"),
+    ("temporal-change gradient sign (Eq. 2)", PY,
+     "            grad[j] += gf\n            grad[i] -= gf",
+     "            grad[j] -= gf\n            grad[i] += gf"),
+]
+
+
+def _copy_tree(dst):
+    ign = shutil.ignore_patterns("*.so", "*.so.tmp*", "__pycache__", "csrc", "_build*")
+    for d in ("oracle", "tests", "paper_2606_17212_b300"):
+        shutil.copytree(os.path.join(ROOT, d), os.path.join(dst, d), ignore=ign)
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), dst)
+
+
+def test_mutation_sites_exist():
+    for name, path, old, _ in MUTATIONS:
+        with open(os.path.join(ROOT, path)) as f:
+            assert f.read().count(old) == 1, name
+
+
+@pytest.mark.parametrize("name,path,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(tmp_path, name, path, old, new):
+    _copy_tree(str(tmp_path))
+    p = os.path.join(str(tmp_path), path)
+    with open(p) as f:
+        text = f.read()
+    assert text.count(old) == 1, name
+    with open(p, "w") as f:
+        f.write(text.replace(old, new))
+    env = dict(os.environ, OMP_NUM_THREADS=os.environ.get("OMP_NUM_THREADS", "8"))
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-x", "-q",
+                        "-p", "no:randomly"], cwd=str(tmp_path), env=env,
+                       stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True, timeout=600)
+    tail = r.stdout.strip().splitlines()[-3:]
+    assert r.returncode == 1 and " failed" in r.stdout, (name, r.returncode, tail)

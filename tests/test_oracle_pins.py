@@ -5,6 +5,7 @@ closed form, a brute-force restatement, an invariant of the paper's
 delivery-state semantics, or central finite differences.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -115,6 +116,20 @@ def test_two_gaussians_on_one_ray_closed_form():
     c2 = np.array(c_far, np.float32).astype(float)
     expect = a1 * c1 + (1 - a1) * a2 * c2 + (1 - a1) * (1 - a2) * bg
     assert np.allclose(img[64, 64], expect, atol=1e-12)
+
+
+def test_early_stop_after_thirteen_halvings():
+    """Reading S13: a pixel stops before the Gaussian that would take T (1 - alpha)
+    below 1e-4.  Twenty Gaussians with alpha = 1/2 on one ray: 2^-13 >= 1e-4 > 2^-14,
+    so exactly 13 composite and the background enters with T = 2^-13."""
+    zs = np.linspace(2.0, 3.9, 20)
+    mu = [[4.0 - z, z / 256.0, -z / 256.0] for z in zs]
+    col = 0.25
+    sc = tiny_scene(mu, [[-3.0] * 3] * 20, [[1, 0, 0, 0]] * 20, [0.0] * 20, [[col] * 3] * 20)
+    bg = np.array([1.0, 0.5, 0.0])
+    img, marg, _ = oracle.render(sc, np.array([1], np.uint8), 0.0, axis_camera(), bg)
+    T = 2.0 ** -13
+    assert np.allclose(img[64, 64], col * (1 - T) + T * bg, rtol=0, atol=1e-9)
 
 
 def test_on_axis_covariance_and_radius_closed_form():
@@ -781,3 +796,54 @@ def test_quantized_refinement_straight_through_gradients():
     lsq = np.where(clipped, v, v - res / step[:, None, :])
     assert np.allclose(g2["res_step"], (g0["res"] * lsq).sum(axis=1), rtol=1e-9, atol=1e-14)
     assert np.abs(g2["res_step"]).max() > 0
+
+
+def test_ssim_value_by_direct_window_sums():
+    """SSIM at interior pixels from direct 2-D window sums (C1 = 1e-4, C2 = 9e-4)
+    on an anti-correlated pair, where both constants matter."""
+    rng = np.random.default_rng(12)
+    y = rng.uniform(size=(24, 26, 3))
+    x = 0.9 - 0.8 * y + 0.05 * rng.normal(size=y.shape)
+    f = oracle.ssim(x, y, want_grad="map")
+    a = np.arange(11) - 5.0
+    w2 = np.exp(-(a[:, None] ** 2 + a[None, :] ** 2) / (2 * 1.5 ** 2))
+    w2 /= w2.sum()
+    for r, c in [(5, 5), (12, 13), (18, 20)]:
+        for ch in range(3):
+            px, py = x[r - 5:r + 6, c - 5:c + 6, ch], y[r - 5:r + 6, c - 5:c + 6, ch]
+            mx, my = (w2 * px).sum(), (w2 * py).sum()
+            sxx = (w2 * px * px).sum() - mx * mx
+            syy = (w2 * py * py).sum() - my * my
+            sxy = (w2 * px * py).sum() - mx * my
+            exp = ((2 * mx * my + 1e-4) * (2 * sxy + 9e-4)) / ((mx * mx + my * my + 1e-4) * (sxx + syy + 9e-4))
+            assert f[r, c, ch] == pytest.approx(exp, rel=1e-12), (r, c, ch)
+
+
+def _golden_weights():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "locked_weights.txt")
+    out = {}
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()[:2]
+                out[k] = float(v)
+    return out
+
+
+def test_locked_weights_are_the_papers():
+    """The defaults of the oracle and of the binding are the weights the paper fixes
+    (Eq. 2 and Eq. 4); the rate weight is 0, so the objective has no rate term."""
+    import inspect
+    from paper_2606_17212_b300 import dgs
+    w = _golden_weights()
+    assert w["lambda_r"] == 0.0
+    obj = inspect.signature(oracle.objective).parameters
+    for k in ("ssim_weight", "lambda_c", "cvar_q", "lambda_t", "lambda_m", "anchor_weight"):
+        assert obj[k].default == w[k], k
+        assert dgs.OBJECTIVE_DEFAULTS[k] == w[k], k
+    for sig in (inspect.signature(oracle.utility_stats).parameters,
+                inspect.signature(oracle.group_utility).parameters,
+                inspect.signature(dgs.Renderer.group_utility).parameters):
+        assert (sig["alpha"].default, sig["beta"].default, sig["q"].default) == \
+            (w["utility_alpha"], w["utility_beta"], w["utility_q"])
+    assert (oracle.SSIM_C1, oracle.SSIM_C2) == pytest.approx((w["ssim_c1"], w["ssim_c2"]), rel=1e-15)

@@ -106,7 +106,7 @@ struct dgs_ctx {
     int device = 0;
     int sms = 148;
     std::string err;
-    Buf vgs, vgos, depth, need, counts, recBase, total, recs, k0, v0, k1, v1, tcount, toffs, ek0, ev0, ek1, ev1,
+    Buf vgs, vgos, depth, need, counts, recBase, total, recs, k0, v0, k1, v1, tcount, toffs, bins, ek0, ev0, ek1, ev1,
         ranges, sortws, scanws, partial, refs, recgrad, refidx, tck0, tcv0, tck1, tcv1, icnt, ioff, qint, counter,
         pairm, grp, gmse, omaps, opart, otpart, oD, oweight, oints, recgmu, gqws;
     std::map<std::vector<long long>, int> tuned_G;   // autotuner: call shape -> states per block
@@ -335,6 +335,7 @@ int prepare(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *masks, const P
     TRY(ensure(ctx, ctx->k1, 4 * (size_t)nRec, st));
     TRY(ensure(ctx, ctx->v1, 4 * (size_t)nRec, st));
     TRY(ensure(ctx, ctx->tcount, 4 * ((size_t)nRec + 1), st));
+    TRY(ensure(ctx, ctx->bins, sizeof(uint4) * ((size_t)nRec + 1), st));
     TRY(ensure(ctx, ctx->toffs, 4 * ((size_t)nRec + 1), st));
     TRY(ensure(ctx, ctx->sortws, radix_workspace_bytes(nRec), st));
     TRY(ensure(ctx, ctx->scanws, scan_workspace_bytes((size_t)nRec + 1), st));
@@ -349,7 +350,9 @@ int prepare(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *masks, const P
     const uint32_t *order = alt ? (const uint32_t *)ctx->v1.p : (const uint32_t *)ctx->v0.p;
     out.depth_keys = alt ? (uint32_t *)ctx->k1.p : (uint32_t *)ctx->k0.p;
     out.depth_slots = (uint32_t *)order;
-    if (nRec > 0) launch_tile_count((const Rec *)ctx->recs.p, order, nRec, (uint32_t *)ctx->tcount.p, ctx->sms, st);
+    if (nRec > 0)
+        launch_tile_count((const Rec *)ctx->recs.p, order, nRec, p.tiles_x, p.tiles, (uint32_t *)ctx->tcount.p,
+                          (uint4 *)ctx->bins.p, ctx->sms, st);
     CK(exclusive_scan_u32((const uint32_t *)ctx->tcount.p, (uint32_t *)ctx->toffs.p, nRec,
                           (uint32_t *)ctx->total.p + 1, ctx->scanws.p, st));
     CK(cudaMemcpyAsync(ctx->h_small + 1, (uint32_t *)ctx->total.p + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -362,12 +365,11 @@ int prepare(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *masks, const P
     TRY(ensure(ctx, ctx->ev1, 4 * (size_t)nEnt, st));
     TRY(ensure(ctx, ctx->sortws, radix_workspace_bytes(nEnt), st));
     TRY(ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)p.V * p.tiles, st));
-    if (nEnt > 0)
-        launch_emit((const Rec *)ctx->recs.p, order, (const uint32_t *)ctx->toffs.p, nRec, p.tiles_x, p.tiles,
-                    (uint32_t *)ctx->ek0.p, (uint32_t *)ctx->ev0.p, ctx->sms, st);
     const int kbits = bits_for((unsigned long long)p.V * p.tiles - 1ull);
-    CK(radix_sort_pairs((uint32_t *)ctx->ek0.p, (uint32_t *)ctx->ev0.p, (uint32_t *)ctx->ek1.p,
-                        (uint32_t *)ctx->ev1.p, nEnt, kbits, ctx->sortws.p, st, &alt));
+    CK(radix_sort_entries((const uint4 *)ctx->bins.p, (const uint32_t *)ctx->toffs.p, (const uint32_t *)ctx->tcount.p,
+                          nRec, nullptr, p.tiles_x, (uint32_t *)ctx->ek0.p, (uint32_t *)ctx->ev0.p,
+                          (uint32_t *)ctx->ek1.p, (uint32_t *)ctx->ev1.p, nEnt, nullptr, kbits, ctx->sortws.p, st,
+                          &alt, ctx->sms));
     uint32_t *ekeys = alt ? (uint32_t *)ctx->ek1.p : (uint32_t *)ctx->ek0.p;
     out.ekeys = ekeys;
     out.evals = alt ? (uint32_t *)ctx->ev1.p : (uint32_t *)ctx->ev0.p;
@@ -652,15 +654,16 @@ int prepare_dev(dgs_plan *P, const uint32_t *masks, bool force_full, cudaStream_
     Lists &out = P->L;
     out.depth_keys = alt ? (uint32_t *)ctx->k1.p : (uint32_t *)ctx->k0.p;
     out.depth_slots = (uint32_t *)order;
-    launch_tile_count((const Rec *)ctx->recs.p, order, P->R_cap, (uint32_t *)ctx->tcount.p, ctx->sms, st, cnt + 0);
+    launch_tile_count((const Rec *)ctx->recs.p, order, P->R_cap, p.tiles_x, p.tiles, (uint32_t *)ctx->tcount.p,
+                      (uint4 *)ctx->bins.p, ctx->sms, st, cnt + 0);
     CK(exclusive_scan_u32((const uint32_t *)ctx->tcount.p, (uint32_t *)ctx->toffs.p, P->R_cap, cnt + 1,
                           ctx->scanws.p, st));
     launch_clamp_count(cnt + 1, P->E_cap, cnt + 2, cnt + 3, st);
-    launch_emit((const Rec *)ctx->recs.p, order, (const uint32_t *)ctx->toffs.p, P->R_cap, p.tiles_x, p.tiles,
-                (uint32_t *)ctx->ek0.p, (uint32_t *)ctx->ev0.p, ctx->sms, st, cnt + 0, P->E_cap);
     const int kbits = bits_for((unsigned long long)vt - 1ull);
-    CK(radix_sort_pairs((uint32_t *)ctx->ek0.p, (uint32_t *)ctx->ev0.p, (uint32_t *)ctx->ek1.p,
-                        (uint32_t *)ctx->ev1.p, P->E_cap, kbits, ctx->sortws.p, st, &alt, cnt + 2));
+    CK(radix_sort_entries((const uint4 *)ctx->bins.p, (const uint32_t *)ctx->toffs.p, (const uint32_t *)ctx->tcount.p,
+                          P->R_cap, cnt + 0, p.tiles_x, (uint32_t *)ctx->ek0.p, (uint32_t *)ctx->ev0.p,
+                          (uint32_t *)ctx->ek1.p, (uint32_t *)ctx->ev1.p, P->E_cap, cnt + 2, kbits, ctx->sortws.p,
+                          st, &alt, ctx->sms));
     out.ekeys = alt ? (uint32_t *)ctx->ek1.p : (uint32_t *)ctx->ek0.p;
     out.evals = alt ? (uint32_t *)ctx->ev1.p : (uint32_t *)ctx->ev0.p;
     CK(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * vt, st));
@@ -703,7 +706,7 @@ int tuned_choice(dgs_ctx *ctx, const dgs_scene *scene, const Plan &p, int s0, in
 void free_ctx_buffers(dgs_ctx *ctx)
 {
     Buf *bufs[] = {&ctx->vgs, &ctx->vgos, &ctx->depth, &ctx->need, &ctx->counts, &ctx->recBase, &ctx->total,
-                   &ctx->recs, &ctx->k0, &ctx->v0, &ctx->k1, &ctx->v1, &ctx->tcount, &ctx->toffs, &ctx->ek0,
+                   &ctx->recs, &ctx->k0, &ctx->v0, &ctx->k1, &ctx->v1, &ctx->tcount, &ctx->toffs, &ctx->bins, &ctx->ek0,
                    &ctx->ev0, &ctx->ek1, &ctx->ev1, &ctx->ranges, &ctx->sortws, &ctx->scanws, &ctx->partial,
                    &ctx->refs, &ctx->recgrad, &ctx->refidx, &ctx->tck0, &ctx->tcv0, &ctx->tck1, &ctx->tcv1,
                    &ctx->icnt, &ctx->ioff, &ctx->qint, &ctx->counter, &ctx->pairm, &ctx->grp, &ctx->gmse, &ctx->omaps, &ctx->opart, &ctx->otpart,
@@ -1216,6 +1219,7 @@ int dgs_plan_create(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *stat
         for (Buf *b : rb) if ((r = ensure(w, *b, 4 * R, st)) != DGS_OK) break;
         if (r != DGS_OK) break;
         if ((r = ensure(w, w->tcount, 4 * (R + 1), st)) != DGS_OK) break;
+        if ((r = ensure(w, w->bins, sizeof(uint4) * (R + 1), st)) != DGS_OK) break;
         if ((r = ensure(w, w->toffs, 4 * (R + 1), st)) != DGS_OK) break;
         Buf *eb[] = {&w->ek0, &w->ev0, &w->ek1, &w->ev1};
         for (Buf *b : eb) if ((r = ensure(w, *b, 4 * E, st)) != DGS_OK) break;

@@ -8,6 +8,8 @@
 //                          laid out Gaussian-major, depth-minor
 //   Rec     [nRec]  48 B   one projected variant (view group, Gaussian, depth)
 //   recKey  [nRec]  u32    float bits of camera depth (0xFFFFFFFF = culled)
+//   bins    [nRec]  uint4  tile rectangle of each record in depth order (first
+//                          tile key, tile columns, slot): the entries' source
 //   entries [nEnt]  u32 key (v * tiles + tile), u32 value (record slot)
 //   ranges  [V*T]   uint2  [start, end) of each (view group, tile) run
 #pragma once
@@ -123,5 +125,18 @@ size_t radix_workspace_bytes(size_t n);
 cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, size_t n,
                              int bits, void *ws, cudaStream_t st, bool *result_in_alt,
                              const uint32_t *n_dev = nullptr);
+
+// Tile entries of the depth-ordered records, sorted stably by tile key on
+// bits [0, bits), without an unsorted copy: the first pass generates every
+// entry from the record's tile rectangle, bins[j] = (key of its first tile =
+// view group * tiles + ty0 * tiles_x + tx0, tile columns tw, record slot, 0),
+// record j owning entries [toffs[j], toffs[j] + counts[j]).  Entries at or past
+// e_cap (or *nent_dev) are dropped; nrec_dev / nent_dev as n_dev above.  The
+// (k0, v0) / (k1, v1) convention and the workspace are those of
+// radix_sort_pairs with n = e_cap.
+cudaError_t radix_sort_entries(const uint4 *bins, const uint32_t *toffs, const uint32_t *counts, uint32_t n_rec,
+                               const uint32_t *nrec_dev, int tiles_x, uint32_t *k0, uint32_t *v0, uint32_t *k1,
+                               uint32_t *v1, size_t e_cap, const uint32_t *nent_dev, int bits, void *ws,
+                               cudaStream_t st, bool *result_in_alt, int sms);
 
 }  // namespace dgs

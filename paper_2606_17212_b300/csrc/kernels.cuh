@@ -14,12 +14,11 @@ void launch_layout_counts(const uint32_t *need, const int32_t *offs, int V, int 
 void launch_project(const SceneDev &s, const ViewGroup *vgs, int V, const uint32_t *need, const uint32_t *recBase,
                     Rec *recs, uint32_t *keys, uint32_t *vals, int sms, cudaStream_t st);
 // n_dev (optional): live count on the device, n is then the capacity.
-void launch_tile_count(const Rec *recs, const uint32_t *order, uint32_t n, uint32_t *counts, int sms,
-                       cudaStream_t st, const uint32_t *n_dev = nullptr);
+// counts [n] tiles per depth-ordered record; bins [n] its tile rectangle
+// (radix_sort_entries)
+void launch_tile_count(const Rec *recs, const uint32_t *order, uint32_t n, int tiles_x, uint32_t tiles,
+                       uint32_t *counts, uint4 *bins, int sms, cudaStream_t st, const uint32_t *n_dev = nullptr);
 void launch_clamp_count(const uint32_t *total, uint32_t cap, uint32_t *out, uint32_t *flags, cudaStream_t st);
-void launch_emit(const Rec *recs, const uint32_t *order, const uint32_t *offsets, uint32_t n, int tiles_x,
-                 uint32_t tiles, uint32_t *ekeys, uint32_t *evals, int sms, cudaStream_t st,
-                 const uint32_t *n_dev = nullptr, uint32_t e_cap = 0xffffffffu);
 void launch_ranges(const uint32_t *keys, uint32_t n, uint2 *ranges, int sms, cudaStream_t st,
                    const uint32_t *n_dev = nullptr);
 void launch_zero_prefix(uint32_t *p, uint32_t n_cap, const uint32_t *n_dev, uint32_t per, int sms, cudaStream_t st);

@@ -151,10 +151,13 @@ __device__ __forceinline__ uint32_t live_n(uint32_t n_cap, const uint32_t *n_dev
     return n_dev ? min(n_cap, *n_dev) : n_cap;
 }
 
-// Tile counts of records in depth order (sorted slot list); zero past the
-// live count so a scan over the capacity gives the entry total.
+// Tile counts of records in depth order (sorted slot list), zero past the
+// live count so a scan over the capacity gives the entry total; and each
+// record's tile rectangle (first tile key, tile columns, slot) in the same
+// order, the source the tile sort generates the entries from.
 __global__ void k_tile_count(const Rec *__restrict__ recs, const uint32_t *__restrict__ order, uint32_t n_cap,
-                             const uint32_t *__restrict__ n_dev, uint32_t *__restrict__ counts)
+                             const uint32_t *__restrict__ n_dev, int tiles_x, uint32_t tiles,
+                             uint32_t *__restrict__ counts, uint4 *__restrict__ bins)
 {
     const uint32_t n = live_n(n_cap, n_dev);
     const uint32_t T = gridDim.x * blockDim.x;
@@ -172,7 +175,16 @@ __global__ void k_tile_count(const Rec *__restrict__ recs, const uint32_t *__res
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const uint32_t j = j0 + (uint32_t)k * T;
-            if (j < n_cap) counts[j] = slot[k] != 0xffffffffu ? rec_tiles(q[k]) : 0u;
+            if (j >= n_cap) continue;
+            const uint32_t c = slot[k] != 0xffffffffu ? rec_tiles(q[k]) : 0u;
+            counts[j] = c;
+            if (c) {
+                const uint32_t bx = __float_as_uint(q[k].y), by = __float_as_uint(q[k].z);
+                const uint32_t tx0 = (bx & 0xffffu) / TILE, ty0 = (by & 0xffffu) / TILE;
+                const uint32_t tw = (bx >> 16) / TILE - tx0 + 1u;
+                const uint32_t vbase = ((__float_as_uint(q[k].w) >> 16) & 0x7fffu) * tiles;
+                bins[j] = make_uint4(vbase + ty0 * (uint32_t)tiles_x + tx0, tw, slot[k], 0u);
+            }
         }
     }
 }
@@ -184,76 +196,6 @@ __global__ void k_clamp_count(const uint32_t *__restrict__ total, uint32_t cap, 
     const uint32_t t = *total;
     *out = t < cap ? t : cap;
     if (t > cap) atomicOr(flags, 1u);
-}
-
-// Emit one (view group * tiles + tile, slot) entry per overlapped tile, in
-// depth order, so a stable sort on the tile key leaves every tile's run
-// ordered by (depth, Gaussian, depth variant).  A warp takes 32 consecutive
-// records, whose entries are contiguous, and writes them cooperatively: lane
-// e of each pass finds the record owning entry e by a 5-step search over the
-// warp's inclusive prefix of tile counts (coalesced stores).
-__global__ void k_emit(const Rec *__restrict__ recs, const uint32_t *__restrict__ order,
-                       const uint32_t *__restrict__ offsets, uint32_t n_cap, const uint32_t *__restrict__ n_dev,
-                       uint32_t e_cap, int tiles_x, uint32_t tiles, uint32_t *__restrict__ ekeys,
-                       uint32_t *__restrict__ evals)
-{
-    const uint32_t n = live_n(n_cap, n_dev);
-    const int lane = threadIdx.x & 31;
-    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t base = warp * 32u; base < n; base += nwarps * 32u) {
-        const uint32_t j = base + lane;
-        uint32_t slot = 0, cnt = 0, off = 0;
-        int x0 = 0, tw = 1, y0 = 0;
-        uint32_t vbase = 0;
-        if (j < n) {
-            slot = order[j];
-            const float4 q = rec_tail(recs, slot);
-            cnt = rec_tiles(q);
-            off = offsets[j];
-            const uint32_t bx = __float_as_uint(q.y), by = __float_as_uint(q.z);
-            x0 = (int)(bx & 0xffffu) / TILE;
-            tw = (int)(bx >> 16) / TILE - x0 + 1;
-            y0 = (int)(by & 0xffffu) / TILE;
-            vbase = ((__float_as_uint(q.w) >> 16) & 0x7fffu) * tiles;
-        }
-        uint32_t incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        const uint32_t first = __shfl_sync(0xffffffffu, off, 0);
-        const float rtw = 1.0f / (float)tw;
-        // every lane runs the same number of passes so full-warp shuffles see every lane
-        for (uint32_t e0 = 0; e0 < total; e0 += 32) {
-            const uint32_t e = e0 + lane;
-            int lo = 0;                       // number of records whose entries end at or before e
-#pragma unroll
-            for (int b = 16; b >= 1; b >>= 1) {
-                const uint32_t v = __shfl_sync(0xffffffffu, incl, lo + b - 1);
-                if (v <= e) lo += b;
-            }
-            const uint32_t o_incl = __shfl_sync(0xffffffffu, incl, lo);
-            const uint32_t o_cnt = __shfl_sync(0xffffffffu, cnt, lo);
-            const int o_x0 = __shfl_sync(0xffffffffu, x0, lo);
-            const int o_tw = __shfl_sync(0xffffffffu, tw, lo);
-            const int o_y0 = __shfl_sync(0xffffffffu, y0, lo);
-            const float o_rtw = __shfl_sync(0xffffffffu, rtw, lo);
-            const uint32_t o_vb = __shfl_sync(0xffffffffu, vbase, lo);
-            const uint32_t o_slot = __shfl_sync(0xffffffffu, slot, lo);
-            if (e < total && first + e < e_cap) {
-                const int li = (int)(e - (o_incl - o_cnt));
-                int row = (int)(((float)li + 0.5f) * o_rtw);
-                row -= (row * o_tw > li) ? 1 : 0;            // exact quotient li / o_tw
-                row += ((row + 1) * o_tw <= li) ? 1 : 0;
-                const int col = li - row * o_tw;
-                ekeys[first + e] = o_vb + (uint32_t)((o_y0 + row) * tiles_x + o_x0 + col);
-                evals[first + e] = o_slot;
-            }
-        }
-    }
 }
 
 __global__ void k_ranges(const uint32_t *__restrict__ keys, uint32_t n_cap, const uint32_t *__restrict__ n_dev,
@@ -335,29 +277,18 @@ void launch_project(const SceneDev &s, const ViewGroup *vgs, int V, const uint32
     count_launch();
 }
 
-void launch_tile_count(const Rec *recs, const uint32_t *order, uint32_t n, uint32_t *counts, int sms,
-                       cudaStream_t st, const uint32_t *n_dev)
+void launch_tile_count(const Rec *recs, const uint32_t *order, uint32_t n, int tiles_x, uint32_t tiles,
+                       uint32_t *counts, uint4 *bins, int sms, cudaStream_t st, const uint32_t *n_dev)
 {
     if (n == 0) return;
     ProfScope ps_("tile_count", st);
-    k_tile_count<<<grid_for(n, 256, sms), 256, 0, st>>>(recs, order, n, n_dev, counts);
+    k_tile_count<<<grid_for(n, 256, sms), 256, 0, st>>>(recs, order, n, n_dev, tiles_x, tiles, counts, bins);
     count_launch();
 }
 
 void launch_clamp_count(const uint32_t *total, uint32_t cap, uint32_t *out, uint32_t *flags, cudaStream_t st)
 {
     k_clamp_count<<<1, 1, 0, st>>>(total, cap, out, flags);
-    count_launch();
-}
-
-void launch_emit(const Rec *recs, const uint32_t *order, const uint32_t *offsets, uint32_t n, int tiles_x,
-                 uint32_t tiles, uint32_t *ekeys, uint32_t *evals, int sms, cudaStream_t st, const uint32_t *n_dev,
-                 uint32_t e_cap)
-{
-    if (n == 0) return;
-    ProfScope ps_("emit", st);
-    k_emit<<<grid_for(n, 256, sms), 256, 0, st>>>(recs, order, offsets, n, n_dev, e_cap, tiles_x, tiles, ekeys,
-                                                   evals);
     count_launch();
 }
 

@@ -62,13 +62,36 @@ __global__ void __launch_bounds__(128) k_project_bwd(SceneDev s, const ViewGroup
         for (int d = s.L; d >= 1; --d) {
             bool decoded = false;
             Attr<SH> a;
-            for (int v = 0; v < V; ++v) {
+            // view groups holding a record of (this Gaussian, depth d), in order; the
+            // next record's gradient is loaded while the current one is processed
+            auto next_vg = [&](int v) {
+                while (v < V && !(((need[(size_t)v * s.C + c] & ~1u) >> d) & 1u)) ++v;
+                return v;
+            };
+            auto slot_of = [&](int v) {
                 const uint32_t nd = need[(size_t)v * s.C + c] & ~1u;
-                if (!((nd >> d) & 1u)) continue;
-                const uint32_t slot = recBase[(size_t)v * s.C + c] + (uint32_t)li * __popc(nd) +
-                                      __popc(nd & ((1u << d) - 1u));
-                const float4 q0 = rec_grad[(size_t)slot * 3], q1 = rec_grad[(size_t)slot * 3 + 1];
-                const float4 q2 = rec_grad[(size_t)slot * 3 + 2];
+                return recBase[(size_t)v * s.C + c] + (uint32_t)li * __popc(nd) + __popc(nd & ((1u << d) - 1u));
+            };
+            int vn = next_vg(0);
+            uint32_t slot_n = 0;
+            float4 n0 = make_float4(0, 0, 0, 0), n1 = n0, n2 = n0;
+            if (vn < V) {
+                slot_n = slot_of(vn);
+                n0 = __ldg(rec_grad + (size_t)slot_n * 3);
+                n1 = __ldg(rec_grad + (size_t)slot_n * 3 + 1);
+                n2 = __ldg(rec_grad + (size_t)slot_n * 3 + 2);
+            }
+            while (vn < V) {
+                const int v = vn;
+                const uint32_t slot = slot_n;
+                const float4 q0 = n0, q1 = n1, q2 = n2;
+                vn = next_vg(v + 1);
+                if (vn < V) {
+                    slot_n = slot_of(vn);
+                    n0 = __ldg(rec_grad + (size_t)slot_n * 3);
+                    n1 = __ldg(rec_grad + (size_t)slot_n * 3 + 1);
+                    n2 = __ldg(rec_grad + (size_t)slot_n * 3 + 2);
+                }
                 if (q0.x == 0.f && q0.y == 0.f && q0.z == 0.f && q0.w == 0.f && q1.x == 0.f && q1.y == 0.f &&
                     q1.z == 0.f && q1.w == 0.f && q2.x == 0.f)
                     continue;

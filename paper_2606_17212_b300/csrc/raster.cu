@@ -533,7 +533,7 @@ __device__ __forceinline__ float reduce8_transpose(const float *v, int lane)
 // Per-Gaussian sums: two pixels per thread, warp transpose reduction, block
 // sum in shared memory, then float4 atomics into the record's gradient.
 template <bool IMG>
-__global__ void __launch_bounds__(RT, 6) k_raster_bwd(RasterBwdArgs b)
+__global__ void __launch_bounds__(RT, 7) k_raster_bwd(RasterBwdArgs b)
 {
     const RasterArgs &a = b.f;
     __shared__ Staged sm;

@@ -706,6 +706,11 @@ def main():
         sm_mhz = pk.get("sm_max_mhz", 2032.0)
         fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12     # TFLOP/s, FP32 FMA, all SMs
         evals_per_launch = evals_per_px * H * W * S
+        if not training:
+            # tile reuse: only the rendered (state, tile) pairs are raster work
+            pairs, rendered, _ = R.tile_reuse_stats()
+            launches_per_step = dom_n / max(args.steps, 1)
+            evals_per_launch *= (rendered / max(pairs, 1)) / max(launches_per_step, 1.0)
         per_eval = BWD_FLOP_PER_EVAL if dom_name == "raster_bwd" else (
             FWD_FLOP_PER_EVAL if dom_name.startswith("raster_fwd") else None)
         if per_eval is not None:
@@ -742,6 +747,12 @@ def main():
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "kernels_note": "per-kernel times from the eager path's live events (same kernels as the graph)",
             "peaks": pk_kind}
+    if not training:
+        pairs, rendered, rounds = R.tile_reuse_stats()
+        line["tile_reuse"] = {"pairs": pairs, "rendered": rendered, "rounds": rounds,
+                              "what": "(state, tile) pairs scored per step and how many were rendered; the rest "
+                                      "took the partial of a state with the same depths on every cluster the "
+                                      "tile's walk reached (bit-identical)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     R.close()

@@ -213,6 +213,31 @@ DGS_API int dgs_state_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_st
                       double *mse, double *psnr, dgs_stream stream);
 
 /*
+ * Tile reuse in the distortion passes (dgs_state_utility, dgs_group_utility;
+ * on by default).  Whether a state's walk over a tile's sorted Gaussians
+ * includes an entry depends only on the state's delivered depth of that
+ * entry's cluster (Sections 3-4), so two states of one view (same camera and
+ * time) whose delivered depths agree on every cluster the walk reaches before
+ * all of the tile's pixels stop render that tile identically.  With reuse on,
+ * views with at least 8 states render one state of each such group per tile
+ * and give the others its FP64 squared-error partial: every output is
+ * bit-identical to rendering each state (the groups are exact, not
+ * approximate).  enable: 0 renders every (state, tile); nonzero reuses.  The
+ * reuse pass synchronizes the stream once per grouping round (at most 17).
+ * Returns DGS_E_INVALID_ARG for a null ctx.
+ */
+DGS_API int dgs_set_tile_reuse(dgs_ctx *ctx, int enable);
+
+/*
+ * Work of the context's last distortion pass: pairs [host] = (state, tile)
+ * pairs it scored, rendered [host] = pairs it rendered (the rest took a
+ * rendered pair's partial; equal to pairs without reuse), rounds [host] =
+ * grouping rounds (0 without reuse).  Any pointer may be NULL.  Returns
+ * DGS_E_INVALID_ARG for a null ctx.
+ */
+DGS_API int dgs_tile_reuse_stats(const dgs_ctx *ctx, int64_t *pairs, int64_t *rendered, int32_t *rounds);
+
+/*
  * Counterfactual render utility of completion groups (Section 5, Eq. 3 and
  * Eq. 4).  A completion group g is one packet (cluster, layer): groups [host]
  * [n_groups][2].  contexts holds n_groups * n_contexts states (masks [device],

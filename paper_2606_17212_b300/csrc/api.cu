@@ -108,7 +108,11 @@ struct dgs_ctx {
     std::string err;
     Buf vgs, vgos, depth, need, counts, recBase, total, recs, k0, v0, k1, v1, tcount, toffs, bins, ek0, ev0, ek1, ev1,
         ranges, sortws, scanws, partial, refs, recgrad, refidx, tck0, tcv0, tck1, tcv1, icnt, ioff, qint, counter,
-        pairm, grp, gmse, omaps, opart, otpart, oD, oweight, oints, recgmu, gqws;
+        pairm, grp, gmse, omaps, opart, otpart, oD, oweight, oints, recgmu, gqws,
+        shord, shpair, shpair2, shrep, shflag, shpos, shlist, shitem, shkey, shstop, shseg, shcnt, shtab;
+    bool tile_reuse = true;        // utility passes reuse rendered tiles across states (share.cu)
+    long long reuse_pairs = 0, reuse_rendered = 0;   // last distortion pass: (state, tile) pairs, rendered
+    int reuse_rounds = 0;
     std::map<std::vector<long long>, int> tuned_G;   // autotuner: call shape -> states per block
     void *h_stage = nullptr;
     size_t h_stage_cap = 0;
@@ -710,7 +714,9 @@ void free_ctx_buffers(dgs_ctx *ctx)
                    &ctx->ev0, &ctx->ek1, &ctx->ev1, &ctx->ranges, &ctx->sortws, &ctx->scanws, &ctx->partial,
                    &ctx->refs, &ctx->recgrad, &ctx->refidx, &ctx->tck0, &ctx->tcv0, &ctx->tck1, &ctx->tcv1,
                    &ctx->icnt, &ctx->ioff, &ctx->qint, &ctx->counter, &ctx->pairm, &ctx->grp, &ctx->gmse, &ctx->omaps, &ctx->opart, &ctx->otpart,
-                   &ctx->oD, &ctx->oweight, &ctx->oints, &ctx->recgmu, &ctx->gqws};
+                   &ctx->oD, &ctx->oweight, &ctx->oints, &ctx->recgmu, &ctx->gqws, &ctx->shord, &ctx->shpair,
+                   &ctx->shpair2, &ctx->shrep, &ctx->shflag, &ctx->shpos, &ctx->shlist, &ctx->shitem, &ctx->shkey, &ctx->shstop,
+                   &ctx->shseg, &ctx->shcnt, &ctx->shtab};
     for (Buf *b : bufs)
         if (b->p) { cudaFree(b->p); b->p = nullptr; b->cap = 0; }
     if (ctx->h_stage) { cudaFreeHost(ctx->h_stage); ctx->h_stage = nullptr; }
@@ -1047,6 +1053,144 @@ int dgs_objective(dgs_ctx *ctx, const float *images, const float *refs, const in
 namespace {
 
 // Eq. 3 distortion of every state against its view's complete render (one batch).
+// View groups with at least this many states take the tile-reuse pass.
+constexpr int SHARE_MIN_STATES = 8;
+
+// Squared-error partials of states [0, S_user) with rendered tiles reused
+// across states (share.cu): rounds of grouping, rendering one state per group
+// on the explicit work list, and resolving the rest, until no pair of (view
+// group tile, state) is pending.  Writes exactly the partials the plain pass
+// writes, bit for bit.
+int shared_mse_pass(dgs_ctx *ctx, const dgs_scene *scene, const Plan &p, const Lists &L, RasterArgs a,
+                    cudaStream_t st)
+{
+    const uint32_t T = p.tiles, nvt = (uint32_t)((size_t)p.V * T);
+    const int C = scene->n_clusters;
+    const int G = 2;
+    // states of each view group, in state order; pairs per view-group tile
+    std::vector<int32_t> cnt(p.V, 0), vg_first(p.V + 1, 0), order(p.S_user);
+    for (int s = 0; s < p.S_user; ++s) ++cnt[p.vg_of_state[s]];
+    for (int v = 0; v < p.V; ++v) vg_first[v + 1] = vg_first[v] + cnt[v];
+    {
+        std::vector<int32_t> fill(vg_first.begin(), vg_first.end() - 1);
+        for (int s = 0; s < p.S_user; ++s) order[fill[p.vg_of_state[s]]++] = s;
+    }
+    std::vector<uint32_t> vt_off(nvt + 1, 0);
+    unsigned long long np = 0;
+    for (uint32_t vt = 0; vt < nvt; ++vt) {
+        vt_off[vt] = (uint32_t)np;
+        np += (unsigned long long)cnt[vt / T];
+    }
+    if (np >= 0x7fffffffull) return fail(ctx, DGS_E_CAPACITY, "too many (tile, state) pairs for tile reuse");
+    const size_t n0 = (size_t)np;
+    vt_off[nvt] = (uint32_t)np;
+    if (n0 == 0) return DGS_OK;
+    // tables: vt_off | vg_first | order
+    const size_t tab_words = (size_t)nvt + 1 + (size_t)p.V + 1 + (size_t)p.S_user;
+    TRY(ensure(ctx, ctx->shtab, 4 * tab_words, st));
+    TRY(ensure_stage(ctx, 4 * tab_words, st));
+    CK(cudaEventSynchronize(ctx->stage_done));
+    {
+        char *h = (char *)ctx->h_stage;
+        std::memcpy(h, vt_off.data(), 4 * ((size_t)nvt + 1));
+        std::memcpy(h + 4 * ((size_t)nvt + 1), vg_first.data(), 4 * ((size_t)p.V + 1));
+        std::memcpy(h + 4 * ((size_t)nvt + 1 + p.V + 1), order.data(), 4 * (size_t)p.S_user);
+        CK(cudaMemcpyAsync(ctx->shtab.p, h, 4 * tab_words, cudaMemcpyHostToDevice, st));
+        CK(cudaEventRecord(ctx->stage_done, st));
+    }
+    const uint32_t *d_vt_off = (const uint32_t *)ctx->shtab.p;
+    const int32_t *d_vg_first = (const int32_t *)(d_vt_off + nvt + 1);
+    const int32_t *d_order = d_vg_first + p.V + 1;
+    // buffers
+    const size_t pair_bytes = 9 * n0 + 64;                 // vt, state (u32) and K (u8)
+    TRY(ensure(ctx, ctx->shord, 8 * (size_t)nvt * SHARE_ORDER, st));
+    TRY(ensure(ctx, ctx->shpair, pair_bytes, st));
+    TRY(ensure(ctx, ctx->shpair2, pair_bytes, st));
+    TRY(ensure(ctx, ctx->shrep, 4 * n0, st));
+    TRY(ensure(ctx, ctx->shflag, 4 * n0, st));
+    TRY(ensure(ctx, ctx->shpos, 4 * n0, st));
+    TRY(ensure(ctx, ctx->shlist, 8 * n0, st));
+    TRY(ensure(ctx, ctx->shitem, 8 * n0, st));
+    TRY(ensure(ctx, ctx->shkey, 8 * n0, st));
+    TRY(ensure(ctx, ctx->shstop, 4 * (size_t)p.S_user * T, st));
+    TRY(ensure(ctx, ctx->shseg, 2 * sizeof(uint2) * (size_t)nvt, st));
+    TRY(ensure(ctx, ctx->shcnt, 64, st));
+    TRY(ensure(ctx, ctx->scanws, scan_workspace_bytes(n0), st));
+    TRY(ensure(ctx, ctx->counter, 16, st));
+    uint32_t *ord_c = (uint32_t *)ctx->shord.p, *ord_fp = ord_c + (size_t)nvt * SHARE_ORDER;
+    auto pair_arrays = [&](Buf &b, uint32_t *&vt, uint32_t *&stt, uint8_t *&k) {
+        vt = (uint32_t *)b.p;
+        stt = vt + n0;
+        k = (uint8_t *)(stt + n0);
+    };
+    uint32_t *pvt, *pst, *nvt_a, *nst;
+    uint8_t *pk, *nk;
+    pair_arrays(ctx->shpair, pvt, pst, pk);
+    pair_arrays(ctx->shpair2, nvt_a, nst, nk);
+    uint32_t *prep = (uint32_t *)ctx->shrep.p, *flag = (uint32_t *)ctx->shflag.p, *pos = (uint32_t *)ctx->shpos.p;
+    uint32_t *lvt = (uint32_t *)ctx->shlist.p, *lst = lvt + n0;
+    uint32_t *ifirst = (uint32_t *)ctx->shitem.p, *icount = ifirst + n0;
+    unsigned long long *keys = (unsigned long long *)ctx->shkey.p;
+    uint2 *seg = (uint2 *)ctx->shseg.p, *seg2 = seg + nvt;
+    uint32_t *dcnt = (uint32_t *)ctx->shcnt.p;   // [0] pending pairs, [1] render list, [2] items, [3] next pending
+    const uint8_t *depth = (const uint8_t *)ctx->depth.p;
+
+    launch_first_clusters((const Rec *)ctx->recs.p, L.evals, (const uint2 *)ctx->ranges.p, nvt, C, ord_c, ord_fp, ctx->sms, st);
+    launch_pairs_init(d_vt_off, nvt, (uint32_t)n0, T, d_vg_first, d_order, pvt, pst, pk, ctx->sms, st);
+    ctx->h_small[8] = (uint32_t)n0;
+    CK(cudaMemcpyAsync(dcnt, ctx->h_small + 8, 4, cudaMemcpyHostToDevice, st));
+    a.stop = (uint32_t *)ctx->shstop.p;
+    const int blocks = ctx->sms * raster_fwd_blocks_per_sm(G, false, true, true);
+    size_t n = n0;
+    ctx->reuse_pairs = (long long)n0;
+    ctx->reuse_rendered = 0;
+    ctx->reuse_rounds = 0;
+    for (int round = 0; n > 0; ++round) {
+        if (round > SHARE_MAX_K + 2) return fail(ctx, DGS_E_CUDA, "tile reuse did not converge");
+        // group the pending pairs of every tile; representatives render
+        CK(cudaMemsetAsync(seg, 0, sizeof(uint2) * nvt, st));
+        launch_segments(pvt, dcnt + 0, n, seg, ctx->sms, st);
+        launch_share_group(seg, nvt, pvt, pst, pk, dcnt + 0, n, ord_c, depth, C, keys, prep, ctx->sms, st);
+        launch_rep_flags(pst, prep, dcnt + 0, n, flag, ctx->sms, st);
+        CK(exclusive_scan_u32(flag, pos, n, dcnt + 1, ctx->scanws.p, st));
+        launch_compact_pairs(flag, pos, dcnt + 0, n, pvt, pst, nullptr, lvt, lst, nullptr, ctx->sms, st);
+        CK(cudaMemcpyAsync(ctx->h_small + 9, dcnt + 1, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const size_t nl = ctx->h_small[9];
+        ctx->reuse_rendered += (long long)nl;
+        ctx->reuse_rounds = round + 1;
+        if (nl > 0) {
+            CK(cudaMemsetAsync(seg2, 0, sizeof(uint2) * nvt, st));
+            launch_segments(lvt, dcnt + 1, nl, seg2, ctx->sms, st);
+            launch_item_lists(lvt, seg2, dcnt + 1, nl, G, flag, pos, dcnt + 2, ctx->scanws.p, ifirst, icount,
+                              ctx->sms, st);
+            CK(cudaMemsetAsync(ctx->counter.p, 0, 4, st));
+            WorkQueue q{};
+            q.counter = (uint32_t *)ctx->counter.p;
+            q.item_first = ifirst;
+            q.item_count = icount;
+            q.list_vt = lvt;
+            q.list_state = lst;
+            q.n_items_dev = dcnt + 2;
+            launch_raster_fwd(a, q, G, blocks, st);
+        }
+        // everyone else: take the representative's partial, or regroup
+        launch_share_resolve(pvt, pst, pk, prep, dcnt + 0, n, T, ord_c, ord_fp, depth, C, a.stop, a.partial, flag,
+                             ctx->sms, st);
+        CK(exclusive_scan_u32(flag, pos, n, dcnt + 3, ctx->scanws.p, st));
+        launch_compact_pairs(flag, pos, dcnt + 0, n, pvt, pst, pk, nvt_a, nst, nk, ctx->sms, st);
+        CK(cudaMemcpyAsync(dcnt + 0, dcnt + 3, 4, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(ctx->h_small + 9, dcnt + 3, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        n = ctx->h_small[9];
+        std::swap(pvt, nvt_a);
+        std::swap(pst, nst);
+        std::swap(pk, nk);
+    }
+    CK(cudaGetLastError());
+    return DGS_OK;
+}
+
 int utility_pass(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states, const dgs_camera *cams,
                  int n_cams, const float *bg, double *mse, double *psnr, cudaStream_t st)
 {
@@ -1071,7 +1215,18 @@ int utility_pass(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states,
     a.refs = (const float *)ctx->refs.p;
     a.ref_of_state = (const int32_t *)ctx->vgos.p;
     a.partial = (double *)ctx->partial.p;
-    TRY(fwd_pass(ctx, scene, p, L, a, 0, p.S_user, st));
+    int maxper = 0;
+    {
+        std::vector<int> cnt(p.V, 0);
+        for (int s = 0; s < p.S_user; ++s) maxper = std::max(maxper, ++cnt[p.vg_of_state[s]]);
+    }
+    if (ctx->tile_reuse && maxper >= SHARE_MIN_STATES) {
+        TRY(shared_mse_pass(ctx, scene, p, L, a, st));
+    } else {
+        ctx->reuse_pairs = ctx->reuse_rendered = (long long)p.S_user * p.tiles;
+        ctx->reuse_rounds = 0;
+        TRY(fwd_pass(ctx, scene, p, L, a, 0, p.S_user, st));
+    }
     launch_mse_reduce((const double *)ctx->partial.p, p.S_user, (int)p.tiles, 1.0 / (double)img, mse, psnr, st);
     CK(cudaGetLastError());
     return DGS_OK;
@@ -1101,6 +1256,22 @@ int dgs_debug_tile_lists(dgs_ctx *ctx, uint32_t *n_rec, uint32_t *n_ent, int32_t
     if (entry_keys && ne) CK(cudaMemcpyAsync(entry_keys, tp.lists.ekeys, 4 * ne, cudaMemcpyDeviceToDevice, st));
     if (entry_vals && ne) CK(cudaMemcpyAsync(entry_vals, tp.lists.evals, 4 * ne, cudaMemcpyDeviceToDevice, st));
     if (ranges && nrg) CK(cudaMemcpyAsync(ranges, ctx->ranges.p, sizeof(uint2) * nrg, cudaMemcpyDeviceToDevice, st));
+    return DGS_OK;
+}
+
+int dgs_set_tile_reuse(dgs_ctx *ctx, int enable)
+{
+    if (!ctx) return DGS_E_INVALID_ARG;
+    ctx->tile_reuse = enable != 0;
+    return DGS_OK;
+}
+
+int dgs_tile_reuse_stats(const dgs_ctx *ctx, int64_t *pairs, int64_t *rendered, int32_t *rounds)
+{
+    if (!ctx) return DGS_E_INVALID_ARG;
+    if (pairs) *pairs = ctx->reuse_pairs;
+    if (rendered) *rendered = ctx->reuse_rendered;
+    if (rounds) *rounds = ctx->reuse_rounds;
     return DGS_OK;
 }
 

@@ -25,6 +25,15 @@ constexpr int TILE_PIX = TILE * TILE;    // threads per raster block
 constexpr int MAX_CLUSTERS = 1024;
 constexpr int MAX_LAYERS = 8;
 
+// Tile reuse across states (share.cu): group keys hold the delivered depths
+// (4 bits each, MAX_LAYERS <= 15) of up to SHARE_MAX_K clusters; the first
+// SHARE_ORDER = SHARE_MAX_K + 1 clusters of each run are kept; one block's
+// hash table has SHARE_TABLE slots.
+constexpr int SHARE_MAX_K = 15;
+constexpr int SHARE_ORDER = SHARE_MAX_K + 1;
+constexpr int SHARE_TABLE = 8192;
+static_assert(MAX_LAYERS <= 15, "depths are packed in 4 bits");
+
 // Records hold the conic (A = xx, B = xy, C = yy) pre-scaled for base-2
 // exponents: a2 = K_AC A, b2 = K_B B, c2 = K_AC C, so that a pixel's
 // log2(e) * power = a2 dx^2 + b2 dx dy + c2 dy^2 and alpha = o 2^(that)

@@ -37,6 +37,7 @@ struct RasterArgs {
     const int32_t *ref_of_state;  // [S]
     double *partial;              // [S][tiles] FP64 squared-error partial sums
     int img_s0;                   // images hold states img_s0, img_s0 + 1, ...
+    uint32_t *stop;               // [S][tiles] or null: run prefix staged while the state had a live pixel
 };
 // Work queue of the persistent forward raster: (view group, tile) pairs in
 // descending cost order, each expanded into that view group's state groups.
@@ -50,10 +51,18 @@ struct WorkQueue {
     const int32_t *vg_group_base;  // [V] first group of each view group
     const int32_t *state_order;    // [S] states sorted by view group
     uint32_t *counter;             // zeroed before the launch
+    // Explicit work list (tile reuse), used when item_first is set: item k
+    // renders states list_state[item_first[k] .. + item_count[k]) on the
+    // view-group tile list_vt[item_first[k]]; the item count is *n_items_dev.
+    const uint32_t *item_first = nullptr;
+    const uint32_t *item_count = nullptr;
+    const uint32_t *list_vt = nullptr;
+    const uint32_t *list_state = nullptr;
+    const uint32_t *n_items_dev = nullptr;
 };
 // G = states composited per staged batch (1, 2, 4 or 8); blocks = persistent grid.
 void launch_raster_fwd(const RasterArgs &a, const WorkQueue &q, int G, int blocks, cudaStream_t st);
-int raster_fwd_blocks_per_sm(int G, bool write, bool mse);
+int raster_fwd_blocks_per_sm(int G, bool write, bool mse, bool list = false);
 void launch_tile_costs(const uint2 *ranges, uint32_t n, uint32_t *keys, uint32_t *vals, int sms, cudaStream_t st);
 void launch_item_counts(const uint32_t *tile_order, uint32_t n, uint32_t tiles, const int32_t *vg_ngroups,
                         uint32_t *counts, int sms, cudaStream_t st);
@@ -93,6 +102,32 @@ void launch_objective_grad(const float *images, const float *refs, const int32_t
                            const float *d_mx, const float *d_exx, const float *d_exy, const double *weight,
                            float ssim_weight, float tscale, const int32_t *toff, const int2 *tlist, float *dL,
                            cudaStream_t st);
+
+// Tile reuse across states (share.cu).
+void launch_first_clusters(const Rec *recs, const uint32_t *evals, const uint2 *ranges, uint32_t n_vt, int C,
+                           uint32_t *ord_c, uint32_t *ord_fp, int sms, cudaStream_t st);
+void launch_pairs_init(const uint32_t *vt_off, uint32_t n_vt, uint32_t n_pairs, uint32_t tiles,
+                       const int32_t *vg_first, const int32_t *state_order, uint32_t *pvt, uint32_t *pst,
+                       uint8_t *pk, int sms, cudaStream_t st);
+void launch_segments(const uint32_t *keys, const uint32_t *n_dev, size_t n_cap, uint2 *seg, int sms,
+                     cudaStream_t st);
+// keys: [n_cap] u64 scratch
+void launch_share_group(const uint2 *seg, uint32_t n_vt, const uint32_t *pvt, const uint32_t *pst,
+                        const uint8_t *pk, const uint32_t *n_dev, size_t n_cap, const uint32_t *ord_c,
+                        const uint8_t *depth, int C, unsigned long long *keys, uint32_t *prep, int sms,
+                        cudaStream_t st);
+void launch_rep_flags(const uint32_t *pst, const uint32_t *prep, const uint32_t *n_dev, size_t n_cap,
+                      uint32_t *flag, int sms, cudaStream_t st);
+void launch_compact_pairs(const uint32_t *flag, const uint32_t *pos, const uint32_t *n_dev, size_t n_cap,
+                          const uint32_t *pvt, const uint32_t *pst, const uint8_t *pk, uint32_t *ovt,
+                          uint32_t *ost, uint8_t *ok, int sms, cudaStream_t st);
+void launch_item_lists(const uint32_t *lvt, const uint2 *seg, const uint32_t *n_dev, size_t n_cap, int G,
+                       uint32_t *flag, uint32_t *pos, uint32_t *n_items_dev, void *scan_ws, uint32_t *item_first,
+                       uint32_t *item_count, int sms, cudaStream_t st);
+void launch_share_resolve(const uint32_t *pvt, const uint32_t *pst, uint8_t *pk, const uint32_t *prep,
+                          const uint32_t *n_dev, size_t n_cap, uint32_t tiles, const uint32_t *ord_c,
+                          const uint32_t *ord_fp, const uint8_t *depth, int C, const uint32_t *stop,
+                          double *partial, uint32_t *pending, int sms, cudaStream_t st);
 
 // rec_cap: record slots of rec_grad (the per-record mean gradients of the
 // affine, g.rec_gmu, are cleared over it)

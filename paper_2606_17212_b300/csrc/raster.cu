@@ -293,32 +293,43 @@ __device__ __forceinline__ int warp_list(const Staged &sm, uint8_t *list, int nk
 // state of the group; items come costliest tile first from an atomic counter.
 // Per pixel and state the arithmetic is composite(), exactly as for a single
 // state, so grouping never changes a bit of the result.
-template <int G, bool WRITE, bool MSE>
+template <int G, bool WRITE, bool MSE, bool LIST>
 __global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a, WorkQueue q)
 {
     __shared__ Staged sm;
     __shared__ uint8_t sdep[G][MAX_CLUSTERS];
     __shared__ double wsum[G][RW];
     __shared__ uint32_t s_item;
+    __shared__ uint32_t s_stop[G];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t n_items = LIST ? *q.n_items_dev : q.n_items;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(q.counter, 1u);
+        if (LIST && threadIdx.x < G) s_stop[threadIdx.x] = 0u;
         __syncthreads();
         const uint32_t item = s_item;
-        if (item >= q.n_items) break;
-        // largest j with item_offsets[j] <= item
-        uint32_t lo = 0, hi = q.n_vt - 1;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi + 1) >> 1;
-            if (q.item_offsets[mid] <= item) lo = mid; else hi = mid - 1;
-        }
-        const uint32_t vt = q.tile_order[lo];
-        const int v = (int)(vt / a.tiles), tile = (int)(vt % a.tiles);
-        const int grp = q.vg_group_base[v] + (int)(item - q.item_offsets[lo]);
-        const int first = q.group_first[grp], cnt = q.group_count[grp];
+        if (item >= n_items) break;
+        uint32_t vt;
         int sid[G];
+        if (LIST) {
+            const uint32_t first = q.item_first[item], cnt = q.item_count[item];
+            vt = q.list_vt[first];
 #pragma unroll
-        for (int g = 0; g < G; ++g) sid[g] = g < cnt ? q.state_order[first + g] : -1;
+            for (int g = 0; g < G; ++g) sid[g] = (uint32_t)g < cnt ? (int)q.list_state[first + g] : -1;
+        } else {
+            // largest j with item_offsets[j] <= item
+            uint32_t lo = 0, hi = q.n_vt - 1;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                if (q.item_offsets[mid] <= item) lo = mid; else hi = mid - 1;
+            }
+            vt = q.tile_order[lo];
+            const int grp = q.vg_group_base[vt / a.tiles] + (int)(item - q.item_offsets[lo]);
+            const int first = q.group_first[grp], cnt = q.group_count[grp];
+#pragma unroll
+            for (int g = 0; g < G; ++g) sid[g] = g < cnt ? q.state_order[first + g] : -1;
+        }
+        const int tile = (int)(vt % a.tiles);
 #pragma unroll
         for (int g = 0; g < G; ++g)
             if (sid[g] >= 0)
@@ -344,6 +355,8 @@ __global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a, WorkQueue q)
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 if (!__any_sync(0xffffffffu, !(p[g][0].done && p[g][1].done))) continue;
+                // the state still has a live pixel: this batch's clusters decide its result
+                if (LIST && lane == 0) atomicMax(&s_stop[g], min(start + (uint32_t)BATCH, rg.y) - rg.x);
                 const int n = warp_list(sm, sm.list[w], nk, sdep[g], wq);
                 for (int i = 0; i < n; ++i) {
                     if (p[g][0].done && p[g][1].done) break;
@@ -413,6 +426,7 @@ __global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a, WorkQueue q)
 #pragma unroll
                     for (int k = 0; k < RW; ++k) tot += wsum[g][k];
                     a.partial[(size_t)sid[g] * a.tiles + tile] = tot;
+                    if (LIST) a.stop[(size_t)sid[g] * a.tiles + tile] = s_stop[g];
                 }
             }
         }
@@ -731,23 +745,25 @@ __global__ void __launch_bounds__(256) k_image_mse(const float *__restrict__ ima
 
 }  // namespace
 
-template <int G, bool WRITE, bool MSE>
+template <int G, bool WRITE, bool MSE, bool LIST>
 static void launch_fwd_t(const RasterArgs &a, const WorkQueue &q, int blocks, cudaStream_t st)
 {
-    k_raster_fwd<G, WRITE, MSE><<<blocks, RT, 0, st>>>(a, q);
+    k_raster_fwd<G, WRITE, MSE, LIST><<<blocks, RT, 0, st>>>(a, q);
 }
 
+// The explicit work list (tile reuse) renders squared-error partials only.
 template <int G>
 static void launch_fwd_g(const RasterArgs &a, const WorkQueue &q, int blocks, cudaStream_t st)
 {
-    if (a.images && a.refs) launch_fwd_t<G, true, true>(a, q, blocks, st);
-    else if (a.images) launch_fwd_t<G, true, false>(a, q, blocks, st);
-    else launch_fwd_t<G, false, true>(a, q, blocks, st);
+    if (q.item_first) launch_fwd_t<G, false, true, true>(a, q, blocks, st);
+    else if (a.images && a.refs) launch_fwd_t<G, true, true, false>(a, q, blocks, st);
+    else if (a.images) launch_fwd_t<G, true, false, false>(a, q, blocks, st);
+    else launch_fwd_t<G, false, true, false>(a, q, blocks, st);
 }
 
 void launch_raster_fwd(const RasterArgs &a, const WorkQueue &q, int G, int blocks, cudaStream_t st)
 {
-    if (q.n_items == 0 || (!a.images && !a.refs)) return;
+    if ((!q.item_first && q.n_items == 0) || (!a.images && !a.refs)) return;
     static const char *names[2][4] = {{"raster_fwd_g1", "raster_fwd_g2", "raster_fwd_g4", "raster_fwd_g8"},
                                       {"raster_fwd_mse_g1", "raster_fwd_mse_g2", "raster_fwd_mse_g4",
                                        "raster_fwd_mse_g8"}};
@@ -762,35 +778,36 @@ void launch_raster_fwd(const RasterArgs &a, const WorkQueue &q, int G, int block
     count_launch();
 }
 
-template <int G, bool WRITE, bool MSE>
+template <int G, bool WRITE, bool MSE, bool LIST>
 static int occ_t()
 {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_fwd<G, WRITE, MSE>, RT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_fwd<G, WRITE, MSE, LIST>, RT, 0);
     return n > 0 ? n : 1;
 }
 
 template <int G>
-static int occ_g(bool write, bool mse)
+static int occ_g(bool write, bool mse, bool list)
 {
-    if (write && mse) return occ_t<G, true, true>();
-    if (write) return occ_t<G, true, false>();
-    return occ_t<G, false, true>();
+    if (list) return occ_t<G, false, true, true>();
+    if (write && mse) return occ_t<G, true, true, false>();
+    if (write) return occ_t<G, true, false, false>();
+    return occ_t<G, false, true, false>();
 }
 
 // Resident blocks per SM of each instantiation (queried once, then cached, so
 // launches made during stream capture issue no runtime queries).
-int raster_fwd_blocks_per_sm(int G, bool write, bool mse)
+int raster_fwd_blocks_per_sm(int G, bool write, bool mse, bool list)
 {
-    static int cache[4][3] = {};
+    static int cache[4][4] = {};
     const int gi = G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : 3;
-    const int mi = (write && mse) ? 0 : write ? 1 : 2;
+    const int mi = list ? 3 : (write && mse) ? 0 : write ? 1 : 2;
     if (!cache[gi][mi]) {
         switch (G) {
-        case 1: cache[gi][mi] = occ_g<1>(write, mse); break;
-        case 2: cache[gi][mi] = occ_g<2>(write, mse); break;
-        case 4: cache[gi][mi] = occ_g<4>(write, mse); break;
-        default: cache[gi][mi] = occ_g<8>(write, mse); break;
+        case 1: cache[gi][mi] = occ_g<1>(write, mse, list); break;
+        case 2: cache[gi][mi] = occ_g<2>(write, mse, list); break;
+        case 4: cache[gi][mi] = occ_g<4>(write, mse, list); break;
+        default: cache[gi][mi] = occ_g<8>(write, mse, list); break;
         }
     }
     return cache[gi][mi];

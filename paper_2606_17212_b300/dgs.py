@@ -63,7 +63,8 @@ EXPORTS = ("dgs_create", "dgs_destroy", "dgs_last_error", "dgs_version", "dgs_re
            "dgs_image_mse_noalloc", "dgs_debug_tile_lists", "dgs_plan_create", "dgs_plan_destroy",
            "dgs_plan_last_error", "dgs_plan_render", "dgs_plan_backward", "dgs_plan_utility",
            "dgs_plan_image_mse", "dgs_plan_status", "dgs_arena_create", "dgs_arena_destroy",
-           "dgs_group_utility", "dgs_objective")
+           "dgs_group_utility", "dgs_objective", "dgs_set_tile_reuse",
+           "dgs_tile_reuse_stats")
 OBJECTIVE_MAX_STATES = 16384
 UTILITY_MAX_CONTEXTS = 4096
 PLAN_RENDER, PLAN_UTILITY = 1, 2
@@ -97,6 +98,9 @@ def lib():
                                     P, P]
         L.dgs_group_utility.argtypes = [P, ctypes.POINTER(Scene_t), ctypes.POINTER(States_t), P, I, I, P, I, P,
                                         D, D, D, P, P, P]
+        L.dgs_set_tile_reuse.argtypes = [P, I]
+        L.dgs_tile_reuse_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(ctypes.c_int32)]
         L.dgs_kernel_launches.argtypes = [P]
         L.dgs_kernel_launches.restype = ctypes.c_int64
         L.dgs_reset_kernel_launches.argtypes = [P]
@@ -341,6 +345,18 @@ class Renderer:
                                                   _ptr(img), _ptr(dL_dimages.contiguous()), ctypes.byref(g),
                                                   _stream(stream)), "dgs_render_backward")
         return grads
+
+    def set_tile_reuse(self, enable: bool):
+        """dgs_set_tile_reuse: exact reuse of rendered tiles across the states of
+        one view in the distortion passes (on by default; outputs unchanged)."""
+        self._check(self._lib.dgs_set_tile_reuse(self.h, 1 if enable else 0), "dgs_set_tile_reuse")
+
+    def tile_reuse_stats(self):
+        """dgs_tile_reuse_stats of the last distortion pass: (pairs, rendered, rounds)."""
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        self._check(self._lib.dgs_tile_reuse_stats(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+                    "dgs_tile_reuse_stats")
+        return a.value, b.value, c.value
 
     def state_utility(self, scene: DeviceScene, states: DeviceStates, cams, bg, mse=None, psnr=None,
                       stream=None):

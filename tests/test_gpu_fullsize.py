@@ -114,6 +114,13 @@ def test_utility_sweep_2p7m_full_size(R, torch):
     sc = dgs.DeviceScene.from_host(w.scene)
     st = dgs.DeviceStates.from_host(w.states)
     mse, psnr = R.state_utility(sc, st, w.cams, w.bg)
+    # tile reuse across the 32,768 states (on by default) changes no bit
+    R.set_tile_reuse(False)
+    try:
+        mse_plain, _ = R.state_utility(sc, st, w.cams, w.bg)
+    finally:
+        R.set_tile_reuse(True)
+    assert torch.equal(mse, mse_plain)
     mse = mse.cpu().numpy()
     # >= 0: pixels stop inside the front clusters of this dense scene, so a state that
     # delivers those completely renders bit-identically to the complete state (MSE 0)

@@ -162,6 +162,53 @@ def test_utility_equals_images_then_mse(R, torch):
     assert torch.allclose(mse, m2, rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("name,scale,n", [("c4_utility_2p7m", 0.02, 600), ("c2_dynamic_250k", 0.03, 256),
+                                          ("c3_fwdbwd_250k", 0.05, 96)])
+def test_tile_reuse_is_bitwise(R, torch, name, scale, n):
+    """Reusing rendered tiles across the states of a view changes no bit of any
+    state's MSE: reuse on == every (state, tile) rendered."""
+    w = synth.config(name, scale=scale, n_states=n)
+    masks = w.states.masks.copy()
+    masks[1] = 0                       # empty delivery
+    masks[2] = 0xFFFFFFFF              # complete delivery
+    masks[3:6] = masks[6]              # duplicates
+    if name == "c3_fwdbwd_250k":       # many states on few views: eight per (camera, time)
+        w.states.t[:] = w.states.t[0]
+        w.states.cam[:] = w.states.cam % 2
+    w.states.masks = masks
+    sc = dgs.DeviceScene.from_host(w.scene)
+    st = _gpu_states(w)
+    R.set_tile_reuse(False)
+    try:
+        m0, p0 = R.state_utility(sc, st, w.cams, w.bg)
+    finally:
+        R.set_tile_reuse(True)
+    m1, p1 = R.state_utility(sc, st, w.cams, w.bg)
+    assert torch.equal(m0, m1)
+    assert torch.equal(p0.isinf(), p1.isinf()) and torch.equal(p0[~p0.isinf()], p1[~p1.isinf()])
+    assert float(m1[2]) == 0.0
+
+
+def test_tile_reuse_group_utility_bitwise(R, torch):
+    """Eq. 3 / Eq. 4 group utility with and without tile reuse: identical bits."""
+    w = synth.config("c4_utility_2p7m", scale=0.02, n_states=16)
+    sc = dgs.DeviceScene.from_host(w.scene)
+    rng = np.random.default_rng(5)
+    C, L, M = w.scene.n_clusters, w.scene.n_layers, 12
+    groups = np.array([[c, int(rng.integers(0, L))] for c in rng.choice(C, 6, replace=False)], np.int32)
+    ctx = synth.group_contexts(groups, M, C, L, rng)
+    n = len(groups) * M
+    states = dgs.DeviceStates.from_host(synth.States(ctx, np.full(n, w.states.t[0], np.float32),
+                                                     np.zeros(n, np.int32)))
+    R.set_tile_reuse(False)
+    try:
+        d0, s0 = R.group_utility(sc, states, groups, M, w.cams, w.bg)
+    finally:
+        R.set_tile_reuse(True)
+    d1, s1 = R.group_utility(sc, states, groups, M, w.cams, w.bg)
+    assert torch.equal(d0, d1) and torch.equal(s0, s1)
+
+
 def test_image_mse_and_gradient(R, torch):
     rng = np.random.default_rng(0)
     a = rng.uniform(size=(3, 37, 29, 3)).astype(np.float32)

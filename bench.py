@@ -35,7 +35,7 @@ FWD_FLOP_PER_EVAL = 24     # FP32 ops of one (pixel, Gaussian) compositing evalu
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of this workload at full
 # size; valid only for the kernel source it was taken on (sha1 of csrc/raster.cu).
-MEASURED_TRAFFIC = {("raster_bwd", "c3_fwdbwd_250k"): (802653952 + 55802624, "08427ecce22a76c8c1bbfcb11870e3049777fcd3")}
+MEASURED_TRAFFIC = {("raster_bwd", "c3_fwdbwd_250k"): (802835968 + 55463424, "08dd772fe4b2c75f61bff03c0bce9fa643c87ec1")}
 BWD_FLOP_PER_EVAL = 57     # forward recompute (24) + adjoint arithmetic (33)
 
 
@@ -196,6 +196,18 @@ def oracle_sample(w, n_states=2, n_bands=8, band_rows=2, n_pix=256, seed=0, want
                 "; adjoint (1 thread): fixed part once + %d random pixels extrapolated to %dx%d" % (n_pix, W, H)
                 if want_backward else ""))
     return tot_t / n_states, tot_eval / max(tot_px, 1), threads, desc
+
+
+def t_interval(samples):
+    """Student-t 95% confidence interval of the mean of per-step times (ms),
+    with the sample count; None for fewer than two samples."""
+    x = np.asarray(samples, np.float64)
+    if x.size < 2:
+        return None
+    from scipy import stats
+    h = float(stats.t.ppf(0.975, x.size - 1) * x.std(ddof=1) / np.sqrt(x.size))
+    return {"lo": float(x.mean() - h), "hi": float(x.mean() + h), "n": int(x.size),
+            "what": "rank-local per-step device times of the headline path"}
 
 
 def workload_config(w, ws, views, path):
@@ -584,8 +596,12 @@ def main():
         torch.cuda.synchronize()
         if ws > 1:
             torch.distributed.barrier()
-        total = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(starts, ends)), device=dev)
+        per = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+        step_ms[0] = per
+        total = max_over_ranks(sum(per), device=dev)
         return total / K
+
+    step_ms = [None]
 
     clocks = ClockSampler(local)
     # ---- eager path through the context calls; the library's event profiler
@@ -593,7 +609,9 @@ def main():
     R.reset_kernel_launches()
     R.profile(True)
     eager_ms = timed(lambda: step(states), args.steps)
+    eager_steps = step_ms[0]
     eager_launches = R.kernel_launches()
+    reuse = R.tile_reuse_stats() if not training else None     # the timed steps' distortion pass
     prof = R.profile_read()
     R.profile(False)
 
@@ -629,6 +647,7 @@ def main():
         for _ in range(args.warmup):
             graph.replay()
         graph_ms = timed(graph.replay, args.steps)
+        graph_steps = step_ms[0]
         plan.status()
         launches = launches_per_step * args.steps
     else:
@@ -637,6 +656,7 @@ def main():
     # headline = the faster public path (both are reported)
     use_graph = graph_ms is not None and graph_ms < eager_ms
     ms_per_step = graph_ms if use_graph else eager_ms
+    ci95 = t_interval(graph_steps if use_graph else eager_steps)
     value = ws * S / (ms_per_step / 1e3)
     if training and not use_graph:
         launches = eager_launches
@@ -708,7 +728,7 @@ def main():
         evals_per_launch = evals_per_px * H * W * S
         if not training:
             # tile reuse: only the rendered (state, tile) pairs are raster work
-            pairs, rendered, _ = R.tile_reuse_stats()
+            pairs, rendered, _ = reuse
             launches_per_step = dom_n / max(args.steps, 1)
             evals_per_launch *= (rendered / max(pairs, 1)) / max(launches_per_step, 1.0)
         per_eval = BWD_FLOP_PER_EVAL if dom_name == "raster_bwd" else (
@@ -740,6 +760,7 @@ def main():
             "graph_per_step": None if graph_ms is None else {
                 "ms": graph_ms, "value": ws * S / (graph_ms / 1e3), "unit": UNIT,
                 "what": "capture-safe plan, whole step replayed as one CUDA graph"},
+            "ms_per_step_ci95": ci95,
             "plain_per_state": {"value": plain, "unit": UNIT} if plain else None,
             "batched_vs_plain": (value / ws / plain) if plain else None,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -748,7 +769,7 @@ def main():
             "kernels_note": "per-kernel times from the eager path's live events (same kernels as the graph)",
             "peaks": pk_kind}
     if not training:
-        pairs, rendered, rounds = R.tile_reuse_stats()
+        pairs, rendered, rounds = reuse
         line["tile_reuse"] = {"pairs": pairs, "rendered": rendered, "rounds": rounds,
                               "what": "(state, tile) pairs scored per step and how many were rendered; the rest "
                                       "took the partial of a state with the same depths on every cluster the "

@@ -17,8 +17,9 @@
 // The states of each (view group, tile) are grouped by their depths on the
 // first K clusters of the run (K = 0 first: one group per tile), one member of
 // each group is rendered, and every member that agrees with it on its first
-// m(P) clusters takes its partial; the others are regrouped with K = m(P),
-// which grows every round.  Keys hold up to SHARE_MAX_K = 15 clusters (4 bits
+// m(P) clusters takes its partial; each other member is regrouped with K one
+// past the first cluster where it differs from the rendered one, so K grows
+// every round and groups split no finer than the walks require.  Keys hold up to SHARE_MAX_K = 15 clusters (4 bits
 // each); a state that would need more is rendered on its own.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -266,7 +267,8 @@ __global__ void k_items(const uint32_t *__restrict__ flag, const uint32_t *__res
 
 // After the representatives rendered: each other pair agreeing with its
 // representative on the first m(P) clusters takes the representative's
-// partial; the rest stay pending with K = m(P) (K > 15: rendered alone).
+// partial; the rest stay pending with K = (first cluster where they differ) + 1,
+// which exceeds the group's K (m(P) > 15: rendered alone).
 __global__ void k_share_resolve(const uint32_t *__restrict__ pvt, const uint32_t *__restrict__ pst,
                                 uint8_t *__restrict__ pk, const uint32_t *__restrict__ prep,
                                 const uint32_t *__restrict__ n_dev, uint32_t tiles,
@@ -284,13 +286,20 @@ __global__ void k_share_resolve(const uint32_t *__restrict__ pvt, const uint32_t
         const uint32_t *of = ord_fp + (size_t)vt * SHARE_ORDER;
         int m = 0;
         while (m < SHARE_ORDER && of[m] < P) ++m;
-        bool agree = m <= SHARE_MAX_K;
-        for (int j = 0; agree && j < m; ++j) agree = depth[(size_t)s * C + oc[j]] == depth[(size_t)q * C + oc[j]];
-        if (agree) {
+        if (m > SHARE_MAX_K) {                       // too many clusters reached: render alone
+            pk[i] = (uint8_t)(SHARE_MAX_K + 1);
+            pending[i] = 1;
+            continue;
+        }
+        int j = 0;                                   // first of the m clusters where the depths differ
+        while (j < m && depth[(size_t)s * C + oc[j]] == depth[(size_t)q * C + oc[j]]) ++j;
+        if (j == m) {
             partial[(size_t)s * tiles + tile] = partial[(size_t)q * tiles + tile];
             pending[i] = 0;
         } else {
-            pk[i] = (uint8_t)(m <= SHARE_MAX_K ? m : SHARE_MAX_K + 1);
+            // the group agreed on its first K clusters, so j >= K: regroup one cluster past
+            // the disagreement (the fewest clusters that separate s from q)
+            pk[i] = (uint8_t)(j + 1);
             pending[i] = 1;
         }
     }

@@ -240,26 +240,61 @@ __device__ __forceinline__ void load_depth_row(const uint8_t *depth, int s, int 
     for (int c = threadIdx.x; c < C; c += blockDim.x) sdep[c] = depth[(size_t)s * C + c];
 }
 
-// Stage entries [start, min(start + BATCH, end)) of the tile run unfiltered
-// (every depth variant: the states of a group filter per warp).  Returns nk.
-__device__ __forceinline__ int stage_all(const Rec *__restrict__ recs, const uint32_t *__restrict__ evals,
-                                         uint32_t start, uint32_t end, Staged &sm)
+// Stage entries [start, min(start + BATCH, end)) of the tile run, keeping the
+// variants that at least one of the group's states renders (variant depth ==
+// that state's delivered depth of the cluster), compacted in order.  A view
+// group's run holds every depth variant its states need; dropping the ones no
+// state of this group renders keeps them out of shared memory and out of
+// every warp's list scan.  Returns the kept count.
+template <int G>
+__device__ __forceinline__ int stage_kept(const Rec *__restrict__ recs, const uint32_t *__restrict__ evals,
+                                          const uint8_t (*sdep)[MAX_CLUSTERS], const int (&sid)[G], uint32_t start,
+                                          uint32_t end, Staged &sm)
 {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    bool keep[2];
+    uint32_t slot[2];
+    // the keep decision needs only the record's cluster / depth word; the kept
+    // records are read whole after the compaction (the same lines, from L1)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const int j = h * RT + threadIdx.x;
-        const uint32_t e = start + (uint32_t)j;
+        const uint32_t e = start + (uint32_t)(h * RT + t);
+        keep[h] = false;
+        slot[h] = 0;
         if (e < end) {
-            const uint32_t slot = __ldg(evals + e);
-            const float4 *p = reinterpret_cast<const float4 *>(recs + slot);
-            sm.r0[j] = __ldg(p); sm.r1[j] = __ldg(p + 1);
-            const float4 r2 = __ldg(p + 2);
-            sm.r2[j] = r2;
-            sm.box[j] = unpack_box(r2);
+            slot[h] = __ldg(evals + e);
+            const uint32_t cd = __ldg(reinterpret_cast<const uint32_t *>(recs + slot[h]) + 11);
+            const uint32_t d = (cd >> 12) & 0xfu, c = cd & 0xfffu;
+#pragma unroll
+            for (int g = 0; g < G; ++g) keep[h] |= sid[g] >= 0 && d == (uint32_t)sdep[g][c];
         }
     }
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t b0 = __ballot_sync(0xffffffffu, keep[0]), b1 = __ballot_sync(0xffffffffu, keep[1]);
+    if (lane == 0) { sm.wcnt[0][w] = __popc(b0); sm.wcnt[1][w] = __popc(b1); }
     __syncthreads();
-    return (int)min(end - start, (uint32_t)BATCH);
+    int base0 = 0, tot0 = 0, base1 = 0, tot1 = 0;
+#pragma unroll
+    for (int k = 0; k < RW; ++k) {
+        const int c0 = sm.wcnt[0][k], c1 = sm.wcnt[1][k];
+        base0 += (k < w) ? c0 : 0;
+        tot0 += c0;
+        base1 += (k < w) ? c1 : 0;
+        tot1 += c1;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (!keep[h]) continue;
+        const int pos = h ? tot0 + base1 + __popc(b1 & lt) : base0 + __popc(b0 & lt);
+        const float4 *p = reinterpret_cast<const float4 *>(recs + slot[h]);
+        const float4 r2 = __ldg(p + 2);
+        sm.r0[pos] = __ldg(p);
+        sm.r1[pos] = __ldg(p + 1);
+        sm.r2[pos] = r2;
+        sm.box[pos] = unpack_box(r2);
+    }
+    __syncthreads();
+    return tot0 + tot1;
 }
 
 // Warp w's list of staged entries that state row `dep` renders (variant depth
@@ -289,12 +324,13 @@ __device__ __forceinline__ int warp_list(const Staged &sm, uint8_t *list, int nk
 
 // Persistent forward raster.  Each block repeatedly takes a work item (one
 // tile of one view group and a group of up to G states of that view group),
-// stages the tile's Gaussians once per batch and composites them for every
-// state of the group; items come costliest tile first from an atomic counter.
+// stages the tile's Gaussians once per batch (the variants some state of the
+// group renders) and composites them for every state of the group; items come
+// costliest tile first from an atomic counter.
 // Per pixel and state the arithmetic is composite(), exactly as for a single
 // state, so grouping never changes a bit of the result.
 template <int G, bool WRITE, bool MSE, bool LIST>
-__global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a, WorkQueue q)
+__global__ void __launch_bounds__(RT, G <= 2 ? 8 : 1) k_raster_fwd(RasterArgs a, WorkQueue q)
 {
     __shared__ Staged sm;
     __shared__ uint8_t sdep[G][MAX_CLUSTERS];
@@ -351,7 +387,7 @@ __global__ void __launch_bounds__(RT) k_raster_fwd(RasterArgs a, WorkQueue q)
 #pragma unroll
             for (int g = 0; g < G; ++g) alive |= !(p[g][0].done && p[g][1].done);
             if (__syncthreads_count(alive) == 0) break;
-            const int nk = stage_all(a.recs, a.evals, start, rg.y, sm);
+            const int nk = stage_kept<G>(a.recs, a.evals, sdep, sid, start, rg.y, sm);
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 if (!__any_sync(0xffffffffu, !(p[g][0].done && p[g][1].done))) continue;

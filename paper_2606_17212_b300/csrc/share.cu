@@ -354,11 +354,8 @@ void launch_share_group(const uint2 *seg, uint32_t n_vt, const uint32_t *pvt, co
     k_pair_keys<<<grid_of(n_cap, sms), 256, 0, st>>>(pvt, pst, pk, n_dev, ord_c, depth, C, keys);
     count_launch();
     const size_t smem = SHARE_TABLE * (sizeof(unsigned long long) + sizeof(uint32_t));
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_share_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    // per device, so set on every call (the pass is never captured: it synchronizes)
+    cudaFuncSetAttribute(k_share_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const unsigned g = n_vt < (uint32_t)sms * 4 ? n_vt : (unsigned)sms * 4;
     k_share_group<<<g, 256, smem, st>>>(seg, n_vt, pst, keys, prep);
     count_launch();

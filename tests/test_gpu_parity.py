@@ -184,6 +184,9 @@ def test_tile_reuse_is_bitwise(R, torch, name, scale, n):
     finally:
         R.set_tile_reuse(True)
     m1, p1 = R.state_utility(sc, st, w.cams, w.bg)
+    pairs, rendered, rounds = R.tile_reuse_stats()
+    tiles = -(-w.cams[0].width // 16) * -(-w.cams[0].height // 16)
+    assert pairs == n * tiles and 0 < rendered <= pairs and 1 <= rounds <= 17
     assert torch.equal(m0, m1)
     assert torch.equal(p0.isinf(), p1.isinf()) and torch.equal(p0[~p0.isinf()], p1[~p1.isinf()])
     assert float(m1[2]) == 0.0

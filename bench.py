@@ -502,6 +502,8 @@ def main():
     ap.add_argument("--states", type=int, default=None, help="override the workload's state count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--entry-headroom", type=float, default=1.1,
+                    help="plan path: tile-entry capacity as a multiple of the sizing run's entries")
     ap.add_argument("--loss", default="mse", choices=["mse", "eq2"],
                     help="training loss: mean MSE, or Eq. 2 (MSE + 0.2 (1 - SSIM), CVaR_0.05 tail)")
     args = ap.parse_args()
@@ -620,7 +622,7 @@ def main():
     graph_ms = None
     if training and args.loss == "mse":     # the Eq. 2 objective call is not capture-safe
         plan = dgs.Plan(R, scene, states, w.cams, w.bg, dgs.PLAN_RENDER, ref_index=ref_index,
-                        n_refs=len(views), entry_headroom=1.5)
+                        n_refs=len(views), entry_headroom=args.entry_headroom)
         g_masks = states.masks.clone()
         g_mse = torch.empty(S, dtype=torch.float64, device=dev)
         g_psnr = torch.empty_like(g_mse)

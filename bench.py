@@ -68,6 +68,31 @@ def max_over_ranks(x, device=None):
     return float(t.item())
 
 
+def flat_gradients(grads, device=None):
+    """Place every scene-gradient tensor in one flat buffer (each slice 16-byte
+    aligned) so that data-parallel ranks can sum them with one all-reduce.
+    Returns (views keyed as grads, flat buffer)."""
+    import torch
+    sizes = {k: v.numel() for k, v in grads.items()}
+    pad = lambda n: (n + 3) // 4 * 4
+    flat = torch.zeros(sum(pad(n) for n in sizes.values()), dtype=torch.float32,
+                       device=device if device is not None else next(iter(grads.values())).device)
+    views, off = {}, 0
+    for k, v in grads.items():
+        views[k] = flat[off:off + sizes[k]].view(v.shape)
+        off += pad(sizes[k])
+    return views, flat
+
+
+def reduce_gradients(flat):
+    """Data-parallel training step: each rank's scene gradient covers its own
+    states; their sum over the process group is the gradient of the loss over
+    all ranks' states (one all-reduce; identity without a group)."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(flat, op=dist.ReduceOp.SUM)
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -561,7 +586,8 @@ def main():
         targets = R.render_states_batched(teacher, tv, w.cams, w.bg)
         del teacher
     images = torch.empty((S, H, W, 3), dtype=torch.float32, device=dev)
-    grads = scene.zeros_like_grads()
+    grads, grad_flat = flat_gradients(scene.zeros_like_grads(), device=dev)
+    loss_w = 1.0 / (S * ws)           # mean over the states of every rank
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 126 MB L2
 
     def step(st):
@@ -570,10 +596,10 @@ def main():
             if args.loss == "eq2":
                 mse, _, dL = R.objective(images, targets, ref_index)
             else:
-                mse, _, dL = R.image_mse(images, targets, ref_index, weight=1.0 / S, want_grad=True)
-            for g in grads.values():
-                g.zero_()
+                mse, _, dL = R.image_mse(images, targets, ref_index, weight=loss_w, want_grad=True)
+            grad_flat.zero_()
             R.render_backward(scene, st, w.cams, w.bg, dL, grads, images=images)
+            reduce_gradients(grad_flat)
             return mse
         mse, _ = R.state_utility(scene, st, w.cams, w.bg)
         return mse
@@ -629,10 +655,9 @@ def main():
         g_dL = torch.empty_like(images)
 
         def plan_step():
-            for g in grads.values():
-                g.zero_()
+            grad_flat.zero_()
             plan.render(g_masks, images)
-            plan.image_mse(images, targets, g_mse, g_psnr, g_dL, weight=1.0 / S)
+            plan.image_mse(images, targets, g_mse, g_psnr, g_dL, weight=loss_w)
             plan.backward(g_dL, grads, images=images)
 
         side = torch.cuda.Stream()
@@ -646,9 +671,14 @@ def main():
         with torch.cuda.graph(graph):
             plan_step()
         launches_per_step = R.kernel_launches()
-        for _ in range(args.warmup):
+
+        def graph_step():
             graph.replay()
-        graph_ms = timed(graph.replay, args.steps)
+            reduce_gradients(grad_flat)     # outside the graph: NCCL between ranks
+
+        for _ in range(args.warmup):
+            graph_step()
+        graph_ms = timed(graph_step, args.steps)
         graph_steps = step_ms[0]
         plan.status()
         launches = launches_per_step * args.steps
@@ -671,7 +701,7 @@ def main():
     for _ in range(args.steps):
         if use_graph:
             g_masks.copy_(host_masks, non_blocking=True)
-            graph.replay()
+            graph_step()
             res_host.copy_(g_mse, non_blocking=True)
         else:
             dev_masks = states.masks

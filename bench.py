@@ -348,7 +348,7 @@ def run_mix(args):
     arena = dgs.Arena(R)
     for c in scenes:
         c["plan"] = dgs.Plan(R, c["sc"], c["st"], c["cams"], c["bg"], dgs.PLAN_RENDER, ref_index=c["ridx"],
-                             n_refs=int(c["targets"].shape[0]), entry_headroom=1.5, arena=arena)
+                             n_refs=int(c["targets"].shape[0]), entry_headroom=args.entry_headroom, arena=arena)
         c["g_masks"] = c["st"].masks.clone()
         c["g_mse"] = torch.empty(c["S"], dtype=torch.float64, device=dev)
         c["g_psnr"] = torch.empty_like(c["g_mse"])

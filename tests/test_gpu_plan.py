@@ -99,6 +99,19 @@ def test_plan_utility_and_image_mse(R, torch):
     m_ref, p_ref = R.state_utility(sc, st, w.cams, w.bg)
     assert torch.equal(mse, m_ref) and torch.equal(psnr, p_ref)
     plan.close()
+    # one view, many states: the context call reuses tiles, the plan renders every pair
+    w4 = synth.config("c4_utility_2p7m", scale=0.02, n_states=96)
+    sc4 = dgs.DeviceScene.from_host(w4.scene)
+    st4 = dgs.DeviceStates.from_host(w4.states)
+    plan4 = dgs.Plan(R, sc4, st4, w4.cams, w4.bg, dgs.PLAN_UTILITY)
+    m4 = torch.empty(st4.n, dtype=torch.float64, device="cuda")
+    p4 = torch.empty_like(m4)
+    plan4.utility(st4.masks.clone(), m4, p4)
+    torch.cuda.synchronize()
+    m4_ref, _ = R.state_utility(sc4, st4, w4.cams, w4.bg)
+    assert R.tile_reuse_stats()[2] > 0
+    assert torch.equal(m4, m4_ref)
+    plan4.close()
     # image MSE through a render plan with reference indices
     tv = np.unique(w.states.t)
     ridx = np.searchsorted(tv, w.states.t).astype(np.int32)

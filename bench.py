@@ -35,7 +35,9 @@ FWD_FLOP_PER_EVAL = 24     # FP32 ops of one (pixel, Gaussian) compositing evalu
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of this workload at full
 # size; valid only for the kernel source it was taken on (sha1 of csrc/raster.cu).
-MEASURED_TRAFFIC = {("raster_bwd", "c3_fwdbwd_250k"): (803081216 + 55618560, "5acbed28709477fc5dfed44380ca03cf8fe3bef3")}
+MEASURED_TRAFFIC = {("raster_bwd", "c3_fwdbwd_250k"): (803081216 + 55618560, "5acbed28709477fc5dfed44380ca03cf8fe3bef3"),
+                    # the tile-reuse rounds' launches, averaged (ncu, full size, one pass)
+                    ("raster_fwd_mse_g2", "c4_utility_2p7m"): (201978844, "5acbed28709477fc5dfed44380ca03cf8fe3bef3")}
 BWD_FLOP_PER_EVAL = 57     # forward recompute (24) + adjoint arithmetic (33)
 
 

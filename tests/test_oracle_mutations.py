@@ -72,6 +72,17 @@ MUTATIONS = [
     ("prefix hinge with the wrong orientation (Eq. 2)", PY,
      "            if D[j] > D[i]:\n                M += (D[j] - D[i]) / len(pairs_m)",
      "            if D[i] > D[j]:\n                M += (D[i] - D[j]) / len(pairs_m)"),
+    ("mean and quantile weights swapped in the risk-adjusted utility (Eq. 4)", PY,
+     "((1.0 - alpha) * mean + alpha * quant) / (1.0 + beta * std)",
+     "(alpha * mean + (1.0 - alpha) * quant) / (1.0 + beta * std)"),
+    ("CVaR weight spread over all states instead of the tail (Eq. 2)", PY,
+     "w[top] += lambda_c / k", "w[top] += lambda_c / S"),
+    ("anchor gradient weight (Eq. 2)", PY,
+     "w[s] += anchor_weight / len(anchors)", "w[s] += anchor_weight"),
+    ("SSIM gradient: covariance term halved", PY,
+     "d_exy = 2 * f / a2", "d_exy = f / a2"),
+    ("SSIM gradient: variance term sign", PY,
+     "d_exx = -f / b2", "d_exx = f / b2"),
     ("temporal-change gradient sign (Eq. 2)", PY,
      "            grad[j] += gf\n            grad[i] -= gf",
      "            grad[j] -= gf\n            grad[i] += gf"),

@@ -651,7 +651,7 @@ def test_objective_gradient_finite_differences_and_special_cases():
     refs = rng.uniform(size=(2, H, W, 3))
     ridx = np.array([0, 1, 0, 1, 0, 1])
     imgs = refs[ridx] + rng.normal(0, [0.05, 0.1, 0.2, 0.02, 0.3, 0.15], size=(H, W, 3, S)).transpose(3, 0, 1, 2)
-    kw = dict(pairs_t=[(0, 2), (1, 3)], pairs_m=[(0, 4), (4, 0), (1, 5)], anchors=[3], cvar_q=0.34)
+    kw = dict(pairs_t=[(0, 2), (1, 3)], pairs_m=[(0, 4), (4, 0), (1, 5)], anchors=[3, 5], cvar_q=0.34)
     L, D, grad = oracle.objective(imgs, refs, ridx, **kw)
     assert np.sum(D > D[3]) >= 1
     for idx in [(0, 3, 4, 1), (2, 0, 0, 0), (4, 11, 13, 2), (5, 6, 7, 1), (3, 5, 5, 0)]:
@@ -663,7 +663,7 @@ def test_objective_gradient_finite_differences_and_special_cases():
     M = (max(0, D[4] - D[0]) + max(0, D[0] - D[4]) + max(0, D[5] - D[1])) / 3
     F = np.mean((((imgs[2] - imgs[0]) - (refs[0] - refs[0])) ** 2)) / 2 + \
         np.mean((((imgs[3] - imgs[1]) - (refs[1] - refs[1])) ** 2)) / 2
-    assert L == pytest.approx(D.mean() + 0.30 * cvar + 0.10 * F + 2.0 * M + 0.5 * D[3], rel=1e-12)
+    assert L == pytest.approx(D.mean() + 0.30 * cvar + 0.10 * F + 2.0 * M + 0.5 * (D[3] + D[5]) / 2, rel=1e-12)
     # perfect renders: zero objective, zero gradient
     L0, D0, g0 = oracle.objective(refs[ridx], refs, ridx, **kw)
     assert L0 == 0.0 and np.all(D0 == 0.0) and np.abs(g0).max() < 1e-12   # SSIM is stationary at x = y

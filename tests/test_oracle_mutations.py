@@ -40,6 +40,17 @@ MUTATIONS = [
     ("refinement layers off by one (Section 3)", C,
      "    for (int l = 1; l < d; ++l) {\n        for (int k = 0; k < 3; ++k) { a->mu[k]",
      "    for (int l = 1; l <= d && l < s->n_layers; ++l) {\n        for (int k = 0; k < 3; ++k) { a->mu[k]"),
+    ("opacity clamp of the forward at 0.999 instead of 0.99", C,
+     "        double alpha = araw < 0.99 ? araw : 0.99;\n        if (fabs(araw - 0.99)",
+     "        double alpha = araw < 0.999 ? araw : 0.999;\n        if (fabs(araw - 0.99)"),
+    ("alpha threshold of the forward at 1/128 instead of 1/255", C,
+     "        if (alpha < 1.0 / 255.0) continue;\n        if (edge) mg = 1;",
+     "        if (alpha < 1.0 / 128.0) continue;\n        if (edge) mg = 1;"),
+    ("temporal basis frequency off by one (Eq. 1)", C,
+     "int j = k / 2 + 1;", "int j = k / 2 + 2;"),
+    ("Jacobian clamp factor", C,
+     "double limx = 1.3 * (0.5 * cam->width) / cam->fx, limy = 1.3 * (0.5 * cam->height) / cam->fy;",
+     "double limx = 1.1 * (0.5 * cam->width) / cam->fx, limy = 1.1 * (0.5 * cam->height) / cam->fy;"),
     ("opacity adjoint misses the Gaussian factor", C,
      "g->o += galpha * ex[q];", "g->o += galpha;"),
     ("suffix term of the alpha adjoint not divided by (1 - alpha)", C,

@@ -101,6 +101,21 @@ def test_single_gaussian_centre_pixel_closed_form():
     assert not marg[64, 64]
 
 
+def test_alpha_clamp_and_threshold_closed_forms():
+    """S12: alpha = min(0.99, o e^power) and alpha < 1/255 is skipped.  On a pixel
+    centre (power 0): o = 0.995 composites with alpha 0.99; o = 0.005 (between
+    1/255 and 1/128) composites with alpha o; o = 0.003 (below 1/255) leaves bg."""
+    mu, _, col = _one_gaussian_at_pixel_centre()
+    bg = np.array([0.2, 0.4, 0.1])
+    sig = lambda x: 1.0 / (1.0 + math.exp(-float(np.float32(x))))
+    c = np.array(col, np.float32).astype(np.float64)
+    for o, expect_alpha in [(0.995, 0.99), (0.005, None), (0.003, 0.0)]:
+        sc = tiny_scene(mu, [[-2.5] * 3], [[1, 0, 0, 0]], [logit_of(o)], [col])
+        img, _, _ = oracle.render(sc, np.array([1], np.uint8), 0.0, axis_camera(), bg)
+        a = sig(logit_of(o)) if expect_alpha is None else expect_alpha
+        assert np.allclose(img[64, 64], a * c + (1 - a) * bg, rtol=0, atol=1e-12), o
+
+
 def test_two_gaussians_on_one_ray_closed_form():
     """Front-to-back order by depth, not by index: the nearer one is index 1."""
     o1, o2 = 0.6, 0.8

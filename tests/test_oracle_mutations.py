@@ -51,6 +51,15 @@ MUTATIONS = [
     ("Jacobian clamp factor", C,
      "double limx = 1.3 * (0.5 * cam->width) / cam->fx, limy = 1.3 * (0.5 * cam->height) / cam->fy;",
      "double limx = 1.1 * (0.5 * cam->width) / cam->fx, limy = 1.1 * (0.5 * cam->height) / cam->fy;"),
+    ("conic-to-covariance adjoint sign", C,
+     "for (int c = 0; c < 2; ++c) GS[2 * r + c] = -(QG[2 * r] * Q[c] + QG[2 * r + 1] * Q[2 + c]);",
+     "for (int c = 0; c < 2; ++c) GS[2 * r + c] = (QG[2 * r] * Q[c] + QG[2 * r + 1] * Q[2 + c]);"),
+    ("off-diagonal conic gradient not halved", C,
+     "double G[4] = {g->A, 0.5 * g->B, 0.5 * g->B, g->Cc};", "double G[4] = {g->A, g->B, g->B, g->Cc};"),
+    ("covariance factor gradient missing the factor 2", C,
+     "            gM[3 * r + c] = 2.0 * acc;", "            gM[3 * r + c] = acc;"),
+    ("mean2d adjoint: depth term sign", C,
+     "gp[2] += -g->mx * fx * x / z2 - g->my * fy * y / z2;", "gp[2] += g->mx * fx * x / z2 - g->my * fy * y / z2;"),
     ("opacity adjoint misses the Gaussian factor", C,
      "g->o += galpha * ex[q];", "g->o += galpha;"),
     ("suffix term of the alpha adjoint not divided by (1 - alpha)", C,

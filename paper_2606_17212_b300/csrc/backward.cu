@@ -34,7 +34,9 @@ __device__ __forceinline__ int cluster_of_b(const int32_t *offs, int C, int i)
     return lo;
 }
 
-template <int SH>
+// RK > 0: exactly RK temporal coefficients (the accumulators stay in registers);
+// RK = 0: any rank up to MAX_RANK.
+template <int SH, int RK>
 __global__ void __launch_bounds__(128) k_project_bwd(SceneDev s, const ViewGroup *__restrict__ vgs, int V,
                                                      const uint32_t *__restrict__ need,
                                                      const uint32_t *__restrict__ recBase,
@@ -54,9 +56,11 @@ __global__ void __launch_bounds__(128) k_project_bwd(SceneDev s, const ViewGroup
         acc.logit = 0.0f;
 #pragma unroll
         for (int k = 0; k < NC; ++k) acc.col[k] = 0.0f;
-        float gu[MAX_RANK][3];
+        constexpr int NR = RK > 0 ? RK : MAX_RANK;
+        const int nr = RK > 0 ? RK : min(s.R, MAX_RANK);
+        float gu[NR][3];
 #pragma unroll
-        for (int r = 0; r < MAX_RANK; ++r) gu[r][0] = gu[r][1] = gu[r][2] = 0.0f;
+        for (int r = 0; r < NR; ++r) gu[r][0] = gu[r][1] = gu[r][2] = 0.0f;
         float gm0[3] = {0.0f, 0.0f, 0.0f};    // base-mean gradient through the affine
         bool any = false;
         for (int d = s.L; d >= 1; --d) {
@@ -116,7 +120,9 @@ __global__ void __launch_bounds__(128) k_project_bwd(SceneDev s, const ViewGroup
 #pragma unroll
                     for (int k = 0; k < 3; ++k) g.rec_gmu[(size_t)slot * 3 + k] = gmu[k];
                 }
-                for (int r = 0; r < s.R && r < MAX_RANK; ++r) {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    if (r >= nr) break;
                     const float bk = temporal_basis(r, vg.time);
 #pragma unroll
                     for (int k = 0; k < 3; ++k) gu[r][k] = fmaf(bk, gmu[k], gu[r][k]);
@@ -152,9 +158,12 @@ __global__ void __launch_bounds__(128) k_project_bwd(SceneDev s, const ViewGroup
             }
         }
         if (any) {
-            for (int r = 0; r < s.R && r < MAX_RANK; ++r)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                if (r >= nr) break;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) g.u[((size_t)r * s.n + i) * 3 + k] += gu[r][k];
+            }
         }
     }
 }
@@ -257,8 +266,11 @@ void launch_project_bwd(const SceneDev &s, const ViewGroup *vgs, int V, const ui
     if (b > (long long)sms * 32) b = (long long)sms * 32;
     {
         ProfScope ps_("project_bwd", st);
-        if (s.sh == 0) k_project_bwd<0><<<(unsigned)b, 128, 0, st>>>(s, vgs, V, need, recBase, rec_grad, g);
-        else k_project_bwd<3><<<(unsigned)b, 128, 0, st>>>(s, vgs, V, need, recBase, rec_grad, g);
+        // the workloads' rank-2 temporal bases take the specialised kernels
+        if (s.sh == 0 && s.R == 2) k_project_bwd<0, 2><<<(unsigned)b, 128, 0, st>>>(s, vgs, V, need, recBase, rec_grad, g);
+        else if (s.sh == 0) k_project_bwd<0, 0><<<(unsigned)b, 128, 0, st>>>(s, vgs, V, need, recBase, rec_grad, g);
+        else if (s.R == 2) k_project_bwd<3, 2><<<(unsigned)b, 128, 0, st>>>(s, vgs, V, need, recBase, rec_grad, g);
+        else k_project_bwd<3, 0><<<(unsigned)b, 128, 0, st>>>(s, vgs, V, need, recBase, rec_grad, g);
         count_launch();
     }
     if (s.res_mode == 2 && s.L > 1) {

@@ -543,7 +543,7 @@ int fwd_pass(dgs_ctx *ctx, const dgs_scene *scene, const Plan &p, const Lists &L
                                         a.images != nullptr, a.refs != nullptr, maxper};
     auto it = ctx->tuned_G.find(key);
     if (it != ctx->tuned_G.end()) return launch_fwd_pass(ctx, p, L, a, s0, s1, it->second, st);
-    const int cands[4] = {1, 2, 4, 8};
+    const int cands[1] = {1};
     int best = 1;
     float best_ms = 1e30f;
     cudaEvent_t e0, e1;
@@ -1066,7 +1066,7 @@ int shared_mse_pass(dgs_ctx *ctx, const dgs_scene *scene, const Plan &p, const L
 {
     const uint32_t T = p.tiles, nvt = (uint32_t)((size_t)p.V * T);
     const int C = scene->n_clusters;
-    const int G = 2;
+    const int G = 1;
     // states of each view group, in state order; pairs per view-group tile
     std::vector<int32_t> cnt(p.V, 0), vg_first(p.V + 1, 0), order(p.S_user);
     for (int s = 0; s < p.S_user; ++s) ++cnt[p.vg_of_state[s]];

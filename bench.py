@@ -281,6 +281,7 @@ def run_mix(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     R = dgs.Renderer(0)
+    R.set_tile_size(args.tile_size)
     specs = synth.mix_specs(scale=args.scale)
     scenes = []
     t_gen = time.perf_counter()
@@ -468,6 +469,7 @@ def run_groups(args):
     G = len(groups)
     states = synth.States(ctx, np.full(G * M, 0.25, np.float32), np.zeros(G * M, np.int32))
     R = dgs.Renderer(0)
+    R.set_tile_size(args.tile_size)
     scene = dgs.DeviceScene.from_host(sc_h, device=dev)
     dst = dgs.DeviceStates.from_host(states)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -529,6 +531,8 @@ def main():
     ap.add_argument("--states", type=int, default=None, help="override the workload's state count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--tile-size", type=int, default=0, choices=[0, 16, 32],
+                    help="sort tile side (0: the library chooses per batch shape)")
     ap.add_argument("--entry-headroom", type=float, default=1.1,
                     help="plan path: tile-entry capacity as a multiple of the sizing run's entries")
     ap.add_argument("--loss", default="mse", choices=["mse", "eq2"],
@@ -570,6 +574,7 @@ def main():
     w.states.masks = rank_states(w, rank)
 
     R = dgs.Renderer(local)
+    R.set_tile_size(args.tile_size)
     scene = dgs.DeviceScene.from_host(w.scene, device=dev)
     states = dgs.DeviceStates.from_host(w.states)
     S = states.n

@@ -228,6 +228,17 @@ DGS_API int dgs_state_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_st
  */
 DGS_API int dgs_set_tile_reuse(dgs_ctx *ctx, int enable);
 
+/* Side of the square sort tiles that binning, the tile sort and the tile
+ * ranges use (an acceleration structure: images, squared errors and
+ * gradients are bit-identical for every size, because a Gaussian's footprint
+ * is a per-pixel test and every sum runs over fixed 16 x 16 pixel blocks).
+ * Larger tiles give fewer (tile, Gaussian) entries to sort; raster warps then
+ * walk the longer run of their tile for their own 16-pixel-wide region.
+ * size: 16 or 32, or 0 to let the library choose per batch shape.  Applies to
+ * the calls and plans made after it.  Returns DGS_E_INVALID_ARG for a null
+ * ctx or another size. */
+DGS_API int dgs_set_tile_size(dgs_ctx *ctx, int size);
+
 /*
  * Work of the context's last distortion pass: pairs [host] = (state, tile)
  * pairs it scored, rendered [host] = pairs it rendered (the rest took a

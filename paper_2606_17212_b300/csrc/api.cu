@@ -77,6 +77,16 @@ struct Plan {
     int V = 0;
     int W = 0, H = 0, tiles_x = 0, tiles_y = 0;
     uint32_t tiles = 0;
+    int tile_shift = 4;                  // sort tiles of 2^tile_shift pixels
+    int blocks_x = 0, blocks_y = 0;      // 16 x 16 pixel blocks (squared-error partials)
+    uint32_t blocks = 0;
+    TileGeom geom() const
+    {
+        TileGeom g;
+        g.tiles_x = tiles_x; g.tiles_y = tiles_y; g.tile_shift = tile_shift;
+        g.blocks_x = blocks_x; g.blocks_y = blocks_y; g.tiles = tiles; g.blocks = blocks;
+        return g;
+    }
     std::vector<int32_t> vg_of_state;
     std::vector<ViewGroup> vgs;
 };
@@ -111,6 +121,9 @@ struct dgs_ctx {
         pairm, grp, gmse, omaps, opart, otpart, oD, oweight, oints, recgmu, gqws,
         shord, shpair, shpair2, shrep, shflag, shpos, shlist, shitem, shkey, shstop, shseg, shcnt, shtab;
     bool tile_reuse = true;        // utility passes reuse rendered tiles across states (share.cu)
+    int tile_size = 0;             // sort tile side in pixels: 16 or 32, or 0 (chosen per batch shape)
+    int active_shift = 4;          // tile shift of the call in progress when tile_size is 0
+    std::map<std::vector<long long>, int> tuned_tile;   // autotuner: call shape -> tile shift
     long long reuse_pairs = 0, reuse_rendered = 0;   // last distortion pass: (state, tile) pairs, rendered
     int reuse_rounds = 0;
     std::map<std::vector<long long>, int> tuned_G;   // autotuner: call shape -> states per block
@@ -235,9 +248,14 @@ int build_plan(dgs_ctx *ctx, const dgs_states *st, const dgs_camera *cams, int n
     p = Plan();
     p.S_user = st->n_states;
     p.W = W; p.H = H;
-    p.tiles_x = (W + TILE - 1) / TILE;
-    p.tiles_y = (H + TILE - 1) / TILE;
+    p.tile_shift = ctx->tile_size == 32 ? 5 : ctx->tile_size == 16 ? 4 : ctx->active_shift;
+    const int T = 1 << p.tile_shift;
+    p.tiles_x = (W + T - 1) / T;
+    p.tiles_y = (H + T - 1) / T;
     p.tiles = (uint32_t)p.tiles_x * (uint32_t)p.tiles_y;
+    p.blocks_x = (W + BLOCK - 1) / BLOCK;
+    p.blocks_y = (H + BLOCK - 1) / BLOCK;
+    p.blocks = (uint32_t)p.blocks_x * (uint32_t)p.blocks_y;
     std::map<std::pair<int, uint32_t>, int> groups;
     p.vg_of_state.resize(st->n_states);
     for (int s = 0; s < st->n_states; ++s) {
@@ -268,7 +286,7 @@ int build_plan(dgs_ctx *ctx, const dgs_states *st, const dgs_camera *cams, int n
     }
     p.V = (int)p.vgs.size();
     if (p.V > 32767) return fail(ctx, DGS_E_UNSUPPORTED, "more than 32767 distinct (camera, time) pairs");
-    if ((unsigned long long)(st->n_states + (add_refs ? p.V : 0)) * p.tiles >= 0x7fffffffull)
+    if ((unsigned long long)(st->n_states + (add_refs ? p.V : 0)) * p.blocks * 8ull >= 0x7fffffffull)
         return fail(ctx, DGS_E_CAPACITY, "states x tiles exceeds the launch grid");
     if ((unsigned long long)p.V * p.tiles >= 0xffffffffull)
         return fail(ctx, DGS_E_CAPACITY, "view groups x tiles exceeds 32 bits");
@@ -355,7 +373,8 @@ int prepare(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *masks, const P
     out.depth_keys = alt ? (uint32_t *)ctx->k1.p : (uint32_t *)ctx->k0.p;
     out.depth_slots = (uint32_t *)order;
     if (nRec > 0)
-        launch_tile_count((const Rec *)ctx->recs.p, order, nRec, p.tiles_x, p.tiles, (uint32_t *)ctx->tcount.p,
+        launch_tile_count((const Rec *)ctx->recs.p, order, nRec, p.tiles_x, p.tiles, p.tile_shift,
+                          (uint32_t *)ctx->tcount.p,
                           (uint4 *)ctx->bins.p, ctx->sms, st);
     CK(exclusive_scan_u32((const uint32_t *)ctx->tcount.p, (uint32_t *)ctx->toffs.p, nRec,
                           (uint32_t *)ctx->total.p + 1, ctx->scanws.p, st));
@@ -406,6 +425,7 @@ RasterArgs raster_args(dgs_ctx *ctx, const Plan &p, int C, const float *bg, uint
     a.depth = (const uint8_t *)ctx->depth.p;
     a.vg_of_state = (const int32_t *)ctx->vgos.p;
     a.S = p.S_user; a.C = C; a.W = p.W; a.H = p.H; a.tiles_x = p.tiles_x; a.tiles = p.tiles;
+    a.tile_shift = p.tile_shift; a.blocks_x = p.blocks_x; a.blocks = p.blocks;
     a.bg0 = bg[0]; a.bg1 = bg[1]; a.bg2 = bg[2];
     a.images = nullptr; a.refs = nullptr; a.ref_of_state = nullptr; a.partial = nullptr;
     a.img_s0 = 0;
@@ -565,6 +585,64 @@ int fwd_pass(dgs_ctx *ctx, const dgs_scene *scene, const Plan &p, const Lists &L
     return DGS_OK;
 }
 
+// ------------------------------------------------------------ tile-size autotuner
+// The sort tile size (16 or 32 px) changes no output bit, only the cost split
+// between sorting (fewer, larger tiles: fewer entries) and rasterization
+// (longer runs to walk per 16-pixel-wide region).  Unless the caller fixed it,
+// the first call of each shape runs once per candidate, timed with events on
+// its stream, and the faster size is kept for that shape in this context.
+enum { TUNE_RENDER = 1, TUNE_UTILITY = 2 };
+
+std::vector<long long> tile_key(int kind, const dgs_scene *scene, const dgs_states *states, const dgs_camera *cams,
+                                int n_cams)
+{
+    return {kind, cams && n_cams > 0 ? cams[0].width : 0, cams && n_cams > 0 ? cams[0].height : 0,
+            states ? states->n_states : 0, n_cams, scene->n, scene->n_clusters, scene->n_layers, scene->sh_degree,
+            scene->temporal_rank};
+}
+
+// Shift for a call of shape `key`: fixed by the caller, cached, or -1 (not tuned yet).
+int known_shift(const dgs_ctx *ctx, const std::vector<long long> &key)
+{
+    if (ctx->tile_size) return ctx->tile_size == 32 ? 5 : 4;
+    auto it = ctx->tuned_tile.find(key);
+    return it == ctx->tuned_tile.end() ? -1 : it->second;
+}
+
+// Run call() (int(void)) with the tuned tile size of its shape, tuning it
+// first if needed.  Every run writes the same outputs; the chosen size runs
+// last, so the context's state (the lists a backward can reuse) is its.
+template <class F>
+int tuned_call(dgs_ctx *ctx, const std::vector<long long> &key, cudaStream_t st, F call)
+{
+    const int known = known_shift(ctx, key);
+    if (known >= 0) {
+        ctx->active_shift = known;
+        return call();
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int best = MIN_TILE_SHIFT, last = -1, r = DGS_OK;
+    float best_ms = 1e30f;
+    for (int sh = MIN_TILE_SHIFT; sh <= MAX_TILE_SHIFT && r == DGS_OK; ++sh) {
+        ctx->active_shift = last = sh;
+        CK(cudaEventRecord(e0, st));
+        r = call();
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) { best_ms = ms; best = sh; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != DGS_OK) return r;
+    ctx->tuned_tile[key] = best;
+    ctx->active_shift = best;
+    return best == last ? DGS_OK : call();
+}
+
 int render_batched(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states, const dgs_camera *cams,
                    int n_cams, const float *bg, float *images, cudaStream_t st)
 {
@@ -658,7 +736,8 @@ int prepare_dev(dgs_plan *P, const uint32_t *masks, bool force_full, cudaStream_
     Lists &out = P->L;
     out.depth_keys = alt ? (uint32_t *)ctx->k1.p : (uint32_t *)ctx->k0.p;
     out.depth_slots = (uint32_t *)order;
-    launch_tile_count((const Rec *)ctx->recs.p, order, P->R_cap, p.tiles_x, p.tiles, (uint32_t *)ctx->tcount.p,
+    launch_tile_count((const Rec *)ctx->recs.p, order, P->R_cap, p.tiles_x, p.tiles, p.tile_shift,
+                      (uint32_t *)ctx->tcount.p,
                       (uint4 *)ctx->bins.p, ctx->sms, st, cnt + 0);
     CK(exclusive_scan_u32((const uint32_t *)ctx->tcount.p, (uint32_t *)ctx->toffs.p, P->R_cap, cnt + 1,
                           ctx->scanws.p, st));
@@ -832,7 +911,10 @@ int dgs_render_states_batched(dgs_ctx *ctx, const dgs_scene *scene, const dgs_st
 {
     if (!ctx) return DGS_E_INVALID_ARG;
     CK(cudaSetDevice(ctx->device));
-    return render_batched(ctx, scene, states, cams, n_cams, bg, images, (cudaStream_t)stream);
+    TRY(check_scene(ctx, scene));
+    if (!states) return fail(ctx, DGS_E_INVALID_ARG, "states is null");
+    return tuned_call(ctx, tile_key(TUNE_RENDER, scene, states, cams, n_cams), (cudaStream_t)stream,
+                      [&] { return render_batched(ctx, scene, states, cams, n_cams, bg, images, (cudaStream_t)stream); });
 }
 
 int dgs_render_state(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *mask, float t, const dgs_camera *cam,
@@ -844,7 +926,9 @@ int dgs_render_state(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *mask,
     const int32_t cam0 = 0;
     dgs_states s;
     s.masks = mask; s.t = &t; s.cam = &cam0; s.n_states = 1;
-    return render_batched(ctx, scene, &s, cam, 1, bg, image, (cudaStream_t)stream);
+    TRY(check_scene(ctx, scene));
+    return tuned_call(ctx, tile_key(TUNE_RENDER, scene, &s, cam, 1), (cudaStream_t)stream,
+                      [&] { return render_batched(ctx, scene, &s, cam, 1, bg, image, (cudaStream_t)stream); });
 }
 
 int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states, const dgs_camera *cams,
@@ -856,6 +940,11 @@ int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *
     cudaStream_t st = (cudaStream_t)stream;
     TRY(check_scene(ctx, scene));
     if (!bg || !grads) return fail(ctx, DGS_E_INVALID_ARG, "bg or grads is null");
+    if (!states) return fail(ctx, DGS_E_INVALID_ARG, "states is null");
+    {   // the tile size the forward of this shape used (any size gives the same gradients)
+        const int known = known_shift(ctx, tile_key(TUNE_RENDER, scene, states, cams, n_cams));
+        ctx->active_shift = known >= 0 ? known : (ctx->tape.valid ? ctx->tape.plan.tile_shift : MIN_TILE_SHIFT);
+    }
     Plan p;
     TRY(build_plan(ctx, states, cams, n_cams, false, p));
     if (p.S_user == 0 || scene->n == 0) return DGS_OK;
@@ -866,7 +955,7 @@ int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *
         (scene->n_layers > 1 && scene->res_mode == 2 && !grads->res_step))
         return fail(ctx, DGS_E_INVALID_ARG, "gradient array is null");
     Lists L;
-    if (same_call(ctx->tape, scene, states, cams, n_cams)) {
+    if (same_call(ctx->tape, scene, states, cams, n_cams) && ctx->tape.plan.tile_shift == p.tile_shift) {
         L = ctx->tape.lists;
     } else {
         ctx->tape.valid = false;
@@ -909,7 +998,9 @@ int dgs_state_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *st
     CK(cudaSetDevice(ctx->device));
     TRY(check_scene(ctx, scene));
     if (!bg) return fail(ctx, DGS_E_INVALID_ARG, "bg is null");
-    return utility_pass(ctx, scene, states, cams, n_cams, bg, mse, psnr, (cudaStream_t)stream);
+    if (!states) return fail(ctx, DGS_E_INVALID_ARG, "states is null");
+    return tuned_call(ctx, tile_key(TUNE_UTILITY, scene, states, cams, n_cams), (cudaStream_t)stream,
+                      [&] { return utility_pass(ctx, scene, states, cams, n_cams, bg, mse, psnr, (cudaStream_t)stream); });
 }
 
 int dgs_group_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *contexts, const int32_t *groups,
@@ -959,7 +1050,8 @@ int dgs_group_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *co
     s2.t = t2.data();
     s2.cam = c2.data();
     s2.n_states = (int)(2 * GM);
-    TRY(utility_pass(ctx, scene, &s2, cams, n_cams, bg, (double *)ctx->gmse.p, nullptr, st));
+    TRY(tuned_call(ctx, tile_key(TUNE_UTILITY, scene, &s2, cams, n_cams), st,
+                   [&] { return utility_pass(ctx, scene, &s2, cams, n_cams, bg, (double *)ctx->gmse.p, nullptr, st); }));
     launch_group_stats((const double *)ctx->gmse.p, G, M, alpha, beta, q, delta, stats, st);
     CK(cudaGetLastError());
     return DGS_OK;
@@ -1175,7 +1267,7 @@ int shared_mse_pass(dgs_ctx *ctx, const dgs_scene *scene, const Plan &p, const L
             launch_raster_fwd(a, q, G, blocks, st);
         }
         // everyone else: take the representative's partial, or regroup
-        launch_share_resolve(pvt, pst, pk, prep, dcnt + 0, n, T, ord_c, ord_fp, depth, C, a.stop, a.partial, flag,
+        launch_share_resolve(pvt, pst, pk, prep, dcnt + 0, n, p.geom(), ord_c, ord_fp, depth, C, a.stop, a.partial, flag,
                              ctx->sms, st);
         CK(exclusive_scan_u32(flag, pos, n, dcnt + 3, ctx->scanws.p, st));
         launch_compact_pairs(flag, pos, dcnt + 0, n, pvt, pst, pk, nvt_a, nst, nk, ctx->sms, st);
@@ -1204,7 +1296,7 @@ int utility_pass(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states,
     uint32_t *sorted = L.evals;
     const size_t img = (size_t)p.W * p.H * 3;
     TRY(ensure(ctx, ctx->refs, sizeof(float) * img * (size_t)p.V, st));
-    TRY(ensure(ctx, ctx->partial, sizeof(double) * (size_t)p.S_user * p.tiles, st));
+    TRY(ensure(ctx, ctx->partial, sizeof(double) * (size_t)p.S_user * p.blocks, st));
     // complete renders of every view group (appended states S_user .. S-1)
     RasterArgs r = raster_args(ctx, p, scene->n_clusters, bg, sorted);
     r.images = (float *)ctx->refs.p;
@@ -1227,7 +1319,7 @@ int utility_pass(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states,
         ctx->reuse_rounds = 0;
         TRY(fwd_pass(ctx, scene, p, L, a, 0, p.S_user, st));
     }
-    launch_mse_reduce((const double *)ctx->partial.p, p.S_user, (int)p.tiles, 1.0 / (double)img, mse, psnr, st);
+    launch_mse_reduce((const double *)ctx->partial.p, p.S_user, (int)p.blocks, 1.0 / (double)img, mse, psnr, st);
     CK(cudaGetLastError());
     return DGS_OK;
 }
@@ -1263,6 +1355,14 @@ int dgs_set_tile_reuse(dgs_ctx *ctx, int enable)
 {
     if (!ctx) return DGS_E_INVALID_ARG;
     ctx->tile_reuse = enable != 0;
+    return DGS_OK;
+}
+
+int dgs_set_tile_size(dgs_ctx *ctx, int size)
+{
+    if (!ctx) return DGS_E_INVALID_ARG;
+    if (size != 0 && size != 16 && size != 32) return fail(ctx, DGS_E_INVALID_ARG, "tile size must be 0, 16 or 32");
+    ctx->tile_size = size;
     return DGS_OK;
 }
 
@@ -1341,6 +1441,30 @@ int dgs_plan_create(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *stat
     TRY(check_scene(ctx, scene));
     if (!bg) return fail(ctx, DGS_E_INVALID_ARG, "bg is null");
     if (mode != DGS_PLAN_RENDER && mode != DGS_PLAN_UTILITY) return fail(ctx, DGS_E_INVALID_ARG, "bad plan mode");
+    if (!states) return fail(ctx, DGS_E_INVALID_ARG, "states is null");
+    {   // the tile size of this shape: fixed, tuned by earlier calls, or tuned now by the same context call
+        const auto key = tile_key(mode == DGS_PLAN_RENDER ? TUNE_RENDER : TUNE_UTILITY, scene, states, cams, n_cams);
+        if (known_shift(ctx, key) < 0 && states->n_states > 0 && cams && n_cams > 0) {
+            const size_t img = (size_t)cams[0].width * cams[0].height * 3;
+            void *tmp = nullptr;
+            const size_t bytes = mode == DGS_PLAN_RENDER ? sizeof(float) * img * (size_t)states->n_states
+                                                         : sizeof(double) * (size_t)states->n_states;
+            if (cudaMalloc(&tmp, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(ctx, DGS_E_OOM, "plan tuning buffer");
+            }
+            const int rt = tuned_call(ctx, key, 0, [&] {
+                return mode == DGS_PLAN_RENDER
+                           ? render_batched(ctx, scene, states, cams, n_cams, bg, (float *)tmp, 0)
+                           : utility_pass(ctx, scene, states, cams, n_cams, bg, (double *)tmp, nullptr, 0);
+            });
+            CK(cudaDeviceSynchronize());
+            cudaFree(tmp);
+            if (rt != DGS_OK) return rt;
+        }
+        const int sh = known_shift(ctx, key);
+        ctx->active_shift = sh >= 0 ? sh : MIN_TILE_SHIFT;
+    }
     Plan p;
     TRY(build_plan(ctx, states, cams, n_cams, mode == DGS_PLAN_UTILITY, p));
     if (p.S_user < 1) return fail(ctx, DGS_E_INVALID_ARG, "a plan needs at least one state");
@@ -1412,7 +1536,7 @@ int dgs_plan_create(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *stat
         const size_t img = (size_t)p.W * p.H * 3;
         if (mode == DGS_PLAN_UTILITY) {
             if ((r = ensure(w, w->refs, sizeof(float) * img * p.V, st)) != DGS_OK) break;
-            if ((r = ensure(w, w->partial, sizeof(double) * (size_t)p.S_user * p.tiles, st)) != DGS_OK) break;
+            if ((r = ensure(w, w->partial, sizeof(double) * (size_t)p.S_user * p.blocks, st)) != DGS_OK) break;
         }
         if (ref_index) {
             P->n_refs = n_refs;
@@ -1420,7 +1544,7 @@ int dgs_plan_create(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *stat
             if ((r = ensure(own, own->refidx, 4 * (size_t)p.S_user, st)) != DGS_OK) break;
             CK(cudaMemcpy(own->refidx.p, ref_index, 4 * (size_t)p.S_user, cudaMemcpyHostToDevice));
             if ((r = ensure(w, w->partial, sizeof(double) * (size_t)p.S_user *
-                                               std::max<size_t>(P->image_parts, p.tiles), st)) != DGS_OK) break;
+                                               std::max<size_t>(P->image_parts, p.blocks), st)) != DGS_OK) break;
         }
         // Growing the workspace above reallocated buffers the sizing run's lists
         // point into: prepare again so every list lives in the final buffers,
@@ -1562,7 +1686,7 @@ int dgs_plan_utility(dgs_plan *P, const uint32_t *masks, double *mse, double *ps
     a.ref_of_state = (const int32_t *)P->ws.vgos.p;
     a.partial = (double *)ctx->partial.p;
     TRY(launch_queue(ctx, P->p, P->L, a, P->tfwd, st));
-    launch_mse_reduce((const double *)ctx->partial.p, P->p.S_user, (int)P->p.tiles,
+    launch_mse_reduce((const double *)ctx->partial.p, P->p.S_user, (int)P->p.blocks,
                       1.0 / (double)((size_t)P->p.W * P->p.H * 3), mse, psnr, st);
     CK(cudaGetLastError());
     return DGS_OK;

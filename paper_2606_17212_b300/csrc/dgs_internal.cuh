@@ -12,6 +12,7 @@
 //                          tile key, tile columns, slot): the entries' source
 //   entries [nEnt]  u32 key (v * tiles + tile), u32 value (record slot)
 //   ranges  [V*T]   uint2  [start, end) of each (view group, tile) run
+//   partial [S][B]  f64    squared-error partial of each state and 16x16 pixel block
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -20,8 +21,28 @@
 
 namespace dgs {
 
-constexpr int TILE = 16;                 // tile side in pixels
-constexpr int TILE_PIX = TILE * TILE;    // threads per raster block
+// Sort tiles (the unit of binning, sorting and tile ranges) are 2^tile_shift
+// pixels square, tile_shift 4 or 5 (16 or 32 px), chosen per batch.  Raster
+// warps work on 16-pixel-wide regions inside a tile, and per-state squared-
+// error partials are kept per BLOCK x BLOCK pixel block of the image whatever
+// the tile size, so every tile size gives the same bits.
+constexpr int BLOCK = 16;                // pixel block of the squared-error partials; raster region width
+constexpr int MIN_TILE_SHIFT = 4, MAX_TILE_SHIFT = 5;
+
+// Tile and block grids of one image size.
+struct TileGeom {
+    int tiles_x, tiles_y, tile_shift;    // sort tiles of 2^tile_shift pixels
+    int blocks_x, blocks_y;              // 16 x 16 pixel blocks
+    uint32_t tiles, blocks;
+};
+// The 16 x 16 pixel blocks of sort tile `tile`: columns [bx0, bx1), rows [by0, by1).
+__host__ __device__ inline void tile_blocks(const TileGeom &g, uint32_t tile, int &bx0, int &bx1, int &by0, int &by1)
+{
+    const int r = 1 << (g.tile_shift - 4), tx = (int)(tile % (uint32_t)g.tiles_x), ty = (int)(tile / (uint32_t)g.tiles_x);
+    bx0 = tx * r; by0 = ty * r;
+    bx1 = bx0 + r < g.blocks_x ? bx0 + r : g.blocks_x;
+    by1 = by0 + r < g.blocks_y ? by0 + r : g.blocks_y;
+}
 constexpr int MAX_CLUSTERS = 1024;
 constexpr int MAX_LAYERS = 8;
 

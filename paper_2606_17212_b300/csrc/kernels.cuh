@@ -17,7 +17,8 @@ void launch_project(const SceneDev &s, const ViewGroup *vgs, int V, const uint32
 // counts [n] tiles per depth-ordered record; bins [n] its tile rectangle
 // (radix_sort_entries)
 void launch_tile_count(const Rec *recs, const uint32_t *order, uint32_t n, int tiles_x, uint32_t tiles,
-                       uint32_t *counts, uint4 *bins, int sms, cudaStream_t st, const uint32_t *n_dev = nullptr);
+                       int tile_shift, uint32_t *counts, uint4 *bins, int sms, cudaStream_t st,
+                       const uint32_t *n_dev = nullptr);
 void launch_clamp_count(const uint32_t *total, uint32_t cap, uint32_t *out, uint32_t *flags, cudaStream_t st);
 void launch_ranges(const uint32_t *keys, uint32_t n, uint2 *ranges, int sms, cudaStream_t st,
                    const uint32_t *n_dev = nullptr);
@@ -31,11 +32,14 @@ struct RasterArgs {
     const int32_t *vg_of_state;   // [S]
     int S, C, W, H, tiles_x;
     uint32_t tiles;
+    int tile_shift;               // sort tiles are 2^tile_shift pixels square
+    int blocks_x;                 // 16 x 16 pixel blocks per image row (squared-error partials)
+    uint32_t blocks;              // blocks per image
     float bg0, bg1, bg2;
     float *images;                // [S][H][W][3] or null
     const float *refs;            // [n_refs][H][W][3] or null (MSE epilogue)
     const int32_t *ref_of_state;  // [S]
-    double *partial;              // [S][tiles] FP64 squared-error partial sums
+    double *partial;              // [S][blocks] FP64 squared-error partial sums per 16 x 16 pixel block
     int img_s0;                   // images hold states img_s0, img_s0 + 1, ...
     uint32_t *stop;               // [S][tiles] or null: run prefix staged while the state had a live pixel
 };
@@ -125,7 +129,7 @@ void launch_item_lists(const uint32_t *lvt, const uint2 *seg, const uint32_t *n_
                        uint32_t *flag, uint32_t *pos, uint32_t *n_items_dev, void *scan_ws, uint32_t *item_first,
                        uint32_t *item_count, int sms, cudaStream_t st);
 void launch_share_resolve(const uint32_t *pvt, const uint32_t *pst, uint8_t *pk, const uint32_t *prep,
-                          const uint32_t *n_dev, size_t n_cap, uint32_t tiles, const uint32_t *ord_c,
+                          const uint32_t *n_dev, size_t n_cap, const TileGeom &geo, const uint32_t *ord_c,
                           const uint32_t *ord_fp, const uint8_t *depth, int C, const uint32_t *stop,
                           double *partial, uint32_t *pending, int sms, cudaStream_t st);
 

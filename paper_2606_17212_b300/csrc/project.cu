@@ -138,12 +138,12 @@ __device__ __forceinline__ float4 rec_tail(const Rec *recs, uint32_t slot)
     return __ldg(reinterpret_cast<const float4 *>(recs + slot) + 2);
 }
 
-__device__ __forceinline__ uint32_t rec_tiles(const float4 &q)
+__device__ __forceinline__ uint32_t rec_tiles(const float4 &q, int shift)
 {
     const uint32_t bx = __float_as_uint(q.y), by = __float_as_uint(q.z), cd = __float_as_uint(q.w);
     const int xlo = bx & 0xffff, xhi = bx >> 16, ylo = by & 0xffff, yhi = by >> 16;
     if ((cd & 0xf000u) == 0 || xlo > xhi || ylo > yhi) return 0;
-    return (uint32_t)((xhi / TILE - xlo / TILE + 1) * (yhi / TILE - ylo / TILE + 1));
+    return (uint32_t)(((xhi >> shift) - (xlo >> shift) + 1) * ((yhi >> shift) - (ylo >> shift) + 1));
 }
 
 __device__ __forceinline__ uint32_t live_n(uint32_t n_cap, const uint32_t *n_dev)
@@ -156,7 +156,7 @@ __device__ __forceinline__ uint32_t live_n(uint32_t n_cap, const uint32_t *n_dev
 // record's tile rectangle (first tile key, tile columns, slot) in the same
 // order, the source the tile sort generates the entries from.
 __global__ void k_tile_count(const Rec *__restrict__ recs, const uint32_t *__restrict__ order, uint32_t n_cap,
-                             const uint32_t *__restrict__ n_dev, int tiles_x, uint32_t tiles,
+                             const uint32_t *__restrict__ n_dev, int tiles_x, uint32_t tiles, int shift,
                              uint32_t *__restrict__ counts, uint4 *__restrict__ bins)
 {
     const uint32_t n = live_n(n_cap, n_dev);
@@ -176,12 +176,12 @@ __global__ void k_tile_count(const Rec *__restrict__ recs, const uint32_t *__res
         for (int k = 0; k < 4; ++k) {
             const uint32_t j = j0 + (uint32_t)k * T;
             if (j >= n_cap) continue;
-            const uint32_t c = slot[k] != 0xffffffffu ? rec_tiles(q[k]) : 0u;
+            const uint32_t c = slot[k] != 0xffffffffu ? rec_tiles(q[k], shift) : 0u;
             counts[j] = c;
             if (c) {
                 const uint32_t bx = __float_as_uint(q[k].y), by = __float_as_uint(q[k].z);
-                const uint32_t tx0 = (bx & 0xffffu) / TILE, ty0 = (by & 0xffffu) / TILE;
-                const uint32_t tw = (bx >> 16) / TILE - tx0 + 1u;
+                const uint32_t tx0 = (bx & 0xffffu) >> shift, ty0 = (by & 0xffffu) >> shift;
+                const uint32_t tw = ((bx >> 16) >> shift) - tx0 + 1u;
                 const uint32_t vbase = ((__float_as_uint(q[k].w) >> 16) & 0x7fffu) * tiles;
                 bins[j] = make_uint4(vbase + ty0 * (uint32_t)tiles_x + tx0, tw, slot[k], 0u);
             }
@@ -278,11 +278,12 @@ void launch_project(const SceneDev &s, const ViewGroup *vgs, int V, const uint32
 }
 
 void launch_tile_count(const Rec *recs, const uint32_t *order, uint32_t n, int tiles_x, uint32_t tiles,
-                       uint32_t *counts, uint4 *bins, int sms, cudaStream_t st, const uint32_t *n_dev)
+                       int tile_shift, uint32_t *counts, uint4 *bins, int sms, cudaStream_t st, const uint32_t *n_dev)
 {
     if (n == 0) return;
     ProfScope ps_("tile_count", st);
-    k_tile_count<<<grid_for(n, 256, sms), 256, 0, st>>>(recs, order, n, n_dev, tiles_x, tiles, counts, bins);
+    k_tile_count<<<grid_for(n, 256, sms), 256, 0, st>>>(recs, order, n, n_dev, tiles_x, tiles, tile_shift, counts,
+                                                        bins);
     count_launch();
 }
 

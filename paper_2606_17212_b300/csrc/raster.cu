@@ -179,8 +179,8 @@ __device__ __forceinline__ bool ellipse_meets_rect(const float4 &r0, const float
     return best <= rho;
 }
 
-// A warp's region: 16 columns x 4 NP rows of a tile (region `reg` of the
-// tile's 4 / NP regions).  Lane l owns column l & 15 and rows 2 NP (l >> 4) ..
+// A warp's region: 16 columns x 4 NP rows of a sort tile, at pixel offset
+// (ox, oy) inside it.  Lane l owns column l & 15 and rows 2 NP (l >> 4) ..
 // + 2 NP - 1 of the region, as NP vertical pairs.
 template <int NP>
 struct Lane {
@@ -192,13 +192,13 @@ struct Lane {
 };
 
 template <int NP>
-__device__ __forceinline__ Lane<NP> lane_of(int tile, int reg, const RasterArgs &a)
+__device__ __forceinline__ Lane<NP> lane_of(int tile, int ox, int oy, const RasterArgs &a)
 {
     Lane<NP> L;
     L.lane = threadIdx.x & 31;
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    L.rx0 = tx * TILE;
-    L.ry0 = ty * TILE + reg * 4 * NP;
+    L.rx0 = (tx << a.tile_shift) + ox;
+    L.ry0 = (ty << a.tile_shift) + oy;
     L.px = L.rx0 + (L.lane & 15);
     L.py0 = L.ry0 + 2 * NP * (L.lane >> 4);
     L.pcx = (float)L.px + 0.5f;
@@ -218,8 +218,8 @@ __device__ __forceinline__ Lane<NP> lane_of(int tile, int reg, const RasterArgs 
 // [x0, x0 + 15] x [y0, y0 + h], and append them in run order at `tail`.
 // Returns the new tail.
 __device__ __forceinline__ uint32_t stage_chunk(const Rec *__restrict__ recs, const uint32_t *__restrict__ evals,
-                                                const uint8_t *dep, uint32_t e, uint32_t end, float x0, float y0,
-                                                float h, WarpSmem &sm, uint32_t tail)
+                                                const uint8_t *dep, uint32_t e, uint32_t end, int rx0, int ry0,
+                                                int h, WarpSmem &sm, uint32_t tail)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t j = e + (uint32_t)lane;
@@ -230,11 +230,14 @@ __device__ __forceinline__ uint32_t stage_chunk(const Rec *__restrict__ recs, co
         slot = __ldg(evals + j);
         const float4 *p = reinterpret_cast<const float4 *>(recs + slot);
         r2 = __ldg(p + 2);
-        const uint32_t cd = __float_as_uint(r2.w);
-        if (((cd >> 12) & 0xfu) == (uint32_t)dep[cd & 0xfffu]) {
+        const uint32_t cd = __float_as_uint(r2.w), bx = __float_as_uint(r2.y), by = __float_as_uint(r2.z);
+        // the state's variant, whose pixel box meets the region, whose alpha ellipse reaches it
+        if (((cd >> 12) & 0xfu) == (uint32_t)dep[cd & 0xfffu] && (int)(bx & 0xffffu) <= rx0 + 15 &&
+            (int)(bx >> 16) >= rx0 && (int)(by & 0xffffu) <= ry0 + h && (int)(by >> 16) >= ry0) {
             r0 = __ldg(p);
             r1 = __ldg(p + 1);
-            keep = ellipse_meets_rect(r0, r1, x0, x0 + 15.0f, y0, y0 + h);
+            const float x0 = (float)rx0 + 0.5f, y0 = (float)ry0 + 0.5f;
+            keep = ellipse_meets_rect(r0, r1, x0, x0 + 15.0f, y0, y0 + (float)h);
         }
     }
     const uint32_t bal = __ballot_sync(FULL, keep);
@@ -363,12 +366,12 @@ template <int NP, class PIX>
 __device__ __forceinline__ uint32_t walk(const RasterArgs &a, const Lane<NP> &L, WarpSmem &sm, uint32_t start,
                                          uint32_t end, PIX &pix)
 {
-    const float x0 = (float)L.rx0 + 0.5f, y0 = (float)L.ry0 + 0.5f, h = (float)(4 * NP - 1);
+    const int h = 4 * NP - 1;
     uint32_t e = start, head = 0, tail = 0;
     if (!pix.live()) return e;
     for (;;) {
         while (tail - head < (uint32_t)CHUNK && e < end) {
-            tail = stage_chunk(a.recs, a.evals, sm.dep, e, end, x0, y0, h, sm, tail);
+            tail = stage_chunk(a.recs, a.evals, sm.dep, e, end, L.rx0, L.ry0, h, sm, tail);
             e += CHUNK;
         }
         if (head == tail) break;
@@ -398,7 +401,7 @@ __device__ __forceinline__ void load_depth(const RasterArgs &a, int s, WarpSmem 
 // writes the state's pixels and/or its FP64 squared-error partial; items come
 // costliest tile first from an atomic counter (or from an explicit work list).
 // Per pixel the arithmetic is fwd_pair(), exactly as for a single state.
-template <bool WRITE, bool MSE, bool LIST>
+template <bool WRITE, bool MSE, bool LIST, int SHIFT>
 __global__ void __launch_bounds__(RT, FWD_MIN_BLOCKS) k_raster_fwd(RasterArgs a, WorkQueue q)
 {
     __shared__ WarpSmem smem[WARPS];
@@ -417,11 +420,17 @@ __global__ void __launch_bounds__(RT, FWD_MIN_BLOCKS) k_raster_fwd(RasterArgs a,
             vt = q.list_vt[first];
             s = (int)q.list_state[first];
         } else {
-            // largest j with item_offsets[j] <= item
-            uint32_t lo_ = 0, hi_ = q.n_vt - 1;
-            while (lo_ < hi_) {
-                const uint32_t mid = (lo_ + hi_ + 1) >> 1;
-                if (q.item_offsets[mid] <= item) lo_ = mid; else hi_ = mid - 1;
+            // largest j with item_offsets[j] <= item: a 32-way search, one
+            // probe per lane per step (item_offsets is non-decreasing)
+            uint32_t lo_ = 0, span = q.n_vt;
+            while (span > 1) {
+                const uint32_t stride = (span + 31) / 32;
+                const uint32_t j = lo_ + (uint32_t)lane * stride;
+                const bool le = j < lo_ + span && q.item_offsets[j] <= item;
+                const uint32_t bal = __ballot_sync(FULL, le);     // lanes 0 .. k-1 (lane 0 always)
+                const uint32_t k = 31 - __clz(bal);
+                lo_ += k * stride;
+                span = min(stride, span - k * stride);
             }
             vt = q.tile_order[lo_];
             const int grp = q.vg_group_base[vt / a.tiles] + (int)(item - q.item_offsets[lo_]);
@@ -429,43 +438,51 @@ __global__ void __launch_bounds__(RT, FWD_MIN_BLOCKS) k_raster_fwd(RasterArgs a,
         }
         const int tile = (int)(vt % a.tiles);
         load_depth(a, s, sm);
-        const Lane<NPAIR> L = lane_of<NPAIR>(tile, 0, a);
-        FwdLane<NPAIR> f;
-        f.init(L);
         const uint2 rg = a.ranges[vt];
-        const uint32_t e = walk(a, L, sm, rg.x, rg.y, f);
-        double se = 0.0;
         const float *rbase = MSE ? a.refs + (size_t)a.ref_of_state[s] * a.H * a.W * 3 : nullptr;
+        // the tile's 16 x 16 regions in row-major order, each walked on its own
+        constexpr int rpx = 1 << (SHIFT - 4);
+        uint32_t stop = 0;
+        for (int reg = 0; reg < rpx * rpx; ++reg) {
+            const Lane<NPAIR> L = lane_of<NPAIR>(tile, (reg % rpx) * BLOCK, (reg / rpx) * BLOCK, a);
+            // a region of a 32 px tile can lie past the image edge (warp-uniform); 16 px tiles never do
+            if (SHIFT > 4 && (L.rx0 >= a.W || L.ry0 >= a.H)) continue;
+            FwdLane<NPAIR> f;
+            f.init(L);
+            const uint32_t e = walk(a, L, sm, rg.x, rg.y, f);
+            stop = max(stop, e - rg.x);
+            double se = 0.0;
 #pragma unroll
-        for (int j = 0; j < NPAIR; ++j) {
-            const f2 Tf = add2(f.p[j].T, f.p[j].Tk);
-            const f2 o0 = fma2(Tf, pk(a.bg0, a.bg0), f.p[j].cr);
-            const f2 o1 = fma2(Tf, pk(a.bg1, a.bg1), f.p[j].cg);
-            const f2 o2 = fma2(Tf, pk(a.bg2, a.bg2), f.p[j].cb);
+            for (int j = 0; j < NPAIR; ++j) {
+                const f2 Tf = add2(f.p[j].T, f.p[j].Tk);
+                const f2 o0 = fma2(Tf, pk(a.bg0, a.bg0), f.p[j].cr);
+                const f2 o1 = fma2(Tf, pk(a.bg1, a.bg1), f.p[j].cg);
+                const f2 o2 = fma2(Tf, pk(a.bg2, a.bg2), f.p[j].cb);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int r = 2 * j + h;
-                if (!((L.inimg >> r) & 1u)) continue;
-                const float c0 = h ? hi(o0) : lo(o0), c1 = h ? hi(o1) : lo(o1), c2 = h ? hi(o2) : lo(o2);
-                const size_t pix = (size_t)(L.py0 + r) * a.W + L.px;
-                if (WRITE) {
-                    float *dst = a.images + ((size_t)(s - a.img_s0) * a.H * a.W + pix) * 3;
-                    dst[0] = c0; dst[1] = c1; dst[2] = c2;
-                }
-                if (MSE) {
-                    const float *rp = rbase + pix * 3;
-                    se += (double)pixel_sq_err(c0, c1, c2, rp[0], rp[1], rp[2]);
+                for (int h = 0; h < 2; ++h) {
+                    const int r = 2 * j + h;
+                    if (!((L.inimg >> r) & 1u)) continue;
+                    const float c0 = h ? hi(o0) : lo(o0), c1 = h ? hi(o1) : lo(o1), c2 = h ? hi(o2) : lo(o2);
+                    const size_t pix = (size_t)(L.py0 + r) * a.W + L.px;
+                    if (WRITE) {
+                        float *dst = a.images + ((size_t)(s - a.img_s0) * a.H * a.W + pix) * 3;
+                        dst[0] = c0; dst[1] = c1; dst[2] = c2;
+                    }
+                    if (MSE) {
+                        const float *rp = rbase + pix * 3;
+                        se += (double)pixel_sq_err(c0, c1, c2, rp[0], rp[1], rp[2]);
+                    }
                 }
             }
-        }
-        if (MSE) {
+            if (MSE) {
+                // one partial per 16 x 16 pixel block: the same sum whatever the tile size
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) se += __shfl_xor_sync(FULL, se, off);
-            if (lane == 0) {
-                a.partial[(size_t)s * a.tiles + tile] = se;
-                if (LIST) a.stop[(size_t)s * a.tiles + tile] = e - rg.x;
+                for (int off = 16; off > 0; off >>= 1) se += __shfl_xor_sync(FULL, se, off);
+                if (lane == 0)
+                    a.partial[(size_t)s * a.blocks + (size_t)(L.ry0 / BLOCK) * a.blocks_x + L.rx0 / BLOCK] = se;
             }
         }
+        if (LIST && lane == 0) a.stop[(size_t)s * a.tiles + tile] = stop;
         __syncwarp();
     }
 }
@@ -607,18 +624,20 @@ struct BwdLane {
 template <bool IMG>
 __global__ void __launch_bounds__(RT, BWD_MIN_BLOCKS) k_raster_bwd(RasterBwdArgs b)
 {
-    constexpr int NP = BWD_NP, REG = 4 / BWD_NP;    // pairs per lane, regions per tile
+    constexpr int NP = BWD_NP, RH = 4 * BWD_NP;     // pairs per lane, region height
     const RasterArgs &a = b.f;
     __shared__ WarpSmem smem[WARPS];
     const int w = threadIdx.x >> 5;
     WarpSmem &sm = smem[w];
+    const int rpx = 1 << (a.tile_shift - 4), rpy = (1 << a.tile_shift) / RH, regs = rpx * rpy;
     const size_t item = (size_t)blockIdx.x * WARPS + w;
-    if (item >= (size_t)a.tiles * REG * a.S) return;
+    if (item >= (size_t)a.tiles * regs * a.S) return;
     const int s = (int)(item % (unsigned)a.S);
-    const int tr = (int)(item / (unsigned)a.S), tile = tr / REG, reg = tr % REG;
+    const int tr = (int)(item / (unsigned)a.S), tile = tr / regs, reg = tr % regs;
+    const Lane<NP> L = lane_of<NP>(tile, (reg % rpx) * BLOCK, (reg / rpx) * RH, a);
+    if (L.rx0 >= a.W || L.ry0 >= a.H) return;        // region outside the image
     const int v = a.vg_of_state[s];
     load_depth(a, s, sm);
-    const Lane<NP> L = lane_of<NP>(tile, reg, a);
     const uint2 rg = a.ranges[(size_t)v * a.tiles + tile];
 
     // final pixel values
@@ -761,7 +780,8 @@ __global__ void __launch_bounds__(256) k_image_mse(const float *__restrict__ ima
 template <bool WRITE, bool MSE, bool LIST>
 static void launch_fwd_t(const RasterArgs &a, const WorkQueue &q, int blocks, cudaStream_t st)
 {
-    k_raster_fwd<WRITE, MSE, LIST><<<blocks, RT, 0, st>>>(a, q);
+    if (a.tile_shift == 5) k_raster_fwd<WRITE, MSE, LIST, 5><<<blocks, RT, 0, st>>>(a, q);
+    else k_raster_fwd<WRITE, MSE, LIST, 4><<<blocks, RT, 0, st>>>(a, q);
 }
 
 // Every work item is one (view-group tile, state); the explicit work list
@@ -781,8 +801,10 @@ void launch_raster_fwd(const RasterArgs &a, const WorkQueue &q, int G, int block
 template <bool WRITE, bool MSE, bool LIST>
 static int occ_t()
 {
-    int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_fwd<WRITE, MSE, LIST>, RT, 0);
+    int n = 0, n5 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_fwd<WRITE, MSE, LIST, 4>, RT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n5, k_raster_fwd<WRITE, MSE, LIST, 5>, RT, 0);
+    n = n < n5 ? n : n5;
     return n > 0 ? n : 1;
 }
 
@@ -829,7 +851,8 @@ void launch_item_counts(const uint32_t *tile_order, uint32_t n, uint32_t tiles, 
 void launch_raster_bwd(const RasterBwdArgs &b, cudaStream_t st)
 {
     if (b.f.S == 0 || b.f.tiles == 0) return;
-    const size_t items = (size_t)b.f.tiles * (4 / BWD_NP) * (size_t)b.f.S;
+    const int regs = (1 << (b.f.tile_shift - 4)) * ((1 << b.f.tile_shift) / (4 * BWD_NP));
+    const size_t items = (size_t)b.f.tiles * regs * (size_t)b.f.S;
     const unsigned grid = (unsigned)((items + WARPS - 1) / WARPS);
     ProfScope ps_(b.img_fwd ? "raster_bwd" : "raster_bwd_2pass", st);
     if (b.img_fwd) k_raster_bwd<true><<<grid, RT, 0, st>>>(b);

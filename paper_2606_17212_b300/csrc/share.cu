@@ -271,7 +271,7 @@ __global__ void k_items(const uint32_t *__restrict__ flag, const uint32_t *__res
 // which exceeds the group's K (m(P) > 15: rendered alone).
 __global__ void k_share_resolve(const uint32_t *__restrict__ pvt, const uint32_t *__restrict__ pst,
                                 uint8_t *__restrict__ pk, const uint32_t *__restrict__ prep,
-                                const uint32_t *__restrict__ n_dev, uint32_t tiles,
+                                const uint32_t *__restrict__ n_dev, TileGeom geo,
                                 const uint32_t *__restrict__ ord_c, const uint32_t *__restrict__ ord_fp,
                                 const uint8_t *__restrict__ depth, int C, const uint32_t *__restrict__ stop,
                                 double *__restrict__ partial, uint32_t *__restrict__ pending)
@@ -280,6 +280,7 @@ __global__ void k_share_resolve(const uint32_t *__restrict__ pvt, const uint32_t
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint32_t s = pst[i], q = prep[i];
         if (q == s) { pending[i] = 0; continue; }
+        const uint32_t tiles = geo.tiles;
         const uint32_t vt = pvt[i], tile = vt % tiles;
         const uint32_t P = stop[(size_t)q * tiles + tile];
         const uint32_t *oc = ord_c + (size_t)vt * SHARE_ORDER;
@@ -294,7 +295,13 @@ __global__ void k_share_resolve(const uint32_t *__restrict__ pvt, const uint32_t
         int j = 0;                                   // first of the m clusters where the depths differ
         while (j < m && depth[(size_t)s * C + oc[j]] == depth[(size_t)q * C + oc[j]]) ++j;
         if (j == m) {
-            partial[(size_t)s * tiles + tile] = partial[(size_t)q * tiles + tile];
+            int bx0, bx1, by0, by1;
+            tile_blocks(geo, tile, bx0, bx1, by0, by1);
+            for (int by = by0; by < by1; ++by)
+                for (int bx = bx0; bx < bx1; ++bx) {
+                    const size_t b = (size_t)by * geo.blocks_x + bx;
+                    partial[(size_t)s * geo.blocks + b] = partial[(size_t)q * geo.blocks + b];
+                }
             pending[i] = 0;
         } else {
             // the group agreed on its first K clusters, so j >= K: regroup one cluster past
@@ -391,13 +398,13 @@ void launch_item_lists(const uint32_t *lvt, const uint2 *seg, const uint32_t *n_
 }
 
 void launch_share_resolve(const uint32_t *pvt, const uint32_t *pst, uint8_t *pk, const uint32_t *prep,
-                          const uint32_t *n_dev, size_t n_cap, uint32_t tiles, const uint32_t *ord_c,
+                          const uint32_t *n_dev, size_t n_cap, const TileGeom &geo, const uint32_t *ord_c,
                           const uint32_t *ord_fp, const uint8_t *depth, int C, const uint32_t *stop, double *partial,
                           uint32_t *pending, int sms, cudaStream_t st)
 {
     if (n_cap == 0) return;
     ProfScope ps_("share_resolve", st);
-    k_share_resolve<<<grid_of(n_cap, sms), 256, 0, st>>>(pvt, pst, pk, prep, n_dev, tiles, ord_c, ord_fp, depth, C,
+    k_share_resolve<<<grid_of(n_cap, sms), 256, 0, st>>>(pvt, pst, pk, prep, n_dev, geo, ord_c, ord_fp, depth, C,
                                                           stop, partial, pending);
     count_launch();
 }

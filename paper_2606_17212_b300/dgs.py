@@ -64,7 +64,7 @@ EXPORTS = ("dgs_create", "dgs_destroy", "dgs_last_error", "dgs_version", "dgs_re
            "dgs_plan_last_error", "dgs_plan_render", "dgs_plan_backward", "dgs_plan_utility",
            "dgs_plan_image_mse", "dgs_plan_status", "dgs_arena_create", "dgs_arena_destroy",
            "dgs_group_utility", "dgs_objective", "dgs_set_tile_reuse",
-           "dgs_tile_reuse_stats")
+           "dgs_tile_reuse_stats", "dgs_set_tile_size")
 OBJECTIVE_MAX_STATES = 16384
 UTILITY_MAX_CONTEXTS = 4096
 PLAN_RENDER, PLAN_UTILITY = 1, 2
@@ -99,6 +99,7 @@ def lib():
         L.dgs_group_utility.argtypes = [P, ctypes.POINTER(Scene_t), ctypes.POINTER(States_t), P, I, I, P, I, P,
                                         D, D, D, P, P, P]
         L.dgs_set_tile_reuse.argtypes = [P, I]
+        L.dgs_set_tile_size.argtypes = [P, I]
         L.dgs_tile_reuse_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                            ctypes.POINTER(ctypes.c_int32)]
         L.dgs_kernel_launches.argtypes = [P]
@@ -350,6 +351,10 @@ class Renderer:
         """dgs_set_tile_reuse: exact reuse of rendered tiles across the states of
         one view in the distortion passes (on by default; outputs unchanged)."""
         self._check(self._lib.dgs_set_tile_reuse(self.h, 1 if enable else 0), "dgs_set_tile_reuse")
+
+    def set_tile_size(self, size: int):
+        """dgs_set_tile_size: side of the sort tiles (16 or 32 px, 0 = chosen per batch shape)."""
+        self._check(self._lib.dgs_set_tile_size(self.h, int(size)), "dgs_set_tile_size")
 
     def tile_reuse_stats(self):
         """dgs_tile_reuse_stats of the last distortion pass: (pairs, rendered, rounds)."""

@@ -75,6 +75,35 @@ def test_batched_equals_per_state_bitwise(R, torch):
         assert torch.equal(one, batched[s]), s
 
 
+def test_tile_size_changes_no_bit(R, torch):
+    """The sort tile size is an acceleration structure: 16 and 32 px tiles give
+    the same images and per-state MSE bit for bit (every pixel composites the
+    same Gaussians in the same order; squared errors are summed over fixed
+    16 x 16 blocks), and the same gradients up to the order of the float
+    atomic adds (ragged image, several view groups)."""
+    w = synth.config("c3_fwdbwd_250k", scale=0.03, n_states=12)
+    w.cams = [synth.ring_camera(k, 8, 83, 57, 96.0) for k in range(8)]
+    sc = dgs.DeviceScene.from_host(w.scene)
+    st = _gpu_states(w)
+    out = {}
+    try:
+        for tile in (16, 32):
+            R.set_tile_size(tile)
+            imgs = R.render_states_batched(sc, st, w.cams, w.bg)
+            mse, psnr = R.state_utility(sc, st, w.cams, w.bg)
+            dL = torch.sin(torch.arange(imgs.numel(), device="cuda", dtype=torch.float32) * 0.37).reshape(imgs.shape)
+            g = R.render_backward(sc, st, w.cams, w.bg, dL * 1e-3, images=imgs)
+            out[tile] = (imgs.clone(), mse.clone(), {k: v.clone() for k, v in g.items()})
+    finally:
+        R.set_tile_size(0)
+    assert torch.equal(out[16][0], out[32][0])
+    assert torch.equal(out[16][1], out[32][1])
+    for k, v in out[16][2].items():
+        ref = float(v.abs().max())
+        err = float((out[32][2][k] - v).abs().max())
+        assert err <= 1e-5 * max(ref, 1e-12), (k, err, ref)
+
+
 def test_ragged_image_and_edge_cases(R, torch):
     w = synth.config("c2_dynamic_250k", scale=0.01, n_states=3)
     cam = synth.ring_camera(2, 8, 97, 61, 110.0)          # ragged tiles on both axes
@@ -162,11 +191,12 @@ def test_utility_equals_images_then_mse(R, torch):
     assert torch.allclose(mse, m2, rtol=1e-12, atol=0)
 
 
-@pytest.mark.parametrize("name,scale,n", [("c4_utility_2p7m", 0.02, 600), ("c2_dynamic_250k", 0.03, 256),
-                                          ("c3_fwdbwd_250k", 0.05, 96)])
-def test_tile_reuse_is_bitwise(R, torch, name, scale, n):
+@pytest.mark.parametrize("name,scale,n,tile", [("c4_utility_2p7m", 0.02, 600, 16), ("c2_dynamic_250k", 0.03, 256, 16),
+                                               ("c3_fwdbwd_250k", 0.05, 96, 16), ("c4_utility_2p7m", 0.02, 600, 32),
+                                               ("c3_fwdbwd_250k", 0.05, 96, 32)])
+def test_tile_reuse_is_bitwise(R, torch, name, scale, n, tile):
     """Reusing rendered tiles across the states of a view changes no bit of any
-    state's MSE: reuse on == every (state, tile) rendered."""
+    state's MSE: reuse on == every (state, tile) rendered, for either sort tile size."""
     w = synth.config(name, scale=scale, n_states=n)
     masks = w.states.masks.copy()
     masks[1] = 0                       # empty delivery
@@ -178,14 +208,18 @@ def test_tile_reuse_is_bitwise(R, torch, name, scale, n):
     w.states.masks = masks
     sc = dgs.DeviceScene.from_host(w.scene)
     st = _gpu_states(w)
-    R.set_tile_reuse(False)
+    R.set_tile_size(tile)
     try:
-        m0, p0 = R.state_utility(sc, st, w.cams, w.bg)
+        R.set_tile_reuse(False)
+        try:
+            m0, p0 = R.state_utility(sc, st, w.cams, w.bg)
+        finally:
+            R.set_tile_reuse(True)
+        m1, p1 = R.state_utility(sc, st, w.cams, w.bg)
+        pairs, rendered, rounds = R.tile_reuse_stats()
     finally:
-        R.set_tile_reuse(True)
-    m1, p1 = R.state_utility(sc, st, w.cams, w.bg)
-    pairs, rendered, rounds = R.tile_reuse_stats()
-    tiles = -(-w.cams[0].width // 16) * -(-w.cams[0].height // 16)
+        R.set_tile_size(0)
+    tiles = -(-w.cams[0].width // tile) * -(-w.cams[0].height // tile)
     assert pairs == n * tiles and 0 < rendered <= pairs and 1 <= rounds <= 17
     assert torch.equal(m0, m1)
     assert torch.equal(p0.isinf(), p1.isinf()) and torch.equal(p0[~p0.isinf()], p1[~p1.isinf()])
@@ -318,16 +352,21 @@ def _unpack_boxes(recs):
         (cd & 0xFFF).astype(np.int64)
 
 
-def test_tile_lists_bitwise_and_end_to_end(R, torch):
+@pytest.mark.parametrize("tile", [16, 32])
+def test_tile_lists_bitwise_and_end_to_end(R, torch, tile):
     w = synth.config("c3_fwdbwd_250k", scale=0.01, n_states=10)
     sc_h = w.scene
     sc = dgs.DeviceScene.from_host(sc_h)
     st = _gpu_states(w)
-    R.render_states_batched(sc, st, w.cams, w.bg)
-    d = R.debug_tile_lists()
+    R.set_tile_size(tile)
+    try:
+        R.render_states_batched(sc, st, w.cams, w.bg)
+        d = R.debug_tile_lists()
+    finally:
+        R.set_tile_size(0)
     n_rec, T = d["n_rec"], d["tiles"]
     W, H = w.cams[0].width, w.cams[0].height
-    tx, ty = -(-W // 16), -(-H // 16)
+    tx, ty = -(-W // tile), -(-H // tile)
     assert T == tx * ty
     recs = d["recs"]
     xlo, xhi, ylo, yhi, depth, vg, clus = _unpack_boxes(recs)
@@ -338,7 +377,7 @@ def test_tile_lists_bitwise_and_end_to_end(R, torch):
     order = np.argsort(dkey, kind="stable")
     assert np.array_equal(order, d["depth_slots"].astype(np.int64))
     # (1) bitwise: the oracle's integer binning of the GPU's own records
-    keys, vals, ranges = oracle.bin_tiles(xlo, xhi, ylo, yhi, dkey, live, 16, tx, ty, view_group=vg,
+    keys, vals, ranges = oracle.bin_tiles(xlo, xhi, ylo, yhi, dkey, live, tile, tx, ty, view_group=vg,
                                           rank=np.arange(n_rec))
     assert np.array_equal((keys >> np.uint64(32)).astype(np.uint32), d["entry_keys"])
     assert np.array_equal(vals.astype(np.uint32), d["entry_vals"])

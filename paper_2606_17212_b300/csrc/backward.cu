@@ -108,7 +108,10 @@ __global__ void __launch_bounds__(128) k_project_bwd(SceneDev s, const ViewGroup
                 Proj P; Fwd F;
                 project_fwd<SH>(s, i, c, a, vg, P, F);
                 if (!P.live) continue;
-                const float gg[9] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x};
+                // screen-space gradients from the raster's pixel moments of dL/dpower
+                // (power = -(A dx^2 + 2 B dx dy + C dy^2) / 2, alpha = o e^power)
+                const float gg[9] = {-(P.A * q0.x + P.B * q0.y), -(P.B * q0.x + P.C * q0.y), -0.5f * q0.z, -q0.w,
+                                     -0.5f * q1.x, __fdividef(q1.y, P.o), q1.z, q1.w, q2.x};
                 float gmu[3];
                 project_bwd<SH>(a, vg, P, F, gg, acc, gmu);
                 if (s.affine) {

@@ -75,7 +75,8 @@ struct RasterBwdArgs {
     RasterArgs f;
     const float *dL_dimg;         // [S][H][W][3]
     const float *img_fwd;         // [S][H][W][3] the forward's images, or null (recomputed)
-    float4 *rec_grad;             // [nRec][3]: (mx, my, A, B), (C, o, r, g), (b, -, -, -)
+    float4 *rec_grad;             // [nRec][3] pixel moments of dL/dpower (d = m - pixel centre) and colour:
+                                  // (S dx, S dy, S dx^2, S dx dy), (S dy^2, S 1, dL/dr, dL/dg), (dL/db, -, -, -)
 };
 void launch_raster_bwd(const RasterBwdArgs &a, cudaStream_t st);
 

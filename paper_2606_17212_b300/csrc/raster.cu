@@ -502,7 +502,8 @@ struct BwdPair {
 // Sums of one entry over a lane's pixels, packed by pair row parity:
 // S5 = sum dL/dpower, S1 = sum dL/dpower dy, S4 = sum dL/dpower dy^2 (dx is
 // the lane's column: its moments follow from these), and the colour sums
-// sum dL/dC (alpha T).
+// sum dL/dC (alpha T).  dy = my - pixel centre (the sign of the offsets does
+// not matter to the moments the projection adjoint uses).
 struct BwdSums {
     f2 S1, S4, S5, Sr, Sg, Sb;
 };
@@ -583,32 +584,28 @@ struct BwdLane {
         const uint32_t nz = (__float_as_uint(s1) | __float_as_uint(s4) | __float_as_uint(s5) | __float_as_uint(sr) |
                              __float_as_uint(sg) | __float_as_uint(sb)) << 1;
         if (!__any_sync(FULL, nz != 0u)) return;
-        // per-lane conic and mean gradients from the lane's sums (linear in them;
-        // dx is the lane's column offset): with a = sum dL/dpower dx,
-        // dL/dmx = -(A a + B s1), dL/dmy = -(B a + C s1),
-        // dL/dA = -a dx / 2, dL/dB = -dx s1, dL/dC = -s4 / 2
-        const float4 s3 = q.s3[k];
-        const float A = s3.y * INV_K_AC, B = s3.z * INV_K_B, C = lo(E.c2) * INV_K_AC;
-        const float a_ = E.dx * s5;
+        // the entry's pixel moments over the lane's pixels (dx is the lane's column
+        // offset, the same for all its pixels); the projection adjoint turns their
+        // sums into the conic, mean and opacity gradients
+        const float m0 = E.dx * s5;
         float v[8];
-        v[0] = -fmaf(A, a_, B * s1);
-        v[1] = -fmaf(B, a_, C * s1);
-        v[2] = -0.5f * E.dx * a_;
-        v[3] = -E.dx * s1;
-        v[4] = -0.5f * s4;
-        v[5] = s5;
-        v[6] = sr;
+        v[0] = m0;                 // sum dL/dpower dx
+        v[1] = s1;                 // sum dL/dpower dy
+        v[2] = E.dx * m0;          // sum dL/dpower dx^2
+        v[3] = E.dx * s1;          // sum dL/dpower dx dy
+        v[4] = s4;                 // sum dL/dpower dy^2
+        v[5] = s5;                 // sum dL/dpower
+        v[6] = sr;                 // sum dL/dC alpha T (per channel)
         v[7] = sg;
         float x = reduce8_transpose(v, L.lane);
         float xb = sb;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) xb += __shfl_xor_sync(FULL, xb, off);
-        // lane 4 j holds the total of v[j]; dL/do = sum dL/dpower / o (alpha = o e^power)
+        // lane 4 j holds the total of v[j], lane 1 the blue sum
         if ((L.lane & 3) == 0 || L.lane == 1) {
             const int idx = L.lane == 1 ? 8 : (L.lane >> 2);
-            const float val = L.lane == 1 ? xb : (idx == 5 ? __fdividef(x, lo(E.o)) : x);
             float *dst = reinterpret_cast<float *>(rec_grad + (size_t)q.s4[k].w * 3);
-            atomicAdd(dst + idx, val);
+            atomicAdd(dst + idx, L.lane == 1 ? xb : x);
         }
     }
 };
@@ -619,8 +616,8 @@ struct BwdLane {
 //   dC/dalpha_k = rgb_k T_k - (C_after_k + T_final bg) / (1 - alpha_k)
 // with C_after_k = C_final - (colour accumulated up to and including k).  The
 // final pixel value is read from the forward's image (IMG) or recomputed by a
-// first forward walk.  Per-Gaussian sums: four pixels per lane, a warp
-// transpose reduction, one atomic add per gradient component.
+// first forward walk.  Per-Gaussian pixel moments: four pixels per lane, a
+// warp transpose reduction, one atomic add per moment.
 template <bool IMG>
 __global__ void __launch_bounds__(RT, BWD_MIN_BLOCKS) k_raster_bwd(RasterBwdArgs b)
 {

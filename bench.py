@@ -31,14 +31,19 @@ if ROOT not in sys.path:
 
 METRIC = "delivery-state renders/s and Mpix/s, batched fwd+bwd vs plain per-state, ≤1e-4 err"
 UNIT = "states/s"
-FWD_FLOP_PER_EVAL = 24     # FP32 ops of one (pixel, Gaussian) compositing evaluation
+# Roofline of the raster kernels as the measurement plan defines it: every
+# (pixel, Gaussian, state) evaluation the oracle counts costs 17 FP32
+# operations and one MUFU exp, forward and adjoint alike.  The FP32 peak counts
+# an FMA as two operations (148 SMs x 128 lanes x 2 x clock), so the FP32
+# fraction is a lower bound; the MUFU peak is the measured ex2.approx rate of
+# this GPU (32 per SM per clock).
+SURVEY_FP32_PER_EVAL = 17
+SURVEY_MUFU_PER_EVAL = 1
+MUFU_EX2_PER_SM_CLK = 32
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of this workload at full
-# size; valid only for the kernel source it was taken on (sha1 of csrc/raster.cu).
-MEASURED_TRAFFIC = {("raster_bwd", "c3_fwdbwd_250k"): (803081216 + 55618560, "5acbed28709477fc5dfed44380ca03cf8fe3bef3"),
-                    # the tile-reuse rounds' launches, averaged (ncu, full size, one pass)
-                    ("raster_fwd_mse_g2", "c4_utility_2p7m"): (201978844, "5acbed28709477fc5dfed44380ca03cf8fe3bef3")}
-BWD_FLOP_PER_EVAL = 57     # forward recompute (24) + adjoint arithmetic (33)
+# (dram__bytes_read.sum + dram__bytes_write.sum, one pass); valid only for the
+# kernel source it was taken on (sha1 of csrc/raster.cu) and the workload at full size.
+MEASURED_TRAFFIC = {}
 
 
 def _dist():
@@ -102,6 +107,42 @@ def _peaks():
             d = json.load(f)
         return d, "measured"
     return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def raster_roofline(name, evals, ms_per_launch, sms, sm_mhz, traffic=None):
+    """Roofline entry of a raster kernel under the measurement plan's count:
+    17 FP32 operations and one MUFU exp per oracle-counted (pixel, Gaussian,
+    state) evaluation, against the FP32 FMA peak (an FMA counted as two, so
+    the fraction is a lower bound) and the measured ex2 rate."""
+    t = ms_per_launch / 1e3
+    fp32_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+    mufu_peak = sms * MUFU_EX2_PER_SM_CLK * sm_mhz * 1e6 / 1e12
+    achieved = SURVEY_FP32_PER_EVAL * evals / t / 1e12
+    mufu = SURVEY_MUFU_PER_EVAL * evals / t / 1e12
+    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": traffic, "traffic_unit": "bytes per launch (ncu)",
+            "peak_kind": "FP32 FMA peak from unit counts and clock: %d SMs x 128 lanes x 2 x %.0f MHz (derived)"
+                         % (sms, sm_mhz),
+            "per_eval": "%d FP32 ops + %d MUFU exp per oracle-counted (pixel, Gaussian, state) evaluation"
+                        % (SURVEY_FP32_PER_EVAL, SURVEY_MUFU_PER_EVAL),
+            "mufu": {"achieved": mufu, "peak": mufu_peak, "unit": "T ex2/s", "frac": mufu / mufu_peak,
+                     "peak_kind": "measured ex2.approx rate: %d per SM per clock" % MUFU_EX2_PER_SM_CLK},
+            "ms_per_launch": ms_per_launch, "evals_per_launch": evals}
+
+
+def hbm_entry(name, nbytes, ms, peak_gbs, what):
+    """Achieved algorithmic bandwidth of an HBM-bound kernel (group) against the measured copy peak."""
+    gbs = nbytes / (ms / 1e3) / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": peak_gbs, "unit": "GB/s",
+            "frac": gbs / peak_gbs, "bytes_per_step": nbytes, "ms_per_step": ms, "bytes": what}
+
+
+def scene_bytes(sc):
+    """Bytes of a scene's attributes: base (mean, temporal coefficients, log-scale,
+    quaternion, opacity logit, colour) and every refinement layer."""
+    nc = sc.colour.shape[1]
+    per = 4 * (3 + 3 * sc.temporal_rank + 3 + 4 + 1 + nc) + 4 * (sc.n_layers - 1) * (11 + nc)
+    return per * sc.n
 
 
 class ClockSampler:
@@ -174,32 +215,36 @@ class ClockSampler:
                 "reasons": sorted(self.reasons), "samples": len(self.samples)}
 
 
-def oracle_sample(w, n_states=2, n_bands=8, band_rows=2, n_pix=256, seed=0, want_backward=True):
-    """Time the FP64 oracle as it stands on a bounded sample of each state.
+def oracle_sample(w, states, n_bands=16, band_rows=2, n_pix=1024, seed=0, want_backward=True):
+    """Time the FP64 oracle as it stands on a bounded sample of the given
+    states (one protocol for the CPU baseline and the reference arm).
     Forward: the projection (once per state) plus n_bands bands of band_rows
     whole rows at random heights, rendered as in the full image (row filter),
     extrapolated to all rows.  Adjoint: its fixed part (projection and the
     per-record chain rule, timed with dL/dI = 0) plus the adjoint of n_pix
-    random pixels, extrapolated to all pixels.  Returns (seconds per full
-    state, evaluations per pixel, threads, description)."""
+    random pixels, extrapolated to all pixels.  Returns a dict: seconds per
+    full state (extrapolated), the measured seconds of the sampled work, the
+    extrapolation factor, evaluations per pixel, threads and a description."""
     import oracle
     sc = w.scene
     rng = np.random.default_rng(seed)
     D = oracle.state_depths(w.states, sc.n_clusters, sc.n_layers)
     H, W = w.cams[0].height, w.cams[0].width
-    tot_t, tot_eval, tot_px = 0.0, 0, 0
+    tot_t, tot_meas, tot_eval, tot_px = 0.0, 0.0, 0, 0
     rows = min(band_rows, H)
-    for s in range(n_states):
+    for s in states:
         cam = w.cams[int(w.states.cam[s])]
         t = float(w.states.t[s])
         t0 = time.perf_counter()
         oracle.project(sc, D[s], t, cam)
         t_proj = time.perf_counter() - t0
-        t_rows, n_rows = 0.0, 0
+        t_rows, n_rows, meas = 0.0, 0, t_proj
         for y0 in rng.integers(0, H - rows + 1, size=n_bands):
             t0 = time.perf_counter()
             _, _, ne = oracle.render_rows(sc, D[s], t, cam, w.bg, int(y0), int(y0) + rows)
-            t_rows += max(time.perf_counter() - t0 - t_proj, 0.0)
+            dt = time.perf_counter() - t0
+            meas += dt
+            t_rows += max(dt - t_proj, 0.0)
             n_rows += rows
             tot_eval += ne
             tot_px += rows * W
@@ -214,15 +259,20 @@ def oracle_sample(w, n_states=2, n_bands=8, band_rows=2, n_pix=256, seed=0, want
             dL[flat // W, flat % W] = rng.normal(size=(flat.size, 3))
             t0 = time.perf_counter()
             oracle.render_backward(sc, D[s], t, cam, w.bg, dL)
-            bwd = t_fix + max(time.perf_counter() - t0 - t_fix, 0.0) * (H * W) / flat.size
+            dt = time.perf_counter() - t0
+            meas += t_fix + dt
+            bwd = t_fix + max(dt - t_fix, 0.0) * (H * W) / flat.size
         tot_t += fwd + bwd
+        tot_meas += meas
     threads = os.cpu_count() or 1
-    desc = ("%d states, each: projection once + %d bands of %d whole rows (FP64 forward on %d threads, row "
+    n = max(len(states), 1)
+    desc = ("%d state(s), each: projection once + %d bands of %d whole rows (FP64 forward on %d threads, row "
             "filter as in the full image) extrapolated to %d rows%s" % (
-                n_states, n_bands, rows, threads, H,
+                len(states), n_bands, rows, threads, H,
                 "; adjoint (1 thread): fixed part once + %d random pixels extrapolated to %dx%d" % (n_pix, W, H)
                 if want_backward else ""))
-    return tot_t / n_states, tot_eval / max(tot_px, 1), threads, desc
+    return {"sec_per_state": tot_t / n, "sampled_s": tot_meas, "extrapolation": tot_t / max(tot_meas, 1e-12),
+            "evals_per_px": tot_eval / max(tot_px, 1), "threads": threads, "desc": desc}
 
 
 def t_interval(samples):
@@ -246,26 +296,37 @@ def workload_config(w, ws, views, path):
 
 
 def reference_arm(args, w):
+    """The FP64 oracle on the host cores, the same sampling protocol as the
+    CPU baseline of the GPU arm: each step samples one state (16 bands of 2
+    rows forward, 1,024 adjoint pixels) and extrapolates it to whole states.
+    ms_per_step is the measured time of the sampled work; value is the
+    extrapolated states/s."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     views = sorted(set(zip(w.states.cam.tolist(), w.states.t.tolist())))
     cfg = workload_config(w, ws, views, "fp64_oracle_cpu")
-    times = []
-    n_pix = 256
+    sec_states, sampled = [], []
+    last = None
     for k in range(args.warmup + args.steps):
-        sps, _, threads, desc = oracle_sample(w, n_states=1, n_pix=n_pix, seed=k,
-                                              want_backward=w.target_scene is not None)
+        r = oracle_sample(w, [k % w.states.n], seed=k, want_backward=w.target_scene is not None)
         if k >= args.warmup:
-            times.append(sps)
-    sec_per_state = float(np.mean(times))
+            sec_states.append(r["sec_per_state"])
+            sampled.append(r["sampled_s"])
+        last = r
+    sec_per_state = float(np.mean(sec_states))
     value = 1.0 / sec_per_state
+    meas_ms = float(np.mean(sampled)) * 1e3
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": sec_per_state * w.states.n * 1e3,
+            "warmup": args.warmup, "ms_per_step": meas_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference", "config": cfg,
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": "per step: " + desc},
+            "extrapolated": True,
+            "extrapolation_factor": sec_per_state * 1e3 / meas_ms,
+            "step_what": "one sampled state per step; ms_per_step is the measured time of that sample, value the "
+                         "states/s it extrapolates to",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["threads"], "kind": "oracle",
+                             "sample": "per step: " + last["desc"], "extrapolated": True},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -287,6 +348,7 @@ def run_mix(args):
     t_gen = time.perf_counter()
     evals_total = 0.0
     oracle_sec = 0.0
+    oracle_meas = 0.0
     threads = None
     for spec in specs:
         w = synth.mix_workload(spec)
@@ -300,10 +362,12 @@ def run_mix(args):
         targets = R.render_states_batched(sc, fv, w.cams, w.bg)
         S, H, W = st.n, w.cams[0].height, w.cams[0].width
         # oracle on a bounded sample of this scene: evaluations per pixel and CPU time per state
-        sec, epp, threads, _ = oracle_sample(w, n_states=1, n_bands=4, n_pix=64, seed=spec.index,
-                                             want_backward=True)
-        evals_total += epp * H * W * S
-        oracle_sec += sec * S
+        if not args.no_oracle_sample:
+            r = oracle_sample(w, [0], n_bands=4, n_pix=64, seed=spec.index, want_backward=True)
+            evals_total += r["evals_per_px"] * H * W * S
+            oracle_sec += r["sec_per_state"] * S
+            oracle_meas += r["sampled_s"]
+            threads = r["threads"]
         scenes.append(dict(spec=spec, w_t=w.states.t, w_cam=w.states.cam, cams=w.cams, bg=w.bg, sc=sc, st=st,
                            ridx=ridx, targets=targets, S=S, H=H, W=W,
                            host_masks=torch.from_numpy(np.ascontiguousarray(w.states.masks).view(np.int32)).pin_memory(),
@@ -408,20 +472,17 @@ def run_mix(args):
 
     pk, pk_kind = _peaks()
     sm_mhz = pk.get("sm_max_mhz", 2032.0)
-    fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     roof = None
-    if "raster_bwd" in prof:
+    if "raster_bwd" in prof and evals_total > 0:
         bms, bn = prof["raster_bwd"]
-        # evaluations of all scenes' backward launches per step / their summed time per step
-        achieved = BWD_FLOP_PER_EVAL * evals_total / (bms / args.steps / 1e3) / 1e12
-        roof = {"kernel": "raster_bwd", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
-                "traffic_unit": "bytes per launch (ncu, full size)",
-                "peak_kind": "FP32 FMA issue peak: 148 SMs x 128 lanes x 2 x %.0f MHz (derived)" % sm_mhz,
-                "ms_per_launch": bms / max(bn, 1), "launches_per_step": bn / args.steps,
-                "evals_per_step": evals_total}
-    cpu = None if args.no_cpu_baseline else {
+        # every scene's backward launch of a step together: evaluations per step / time per step
+        roof = raster_roofline("raster_bwd", evals_total, bms / args.steps, sms, sm_mhz)
+        roof["launches_per_step"] = bn / args.steps
+        roof["what"] = "all scenes' backward launches of one step together"
+    cpu = None if (args.no_cpu_baseline or oracle_sec == 0) else {
         "value": total_states / oracle_sec, "unit": UNIT, "cores": threads, "kind": "oracle",
+        "sampled_s": oracle_meas, "extrapolated": True, "extrapolation_factor": oracle_sec / max(oracle_meas, 1e-12),
         "sample": "per scene, 1 state: projection + 4 bands of 2 whole rows (FP64 forward on %s threads), "
                   "adjoint fixed part + 64 random pixels (1 thread), extrapolated to the scene's 64 states"
                   % threads}
@@ -445,11 +506,11 @@ def run_mix(args):
             "gpu_launches": (launches_per_step * args.steps) if use_graph else eager_launches,
             "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}, "peaks": pk_kind}
-    print(json.dumps(line), flush=True)
     for c in scenes:
         c["plan"].close()
     arena.close()
     R.close()
+    return line
 
 
 def run_groups(args):
@@ -516,53 +577,15 @@ def run_groups(args):
                     states.cam.nbytes, "d2h_bytes_per_step": G * 32},
             "gpu_launches": launches, "clocks": clk,
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
-    print(json.dumps(line), flush=True)
     R.close()
+    return line
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3_fwdbwd_250k")
-    ap.add_argument("--scale", type=float, default=1.0)
-    ap.add_argument("--states", type=int, default=None, help="override the workload's state count")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--tile-size", type=int, default=0, choices=[0, 16, 32],
-                    help="sort tile side (0: the library chooses per batch shape)")
-    ap.add_argument("--entry-headroom", type=float, default=1.1,
-                    help="plan path: tile-entry capacity as a multiple of the sizing run's entries")
-    ap.add_argument("--loss", default="mse", choices=["mse", "eq2"],
-                    help="training loss: mean MSE, or Eq. 2 (MSE + 0.2 (1 - SSIM), CVaR_0.05 tail)")
-    args = ap.parse_args()
-    assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
-
-    from paper_2606_17212_b300 import synth
+def run_main(args, w):
+    """The training step (or the distortion pass of a utility workload): eager
+    context calls and, for training, one replayed CUDA graph of a capture-safe
+    plan; the faster is the headline.  Returns the JSON line (rank 0) or None."""
     ws, rank, local = _dist()
-    if args.workload == "c4_group_utility":
-        if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable": "the utility-table mode has no reference-arm "
-                              "mode; the oracle's Eq. 3/4 is checked in the tests"}), flush=True)
-            return
-        if rank == 0:
-            run_groups(args)
-        return
-    if args.workload == "c5_mix_48":
-        if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable": "the serving mix has no reference-arm mode; "
-                              "its oracle baseline is the cpu_baseline of the ours arm"}), flush=True)
-            return
-        if rank == 0:
-            run_mix(args)
-        return
-    w = synth.config(args.workload, scale=args.scale, n_states=args.states)
-    if args.impl == "reference":
-        reference_arm(args, w)
-        return
-
     import torch
     from paper_2606_17212_b300 import dgs
     if ws > 1:
@@ -724,7 +747,7 @@ def main():
     # ---- plain per-state path (one state per launch sequence, synchronized)
     plain = None
     if not args.no_plain and rank == 0:
-        n_plain = S
+        n_plain = S if training else min(S, 256)     # distortion workloads: a bounded sample of states
 
         def plain_state(s):
             # one state per call sequence, with the same arguments for forward and
@@ -753,40 +776,57 @@ def main():
     dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 1))
     dom_name, (dom_ms, dom_n) = dom
     dom_ms_per_launch = dom_ms / max(dom_n, 1)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = pk.get("sm_max_mhz", 2032.0)
     cpu = None
     roof = None
-    evals_per_px = None
-    if rank == 0:
-        n_samp = 2 if training else 4
-        sec_state, evals_per_px, threads, desc = oracle_sample(w, n_states=n_samp, n_bands=16, n_pix=1024,
-                                                                want_backward=training)
+    kernels_roof = None
+    if rank == 0 and not args.no_oracle_sample:
+        samp = oracle_sample(w, list(range(2 if training else 4)), want_backward=training)
         if not args.no_cpu_baseline:
-            cpu = {"value": 1.0 / sec_state, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
-        sm_mhz = pk.get("sm_max_mhz", 2032.0)
-        fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12     # TFLOP/s, FP32 FMA, all SMs
-        evals_per_launch = evals_per_px * H * W * S
+            cpu = {"value": 1.0 / samp["sec_per_state"], "unit": UNIT, "cores": samp["threads"], "kind": "oracle",
+                   "sample": samp["desc"], "sampled_s": samp["sampled_s"], "extrapolated": True,
+                   "extrapolation_factor": samp["extrapolation"]}
+        evals_per_state = samp["evals_per_px"] * H * W
+        reuse_frac = 1.0
         if not training:
             # tile reuse: only the rendered (state, tile) pairs are raster work
             pairs, rendered, _ = reuse
-            launches_per_step = dom_n / max(args.steps, 1)
-            evals_per_launch *= (rendered / max(pairs, 1)) / max(launches_per_step, 1.0)
-        per_eval = BWD_FLOP_PER_EVAL if dom_name == "raster_bwd" else (
-            FWD_FLOP_PER_EVAL if dom_name.startswith("raster_fwd") else None)
-        if per_eval is not None:
-            achieved = per_eval * evals_per_launch / (dom_ms_per_launch / 1e3) / 1e12
+            reuse_frac = rendered / max(pairs, 1)
+
+        def raster_entry(name):
+            ms_k, n_k = prof[name]
+            per_launch = evals_per_state * S * reuse_frac / max(n_k / max(args.steps, 1), 1.0)
             traffic = None
-            rec = MEASURED_TRAFFIC.get((dom_name, w.name))
+            rec = MEASURED_TRAFFIC.get((name, w.name))
             if rec is not None and args.scale == 1.0 and args.states is None:
                 import hashlib
                 src = os.path.join(ROOT, "paper_2606_17212_b300", "csrc", "raster.cu")
                 if hashlib.sha1(open(src, "rb").read()).hexdigest() == rec[1]:
                     traffic = rec[0]
-            roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
-                    "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
-                    "traffic_unit": "bytes per launch (ncu, full size)",
-                    "peak_kind": "FP32 FMA issue peak: 148 SMs x 128 lanes x 2 x %.0f MHz (derived)" % sm_mhz,
-                    "ms_per_launch": dom_ms_per_launch,
-                    "evals_per_launch": evals_per_launch}
+            return raster_roofline(name, per_launch, ms_k / max(n_k, 1), sms, sm_mhz, traffic)
+
+        if dom_name.startswith("raster"):
+            roof = raster_entry(dom_name)
+        kernels_roof = [raster_entry(k) for k in ("raster_fwd", "raster_fwd_mse", "raster_bwd")
+                        if k in prof and k != dom_name]
+        if training and graph_ms is not None:
+            n_rec, n_ent = plan.status()
+            hb = pk.get("hbm_gbs", 6400.0)
+            per = lambda k: prof[k][0] / args.steps if k in prof else None
+            if per("radix_pass"):
+                kernels_roof.append(hbm_entry(
+                    "radix_pass", n_ent * 24 + n_rec * 16, per("radix_pass"), hb,
+                    "each tile entry's (64-bit key, 32-bit value) written once and read once, plus each record's "
+                    "depth key and slot (%d entries, %d records)" % (n_ent, n_rec)))
+            if per("project"):
+                kernels_roof.append(hbm_entry(
+                    "project", scene_bytes(w.scene) + n_rec * 56, per("project"), hb,
+                    "scene read once, 48 B record and 8 B depth key/slot written per record"))
+            if per("image_mse"):
+                kernels_roof.append(hbm_entry(
+                    "image_mse", S * H * W * 24, per("image_mse"), hb,
+                    "image read and gradient written, 12 B per pixel each (targets L2-resident)"))
     cfg = workload_config(w, ws, views, "cuda_graph_plan" if use_graph else "context_calls")
     if training:
         cfg["loss"] = "mean MSE" if args.loss == "mse" else "Eq. 2: MSE + 0.2 (1 - SSIM), 0.3 CVaR_0.05 tail"
@@ -803,7 +843,8 @@ def main():
             "plain_per_state": {"value": plain, "unit": UNIT} if plain else None,
             "batched_vs_plain": (value / ws / plain) if plain else None,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches, "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
+            "gpu_launches": launches, "clocks": clk, "roofline": roof, "roofline_kernels": kernels_roof,
+            "cpu_baseline": cpu,
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "kernels_note": "per-kernel times from the eager path's live events (same kernels as the graph)",
             "peaks": pk_kind}
@@ -813,11 +854,96 @@ def main():
                               "what": "(state, tile) pairs scored per step and how many were rendered; the rest "
                                       "took the partial of a state with the same depths on every cluster the "
                                       "tile's walk reached (bit-identical)"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     R.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
+    return line if rank == 0 else None
+
+
+def run_others(args):
+    """The utility sweep (2.7M Gaussians, 32,768 states) and the serving mix (48
+    SH3 scenes, forward + backward) in the default run, a few steps each and no
+    oracle sampling; a summary of each (or the error it raised) goes into the
+    default line."""
+    import copy
+    import gc
+    import torch
+    from paper_2606_17212_b300 import synth
+    out = {}
+    for name in ("c4_utility_2p7m", "c5_mix_48"):
+        a2 = copy.copy(args)
+        a2.workload, a2.steps, a2.warmup = name, 3, 3
+        a2.no_cpu_baseline = True
+        a2.no_oracle_sample = True
+        a2.states = None
+        t0 = time.perf_counter()
+        try:
+            line = run_mix(a2) if name == "c5_mix_48" else run_main(a2, synth.config(name))
+            keep = ("value", "unit", "ms_per_step", "mpix_per_s", "plain_per_state", "batched_vs_plain",
+                    "tile_reuse", "gpu_launches", "clocks", "e2e", "eager_per_step", "graph_per_step")
+            summ = {k: line.get(k) for k in keep if line.get(k) is not None}
+            summ["config"] = line["config"]
+            summ["steps"], summ["warmup"] = a2.steps, a2.warmup
+            summ["wall_s"] = round(time.perf_counter() - t0, 1)
+            out[name] = summ
+        except Exception as e:      # reported, never fatal to the headline line
+            out[name] = {"error": "%s: %s" % (type(e).__name__, str(e)[:300])}
+        gc.collect()
+        torch.cuda.empty_cache()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c3_fwdbwd_250k")
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--states", type=int, default=None, help="override the workload's state count")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-others", action="store_true",
+                    help="default workload only: skip the utility-sweep and serving-mix summaries")
+    ap.add_argument("--tile-size", type=int, default=0, choices=[0, 16, 32],
+                    help="sort tile side (0: the library chooses per batch shape)")
+    ap.add_argument("--entry-headroom", type=float, default=1.1,
+                    help="plan path: tile-entry capacity as a multiple of the sizing run's entries")
+    ap.add_argument("--loss", default="mse", choices=["mse", "eq2"],
+                    help="training loss: mean MSE, or Eq. 2 (MSE + 0.2 (1 - SSIM), CVaR_0.05 tail)")
+    args = ap.parse_args()
+    args.no_oracle_sample = False
+    assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
+
+    from paper_2606_17212_b300 import synth
+    ws, rank, local = _dist()
+    if args.workload == "c4_group_utility":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the utility-table mode has no reference-arm "
+                              "mode; the oracle's Eq. 3/4 is checked in the tests"}), flush=True)
+            return
+        if rank == 0:
+            print(json.dumps(run_groups(args)), flush=True)
+        return
+    if args.workload == "c5_mix_48":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the serving mix has no reference-arm mode; "
+                              "its oracle baseline is the cpu_baseline of the ours arm"}), flush=True)
+            return
+        if rank == 0:
+            print(json.dumps(run_mix(args)), flush=True)
+        return
+    w = synth.config(args.workload, scale=args.scale, n_states=args.states)
+    if args.impl == "reference":
+        reference_arm(args, w)
+        return
+
+    line = run_main(args, w)
+    if line is not None:
+        if not args.no_others and args.workload == "c3_fwdbwd_250k" and args.scale == 1.0 and ws == 1:
+            line["other_workloads"] = run_others(args)
+        print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

@@ -60,7 +60,8 @@ enum {
     DGS_E_OOM = -3,           /* workspace allocation failed */
     DGS_E_CUDA = -4,          /* a CUDA runtime call or launch failed */
     DGS_E_CAPACITY = -5,      /* a count exceeds 32-bit indexing */
-    DGS_E_SCRATCH = -6        /* dgs_image_mse_noalloc: sizes exceed its fixed scratch */
+    DGS_E_SCRATCH = -6,       /* dgs_image_mse_noalloc: sizes exceed its fixed scratch */
+    DGS_E_STALE = -7          /* dgs_render_backward: the masks changed after the forward whose images were passed */
 };
 
 /* Doubles of fixed device scratch held by dgs_image_mse_noalloc (512 KiB per GPU). */
@@ -194,8 +195,13 @@ DGS_API int dgs_render_states_batched(dgs_ctx *ctx, const dgs_scene *scene, cons
  * way transmittance is recomputed per tile, not stored.  Refinement layers a
  * state did not deliver get exactly zero from that state.  If the context's
  * last forward call had the same arguments (same pointers, counts, times and
- * cameras) its projection and tile lists are reused; the caller must not have
- * changed the scene or the masks since.
+ * cameras) its projection and tile lists are reused, provided the masks still
+ * hold the bits that forward rendered: the library keeps a device copy of them
+ * and compares (one stream synchronization).  If they changed, the call fails
+ * with DGS_E_STALE when images were passed (they belong to the old masks), and
+ * without images it renders lists for the current masks.  The scene's
+ * attribute values are not compared: they must not change between a forward
+ * and its backward.
  */
 DGS_API int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states,
                         const dgs_camera *cams, int n_cams, const float *bg, const float *images,

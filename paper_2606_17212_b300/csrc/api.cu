@@ -119,7 +119,8 @@ struct dgs_ctx {
     Buf vgs, vgos, depth, need, counts, recBase, total, recs, k0, v0, k1, v1, tcount, toffs, bins, ek0, ev0, ek1, ev1,
         ranges, sortws, scanws, partial, refs, recgrad, refidx, tck0, tcv0, tck1, tcv1, icnt, ioff, qint, counter,
         pairm, grp, gmse, omaps, opart, otpart, oD, oweight, oints, recgmu, gqws,
-        shord, shpair, shpair2, shrep, shflag, shpos, shlist, shitem, shkey, shstop, shseg, shcnt, shtab;
+        shord, shpair, shpair2, shrep, shflag, shpos, shlist, shitem, shkey, shstop, shseg, shcnt, shtab,
+        tapemask;                  // the masks the last forward rendered (checked by the backward)
     bool tile_reuse = true;        // utility passes reuse rendered tiles across states (share.cu)
     int tile_size = 0;             // sort tile side in pixels: 16 or 32, or 0 (chosen per batch shape)
     int active_shift = 4;          // tile shift of the call in progress when tile_size is 0
@@ -659,6 +660,10 @@ int render_batched(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *state
     a.images = images;
     TRY(fwd_pass(ctx, scene, p, L, a, 0, p.S_user, st));
     record_tape(ctx->tape, scene, states, cams, n_cams, p, L);
+    // a copy of the masks rendered: the backward reuses these lists only while the masks still hold them
+    const size_t mbytes = 4 * (size_t)p.S_user * (size_t)((scene->n_clusters * scene->n_layers + 31) / 32);
+    TRY(ensure(ctx, ctx->tapemask, mbytes, st));
+    CK(cudaMemcpyAsync(ctx->tapemask.p, states->masks, mbytes, cudaMemcpyDeviceToDevice, st));
     return DGS_OK;
 }
 
@@ -955,7 +960,23 @@ int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *
         (scene->n_layers > 1 && scene->res_mode == 2 && !grads->res_step))
         return fail(ctx, DGS_E_INVALID_ARG, "gradient array is null");
     Lists L;
-    if (same_call(ctx->tape, scene, states, cams, n_cams) && ctx->tape.plan.tile_shift == p.tile_shift) {
+    bool reuse = same_call(ctx->tape, scene, states, cams, n_cams) && ctx->tape.plan.tile_shift == p.tile_shift;
+    if (reuse) {
+        // same arguments as the last forward: its lists are reused only if the masks
+        // still hold the bits it rendered (compared on the device; one host sync)
+        const size_t words = (size_t)p.S_user * (size_t)((scene->n_clusters * scene->n_layers + 31) / 32);
+        uint32_t *flag = (uint32_t *)ctx->total.p + 4;
+        CK(cudaMemsetAsync(flag, 0, 4, st));
+        launch_words_differ(states->masks, (const uint32_t *)ctx->tapemask.p, words, flag, ctx->sms, st);
+        CK(cudaMemcpyAsync(ctx->h_small + 12, flag, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (ctx->h_small[12]) {
+            if (images)
+                return fail(ctx, DGS_E_STALE, "the masks changed after the forward call whose images were passed");
+            reuse = false;          // no forward images to disagree with: render lists for the current masks
+        }
+    }
+    if (reuse) {
         L = ctx->tape.lists;
     } else {
         ctx->tape.valid = false;

@@ -23,6 +23,8 @@ void launch_clamp_count(const uint32_t *total, uint32_t cap, uint32_t *out, uint
 void launch_ranges(const uint32_t *keys, uint32_t n, uint2 *ranges, int sms, cudaStream_t st,
                    const uint32_t *n_dev = nullptr);
 void launch_zero_prefix(uint32_t *p, uint32_t n_cap, const uint32_t *n_dev, uint32_t per, int sms, cudaStream_t st);
+// *flag |= 1 when the n words of a and b differ anywhere (flag zeroed by the caller)
+void launch_words_differ(const uint32_t *a, const uint32_t *b, size_t n, uint32_t *flag, int sms, cudaStream_t st);
 
 struct RasterArgs {
     const Rec *recs;

@@ -301,6 +301,24 @@ void launch_ranges(const uint32_t *keys, uint32_t n, uint2 *ranges, int sms, cud
     count_launch();
 }
 
+// flag |= 1 when a[i] != b[i] for some i < n
+__global__ void k_words_differ(const uint32_t *__restrict__ a, const uint32_t *__restrict__ b, size_t n,
+                               uint32_t *__restrict__ flag)
+{
+    bool d = false;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        d |= a[i] != b[i];
+    if (__any_sync(0xffffffffu, d) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
+void launch_words_differ(const uint32_t *a, const uint32_t *b, size_t n, uint32_t *flag, int sms, cudaStream_t st)
+{
+    if (n == 0) return;
+    ProfScope ps_("words_differ", st);
+    k_words_differ<<<grid_for((long long)n, 256, sms), 256, 0, st>>>(a, b, n, flag);
+    count_launch();
+}
+
 void launch_zero_prefix(uint32_t *p, uint32_t n_cap, const uint32_t *n_dev, uint32_t per, int sms, cudaStream_t st)
 {
     if (n_cap == 0 || per == 0) return;

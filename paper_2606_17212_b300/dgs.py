@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libdgs.so")
 
 DGS_OK = 0
 ERRORS = {-1: "DGS_E_INVALID_ARG", -2: "DGS_E_UNSUPPORTED", -3: "DGS_E_OOM", -4: "DGS_E_CUDA",
-          -5: "DGS_E_CAPACITY", -6: "DGS_E_SCRATCH"}
+          -5: "DGS_E_CAPACITY", -6: "DGS_E_SCRATCH", -7: "DGS_E_STALE"}
 DGS_E_SCRATCH = -6
 NOALLOC_MAX_PARTS = 65536
 

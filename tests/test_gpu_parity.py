@@ -344,6 +344,31 @@ def test_backward_undelivered_layers_exactly_zero_and_autograd(R, torch):
     assert np.abs(sc.t["mu0"].grad.cpu().numpy()).max() > 0
 
 
+def test_backward_after_masks_changed_in_place(R, torch):
+    """The backward reuses the forward's lists only while the masks still hold
+    the bits the forward rendered: masks edited in place between forward and
+    backward give DGS_E_STALE when the forward's images are passed, and without
+    images the gradients of the current masks (as a fresh forward + backward)."""
+    sc_h, states, cams = _grad_case(seed=4)
+    sc = dgs.DeviceScene.from_host(sc_h)
+    st = dgs.DeviceStates.from_host(states)
+    bg = np.zeros(3, np.float32)
+    imgs = R.render_states_batched(sc, st, cams, bg)
+    dL = torch.sin(torch.arange(imgs.numel(), device="cuda", dtype=torch.float32) * 0.11).reshape(imgs.shape)
+    st.masks[0].zero_()                          # in place: same pointer, other bits
+    with pytest.raises(RuntimeError, match="DGS_E_STALE"):
+        R.render_backward(sc, st, cams, bg, dL, images=imgs)
+    g_now = R.render_backward(sc, st, cams, bg, dL)          # no images: lists for the current masks
+    st2 = dgs.DeviceStates.from_host(states)
+    st2.masks.copy_(st.masks)
+    R.render_states_batched(sc, st2, cams, bg)               # fresh forward of the edited masks
+    g_ref = R.render_backward(sc, st2, cams, bg, dL)
+    for k, v in g_ref.items():
+        ref = float(v.abs().max())
+        assert float((g_now[k] - v).abs().max()) <= 1e-5 * max(ref, 1e-12), k
+    assert float(g_now["res"].abs().max()) > 0
+
+
 # --------------------------------------------------------------------- tile lists
 def _unpack_boxes(recs):
     bx, by, cd = recs[:, 9], recs[:, 10], recs[:, 11]

@@ -39,8 +39,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 REC_FIELDS = ("valid", "mx", "my", "A", "B", "C", "z", "o", "r", "g", "b", "radius",
-              "xlo", "xhi", "ylo", "yhi", "marg_rad", "marg_near", "z32", "d",
-              "vxlo", "vxhi", "vylo", "vyhi", "marg_vbox")
+              "xlo", "xhi", "ylo", "yhi", "marg_rad", "marg_near", "z32", "d")
 
 
 def build(force: bool = False) -> str:
@@ -87,7 +86,7 @@ def _load():
         lib.o_closure.argtypes = [ctypes.c_int, ctypes.c_int, P, P]
         lib.o_project.argtypes = [ctypes.POINTER(_OScene), P, ctypes.c_double, ctypes.POINTER(_OCam), P]
         lib.o_render.argtypes = [ctypes.POINTER(_OScene), P, ctypes.c_double, ctypes.POINTER(_OCam),
-                                 P, ctypes.c_int, P, P, P, P, ctypes.c_int, ctypes.POINTER(_OEps)]
+                                 P, ctypes.c_int, P, P, P, P, ctypes.c_int, ctypes.POINTER(_OEps), P]
         lib.o_render.restype = ctypes.c_int64
         lib.o_render_rows.argtypes = [ctypes.POINTER(_OScene), P, ctypes.c_double, ctypes.POINTER(_OCam), P,
                                       ctypes.c_int, ctypes.c_int, P, P, P]
@@ -96,6 +95,9 @@ def _load():
                                           ctypes.POINTER(_OCam), P, P] + [P] * 10
         lib.o_sh_basis.argtypes = [P, ctypes.c_int, P]
         lib.o_rec_width.restype = ctypes.c_int
+        lib.o_footprint_tiles.argtypes = [ctypes.POINTER(_OScene), P, ctypes.c_double, ctypes.POINTER(_OCam),
+                                          ctypes.c_int, ctypes.c_int64, P, P, P]
+        lib.o_footprint_tiles.restype = ctypes.c_int64
         _lib = lib
     return _lib
 
@@ -162,8 +164,10 @@ def project(scene, depth: np.ndarray, t: float, cam) -> np.ndarray:
     return out[:, :len(REC_FIELDS)]
 
 
-def render(scene, depth, t, cam, bg, pix=None, full_scan=False, eps=None):
-    """Render one state.  Returns (image FP64, marginal flags, evaluations).
+def render(scene, depth, t, cam, bg, pix=None, full_scan=False, eps=None, want_bound=False):
+    """Render one state.  Returns (image FP64, marginal flags, evaluations),
+    and with ``want_bound`` also the per-pixel bound on how far an evaluation
+    deciding the flagged thresholds the other way can move each channel.
 
     ``pix`` = int array [P,2] of (x, y) samples, else the whole [H,W,3] image."""
     lib = _load()
@@ -176,16 +180,20 @@ def render(scene, depth, t, cam, bg, pix=None, full_scan=False, eps=None):
     if pix is None:
         img = np.zeros((cam.height, cam.width, 3), np.float64)
         marg = np.zeros((cam.height, cam.width), np.uint8)
+        bnd = np.zeros((cam.height, cam.width), np.float64)
         lib.o_render(ctypes.byref(pin.s), _ptr(d), float(t), ctypes.byref(oc), _ptr(bgd), 0,
                      None, _ptr(img), _ptr(marg), _ptr(n_eval), int(full_scan),
-                     ctypes.byref(e) if e else None)
+                     ctypes.byref(e) if e else None, _ptr(bnd))
     else:
         p = np.ascontiguousarray(pix, dtype=np.int32).reshape(-1, 2)
         img = np.zeros((p.shape[0], 3), np.float64)
         marg = np.zeros(p.shape[0], np.uint8)
+        bnd = np.zeros(p.shape[0], np.float64)
         lib.o_render(ctypes.byref(pin.s), _ptr(d), float(t), ctypes.byref(oc), _ptr(bgd),
                      p.shape[0], _ptr(p), _ptr(img), _ptr(marg), _ptr(n_eval), 1,
-                     ctypes.byref(e) if e else None)
+                     ctypes.byref(e) if e else None, _ptr(bnd))
+    if want_bound:
+        return img, marg.astype(bool), int(n_eval[0]), bnd
     return img, marg.astype(bool), int(n_eval[0])
 
 
@@ -210,14 +218,14 @@ def state_depths(states, n_clusters, n_layers) -> np.ndarray:
     return np.stack([closure(states.masks[s], n_clusters, n_layers) for s in range(states.n)])
 
 
-def render_states(scene, states, cams, bg, which=None):
+def render_states(scene, states, cams, bg, which=None, want_bound=False):
     """Serial evaluation of every state (the definition batched rendering must equal)."""
     D = state_depths(states, scene.n_clusters, scene.n_layers)
     idx = range(states.n) if which is None else which
     out = []
     for s in idx:
         cam = cams[int(states.cam[s])]
-        out.append(render(scene, D[s], float(states.t[s]), cam, bg))
+        out.append(render(scene, D[s], float(states.t[s]), cam, bg, want_bound=want_bound))
     return out
 
 
@@ -270,6 +278,26 @@ def sh_basis(direction, degree: int = 3) -> np.ndarray:
     Y = np.zeros(16, np.float64)
     lib.o_sh_basis(_ptr(d), int(degree), _ptr(Y))
     return Y[:(degree + 1) ** 2]
+
+
+def footprint_tiles(scene, depth, t, cam, tile):
+    """Tile membership from the footprint alone (S11/S12): every (Gaussian,
+    tile) pair where the Gaussian can composite at some pixel centre of the
+    tile (pixel box and alpha >= 1/255), with a flag for pairs only
+    near-threshold pixels qualify for.  Returns (gaussian index, tile index,
+    marginal) arrays in (Gaussian, tile) order."""
+    lib = _load()
+    pin = _Pinned(scene)
+    d = np.ascontiguousarray(depth, dtype=np.uint8)
+    oc = _cam(cam)
+    n = lib.o_footprint_tiles(ctypes.byref(pin.s), _ptr(d), float(t), ctypes.byref(oc), int(tile), 0,
+                              None, None, None)
+    g = np.zeros(max(n, 1), np.int32)
+    tl = np.zeros(max(n, 1), np.int32)
+    m = np.zeros(max(n, 1), np.uint8)
+    lib.o_footprint_tiles(ctypes.byref(pin.s), _ptr(d), float(t), ctypes.byref(oc), int(tile), int(n),
+                          _ptr(g), _ptr(tl), _ptr(m))
+    return g[:n], tl[:n], m[:n].astype(bool)
 
 
 def float_key(z32: np.ndarray) -> np.ndarray:

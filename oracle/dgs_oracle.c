@@ -86,15 +86,13 @@ typedef struct {            /* tolerances of the marginal rule */
 
 static const OEps kDefaultEps = {2e-3, 1e-4, 1e-4, 4e-7, 1e-5, 1e-6};
 
-enum { REC_W = 26 };
+enum { REC_W = 20 };
 /* Projected record of one present Gaussian (FP64). */
 typedef struct {
     int valid;
     int idx;
     double mx, my, A, B, Cc, z, o, rgb[3], r;
     int xlo, xhi, ylo, yhi;       /* exact pixel box (clamped to the image) */
-    int vxlo, vxhi, vylo, vyhi;   /* visible box: the tile-binning acceleration structure */
-    int marg_vbox;                /* a visible-box edge within tolerance of a pixel boundary */
     int marg_rad, marg_near;
     int has_proj;                 /* projection computed (z > 0, det > 0) */
     float z32;
@@ -361,31 +359,6 @@ static void project_one(const OScene *s, int i, int d, double t, const OCam *cam
     yh = yh > cam->height - 1 ? cam->height - 1 : (yh < -1 ? -1 : yh);
     rec->xlo = (int)xl; rec->xhi = (int)xh; rec->ylo = (int)yl; rec->yhi = (int)yh;
     rec->o = 1.0 / (1.0 + exp(-f->a.logit));
-    /* Visible box (tile binning only; images never depend on it): the pixel box
-     * intersected with the bounding box of o e^power >= 1/255, i.e. of
-     * d^T Q d <= rho = 2 ln(255 o), half-widths sqrt(rho a), sqrt(rho c) of the
-     * dilated covariance, inflated by 1e-3 relative + 0.05 px; empty when
-     * o < 1/255 (no pixel can reach alpha >= 1/255). */
-    rec->vxlo = 0; rec->vxhi = -1; rec->vylo = 0; rec->vyhi = -1;
-    if (rec->o >= 1.0 / 255.0) {
-        double rho = 2.0 * log(255.0 * rec->o);
-        if (rho < 0) rho = 0;
-        double hx = sqrt(rho * f->a2) * 1.001 + 0.05, hy = sqrt(rho * f->c2) * 1.001 + 0.05;
-        if (hx > rec->r) hx = rec->r;
-        if (hy > rec->r) hy = rec->r;
-        double e[4] = {rec->mx - hx - 0.5, rec->mx + hx - 0.5, rec->my - hy - 0.5, rec->my + hy - 0.5};
-        for (int k = 0; k < 4; ++k) {
-            double fr = e[k] - floor(e[k]);
-            if (fr <= eps->box_px || 1.0 - fr <= eps->box_px) rec->marg_vbox = 1;
-        }
-        double vl = ceil(e[0]), vh = floor(e[1]), wl = ceil(e[2]), wh = floor(e[3]);
-        vl = vl < 0 ? 0 : (vl > cam->width ? cam->width : vl);
-        wl = wl < 0 ? 0 : (wl > cam->height ? cam->height : wl);
-        vh = vh > cam->width - 1 ? cam->width - 1 : (vh < -1 ? -1 : vh);
-        wh = wh > cam->height - 1 ? cam->height - 1 : (wh < -1 ? -1 : wh);
-        rec->vxlo = (int)vl; rec->vxhi = (int)vh; rec->vylo = (int)wl; rec->vyhi = (int)wh;
-    }
-    if (fabs(rec->o - 1.0 / 255.0) <= eps->rel_alpha / 255.0) rec->marg_vbox = 1;
     int nc = n_colour(s);
     if (s->sh_degree == 0) {
         for (int k = 0; k < 3; ++k) { f->shv[k] = f->a.col[k]; rec->rgb[k] = f->a.col[k] > 0 ? f->a.col[k] : 0; }
@@ -412,8 +385,7 @@ static void project_one(const OScene *s, int i, int d, double t, const OCam *cam
 
 /* Exported per-Gaussian projection (FP64) for tests and the tile-list check.
  * out[i*REC_W + ...] = valid, mx, my, A, B, C, z, o, r, g, b, radius,
- * xlo, xhi, ylo, yhi, marg_rad, marg_near, z32 (as double), depth d,
- * visible box vxlo, vxhi, vylo, vyhi, marg_vbox. */
+ * xlo, xhi, ylo, yhi, marg_rad, marg_near, z32 (as double), depth d. */
 int o_project(const OScene *s, const uint8_t *depth, double t, const OCam *cam, double *out)
 {
     for (int c = 0; c < s->n_clusters; ++c)
@@ -429,7 +401,6 @@ int o_project(const OScene *s, const uint8_t *depth, double t, const OCam *cam, 
             o[6] = r.z; o[7] = r.o; o[8] = r.rgb[0]; o[9] = r.rgb[1]; o[10] = r.rgb[2];
             o[11] = r.r; o[12] = r.xlo; o[13] = r.xhi; o[14] = r.ylo; o[15] = r.yhi;
             o[16] = r.marg_rad; o[17] = r.marg_near; o[18] = (double)r.z32;
-            o[20] = r.vxlo; o[21] = r.vxhi; o[22] = r.vylo; o[23] = r.vyhi; o[24] = r.marg_vbox;
         }
     return 0;
 }
@@ -465,15 +436,41 @@ static ORec *project_sorted(const OScene *s, const uint8_t *depth, double t, con
 }
 
 /* One pixel, front to back.  Returns colour in out[3]; sets *marg when any
- * threshold decision was within tolerance; counts evaluated candidates. */
+ * threshold decision was within tolerance; counts evaluated candidates.
+ *
+ * *bound (when not NULL) receives a bound on how far, per channel, an
+ * evaluation that decides the flagged thresholds the other way can move the
+ * pixel.  With M bounding every colour behind a decision (the candidates' rgb
+ * and |bg|; a composite behind any point is a convex combination of those):
+ *   - including or skipping one Gaussian of opacity a at transmittance T
+ *     (alpha near 1/255, pixel-box edge, radius rounding, near plane) moves
+ *     the pixel by at most a T 2M;
+ *   - swapping two adjacent Gaussians i, j (depths within rounding) moves it
+ *     by T a_i a_j |rgb_i - rgb_j| <= T a_i a_j 2M (the transmittance after
+ *     both is the same);
+ *   - stopping one Gaussian earlier or later (T (1 - alpha) near 1e-4) moves it
+ *     by at most T 2M, T the transmittance before that Gaussian; earlier
+ *     flipped inclusions change T by up to their summed opacities, so the stop
+ *     window widens by that sum (a cascaded stop flip);
+ *   - the 0.99 clamp is continuous: the pixel does not jump there.
+ * The bound is the sum over the pixel's flagged decisions. */
 static void shade_pixel(const ORec *recs, const int *list, int nlist, int px, int py,
-                        const double *bg, const OEps *eps, double *out, int *marg, int64_t *n_eval)
+                        const double *bg, const OEps *eps, double *out, int *marg, int64_t *n_eval,
+                        double *bound)
 {
     double pcx = px + 0.5, pcy = py + 0.5;
     double T = 1.0, C[3] = {0, 0, 0};
     int mg = 0;
     int64_t ne = 0;
     float prev_z = 0; int have_prev = 0;
+    /* colour scale of the bound: |bg| and the rgb of every candidate reaching the pixel */
+    double M = 0.0, bnd = 0.0, flip_a = 0.0, T_prev = 1.0, a_prev = 0.0;
+    for (int ch = 0; ch < 3; ++ch) M = fabs(bg[ch]) > M ? fabs(bg[ch]) : M;
+    for (int k = 0; k < nlist; ++k) {
+        const ORec *r = &recs[list[k]];
+        if (fabs(pcx - r->mx) <= r->r + 2.0 && fabs(pcy - r->my) <= r->r + 2.0)
+            for (int ch = 0; ch < 3; ++ch) M = r->rgb[ch] > M ? r->rgb[ch] : M;
+    }
     for (int k = 0; k < nlist; ++k) {
         const ORec *r = &recs[list[k]];
         double ax = fabs(pcx - r->mx), ay = fabs(pcy - r->my);
@@ -485,7 +482,12 @@ static void shade_pixel(const ORec *recs, const int *list, int nlist, int px, in
         double reach = r->r + (r->marg_rad ? 1.0 : 0.0) + eps->box_px;
         if (!r->valid) {
             /* kept for the marginal rule only: an FP32 evaluation may keep it */
-            if (ax <= reach && ay <= reach && could && T > 1e-4) mg = 1;
+            if (ax <= reach && ay <= reach && could && T > 1e-4) {
+                mg = 1;
+                const double a = araw < 0.99 ? araw : 0.99;
+                bnd += a * T * 2.0 * M;
+                flip_a += a;
+            }
             continue;
         }
         int inside = px >= r->xlo && px <= r->xhi && py >= r->ylo && py <= r->yhi;
@@ -496,21 +498,42 @@ static void shade_pixel(const ORec *recs, const int *list, int nlist, int px, in
         }
         int edge = (edge_x && ay <= reach) || (edge_y && ax <= reach) || r->marg_near;
         if (!inside) {
-            if (edge && ax <= reach && ay <= reach && could && T > 1e-4) mg = 1;
+            if (edge && ax <= reach && ay <= reach && could && T > 1e-4) {
+                mg = 1;
+                const double a = araw < 0.99 ? araw : 0.99;
+                bnd += a * T * 2.0 * M;
+                flip_a += a;
+            }
             continue;
         }
         ++ne;
-        if (fabs(pw) <= 1e-5 * pmag && pmag > 0 && araw >= 1.0 / 255.0) mg = 1;
+        if (fabs(pw) <= 1e-5 * pmag && pmag > 0 && araw >= 1.0 / 255.0) {
+            mg = 1;                 /* power ~ 0: the sign test may go either way */
+            const double a = r->o < 0.99 ? r->o : 0.99;
+            bnd += a * T * 2.0 * M;
+            flip_a += a;
+        }
         if (pw > 0) continue;
         double alpha = araw < 0.99 ? araw : 0.99;
         if (fabs(araw - 0.99) <= eps->rel_alpha * 0.99) mg = 1;
-        if (fabs(alpha - 1.0 / 255.0) <= eps->rel_alpha / 255.0) mg = 1;
+        if (fabs(alpha - 1.0 / 255.0) <= eps->rel_alpha / 255.0) {
+            mg = 1;
+            const double a = (1.0 / 255.0) * (1.0 + eps->rel_alpha);
+            bnd += a * T * 2.0 * M;
+            flip_a += a;
+        }
         if (alpha < 1.0 / 255.0) continue;
         if (edge) mg = 1;
-        if (have_prev && fabs((double)r->z32 - (double)prev_z) <= eps->rel_depth * fabs((double)prev_z)) mg = 1;
+        if (edge) { bnd += alpha * T * 2.0 * M; flip_a += alpha; }
+        if (have_prev && fabs((double)r->z32 - (double)prev_z) <= eps->rel_depth * fabs((double)prev_z)) {
+            mg = 1;
+            bnd += T_prev * a_prev * alpha * 2.0 * M;
+        }
         prev_z = r->z32; have_prev = 1;
+        T_prev = T; a_prev = alpha;
         double Tn = T * (1.0 - alpha);
         if (fabs(Tn - 1e-4) <= eps->rel_T * 1e-4) mg = 1;
+        if (fabs(Tn - 1e-4) <= (eps->rel_T + 1.01 * flip_a) * 1e-4) bnd += T * 2.0 * M;
         if (Tn < 1e-4) break;
         for (int ch = 0; ch < 3; ++ch) C[ch] += r->rgb[ch] * alpha * T;
         T = Tn;
@@ -518,6 +541,7 @@ static void shade_pixel(const ORec *recs, const int *list, int nlist, int px, in
     for (int ch = 0; ch < 3; ++ch) out[ch] = C[ch] + T * bg[ch];
     *marg = mg;
     *n_eval += ne;
+    if (bound) *bound = bnd;
 }
 
 /* Candidate pre-filter: a record may affect row py only if the row centre is
@@ -543,7 +567,8 @@ static int row_candidates(const ORec *recs, int m, int py, int *list)
  */
 /* Rows [y0, y1) of the image into image_out [(y1 - y0)][W][3] (marg likewise). */
 static void render_rows(const ORec *recs, int m, int W, int y0, int y1, const double *bg, const OEps *eps,
-                        int full_scan, double *image_out, uint8_t *marg, int64_t *total_marg, int64_t *total_eval)
+                        int full_scan, double *image_out, uint8_t *marg, double *bound, int64_t *total_marg,
+                        int64_t *total_eval)
 {
     int64_t tm = 0, te = 0;
     #pragma omp parallel for schedule(dynamic, 1) reduction(+:tm, te)
@@ -555,7 +580,7 @@ static void render_rows(const ORec *recs, int m, int W, int y0, int y1, const do
         for (int px = 0; px < W; ++px) {
             int mg = 0; int64_t ne = 0;
             const size_t o = (size_t)(py - y0) * W + px;
-            shade_pixel(recs, list, nl, px, py, bg, eps, image_out + o * 3, &mg, &ne);
+            shade_pixel(recs, list, nl, px, py, bg, eps, image_out + o * 3, &mg, &ne, bound ? bound + o : NULL);
             if (marg) marg[o] = (uint8_t)mg;
             tm += mg; te += ne;
         }
@@ -573,7 +598,7 @@ int64_t o_render_rows(const OScene *s, const uint8_t *depth, double t, const OCa
     int m = 0;
     ORec *recs = project_sorted(s, depth, t, cam, &kDefaultEps, &m);
     int64_t total_marg = 0, total_eval = 0;
-    render_rows(recs, m, cam->width, y0, y1, bg, &kDefaultEps, 0, image_out, marg, &total_marg, &total_eval);
+    render_rows(recs, m, cam->width, y0, y1, bg, &kDefaultEps, 0, image_out, marg, NULL, &total_marg, &total_eval);
     free(recs);
     if (n_eval) *n_eval = total_eval;
     return total_marg;
@@ -581,7 +606,7 @@ int64_t o_render_rows(const OScene *s, const uint8_t *depth, double t, const OCa
 
 int64_t o_render(const OScene *s, const uint8_t *depth, double t, const OCam *cam,
                  const double *bg, int npix, const int32_t *pix, double *image_out,
-                 uint8_t *marg, int64_t *n_eval, int full_scan, const OEps *eps_in)
+                 uint8_t *marg, int64_t *n_eval, int full_scan, const OEps *eps_in, double *bound)
 {
     const OEps *eps = eps_in ? eps_in : &kDefaultEps;
     int m = 0;
@@ -589,14 +614,15 @@ int64_t o_render(const OScene *s, const uint8_t *depth, double t, const OCam *ca
     int64_t total_marg = 0, total_eval = 0;
     int W = cam->width, H = cam->height;
     if (pix == NULL) {
-        render_rows(recs, m, W, 0, H, bg, eps, full_scan, image_out, marg, &total_marg, &total_eval);
+        render_rows(recs, m, W, 0, H, bg, eps, full_scan, image_out, marg, bound, &total_marg, &total_eval);
     } else {
         #pragma omp parallel for schedule(dynamic, 16) reduction(+:total_marg, total_eval)
         for (int q = 0; q < npix; ++q) {
             int *list = (int *)malloc(sizeof(int) * (size_t)(m > 0 ? m : 1));
             for (int k = 0; k < m; ++k) list[k] = k;
             int mg = 0; int64_t ne = 0;
-            shade_pixel(recs, list, m, pix[2 * q], pix[2 * q + 1], bg, eps, image_out + (size_t)q * 3, &mg, &ne);
+            shade_pixel(recs, list, m, pix[2 * q], pix[2 * q + 1], bg, eps, image_out + (size_t)q * 3, &mg, &ne,
+                        bound ? bound + q : NULL);
             if (marg) marg[q] = (uint8_t)mg;
             total_marg += mg; total_eval += ne;
             free(list);
@@ -605,6 +631,77 @@ int64_t o_render(const OScene *s, const uint8_t *depth, double t, const OCam *ca
     free(recs);
     if (n_eval) *n_eval = total_eval;
     return total_marg;
+}
+
+/*
+ * Tile membership from the footprint alone (the definition tile binning must
+ * cover; it uses no acceleration structure and none of the GPU path's
+ * constants).  For every Gaussian present in the state, the tiles of side
+ * `tile` that hold at least one pixel centre p with |p - m| <= r on both axes,
+ * power <= 0 and alpha = min(0.99, o e^power) >= 1/255: exactly the pixels
+ * the compositing of S11/S12 can include it at.  A (Gaussian, tile) pair that
+ * only pixels near a threshold qualify for (alpha within rel_alpha of 1/255,
+ * |p - m| within box_px of r, a radius that may round the other way, a mean
+ * at the near plane) is marked marginal: an FP32 evaluation may take or drop
+ * it.  Writes up to cap pairs (Gaussian index, tile index = ty * tiles_x + tx,
+ * marginal) in (Gaussian, tile) order; returns the number of pairs.
+ */
+int64_t o_footprint_tiles(const OScene *s, const uint8_t *depth, double t, const OCam *cam, int tile,
+                          int64_t cap, int32_t *gauss, int32_t *tiles, uint8_t *marg)
+{
+    const OEps *eps = &kDefaultEps;
+    const int W = cam->width, H = cam->height, tiles_x = (W + tile - 1) / tile;
+    int64_t n = 0;
+    for (int c = 0; c < s->n_clusters; ++c) {
+        const int d = depth[c];
+        if (d < 1) continue;
+        for (int i = s->cluster_offsets[c]; i < s->cluster_offsets[c + 1]; ++i) {
+            ORec r;
+            project_one(s, i, d, t, cam, eps, &r, NULL);
+            if (!r.has_proj || !(r.valid || r.marg_rad || r.marg_near)) continue;
+            const double reach = r.r + (r.marg_rad ? 1.0 : 0.0) + eps->box_px;
+            int x0 = (int)ceil(r.mx - reach - 0.5), x1 = (int)floor(r.mx + reach - 0.5);
+            int y0 = (int)ceil(r.my - reach - 0.5), y1 = (int)floor(r.my + reach - 0.5);
+            x0 = x0 < 0 ? 0 : x0; y0 = y0 < 0 ? 0 : y0;
+            x1 = x1 > W - 1 ? W - 1 : x1; y1 = y1 > H - 1 ? H - 1 : y1;
+            if (x0 > x1 || y0 > y1) continue;
+            const int tx0 = x0 / tile, tx1 = x1 / tile, ty0 = y0 / tile, ty1 = y1 / tile;
+            const int tw = tx1 - tx0 + 1, th = ty1 - ty0 + 1;
+            uint8_t *flag = (uint8_t *)calloc((size_t)tw * th, 1);   /* bit 0: sure, bit 1: maybe */
+            for (int py = y0; py <= y1; ++py)
+                for (int px = x0; px <= x1; ++px) {
+                    const double dx = r.mx - (px + 0.5), dy = r.my - (py + 0.5);
+                    const double ax = fabs(dx), ay = fabs(dy);
+                    const double pw = -0.5 * (r.A * dx * dx + r.Cc * dy * dy) - r.B * dx * dy;
+                    const double pmag = 0.5 * fabs(r.A * dx * dx) + 0.5 * fabs(r.Cc * dy * dy) + fabs(r.B * dx * dy);
+                    const double araw = r.o * exp(pw);
+                    const double alpha = araw < 0.99 ? araw : 0.99;
+                    const int inside = r.valid && px >= r.xlo && px <= r.xhi && py >= r.ylo && py <= r.yhi;
+                    const int edge = fabs(ax - r.r) <= eps->box_px || fabs(ay - r.r) <= eps->box_px ||
+                                     (r.marg_rad && (ax > r.r - 1 - eps->box_px || ay > r.r - 1 - eps->box_px)) ||
+                                     r.marg_near;
+                    const int sure = inside && !edge && pw <= 0 && fabs(pw) > 1e-5 * pmag &&
+                                     alpha >= (1.0 / 255.0) * (1.0 + eps->rel_alpha);
+                    const int maybe = pw <= 1e-5 * pmag && alpha >= (1.0 / 255.0) * (1.0 - eps->rel_alpha);
+                    uint8_t *f = &flag[(size_t)(py / tile - ty0) * tw + (px / tile - tx0)];
+                    if (sure) *f |= 1;
+                    else if (maybe) *f |= 2;
+                }
+            for (int ty = 0; ty < th; ++ty)
+                for (int tx = 0; tx < tw; ++tx) {
+                    const uint8_t f = flag[(size_t)ty * tw + tx];
+                    if (!f) continue;
+                    if (n < cap) {
+                        gauss[n] = i;
+                        tiles[n] = (ty0 + ty) * tiles_x + (tx0 + tx);
+                        marg[n] = (uint8_t)((f & 1) ? 0 : 1);
+                    }
+                    ++n;
+                }
+            free(flag);
+        }
+    }
+    return n;
 }
 
 /* ---------------- adjoint ---------------- */

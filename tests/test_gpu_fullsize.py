@@ -2,9 +2,11 @@
 
 The oracle cannot render 250k-2.7M Gaussian scenes in full, so these tests check
 sampled outputs it computes one pixel at a time (forward) and the adjoint of
-sampled pixels (backward: dL/dI is non-zero only at sampled, non-marginal
-pixels, so the oracle's adjoint costs one pixel scan per sample), plus
-properties that hold at any size.
+sampled pixels (backward: dL/dI is non-zero only at sampled pixels, so the
+oracle's adjoint costs one pixel scan per sample), plus properties that hold at
+any size.  Every sampled pixel is compared: where the oracle flags a threshold
+decision FP32 may take the other way, the tolerance adds the oracle's derived
+bound on how far that decision moves the pixel.
 """
 import numpy as np
 import pytest
@@ -43,11 +45,14 @@ def _check_sampled(w, imgs, which, rng, n_pix=96):
     for s in which:
         cam = w.cams[int(w.states.cam[s])]
         pix = _samples(rng, cam.width, cam.height, n_pix)
-        ref, marg, _ = oracle.render(w.scene, D[s], float(w.states.t[s]), cam, w.bg, pix=pix)
+        ref, marg, _, bnd = oracle.render(w.scene, D[s], float(w.states.t[s]), cam, w.bg, pix=pix,
+                                          want_bound=True)
         got = imgs[s][pix[:, 1], pix[:, 0]].astype(np.float64)
-        err = np.abs(got - ref)[~marg]
+        err = np.abs(got - ref) - bnd[:, None]
         assert err.max() <= IMG_TOL, (s, err.max(), int(marg.sum()))
-        assert marg.mean() < 0.10          # ~200 Gaussians per pixel: near-threshold cases are common
+        # ~150 Gaussians per pixel: near-threshold decisions are common, but their
+        # derived bounds stay small; few pixels are checked only loosely
+        assert (bnd > 1e-2).mean() <= 0.03, (s, np.sort(bnd)[-5:])
         out[s] = (pix, marg)
     return out
 
@@ -73,7 +78,7 @@ def test_fwdbwd_250k_full_size(R, torch):
     ref = None
     for s in which:
         pix, marg = samp[s]
-        keep = pix[~marg]
+        keep = pix
         dL[s, keep[:, 1], keep[:, 0]] = rng.normal(size=(len(keep), 3)).astype(np.float32)
         g = oracle.render_backward(w.scene, D[s], float(w.states.t[s]), w.cams[int(w.states.cam[s])], w.bg,
                                    dL[s].astype(np.float64))
@@ -163,7 +168,7 @@ def test_serving_mix_scenes_full_size(R, torch):
         ref = None
         for s in which:
             pix, marg = samp[s]
-            keep = pix[~marg]
+            keep = pix
             dL[s, keep[:, 1], keep[:, 0]] = rng.normal(size=(len(keep), 3)).astype(np.float32)
             g = oracle.render_backward(w.scene, D[s], float(w.states.t[s]), w.cams[int(w.states.cam[s])], w.bg,
                                        dL[s].astype(np.float64))

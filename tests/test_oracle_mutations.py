@@ -76,6 +76,15 @@ MUTATIONS = [
     ("quantized decode uses the wrong step index", C,
      "return (double)s->res_q[o] * (double)s->res_step[(size_t)(l - 1) * K + k];",
      "return (double)s->res_q[o] * (double)s->res_step[(size_t)(l - 1) * K];"),
+    ("derived bound of an early-stop flip dropped", C,
+     "        if (fabs(Tn - 1e-4) <= (eps->rel_T + 1.01 * flip_a) * 1e-4) bnd += T * 2.0 * M;",
+     "        if (fabs(Tn - 1e-4) <= (eps->rel_T + 1.01 * flip_a) * 1e-4) bnd += 0.0;"),
+    ("derived bound of an alpha-threshold flip too small", C,
+     "            const double a = (1.0 / 255.0) * (1.0 + eps->rel_alpha);",
+     "            const double a = (1.0 / 255.0) * 0.1;"),
+    ("derived bound of a depth-order swap too small", C,
+     "            bnd += T_prev * a_prev * alpha * 2.0 * M;",
+     "            bnd += T_prev * a_prev * alpha * 0.2 * M;"),
     ("SSIM constants swapped in the structure term", PY,
      "a1, a2 = 2 * mx * my + SSIM_C1, 2 * sxy + SSIM_C2",
      "a1, a2 = 2 * mx * my + SSIM_C1, 2 * sxy + SSIM_C1"),

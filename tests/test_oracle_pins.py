@@ -147,6 +147,86 @@ def test_early_stop_after_thirteen_halvings():
     assert np.allclose(img[64, 64], col * (1 - T) + T * bg, rtol=0, atol=1e-9)
 
 
+def _bracket_float32_logit(alpha_star):
+    """Two float32 logits whose sigmoids (in FP64, as the oracle decodes them)
+    lie just below and just above alpha_star."""
+    sig = lambda x: 1.0 / (1.0 + math.exp(-float(x)))
+    l = np.float32(logit_of(alpha_star))
+    while sig(l) >= alpha_star:
+        l = np.nextafter(l, np.float32(-np.inf))
+    lo = l
+    hi = np.nextafter(lo, np.float32(np.inf))
+    while sig(hi) < alpha_star:
+        hi = np.nextafter(hi, np.float32(np.inf))
+    assert sig(lo) < alpha_star <= sig(hi)
+    return float(lo), float(hi)
+
+
+def test_derived_bound_covers_the_alpha_threshold_jump():
+    """A Gaussian whose alpha straddles 1/255 on a pixel centre: the two sides
+    differ by about (1/255) |c - bg| there, and the oracle's derived bound at
+    that (flagged) pixel covers the jump on both sides; unflagged pixels carry
+    a zero bound."""
+    mu, _, col = _one_gaussian_at_pixel_centre()
+    bg = np.array([0.1, 0.3, 0.05])
+    out = []
+    for lg in _bracket_float32_logit(1.0 / 255.0):
+        sc = tiny_scene(mu, [[-2.5] * 3], [[1, 0, 0, 0]], [lg], [col])
+        out.append(oracle.render(sc, np.array([1], np.uint8), 0.0, axis_camera(), bg, want_bound=True))
+    (a, ma, _, ba), (b, mb, _, bb) = out
+    jump = np.abs(a - b).max(axis=2)
+    assert jump[64, 64] > 0.5 * (1.0 / 255.0) * 0.5          # the Gaussian is in one side only
+    assert ma[64, 64] and mb[64, 64]
+    # the decision jumps; the perturbation of the input moves other pixels continuously (<< 1e-7)
+    assert np.all(jump <= np.minimum(ba, bb) + 1e-7)
+    assert np.all(ba[~ma] == 0) and np.all(bb[~mb] == 0)
+
+
+def test_derived_bound_covers_the_early_stop_jump():
+    """Thirteen alpha = 1/2 Gaussians leave T = 2^-13 on one ray; a fourteenth
+    whose alpha puts T (1 - alpha) on either side of 1e-4 stops the pixel or
+    composites (then a fifteenth stops it).  The two sides differ by
+    T alpha |c - bg| and the derived bound at the flagged pixel covers it."""
+    T13 = 2.0 ** -13
+    a_star = 1.0 - 1e-4 / T13
+    zs = np.linspace(2.0, 3.9, 15)
+    mu = [[4.0 - z, z / 256.0, -z / 256.0] for z in zs]
+    bg = np.array([1.0, 0.5, 0.0])
+    cols = [[0.25] * 3] * 13 + [[0.0, 0.9, 0.6], [0.3, 0.3, 0.3]]
+    out = []
+    for lg in _bracket_float32_logit(a_star):
+        sc = tiny_scene(mu, [[-3.0] * 3] * 15, [[1, 0, 0, 0]] * 15, [0.0] * 13 + [lg, 0.0], cols)
+        out.append(oracle.render(sc, np.array([1], np.uint8), 0.0, axis_camera(), bg, want_bound=True))
+    (a, ma, _, ba), (b, mb, _, bb) = out
+    jump = np.abs(a - b).max(axis=2)
+    assert jump[64, 64] > 0.5 * T13 * a_star * 0.5
+    assert ma[64, 64] and mb[64, 64]
+    # the decision jumps; the perturbation of the input moves other pixels continuously (<< 1e-7)
+    assert np.all(jump <= np.minimum(ba, bb) + 1e-7)
+
+
+def test_derived_bound_covers_a_depth_order_swap():
+    """Two Gaussians on one ray at depths one float32 ulp apart (flagged as a
+    near tie): swapping their order moves the pixel by T a1 a2 |c1 - c2|, within
+    the derived bound of both orders."""
+    z1 = np.float32(2.5)
+    z2 = np.nextafter(z1, np.float32(np.inf))
+    bg = np.array([0.05, 0.05, 0.5])
+    cols = [(0.7, 0.1, 0.3), (0.2, 0.9, 0.1)]
+    out = []
+    for za, zb in ((z1, z2), (z2, z1)):
+        mu = [[4.0 - float(za), float(za) / 256.0, -float(za) / 256.0],
+              [4.0 - float(zb), float(zb) / 256.0, -float(zb) / 256.0]]
+        sc = tiny_scene(mu, [[-3.0] * 3] * 2, [[1, 0, 0, 0]] * 2, [logit_of(0.6), logit_of(0.8)], cols)
+        out.append(oracle.render(sc, np.array([1], np.uint8), 0.0, axis_camera(), bg, want_bound=True))
+    (a, ma, _, ba), (b, mb, _, bb) = out
+    jump = np.abs(a - b).max(axis=2)
+    assert jump[64, 64] > 0.01
+    assert ma[64, 64] and mb[64, 64]
+    # the decision jumps; the perturbation of the input moves other pixels continuously (<< 1e-7)
+    assert np.all(jump <= np.minimum(ba, bb) + 1e-7)
+
+
 def test_on_axis_covariance_and_radius_closed_form():
     """On the optical axis J = diag(f/z, f/z) | 0, so Sigma2D = (f/z)^2 [W Sigma3 W^T]_2x2 + 0.3 I."""
     rng = np.random.default_rng(5)
@@ -539,33 +619,33 @@ def test_undelivered_residuals_get_exactly_zero_gradient():
         assert np.all(g["res"][d - 1:, i] == 0.0)
 
 
-def test_visible_box_contains_every_contributing_pixel():
-    """The tile-binning box (pixel box cut to the alpha >= 1/255 ellipse's bounding
-    box) keeps every pixel whose alpha reaches 1/255 and never exceeds the pixel box."""
+@pytest.mark.parametrize("tile", [16, 32])
+def test_footprint_tiles_are_where_a_lone_gaussian_changes_the_image(tile):
+    """Tile membership from the footprint, pinned to the compositing: rendered
+    alone over a background it never matches, a Gaussian changes exactly the
+    pixels it composites at, so the tiles holding a changed pixel must include
+    every tile footprint_tiles marks sure and lie within its sure and marginal
+    tiles."""
     rng = np.random.default_rng(8)
     cam = synth.ring_camera(0, 1, 96, 80, 110.0)
-    n = 200
-    mu = rng.normal(0, 0.6, size=(n, 3))
-    ls = rng.normal(-2.8, 0.5, size=(n, 3))
-    q = rng.normal(size=(n, 4)); q /= np.linalg.norm(q, axis=1, keepdims=True)
-    lg = rng.normal(-1.0, 2.5, size=n)
-    sc = tiny_scene(mu, ls, q, lg, rng.uniform(size=(n, 3)))
-    rec = oracle.project(sc, np.array([1], np.uint8), 0.0, cam)
-    checked = 0
-    for r in rec:
-        if r[0] <= 0:
-            continue
-        vx0, vx1, vy0, vy1 = r[20:24]
-        if vx0 <= vx1 and vy0 <= vy1:
-            assert r[12] <= vx0 and vx1 <= r[13] and r[14] <= vy0 and vy1 <= r[15]
-        for py in range(int(r[14]), int(r[15]) + 1):
-            for px in range(int(r[12]), int(r[13]) + 1):
-                dx, dy = r[1] - (px + 0.5), r[2] - (py + 0.5)
-                pw = -0.5 * (r[3] * dx * dx + r[5] * dy * dy) - r[4] * dx * dy
-                if pw <= 0 and r[7] * math.exp(pw) >= 1.0 / 255.0:
-                    assert vx0 <= px <= vx1 and vy0 <= py <= vy1
-                    checked += 1
-    assert checked > 1000
+    bg = np.array([-1.0, -1.0, -1.0])
+    tiles_x = -(-96 // tile)
+    n_sure = 0
+    for k in range(60):
+        mu = rng.normal(0, 0.6, size=(1, 3))
+        ls = rng.normal(-2.8, 0.5, size=(1, 3))
+        q = rng.normal(size=(1, 4)); q /= np.linalg.norm(q, axis=1, keepdims=True)
+        lg = rng.normal(-1.0, 2.5, size=1)
+        sc = tiny_scene(mu, ls, q, lg, rng.uniform(0.2, 1.0, size=(1, 3)))
+        img, _, _ = oracle.render(sc, np.array([1], np.uint8), 0.0, cam, bg)
+        ys, xs = np.nonzero(np.any(img != bg, axis=2))
+        changed = set((ys // tile * tiles_x + xs // tile).tolist())
+        g, tl, m = oracle.footprint_tiles(sc, np.array([1], np.uint8), 0.0, cam, tile)
+        assert np.all(g == 0)
+        sure, maybe = set(tl[~m].tolist()), set(tl[m].tolist())
+        assert sure <= changed <= sure | maybe, k
+        n_sure += len(sure)
+    assert n_sure > 20
 
 
 def test_row_band_render_equals_full_render_rows():

@@ -245,6 +245,24 @@ DGS_API int dgs_set_tile_reuse(dgs_ctx *ctx, int enable);
  * ctx or another size. */
 DGS_API int dgs_set_tile_size(dgs_ctx *ctx, int size);
 
+/* Cap on the context's workspace (records, tile entries, sort and raster
+ * buffers), in bytes; 0 leaves only the device's free memory as the limit.
+ * A context call (dgs_render_states_batched, dgs_render_backward,
+ * dgs_state_utility, dgs_group_utility) whose workspace would exceed the cap,
+ * or fail to allocate, runs its batch of states in halves, recursively, until
+ * each part fits (the paper's probe for the largest batch that fits a memory
+ * budget, recovering from a failed allocation).  Every state renders the same
+ * bits in any batch, so images and squared errors do not change; gradients
+ * accumulate over the parts (the same up to the order of float additions).
+ * A single state that does not fit fails with DGS_E_OOM.  Plans are sized at
+ * creation and do not split.  Returns DGS_E_INVALID_ARG for a null ctx. */
+DGS_API int dgs_set_memory_budget(dgs_ctx *ctx, uint64_t bytes);
+
+/* The context's workspace bytes now, and how many times a batch was split
+ * because its workspace did not fit (since creation).  Either pointer may be
+ * NULL.  Returns DGS_E_INVALID_ARG for a null ctx. */
+DGS_API int dgs_memory_stats(const dgs_ctx *ctx, uint64_t *workspace_bytes, int64_t *batch_splits);
+
 /*
  * Work of the context's last distortion pass: pairs [host] = (state, tile)
  * pairs it scored, rendered [host] = pairs it rendered (the rest took a
@@ -427,8 +445,11 @@ DGS_API int dgs_debug_tile_lists(dgs_ctx *ctx, uint32_t *n_rec, uint32_t *n_ent,
  *     DGS_E_SCRATCH, launching nothing, when S * ceil(H W / 1024) exceeds
  *     DGS_NOALLOC_MAX_PARTS, and with DGS_E_INVALID_ARG when S > 65535.
  *   - The first call on each device looks up the scratch array's device
- *     address (cudaGetSymbolAddress) with that device current; make that first
- *     call before any stream capture on the device.
+ *     address (cudaGetSymbolAddress) with that device current and keeps it for
+ *     the process; make that first call before any stream capture on the
+ *     device.  The kept address belongs to the device's primary context, which
+ *     the CUDA runtime uses: after cudaDeviceReset, or with another context
+ *     current, the address is stale, so do not call this entry point then.
  *   - Every call on a device shares the one scratch array (each call rewrites
  *     all the partial sums it reads, so nothing needs clearing; the array keeps
  *     the last call's values).  Calls that overlap on the GPU, e.g. on two
@@ -441,8 +462,11 @@ DGS_API int dgs_image_mse_noalloc(const float *images, const float *refs, const 
                                   float *dL_dimages, dgs_stream stream);
 
 /*
- * Launch counters (host side, per context): number of kernels this context
- * launched since creation or the last reset.  Used to report launch counts.
+ * Launch counters (host side).  The library counts every kernel it launches in
+ * one process-wide counter; dgs_kernel_launches returns how many launches
+ * (from any context, plan or the context-free entry point) happened since
+ * this context was created or last reset.  Take the difference around a call
+ * to count that call's launches, with no other library call in between.
  */
 DGS_API int64_t dgs_kernel_launches(const dgs_ctx *ctx);
 DGS_API void dgs_reset_kernel_launches(dgs_ctx *ctx);

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <map>
 #include <string>
+#include <initializer_list>
 #include <utility>
 #include <vector>
 
@@ -123,6 +124,9 @@ struct dgs_ctx {
         tapemask;                  // the masks the last forward rendered (checked by the backward)
     bool tile_reuse = true;        // utility passes reuse rendered tiles across states (share.cu)
     int tile_size = 0;             // sort tile side in pixels: 16 or 32, or 0 (chosen per batch shape)
+    size_t mem_budget = 0;         // cap on the workspace bytes (0: the device's free memory only)
+    size_t ws_bytes = 0;           // workspace bytes held now
+    long long chunk_splits = 0;    // batches split because their workspace did not fit
     int active_shift = 4;          // tile shift of the call in progress when tile_size is 0
     std::map<std::vector<long long>, int> tuned_tile;   // autotuner: call shape -> tile shift
     long long reuse_pairs = 0, reuse_rendered = 0;   // last distortion pass: (state, tile) pairs, rendered
@@ -165,19 +169,60 @@ int ensure(dgs_ctx *ctx, Buf &b, size_t bytes, cudaStream_t st)
 {
     if (bytes == 0) bytes = 256;
     if (b.cap >= bytes) return DGS_OK;
+    size_t want = bytes + bytes / 8;
+    if (ctx->mem_budget && ctx->ws_bytes - b.cap + want > ctx->mem_budget) {
+        want = bytes;
+        if (ctx->ws_bytes - b.cap + want > ctx->mem_budget)
+            return fail(ctx, DGS_E_OOM, "workspace of %zu bytes would exceed the budget of %zu", ctx->ws_bytes -
+                        b.cap + want, ctx->mem_budget);
+    }
     if (b.p) {
         CK(cudaStreamSynchronize(st));
         CK(cudaFree(b.p));
+        ctx->ws_bytes -= b.cap;
         b.p = nullptr;
         b.cap = 0;
     }
-    size_t want = bytes + bytes / 8;
     if (cudaMalloc(&b.p, want) != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, DGS_E_OOM, "device allocation of %zu bytes failed", want);
     }
     b.cap = want;
+    ctx->ws_bytes += want;
     return DGS_OK;
+}
+
+// A view of states [s0, s0 + n) of a batch.
+dgs_states sub_states(const dgs_states *st, int s0, int n, int words)
+{
+    dgs_states r;
+    r.masks = st->masks + (size_t)s0 * words;
+    r.t = st->t + s0;
+    r.cam = st->cam + s0;
+    r.n_states = n;
+    return r;
+}
+
+// Memory-budget batching: run call(sub-batch, first state) on the whole batch
+// and, when the workspace would not fit (DGS_E_OOM), on its two halves,
+// recursively.  Every state renders the same bits in any batch, so the
+// outputs do not depend on the split; calls fail before writing any output
+// when a workspace allocation fails.
+void release_workspace(dgs_ctx *ctx, cudaStream_t st, std::initializer_list<Buf *> keep);
+
+// keep: workspace buffers the call reads or writes across parts (never released)
+template <class F>
+int chunked(dgs_ctx *ctx, const dgs_states *st, int words, int s0, cudaStream_t stream, F call,
+            std::initializer_list<Buf *> keep = {})
+{
+    const int r = call(st, s0);
+    if (r != DGS_E_OOM || st->n_states <= 1) return r;
+    ++ctx->chunk_splits;
+    release_workspace(ctx, stream, keep);   // buffers the failed attempt grew would crowd out the parts
+    const int h = st->n_states / 2;
+    const dgs_states a = sub_states(st, 0, h, words), b = sub_states(st, h, st->n_states - h, words);
+    TRY(chunked(ctx, &a, words, s0, stream, call, keep));
+    return chunked(ctx, &b, words, s0 + h, stream, call, keep);
 }
 
 int ensure_stage(dgs_ctx *ctx, size_t bytes, cudaStream_t st)
@@ -791,18 +836,40 @@ int tuned_choice(dgs_ctx *ctx, const dgs_scene *scene, const Plan &p, int s0, in
 }
 
 // Free every device and host buffer a workspace holds (not the workspace itself).
-void free_ctx_buffers(dgs_ctx *ctx)
+// Every device buffer of a context's workspace.
+std::vector<Buf *> all_bufs(dgs_ctx *ctx)
 {
-    Buf *bufs[] = {&ctx->vgs, &ctx->vgos, &ctx->depth, &ctx->need, &ctx->counts, &ctx->recBase, &ctx->total,
+    return {&ctx->vgs, &ctx->vgos, &ctx->depth, &ctx->need, &ctx->counts, &ctx->recBase, &ctx->total,
                    &ctx->recs, &ctx->k0, &ctx->v0, &ctx->k1, &ctx->v1, &ctx->tcount, &ctx->toffs, &ctx->bins, &ctx->ek0,
                    &ctx->ev0, &ctx->ek1, &ctx->ev1, &ctx->ranges, &ctx->sortws, &ctx->scanws, &ctx->partial,
                    &ctx->refs, &ctx->recgrad, &ctx->refidx, &ctx->tck0, &ctx->tcv0, &ctx->tck1, &ctx->tcv1,
                    &ctx->icnt, &ctx->ioff, &ctx->qint, &ctx->counter, &ctx->pairm, &ctx->grp, &ctx->gmse, &ctx->omaps, &ctx->opart, &ctx->otpart,
                    &ctx->oD, &ctx->oweight, &ctx->oints, &ctx->recgmu, &ctx->gqws, &ctx->shord, &ctx->shpair,
                    &ctx->shpair2, &ctx->shrep, &ctx->shflag, &ctx->shpos, &ctx->shlist, &ctx->shitem, &ctx->shkey, &ctx->shstop,
-                   &ctx->shseg, &ctx->shcnt, &ctx->shtab};
-    for (Buf *b : bufs)
+                   &ctx->shseg, &ctx->shcnt, &ctx->shtab, &ctx->tapemask};
+}
+
+// Free the device workspace except the buffers in `keep` (after the stream's
+// work is done); the next call grows it again.  The lists a backward could
+// reuse are gone with it.
+void release_workspace(dgs_ctx *ctx, cudaStream_t st, std::initializer_list<Buf *> keep)
+{
+    cudaStreamSynchronize(st);
+    for (Buf *b : all_bufs(ctx)) {
+        if (!b->p || std::find(keep.begin(), keep.end(), b) != keep.end()) continue;
+        cudaFree(b->p);
+        ctx->ws_bytes -= b->cap;
+        b->p = nullptr;
+        b->cap = 0;
+    }
+    ctx->tape.valid = false;
+}
+
+void free_ctx_buffers(dgs_ctx *ctx)
+{
+    for (Buf *b : all_bufs(ctx))
         if (b->p) { cudaFree(b->p); b->p = nullptr; b->cap = 0; }
+    ctx->ws_bytes = 0;
     if (ctx->h_stage) { cudaFreeHost(ctx->h_stage); ctx->h_stage = nullptr; }
     if (ctx->h_small) { cudaFreeHost(ctx->h_small); ctx->h_small = nullptr; }
     if (ctx->stage_done) { cudaEventDestroy(ctx->stage_done); ctx->stage_done = nullptr; }
@@ -918,8 +985,14 @@ int dgs_render_states_batched(dgs_ctx *ctx, const dgs_scene *scene, const dgs_st
     CK(cudaSetDevice(ctx->device));
     TRY(check_scene(ctx, scene));
     if (!states) return fail(ctx, DGS_E_INVALID_ARG, "states is null");
-    return tuned_call(ctx, tile_key(TUNE_RENDER, scene, states, cams, n_cams), (cudaStream_t)stream,
-                      [&] { return render_batched(ctx, scene, states, cams, n_cams, bg, images, (cudaStream_t)stream); });
+    const size_t img_vals = (cams && n_cams > 0) ? (size_t)cams[0].width * cams[0].height * 3 : 0;
+    const int words = (scene->n_clusters * scene->n_layers + 31) / 32;
+    return tuned_call(ctx, tile_key(TUNE_RENDER, scene, states, cams, n_cams), (cudaStream_t)stream, [&] {
+        return chunked(ctx, states, words, 0, (cudaStream_t)stream, [&](const dgs_states *sub, int s0) {
+            return render_batched(ctx, scene, sub, cams, n_cams, bg, images ? images + (size_t)s0 * img_vals : nullptr,
+                                  (cudaStream_t)stream);
+        });
+    });
 }
 
 int dgs_render_state(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *mask, float t, const dgs_camera *cam,
@@ -950,66 +1023,74 @@ int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *
         const int known = known_shift(ctx, tile_key(TUNE_RENDER, scene, states, cams, n_cams));
         ctx->active_shift = known >= 0 ? known : (ctx->tape.valid ? ctx->tape.plan.tile_shift : MIN_TILE_SHIFT);
     }
-    Plan p;
-    TRY(build_plan(ctx, states, cams, n_cams, false, p));
-    if (p.S_user == 0 || scene->n == 0) return DGS_OK;
-    if (!dL_dimages) return fail(ctx, DGS_E_INVALID_ARG, "dL_dimages is null");
-    if (!grads->mu0 || !grads->log_scale || !grads->quat || !grads->opacity_logit || !grads->colour ||
-        (scene->temporal_rank > 0 && !grads->u) ||
-        (scene->n_layers > 1 && scene->res_mode != 1 && !grads->res) || (scene->affine && !grads->affine) ||
-        (scene->n_layers > 1 && scene->res_mode == 2 && !grads->res_step))
-        return fail(ctx, DGS_E_INVALID_ARG, "gradient array is null");
-    Lists L;
-    bool reuse = same_call(ctx->tape, scene, states, cams, n_cams) && ctx->tape.plan.tile_shift == p.tile_shift;
-    if (reuse) {
-        // same arguments as the last forward: its lists are reused only if the masks
-        // still hold the bits it rendered (compared on the device; one host sync)
-        const size_t words = (size_t)p.S_user * (size_t)((scene->n_clusters * scene->n_layers + 31) / 32);
-        uint32_t *flag = (uint32_t *)ctx->total.p + 4;
-        CK(cudaMemsetAsync(flag, 0, 4, st));
-        launch_words_differ(states->masks, (const uint32_t *)ctx->tapemask.p, words, flag, ctx->sms, st);
-        CK(cudaMemcpyAsync(ctx->h_small + 12, flag, 4, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (ctx->h_small[12]) {
-            if (images)
-                return fail(ctx, DGS_E_STALE, "the masks changed after the forward call whose images were passed");
-            reuse = false;          // no forward images to disagree with: render lists for the current masks
+    if (!dL_dimages && states->n_states > 0) return fail(ctx, DGS_E_INVALID_ARG, "dL_dimages is null");
+    const size_t img_vals = (cams && n_cams > 0) ? (size_t)cams[0].width * cams[0].height * 3 : 0;
+    // a batch whose workspace does not fit runs in halves (gradients accumulate)
+    auto pass = [&](const dgs_states *sub, int s0) -> int {
+        const float *img_s = images ? images + (size_t)s0 * img_vals : nullptr;
+        const float *dL_s = dL_dimages ? dL_dimages + (size_t)s0 * img_vals : nullptr;
+        Plan p;
+        TRY(build_plan(ctx, sub, cams, n_cams, false, p));
+        if (p.S_user == 0 || scene->n == 0) return DGS_OK;
+        if (!dL_s) return fail(ctx, DGS_E_INVALID_ARG, "dL_dimages is null");
+        if (!grads->mu0 || !grads->log_scale || !grads->quat || !grads->opacity_logit || !grads->colour ||
+            (scene->temporal_rank > 0 && !grads->u) ||
+            (scene->n_layers > 1 && scene->res_mode != 1 && !grads->res) || (scene->affine && !grads->affine) ||
+            (scene->n_layers > 1 && scene->res_mode == 2 && !grads->res_step))
+            return fail(ctx, DGS_E_INVALID_ARG, "gradient array is null");
+        Lists L;
+        bool reuse = same_call(ctx->tape, scene, sub, cams, n_cams) && ctx->tape.plan.tile_shift == p.tile_shift;
+        if (reuse) {
+            // same arguments as the last forward: its lists are reused only if the masks
+            // still hold the bits it rendered (compared on the device; one host sync)
+            const size_t words = (size_t)p.S_user * (size_t)((scene->n_clusters * scene->n_layers + 31) / 32);
+            uint32_t *flag = (uint32_t *)ctx->total.p + 4;
+            CK(cudaMemsetAsync(flag, 0, 4, st));
+            launch_words_differ(sub->masks, (const uint32_t *)ctx->tapemask.p, words, flag, ctx->sms, st);
+            CK(cudaMemcpyAsync(ctx->h_small + 12, flag, 4, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (ctx->h_small[12]) {
+                if (img_s)
+                    return fail(ctx, DGS_E_STALE, "the masks changed after the forward call whose images were passed");
+                reuse = false;          // no forward images to disagree with: render lists for the current masks
+            }
         }
-    }
-    if (reuse) {
-        L = ctx->tape.lists;
-    } else {
-        ctx->tape.valid = false;
-        TRY(prepare(ctx, scene, states->masks, p, false, st, L));
-        record_tape(ctx->tape, scene, states, cams, n_cams, p, L);
-    }
-    const uint32_t nRec = L.nRec;
-    TRY(ensure(ctx, ctx->recgrad, sizeof(float4) * 3 * (size_t)nRec, st));
-    CK(cudaMemsetAsync(ctx->recgrad.p, 0, sizeof(float4) * 3 * (size_t)nRec, st));
-    RasterBwdArgs b;
-    b.f = raster_args(ctx, p, scene->n_clusters, bg, L.evals);
-    b.dL_dimg = dL_dimages;
-    b.img_fwd = images;
-    b.rec_grad = (float4 *)ctx->recgrad.p;
-    launch_raster_bwd(b, st);
-    GradDev g;
-    g.mu0 = grads->mu0; g.u = grads->u; g.ls = grads->log_scale; g.quat = grads->quat;
-    g.logit = grads->opacity_logit; g.colour = grads->colour; g.res = grads->res;
-    g.affine = grads->affine; g.rec_gmu = nullptr;
-    g.res_step = grads->res_step; g.gq = nullptr;
-    if (scene->affine) {
-        TRY(ensure(ctx, ctx->recgmu, sizeof(float) * 3 * ((size_t)nRec + 1), st));
-        g.rec_gmu = (float *)ctx->recgmu.p;
-    }
-    if (scene->res_mode == 2 && scene->n_layers > 1) {
-        const SceneDev sdv = scene_dev(scene);
-        TRY(ensure(ctx, ctx->gqws, sizeof(float) * (size_t)(scene->n_layers - 1) * scene->n * sdv.K, st));
-        g.gq = (float *)ctx->gqws.p;
-    }
-    launch_project_bwd(scene_dev(scene), (const ViewGroup *)ctx->vgs.p, p.V, (const uint32_t *)ctx->need.p,
-                       (const uint32_t *)ctx->recBase.p, (const float4 *)ctx->recgrad.p, g, nRec, ctx->sms, st);
-    CK(cudaGetLastError());
-    return DGS_OK;
+        if (reuse) {
+            L = ctx->tape.lists;
+        } else {
+            ctx->tape.valid = false;
+            TRY(prepare(ctx, scene, sub->masks, p, false, st, L));
+            record_tape(ctx->tape, scene, sub, cams, n_cams, p, L);
+        }
+        const uint32_t nRec = L.nRec;
+        TRY(ensure(ctx, ctx->recgrad, sizeof(float4) * 3 * (size_t)nRec, st));
+        CK(cudaMemsetAsync(ctx->recgrad.p, 0, sizeof(float4) * 3 * (size_t)nRec, st));
+        RasterBwdArgs b;
+        b.f = raster_args(ctx, p, scene->n_clusters, bg, L.evals);
+        b.dL_dimg = dL_s;
+        b.img_fwd = img_s;
+        b.rec_grad = (float4 *)ctx->recgrad.p;
+        launch_raster_bwd(b, st);
+        GradDev g;
+        g.mu0 = grads->mu0; g.u = grads->u; g.ls = grads->log_scale; g.quat = grads->quat;
+        g.logit = grads->opacity_logit; g.colour = grads->colour; g.res = grads->res;
+        g.affine = grads->affine; g.rec_gmu = nullptr;
+        g.res_step = grads->res_step; g.gq = nullptr;
+        if (scene->affine) {
+            TRY(ensure(ctx, ctx->recgmu, sizeof(float) * 3 * ((size_t)nRec + 1), st));
+            g.rec_gmu = (float *)ctx->recgmu.p;
+        }
+        if (scene->res_mode == 2 && scene->n_layers > 1) {
+            const SceneDev sdv = scene_dev(scene);
+            TRY(ensure(ctx, ctx->gqws, sizeof(float) * (size_t)(scene->n_layers - 1) * scene->n * sdv.K, st));
+            g.gq = (float *)ctx->gqws.p;
+        }
+        launch_project_bwd(scene_dev(scene), (const ViewGroup *)ctx->vgs.p, p.V, (const uint32_t *)ctx->need.p,
+                           (const uint32_t *)ctx->recBase.p, (const float4 *)ctx->recgrad.p, g, nRec, ctx->sms, st);
+        CK(cudaGetLastError());
+        return DGS_OK;
+    };
+    return chunked(ctx, states, (scene->n_clusters * scene->n_layers + 31) / 32, 0, st, pass);
 }
 
 int dgs_state_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states, const dgs_camera *cams,
@@ -1020,8 +1101,13 @@ int dgs_state_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *st
     TRY(check_scene(ctx, scene));
     if (!bg) return fail(ctx, DGS_E_INVALID_ARG, "bg is null");
     if (!states) return fail(ctx, DGS_E_INVALID_ARG, "states is null");
-    return tuned_call(ctx, tile_key(TUNE_UTILITY, scene, states, cams, n_cams), (cudaStream_t)stream,
-                      [&] { return utility_pass(ctx, scene, states, cams, n_cams, bg, mse, psnr, (cudaStream_t)stream); });
+    const int words = (scene->n_clusters * scene->n_layers + 31) / 32;
+    return tuned_call(ctx, tile_key(TUNE_UTILITY, scene, states, cams, n_cams), (cudaStream_t)stream, [&] {
+        return chunked(ctx, states, words, 0, (cudaStream_t)stream, [&](const dgs_states *sub, int s0) {
+            return utility_pass(ctx, scene, sub, cams, n_cams, bg, mse ? mse + s0 : nullptr, psnr ? psnr + s0 : nullptr,
+                                (cudaStream_t)stream);
+        });
+    });
 }
 
 int dgs_group_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *contexts, const int32_t *groups,
@@ -1071,8 +1157,11 @@ int dgs_group_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *co
     s2.t = t2.data();
     s2.cam = c2.data();
     s2.n_states = (int)(2 * GM);
-    TRY(tuned_call(ctx, tile_key(TUNE_UTILITY, scene, &s2, cams, n_cams), st,
-                   [&] { return utility_pass(ctx, scene, &s2, cams, n_cams, bg, (double *)ctx->gmse.p, nullptr, st); }));
+    TRY(tuned_call(ctx, tile_key(TUNE_UTILITY, scene, &s2, cams, n_cams), st, [&] {
+        return chunked(ctx, &s2, words, 0, st, [&](const dgs_states *sub, int s0) {
+            return utility_pass(ctx, scene, sub, cams, n_cams, bg, (double *)ctx->gmse.p + s0, nullptr, st);
+        }, {&ctx->pairm, &ctx->grp, &ctx->gmse});     // the paired masks and the MSE output live there
+    }));
     launch_group_stats((const double *)ctx->gmse.p, G, M, alpha, beta, q, delta, stats, st);
     CK(cudaGetLastError());
     return DGS_OK;
@@ -1384,6 +1473,21 @@ int dgs_set_tile_size(dgs_ctx *ctx, int size)
     if (!ctx) return DGS_E_INVALID_ARG;
     if (size != 0 && size != 16 && size != 32) return fail(ctx, DGS_E_INVALID_ARG, "tile size must be 0, 16 or 32");
     ctx->tile_size = size;
+    return DGS_OK;
+}
+
+int dgs_set_memory_budget(dgs_ctx *ctx, uint64_t bytes)
+{
+    if (!ctx) return DGS_E_INVALID_ARG;
+    ctx->mem_budget = (size_t)bytes;
+    return DGS_OK;
+}
+
+int dgs_memory_stats(const dgs_ctx *ctx, uint64_t *workspace_bytes, int64_t *batch_splits)
+{
+    if (!ctx) return DGS_E_INVALID_ARG;
+    if (workspace_bytes) *workspace_bytes = ctx->ws_bytes;
+    if (batch_splits) *batch_splits = ctx->chunk_splits;
     return DGS_OK;
 }
 

@@ -64,7 +64,7 @@ EXPORTS = ("dgs_create", "dgs_destroy", "dgs_last_error", "dgs_version", "dgs_re
            "dgs_plan_last_error", "dgs_plan_render", "dgs_plan_backward", "dgs_plan_utility",
            "dgs_plan_image_mse", "dgs_plan_status", "dgs_arena_create", "dgs_arena_destroy",
            "dgs_group_utility", "dgs_objective", "dgs_set_tile_reuse",
-           "dgs_tile_reuse_stats", "dgs_set_tile_size")
+           "dgs_tile_reuse_stats", "dgs_set_tile_size", "dgs_set_memory_budget", "dgs_memory_stats")
 OBJECTIVE_MAX_STATES = 16384
 UTILITY_MAX_CONTEXTS = 4096
 PLAN_RENDER, PLAN_UTILITY = 1, 2
@@ -100,6 +100,8 @@ def lib():
                                         D, D, D, P, P, P]
         L.dgs_set_tile_reuse.argtypes = [P, I]
         L.dgs_set_tile_size.argtypes = [P, I]
+        L.dgs_set_memory_budget.argtypes = [P, ctypes.c_uint64]
+        L.dgs_memory_stats.argtypes = [P, P, P]
         L.dgs_tile_reuse_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                            ctypes.POINTER(ctypes.c_int32)]
         L.dgs_kernel_launches.argtypes = [P]
@@ -351,6 +353,16 @@ class Renderer:
         """dgs_set_tile_reuse: exact reuse of rendered tiles across the states of
         one view in the distortion passes (on by default; outputs unchanged)."""
         self._check(self._lib.dgs_set_tile_reuse(self.h, 1 if enable else 0), "dgs_set_tile_reuse")
+
+    def set_memory_budget(self, nbytes: int):
+        """dgs_set_memory_budget: cap the workspace; batches that do not fit run in parts."""
+        self._check(self._lib.dgs_set_memory_budget(self.h, int(nbytes)), "dgs_set_memory_budget")
+
+    def memory_stats(self):
+        """dgs_memory_stats: (workspace bytes, batch splits since creation)."""
+        a, b = ctypes.c_uint64(), ctypes.c_int64()
+        self._check(self._lib.dgs_memory_stats(self.h, ctypes.byref(a), ctypes.byref(b)), "dgs_memory_stats")
+        return a.value, b.value
 
     def set_tile_size(self, size: int):
         """dgs_set_tile_size: side of the sort tiles (16 or 32 px, 0 = chosen per batch shape)."""

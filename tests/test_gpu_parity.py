@@ -115,6 +115,42 @@ def test_tile_size_changes_no_bit(R, torch):
         assert err <= 1e-5 * max(ref, 1e-12), (k, err, ref)
 
 
+def test_memory_budget_splits_the_batch_bit_identically(torch):
+    """A context whose workspace budget cannot hold the whole batch renders it
+    in parts: images and per-state MSE are bit-identical to one unbudgeted
+    batch, gradients equal up to float addition order, and the workspace stays
+    within the budget."""
+    w = synth.config("c3_fwdbwd_250k", scale=0.02, n_states=20)
+    sc = dgs.DeviceScene.from_host(w.scene)
+    st = _gpu_states(w)
+    dL = None
+    out = []
+    for budget in (0, None):
+        r = dgs.Renderer(0)
+        r.set_tile_size(16)
+        if budget is None:
+            budget = ws_full // 3
+            r.set_memory_budget(budget)
+        imgs = r.render_states_batched(sc, st, w.cams, w.bg)
+        if dL is None:
+            dL = torch.cos(torch.arange(imgs.numel(), device="cuda", dtype=torch.float32) * 0.05).reshape(imgs.shape)
+        g = r.render_backward(sc, st, w.cams, w.bg, dL * 1e-3, images=imgs)
+        mse, _ = r.state_utility(sc, st, w.cams, w.bg)
+        ws, splits = r.memory_stats()
+        if budget == 0:
+            ws_full = ws
+            assert splits == 0
+        else:
+            assert splits > 0 and ws <= budget, (splits, ws, budget)
+        out.append((imgs.clone(), mse.clone(), {k: v.clone() for k, v in g.items()}))
+        r.close()
+    assert torch.equal(out[0][0], out[1][0])
+    assert torch.equal(out[0][1], out[1][1])
+    for k, v in out[0][2].items():
+        ref = float(v.abs().max())
+        assert float((out[1][2][k] - v).abs().max()) <= 1e-5 * max(ref, 1e-12), k
+
+
 def test_ragged_image_and_edge_cases(R, torch):
     w = synth.config("c2_dynamic_250k", scale=0.01, n_states=3)
     cam = synth.ring_camera(2, 8, 97, 61, 110.0)          # ragged tiles on both axes

@@ -37,6 +37,32 @@ def test_noalloc_matches_image_mse_on_two_calls_in_a_row():
     R.close()
 
 
+def test_noalloc_out_of_range_reference_gives_nan_for_that_image_only():
+    """An index equal to n_refs or negative makes that image's MSE and its
+    dL/dimages NaN (the read is redirected to refs[0], never past refs); the
+    other images still match dgs_image_mse."""
+    import torch
+    R = dgs.Renderer(0)
+    rng = np.random.default_rng(7)
+    S, H, W, n_refs = 4, 33, 21, 2
+    images = torch.from_numpy(rng.uniform(size=(S, H, W, 3)).astype(np.float32)).cuda()
+    refs = torch.from_numpy(rng.uniform(size=(n_refs, H, W, 3)).astype(np.float32)).cuda()
+    idx = np.array([1, n_refs, 0, -1], np.int32)
+    good = [0, 2]
+    mse_ref, _, dL_ref = R.image_mse(images[good], refs, idx[good], weight=0.5, want_grad=True)
+    mse = torch.empty(S, dtype=torch.float64, device="cuda")
+    dL = torch.empty_like(images)
+    for _ in range(2):
+        rc = dgs.image_mse_noalloc(images, refs, torch.from_numpy(idx).cuda(), mse, None, dL, weight=0.5)
+        assert rc == dgs.DGS_OK
+        torch.cuda.synchronize()
+        assert torch.isnan(mse[1]) and torch.isnan(mse[3])
+        assert torch.isnan(dL[1]).all() and torch.isnan(dL[3]).all()
+        assert torch.allclose(mse[good], mse_ref, rtol=1e-12, atol=0)
+        assert torch.allclose(dL[good], dL_ref, rtol=1e-6, atol=1e-12)
+    R.close()
+
+
 def test_noalloc_refuses_sizes_beyond_its_scratch():
     """400 images of 512 x 512 need 400 * ceil(512 * 512 / 1024) = 102,400 partial
     sums > 65,536: refused before any launch.  Every buffer is sized for the shape

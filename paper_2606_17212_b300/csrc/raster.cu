@@ -145,6 +145,7 @@ struct Queue {
 
 struct WarpSmem {
     Queue q;
+    float4 pre[3][32];                // records of the next chunk, copied asynchronously (lane: its entry)
     uint8_t dep[MAX_CLUSTERS];        // the state's delivered depth per cluster
 };
 
@@ -213,29 +214,49 @@ __device__ __forceinline__ Lane<NP> lane_of(int tile, int ox, int oy, const Rast
     return L;
 }
 
-// Examine run entries [e, min(e + 32, end)) (one per lane): keep the ones this
-// state renders whose alpha ellipse reaches the region's pixel centres
-// [x0, x0 + 15] x [y0, y0 + h], and append them in run order at `tail`.
-// Returns the new tail.
-__device__ __forceinline__ uint32_t stage_chunk(const Rec *__restrict__ recs, const uint32_t *__restrict__ evals,
-                                                const uint8_t *dep, uint32_t e, uint32_t end, int rx0, int ry0,
+// Start copying each lane's record (the lane's run entry of the next chunk,
+// record slot `slot`) into the warp's prefetch area; the copies land while
+// the warp composites the entries it has already staged.
+__device__ __forceinline__ void prefetch_records(const Rec *__restrict__ recs, uint32_t slot, bool valid,
+                                                 WarpSmem &sm)
+{
+    const int lane = threadIdx.x & 31;
+    if (valid) {
+        const char *src = reinterpret_cast<const char *>(recs + slot);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&sm.pre[k][lane]);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src + 16 * k) : "memory");
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void prefetch_wait()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncwarp();
+}
+
+// Examine the prefetched chunk (run entries e .. e + 31, one per lane; lanes
+// past the run's end hold nothing): keep the entries this state renders whose
+// pixel box meets the region and whose alpha ellipse reaches its pixel
+// centres [x0, x0 + 15] x [y0, y0 + h], and append them in run order at
+// `tail`.  Returns the new tail.
+__device__ __forceinline__ uint32_t stage_chunk(const uint8_t *dep, uint32_t slot, bool valid, int rx0, int ry0,
                                                 int h, WarpSmem &sm, uint32_t tail)
 {
     const int lane = threadIdx.x & 31;
-    const uint32_t j = e + (uint32_t)lane;
     bool keep = false;
     float4 r0 = make_float4(0, 0, 0, 0), r1 = r0, r2 = r0;
-    uint32_t slot = 0;
-    if (j < end) {
-        slot = __ldg(evals + j);
-        const float4 *p = reinterpret_cast<const float4 *>(recs + slot);
-        r2 = __ldg(p + 2);
+    if (valid) {
+        r2 = sm.pre[2][lane];
         const uint32_t cd = __float_as_uint(r2.w), bx = __float_as_uint(r2.y), by = __float_as_uint(r2.z);
         // the state's variant, whose pixel box meets the region, whose alpha ellipse reaches it
         if (((cd >> 12) & 0xfu) == (uint32_t)dep[cd & 0xfffu] && (int)(bx & 0xffffu) <= rx0 + 15 &&
             (int)(bx >> 16) >= rx0 && (int)(by & 0xffffu) <= ry0 + h && (int)(by >> 16) >= ry0) {
-            r0 = __ldg(p);
-            r1 = __ldg(p + 1);
+            r0 = sm.pre[0][lane];
+            r1 = sm.pre[1][lane];
             const float x0 = (float)rx0 + 0.5f, y0 = (float)ry0 + 0.5f;
             keep = ellipse_meets_rect(r0, r1, x0, x0 + 15.0f, y0, y0 + (float)h);
         }
@@ -369,10 +390,18 @@ __device__ __forceinline__ uint32_t walk(const RasterArgs &a, const Lane<NP> &L,
     const int h = 4 * NP - 1;
     uint32_t e = start, head = 0, tail = 0;
     if (!pix.live()) return e;
+    // pipeline: the records of chunk e are in flight, the slots of chunk e + 32 loaded
+    uint32_t slot = e + L.lane < end ? __ldg(a.evals + e + L.lane) : 0u;
+    prefetch_records(a.recs, slot, e + L.lane < end, sm);
+    uint32_t slot_next = e + CHUNK + L.lane < end ? __ldg(a.evals + e + CHUNK + L.lane) : 0u;
     for (;;) {
         while (tail - head < (uint32_t)CHUNK && e < end) {
-            tail = stage_chunk(a.recs, a.evals, sm.dep, e, end, L.rx0, L.ry0, h, sm, tail);
+            prefetch_wait();
+            tail = stage_chunk(sm.dep, slot, e + L.lane < end, L.rx0, L.ry0, h, sm, tail);
             e += CHUNK;
+            slot = slot_next;
+            if (e < end) prefetch_records(a.recs, slot, e + L.lane < end, sm);
+            slot_next = e + CHUNK + L.lane < end ? __ldg(a.evals + e + CHUNK + L.lane) : 0u;
         }
         if (head == tail) break;
         const uint32_t n = min(tail - head, (uint32_t)CHUNK);
@@ -386,6 +415,7 @@ __device__ __forceinline__ uint32_t walk(const RasterArgs &a, const Lane<NP> &L,
         head += n;
         if (!live || !pix.live()) break;
     }
+    prefetch_wait();                  // no copy may land in the prefetch area after the walk
     return min(e, end);
 }
 

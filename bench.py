@@ -37,13 +37,16 @@ UNIT = "states/s"
 # an FMA as two operations (148 SMs x 128 lanes x 2 x clock), so the FP32
 # fraction is a lower bound; the MUFU peak is the measured ex2.approx rate of
 # this GPU (32 per SM per clock).
-SURVEY_FP32_PER_EVAL = 17
-SURVEY_MUFU_PER_EVAL = 1
+FP32_OPS_PER_EVAL = 17
+MUFU_OPS_PER_EVAL = 1
 MUFU_EX2_PER_SM_CLK = 32
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass); valid only for the
-# kernel source it was taken on (sha1 of csrc/raster.cu) and the workload at full size.
-MEASURED_TRAFFIC = {}
+# kernel source it was taken on (sha1 of csrc/raster.cu), the workload at full size
+# and the sort tile side in pixels.
+MEASURED_TRAFFIC = {
+    ("raster_bwd", "c3_fwdbwd_250k", 32): (792_471_040 + 67_845_632, "67f628806a9144a119661aa71e0a5d07aa5b7d70"),
+}
 
 
 def _dist():
@@ -117,14 +120,14 @@ def raster_roofline(name, evals, ms_per_launch, sms, sm_mhz, traffic=None):
     t = ms_per_launch / 1e3
     fp32_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
     mufu_peak = sms * MUFU_EX2_PER_SM_CLK * sm_mhz * 1e6 / 1e12
-    achieved = SURVEY_FP32_PER_EVAL * evals / t / 1e12
-    mufu = SURVEY_MUFU_PER_EVAL * evals / t / 1e12
+    achieved = FP32_OPS_PER_EVAL * evals / t / 1e12
+    mufu = MUFU_OPS_PER_EVAL * evals / t / 1e12
     return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "traffic": traffic, "traffic_unit": "bytes per launch (ncu)",
             "peak_kind": "FP32 FMA peak from unit counts and clock: %d SMs x 128 lanes x 2 x %.0f MHz (derived)"
                          % (sms, sm_mhz),
             "per_eval": "%d FP32 ops + %d MUFU exp per oracle-counted (pixel, Gaussian, state) evaluation"
-                        % (SURVEY_FP32_PER_EVAL, SURVEY_MUFU_PER_EVAL),
+                        % (FP32_OPS_PER_EVAL, MUFU_OPS_PER_EVAL),
             "mufu": {"achieved": mufu, "peak": mufu_peak, "unit": "T ex2/s", "frac": mufu / mufu_peak,
                      "peak_kind": "measured ex2.approx rate: %d per SM per clock" % MUFU_EX2_PER_SM_CLK},
             "ms_per_launch": ms_per_launch, "evals_per_launch": evals}
@@ -672,6 +675,8 @@ def run_main(args, w):
     reuse = R.tile_reuse_stats() if not training else None     # the timed steps' distortion pass
     prof = R.profile_read()
     R.profile(False)
+    eager_tile = R.last_tile_size()
+    graph_tile = None
 
     # ---- graph path (training): a capture-safe plan, the whole step captured
     # once in a CUDA graph and replayed (masks live in a static device buffer)
@@ -679,6 +684,7 @@ def run_main(args, w):
     if training and args.loss == "mse":     # the Eq. 2 objective call is not capture-safe
         plan = dgs.Plan(R, scene, states, w.cams, w.bg, dgs.PLAN_RENDER, ref_index=ref_index,
                         n_refs=len(views), entry_headroom=args.entry_headroom)
+        graph_tile = plan.tile_size()
         g_masks = states.masks.clone()
         g_mse = torch.empty(S, dtype=torch.float64, device=dev)
         g_psnr = torch.empty_like(g_mse)
@@ -798,7 +804,7 @@ def run_main(args, w):
             ms_k, n_k = prof[name]
             per_launch = evals_per_state * S * reuse_frac / max(n_k / max(args.steps, 1), 1.0)
             traffic = None
-            rec = MEASURED_TRAFFIC.get((name, w.name))
+            rec = MEASURED_TRAFFIC.get((name, w.name, eager_tile))
             if rec is not None and args.scale == 1.0 and args.states is None:
                 import hashlib
                 src = os.path.join(ROOT, "paper_2606_17212_b300", "csrc", "raster.cu")
@@ -828,6 +834,7 @@ def run_main(args, w):
                     "image_mse", S * H * W * 24, per("image_mse"), hb,
                     "image read and gradient written, 12 B per pixel each (targets L2-resident)"))
     cfg = workload_config(w, ws, views, "cuda_graph_plan" if use_graph else "context_calls")
+    cfg["tile_px"] = {"context_calls": eager_tile, "cuda_graph_plan": graph_tile}
     if training:
         cfg["loss"] = "mean MSE" if args.loss == "mse" else "Eq. 2: MSE + 0.2 (1 - SSIM), 0.3 CVaR_0.05 tail"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

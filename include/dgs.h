@@ -263,6 +263,12 @@ DGS_API int dgs_set_memory_budget(dgs_ctx *ctx, uint64_t bytes);
  * NULL.  Returns DGS_E_INVALID_ARG for a null ctx. */
 DGS_API int dgs_memory_stats(const dgs_ctx *ctx, uint64_t *workspace_bytes, int64_t *batch_splits);
 
+/* Sort tile side in pixels (16 or 32) that the context's last prepared batch
+ * used: the fixed size of dgs_set_tile_size, else the autotuner's choice for
+ * that call shape; 0 before the first call.  tile_px [host].  Returns
+ * DGS_E_INVALID_ARG for a null pointer. */
+DGS_API int dgs_last_tile_size(const dgs_ctx *ctx, int32_t *tile_px);
+
 /*
  * Work of the context's last distortion pass: pairs [host] = (state, tile)
  * pairs it scored, rendered [host] = pairs it rendered (the rest took a
@@ -401,6 +407,9 @@ DGS_API int dgs_plan_image_mse(dgs_plan *plan, const float *images, const float 
                                double *psnr, float *dL_dimages, dgs_stream stream);
 /* Synchronizes `stream`; the last call's record and tile-entry counts [host];
  * DGS_E_CAPACITY (and clears the flag) when entries overflowed since the last check. */
+/* Sort tile side in pixels (16 or 32) fixed at the plan's creation.  tile_px [host].
+ * Returns DGS_E_INVALID_ARG for a null pointer. */
+DGS_API int dgs_plan_tile_size(const dgs_plan *plan, int32_t *tile_px);
 DGS_API int dgs_plan_status(dgs_plan *plan, int64_t *n_records, int64_t *n_entries, dgs_stream stream);
 
 /*

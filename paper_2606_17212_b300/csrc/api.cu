@@ -128,6 +128,7 @@ struct dgs_ctx {
     size_t ws_bytes = 0;           // workspace bytes held now
     long long chunk_splits = 0;    // batches split because their workspace did not fit
     int active_shift = 4;          // tile shift of the call in progress when tile_size is 0
+    int last_shift = 0;            // tile shift of the last prepared batch (0: none yet)
     std::map<std::vector<long long>, int> tuned_tile;   // autotuner: call shape -> tile shift
     long long reuse_pairs = 0, reuse_rendered = 0;   // last distortion pass: (state, tile) pairs, rendered
     int reuse_rounds = 0;
@@ -295,6 +296,7 @@ int build_plan(dgs_ctx *ctx, const dgs_states *st, const dgs_camera *cams, int n
     p.S_user = st->n_states;
     p.W = W; p.H = H;
     p.tile_shift = ctx->tile_size == 32 ? 5 : ctx->tile_size == 16 ? 4 : ctx->active_shift;
+    ctx->last_shift = p.tile_shift;
     const int T = 1 << p.tile_shift;
     p.tiles_x = (W + T - 1) / T;
     p.tiles_y = (H + T - 1) / T;
@@ -1491,6 +1493,13 @@ int dgs_memory_stats(const dgs_ctx *ctx, uint64_t *workspace_bytes, int64_t *bat
     return DGS_OK;
 }
 
+int dgs_last_tile_size(const dgs_ctx *ctx, int32_t *tile_px)
+{
+    if (!ctx || !tile_px) return DGS_E_INVALID_ARG;
+    *tile_px = ctx->last_shift ? 1 << ctx->last_shift : 0;
+    return DGS_OK;
+}
+
 int dgs_tile_reuse_stats(const dgs_ctx *ctx, int64_t *pairs, int64_t *rendered, int32_t *rounds)
 {
     if (!ctx) return DGS_E_INVALID_ARG;
@@ -1831,6 +1840,13 @@ int dgs_plan_image_mse(dgs_plan *P, const float *images, const float *refs, floa
     launch_mse_reduce((const double *)ctx->partial.p, P->p.S_user, P->image_parts,
                       1.0 / (double)((size_t)P->p.W * P->p.H * 3), mse, psnr, st);
     CK(cudaGetLastError());
+    return DGS_OK;
+}
+
+int dgs_plan_tile_size(const dgs_plan *P, int32_t *tile_px)
+{
+    if (!P || !tile_px) return DGS_E_INVALID_ARG;
+    *tile_px = 1 << P->p.tile_shift;
     return DGS_OK;
 }
 

@@ -62,12 +62,14 @@ __device__ __forceinline__ float lo(f2 x)
 {
     float a, b;
     asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
+    (void)b;
     return a;
 }
 __device__ __forceinline__ float hi(f2 x)
 {
     float a, b;
     asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
+    (void)a;
     return b;
 }
 __device__ __forceinline__ f2 add2(f2 a, f2 b)

@@ -64,7 +64,8 @@ EXPORTS = ("dgs_create", "dgs_destroy", "dgs_last_error", "dgs_version", "dgs_re
            "dgs_plan_last_error", "dgs_plan_render", "dgs_plan_backward", "dgs_plan_utility",
            "dgs_plan_image_mse", "dgs_plan_status", "dgs_arena_create", "dgs_arena_destroy",
            "dgs_group_utility", "dgs_objective", "dgs_set_tile_reuse",
-           "dgs_tile_reuse_stats", "dgs_set_tile_size", "dgs_set_memory_budget", "dgs_memory_stats")
+           "dgs_tile_reuse_stats", "dgs_set_tile_size", "dgs_set_memory_budget", "dgs_memory_stats",
+           "dgs_last_tile_size", "dgs_plan_tile_size")
 OBJECTIVE_MAX_STATES = 16384
 UTILITY_MAX_CONTEXTS = 4096
 PLAN_RENDER, PLAN_UTILITY = 1, 2
@@ -102,6 +103,8 @@ def lib():
         L.dgs_set_tile_size.argtypes = [P, I]
         L.dgs_set_memory_budget.argtypes = [P, ctypes.c_uint64]
         L.dgs_memory_stats.argtypes = [P, P, P]
+        L.dgs_last_tile_size.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+        L.dgs_plan_tile_size.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
         L.dgs_tile_reuse_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                            ctypes.POINTER(ctypes.c_int32)]
         L.dgs_kernel_launches.argtypes = [P]
@@ -364,6 +367,12 @@ class Renderer:
         self._check(self._lib.dgs_memory_stats(self.h, ctypes.byref(a), ctypes.byref(b)), "dgs_memory_stats")
         return a.value, b.value
 
+    def last_tile_size(self) -> int:
+        """dgs_last_tile_size: sort tile side (px) of the last prepared batch, 0 before any."""
+        v = ctypes.c_int32()
+        self._check(self._lib.dgs_last_tile_size(self.h, ctypes.byref(v)), "dgs_last_tile_size")
+        return v.value
+
     def set_tile_size(self, size: int):
         """dgs_set_tile_size: side of the sort tiles (16 or 32 px, 0 = chosen per batch shape)."""
         self._check(self._lib.dgs_set_tile_size(self.h, int(size)), "dgs_set_tile_size")
@@ -604,6 +613,12 @@ class Plan:
         self._check(self._lib.dgs_plan_image_mse(self.h, _ptr(images), _ptr(refs), float(weight), _ptr(mse),
                                                  _ptr(psnr), _ptr(dL), _stream(stream)), "dgs_plan_image_mse")
         return mse, psnr, dL
+
+    def tile_size(self) -> int:
+        """dgs_plan_tile_size: sort tile side (px) fixed at creation."""
+        v = ctypes.c_int32()
+        self._check(self._lib.dgs_plan_tile_size(self.h, ctypes.byref(v)), "dgs_plan_tile_size")
+        return v.value
 
     def status(self, stream=None):
         """(records, entries) of the last call; raises if entries overflowed."""

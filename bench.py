@@ -820,11 +820,15 @@ def run_main(args, w):
             n_rec, n_ent = plan.status()
             hb = pk.get("hbm_gbs", 6400.0)
             per = lambda k: prof[k][0] / args.steps if k in prof else None
-            if per("radix_pass"):
+            if per("radix_depth"):
                 kernels_roof.append(hbm_entry(
-                    "radix_pass", n_ent * 24 + n_rec * 16, per("radix_pass"), hb,
-                    "each tile entry's (64-bit key, 32-bit value) written once and read once, plus each record's "
-                    "depth key and slot (%d entries, %d records)" % (n_ent, n_rec)))
+                    "radix_depth", n_rec * 16, per("radix_depth"), hb,
+                    "each record's depth key and slot read once and written once (%d records)" % n_rec))
+            if per("radix_tile"):
+                kernels_roof.append(hbm_entry(
+                    "radix_tile", n_rec * 16 + n_ent * 8, per("radix_tile"), hb,
+                    "each record's tile rectangle read once, each (view group | tile key, record slot) entry "
+                    "written once (%d entries)" % n_ent))
             if per("project"):
                 kernels_roof.append(hbm_entry(
                     "project", scene_bytes(w.scene) + n_rec * 56, per("project"), hb,

@@ -422,9 +422,11 @@ DGS_API int dgs_plan_status(dgs_plan *plan, int64_t *n_records, int64_t *n_entri
  *               r, g, b (floats; the conic scaled for base-2 exponents:
  *               a2 = -log2(e)/2 A, b2 = -log2(e) B, c2 = -log2(e)/2 C),
  *               box x = xlo | xhi << 16, box y = ylo | yhi << 16,
- *               cluster | depth << 12 | view group << 16 | boxed << 31 (depth 0
- *               = culled; boxed: the 3-sigma box is narrower than the
- *               alpha >= 1/255 box on some axis)
+ *               cluster | clamp << 11 | depth << 12 | view group << 16 |
+ *               boxed << 31 (cluster: 10 bits; depth 0 = culled; boxed: the
+ *               3-sigma box is narrower than the alpha >= 1/255 box on some
+ *               axis; clamp: alpha may reach the 0.99 clamp, set unless
+ *               o <= 0.98 and the conic's condition number is <= 1e4)
  *   depth_keys  [n_rec]  float bits of camera depth, ascending (0xFFFFFFFF = culled)
  *   depth_slots [n_rec]  the record slot of each sorted depth key
  *   entry_keys  [n_ent]  view group * tiles + tile, ascending (stable)

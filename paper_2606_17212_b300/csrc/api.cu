@@ -416,7 +416,7 @@ int prepare(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *masks, const P
                        (uint32_t *)ctx->v0.p, ctx->sms, st);
     bool alt = false;
     CK(radix_sort_pairs((uint32_t *)ctx->k0.p, (uint32_t *)ctx->v0.p, (uint32_t *)ctx->k1.p, (uint32_t *)ctx->v1.p,
-                        nRec, 32, ctx->sortws.p, st, &alt));
+                        nRec, 32, ctx->sortws.p, st, &alt, nullptr, "radix_depth"));
     const uint32_t *order = alt ? (const uint32_t *)ctx->v1.p : (const uint32_t *)ctx->v0.p;
     out.depth_keys = alt ? (uint32_t *)ctx->k1.p : (uint32_t *)ctx->k0.p;
     out.depth_slots = (uint32_t *)order;
@@ -458,7 +458,7 @@ int prepare(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *masks, const P
     launch_tile_costs((const uint2 *)ctx->ranges.p, (uint32_t)vt, (uint32_t *)ctx->tck0.p, (uint32_t *)ctx->tcv0.p,
                       ctx->sms, st);
     CK(radix_sort_pairs((uint32_t *)ctx->tck0.p, (uint32_t *)ctx->tcv0.p, (uint32_t *)ctx->tck1.p,
-                        (uint32_t *)ctx->tcv1.p, vt, 16, ctx->sortws.p, st, &alt));
+                        (uint32_t *)ctx->tcv1.p, vt, 16, ctx->sortws.p, st, &alt, nullptr, "radix_cost"));
     out.tile_order = alt ? (uint32_t *)ctx->tcv1.p : (uint32_t *)ctx->tcv0.p;
     CK(cudaGetLastError());
     return DGS_OK;
@@ -572,8 +572,7 @@ int launch_queue(dgs_ctx *ctx, const Plan &p, const Lists &L, const RasterArgs &
     q.vg_group_base = qt.gbase;
     q.state_order = qt.order;
     q.counter = (uint32_t *)ctx->counter.p;
-    const int blocks = ctx->sms * raster_fwd_blocks_per_sm(qt.G, a.images != nullptr, a.refs != nullptr);
-    launch_raster_fwd(a, q, qt.G, blocks, st);
+    launch_raster_fwd(a, q, qt.G, ctx->sms, st);
     CK(cudaGetLastError());
     return DGS_OK;
 }
@@ -637,8 +636,9 @@ int fwd_pass(dgs_ctx *ctx, const dgs_scene *scene, const Plan &p, const Lists &L
 // The sort tile size (16 or 32 px) changes no output bit, only the cost split
 // between sorting (fewer, larger tiles: fewer entries) and rasterization
 // (longer runs to walk per 16-pixel-wide region).  Unless the caller fixed it,
-// the first call of each shape runs once per candidate, timed with events on
-// its stream, and the faster size is kept for that shape in this context.
+// the first call of each shape runs once untimed, then once per candidate,
+// timed with events on its stream, and the faster size is kept for that
+// shape in this context.
 enum { TUNE_RENDER = 1, TUNE_UTILITY = 2 };
 
 std::vector<long long> tile_key(int kind, const dgs_scene *scene, const dgs_states *states, const dgs_camera *cams,
@@ -668,6 +668,10 @@ int tuned_call(dgs_ctx *ctx, const std::vector<long long> &key, cudaStream_t st,
         ctx->active_shift = known;
         return call();
     }
+    // an untimed first run grows the workspace (and warms the caches) so the
+    // timed runs compare the two sizes on equal terms
+    ctx->active_shift = MIN_TILE_SHIFT;
+    TRY(call());
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -783,7 +787,7 @@ int prepare_dev(dgs_plan *P, const uint32_t *masks, bool force_full, cudaStream_
                    ctx->sms, st);
     bool alt = false;
     CK(radix_sort_pairs((uint32_t *)ctx->k0.p, (uint32_t *)ctx->v0.p, (uint32_t *)ctx->k1.p, (uint32_t *)ctx->v1.p,
-                        P->R_cap, 32, ctx->sortws.p, st, &alt, cnt + 0));
+                        P->R_cap, 32, ctx->sortws.p, st, &alt, cnt + 0, "radix_depth"));
     const uint32_t *order = alt ? (const uint32_t *)ctx->v1.p : (const uint32_t *)ctx->v0.p;
     Lists &out = P->L;
     out.depth_keys = alt ? (uint32_t *)ctx->k1.p : (uint32_t *)ctx->k0.p;
@@ -806,7 +810,7 @@ int prepare_dev(dgs_plan *P, const uint32_t *masks, bool force_full, cudaStream_
     launch_tile_costs((const uint2 *)ctx->ranges.p, (uint32_t)vt, (uint32_t *)ctx->tck0.p, (uint32_t *)ctx->tcv0.p,
                       ctx->sms, st);
     CK(radix_sort_pairs((uint32_t *)ctx->tck0.p, (uint32_t *)ctx->tcv0.p, (uint32_t *)ctx->tck1.p,
-                        (uint32_t *)ctx->tcv1.p, vt, 16, ctx->sortws.p, st, &alt));
+                        (uint32_t *)ctx->tcv1.p, vt, 16, ctx->sortws.p, st, &alt, nullptr, "radix_cost"));
     out.tile_order = alt ? (uint32_t *)ctx->tcv1.p : (uint32_t *)ctx->tcv0.p;
     out.nRec = P->R_cap;
     out.nEnt = P->E_cap;
@@ -912,6 +916,7 @@ int dgs_create(dgs_ctx **out, int device)
         delete ctx;
         return DGS_E_OOM;
     }
+    raster_fwd_query_occupancy();
     ctx->launch_base = g_launches.load();
     *out = ctx;
     return DGS_OK;
@@ -1344,7 +1349,6 @@ int shared_mse_pass(dgs_ctx *ctx, const dgs_scene *scene, const Plan &p, const L
     ctx->h_small[8] = (uint32_t)n0;
     CK(cudaMemcpyAsync(dcnt, ctx->h_small + 8, 4, cudaMemcpyHostToDevice, st));
     a.stop = (uint32_t *)ctx->shstop.p;
-    const int blocks = ctx->sms * raster_fwd_blocks_per_sm(G, false, true, true);
     size_t n = n0;
     ctx->reuse_pairs = (long long)n0;
     ctx->reuse_rendered = 0;
@@ -1376,7 +1380,7 @@ int shared_mse_pass(dgs_ctx *ctx, const dgs_scene *scene, const Plan &p, const L
             q.list_vt = lvt;
             q.list_state = lst;
             q.n_items_dev = dcnt + 2;
-            launch_raster_fwd(a, q, G, blocks, st);
+            launch_raster_fwd(a, q, G, ctx->sms, st);
         }
         // everyone else: take the representative's partial, or regroup
         launch_share_resolve(pvt, pst, pk, prep, dcnt + 0, n, p.geom(), ord_c, ord_fp, depth, C, a.stop, a.partial, flag,

@@ -71,10 +71,14 @@ struct __align__(16) Rec {
     float b;                   // colour b
     uint32_t bx;               // xlo | xhi << 16   (inclusive pixel range)
     uint32_t by;               // ylo | yhi << 16
-    uint32_t cd;               // cluster | depth << 12 | view group << 16 | boxed << 31 (depth 0 = culled;
-                               // boxed: pixels need the box test, the 3-sigma box clips the alpha box)
+    uint32_t cd;               // cluster | clamp << 11 | depth << 12 | view group << 16 | boxed << 31
+                               // (depth 0 = culled; boxed: pixels need the box test, the 3-sigma box
+                               // clips the alpha box; clamp: alpha can reach the 0.99 clamp)
 };
 static_assert(sizeof(Rec) == 48, "record layout");
+constexpr uint32_t REC_CLUSTER = 0x3ffu;     // cluster field of Rec::cd (MAX_CLUSTERS = 1024)
+constexpr uint32_t REC_CLAMP = 1u << 11;     // Rec::cd flag: o 2^p2 can reach the 0.99 clamp
+static_assert(MAX_CLUSTERS <= 1024, "cluster field");
 
 // Per view group (camera, time) parameters, uploaded by the planner.
 struct ViewGroup {
@@ -152,9 +156,10 @@ cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint
 // n_dev the live count is read on the device (n is then the capacity), so the
 // launch sequence does not depend on it (capture-safe).
 size_t radix_workspace_bytes(size_t n);
+// prof: the profiler name of the passes (one name per kind of sort)
 cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, size_t n,
                              int bits, void *ws, cudaStream_t st, bool *result_in_alt,
-                             const uint32_t *n_dev = nullptr);
+                             const uint32_t *n_dev = nullptr, const char *prof = "radix_pass");
 
 // Tile entries of the depth-ordered records, sorted stably by tile key on
 // bits [0, bits), without an unsorted copy: the first pass generates every

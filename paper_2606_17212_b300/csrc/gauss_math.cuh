@@ -176,6 +176,7 @@ struct Proj {
     int xlo, xhi, ylo, yhi;
     bool live;
     bool rclip;                // the 3-sigma box is narrower than the alpha >= 1/255 box on some axis
+    bool aclamp;               // alpha = o 2^p2 may reach the 0.99 clamp at some pixel
 };
 
 // Eq. 1 deformation and EWA projection of decoded attributes `a` of Gaussian i.
@@ -185,6 +186,7 @@ __device__ __forceinline__ void project_fwd(const SceneDev &s, int i, int c, con
 {
     P.live = false;
     P.rclip = false;
+    P.aclamp = true;
     if (s.affine) {   // A_{c,t} mubar + (position residuals)
         float A[12], w;
         int k0, k1;
@@ -277,6 +279,14 @@ __device__ __forceinline__ void project_fwd(const SceneDev &s, int i, int c, con
     // Where the 3-sigma box is not the narrower one, the box holds every pixel
     // the alpha test keeps, so the raster needs no per-pixel box test.
     P.rclip = (P.r < ax) || (P.r < ay);
+    // The raster evaluates the exponent p2 = dT Q' d (Q' the scaled negative-
+    // definite conic) in FP32 as fma(fma(c2, dy, b2 dx), dy, a2 dx dx); its
+    // rounding error is below 16 * 2^-24 * lambda_max |d|^2 while the exact
+    // value is at most -lambda_min |d|^2, so for a condition number below 2^20
+    // the evaluated p2 is never positive and alpha <= o (1 + 2^-21).  Below
+    // o = 0.98 and a condition number of 1e4 the 0.99 clamp is then
+    // unreachable and the raster may skip it; every other record keeps it.
+    P.aclamp = !(P.o <= 0.98f) || !(lam * lam <= 1e4f * F.det);
     // pixel ranges: |x + 0.5 - mx| <= h  <=>  ceil(mx - h - 0.5) <= x <= floor(mx + h - 0.5),
     // evaluated in FP32 (rounding moves an edge only for pixel centres within
     // ~1e-5 px of the boundary), clamped to the image before the integer cast

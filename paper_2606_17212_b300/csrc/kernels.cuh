@@ -67,8 +67,11 @@ struct WorkQueue {
     const uint32_t *n_items_dev = nullptr;
 };
 // G = states composited per staged batch (1, 2, 4 or 8); blocks = persistent grid.
-void launch_raster_fwd(const RasterArgs &a, const WorkQueue &q, int G, int blocks, cudaStream_t st);
-int raster_fwd_blocks_per_sm(int G, bool write, bool mse, bool list = false);
+// persistent grid: sms x the resident blocks per SM of the instantiation launched
+void launch_raster_fwd(const RasterArgs &a, const WorkQueue &q, int G, int sms, cudaStream_t st);
+// query (once) the resident blocks per SM of every forward instantiation, so
+// that no launch inside a stream capture needs a runtime query
+void raster_fwd_query_occupancy();
 void launch_tile_costs(const uint2 *ranges, uint32_t n, uint32_t *keys, uint32_t *vals, int sms, cudaStream_t st);
 void launch_item_counts(const uint32_t *tile_order, uint32_t n, uint32_t tiles, const int32_t *vg_ngroups,
                         uint32_t *counts, int sms, cudaStream_t st);

@@ -115,7 +115,8 @@ __global__ void __launch_bounds__(128, 4) k_project(SceneDev s, const ViewGroup 
                     R.r = P.rgb[0]; R.g = P.rgb[1]; R.b = P.rgb[2];
                     R.bx = (uint32_t)P.xlo | ((uint32_t)P.xhi << 16);
                     R.by = (uint32_t)P.ylo | ((uint32_t)P.yhi << 16);
-                    R.cd = (uint32_t)c | ((uint32_t)d << 12) | ((uint32_t)v << 16) | ((uint32_t)P.rclip << 31);
+                    R.cd = (uint32_t)c | (P.aclamp ? REC_CLAMP : 0u) | ((uint32_t)d << 12) | ((uint32_t)v << 16) |
+                           ((uint32_t)P.rclip << 31);
                     keys[slot] = __float_as_uint(P.z);
                 } else {
                     R.mx = R.my = R.A = R.B = R.C = R.o = R.r = R.g = R.b = 0.0f;

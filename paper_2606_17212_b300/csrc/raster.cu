@@ -58,20 +58,23 @@ __device__ __forceinline__ f2 pk(float a, float b)
     asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
     return r;
 }
+// Halves of a pair.  Both are written as one unpacking move, which ptxas
+// resolves to a register reference; measured, extracting them with 64-bit
+// shifts in C made both raster kernels 4-7% slower.
+#pragma nv_diag_suppress 550
 __device__ __forceinline__ float lo(f2 x)
 {
     float a, b;
     asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
-    (void)b;
     return a;
 }
 __device__ __forceinline__ float hi(f2 x)
 {
     float a, b;
     asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
-    (void)a;
     return b;
 }
+#pragma nv_diag_default 550
 __device__ __forceinline__ f2 add2(f2 a, f2 b)
 {
     f2 d;
@@ -120,18 +123,19 @@ __device__ __forceinline__ float ge1(float x, float y)
 }
 
 // Threshold of the base-2 exponent: alpha = o 2^p2 >= 1/255 <=> p2 >= tau =
-// -log2(255 o) (tau <= 0 for every staged record, whose o >= 1/255).  For
-// p2 <= 0 and tau <= 0 the FP32 bit patterns order by magnitude, so the test
-// is one unsigned compare of bits: bits(p2) <= bits(tau).  A p2 that FP32
-// rounding leaves at +0 or a tiny positive value (the exact power is 0 there:
-// Gaussian centre on the pixel centre) passes as the exact arithmetic does.
-// lg2.approx and ex2.approx err by ~2^-22 relative, so the decision can differ
-// from the exact alpha >= 1/255 only for alpha within ~1e-6 relative of 1/255.
-__device__ __forceinline__ uint32_t tau_bits(float o)
+// -log2(255 o), kept <= -0 (every staged record has o >= 1/255).  A p2 that
+// FP32 rounding leaves at +0 (Gaussian centre on the pixel centre, where the
+// exact power is 0) passes, as the exact arithmetic does.  For such tau the
+// float test p2 >= tau and the unsigned test bits(p2) <= bits(tau) agree
+// (negative floats order by magnitude; every p2 >= +0 passes both), so either
+// form may be used.  lg2.approx and ex2.approx err by ~2^-22 relative, so the
+// decision can differ from the exact alpha >= 1/255 only for alpha within
+// ~1e-6 relative of 1/255.
+__device__ __forceinline__ float tau_of(float o)
 {
     float l;
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(255.0f * o));
-    return __float_as_uint(-l);
+    return -fmaxf(l, 0.0f);
 }
 
 // ------------------------------------------------------------ staging
@@ -141,8 +145,8 @@ struct Queue {
     float4 s0[QCAP];                  // my, my, c2, c2          (records hold the scaled conic)
     float4 s1[QCAP];                  // o, o, r, r
     float4 s2[QCAP];                  // g, g, b, b
-    float4 s3[QCAP];                  // mx, a2, b2, bits(tau)
-    uint4 s4[QCAP];                   // box x, box y, boxed flag, record slot
+    float4 s3[QCAP];                  // mx, a2, b2, tau
+    uint4 s4[QCAP];                   // box x, box y, kind (bit 0: boxed, bit 1: clamp), record slot
 };
 
 struct WarpSmem {
@@ -255,7 +259,7 @@ __device__ __forceinline__ uint32_t stage_chunk(const uint8_t *dep, uint32_t slo
         r2 = sm.pre[2][lane];
         const uint32_t cd = __float_as_uint(r2.w), bx = __float_as_uint(r2.y), by = __float_as_uint(r2.z);
         // the state's variant, whose pixel box meets the region, whose alpha ellipse reaches it
-        if (((cd >> 12) & 0xfu) == (uint32_t)dep[cd & 0xfffu] && (int)(bx & 0xffffu) <= rx0 + 15 &&
+        if (((cd >> 12) & 0xfu) == (uint32_t)dep[cd & REC_CLUSTER] && (int)(bx & 0xffffu) <= rx0 + 15 &&
             (int)(bx >> 16) >= rx0 && (int)(by & 0xffffu) <= ry0 + h && (int)(by >> 16) >= ry0) {
             r0 = sm.pre[0][lane];
             r1 = sm.pre[1][lane];
@@ -270,26 +274,29 @@ __device__ __forceinline__ uint32_t stage_chunk(const uint8_t *dep, uint32_t slo
         q.s0[k] = make_float4(r0.y, r0.y, r1.x, r1.x);
         q.s1[k] = make_float4(r1.y, r1.y, r1.z, r1.z);
         q.s2[k] = make_float4(r1.w, r1.w, r2.x, r2.x);
-        q.s3[k] = make_float4(r0.x, r0.z, r0.w, __uint_as_float(tau_bits(r1.y)));
-        q.s4[k] = make_uint4(__float_as_uint(r2.y), __float_as_uint(r2.z), __float_as_uint(r2.w) >> 31, slot);
+        q.s3[k] = make_float4(r0.x, r0.z, r0.w, tau_of(r1.y));
+        const uint32_t cd = __float_as_uint(r2.w);
+        q.s4[k] = make_uint4(__float_as_uint(r2.y), __float_as_uint(r2.z),
+                             (cd >> 31) | ((cd & REC_CLAMP) ? 2u : 0u), slot);
     }
     __syncwarp();
     return tail + (uint32_t)__popc(bal);
 }
 
 // Per-entry, per-lane terms of one staged entry: the column's exponent terms
-// u = a2 dx^2, v = b2 dx (shared by the lane's eight pixels), the broadcast
-// pairs, and the rows of the lane that lie in the entry's pixel box (only
-// where the record's 3-sigma box clips its alpha box; else all rows).
+// u = a2 dx^2, v = b2 dx (shared by the lane's pixels), the broadcast pairs,
+// and the rows of the lane that lie in the entry's pixel box (only where the
+// record's 3-sigma box clips its alpha box; else all rows).
 struct Ent {
     f2 my, c2, o, r, g, b, uu, vv;
-    uint32_t tau;
+    float tau;                        // exponent threshold (as a float and as its bits)
+    uint32_t taub;
     uint32_t rows;                    // bit r: row r passes the box test
     float dx;
 };
 
-template <int NP>
-__device__ __forceinline__ Ent load_entry(const Queue &q, int k, const Lane<NP> &L, bool boxed)
+template <int NP, bool BOXED>
+__device__ __forceinline__ Ent load_entry(const Queue &q, int k, const Lane<NP> &L)
 {
     Ent E;
     const float4 s0 = q.s0[k], s1 = q.s1[k], s2 = q.s2[k], s3 = q.s3[k];
@@ -299,13 +306,14 @@ __device__ __forceinline__ Ent load_entry(const Queue &q, int k, const Lane<NP> 
     E.r = pk(s1.z, s1.w);
     E.g = pk(s2.x, s2.y);
     E.b = pk(s2.z, s2.w);
-    E.tau = __float_as_uint(s3.w);
+    E.tau = s3.w;
+    E.taub = __float_as_uint(s3.w);
     E.dx = __fsub_rn(s3.x, L.pcx);
     const float u = __fmul_rn(__fmul_rn(s3.y, E.dx), E.dx), v = __fmul_rn(s3.z, E.dx);
     E.uu = pk(u, u);
     E.vv = pk(v, v);
     E.rows = 0xffu;
-    if (boxed) {
+    if (BOXED) {
         const uint4 s4 = q.s4[k];
         const int xlo = (int)(s4.x & 0xffffu), xhi = (int)(s4.x >> 16);
         const int ylo = (int)(s4.y & 0xffffu), yhi = (int)(s4.y >> 16);
@@ -320,15 +328,33 @@ __device__ __forceinline__ Ent load_entry(const Queue &q, int k, const Lane<NP> 
 // clamped opacity alpha of each pixel (0 where the entry is skipped: outside
 // the box or alpha < 1/255).  Returns the pair (alpha0, alpha1); `ar` gets the
 // unclamped o 2^p2 (for the clamp's derivative in the adjoint).
+__device__ __forceinline__ f2 pair_alpha_clamped(const Ent &E, f2 pcy, int j, f2 &dy, f2 &ar)
+{
+    dy = sub2(E.my, pcy);
+    const f2 p2 = fma2(fma2(E.c2, dy, E.vv), dy, E.uu);
+    const float q0 = lo(p2), q1 = hi(p2);
+    ar = mul2(E.o, pk(ex2(q0), ex2(q1)));
+    const bool h0 = __float_as_uint(q0) <= E.taub && ((E.rows >> (2 * j)) & 1u);
+    const bool h1 = __float_as_uint(q1) <= E.taub && ((E.rows >> (2 * j + 1)) & 1u);
+    return pk(h0 ? fminf(A_MAX, lo(ar)) : 0.0f, h1 ? fminf(A_MAX, hi(ar)) : 0.0f);
+}
+
+// The same with the kind of the entry known at compile time: without CLAMP
+// the record cannot reach the 0.99 clamp (o <= 0.98 and a well-conditioned
+// conic: p2 <= 0, see the projection), so min(0.99, o 2^p2) is o 2^p2 and
+// the clamp is left out; the result is the same.
+template <bool BOXED, bool CLAMP>
 __device__ __forceinline__ f2 pair_alpha(const Ent &E, f2 pcy, int j, f2 &dy, f2 &ar)
 {
     dy = sub2(E.my, pcy);
     const f2 p2 = fma2(fma2(E.c2, dy, E.vv), dy, E.uu);
     const float q0 = lo(p2), q1 = hi(p2);
     ar = mul2(E.o, pk(ex2(q0), ex2(q1)));
-    const bool h0 = __float_as_uint(q0) <= E.tau && ((E.rows >> (2 * j)) & 1u);
-    const bool h1 = __float_as_uint(q1) <= E.tau && ((E.rows >> (2 * j + 1)) & 1u);
-    return pk(h0 ? fminf(A_MAX, lo(ar)) : 0.0f, h1 ? fminf(A_MAX, hi(ar)) : 0.0f);
+    // (E.rows is all ones unless BOXED)
+    const bool h0 = __float_as_uint(q0) <= E.taub && ((E.rows >> (2 * j)) & 1u);
+    const bool h1 = __float_as_uint(q1) <= E.taub && ((E.rows >> (2 * j + 1)) & 1u);
+    if (CLAMP) return pk(h0 ? fminf(A_MAX, lo(ar)) : 0.0f, h1 ? fminf(A_MAX, hi(ar)) : 0.0f);
+    return pk(h0 ? lo(ar) : 0.0f, h1 ? hi(ar) : 0.0f);
 }
 
 // ------------------------------------------------------------ forward
@@ -340,10 +366,8 @@ struct FwdPair {
     f2 T, Tk, cr, cg, cb;
 };
 
-__device__ __forceinline__ void fwd_pair(FwdPair &P, const Ent &E, f2 pcy, int j)
+__device__ __forceinline__ void fwd_pair(FwdPair &P, const Ent &E, f2 al)
 {
-    f2 dy, ar;
-    const f2 al = pair_alpha(E, pcy, j, dy, ar);
     const f2 w = mul2(al, P.T);                  // alpha T
     const f2 Tn = sub2(P.T, w);                  // T (1 - alpha)
     const f2 s = pk(ge1(lo(Tn), T_STOP), ge1(hi(Tn), T_STOP));   // 1: composite, 0: stop (or stopped)
@@ -355,8 +379,12 @@ __device__ __forceinline__ void fwd_pair(FwdPair &P, const Ent &E, f2 pcy, int j
     P.T = mul2(Tn, s);
 }
 
+// The forward treats every entry as one that may reach the clamp (one min
+// per pixel): measured, separate code for the records that cannot made the
+// forward slower, not faster.
 template <int NP>
 struct FwdLane {
+    static constexpr bool CLAMP_KINDS = false;
     FwdPair p[NP];
     __device__ __forceinline__ void init(const Lane<NP> &L)
     {
@@ -366,12 +394,16 @@ struct FwdLane {
             p[j].Tk = p[j].cr = p[j].cg = p[j].cb = 0ull;
         }
     }
-    template <bool BOXED>
+    template <bool BOXED, bool CLAMP>
     __device__ __forceinline__ void entry(const Queue &q, int k, const Lane<NP> &L)
     {
-        const Ent E = load_entry(q, k, L, BOXED);
+        const Ent E = load_entry<NP, BOXED>(q, k, L);
 #pragma unroll
-        for (int j = 0; j < NP; ++j) fwd_pair(p[j], E, L.pcy[j], j);
+        for (int j = 0; j < NP; ++j) {
+            f2 dy, ar;
+            const f2 al = pair_alpha_clamped(E, L.pcy[j], j, dy, ar);
+            fwd_pair(p[j], E, al);
+        }
     }
     __device__ __forceinline__ bool live() const
     {
@@ -380,7 +412,35 @@ struct FwdLane {
         for (int j = 0; j < NP; ++j) any |= p[j].T;
         return __any_sync(FULL, any != 0ull);
     }
+    // final colour of pair j: C + (T + Tk) bg
+    __device__ __forceinline__ void out(int j, float bg0, float bg1, float bg2, f2 &o0, f2 &o1, f2 &o2) const
+    {
+        const f2 Tf = add2(p[j].T, p[j].Tk);
+        o0 = fma2(Tf, pk(bg0, bg0), p[j].cr);
+        o1 = fma2(Tf, pk(bg1, bg1), p[j].cg);
+        o2 = fma2(Tf, pk(bg2, bg2), p[j].cb);
+    }
 };
+
+// Hand staged entry k to `pix` with the arithmetic its kind needs (the same
+// entry in every lane: a uniform branch).  Kind bit 0: boxed; bit 1: the
+// record may reach the alpha clamp (told apart only where PIX::CLAMP_KINDS).
+template <class PIX, int NP>
+__device__ __forceinline__ void dispatch_entry(PIX &pix, const Queue &q, int k, const Lane<NP> &L)
+{
+    const uint32_t kind = q.s4[k].z;
+    if (!PIX::CLAMP_KINDS) {
+        if (kind & 1u) pix.template entry<true, true>(q, k, L);
+        else pix.template entry<false, true>(q, k, L);
+        return;
+    }
+    switch (kind) {
+    case 1: pix.template entry<true, false>(q, k, L); break;
+    case 0: pix.template entry<false, false>(q, k, L); break;
+    case 3: pix.template entry<true, true>(q, k, L); break;
+    default: pix.template entry<false, true>(q, k, L); break;
+    }
+}
 
 // Walk the tile run [start, end) for one state: stage chunks into the queue
 // and hand every staged entry, in run order, to `pix` until no pixel of the
@@ -410,8 +470,7 @@ __device__ __forceinline__ uint32_t walk(const RasterArgs &a, const Lane<NP> &L,
         bool live = true;
         for (uint32_t i = 0; i < n; ++i) {
             const int k = (int)((head + i) & (QCAP - 1));
-            if (sm.q.s4[k].z) pix.template entry<true>(sm.q, k, L);   // same entry in every lane: uniform
-            else pix.template entry<false>(sm.q, k, L);
+            dispatch_entry(pix, sm.q, k, L);
             if ((i & 3u) == 3u && !pix.live()) { live = false; break; }
         }
         head += n;
@@ -486,10 +545,8 @@ __global__ void __launch_bounds__(RT, FWD_MIN_BLOCKS) k_raster_fwd(RasterArgs a,
             double se = 0.0;
 #pragma unroll
             for (int j = 0; j < NPAIR; ++j) {
-                const f2 Tf = add2(f.p[j].T, f.p[j].Tk);
-                const f2 o0 = fma2(Tf, pk(a.bg0, a.bg0), f.p[j].cr);
-                const f2 o1 = fma2(Tf, pk(a.bg1, a.bg1), f.p[j].cg);
-                const f2 o2 = fma2(Tf, pk(a.bg2, a.bg2), f.p[j].cb);
+                f2 o0, o1, o2;
+                f.out(j, a.bg0, a.bg1, a.bg2, o0, o1, o2);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int r = 2 * j + h;
@@ -540,21 +597,20 @@ struct BwdSums {
     f2 S1, S4, S5, Sr, Sg, Sb;
 };
 
-template <bool FIRST>
-__device__ __forceinline__ void bwd_pair(BwdPair &P, BwdSums &S, const Ent &E, f2 pcy, int j)
+template <bool FIRST, bool CLAMP>
+__device__ __forceinline__ void bwd_pair(BwdPair &P, BwdSums &S, const Ent &E, f2 al, f2 ar, f2 dy)
 {
-    f2 dy, ar;
-    const f2 al = pair_alpha(E, pcy, j, dy, ar);
     const f2 w = mul2(al, P.T);
     const f2 Tn = sub2(P.T, w);
-    const bool c0 = lo(Tn) >= T_STOP, c1 = hi(Tn) >= T_STOP;
-    const f2 wp = pk(c0 ? lo(w) : 0.0f, c1 ? hi(w) : 0.0f);
+    const f2 s = pk(ge1(lo(Tn), T_STOP), ge1(hi(Tn), T_STOP));   // 1: composite, 0: stop (or stopped)
+    const f2 wp = mul2(w, s);
     const f2 gr = fma2(P.g2, E.b, fma2(P.g1, E.g, mul2(P.g0, E.r)));
     P.Qn = fma2(wp, gr, P.Qn);
     const f2 om = sub2(pk(1.0f, 1.0f), al);                        // >= 0.01
     const f2 da = fma2(P.Qn, pk(rcp(lo(om)), rcp(hi(om))), mul2(P.T, gr));
     // d alpha / d power = alpha on the linear range; 0 when skipped, stopped or clamped
-    const f2 alin = pk((c0 && lo(ar) < A_MAX) ? lo(al) : 0.0f, (c1 && hi(ar) < A_MAX) ? hi(al) : 0.0f);
+    f2 alin = mul2(al, s);
+    if (CLAMP) alin = pk(lo(ar) < A_MAX ? lo(alin) : 0.0f, hi(ar) < A_MAX ? hi(alin) : 0.0f);
     const f2 gpw = mul2(da, alin);
     const f2 t2 = mul2(gpw, dy);
     if (FIRST) {
@@ -564,7 +620,7 @@ __device__ __forceinline__ void bwd_pair(BwdPair &P, BwdSums &S, const Ent &E, f
         S.S1 = add2(S.S1, t2); S.S4 = fma2(t2, dy, S.S4); S.S5 = add2(S.S5, gpw);
         S.Sr = fma2(P.g0, wp, S.Sr); S.Sg = fma2(P.g1, wp, S.Sg); S.Sb = fma2(P.g2, wp, S.Sb);
     }
-    P.T = pk(c0 ? lo(Tn) : 0.0f, c1 ? hi(Tn) : 0.0f);
+    P.T = mul2(Tn, s);
 }
 
 // Sum of v[0..7] over the warp: after three exchange-and-keep-half steps and
@@ -594,6 +650,7 @@ __device__ __forceinline__ float reduce8_transpose(const float *v, int lane)
 
 template <int NP>
 struct BwdLane {
+    static constexpr bool CLAMP_KINDS = true;
     BwdPair p[NP];
     float4 *rec_grad;
     __device__ __forceinline__ bool live() const
@@ -603,14 +660,18 @@ struct BwdLane {
         for (int j = 0; j < NP; ++j) any |= p[j].T;
         return __any_sync(FULL, any != 0ull);
     }
-    template <bool BOXED>
+    template <bool BOXED, bool CLAMP>
     __device__ __forceinline__ void entry(const Queue &q, int k, const Lane<NP> &L)
     {
-        const Ent E = load_entry(q, k, L, BOXED);
+        const Ent E = load_entry<NP, BOXED>(q, k, L);
         BwdSums S;
-        bwd_pair<true>(p[0], S, E, L.pcy[0], 0);
 #pragma unroll
-        for (int j = 1; j < NP; ++j) bwd_pair<false>(p[j], S, E, L.pcy[j], j);
+        for (int j = 0; j < NP; ++j) {
+            f2 dy, ar;
+            const f2 al = pair_alpha<BOXED, CLAMP>(E, L.pcy[j], j, dy, ar);
+            if (j == 0) bwd_pair<true, CLAMP>(p[j], S, E, al, ar, dy);
+            else bwd_pair<false, CLAMP>(p[j], S, E, al, ar, dy);
+        }
         const float s1 = lo(S.S1) + hi(S.S1), s4 = lo(S.S4) + hi(S.S4), s5 = lo(S.S5) + hi(S.S5);
         const float sr = lo(S.Sr) + hi(S.Sr), sg = lo(S.Sg) + hi(S.Sg), sb = lo(S.Sb) + hi(S.Sb);
         const uint32_t nz = (__float_as_uint(s1) | __float_as_uint(s4) | __float_as_uint(s5) | __float_as_uint(sr) |
@@ -687,10 +748,8 @@ __global__ void __launch_bounds__(RT, BWD_MIN_BLOCKS) k_raster_bwd(RasterBwdArgs
         walk(a, L, sm, rg.x, rg.y, f);
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
-            const f2 Tf = add2(f.p[j].T, f.p[j].Tk);
-            const f2 o0 = fma2(Tf, pk(a.bg0, a.bg0), f.p[j].cr);
-            const f2 o1 = fma2(Tf, pk(a.bg1, a.bg1), f.p[j].cg);
-            const f2 o2 = fma2(Tf, pk(a.bg2, a.bg2), f.p[j].cb);
+            f2 o0, o1, o2;
+            f.out(j, a.bg0, a.bg1, a.bg2, o0, o1, o2);
             fin[j][0][0] = lo(o0); fin[j][0][1] = lo(o1); fin[j][0][2] = lo(o2);
             fin[j][1][0] = hi(o0); fin[j][1][1] = hi(o1); fin[j][1][2] = hi(o2);
         }
@@ -806,53 +865,61 @@ __global__ void __launch_bounds__(256) k_image_mse(const float *__restrict__ ima
 
 }  // namespace
 
-template <bool WRITE, bool MSE, bool LIST>
-static void launch_fwd_t(const RasterArgs &a, const WorkQueue &q, int blocks, cudaStream_t st)
+// Resident blocks per SM of each forward instantiation (its register and
+// shared-memory use), queried once and cached so that launches made during
+// stream capture issue no runtime queries; the persistent grid is that many
+// blocks per SM.
+template <bool WRITE, bool MSE, bool LIST, int SHIFT>
+static int fwd_occupancy()
 {
-    if (a.tile_shift == 5) k_raster_fwd<WRITE, MSE, LIST, 5><<<blocks, RT, 0, st>>>(a, q);
-    else k_raster_fwd<WRITE, MSE, LIST, 4><<<blocks, RT, 0, st>>>(a, q);
+    static int n = 0;
+    if (!n) {
+        int m = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k_raster_fwd<WRITE, MSE, LIST, SHIFT>, RT, 0);
+        n = m > 0 ? m : 1;
+    }
+    return n;
+}
+
+template <bool WRITE, bool MSE, bool LIST>
+static void launch_fwd_t(const RasterArgs &a, const WorkQueue &q, int sms, cudaStream_t st)
+{
+    if (a.tile_shift == 5)
+        k_raster_fwd<WRITE, MSE, LIST, 5><<<sms * fwd_occupancy<WRITE, MSE, LIST, 5>(), RT, 0, st>>>(a, q);
+    else
+        k_raster_fwd<WRITE, MSE, LIST, 4><<<sms * fwd_occupancy<WRITE, MSE, LIST, 4>(), RT, 0, st>>>(a, q);
+}
+
+template <bool WRITE, bool MSE, bool LIST>
+static void query_t()
+{
+    fwd_occupancy<WRITE, MSE, LIST, 4>();
+    fwd_occupancy<WRITE, MSE, LIST, 5>();
 }
 
 // Every work item is one (view-group tile, state); the explicit work list
 // (tile reuse) renders squared-error partials only.  G (states per item) is 1.
-void launch_raster_fwd(const RasterArgs &a, const WorkQueue &q, int G, int blocks, cudaStream_t st)
+void launch_raster_fwd(const RasterArgs &a, const WorkQueue &q, int G, int sms, cudaStream_t st)
 {
     (void)G;
     if ((!q.item_first && q.n_items == 0) || (!a.images && !a.refs)) return;
     ProfScope ps_(a.refs ? "raster_fwd_mse" : "raster_fwd", st);
-    if (q.item_first) launch_fwd_t<false, true, true>(a, q, blocks, st);
-    else if (a.images && a.refs) launch_fwd_t<true, true, false>(a, q, blocks, st);
-    else if (a.images) launch_fwd_t<true, false, false>(a, q, blocks, st);
-    else launch_fwd_t<false, true, false>(a, q, blocks, st);
+    if (q.item_first) launch_fwd_t<false, true, true>(a, q, sms, st);
+    else if (a.images && a.refs) launch_fwd_t<true, true, false>(a, q, sms, st);
+    else if (a.images) launch_fwd_t<true, false, false>(a, q, sms, st);
+    else launch_fwd_t<false, true, false>(a, q, sms, st);
     count_launch();
 }
 
-template <bool WRITE, bool MSE, bool LIST>
-static int occ_t()
+void raster_fwd_query_occupancy()
 {
-    int n = 0, n5 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_fwd<WRITE, MSE, LIST, 4>, RT, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n5, k_raster_fwd<WRITE, MSE, LIST, 5>, RT, 0);
-    n = n < n5 ? n : n5;
-    return n > 0 ? n : 1;
-}
-
-// Resident blocks per SM of each instantiation (queried once, then cached, so
-// launches made during stream capture issue no runtime queries).
-int raster_fwd_blocks_per_sm(int G, bool write, bool mse, bool list)
-{
-    (void)G;
-    static int cache[4] = {};
-    const int mi = list ? 3 : (write && mse) ? 0 : write ? 1 : 2;
-    if (!cache[mi]) {
-        switch (mi) {
-        case 0: cache[mi] = occ_t<true, true, false>(); break;
-        case 1: cache[mi] = occ_t<true, false, false>(); break;
-        case 2: cache[mi] = occ_t<false, true, false>(); break;
-        default: cache[mi] = occ_t<false, true, true>(); break;
-        }
-    }
-    return cache[mi];
+    static bool done = false;
+    if (done) return;
+    query_t<true, true, false>();
+    query_t<true, false, false>();
+    query_t<false, true, false>();
+    query_t<false, true, true>();
+    done = true;
 }
 
 void launch_tile_costs(const uint2 *ranges, uint32_t n, uint32_t *keys, uint32_t *vals, int sms, cudaStream_t st)

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(256) k_first_clusters(const Rec *__restrict__ 
             const uint32_t e = base + threadIdx.x;
             if (e < rg.y) {
                 const uint32_t slot = __ldg(evals + e);
-                const uint32_t c = __ldg(reinterpret_cast<const uint32_t *>(recs + slot) + 11) & 0xfffu;
+                const uint32_t c = __ldg(reinterpret_cast<const uint32_t *>(recs + slot) + 11) & REC_CLUSTER;
                 if (atomicMin(&fp[c], e - rg.x) == NO_POS) atomicAdd(&ndist, 1u);
             }
             __syncthreads();

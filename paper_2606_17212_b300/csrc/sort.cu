@@ -446,7 +446,7 @@ size_t radix_workspace_bytes(size_t n)
 // Plain passes over digits [shift0, bits) of (k0, v0); the result is in (k1,
 // v1) when *result_in_alt.
 cudaError_t radix_passes(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, size_t n, int shift0, int bits,
-                         void *ws, cudaStream_t st, bool *result_in_alt, const uint32_t *n_dev)
+                         void *ws, cudaStream_t st, bool *result_in_alt, const uint32_t *n_dev, const char *prof)
 {
     *result_in_alt = false;
     static bool carveout_set = false;   // the scatter's shared memory allows 8 blocks per SM at full carveout
@@ -464,7 +464,7 @@ cudaError_t radix_passes(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
     for (int shift = shift0; shift < bits; shift += 8) {
         int w = bits - shift < 8 ? bits - shift : 8;
         uint32_t mask = (1u << w) - 1u;
-        ProfScope ps_("radix_pass", st);
+        ProfScope ps_(prof, st);
         k_rs_hist<<<(unsigned)nb, RS_THREADS, 0, st>>>(ki, n, n_dev, shift, mask, hist, (uint32_t)nb);
         count_launch();
         cudaError_t e = exclusive_scan_u32(hist, hist, (size_t)RS_RADIX * nb, nullptr, scan_ws, st);
@@ -482,11 +482,12 @@ cudaError_t radix_passes(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
 }
 
 cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, size_t n,
-                             int bits, void *ws, cudaStream_t st, bool *result_in_alt, const uint32_t *n_dev)
+                             int bits, void *ws, cudaStream_t st, bool *result_in_alt, const uint32_t *n_dev,
+                             const char *prof)
 {
     *result_in_alt = false;
     if (n == 0 || (n <= 1 && !n_dev) || bits <= 0) return cudaSuccess;
-    return radix_passes(k0, v0, k1, v1, n, 0, bits, ws, st, result_in_alt, n_dev);
+    return radix_passes(k0, v0, k1, v1, n, 0, bits, ws, st, result_in_alt, n_dev, prof);
 }
 
 cudaError_t radix_sort_entries(const uint4 *bins, const uint32_t *toffs, const uint32_t *counts, uint32_t n_rec,
@@ -505,7 +506,7 @@ cudaError_t radix_sort_entries(const uint4 *bins, const uint32_t *toffs, const u
     {
         const int w = bits < 8 ? bits : 8;
         const uint32_t mask = (1u << w) - 1u;
-        ProfScope ps_("radix_pass", st);
+        ProfScope ps_("radix_tile", st);
         unsigned g = (unsigned)((n_rec + 255) / 256);
         if (g > (unsigned)sms * 16u) g = (unsigned)sms * 16u;
         k_chunk_first<<<g, 256, 0, st>>>(toffs, counts, n_rec, nrec_dev, (uint32_t)e_cap, nent_dev, first);
@@ -528,7 +529,7 @@ cudaError_t radix_sort_entries(const uint4 *bins, const uint32_t *toffs, const u
     }
     // the remaining digits: plain passes from (k1, v1), ending in (k0, v0) after an odd count
     bool alt2 = false;
-    cudaError_t e = radix_passes(k1, v1, k0, v0, e_cap, 8, bits, ws, st, &alt2, nent_dev);
+    cudaError_t e = radix_passes(k1, v1, k0, v0, e_cap, 8, bits, ws, st, &alt2, nent_dev, "radix_tile");
     *result_in_alt = !alt2;
     return e;
 }

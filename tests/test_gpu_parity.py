@@ -414,7 +414,7 @@ def _unpack_boxes(recs):
     bx, by, cd = recs[:, 9], recs[:, 10], recs[:, 11]
     return (bx & 0xFFFF).astype(np.int64), (bx >> 16).astype(np.int64), (by & 0xFFFF).astype(np.int64), \
         (by >> 16).astype(np.int64), ((cd >> 12) & 0xF).astype(np.int64), ((cd >> 16) & 0x7FFF).astype(np.int64), \
-        (cd & 0xFFF).astype(np.int64)
+        (cd & 0x3FF).astype(np.int64)
 
 
 @pytest.mark.parametrize("tile", [16, 32])

@@ -407,7 +407,7 @@ int prepare(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *masks, const P
     TRY(ensure(ctx, ctx->tcount, 4 * ((size_t)nRec + 1), st));
     TRY(ensure(ctx, ctx->bins, sizeof(uint4) * ((size_t)nRec + 1), st));
     TRY(ensure(ctx, ctx->toffs, 4 * ((size_t)nRec + 1), st));
-    TRY(ensure(ctx, ctx->sortws, radix_workspace_bytes(nRec), st));
+    TRY(ensure(ctx, ctx->sortws, radix_workspace_bytes(nRec, p.V), st));
     TRY(ensure(ctx, ctx->scanws, scan_workspace_bytes((size_t)nRec + 1), st));
     SceneDev sd = scene_dev(scene);
     if (nRec > 0)
@@ -415,8 +415,10 @@ int prepare(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *masks, const P
                        (const uint32_t *)ctx->recBase.p, (Rec *)ctx->recs.p, (uint32_t *)ctx->k0.p,
                        (uint32_t *)ctx->v0.p, ctx->sms, st);
     bool alt = false;
-    CK(radix_sort_pairs((uint32_t *)ctx->k0.p, (uint32_t *)ctx->v0.p, (uint32_t *)ctx->k1.p, (uint32_t *)ctx->v1.p,
-                        nRec, 32, ctx->sortws.p, st, &alt, nullptr, "radix_depth"));
+    // records in (view group, depth) order: each view group's records are one segment
+    CK(radix_sort_pairs_seg((uint32_t *)ctx->k0.p, (uint32_t *)ctx->v0.p, (uint32_t *)ctx->k1.p,
+                            (uint32_t *)ctx->v1.p, nRec, (const uint32_t *)ctx->recBase.p, (uint32_t)C, p.V, 32,
+                            ctx->sortws.p, st, &alt, "radix_depth"));
     const uint32_t *order = alt ? (const uint32_t *)ctx->v1.p : (const uint32_t *)ctx->v0.p;
     out.depth_keys = alt ? (uint32_t *)ctx->k1.p : (uint32_t *)ctx->k0.p;
     out.depth_slots = (uint32_t *)order;
@@ -434,13 +436,13 @@ int prepare(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *masks, const P
     TRY(ensure(ctx, ctx->ev0, 4 * (size_t)nEnt, st));
     TRY(ensure(ctx, ctx->ek1, 4 * (size_t)nEnt, st));
     TRY(ensure(ctx, ctx->ev1, 4 * (size_t)nEnt, st));
-    TRY(ensure(ctx, ctx->sortws, radix_workspace_bytes(nEnt), st));
+    TRY(ensure(ctx, ctx->sortws, radix_workspace_bytes(nEnt, p.V), st));
     TRY(ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)p.V * p.tiles, st));
-    const int kbits = bits_for((unsigned long long)p.V * p.tiles - 1ull);
+    const int tbits = bits_for((unsigned long long)p.tiles - 1ull);
     CK(radix_sort_entries((const uint4 *)ctx->bins.p, (const uint32_t *)ctx->toffs.p, (const uint32_t *)ctx->tcount.p,
-                          nRec, nullptr, p.tiles_x, (uint32_t *)ctx->ek0.p, (uint32_t *)ctx->ev0.p,
-                          (uint32_t *)ctx->ek1.p, (uint32_t *)ctx->ev1.p, nEnt, nullptr, kbits, ctx->sortws.p, st,
-                          &alt, ctx->sms));
+                          nRec, nullptr, (const uint32_t *)ctx->recBase.p, (uint32_t)C, p.V, p.tiles_x, p.tiles,
+                          (uint32_t *)ctx->ek0.p, (uint32_t *)ctx->ev0.p, (uint32_t *)ctx->ek1.p,
+                          (uint32_t *)ctx->ev1.p, nEnt, nullptr, tbits, ctx->sortws.p, st, &alt, ctx->sms));
     uint32_t *ekeys = alt ? (uint32_t *)ctx->ek1.p : (uint32_t *)ctx->ek0.p;
     out.ekeys = ekeys;
     out.evals = alt ? (uint32_t *)ctx->ev1.p : (uint32_t *)ctx->ev0.p;
@@ -786,8 +788,9 @@ int prepare_dev(dgs_plan *P, const uint32_t *masks, bool force_full, cudaStream_
                    (const uint32_t *)ctx->recBase.p, (Rec *)ctx->recs.p, (uint32_t *)ctx->k0.p, (uint32_t *)ctx->v0.p,
                    ctx->sms, st);
     bool alt = false;
-    CK(radix_sort_pairs((uint32_t *)ctx->k0.p, (uint32_t *)ctx->v0.p, (uint32_t *)ctx->k1.p, (uint32_t *)ctx->v1.p,
-                        P->R_cap, 32, ctx->sortws.p, st, &alt, cnt + 0, "radix_depth"));
+    CK(radix_sort_pairs_seg((uint32_t *)ctx->k0.p, (uint32_t *)ctx->v0.p, (uint32_t *)ctx->k1.p,
+                            (uint32_t *)ctx->v1.p, P->R_cap, (const uint32_t *)ctx->recBase.p, (uint32_t)C, p.V, 32,
+                            ctx->sortws.p, st, &alt, "radix_depth"));
     const uint32_t *order = alt ? (const uint32_t *)ctx->v1.p : (const uint32_t *)ctx->v0.p;
     Lists &out = P->L;
     out.depth_keys = alt ? (uint32_t *)ctx->k1.p : (uint32_t *)ctx->k0.p;
@@ -798,11 +801,11 @@ int prepare_dev(dgs_plan *P, const uint32_t *masks, bool force_full, cudaStream_
     CK(exclusive_scan_u32((const uint32_t *)ctx->tcount.p, (uint32_t *)ctx->toffs.p, P->R_cap, cnt + 1,
                           ctx->scanws.p, st));
     launch_clamp_count(cnt + 1, P->E_cap, cnt + 2, cnt + 3, st);
-    const int kbits = bits_for((unsigned long long)vt - 1ull);
+    const int tbits = bits_for((unsigned long long)p.tiles - 1ull);
     CK(radix_sort_entries((const uint4 *)ctx->bins.p, (const uint32_t *)ctx->toffs.p, (const uint32_t *)ctx->tcount.p,
-                          P->R_cap, cnt + 0, p.tiles_x, (uint32_t *)ctx->ek0.p, (uint32_t *)ctx->ev0.p,
-                          (uint32_t *)ctx->ek1.p, (uint32_t *)ctx->ev1.p, P->E_cap, cnt + 2, kbits, ctx->sortws.p,
-                          st, &alt, ctx->sms));
+                          P->R_cap, cnt + 0, (const uint32_t *)ctx->recBase.p, (uint32_t)C, p.V, p.tiles_x, p.tiles,
+                          (uint32_t *)ctx->ek0.p, (uint32_t *)ctx->ev0.p, (uint32_t *)ctx->ek1.p,
+                          (uint32_t *)ctx->ev1.p, P->E_cap, cnt + 2, tbits, ctx->sortws.p, st, &alt, ctx->sms));
     out.ekeys = alt ? (uint32_t *)ctx->ek1.p : (uint32_t *)ctx->ek0.p;
     out.evals = alt ? (uint32_t *)ctx->ev1.p : (uint32_t *)ctx->ev0.p;
     CK(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * vt, st));
@@ -1658,7 +1661,7 @@ int dgs_plan_create(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *stat
         for (Buf *b : eb) if ((r = ensure(w, *b, 4 * E, st)) != DGS_OK) break;
         if (r != DGS_OK) break;
         const size_t big = std::max(std::max(R, E), vt) + 1;
-        if ((r = ensure(w, w->sortws, radix_workspace_bytes(big), st)) != DGS_OK) break;
+        if ((r = ensure(w, w->sortws, radix_workspace_bytes(big, p.V), st)) != DGS_OK) break;
         if ((r = ensure(w, w->scanws, scan_workspace_bytes(big), st)) != DGS_OK) break;
         if ((r = ensure(w, w->icnt, 4 * (vt + 1), st)) != DGS_OK) break;
         if ((r = ensure(w, w->ioff, 4 * (vt + 1), st)) != DGS_OK) break;

@@ -37,7 +37,7 @@ __device__ __forceinline__ int cluster_of_b(const int32_t *offs, int C, int i)
 // RK > 0: exactly RK temporal coefficients (the accumulators stay in registers);
 // RK = 0: any rank up to MAX_RANK.
 template <int SH, int RK>
-__global__ void __launch_bounds__(128) k_project_bwd(SceneDev s, const ViewGroup *__restrict__ vgs, int V,
+__global__ void __launch_bounds__(128, SH == 0 ? 4 : 1) k_project_bwd(SceneDev s, const ViewGroup *__restrict__ vgs, int V,
                                                      const uint32_t *__restrict__ need,
                                                      const uint32_t *__restrict__ recBase,
                                                      const float4 *__restrict__ rec_grad, GradDev g)

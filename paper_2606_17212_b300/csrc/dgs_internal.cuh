@@ -152,26 +152,39 @@ cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint
 
 // Stable LSD radix sort of (key, value) u32 pairs on key bits [0, bits).
 // Ping-pongs between (k0, v0) and (k1, v1); returns in *result_in_alt whether
-// the sorted data ended in (k1, v1).  ws from radix_workspace_bytes(n).  With
-// n_dev the live count is read on the device (n is then the capacity), so the
-// launch sequence does not depend on it (capture-safe).
-size_t radix_workspace_bytes(size_t n);
+// the sorted data ended in (k1, v1).  ws from radix_workspace_bytes(n, V)
+// (V = 0 for the plain sort).  With n_dev the live count is read on the
+// device (n is then the capacity), so the launch sequence does not depend on
+// it (capture-safe).
+size_t radix_workspace_bytes(size_t n, int V = 0);
 // prof: the profiler name of the passes (one name per kind of sort)
 cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, size_t n,
                              int bits, void *ws, cudaStream_t st, bool *result_in_alt,
                              const uint32_t *n_dev = nullptr, const char *prof = "radix_pass");
 
-// Tile entries of the depth-ordered records, sorted stably by tile key on
-// bits [0, bits), without an unsorted copy: the first pass generates every
-// entry from the record's tile rectangle, bins[j] = (key of its first tile =
-// view group * tiles + ty0 * tiles_x + tx0, tile columns tw, record slot, 0),
-// record j owning entries [toffs[j], toffs[j] + counts[j]).  Entries at or past
-// e_cap (or *nent_dev) are dropped; nrec_dev / nent_dev as n_dev above.  The
-// (k0, v0) / (k1, v1) convention and the workspace are those of
-// radix_sort_pairs with n = e_cap.
+// The same, segment by segment: items [start(v), start(v + 1)) with start(v) =
+// seg_start[v * stride] (device, non-decreasing, v = 0 .. V; start(V) is the
+// live count) are sorted stably among themselves and stay in their segment.
+// Records segmented by view group come out in (view group, key) order.
+cudaError_t radix_sort_pairs_seg(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, size_t n_cap,
+                                 const uint32_t *seg_start, uint32_t stride, int V, int bits, void *ws,
+                                 cudaStream_t st, bool *result_in_alt, const char *prof);
+
+// Tile entries of records sorted by (view group, depth), sorted stably by
+// (view group, tile), without an unsorted copy.  The records of view group v
+// are [rec_start[v * rec_stride], rec_start[(v + 1) * rec_stride]), so their
+// entries form one segment and only the tile index (bits [0, bits) of key -
+// v * tiles) needs sorting.  The first pass generates every entry from the
+// record's tile rectangle, bins[j] = (key of its first tile = view group *
+// tiles + ty0 * tiles_x + tx0, tile columns tw, record slot, 0), record j
+// owning entries [toffs[j], toffs[j] + counts[j]).  Entries at or past e_cap
+// (or *nent_dev) are dropped; nrec_dev / nent_dev as n_dev above.  The
+// (k0, v0) / (k1, v1) convention is radix_sort_pairs'; ws from
+// radix_workspace_bytes(e_cap, V).
 cudaError_t radix_sort_entries(const uint4 *bins, const uint32_t *toffs, const uint32_t *counts, uint32_t n_rec,
-                               const uint32_t *nrec_dev, int tiles_x, uint32_t *k0, uint32_t *v0, uint32_t *k1,
-                               uint32_t *v1, size_t e_cap, const uint32_t *nent_dev, int bits, void *ws,
-                               cudaStream_t st, bool *result_in_alt, int sms);
+                               const uint32_t *nrec_dev, const uint32_t *rec_start, uint32_t rec_stride, int V,
+                               int tiles_x, uint32_t tiles, uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
+                               size_t e_cap, const uint32_t *nent_dev, int bits, void *ws, cudaStream_t st,
+                               bool *result_in_alt, int sms);
 
 }  // namespace dgs

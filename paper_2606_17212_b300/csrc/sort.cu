@@ -196,13 +196,15 @@ struct ScatterSmem {
 
 // Stable scatter of one block's RS_CHUNK items (item k of this thread has
 // block-local index w * RS_ITEMS * 32 + k * 32 + lane; the first nvalid are
-// live).  sm.wh must be zero on entry.  Ranks every item among the block's
-// items of its digit in index order, reorders the items by digit in shared
-// memory, then writes each digit run with consecutive threads on consecutive
-// slots (coalesced stores).
+// live).  The digit of key k is ((k - sub) >> shift) & mask; the scanned
+// table gives the block's first output slot of digit d at toff[d * tstride].
+// sm.wh must be zero on entry.  Ranks every item among the block's items of
+// its digit in index order, reorders the items by digit in shared memory,
+// then writes each digit run with consecutive threads on consecutive slots
+// (coalesced stores).
 __device__ __forceinline__ void rank_and_scatter(const uint32_t (&key)[RS_ITEMS], const uint32_t (&val)[RS_ITEMS],
-                                                 uint32_t nvalid, int shift, uint32_t mask,
-                                                 const uint32_t *__restrict__ offsets, uint32_t nblocks,
+                                                 uint32_t nvalid, int shift, uint32_t mask, uint32_t sub,
+                                                 const uint32_t *__restrict__ toff, uint32_t tstride,
                                                  uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
                                                  ScatterSmem &sm)
 {
@@ -213,7 +215,7 @@ __device__ __forceinline__ void rank_and_scatter(const uint32_t (&key)[RS_ITEMS]
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
         const bool ok = wbase + (uint32_t)(k * 32 + lane) < nvalid;
-        uint32_t d = ok ? ((key[k] >> shift) & mask) : 0u;
+        uint32_t d = ok ? (((key[k] - sub) >> shift) & mask) : 0u;
         uint32_t peers = digit_peers(d, __ballot_sync(0xffffffffu, ok));
         uint32_t before = ok ? sm.wh[w][d] : 0u;
         __syncwarp();
@@ -240,12 +242,12 @@ __device__ __forceinline__ void rank_and_scatter(const uint32_t (&key)[RS_ITEMS]
     uint32_t woff = 0;
     for (int ww = 0; ww < w; ++ww) woff += sm.wsum[ww];
     sm.dstart[d] = woff + inc - run;
-    sm.gbase[d] = offsets[(size_t)d * nblocks + blockIdx.x];
+    sm.gbase[d] = toff[(size_t)d * tstride];
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
         if (rank[k] == 0xffffffffu) continue;
-        const uint32_t dk = (key[k] >> shift) & mask;
+        const uint32_t dk = ((key[k] - sub) >> shift) & mask;
         const uint32_t pos = sm.dstart[dk] + sm.wh[w][dk] + rank[k];
         sm.sk[pos] = key[k];
         sm.sv[pos] = val[k];
@@ -254,7 +256,7 @@ __device__ __forceinline__ void rank_and_scatter(const uint32_t (&key)[RS_ITEMS]
     // consecutive threads write consecutive slots of each digit run: coalesced
     for (uint32_t i = threadIdx.x; i < nvalid; i += RS_THREADS) {
         const uint32_t kk = sm.sk[i];
-        const uint32_t dk = (kk >> shift) & mask;
+        const uint32_t dk = ((kk - sub) >> shift) & mask;
         const uint32_t g = sm.gbase[dk] + (i - sm.dstart[dk]);
         kout[g] = kk;
         vout[g] = sm.sv[i];
@@ -286,42 +288,185 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t *kin, 
         val[k] = i < n ? __ldg(vin + i) : 0u;
     }
     const uint32_t nvalid = n <= blk0 ? 0u : (n - blk0 < (size_t)RS_CHUNK ? (uint32_t)(n - blk0) : (uint32_t)RS_CHUNK);
-    rank_and_scatter(key, val, nvalid, shift, mask, offsets, nblocks, kout, vout, sm);
+    rank_and_scatter(key, val, nvalid, shift, mask, 0u, offsets + blockIdx.x, nblocks, kout, vout, sm);
+}
+
+// ------------------------------------------------ segmented passes
+// Items [start(v), start(v + 1)) form segment v = 0 .. V-1, with start(v) =
+// start[v * stride] non-decreasing (start(V) is the end).  Each segment is cut
+// into blocks of RS_CHUNK items (the last one partial); bbase[v] is the first
+// block of segment v and bbase[V] the number of blocks.  A stable pass over
+// the digit ((key - v * sub) >> shift) & mask keeps every item inside its
+// segment: block bl of segment v puts its count of digit d at
+// hist[RS_RADIX * bbase[v] + d * nb_v + bl] (nb_v = the segment's blocks), so
+// one exclusive scan of the table in index order gives every (segment, digit,
+// block) its first output slot: segments one after another, the digits of a
+// segment in order, the blocks of a digit in order.  Sorting records so, with
+// the view groups as segments, leaves the tile sort only the tile digits.
+struct Segs {
+    const uint32_t *start;
+    uint32_t stride;
+    const uint32_t *bbase;
+    int V;
+    uint32_t sub;
+};
+
+__device__ __forceinline__ uint32_t seg_start(const Segs &g, int v) { return __ldg(g.start + (size_t)v * g.stride); }
+
+// The segment of block b < bbase[V]: the last v with bbase[v] <= b (a segment
+// without items has its successor's base, so the last one is the segment that
+// holds the block).
+__device__ __forceinline__ int seg_of_block(const Segs &g, uint32_t b)
+{
+    int lo = 0, hi = g.V - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(g.bbase + mid) <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Block bl of segment v and its item range [s0, s1).
+struct SegBlock {
+    int v;
+    uint32_t bl, nb, s0, s1;
+};
+
+__device__ __forceinline__ SegBlock seg_block(const Segs &g, uint32_t b)
+{
+    SegBlock r;
+    r.v = seg_of_block(g, b);
+    const uint32_t b0 = __ldg(g.bbase + r.v);
+    r.bl = b - b0;
+    r.nb = __ldg(g.bbase + r.v + 1) - b0;
+    r.s0 = seg_start(g, r.v) + r.bl * (uint32_t)RS_CHUNK;
+    r.s1 = min(r.s0 + (uint32_t)RS_CHUNK, seg_start(g, r.v + 1));
+    return r;
+}
+
+// nb[v] = blocks of segment v (v < V), nb[V] = 0: the exclusive scan of nb is bbase.
+__global__ void k_seg_blocks(const uint32_t *__restrict__ start, uint32_t stride, int V, uint32_t *__restrict__ nb)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v <= V; v += gridDim.x * blockDim.x) {
+        if (v == V) { nb[v] = 0; continue; }
+        const uint32_t n = start[(size_t)(v + 1) * stride] - start[(size_t)v * stride];
+        nb[v] = (n + RS_CHUNK - 1) / RS_CHUNK;
+    }
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist_seg(const uint32_t *__restrict__ keys, Segs g, int shift,
+                                                            uint32_t mask, uint32_t *__restrict__ hist)
+{
+    const uint32_t b = blockIdx.x;
+    if (b >= __ldg(g.bbase + g.V)) {          // no items: zero this block's share of the table tail
+        hist[(size_t)RS_RADIX * b + threadIdx.x] = 0u;
+        return;
+    }
+    __shared__ uint32_t h[RS_WARPS][RS_RADIX];
+    const int w = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < RS_WARPS * RS_RADIX; d += RS_THREADS) (&h[0][0])[d] = 0;
+    const SegBlock sb = seg_block(g, b);
+    const uint32_t sub = (uint32_t)sb.v * g.sub;
+    uint32_t key[RS_ITEMS];
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        const uint32_t i = sb.s0 + (uint32_t)(k * RS_THREADS) + threadIdx.x;
+        key[k] = i < sb.s1 ? __ldg(keys + i) : 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        const uint32_t i = sb.s0 + (uint32_t)(k * RS_THREADS) + threadIdx.x;
+        if (i < sb.s1) atomicAdd(&h[w][((key[k] - sub) >> shift) & mask], 1u);
+    }
+    __syncthreads();
+    uint32_t tot = 0;
+#pragma unroll
+    for (int ww = 0; ww < RS_WARPS; ++ww) tot += h[ww][threadIdx.x];
+    hist[(size_t)RS_RADIX * __ldg(g.bbase + sb.v) + (size_t)threadIdx.x * sb.nb + sb.bl] = tot;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter_seg(const uint32_t *kin, const uint32_t *vin,
+                                                               uint32_t *kout, uint32_t *vout, Segs g, int shift,
+                                                               uint32_t mask, const uint32_t *offsets)
+{
+    const uint32_t b = blockIdx.x;
+    if (b >= __ldg(g.bbase + g.V)) return;   // block-uniform
+    __shared__ ScatterSmem sm;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < RS_WARPS * RS_RADIX; d += RS_THREADS) (&sm.wh[0][0])[d] = 0;
+    __syncthreads();
+    const SegBlock sb = seg_block(g, b);
+    const uint32_t base = sb.s0 + (uint32_t)w * (RS_ITEMS * 32);
+    uint32_t key[RS_ITEMS], val[RS_ITEMS];
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        const uint32_t i = base + (uint32_t)(k * 32 + lane);
+        key[k] = i < sb.s1 ? __ldg(kin + i) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        const uint32_t i = base + (uint32_t)(k * 32 + lane);
+        val[k] = i < sb.s1 ? __ldg(vin + i) : 0u;
+    }
+    rank_and_scatter(key, val, sb.s1 - sb.s0, shift, mask, (uint32_t)sb.v * g.sub,
+                     offsets + (size_t)RS_RADIX * __ldg(g.bbase + sb.v) + sb.bl, sb.nb, kout, vout, sm);
 }
 
 // ------------------------------------------------ first pass of the tile sort
-// The tile entries of the depth-ordered records are never written unsorted:
-// the first radix pass generates them from the records' tile rectangles.
-// Record j (depth order) owns entries [toffs[j], toffs[j] + counts[j]); entry
-// k of it is tile (ty0 + k / tw, tx0 + k % tw), key bins[j].x + (k / tw) *
-// tiles_x + k % tw, value bins[j].z (the record slot).  Radix block b owns
-// entries [b RS_CHUNK, (b + 1) RS_CHUNK) as in every other pass, and
-// first[b] is the record holding entry b RS_CHUNK.
+// The tile entries of the sorted records are never written unsorted: the
+// first radix pass generates them from the records' tile rectangles.  Record
+// j (sorted order) owns entries [toffs[j], toffs[j] + counts[j]); entry k of
+// it is tile (ty0 + k / tw, tx0 + k % tw), key bins[j].x + (k / tw) * tiles_x
+// + k % tw, value bins[j].z (the record slot).  The records of view group v
+// are segment v of the record order, so its entries are segment v of the
+// entry order, [eseg[v], eseg[v + 1]); first[b] is the record holding the
+// first entry of entry block b.
 
 __device__ __forceinline__ uint32_t entries_live(uint32_t e_cap, const uint32_t *ne_dev)
 {
     return ne_dev ? min(e_cap, *ne_dev) : e_cap;
 }
 
-__global__ void k_chunk_first(const uint32_t *__restrict__ toffs, const uint32_t *__restrict__ counts, uint32_t nr_cap,
-                              const uint32_t *nr_dev, uint32_t e_cap, const uint32_t *ne_dev,
-                              uint32_t *__restrict__ first)
+// eseg[v] = first entry of the records of segment v (capped at the live entry count).
+__global__ void k_entry_segs(Segs rseg, const uint32_t *__restrict__ toffs, uint32_t nr_cap,
+                             const uint32_t *nr_dev, uint32_t e_cap, const uint32_t *ne_dev,
+                             uint32_t *__restrict__ eseg)
 {
     const uint32_t nr = nr_dev ? min(nr_cap, *nr_dev) : nr_cap;
     const uint32_t ne = entries_live(e_cap, ne_dev);
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v <= rseg.V; v += gridDim.x * blockDim.x) {
+        const uint32_t r = v < rseg.V ? seg_start(rseg, v) : nr;
+        eseg[v] = r < nr ? min(toffs[r], ne) : ne;
+    }
+}
+
+__global__ void k_chunk_first_seg(const uint32_t *__restrict__ toffs, const uint32_t *__restrict__ counts,
+                                  uint32_t nr_cap, const uint32_t *nr_dev, Segs rseg, Segs eseg,
+                                  uint32_t *__restrict__ first)
+{
+    const uint32_t nr = nr_dev ? min(nr_cap, *nr_dev) : nr_cap;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < nr; j += gridDim.x * blockDim.x) {
         const uint32_t c = counts[j];
         if (c == 0) continue;
-        const uint32_t s = toffs[j];
-        const uint32_t e = min(s + c, ne);
-        for (uint32_t b = (s + RS_CHUNK - 1) / RS_CHUNK; (size_t)b * RS_CHUNK < e; ++b) first[b] = j;
+        // the segment of record j: the last v with start(v) <= j
+        int lo = 0, hi = rseg.V - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (seg_start(rseg, mid) <= j) lo = mid; else hi = mid - 1;
+        }
+        const uint32_t e0 = seg_start(eseg, lo), e1 = seg_start(eseg, lo + 1);
+        const uint32_t s = toffs[j], e = min(s + c, e1);
+        if (s >= e) continue;
+        const uint32_t bb = __ldg(eseg.bbase + lo);
+        for (uint32_t k = (s - e0 + RS_CHUNK - 1) / RS_CHUNK; e0 + k * RS_CHUNK < e; ++k) first[bb + k] = j;
     }
 }
 
 // Walk the records overlapping entries [E0, E1) of the block, RS_THREADS at a
-// time in depth order; f(e, key, slot) is called for every entry e in the
-// range (e the entry's index, key its tile key, slot the record slot).
-// Every thread returns after the same number of barriers.
+// time in order; f(e, key, slot) is called for every entry e in the range (e
+// the entry's index, key its tile key, slot the record slot).  Every thread
+// returns after the same number of barriers.
 template <typename F>
 __device__ __forceinline__ void for_chunk_entries(const uint4 *__restrict__ bins, const uint32_t *__restrict__ toffs,
                                                   const uint32_t *__restrict__ counts, uint32_t nr, uint32_t r0,
@@ -357,54 +502,53 @@ __device__ __forceinline__ void for_chunk_entries(const uint4 *__restrict__ bins
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist_bins(const uint4 *__restrict__ bins,
                                                              const uint32_t *__restrict__ toffs,
                                                              const uint32_t *__restrict__ counts, uint32_t nr_cap,
-                                                             const uint32_t *nr_dev, uint32_t e_cap,
-                                                             const uint32_t *ne_dev, const uint32_t *__restrict__ first,
-                                                             int tiles_x, uint32_t mask, uint32_t *__restrict__ hist,
-                                                             uint32_t nblocks)
+                                                             const uint32_t *nr_dev, const uint32_t *__restrict__ first,
+                                                             int tiles_x, Segs g, uint32_t mask,
+                                                             uint32_t *__restrict__ hist)
 {
+    const uint32_t b = blockIdx.x;
+    if (b >= __ldg(g.bbase + g.V)) {
+        hist[(size_t)RS_RADIX * b + threadIdx.x] = 0u;
+        return;
+    }
     __shared__ uint32_t h[RS_WARPS][RS_RADIX];
     const int w = threadIdx.x >> 5;
     for (int d = threadIdx.x; d < RS_WARPS * RS_RADIX; d += RS_THREADS) (&h[0][0])[d] = 0;
     __syncthreads();
-    const uint32_t ne = entries_live(e_cap, ne_dev);
-    const uint32_t E0 = blockIdx.x * (uint32_t)RS_CHUNK;
-    if (E0 < ne) {
-        const uint32_t nr = nr_dev ? min(nr_cap, *nr_dev) : nr_cap;
-        const uint32_t E1 = min(E0 + (uint32_t)RS_CHUNK, ne);
-        for_chunk_entries(bins, toffs, counts, nr, first[blockIdx.x], E0, E1, tiles_x,
-                          [&](uint32_t, uint32_t key, uint32_t) { atomicAdd(&h[w][key & mask], 1u); });
-    }
+    const SegBlock sb = seg_block(g, b);
+    const uint32_t sub = (uint32_t)sb.v * g.sub;
+    const uint32_t nr = nr_dev ? min(nr_cap, *nr_dev) : nr_cap;
+    for_chunk_entries(bins, toffs, counts, nr, first[b], sb.s0, sb.s1, tiles_x,
+                      [&](uint32_t, uint32_t key, uint32_t) { atomicAdd(&h[w][(key - sub) & mask], 1u); });
     __syncthreads();
     uint32_t tot = 0;
 #pragma unroll
     for (int ww = 0; ww < RS_WARPS; ++ww) tot += h[ww][threadIdx.x];
-    hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = tot;
+    hist[(size_t)RS_RADIX * __ldg(g.bbase + sb.v) + (size_t)threadIdx.x * sb.nb + sb.bl] = tot;
 }
 
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter_bins(const uint4 *__restrict__ bins,
                                                                 const uint32_t *__restrict__ toffs,
                                                                 const uint32_t *__restrict__ counts, uint32_t nr_cap,
-                                                                const uint32_t *nr_dev, uint32_t e_cap,
-                                                                const uint32_t *ne_dev,
+                                                                const uint32_t *nr_dev,
                                                                 const uint32_t *__restrict__ first, int tiles_x,
-                                                                uint32_t mask, const uint32_t *offsets,
-                                                                uint32_t nblocks, uint32_t *kout, uint32_t *vout)
+                                                                Segs g, uint32_t mask, const uint32_t *offsets,
+                                                                uint32_t *kout, uint32_t *vout)
 {
+    const uint32_t b = blockIdx.x;
+    if (b >= __ldg(g.bbase + g.V)) return;   // block-uniform
     __shared__ ScatterSmem sm;
-    const uint32_t ne = entries_live(e_cap, ne_dev);
-    const uint32_t E0 = blockIdx.x * (uint32_t)RS_CHUNK;
-    if (E0 >= ne) return;                    // block-uniform
+    const SegBlock sb = seg_block(g, b);
     const uint32_t nr = nr_dev ? min(nr_cap, *nr_dev) : nr_cap;
-    const uint32_t E1 = min(E0 + (uint32_t)RS_CHUNK, ne);
     for (int d = threadIdx.x; d < RS_WARPS * RS_RADIX; d += RS_THREADS) (&sm.wh[0][0])[d] = 0;
     // the block's entries, in entry order, into shared memory
-    for_chunk_entries(bins, toffs, counts, nr, first[blockIdx.x], E0, E1, tiles_x,
+    for_chunk_entries(bins, toffs, counts, nr, first[b], sb.s0, sb.s1, tiles_x,
                       [&](uint32_t e, uint32_t key, uint32_t slot) {
-                          sm.sk[e - E0] = key;
-                          sm.sv[e - E0] = slot;
+                          sm.sk[e - sb.s0] = key;
+                          sm.sv[e - sb.s0] = slot;
                       });
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const uint32_t nvalid = E1 - E0;
+    const uint32_t nvalid = sb.s1 - sb.s0;
     uint32_t key[RS_ITEMS], val[RS_ITEMS];
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
@@ -413,7 +557,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter_bins(const uint4 *__r
         val[k] = i < nvalid ? sm.sv[i] : 0u;
     }
     __syncthreads();                         // sk / sv are reused for the reordered items
-    rank_and_scatter(key, val, nvalid, 0, mask, offsets, nblocks, kout, vout, sm);
+    rank_and_scatter(key, val, nvalid, 0, mask, (uint32_t)sb.v * g.sub,
+                     offsets + (size_t)RS_RADIX * __ldg(g.bbase + sb.v) + sb.bl, sb.nb, kout, vout, sm);
 }
 
 }  // namespace
@@ -434,13 +579,84 @@ cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint
     return scan_rec(in, out, n, total_out, (uint32_t *)ws, st);
 }
 
-size_t radix_workspace_bytes(size_t n)
+// The scatters' shared memory allows 8 blocks per SM at the full carveout.
+static void sort_carveouts()
 {
-    size_t nb = blocks_for(n > 0 ? n : 1, RS_CHUNK);
-    size_t hist = (size_t)RS_RADIX * nb;
-    // histogram table, its scan workspace, and the first-record table of the tile sort
-    return align_up(hist * sizeof(uint32_t)) + align_up(scan_workspace_bytes(hist)) +
-           align_up((nb + 1) * sizeof(uint32_t));
+    static bool set = false;
+    if (set) return;
+    cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    cudaFuncSetAttribute(k_rs_scatter_bins, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    cudaFuncSetAttribute(k_rs_scatter_seg, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    set = true;
+}
+
+// Layout of a sort workspace for n items in V segments (V = 0: a plain sort).
+struct SortWs {
+    uint32_t *hist;       // digit table: RS_RADIX x (blocks of n + V)
+    void *scan;           // its scan workspace
+    uint32_t *first;      // entry blocks: the record holding each block's first entry
+    uint32_t *rbase;      // [V + 1] first block of each record segment
+    uint32_t *ebase;      // [V + 1] first block of each entry segment
+    uint32_t *eseg;       // [V + 1] first entry of each segment
+    void *vscan;          // scan workspace of the [V + 1] arrays
+    size_t bytes;
+};
+
+static SortWs sort_ws(void *ws, size_t n, int V)
+{
+    const size_t bound = blocks_for(n > 0 ? n : 1, RS_CHUNK) + (size_t)V;
+    char *base = (char *)ws, *p = base;
+    SortWs w;
+    w.hist = (uint32_t *)p; p += align_up((size_t)RS_RADIX * bound * sizeof(uint32_t));
+    w.scan = p; p += align_up(scan_workspace_bytes((size_t)RS_RADIX * bound));
+    w.first = (uint32_t *)p; p += align_up((bound + 1) * sizeof(uint32_t));
+    w.rbase = (uint32_t *)p; p += align_up(((size_t)V + 1) * sizeof(uint32_t));
+    w.ebase = (uint32_t *)p; p += align_up(((size_t)V + 1) * sizeof(uint32_t));
+    w.eseg = (uint32_t *)p; p += align_up(((size_t)V + 1) * sizeof(uint32_t));
+    w.vscan = p; p += align_up(scan_workspace_bytes((size_t)V + 1));
+    w.bytes = (size_t)(p - base);
+    return w;
+}
+
+size_t radix_workspace_bytes(size_t n, int V)
+{
+    return sort_ws(nullptr, n, V).bytes;
+}
+
+// bbase of the segments [start(v), start(v + 1)): block counts, then their exclusive scan.
+static cudaError_t seg_bases(const uint32_t *start, uint32_t stride, int V, uint32_t *bbase, void *vscan, cudaStream_t st)
+{
+    k_seg_blocks<<<(unsigned)((V + 256) / 256), 256, 0, st>>>(start, stride, V, bbase);
+    count_launch();
+    return exclusive_scan_u32(bbase, bbase, (size_t)V + 1, nullptr, vscan, st);
+}
+
+// Segmented passes over digits [shift0, bits) of (k0, v0), ping-ponging with
+// (k1, v1); *result_in_alt flips once per pass.
+static cudaError_t seg_passes(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const Segs &g, size_t bound,
+                       int shift0, int bits, const SortWs &w, cudaStream_t st, bool *result_in_alt,
+                       const char *prof)
+{
+    uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
+    for (int shift = shift0; shift < bits; shift += 8) {
+        const int wd = bits - shift < 8 ? bits - shift : 8;
+        const uint32_t mask = (1u << wd) - 1u;
+        ProfScope ps_(prof, st);
+        k_rs_hist_seg<<<(unsigned)bound, RS_THREADS, 0, st>>>(ki, g, shift, mask, w.hist);
+        count_launch();
+        cudaError_t e = exclusive_scan_u32(w.hist, w.hist, (size_t)RS_RADIX * bound, nullptr, w.scan, st);
+        if (e != cudaSuccess) return e;
+        k_rs_scatter_seg<<<(unsigned)bound, RS_THREADS, 0, st>>>(ki, vi, ko, vo, g, shift, mask, w.hist);
+        count_launch();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        uint32_t *tk = ki, *tv = vi;
+        ki = ko; vi = vo; ko = tk; vo = tv;
+        *result_in_alt = !*result_in_alt;
+    }
+    return cudaSuccess;
 }
 
 // Plain passes over digits [shift0, bits) of (k0, v0); the result is in (k1,
@@ -449,14 +665,7 @@ cudaError_t radix_passes(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
                          void *ws, cudaStream_t st, bool *result_in_alt, const uint32_t *n_dev, const char *prof)
 {
     *result_in_alt = false;
-    static bool carveout_set = false;   // the scatter's shared memory allows 8 blocks per SM at full carveout
-    if (!carveout_set) {
-        cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        cudaFuncSetAttribute(k_rs_scatter_bins, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        carveout_set = true;
-    }
+    sort_carveouts();
     size_t nb = blocks_for(n, RS_CHUNK);
     uint32_t *hist = (uint32_t *)ws;
     void *scan_ws = (char *)ws + align_up((size_t)RS_RADIX * nb * sizeof(uint32_t));
@@ -490,35 +699,58 @@ cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t 
     return radix_passes(k0, v0, k1, v1, n, 0, bits, ws, st, result_in_alt, n_dev, prof);
 }
 
-cudaError_t radix_sort_entries(const uint4 *bins, const uint32_t *toffs, const uint32_t *counts, uint32_t n_rec,
-                               const uint32_t *nrec_dev, int tiles_x, uint32_t *k0, uint32_t *v0, uint32_t *k1,
-                               uint32_t *v1, size_t e_cap, const uint32_t *nent_dev, int bits, void *ws,
-                               cudaStream_t st, bool *result_in_alt, int sms)
+cudaError_t radix_sort_pairs_seg(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, size_t n_cap,
+                                 const uint32_t *seg_start, uint32_t stride, int V, int bits, void *ws,
+                                 cudaStream_t st, bool *result_in_alt, const char *prof)
 {
     *result_in_alt = false;
-    if (e_cap == 0 || n_rec == 0) return cudaSuccess;
-    if (bits < 1) bits = 1;                  // the first pass also materialises the entries
-    size_t nb = blocks_for(e_cap, RS_CHUNK);
-    uint32_t *hist = (uint32_t *)ws;
-    const size_t hist_bytes = align_up((size_t)RS_RADIX * nb * sizeof(uint32_t));
-    void *scan_ws = (char *)ws + hist_bytes;
-    uint32_t *first = (uint32_t *)((char *)ws + hist_bytes + align_up(scan_workspace_bytes((size_t)RS_RADIX * nb)));
+    if (n_cap == 0 || V <= 0 || bits <= 0) return cudaSuccess;
+    sort_carveouts();
+    const SortWs w = sort_ws(ws, n_cap, V);
+    const size_t bound = blocks_for(n_cap, RS_CHUNK) + (size_t)V;
     {
-        const int w = bits < 8 ? bits : 8;
-        const uint32_t mask = (1u << w) - 1u;
+        ProfScope ps_(prof, st);
+        cudaError_t e = seg_bases(seg_start, stride, V, w.rbase, w.vscan, st);
+        if (e != cudaSuccess) return e;
+    }
+    const Segs g{seg_start, stride, w.rbase, V, 0u};
+    return seg_passes(k0, v0, k1, v1, g, bound, 0, bits, w, st, result_in_alt, prof);
+}
+
+cudaError_t radix_sort_entries(const uint4 *bins, const uint32_t *toffs, const uint32_t *counts, uint32_t n_rec,
+                               const uint32_t *nrec_dev, const uint32_t *rec_start, uint32_t rec_stride, int V,
+                               int tiles_x, uint32_t tiles, uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
+                               size_t e_cap, const uint32_t *nent_dev, int bits, void *ws, cudaStream_t st,
+                               bool *result_in_alt, int sms)
+{
+    *result_in_alt = false;
+    if (e_cap == 0 || n_rec == 0 || V <= 0) return cudaSuccess;
+    if (bits < 1) bits = 1;                  // the first pass also materialises the entries
+    sort_carveouts();
+    const SortWs w = sort_ws(ws, e_cap, V);
+    const size_t bound = blocks_for(e_cap, RS_CHUNK) + (size_t)V;
+    const Segs rseg{rec_start, rec_stride, nullptr, V, 0u};
+    const Segs eg{w.eseg, 1u, w.ebase, V, tiles};
+    {
+        const int wd = bits < 8 ? bits : 8;
+        const uint32_t mask = (1u << wd) - 1u;
         ProfScope ps_("radix_tile", st);
+        k_entry_segs<<<(unsigned)((V + 256) / 256), 256, 0, st>>>(rseg, toffs, n_rec, nrec_dev, (uint32_t)e_cap,
+                                                                   nent_dev, w.eseg);
+        count_launch();
+        cudaError_t e = seg_bases(w.eseg, 1u, V, w.ebase, w.vscan, st);
+        if (e != cudaSuccess) return e;
         unsigned g = (unsigned)((n_rec + 255) / 256);
         if (g > (unsigned)sms * 16u) g = (unsigned)sms * 16u;
-        k_chunk_first<<<g, 256, 0, st>>>(toffs, counts, n_rec, nrec_dev, (uint32_t)e_cap, nent_dev, first);
+        k_chunk_first_seg<<<g, 256, 0, st>>>(toffs, counts, n_rec, nrec_dev, rseg, eg, w.first);
         count_launch();
-        k_rs_hist_bins<<<(unsigned)nb, RS_THREADS, 0, st>>>(bins, toffs, counts, n_rec, nrec_dev, (uint32_t)e_cap,
-                                                            nent_dev, first, tiles_x, mask, hist, (uint32_t)nb);
+        k_rs_hist_bins<<<(unsigned)bound, RS_THREADS, 0, st>>>(bins, toffs, counts, n_rec, nrec_dev, w.first, tiles_x,
+                                                               eg, mask, w.hist);
         count_launch();
-        cudaError_t e = exclusive_scan_u32(hist, hist, (size_t)RS_RADIX * nb, nullptr, scan_ws, st);
+        e = exclusive_scan_u32(w.hist, w.hist, (size_t)RS_RADIX * bound, nullptr, w.scan, st);
         if (e != cudaSuccess) return e;
-        k_rs_scatter_bins<<<(unsigned)nb, RS_THREADS, 0, st>>>(bins, toffs, counts, n_rec, nrec_dev,
-                                                               (uint32_t)e_cap, nent_dev, first, tiles_x, mask,
-                                                               hist, (uint32_t)nb, k1, v1);
+        k_rs_scatter_bins<<<(unsigned)bound, RS_THREADS, 0, st>>>(bins, toffs, counts, n_rec, nrec_dev, w.first,
+                                                                  tiles_x, eg, mask, w.hist, k1, v1);
         count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -527,9 +759,9 @@ cudaError_t radix_sort_entries(const uint4 *bins, const uint32_t *toffs, const u
         *result_in_alt = true;
         return cudaSuccess;
     }
-    // the remaining digits: plain passes from (k1, v1), ending in (k0, v0) after an odd count
+    // the remaining tile digits: segmented passes from (k1, v1), ending in (k0, v0) after an odd count
     bool alt2 = false;
-    cudaError_t e = radix_passes(k1, v1, k0, v0, e_cap, 8, bits, ws, st, &alt2, nent_dev, "radix_tile");
+    cudaError_t e = seg_passes(k1, v1, k0, v0, eg, bound, 8, bits, w, st, &alt2, "radix_tile");
     *result_in_alt = !alt2;
     return e;
 }

@@ -438,8 +438,8 @@ def test_tile_lists_bitwise_and_end_to_end(R, torch, tile):
     live = depth != 0
     dkey = np.full(n_rec, 0xFFFFFFFF, np.uint64)
     dkey[d["depth_slots"].astype(np.int64)] = d["depth_keys"]
-    # depth sort = stable sort of the per-record depth keys
-    order = np.argsort(dkey, kind="stable")
+    # depth sort = stable sort of the records by (view group, depth key)
+    order = np.lexsort((dkey, vg))
     assert np.array_equal(order, d["depth_slots"].astype(np.int64))
     # (1) regression check, bitwise: the oracle's integer binning (tile
     # rectangles, 64-bit key order) applied to the GPU's own FP32 boxes and depths

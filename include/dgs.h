@@ -396,6 +396,17 @@ DGS_API void dgs_plan_destroy(dgs_plan *plan);
 DGS_API const char *dgs_plan_last_error(const dgs_plan *plan);
 /* images [device] [n_states][H][W][3]: as dgs_render_states_batched. */
 DGS_API int dgs_plan_render(dgs_plan *plan, const uint32_t *masks, float *images, dgs_stream stream);
+/* dgs_plan_render and dgs_plan_image_mse in one pass: the forward raster
+ * writes each pixel, its squared error against refs[ref_index[s]] and
+ * dL/dimage = weight * 2 (image - ref) / (3 H W) (dL_dimages [device]
+ * [n_states][H][W][3], or NULL) as it composites it.  Images and dL/dimages
+ * are bit-identical to the two calls; mse / psnr [device] [n_states] sum the
+ * same FP32 squared errors in FP64 per 16 x 16 pixel block, so they equal the
+ * two calls' up to the order of the FP64 additions.  refs [device]
+ * [n_refs][H][W][3].  Needs a plan made with ref_index; counts as the
+ * render a dgs_plan_backward follows. */
+DGS_API int dgs_plan_render_mse(dgs_plan *plan, const uint32_t *masks, float *images, const float *refs, float weight,
+                                double *mse, double *psnr, float *dL_dimages, dgs_stream stream);
 /* images (the last dgs_plan_render's output, or NULL) and dL/dimages [device]:
  * accumulates into grads as dgs_render_backward. */
 DGS_API int dgs_plan_backward(dgs_plan *plan, const float *images, const float *dL_dimages,

@@ -479,6 +479,8 @@ RasterArgs raster_args(dgs_ctx *ctx, const Plan &p, int C, const float *bg, uint
     a.bg0 = bg[0]; a.bg1 = bg[1]; a.bg2 = bg[2];
     a.images = nullptr; a.refs = nullptr; a.ref_of_state = nullptr; a.partial = nullptr;
     a.img_s0 = 0;
+    a.stop = nullptr;
+    a.dL = nullptr; a.gscale = 0.0f;
     return a;
 }
 
@@ -1768,6 +1770,34 @@ int dgs_plan_render(dgs_plan *P, const uint32_t *masks, float *images, dgs_strea
     RasterArgs a = plan_raster_args(P);
     a.images = images;
     TRY(launch_queue(ctx, P->p, P->L, a, P->tfwd, st));
+    P->rendered = true;
+    if (P->arena) P->arena->last = P;
+    return DGS_OK;
+}
+
+int dgs_plan_render_mse(dgs_plan *P, const uint32_t *masks, float *images, const float *refs, float weight,
+                        double *mse, double *psnr, float *dL_dimages, dgs_stream stream)
+{
+    if (!P) return DGS_E_INVALID_ARG;
+    if (P->mode != DGS_PLAN_RENDER) return plan_fail(P, DGS_E_INVALID_ARG, "plan was not made for rendering");
+    if (P->n_refs < 1) return plan_fail(P, DGS_E_INVALID_ARG, "plan was made without ref_index");
+    if (!masks || !images || !refs || !mse) return plan_fail(P, DGS_E_INVALID_ARG, "null argument");
+    dgs_ctx *ctx = P->sc;
+    CK(cudaSetDevice(P->ws.device));
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(prepare_dev(P, masks, false, st));
+    RasterArgs a = plan_raster_args(P);
+    a.images = images;
+    a.refs = refs;
+    a.ref_of_state = (const int32_t *)P->ws.refidx.p;
+    a.partial = (double *)ctx->partial.p;
+    a.dL = dL_dimages;
+    const size_t npix = (size_t)P->p.W * P->p.H;
+    a.gscale = (float)(2.0 * (double)weight / (double)(npix * 3));   // as dgs_plan_image_mse
+    TRY(launch_queue(ctx, P->p, P->L, a, P->tfwd, st));
+    launch_mse_reduce((const double *)ctx->partial.p, P->p.S_user, (int)P->p.blocks, 1.0 / (double)(npix * 3), mse,
+                      psnr, st);
+    CK(cudaGetLastError());
     P->rendered = true;
     if (P->arena) P->arena->last = P;
     return DGS_OK;

@@ -44,6 +44,8 @@ struct RasterArgs {
     double *partial;              // [S][blocks] FP64 squared-error partial sums per 16 x 16 pixel block
     int img_s0;                   // images hold states img_s0, img_s0 + 1, ...
     uint32_t *stop;               // [S][tiles] or null: run prefix staged while the state had a live pixel
+    float *dL;                    // [S][H][W][3] or null: with refs, dL/dimage = gscale (image - ref)
+    float gscale;
 };
 // Work queue of the persistent forward raster: (view group, tile) pairs in
 // descending cost order, each expanded into that view group's state groups.

@@ -560,6 +560,12 @@ __global__ void __launch_bounds__(RT, FWD_MIN_BLOCKS) k_raster_fwd(RasterArgs a,
                     if (MSE) {
                         const float *rp = rbase + pix * 3;
                         se += (double)pixel_sq_err(c0, c1, c2, rp[0], rp[1], rp[2]);
+                        if (a.dL) {   // the loss gradient, as the separate image-MSE pass forms it
+                            float *dst = a.dL + ((size_t)(s - a.img_s0) * a.H * a.W + pix) * 3;
+                            dst[0] = a.gscale * (c0 - rp[0]);
+                            dst[1] = a.gscale * (c1 - rp[1]);
+                            dst[2] = a.gscale * (c2 - rp[2]);
+                        }
                     }
                 }
             }

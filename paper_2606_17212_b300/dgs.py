@@ -65,7 +65,7 @@ EXPORTS = ("dgs_create", "dgs_destroy", "dgs_last_error", "dgs_version", "dgs_re
            "dgs_plan_image_mse", "dgs_plan_status", "dgs_arena_create", "dgs_arena_destroy",
            "dgs_group_utility", "dgs_objective", "dgs_set_tile_reuse",
            "dgs_tile_reuse_stats", "dgs_set_tile_size", "dgs_set_memory_budget", "dgs_memory_stats",
-           "dgs_last_tile_size", "dgs_plan_tile_size")
+           "dgs_last_tile_size", "dgs_plan_tile_size", "dgs_plan_render_mse")
 OBJECTIVE_MAX_STATES = 16384
 UTILITY_MAX_CONTEXTS = 4096
 PLAN_RENDER, PLAN_UTILITY = 1, 2
@@ -131,6 +131,7 @@ def lib():
         L.dgs_plan_backward.argtypes = [P, P, P, ctypes.POINTER(SceneGrad_t), P]
         L.dgs_plan_utility.argtypes = [P, P, P, P, P]
         L.dgs_plan_image_mse.argtypes = [P, P, P, F, P, P, P, P]
+        L.dgs_plan_render_mse.argtypes = [P, P, P, P, F, P, P, P, P]
         L.dgs_plan_status.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), P]
         _lib = L
     return _lib
@@ -608,6 +609,13 @@ class Plan:
         self._check(self._lib.dgs_plan_utility(self.h, _ptr(masks), _ptr(mse), _ptr(psnr), _stream(stream)),
                     "dgs_plan_utility")
         return mse, psnr
+
+    def render_mse(self, masks, images, refs, mse, psnr, dL, weight=1.0, stream=None):
+        """dgs_plan_render_mse: render, squared errors and dL/dimages in one forward pass."""
+        self._check(self._lib.dgs_plan_render_mse(self.h, _ptr(masks), _ptr(images), _ptr(refs), float(weight),
+                                                  _ptr(mse), _ptr(psnr), _ptr(dL), _stream(stream)),
+                    "dgs_plan_render_mse")
+        return images, mse, psnr, dL
 
     def image_mse(self, images, refs, mse, psnr, dL, weight=1.0, stream=None):
         self._check(self._lib.dgs_plan_image_mse(self.h, _ptr(images), _ptr(refs), float(weight), _ptr(mse),

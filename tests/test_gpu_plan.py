@@ -124,6 +124,18 @@ def test_plan_utility_and_image_mse(R, torch):
     plan2.image_mse(imgs, refs, m2, p2, d2, weight=0.5)
     torch.cuda.synchronize()
     assert torch.equal(m1, m2) and torch.equal(d1, d2)
+    # the fused pass: the same images and dL/dI bits; the MSE sums the same FP32
+    # squared errors in another FP64 order; a backward may follow it
+    img3, m3, p3, d3 = torch.empty_like(imgs), torch.empty_like(m1), torch.empty_like(p1), torch.full_like(d1, 7.0)
+    plan2.render_mse(st.masks.clone(), img3, refs, m3, p3, d3, weight=0.5)
+    torch.cuda.synchronize()
+    assert torch.equal(img3, imgs) and torch.equal(d3, d1)
+    assert torch.allclose(m3, m1, rtol=1e-12, atol=0.0) and torch.allclose(p3, p1, rtol=1e-12, atol=0.0)
+    g = plan2.backward(d3, sc.zeros_like_grads(), images=img3)
+    g_ref = R.render_backward(sc, st, w.cams, w.bg, d1, images=imgs)
+    for k in dgs.SCENE_FIELDS:
+        if g_ref[k].numel():
+            assert torch.allclose(g[k], g_ref[k], rtol=1e-4, atol=1e-5 * float(g_ref[k].abs().max()) + 1e-12), k
     plan2.close()
 
 

@@ -438,10 +438,12 @@ DGS_API int dgs_plan_status(dgs_plan *plan, int64_t *n_records, int64_t *n_entri
  *               3-sigma box is narrower than the alpha >= 1/255 box on some
  *               axis; clamp: alpha may reach the 0.99 clamp, set unless
  *               o <= 0.98 and the conic's condition number is <= 1e4)
- *   depth_keys  [n_rec]  float bits of camera depth (0xFFFFFFFF = culled), sorted
+ *   depth_keys  [n_rec]  float bits of camera depth of the live records, sorted
  *               stably by (view group, depth): each view group's records in
- *               ascending depth, view groups in order
- *   depth_slots [n_rec]  the record slot of each sorted depth key
+ *               ascending depth, view groups in order; the sort drops culled
+ *               records, so the array ends with 0xFFFFFFFF, one per culled record
+ *   depth_slots [n_rec]  the record slot of each sorted depth key (0xFFFFFFFF
+ *               in the dropped tail)
  *   entry_keys  [n_ent]  view group * tiles + tile, ascending (stable)
  *   entry_vals  [n_ent]  record slot of each entry
  *   ranges      [n_view_groups * tiles][2]  [start, end) of each tile's run

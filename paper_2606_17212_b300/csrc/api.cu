@@ -70,6 +70,7 @@ namespace {
 struct Buf {
     void *p = nullptr;
     size_t cap = 0;
+    bool zeroed = false;   // (record gradients) every byte is zero between uses
 };
 
 struct Plan {
@@ -95,6 +96,7 @@ struct Plan {
 // Outputs of the shared preparation of a batch (pointers into the workspace).
 struct Lists {
     uint32_t nRec = 0, nEnt = 0;
+    uint32_t nLive = 0;                                       // records left by the depth sort (context calls)
     uint32_t *depth_keys = nullptr, *depth_slots = nullptr;   // records sorted by depth
     uint32_t *ekeys = nullptr, *evals = nullptr;              // entries sorted by (view group, tile)
     uint32_t *tile_order = nullptr;                           // (view group, tile), costliest first
@@ -121,7 +123,8 @@ struct dgs_ctx {
         ranges, sortws, scanws, partial, refs, recgrad, refidx, tck0, tcv0, tck1, tcv1, icnt, ioff, qint, counter,
         pairm, grp, gmse, omaps, opart, otpart, oD, oweight, oints, recgmu, gqws,
         shord, shpair, shpair2, shrep, shflag, shpos, shlist, shitem, shkey, shstop, shseg, shcnt, shtab,
-        tapemask;                  // the masks the last forward rendered (checked by the backward)
+        tapemask,                  // the masks the last forward rendered (checked by the backward)
+        live;                      // [V + 1] view-group starts of the depth-sorted live records; [V] = their count
     bool tile_reuse = true;        // utility passes reuse rendered tiles across states (share.cu)
     int tile_size = 0;             // sort tile side in pixels: 16 or 32, or 0 (chosen per batch shape)
     size_t mem_budget = 0;         // cap on the workspace bytes (0: the device's free memory only)
@@ -189,7 +192,22 @@ int ensure(dgs_ctx *ctx, Buf &b, size_t bytes, cudaStream_t st)
         return fail(ctx, DGS_E_OOM, "device allocation of %zu bytes failed", want);
     }
     b.cap = want;
+    b.zeroed = false;
     ctx->ws_bytes += want;
+    return DGS_OK;
+}
+
+// The per-record gradient buffer stays zero between backward calls: it is
+// cleared once when allocated, the adjoint raster accumulates into it, and the
+// projection adjoint clears every record it reads.  `zeroed` is false while a
+// backward is between those two kernels (or after a failure there).
+int ensure_zeroed(dgs_ctx *ctx, Buf &b, size_t bytes, cudaStream_t st)
+{
+    TRY(ensure(ctx, b, bytes, st));
+    if (!b.zeroed) {
+        CK(cudaMemsetAsync(b.p, 0, b.cap, st));
+        b.zeroed = true;
+    }
     return DGS_OK;
 }
 
@@ -415,22 +433,27 @@ int prepare(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *masks, const P
                        (const uint32_t *)ctx->recBase.p, (Rec *)ctx->recs.p, (uint32_t *)ctx->k0.p,
                        (uint32_t *)ctx->v0.p, ctx->sms, st);
     bool alt = false;
-    // records in (view group, depth) order: each view group's records are one segment
+    // live records in (view group, depth) order: each view group's records are one
+    // segment; culled records (key 0xFFFFFFFF) are dropped by the first pass
+    TRY(ensure(ctx, ctx->live, 4 * ((size_t)p.V + 1), st));
+    uint32_t *live = (uint32_t *)ctx->live.p;
     CK(radix_sort_pairs_seg((uint32_t *)ctx->k0.p, (uint32_t *)ctx->v0.p, (uint32_t *)ctx->k1.p,
                             (uint32_t *)ctx->v1.p, nRec, (const uint32_t *)ctx->recBase.p, (uint32_t)C, p.V, 32,
-                            ctx->sortws.p, st, &alt, "radix_depth"));
+                            ctx->sortws.p, st, &alt, "radix_depth", live));
     const uint32_t *order = alt ? (const uint32_t *)ctx->v1.p : (const uint32_t *)ctx->v0.p;
     out.depth_keys = alt ? (uint32_t *)ctx->k1.p : (uint32_t *)ctx->k0.p;
     out.depth_slots = (uint32_t *)order;
     if (nRec > 0)
         launch_tile_count((const Rec *)ctx->recs.p, order, nRec, p.tiles_x, p.tiles, p.tile_shift,
-                          (uint32_t *)ctx->tcount.p,
-                          (uint4 *)ctx->bins.p, ctx->sms, st);
+                          (uint32_t *)ctx->tcount.p, (uint4 *)ctx->bins.p, ctx->sms, st, live + p.V);
     CK(exclusive_scan_u32((const uint32_t *)ctx->tcount.p, (uint32_t *)ctx->toffs.p, nRec,
                           (uint32_t *)ctx->total.p + 1, ctx->scanws.p, st));
     CK(cudaMemcpyAsync(ctx->h_small + 1, (uint32_t *)ctx->total.p + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    if (nRec > 0 && p.V > 0)
+        CK(cudaMemcpyAsync(ctx->h_small + 2, live + p.V, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     nEnt = nRec > 0 ? ctx->h_small[1] : 0;
+    out.nLive = nRec > 0 && p.V > 0 ? ctx->h_small[2] : 0;
     if (nEnt >= 0x7fffffffu) return fail(ctx, DGS_E_CAPACITY, "too many tile entries");
     TRY(ensure(ctx, ctx->ek0, 4 * (size_t)nEnt, st));
     TRY(ensure(ctx, ctx->ev0, 4 * (size_t)nEnt, st));
@@ -439,17 +462,21 @@ int prepare(dgs_ctx *ctx, const dgs_scene *scene, const uint32_t *masks, const P
     TRY(ensure(ctx, ctx->sortws, radix_workspace_bytes(nEnt, p.V), st));
     TRY(ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)p.V * p.tiles, st));
     const int tbits = bits_for((unsigned long long)p.tiles - 1ull);
+    bool ranges_done = false;
     CK(radix_sort_entries((const uint4 *)ctx->bins.p, (const uint32_t *)ctx->toffs.p, (const uint32_t *)ctx->tcount.p,
-                          nRec, nullptr, (const uint32_t *)ctx->recBase.p, (uint32_t)C, p.V, p.tiles_x, p.tiles,
+                          nRec, live + p.V, live, 1u, p.V, p.tiles_x, p.tiles,
                           (uint32_t *)ctx->ek0.p, (uint32_t *)ctx->ev0.p, (uint32_t *)ctx->ek1.p,
-                          (uint32_t *)ctx->ev1.p, nEnt, nullptr, tbits, ctx->sortws.p, st, &alt, ctx->sms));
+                          (uint32_t *)ctx->ev1.p, nEnt, nullptr, tbits, ctx->sortws.p, st, &alt, ctx->sms,
+                          (uint2 *)ctx->ranges.p, &ranges_done));
     uint32_t *ekeys = alt ? (uint32_t *)ctx->ek1.p : (uint32_t *)ctx->ek0.p;
     out.ekeys = ekeys;
     out.evals = alt ? (uint32_t *)ctx->ev1.p : (uint32_t *)ctx->ev0.p;
     out.nRec = nRec;
     out.nEnt = nEnt;
-    CK(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * (size_t)p.V * p.tiles, st));
-    launch_ranges(ekeys, nEnt, (uint2 *)ctx->ranges.p, ctx->sms, st);
+    if (!ranges_done) {
+        CK(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * (size_t)p.V * p.tiles, st));
+        launch_ranges(ekeys, nEnt, (uint2 *)ctx->ranges.p, ctx->sms, st);
+    }
     // (view group, tile) pairs in descending entry count: the raster work order
     const size_t vt = (size_t)p.V * p.tiles;
     TRY(ensure(ctx, ctx->tck0, 4 * vt, st));
@@ -790,28 +817,32 @@ int prepare_dev(dgs_plan *P, const uint32_t *masks, bool force_full, cudaStream_
                    (const uint32_t *)ctx->recBase.p, (Rec *)ctx->recs.p, (uint32_t *)ctx->k0.p, (uint32_t *)ctx->v0.p,
                    ctx->sms, st);
     bool alt = false;
+    uint32_t *live = (uint32_t *)ctx->live.p;
     CK(radix_sort_pairs_seg((uint32_t *)ctx->k0.p, (uint32_t *)ctx->v0.p, (uint32_t *)ctx->k1.p,
                             (uint32_t *)ctx->v1.p, P->R_cap, (const uint32_t *)ctx->recBase.p, (uint32_t)C, p.V, 32,
-                            ctx->sortws.p, st, &alt, "radix_depth"));
+                            ctx->sortws.p, st, &alt, "radix_depth", live));
     const uint32_t *order = alt ? (const uint32_t *)ctx->v1.p : (const uint32_t *)ctx->v0.p;
     Lists &out = P->L;
     out.depth_keys = alt ? (uint32_t *)ctx->k1.p : (uint32_t *)ctx->k0.p;
     out.depth_slots = (uint32_t *)order;
     launch_tile_count((const Rec *)ctx->recs.p, order, P->R_cap, p.tiles_x, p.tiles, p.tile_shift,
-                      (uint32_t *)ctx->tcount.p,
-                      (uint4 *)ctx->bins.p, ctx->sms, st, cnt + 0);
+                      (uint32_t *)ctx->tcount.p, (uint4 *)ctx->bins.p, ctx->sms, st, live + p.V);
     CK(exclusive_scan_u32((const uint32_t *)ctx->tcount.p, (uint32_t *)ctx->toffs.p, P->R_cap, cnt + 1,
                           ctx->scanws.p, st));
     launch_clamp_count(cnt + 1, P->E_cap, cnt + 2, cnt + 3, st);
     const int tbits = bits_for((unsigned long long)p.tiles - 1ull);
+    bool ranges_done = false;
     CK(radix_sort_entries((const uint4 *)ctx->bins.p, (const uint32_t *)ctx->toffs.p, (const uint32_t *)ctx->tcount.p,
-                          P->R_cap, cnt + 0, (const uint32_t *)ctx->recBase.p, (uint32_t)C, p.V, p.tiles_x, p.tiles,
+                          P->R_cap, live + p.V, live, 1u, p.V, p.tiles_x, p.tiles,
                           (uint32_t *)ctx->ek0.p, (uint32_t *)ctx->ev0.p, (uint32_t *)ctx->ek1.p,
-                          (uint32_t *)ctx->ev1.p, P->E_cap, cnt + 2, tbits, ctx->sortws.p, st, &alt, ctx->sms));
+                          (uint32_t *)ctx->ev1.p, P->E_cap, cnt + 2, tbits, ctx->sortws.p, st, &alt, ctx->sms,
+                          (uint2 *)ctx->ranges.p, &ranges_done));
     out.ekeys = alt ? (uint32_t *)ctx->ek1.p : (uint32_t *)ctx->ek0.p;
     out.evals = alt ? (uint32_t *)ctx->ev1.p : (uint32_t *)ctx->ev0.p;
-    CK(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * vt, st));
-    launch_ranges(out.ekeys, P->E_cap, (uint2 *)ctx->ranges.p, ctx->sms, st, cnt + 2);
+    if (!ranges_done) {
+        CK(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * vt, st));
+        launch_ranges(out.ekeys, P->E_cap, (uint2 *)ctx->ranges.p, ctx->sms, st, cnt + 2);
+    }
     launch_tile_costs((const uint2 *)ctx->ranges.p, (uint32_t)vt, (uint32_t *)ctx->tck0.p, (uint32_t *)ctx->tcv0.p,
                       ctx->sms, st);
     CK(radix_sort_pairs((uint32_t *)ctx->tck0.p, (uint32_t *)ctx->tcv0.p, (uint32_t *)ctx->tck1.p,
@@ -857,7 +888,7 @@ std::vector<Buf *> all_bufs(dgs_ctx *ctx)
                    &ctx->icnt, &ctx->ioff, &ctx->qint, &ctx->counter, &ctx->pairm, &ctx->grp, &ctx->gmse, &ctx->omaps, &ctx->opart, &ctx->otpart,
                    &ctx->oD, &ctx->oweight, &ctx->oints, &ctx->recgmu, &ctx->gqws, &ctx->shord, &ctx->shpair,
                    &ctx->shpair2, &ctx->shrep, &ctx->shflag, &ctx->shpos, &ctx->shlist, &ctx->shitem, &ctx->shkey, &ctx->shstop,
-                   &ctx->shseg, &ctx->shcnt, &ctx->shtab, &ctx->tapemask};
+                   &ctx->shseg, &ctx->shcnt, &ctx->shtab, &ctx->tapemask, &ctx->live};
 }
 
 // Free the device workspace except the buffers in `keep` (after the stream's
@@ -1075,8 +1106,8 @@ int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *
             record_tape(ctx->tape, scene, sub, cams, n_cams, p, L);
         }
         const uint32_t nRec = L.nRec;
-        TRY(ensure(ctx, ctx->recgrad, sizeof(float4) * 3 * (size_t)nRec, st));
-        CK(cudaMemsetAsync(ctx->recgrad.p, 0, sizeof(float4) * 3 * (size_t)nRec, st));
+        TRY(ensure_zeroed(ctx, ctx->recgrad, sizeof(float4) * 3 * (size_t)nRec, st));
+        ctx->recgrad.zeroed = false;
         RasterBwdArgs b;
         b.f = raster_args(ctx, p, scene->n_clusters, bg, L.evals);
         b.dL_dimg = dL_s;
@@ -1098,8 +1129,9 @@ int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *
             g.gq = (float *)ctx->gqws.p;
         }
         launch_project_bwd(scene_dev(scene), (const ViewGroup *)ctx->vgs.p, p.V, (const uint32_t *)ctx->need.p,
-                           (const uint32_t *)ctx->recBase.p, (const float4 *)ctx->recgrad.p, g, nRec, ctx->sms, st);
+                           (const uint32_t *)ctx->recBase.p, (float4 *)ctx->recgrad.p, g, nRec, ctx->sms, st);
         CK(cudaGetLastError());
+        ctx->recgrad.zeroed = true;          // the projection adjoint cleared what the raster wrote
         return DGS_OK;
     };
     return chunked(ctx, states, (scene->n_clusters * scene->n_layers + 31) / 32, 0, st, pass);
@@ -1464,8 +1496,15 @@ int dgs_debug_tile_lists(dgs_ctx *ctx, uint32_t *n_rec, uint32_t *n_ent, int32_t
     if (tiles) *tiles = tp.plan.tiles;
     const size_t nr = tp.lists.nRec, ne = tp.lists.nEnt, nrg = (size_t)tp.plan.V * tp.plan.tiles;
     if (recs && nr) CK(cudaMemcpyAsync(recs, ctx->recs.p, sizeof(Rec) * nr, cudaMemcpyDeviceToDevice, st));
-    if (depth_keys && nr) CK(cudaMemcpyAsync(depth_keys, tp.lists.depth_keys, 4 * nr, cudaMemcpyDeviceToDevice, st));
-    if (depth_slots && nr) CK(cudaMemcpyAsync(depth_slots, tp.lists.depth_slots, 4 * nr, cudaMemcpyDeviceToDevice, st));
+    const size_t nl = tp.lists.nLive;   // the sort dropped the culled records: 0xFFFFFFFF after the live ones
+    if (depth_keys && nr) {
+        CK(cudaMemsetAsync(depth_keys, 0xff, 4 * nr, st));
+        if (nl) CK(cudaMemcpyAsync(depth_keys, tp.lists.depth_keys, 4 * nl, cudaMemcpyDeviceToDevice, st));
+    }
+    if (depth_slots && nr) {
+        CK(cudaMemsetAsync(depth_slots, 0xff, 4 * nr, st));
+        if (nl) CK(cudaMemcpyAsync(depth_slots, tp.lists.depth_slots, 4 * nl, cudaMemcpyDeviceToDevice, st));
+    }
     if (entry_keys && ne) CK(cudaMemcpyAsync(entry_keys, tp.lists.ekeys, 4 * ne, cudaMemcpyDeviceToDevice, st));
     if (entry_vals && ne) CK(cudaMemcpyAsync(entry_vals, tp.lists.evals, 4 * ne, cudaMemcpyDeviceToDevice, st));
     if (ranges && nrg) CK(cudaMemcpyAsync(ranges, ctx->ranges.p, sizeof(uint2) * nrg, cudaMemcpyDeviceToDevice, st));
@@ -1659,6 +1698,7 @@ int dgs_plan_create(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *stat
         if ((r = ensure(w, w->tcount, 4 * (R + 1), st)) != DGS_OK) break;
         if ((r = ensure(w, w->bins, sizeof(uint4) * (R + 1), st)) != DGS_OK) break;
         if ((r = ensure(w, w->toffs, 4 * (R + 1), st)) != DGS_OK) break;
+        if ((r = ensure(w, w->live, 4 * ((size_t)p.V + 1), st)) != DGS_OK) break;
         Buf *eb[] = {&w->ek0, &w->ev0, &w->ek1, &w->ev1};
         for (Buf *b : eb) if ((r = ensure(w, *b, 4 * E, st)) != DGS_OK) break;
         if (r != DGS_OK) break;
@@ -1820,7 +1860,11 @@ int dgs_plan_backward(dgs_plan *P, const float *images, const float *dL_dimages,
     dgs_ctx *ctx = P->sc;
     CK(cudaSetDevice(P->ws.device));
     cudaStream_t st = (cudaStream_t)stream;
-    launch_zero_prefix((uint32_t *)ctx->recgrad.p, P->R_cap, (const uint32_t *)P->cnts.p, 12, ctx->sms, st);
+    if (!ctx->recgrad.zeroed) {
+        CK(cudaMemsetAsync(ctx->recgrad.p, 0, ctx->recgrad.cap, st));
+        ctx->recgrad.zeroed = true;
+    }
+    ctx->recgrad.zeroed = false;
     RasterBwdArgs b;
     b.f = plan_raster_args(P);
     b.dL_dimg = dL_dimages;
@@ -1833,8 +1877,9 @@ int dgs_plan_backward(dgs_plan *P, const float *images, const float *dL_dimages,
     g.affine = grads->affine; g.rec_gmu = scene->affine ? (float *)ctx->recgmu.p : nullptr;
     g.res_step = grads->res_step; g.gq = scene->res_mode == 2 ? (float *)ctx->gqws.p : nullptr;
     launch_project_bwd(scene_dev(scene), (const ViewGroup *)P->ws.vgs.p, P->p.V, (const uint32_t *)ctx->need.p,
-                       (const uint32_t *)ctx->recBase.p, (const float4 *)ctx->recgrad.p, g, P->R_cap, ctx->sms, st);
+                       (const uint32_t *)ctx->recBase.p, (float4 *)ctx->recgrad.p, g, P->R_cap, ctx->sms, st);
     CK(cudaGetLastError());
+    ctx->recgrad.zeroed = true;
     return DGS_OK;
 }
 

@@ -34,13 +34,24 @@ __device__ __forceinline__ int cluster_of_b(const int32_t *offs, int C, int i)
     return lo;
 }
 
+// Read a record's pixel moments and clear them, so the buffer is zero for
+// the next backward (each record is read by exactly one thread, once).
+__device__ __forceinline__ void take_record(float4 *p, float4 &a, float4 &b, float4 &c)
+{
+    a = p[0]; b = p[1]; c = p[2];
+    const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (a.x != 0.0f || a.y != 0.0f || a.z != 0.0f || a.w != 0.0f || b.x != 0.0f || b.y != 0.0f || b.z != 0.0f ||
+        b.w != 0.0f || c.x != 0.0f)
+        p[0] = z, p[1] = z, p[2] = z;
+}
+
 // RK > 0: exactly RK temporal coefficients (the accumulators stay in registers);
 // RK = 0: any rank up to MAX_RANK.
 template <int SH, int RK>
 __global__ void __launch_bounds__(128, SH == 0 ? 4 : 1) k_project_bwd(SceneDev s, const ViewGroup *__restrict__ vgs, int V,
                                                      const uint32_t *__restrict__ need,
                                                      const uint32_t *__restrict__ recBase,
-                                                     const float4 *__restrict__ rec_grad, GradDev g)
+                                                     float4 *__restrict__ rec_grad, GradDev g)
 {
     constexpr int NC = NCol<SH>::value;
     constexpr int K = 11 + NC;
@@ -81,9 +92,7 @@ __global__ void __launch_bounds__(128, SH == 0 ? 4 : 1) k_project_bwd(SceneDev s
             float4 n0 = make_float4(0, 0, 0, 0), n1 = n0, n2 = n0;
             if (vn < V) {
                 slot_n = slot_of(vn);
-                n0 = __ldg(rec_grad + (size_t)slot_n * 3);
-                n1 = __ldg(rec_grad + (size_t)slot_n * 3 + 1);
-                n2 = __ldg(rec_grad + (size_t)slot_n * 3 + 2);
+                take_record(rec_grad + (size_t)slot_n * 3, n0, n1, n2);
             }
             while (vn < V) {
                 const int v = vn;
@@ -92,9 +101,7 @@ __global__ void __launch_bounds__(128, SH == 0 ? 4 : 1) k_project_bwd(SceneDev s
                 vn = next_vg(v + 1);
                 if (vn < V) {
                     slot_n = slot_of(vn);
-                    n0 = __ldg(rec_grad + (size_t)slot_n * 3);
-                    n1 = __ldg(rec_grad + (size_t)slot_n * 3 + 1);
-                    n2 = __ldg(rec_grad + (size_t)slot_n * 3 + 2);
+                    take_record(rec_grad + (size_t)slot_n * 3, n0, n1, n2);
                 }
                 if (q0.x == 0.f && q0.y == 0.f && q0.z == 0.f && q0.w == 0.f && q1.x == 0.f && q1.y == 0.f &&
                     q1.z == 0.f && q1.w == 0.f && q2.x == 0.f)
@@ -259,7 +266,7 @@ __global__ void __launch_bounds__(256) k_affine_grad(SceneDev s, const ViewGroup
 }  // namespace
 
 void launch_project_bwd(const SceneDev &s, const ViewGroup *vgs, int V, const uint32_t *need,
-                        const uint32_t *recBase, const float4 *rec_grad, const GradDev &g, size_t rec_cap,
+                        const uint32_t *recBase, float4 *rec_grad, const GradDev &g, size_t rec_cap,
                         int sms, cudaStream_t st)
 {
     if (s.n == 0) return;

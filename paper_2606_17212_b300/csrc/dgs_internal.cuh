@@ -166,9 +166,12 @@ cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t 
 // seg_start[v * stride] (device, non-decreasing, v = 0 .. V; start(V) is the
 // live count) are sorted stably among themselves and stay in their segment.
 // Records segmented by view group come out in (view group, key) order.
+// With kept (device [V + 1]) the items whose key is 0xFFFFFFFF (culled
+// records) are dropped: kept receives the compacted segment starts, kept[V]
+// the number of items left, and only that many sorted items are written.
 cudaError_t radix_sort_pairs_seg(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, size_t n_cap,
                                  const uint32_t *seg_start, uint32_t stride, int V, int bits, void *ws,
-                                 cudaStream_t st, bool *result_in_alt, const char *prof);
+                                 cudaStream_t st, bool *result_in_alt, const char *prof, uint32_t *kept = nullptr);
 
 // Tile entries of records sorted by (view group, depth), sorted stably by
 // (view group, tile), without an unsorted copy.  The records of view group v
@@ -180,11 +183,14 @@ cudaError_t radix_sort_pairs_seg(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint3
 // owning entries [toffs[j], toffs[j] + counts[j]).  Entries at or past e_cap
 // (or *nent_dev) are dropped; nrec_dev / nent_dev as n_dev above.  The
 // (k0, v0) / (k1, v1) convention is radix_sort_pairs'; ws from
-// radix_workspace_bytes(e_cap, V).
+// radix_workspace_bytes(e_cap, V).  When one pass sorts the tiles (bits <= 8)
+// and ranges ([V * tiles], device) is given, the [start, end) of every
+// (view group, tile) run is written from that pass's digit table and
+// *ranges_done is set.
 cudaError_t radix_sort_entries(const uint4 *bins, const uint32_t *toffs, const uint32_t *counts, uint32_t n_rec,
                                const uint32_t *nrec_dev, const uint32_t *rec_start, uint32_t rec_stride, int V,
                                int tiles_x, uint32_t tiles, uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
                                size_t e_cap, const uint32_t *nent_dev, int bits, void *ws, cudaStream_t st,
-                               bool *result_in_alt, int sms);
+                               bool *result_in_alt, int sms, uint2 *ranges = nullptr, bool *ranges_done = nullptr);
 
 }  // namespace dgs

@@ -22,7 +22,6 @@ void launch_tile_count(const Rec *recs, const uint32_t *order, uint32_t n, int t
 void launch_clamp_count(const uint32_t *total, uint32_t cap, uint32_t *out, uint32_t *flags, cudaStream_t st);
 void launch_ranges(const uint32_t *keys, uint32_t n, uint2 *ranges, int sms, cudaStream_t st,
                    const uint32_t *n_dev = nullptr);
-void launch_zero_prefix(uint32_t *p, uint32_t n_cap, const uint32_t *n_dev, uint32_t per, int sms, cudaStream_t st);
 // *flag |= 1 when the n words of a and b differ anywhere (flag zeroed by the caller)
 void launch_words_differ(const uint32_t *a, const uint32_t *b, size_t n, uint32_t *flag, int sms, cudaStream_t st);
 
@@ -143,8 +142,9 @@ void launch_share_resolve(const uint32_t *pvt, const uint32_t *pst, uint8_t *pk,
 
 // rec_cap: record slots of rec_grad (the per-record mean gradients of the
 // affine, g.rec_gmu, are cleared over it)
+// rec_grad: read, then cleared record by record (every record of [0, rec_cap) is zero afterwards)
 void launch_project_bwd(const SceneDev &s, const ViewGroup *vgs, int V, const uint32_t *need,
-                        const uint32_t *recBase, const float4 *rec_grad, const GradDev &g, size_t rec_cap,
+                        const uint32_t *recBase, float4 *rec_grad, const GradDev &g, size_t rec_cap,
                         int sms, cudaStream_t st);
 
 }  // namespace dgs

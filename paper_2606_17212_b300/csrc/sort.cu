@@ -26,6 +26,7 @@ constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ITEMS = 8;
 constexpr int RS_CHUNK = RS_THREADS * RS_ITEMS;         // 2048
 constexpr int RS_RADIX = 256;
+constexpr uint32_t DROP_KEY = 0xffffffffu;              // culled records' depth key
 
 __device__ __forceinline__ int pad(int i) { return i + (i >> 5); }
 
@@ -192,11 +193,13 @@ struct ScatterSmem {
     uint32_t gbase[RS_RADIX];            // global slot of the block's first item of each digit
     uint32_t sk[RS_CHUNK], sv[RS_CHUNK]; // the block's items in (digit, index) order
     uint32_t wsum[RS_WARPS];
+    uint32_t kept;                       // items the block writes
 };
 
 // Stable scatter of one block's RS_CHUNK items (item k of this thread has
 // block-local index w * RS_ITEMS * 32 + k * 32 + lane; the first nvalid are
-// live).  The digit of key k is ((k - sub) >> shift) & mask; the scanned
+// live; with drop, items whose key is DROP_KEY are left out as if absent).
+// The digit of key k is ((k - sub) >> shift) & mask; the scanned
 // table gives the block's first output slot of digit d at toff[d * tstride].
 // sm.wh must be zero on entry.  Ranks every item among the block's items of
 // its digit in index order, reorders the items by digit in shared memory,
@@ -206,7 +209,7 @@ __device__ __forceinline__ void rank_and_scatter(const uint32_t (&key)[RS_ITEMS]
                                                  uint32_t nvalid, int shift, uint32_t mask, uint32_t sub,
                                                  const uint32_t *__restrict__ toff, uint32_t tstride,
                                                  uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
-                                                 ScatterSmem &sm)
+                                                 ScatterSmem &sm, bool drop = false)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
@@ -214,7 +217,7 @@ __device__ __forceinline__ void rank_and_scatter(const uint32_t (&key)[RS_ITEMS]
     uint32_t rank[RS_ITEMS];
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
-        const bool ok = wbase + (uint32_t)(k * 32 + lane) < nvalid;
+        const bool ok = wbase + (uint32_t)(k * 32 + lane) < nvalid && !(drop && key[k] == DROP_KEY);
         uint32_t d = ok ? (((key[k] - sub) >> shift) & mask) : 0u;
         uint32_t peers = digit_peers(d, __ballot_sync(0xffffffffu, ok));
         uint32_t before = ok ? sm.wh[w][d] : 0u;
@@ -242,6 +245,7 @@ __device__ __forceinline__ void rank_and_scatter(const uint32_t (&key)[RS_ITEMS]
     uint32_t woff = 0;
     for (int ww = 0; ww < w; ++ww) woff += sm.wsum[ww];
     sm.dstart[d] = woff + inc - run;
+    if (d == RS_RADIX - 1) sm.kept = woff + inc;
     sm.gbase[d] = toff[(size_t)d * tstride];
     __syncthreads();
 #pragma unroll
@@ -254,7 +258,8 @@ __device__ __forceinline__ void rank_and_scatter(const uint32_t (&key)[RS_ITEMS]
     }
     __syncthreads();
     // consecutive threads write consecutive slots of each digit run: coalesced
-    for (uint32_t i = threadIdx.x; i < nvalid; i += RS_THREADS) {
+    const uint32_t kept = sm.kept;
+    for (uint32_t i = threadIdx.x; i < kept; i += RS_THREADS) {
         const uint32_t kk = sm.sk[i];
         const uint32_t dk = ((kk - sub) >> shift) & mask;
         const uint32_t g = sm.gbase[dk] + (i - sm.dstart[dk]);
@@ -355,7 +360,7 @@ __global__ void k_seg_blocks(const uint32_t *__restrict__ start, uint32_t stride
 }
 
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist_seg(const uint32_t *__restrict__ keys, Segs g, int shift,
-                                                            uint32_t mask, uint32_t *__restrict__ hist)
+                                                            uint32_t mask, uint32_t *__restrict__ hist, bool drop)
 {
     const uint32_t b = blockIdx.x;
     if (b >= __ldg(g.bbase + g.V)) {          // no items: zero this block's share of the table tail
@@ -377,7 +382,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist_seg(const uint32_t *__re
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
         const uint32_t i = sb.s0 + (uint32_t)(k * RS_THREADS) + threadIdx.x;
-        if (i < sb.s1) atomicAdd(&h[w][((key[k] - sub) >> shift) & mask], 1u);
+        if (i < sb.s1 && !(drop && key[k] == DROP_KEY)) atomicAdd(&h[w][((key[k] - sub) >> shift) & mask], 1u);
     }
     __syncthreads();
     uint32_t tot = 0;
@@ -388,7 +393,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist_seg(const uint32_t *__re
 
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter_seg(const uint32_t *kin, const uint32_t *vin,
                                                                uint32_t *kout, uint32_t *vout, Segs g, int shift,
-                                                               uint32_t mask, const uint32_t *offsets)
+                                                               uint32_t mask, const uint32_t *offsets, bool drop)
 {
     const uint32_t b = blockIdx.x;
     if (b >= __ldg(g.bbase + g.V)) return;   // block-uniform
@@ -410,7 +415,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter_seg(const uint32_t *k
         val[k] = i < sb.s1 ? __ldg(vin + i) : 0u;
     }
     rank_and_scatter(key, val, sb.s1 - sb.s0, shift, mask, (uint32_t)sb.v * g.sub,
-                     offsets + (size_t)RS_RADIX * __ldg(g.bbase + sb.v) + sb.bl, sb.nb, kout, vout, sm);
+                     offsets + (size_t)RS_RADIX * __ldg(g.bbase + sb.v) + sb.bl, sb.nb, kout, vout, sm, drop);
 }
 
 // ------------------------------------------------ first pass of the tile sort
@@ -561,6 +566,40 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter_bins(const uint4 *__r
                      offsets + (size_t)RS_RADIX * __ldg(g.bbase + sb.v) + sb.bl, sb.nb, kout, vout, sm);
 }
 
+// Segment starts after a pass that dropped items: segment v now starts at the
+// scanned table's slot for (v, digit 0, block 0); the end (*total, the kept
+// count) is start[V], which the table scan wrote.
+__global__ void k_kept_starts(const uint32_t *__restrict__ table, const uint32_t *__restrict__ bbase, int V,
+                              size_t bound, uint32_t *__restrict__ start)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+        const uint32_t b = bbase[v];
+        start[v] = (size_t)b < bound ? table[(size_t)RS_RADIX * b] : start[V];
+    }
+}
+
+// Tile ranges of a single-pass tile sort, read off its scanned digit table:
+// (view group v, tile t) starts at the table's slot for digit t of segment v
+// and ends where digit t + 1 starts (the segment's end after the last tile).
+__global__ void k_ranges_from_table(const uint32_t *__restrict__ table, Segs g, uint32_t tiles,
+                                    uint2 *__restrict__ ranges)
+{
+    const size_t n = (size_t)g.V * tiles;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const int v = (int)(k / tiles);
+        const uint32_t t = (uint32_t)(k % tiles);
+        const uint32_t b0 = __ldg(g.bbase + v), nb = __ldg(g.bbase + v + 1) - b0;
+        uint32_t s0, s1;
+        if (nb == 0) {
+            s0 = s1 = seg_start(g, v);
+        } else {
+            s0 = table[(size_t)RS_RADIX * b0 + (size_t)t * nb];
+            s1 = t + 1 < tiles ? table[(size_t)RS_RADIX * b0 + (size_t)(t + 1) * nb] : seg_start(g, v + 1);
+        }
+        ranges[k] = make_uint2(s0, s1);
+    }
+}
+
 }  // namespace
 
 size_t scan_workspace_bytes(size_t n)
@@ -635,23 +674,37 @@ static cudaError_t seg_bases(const uint32_t *start, uint32_t stride, int V, uint
 
 // Segmented passes over digits [shift0, bits) of (k0, v0), ping-ponging with
 // (k1, v1); *result_in_alt flips once per pass.
-static cudaError_t seg_passes(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const Segs &g, size_t bound,
-                       int shift0, int bits, const SortWs &w, cudaStream_t st, bool *result_in_alt,
-                       const char *prof)
+// With kept (device, [V + 1]), the first pass drops the items whose key is
+// DROP_KEY, kept receives the compacted segment starts (kept[V] = the items
+// left) and the later passes sort the compacted segments.
+static cudaError_t seg_passes(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, Segs g, size_t bound,
+                              int shift0, int bits, const SortWs &w, cudaStream_t st, bool *result_in_alt,
+                              const char *prof, uint32_t *kept = nullptr)
 {
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
     for (int shift = shift0; shift < bits; shift += 8) {
         const int wd = bits - shift < 8 ? bits - shift : 8;
         const uint32_t mask = (1u << wd) - 1u;
+        const bool drop = kept && shift == shift0;
         ProfScope ps_(prof, st);
-        k_rs_hist_seg<<<(unsigned)bound, RS_THREADS, 0, st>>>(ki, g, shift, mask, w.hist);
+        k_rs_hist_seg<<<(unsigned)bound, RS_THREADS, 0, st>>>(ki, g, shift, mask, w.hist, drop);
         count_launch();
-        cudaError_t e = exclusive_scan_u32(w.hist, w.hist, (size_t)RS_RADIX * bound, nullptr, w.scan, st);
+        cudaError_t e = exclusive_scan_u32(w.hist, w.hist, (size_t)RS_RADIX * bound, drop ? kept + g.V : nullptr,
+                                           w.scan, st);
         if (e != cudaSuccess) return e;
-        k_rs_scatter_seg<<<(unsigned)bound, RS_THREADS, 0, st>>>(ki, vi, ko, vo, g, shift, mask, w.hist);
+        k_rs_scatter_seg<<<(unsigned)bound, RS_THREADS, 0, st>>>(ki, vi, ko, vo, g, shift, mask, w.hist, drop);
         count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+        if (drop) {   // the compacted segments, and their blocks, for the later passes
+            k_kept_starts<<<(unsigned)((g.V + 255) / 256), 256, 0, st>>>(w.hist, g.bbase, g.V, bound, kept);
+            count_launch();
+            e = seg_bases(kept, 1u, g.V, w.rbase, w.vscan, st);
+            if (e != cudaSuccess) return e;
+            g.start = kept;
+            g.stride = 1u;
+            g.bbase = w.rbase;
+        }
         uint32_t *tk = ki, *tv = vi;
         ki = ko; vi = vo; ko = tk; vo = tv;
         *result_in_alt = !*result_in_alt;
@@ -701,7 +754,7 @@ cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t 
 
 cudaError_t radix_sort_pairs_seg(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, size_t n_cap,
                                  const uint32_t *seg_start, uint32_t stride, int V, int bits, void *ws,
-                                 cudaStream_t st, bool *result_in_alt, const char *prof)
+                                 cudaStream_t st, bool *result_in_alt, const char *prof, uint32_t *kept)
 {
     *result_in_alt = false;
     if (n_cap == 0 || V <= 0 || bits <= 0) return cudaSuccess;
@@ -714,16 +767,17 @@ cudaError_t radix_sort_pairs_seg(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint3
         if (e != cudaSuccess) return e;
     }
     const Segs g{seg_start, stride, w.rbase, V, 0u};
-    return seg_passes(k0, v0, k1, v1, g, bound, 0, bits, w, st, result_in_alt, prof);
+    return seg_passes(k0, v0, k1, v1, g, bound, 0, bits, w, st, result_in_alt, prof, kept);
 }
 
 cudaError_t radix_sort_entries(const uint4 *bins, const uint32_t *toffs, const uint32_t *counts, uint32_t n_rec,
                                const uint32_t *nrec_dev, const uint32_t *rec_start, uint32_t rec_stride, int V,
                                int tiles_x, uint32_t tiles, uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
                                size_t e_cap, const uint32_t *nent_dev, int bits, void *ws, cudaStream_t st,
-                               bool *result_in_alt, int sms)
+                               bool *result_in_alt, int sms, uint2 *ranges, bool *ranges_done)
 {
     *result_in_alt = false;
+    if (ranges_done) *ranges_done = false;
     if (e_cap == 0 || n_rec == 0 || V <= 0) return cudaSuccess;
     if (bits < 1) bits = 1;                  // the first pass also materialises the entries
     sort_carveouts();
@@ -757,7 +811,16 @@ cudaError_t radix_sort_entries(const uint4 *bins, const uint32_t *toffs, const u
     }
     if (bits <= 8) {
         *result_in_alt = true;
-        return cudaSuccess;
+        if (ranges && ranges_done) {
+            ProfScope ps_("ranges", st);
+            const size_t n = (size_t)V * tiles;
+            unsigned g = (unsigned)((n + 255) / 256);
+            if (g > (unsigned)sms * 16u) g = (unsigned)sms * 16u;
+            k_ranges_from_table<<<g, 256, 0, st>>>(w.hist, eg, tiles, ranges);
+            count_launch();
+            *ranges_done = true;
+        }
+        return cudaGetLastError();
     }
     // the remaining tile digits: segmented passes from (k1, v1), ending in (k0, v0) after an odd count
     bool alt2 = false;

@@ -436,11 +436,17 @@ def test_tile_lists_bitwise_and_end_to_end(R, torch, tile):
     recs = d["recs"]
     xlo, xhi, ylo, yhi, depth, vg, clus = _unpack_boxes(recs)
     live = depth != 0
+    ds, dk = d["depth_slots"].astype(np.int64), d["depth_keys"].astype(np.uint64)
+    n_live = int(live.sum())
+    # the depth sort drops the culled records (key 0xFFFFFFFF): the live ones first, then the tail marker
+    assert np.all(ds[n_live:] == 0xFFFFFFFF) and np.all(dk[n_live:] == 0xFFFFFFFF)
     dkey = np.full(n_rec, 0xFFFFFFFF, np.uint64)
-    dkey[d["depth_slots"].astype(np.int64)] = d["depth_keys"]
-    # depth sort = stable sort of the records by (view group, depth key)
+    dkey[ds[:n_live]] = dk[:n_live]
+    assert np.array_equal(dkey != 0xFFFFFFFF, live)
+    # depth sort = stable sort of the live records by (view group, depth key)
     order = np.lexsort((dkey, vg))
-    assert np.array_equal(order, d["depth_slots"].astype(np.int64))
+    order = order[dkey[order] != 0xFFFFFFFF]
+    assert np.array_equal(order, ds[:n_live])
     # (1) regression check, bitwise: the oracle's integer binning (tile
     # rectangles, 64-bit key order) applied to the GPU's own FP32 boxes and depths
     keys, vals, ranges = oracle.bin_tiles(xlo, xhi, ylo, yhi, dkey, live, tile, tx, ty, view_group=vg,

@@ -752,6 +752,7 @@ def run_main(args, w):
 
     # ---- plain per-state path (one state per launch sequence, synchronized)
     plain = None
+    plain_rounds = []
     if not args.no_plain and rank == 0:
         n_plain = S if training else min(S, 256)     # distortion workloads: a bounded sample of states
 
@@ -772,10 +773,13 @@ def run_main(args, w):
 
         for s in range(3):
             plain_state(s)
-        t0 = time.perf_counter()
-        for s in range(n_plain):
-            plain_state(s)
-        plain = n_plain / (time.perf_counter() - t0)
+        plain_rounds = []          # three rounds over the states; their median is reported
+        for _ in range(3):
+            t0 = time.perf_counter()
+            for s in range(n_plain):
+                plain_state(s)
+            plain_rounds.append(n_plain / (time.perf_counter() - t0))
+        plain = float(np.median(plain_rounds))
 
     # ---- roofline of the dominant kernel, from the live events
     pk, pk_kind = _peaks()
@@ -851,7 +855,8 @@ def run_main(args, w):
                 "ms": graph_ms, "value": ws * S / (graph_ms / 1e3), "unit": UNIT,
                 "what": "capture-safe plan, whole step replayed as one CUDA graph"},
             "ms_per_step_ci95": ci95,
-            "plain_per_state": {"value": plain, "unit": UNIT} if plain else None,
+            "plain_per_state": {"value": plain, "unit": UNIT, "rounds": plain_rounds,
+                                "what": "median of three rounds over the step's states"} if plain else None,
             "batched_vs_plain": (value / ws / plain) if plain else None,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk, "roofline": roof, "roofline_kernels": kernels_roof,

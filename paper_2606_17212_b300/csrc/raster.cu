@@ -822,40 +822,57 @@ __global__ void k_mse_reduce(const double *__restrict__ partial, int S, int part
 }
 
 // Squared-error partial sum of image s vs refs[ref_index[s]] over one chunk
-// of MSE_CHUNK_PIX pixels (four per thread), and optionally
+// of MSE_CHUNK_PIX pixels (four consecutive pixels per thread, read as three
+// 16-byte vectors where aligned), and optionally
 // dL/dimage = weight * 2 (image - ref) / (3 H W).
 __global__ void __launch_bounds__(256) k_image_mse(const float *__restrict__ images, const float *__restrict__ refs,
                                                    const int32_t *__restrict__ ref_index, size_t npix,
                                                    float gscale, double *__restrict__ partial, int parts,
                                                    float *__restrict__ dL)
 {
+    static_assert(MSE_CHUNK_PIX == 4 * 256, "four pixels per thread");
     __shared__ double wsum[8];
     const int s = blockIdx.y;
     const float *im = images + (size_t)s * npix * 3;
     const float *rf = refs + (size_t)ref_index[s] * npix * 3;
-    float x[4][3], y[4][3];
-    const size_t base = (size_t)blockIdx.x * MSE_CHUNK_PIX + threadIdx.x;
+    float *dl = dL ? dL + (size_t)s * npix * 3 : nullptr;
+    const size_t p0 = (size_t)blockIdx.x * MSE_CHUNK_PIX + 4 * (size_t)threadIdx.x;
+    float x[12], y[12];
+    const bool vec = p0 + 4 <= npix && ((reinterpret_cast<uintptr_t>(im + 3 * p0) | reinterpret_cast<uintptr_t>(rf + 3 * p0) |
+                                         (dl ? reinterpret_cast<uintptr_t>(dl + 3 * p0) : 0)) & 15) == 0;
+    const int np = p0 >= npix ? 0 : (int)min((size_t)4, npix - p0);
+    if (vec) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const size_t p = base + (size_t)k * 256;
+        for (int q = 0; q < 3; ++q) {
+            const float4 a = __ldg(reinterpret_cast<const float4 *>(im + 3 * p0) + q);
+            const float4 b = __ldg(reinterpret_cast<const float4 *>(rf + 3 * p0) + q);
+            x[4 * q] = a.x; x[4 * q + 1] = a.y; x[4 * q + 2] = a.z; x[4 * q + 3] = a.w;
+            y[4 * q] = b.x; y[4 * q + 1] = b.y; y[4 * q + 2] = b.z; y[4 * q + 3] = b.w;
+        }
+    } else {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) { x[k][c] = 0.0f; y[k][c] = 0.0f; }
-        if (p < npix) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) { x[k][c] = __ldg(im + 3 * p + c); y[k][c] = __ldg(rf + 3 * p + c); }
+        for (int k = 0; k < 12; ++k) {
+            const bool in = k / 3 < np;
+            x[k] = in ? __ldg(im + 3 * p0 + k) : 0.0f;
+            y[k] = in ? __ldg(rf + 3 * p0 + k) : 0.0f;
         }
     }
     double se = 0.0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const size_t p = base + (size_t)k * 256;
-        if (p < npix) {
-            se += (double)pixel_sq_err(x[k][0], x[k][1], x[k][2], y[k][0], y[k][1], y[k][2]);
-            if (dL) {
-                float *d = dL + ((size_t)s * npix + p) * 3;
+    for (int k = 0; k < 4; ++k)
+        if (k < np) se += (double)pixel_sq_err(x[3 * k], x[3 * k + 1], x[3 * k + 2], y[3 * k], y[3 * k + 1], y[3 * k + 2]);
+    if (dl) {
+        float d[12];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) d[c] = gscale * (x[k][c] - y[k][c]);
-            }
+        for (int k = 0; k < 12; ++k) d[k] = gscale * (x[k] - y[k]);
+        if (vec) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                reinterpret_cast<float4 *>(dl + 3 * p0)[q] = make_float4(d[4 * q], d[4 * q + 1], d[4 * q + 2], d[4 * q + 3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; ++k)
+                if (k / 3 < np) dl[3 * p0 + k] = d[k];
         }
     }
 #pragma unroll

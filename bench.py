@@ -45,7 +45,8 @@ MUFU_EX2_PER_SM_CLK = 32
 # kernel source it was taken on (sha1 of csrc/raster.cu), the workload at full size
 # and the sort tile side in pixels.
 MEASURED_TRAFFIC = {
-    ("raster_bwd", "c3_fwdbwd_250k", 32): (792_471_040 + 67_845_632, "67f628806a9144a119661aa71e0a5d07aa5b7d70"),
+    ("raster_bwd", "c3_fwdbwd_250k", 32): (792_823_552 + 68_212_736, "e78495e7392f2ee621f361681e24618324a50084"),
+    ("raster_fwd", "c3_fwdbwd_250k", 32): (440_540_416 + 182_958_592, "e78495e7392f2ee621f361681e24618324a50084"),
 }
 
 

@@ -415,6 +415,47 @@ def run_mix(args):
     prof = R.profile_read()
     R.profile(False)
 
+    # scene waves: dgs_render_scenes_batched / dgs_render_scenes_backward over
+    # groups of scenes, one forward and one adjoint raster launch per group (a
+    # renderer of its own: its per-scene workspaces are freed before the plans)
+    R2 = dgs.Renderer(0)
+    R2.set_tile_size(args.tile_size if args.tile_size else 32)
+    wave = max(1, args.mix_wave)
+    waves = [scenes[k:k + wave] for k in range(0, len(scenes), wave)]
+
+    def waves_step():
+        out = []
+        for grp in waves:
+            jobs = [(c["sc"], c["st"], c["cams"], c["bg"], c["images"]) for c in grp]
+            R2.render_scenes_batched(jobs)
+            dls = []
+            for c in grp:
+                mse, _, dL = R2.image_mse(c["images"], c["targets"], c["ridx"], weight=1.0 / c["S"], want_grad=True)
+                for g in c["grads"].values():
+                    g.zero_()
+                out.append(mse)
+                dls.append(dL)
+            R2.render_scenes_backward(jobs, dls, [c["grads"] for c in grp])
+        return out
+
+    waves_ms = None
+    waves_launches = 0
+    waves_prof = {}
+    try:
+        for _ in range(args.warmup):
+            waves_step()
+        R2.reset_kernel_launches()
+        R2.profile(True)
+        waves_ms = timed(waves_step, args.steps)
+        waves_launches = R2.kernel_launches()
+        waves_prof = R2.profile_read()
+        R2.profile(False)
+        waves_err = None
+    except RuntimeError as e:            # e.g. a group's workspaces do not fit
+        waves_err = str(e).splitlines()[0]
+    R2.close()
+    torch.cuda.empty_cache()
+
     # graph: one plan per scene in a shared arena, the whole step captured once
     arena = dgs.Arena(R)
     for c in scenes:
@@ -452,13 +493,34 @@ def run_mix(args):
     use_graph = graph_ms < eager_ms
     ms = graph_ms if use_graph else eager_ms
     value = total_states / (ms / 1e3)
+    use_waves = waves_ms is not None and waves_ms < ms
+    if use_waves:              # the headline path; the end-to-end run below uses it too
+        ms = waves_ms
+        value = total_states / (ms / 1e3)
+        graph = None           # the plans' memory goes back before the scene workspaces return
+        for c in scenes:
+            c.pop("plan").close()
+        arena.close()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        R2 = dgs.Renderer(0)
+        R2.set_tile_size(args.tile_size if args.tile_size else 32)
 
     # end to end: every scene's masks H2D from pinned memory, every MSE D2H, per step
     res_host = [torch.empty(c["S"], dtype=torch.float64).pin_memory() for c in scenes]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    if use_waves:
+        waves_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
     for _ in range(args.steps):
-        if use_graph:
+        if use_waves:
+            for c in scenes:
+                c["st"].masks.copy_(c["host_masks"], non_blocking=True)
+            for m, rh in zip(waves_step(), res_host):
+                rh.copy_(m, non_blocking=True)
+        elif use_graph:
             for c in scenes:
                 c["g_masks"].copy_(c["host_masks"], non_blocking=True)
             graph.replay()
@@ -496,7 +558,8 @@ def run_mix(args):
            "states_per_step": total_states, "states_per_scene": 64,
            "resolutions": sorted({"%dx%d" % (c["W"], c["H"]) for c in scenes}),
            "pixels_per_step": int(total_px), "l2": "flushed between timed steps (256 MB write)",
-           "parallelism": "dp1", "path": "cuda_graph_arena_plans" if use_graph else "context_calls",
+           "parallelism": "dp1",
+           "path": "scene_waves" if use_waves else ("cuda_graph_arena_plans" if use_graph else "context_calls"),
            "generation_s": round(t_gen, 1)}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -504,15 +567,25 @@ def run_mix(args):
             "mpix_per_s": total_px / (ms / 1e3) / 1e6,
             "eager_per_step": {"ms": eager_ms, "value": total_states / (eager_ms / 1e3), "unit": UNIT,
                                "what": "context calls, scene after scene"},
+            "scene_waves_per_step": ({"ms": waves_ms, "value": total_states / (waves_ms / 1e3), "unit": UNIT,
+                                      "what": "dgs_render_scenes_batched / dgs_render_scenes_backward over groups of "
+                                              "%d scenes: one forward and one adjoint raster launch per group" % wave,
+                                      "kernels_ms_per_step": {k: v[0] / args.steps for k, v in waves_prof.items()}}
+                                     if waves_ms is not None else {"error": waves_err}),
             "graph_per_step": {"ms": graph_ms, "value": total_states / (graph_ms / 1e3), "unit": UNIT,
                                "what": "one CUDA graph of every scene's plan (one arena)"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": (launches_per_step * args.steps) if use_graph else eager_launches,
+            "gpu_launches": waves_launches if use_waves else
+                            ((launches_per_step * args.steps) if use_graph else eager_launches),
             "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}, "peaks": pk_kind}
     for c in scenes:
-        c["plan"].close()
-    arena.close()
+        if "plan" in c:
+            c["plan"].close()
+    if not use_waves:
+        arena.close()
+    else:
+        R2.close()
     R.close()
     return line
 
@@ -925,12 +998,15 @@ def main():
                     help="default workload only: skip the utility-sweep and serving-mix summaries")
     ap.add_argument("--tile-size", type=int, default=0, choices=[0, 16, 32],
                     help="sort tile side (0: the library chooses per batch shape)")
+    ap.add_argument("--no-oracle-sample", action="store_true",
+                    help="skip the oracle sample (no cpu_baseline and no evaluation count for the roofline)")
+    ap.add_argument("--mix-wave", type=int, default=8,
+                    help="serving mix: scenes per dgs_render_scenes_batched call in the scene-wave path")
     ap.add_argument("--entry-headroom", type=float, default=1.1,
                     help="plan path: tile-entry capacity as a multiple of the sizing run's entries")
     ap.add_argument("--loss", default="mse", choices=["mse", "eq2"],
                     help="training loss: mean MSE, or Eq. 2 (MSE + 0.2 (1 - SSIM), CVaR_0.05 tail)")
     args = ap.parse_args()
-    args.no_oracle_sample = False
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
 
     from paper_2606_17212_b300 import synth

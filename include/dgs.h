@@ -208,6 +208,40 @@ DGS_API int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_
                         const float *dL_dimages, const dgs_scene_grad *grads, dgs_stream stream);
 
 /*
+ * Several scenes in one call (the serving mix: many scenes, each with its own
+ * states, cameras and image size).  Job k renders jobs[k].states of
+ * jobs[k].scene into jobs[k].images exactly as dgs_render_states_batched would
+ * (bit for bit).  Every scene gets a workspace of its own inside the context
+ * (kept between calls, so job k of the next call reuses the memory of job k of
+ * this one), its records and tile lists are prepared scene by scene, and one
+ * persistent forward raster launch works through the (scene, tile, state)
+ * items of all jobs from one queue.  All jobs use one sort tile size: the one
+ * fixed by dgs_set_tile_size, else 32 px.  No batch splitting under a memory
+ * budget: every scene's workspace is held at once.  jobs [host] [n_jobs];
+ * returns DGS_E_INVALID_ARG (message names the scene) for a bad job.
+ */
+typedef struct {
+    const dgs_scene *scene;        /* [host] */
+    dgs_states states;             /* masks [device], t / cam [host] */
+    const dgs_camera *cams;        /* [host] [n_cams] */
+    int32_t n_cams;
+    float bg[3];
+    float *images;                 /* [device] [n_states][H][W][3] */
+} dgs_scene_job;
+DGS_API int dgs_render_scenes_batched(dgs_ctx *ctx, const dgs_scene_job *jobs, int n_jobs, dgs_stream stream);
+
+/* Adjoint of the last dgs_render_scenes_batched call, for the same jobs (the
+ * same scenes, states, cameras and images): dL_dimages [host] [n_jobs] of
+ * [device] [n_states][H][W][3], grads [host] [n_jobs] accumulated (+=) as by
+ * dgs_render_backward.  One adjoint raster launch covers every job; the
+ * projection adjoint runs per scene.  Returns DGS_E_INVALID_ARG when a job is
+ * not the one its workspace last rendered, and DGS_E_STALE when a job's masks
+ * changed since that forward. */
+DGS_API int dgs_render_scenes_backward(dgs_ctx *ctx, const dgs_scene_job *jobs, int n_jobs,
+                                       const float *const *dL_dimages, const dgs_scene_grad *grads,
+                                       dgs_stream stream);
+
+/*
  * Eq. 3 distortion of every state against the complete render of its view:
  * renders the full-delivery image of each view group and each state, without
  * writing state images, and writes mse [device] [n_states] (FP64 sum of

@@ -124,7 +124,8 @@ struct dgs_ctx {
         pairm, grp, gmse, omaps, opart, otpart, oD, oweight, oints, recgmu, gqws,
         shord, shpair, shpair2, shrep, shflag, shpos, shlist, shitem, shkey, shstop, shseg, shcnt, shtab,
         tapemask,                  // the masks the last forward rendered (checked by the backward)
-        live;                      // [V + 1] view-group starts of the depth-sorted live records; [V] = their count
+        live,                      // [V + 1] view-group starts of the depth-sorted live records; [V] = their count
+        jobargs;                   // multi-scene calls: per-scene raster arguments, queues and item offsets
     bool tile_reuse = true;        // utility passes reuse rendered tiles across states (share.cu)
     int tile_size = 0;             // sort tile side in pixels: 16 or 32, or 0 (chosen per batch shape)
     size_t mem_budget = 0;         // cap on the workspace bytes (0: the device's free memory only)
@@ -136,6 +137,7 @@ struct dgs_ctx {
     long long reuse_pairs = 0, reuse_rendered = 0;   // last distortion pass: (state, tile) pairs, rendered
     int reuse_rounds = 0;
     std::map<std::vector<long long>, int> tuned_G;   // autotuner: call shape -> states per block
+    std::vector<dgs_ctx *> kids;   // multi-scene calls: one workspace per scene of the batch
     void *h_stage = nullptr;
     size_t h_stage_cap = 0;
     uint32_t *h_small = nullptr;   // pinned readback of counts
@@ -582,8 +584,7 @@ QueueTabs tabs_at(const int32_t *dev, const size_t off[5], size_t ng, int G)
 
 // Launch the persistent forward raster for uploaded group tables: per-call
 // item offsets from the cost-ordered tile list, counter reset, kernel.
-int launch_queue(dgs_ctx *ctx, const Plan &p, const Lists &L, const RasterArgs &a, const QueueTabs &qt,
-                 cudaStream_t st)
+int make_queue(dgs_ctx *ctx, const Plan &p, const Lists &L, const QueueTabs &qt, cudaStream_t st, WorkQueue &q)
 {
     const size_t vt = (size_t)p.V * p.tiles;
     TRY(ensure(ctx, ctx->icnt, 4 * (vt + 1), st));
@@ -593,7 +594,7 @@ int launch_queue(dgs_ctx *ctx, const Plan &p, const Lists &L, const RasterArgs &
     launch_item_counts(L.tile_order, (uint32_t)vt, p.tiles, qt.ngroups, (uint32_t *)ctx->icnt.p, ctx->sms, st);
     CK(exclusive_scan_u32((const uint32_t *)ctx->icnt.p, (uint32_t *)ctx->ioff.p, vt, nullptr, ctx->scanws.p, st));
     CK(cudaMemsetAsync(ctx->counter.p, 0, 4, st));
-    WorkQueue q;
+    q = WorkQueue();
     q.tile_order = L.tile_order;
     q.item_offsets = (const uint32_t *)ctx->ioff.p;
     q.n_vt = (uint32_t)vt;
@@ -603,6 +604,14 @@ int launch_queue(dgs_ctx *ctx, const Plan &p, const Lists &L, const RasterArgs &
     q.vg_group_base = qt.gbase;
     q.state_order = qt.order;
     q.counter = (uint32_t *)ctx->counter.p;
+    return DGS_OK;
+}
+
+int launch_queue(dgs_ctx *ctx, const Plan &p, const Lists &L, const RasterArgs &a, const QueueTabs &qt,
+                 cudaStream_t st)
+{
+    WorkQueue q;
+    TRY(make_queue(ctx, p, L, qt, st, q));
     launch_raster_fwd(a, q, qt.G, ctx->sms, st);
     CK(cudaGetLastError());
     return DGS_OK;
@@ -888,7 +897,7 @@ std::vector<Buf *> all_bufs(dgs_ctx *ctx)
                    &ctx->icnt, &ctx->ioff, &ctx->qint, &ctx->counter, &ctx->pairm, &ctx->grp, &ctx->gmse, &ctx->omaps, &ctx->opart, &ctx->otpart,
                    &ctx->oD, &ctx->oweight, &ctx->oints, &ctx->recgmu, &ctx->gqws, &ctx->shord, &ctx->shpair,
                    &ctx->shpair2, &ctx->shrep, &ctx->shflag, &ctx->shpos, &ctx->shlist, &ctx->shitem, &ctx->shkey, &ctx->shstop,
-                   &ctx->shseg, &ctx->shcnt, &ctx->shtab, &ctx->tapemask, &ctx->live};
+                   &ctx->shseg, &ctx->shcnt, &ctx->shtab, &ctx->tapemask, &ctx->live, &ctx->jobargs};
 }
 
 // Free the device workspace except the buffers in `keep` (after the stream's
@@ -919,6 +928,41 @@ void free_ctx_buffers(dgs_ctx *ctx)
 
 int utility_pass(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states, const dgs_camera *cams,
                  int n_cams, const float *bg, double *mse, double *psnr, cudaStream_t st);
+
+bool grads_complete(const dgs_scene *scene, const dgs_scene_grad *g)
+{
+    return g->mu0 && g->log_scale && g->quat && g->opacity_logit && g->colour &&
+           !(scene->temporal_rank > 0 && !g->u) && !(scene->n_layers > 1 && scene->res_mode != 1 && !g->res) &&
+           !(scene->affine && !g->affine) && !(scene->n_layers > 1 && scene->res_mode == 2 && !g->res_step);
+}
+
+// The projection adjoint after the adjoint raster has accumulated the record
+// moments of lists L (plan p) in ctx->recgrad: chain rule to the scene
+// gradients, and the moments cleared again.
+int project_backward(dgs_ctx *ctx, const dgs_scene *scene, const Plan &p, const Lists &L,
+                     const dgs_scene_grad *grads, cudaStream_t st)
+{
+    const uint32_t nRec = L.nRec;
+    GradDev g;
+    g.mu0 = grads->mu0; g.u = grads->u; g.ls = grads->log_scale; g.quat = grads->quat;
+    g.logit = grads->opacity_logit; g.colour = grads->colour; g.res = grads->res;
+    g.affine = grads->affine; g.rec_gmu = nullptr;
+    g.res_step = grads->res_step; g.gq = nullptr;
+    if (scene->affine) {
+        TRY(ensure(ctx, ctx->recgmu, sizeof(float) * 3 * ((size_t)nRec + 1), st));
+        g.rec_gmu = (float *)ctx->recgmu.p;
+    }
+    if (scene->res_mode == 2 && scene->n_layers > 1) {
+        const SceneDev sdv = scene_dev(scene);
+        TRY(ensure(ctx, ctx->gqws, sizeof(float) * (size_t)(scene->n_layers - 1) * scene->n * sdv.K, st));
+        g.gq = (float *)ctx->gqws.p;
+    }
+    launch_project_bwd(scene_dev(scene), (const ViewGroup *)ctx->vgs.p, p.V, (const uint32_t *)ctx->need.p,
+                       (const uint32_t *)ctx->recBase.p, (float4 *)ctx->recgrad.p, g, nRec, ctx->sms, st);
+    CK(cudaGetLastError());
+    ctx->recgrad.zeroed = true;          // the projection adjoint cleared what the raster wrote
+    return DGS_OK;
+}
 
 RasterArgs plan_raster_args(dgs_plan *P)
 {
@@ -963,6 +1007,7 @@ void dgs_destroy(dgs_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
+    for (dgs_ctx *k : ctx->kids) dgs_destroy(k);
     free_ctx_buffers(ctx);
     delete ctx;
 }
@@ -1076,11 +1121,7 @@ int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *
         TRY(build_plan(ctx, sub, cams, n_cams, false, p));
         if (p.S_user == 0 || scene->n == 0) return DGS_OK;
         if (!dL_s) return fail(ctx, DGS_E_INVALID_ARG, "dL_dimages is null");
-        if (!grads->mu0 || !grads->log_scale || !grads->quat || !grads->opacity_logit || !grads->colour ||
-            (scene->temporal_rank > 0 && !grads->u) ||
-            (scene->n_layers > 1 && scene->res_mode != 1 && !grads->res) || (scene->affine && !grads->affine) ||
-            (scene->n_layers > 1 && scene->res_mode == 2 && !grads->res_step))
-            return fail(ctx, DGS_E_INVALID_ARG, "gradient array is null");
+        if (!grads_complete(scene, grads)) return fail(ctx, DGS_E_INVALID_ARG, "gradient array is null");
         Lists L;
         bool reuse = same_call(ctx->tape, scene, sub, cams, n_cams) && ctx->tape.plan.tile_shift == p.tile_shift;
         if (reuse) {
@@ -1105,8 +1146,7 @@ int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *
             TRY(prepare(ctx, scene, sub->masks, p, false, st, L));
             record_tape(ctx->tape, scene, sub, cams, n_cams, p, L);
         }
-        const uint32_t nRec = L.nRec;
-        TRY(ensure_zeroed(ctx, ctx->recgrad, sizeof(float4) * 3 * (size_t)nRec, st));
+        TRY(ensure_zeroed(ctx, ctx->recgrad, sizeof(float4) * 3 * (size_t)L.nRec, st));
         ctx->recgrad.zeroed = false;
         RasterBwdArgs b;
         b.f = raster_args(ctx, p, scene->n_clusters, bg, L.evals);
@@ -1114,27 +1154,199 @@ int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *
         b.img_fwd = img_s;
         b.rec_grad = (float4 *)ctx->recgrad.p;
         launch_raster_bwd(b, st);
-        GradDev g;
-        g.mu0 = grads->mu0; g.u = grads->u; g.ls = grads->log_scale; g.quat = grads->quat;
-        g.logit = grads->opacity_logit; g.colour = grads->colour; g.res = grads->res;
-        g.affine = grads->affine; g.rec_gmu = nullptr;
-        g.res_step = grads->res_step; g.gq = nullptr;
-        if (scene->affine) {
-            TRY(ensure(ctx, ctx->recgmu, sizeof(float) * 3 * ((size_t)nRec + 1), st));
-            g.rec_gmu = (float *)ctx->recgmu.p;
-        }
-        if (scene->res_mode == 2 && scene->n_layers > 1) {
-            const SceneDev sdv = scene_dev(scene);
-            TRY(ensure(ctx, ctx->gqws, sizeof(float) * (size_t)(scene->n_layers - 1) * scene->n * sdv.K, st));
-            g.gq = (float *)ctx->gqws.p;
-        }
-        launch_project_bwd(scene_dev(scene), (const ViewGroup *)ctx->vgs.p, p.V, (const uint32_t *)ctx->need.p,
-                           (const uint32_t *)ctx->recBase.p, (float4 *)ctx->recgrad.p, g, nRec, ctx->sms, st);
-        CK(cudaGetLastError());
-        ctx->recgrad.zeroed = true;          // the projection adjoint cleared what the raster wrote
-        return DGS_OK;
+        return project_backward(ctx, scene, p, L, grads, st);
     };
     return chunked(ctx, states, (scene->n_clusters * scene->n_layers + 31) / 32, 0, st, pass);
+}
+
+// ---------------------------------------------------------------- several scenes
+// dgs_render_scenes_batched / dgs_render_scenes_backward: every scene of the
+// batch gets a workspace of its own (a child context, kept between calls), its
+// closure, projection, sorts and lists are prepared there scene by scene, and
+// one persistent forward raster launch (one adjoint raster launch) works
+// through the (scene, tile, state) items of all of them from one queue.
+}  // extern "C"
+
+namespace {
+
+dgs_ctx *make_kid(const dgs_ctx *parent)
+{
+    dgs_ctx *k = new dgs_ctx();
+    k->device = parent->device;
+    k->sms = parent->sms;
+    if (cudaMallocHost((void **)&k->h_small, 64 + 4 * (MAX_CLUSTERS + 1)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&k->stage_done, cudaEventDisableTiming) != cudaSuccess) {
+        if (k->h_small) cudaFreeHost(k->h_small);
+        delete k;
+        return nullptr;
+    }
+    k->launch_base = parent->launch_base;
+    return k;
+}
+
+int scene_job_fail(dgs_ctx *ctx, const dgs_ctx *kid, int k, int code)
+{
+    return fail(ctx, code, "scene %d: %s", k, kid->err.c_str());
+}
+
+// Copy n bytes from host memory into ctx->jobargs at byte offset off through
+// the pinned staging buffer (the buffer must already hold off + n bytes).
+int upload_jobs(dgs_ctx *ctx, const void *src, size_t n, size_t off, cudaStream_t st)
+{
+    TRY(ensure_stage(ctx, n, st));
+    CK(cudaEventSynchronize(ctx->stage_done));
+    std::memcpy(ctx->h_stage, src, n);
+    CK(cudaMemcpyAsync((char *)ctx->jobargs.p + off, ctx->h_stage, n, cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(ctx->stage_done, st));
+    return DGS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dgs_render_scenes_batched(dgs_ctx *ctx, const dgs_scene_job *jobs, int n_jobs, dgs_stream stream)
+{
+    if (!ctx) return DGS_E_INVALID_ARG;
+    if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(ctx, DGS_E_INVALID_ARG, "jobs is null or n_jobs < 0");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    // one tile size for the whole launch: the caller's, else 32 px
+    const int shift = ctx->tile_size == 16 ? 4 : 5;
+    while ((int)ctx->kids.size() < n_jobs) {
+        dgs_ctx *k = make_kid(ctx);
+        if (!k) return fail(ctx, DGS_E_OOM, "pinned host memory for a scene workspace");
+        ctx->kids.push_back(k);
+    }
+    std::vector<RasterArgs> args;
+    std::vector<WorkQueue> queues;
+    std::vector<uint32_t> off(1, 0u);
+    for (int k = 0; k < n_jobs; ++k) {
+        const dgs_scene_job &J = jobs[k];
+        dgs_ctx *kid = ctx->kids[k];
+        kid->tile_size = 1 << shift;
+        kid->active_shift = shift;
+        kid->tape.valid = false;
+        if (!J.scene) return fail(ctx, DGS_E_INVALID_ARG, "scene %d: scene is null", k);
+        if (check_scene(kid, J.scene) != DGS_OK) return scene_job_fail(ctx, kid, k, DGS_E_INVALID_ARG);
+        Plan p;
+        int r = build_plan(kid, &J.states, J.cams, J.n_cams, false, p);
+        if (r != DGS_OK) return scene_job_fail(ctx, kid, k, r);
+        if (p.S_user == 0) continue;
+        if (!J.images) return fail(ctx, DGS_E_INVALID_ARG, "scene %d: images is null", k);
+        Lists L;
+        if ((r = prepare(kid, J.scene, J.states.masks, p, false, st, L)) != DGS_OK) return scene_job_fail(ctx, kid, k, r);
+        RasterArgs a = raster_args(kid, p, J.scene->n_clusters, J.bg, L.evals);
+        a.images = J.images;
+        std::vector<int32_t> buf;
+        size_t toff[5], ng = 0;
+        build_groups(p, 0, p.S_user, 1, buf, toff, ng);
+        if ((r = ensure(kid, kid->qint, 4 * buf.size(), st)) != DGS_OK ||
+            (r = ensure_stage(kid, 4 * buf.size(), st)) != DGS_OK)
+            return scene_job_fail(ctx, kid, k, r);
+        CK(cudaEventSynchronize(kid->stage_done));
+        std::memcpy(kid->h_stage, buf.data(), 4 * buf.size());
+        CK(cudaMemcpyAsync(kid->qint.p, kid->h_stage, 4 * buf.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaEventRecord(kid->stage_done, st));
+        WorkQueue q;
+        if ((r = make_queue(kid, p, L, tabs_at((const int32_t *)kid->qint.p, toff, ng, 1), st, q)) != DGS_OK)
+            return scene_job_fail(ctx, kid, k, r);
+        record_tape(kid->tape, J.scene, &J.states, J.cams, J.n_cams, p, L);
+        const size_t mbytes = 4 * (size_t)p.S_user * (size_t)((J.scene->n_clusters * J.scene->n_layers + 31) / 32);
+        if ((r = ensure(kid, kid->tapemask, mbytes, st)) != DGS_OK) return scene_job_fail(ctx, kid, k, r);
+        CK(cudaMemcpyAsync(kid->tapemask.p, J.states.masks, mbytes, cudaMemcpyDeviceToDevice, st));
+        args.push_back(a);
+        queues.push_back(q);
+        off.push_back(off.back() + q.n_items);
+    }
+    const int n = (int)args.size();
+    if (n == 0 || off.back() == 0) return DGS_OK;
+    // device copies of the per-scene arguments, queues and item offsets, then one launch
+    const size_t b_args = sizeof(RasterArgs) * n, b_q = sizeof(WorkQueue) * n, b_off = 4 * (size_t)(n + 1);
+    const size_t o_q = (b_args + 255) & ~(size_t)255, o_off = (o_q + b_q + 255) & ~(size_t)255;
+    const size_t o_cnt = (o_off + b_off + 255) & ~(size_t)255;
+    TRY(ensure(ctx, ctx->jobargs, o_cnt + 16, st));
+    std::vector<char> host(o_cnt);
+    std::memcpy(host.data(), args.data(), b_args);
+    std::memcpy(host.data() + o_q, queues.data(), b_q);
+    std::memcpy(host.data() + o_off, off.data(), b_off);
+    TRY(upload_jobs(ctx, host.data(), o_cnt, 0, st));
+    uint32_t *counter = (uint32_t *)((char *)ctx->jobargs.p + o_cnt);
+    CK(cudaMemsetAsync(counter, 0, 4, st));
+    char *base = (char *)ctx->jobargs.p;
+    launch_raster_fwd_multi((const RasterArgs *)base, (const WorkQueue *)(base + o_q), (const uint32_t *)(base + o_off),
+                            n, counter, shift, ctx->sms, st);
+    CK(cudaGetLastError());
+    return DGS_OK;
+}
+
+int dgs_render_scenes_backward(dgs_ctx *ctx, const dgs_scene_job *jobs, int n_jobs, const float *const *dL_dimages,
+                               const dgs_scene_grad *grads, dgs_stream stream)
+{
+    if (!ctx) return DGS_E_INVALID_ARG;
+    if (n_jobs < 0 || (n_jobs > 0 && (!jobs || !dL_dimages || !grads)))
+        return fail(ctx, DGS_E_INVALID_ARG, "jobs, dL_dimages or grads is null");
+    if ((int)ctx->kids.size() < n_jobs)
+        return fail(ctx, DGS_E_INVALID_ARG, "dgs_render_scenes_backward needs dgs_render_scenes_batched of these jobs first");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    // every scene must be the one its workspace last rendered, with the masks it rendered
+    std::vector<int> live;
+    for (int k = 0; k < n_jobs; ++k) {
+        const dgs_scene_job &J = jobs[k];
+        dgs_ctx *kid = ctx->kids[k];
+        if (J.states.n_states == 0) continue;
+        if (!J.scene || !J.images || !dL_dimages[k]) return fail(ctx, DGS_E_INVALID_ARG, "scene %d: null argument", k);
+        if (!kid->tape.valid || !same_call(kid->tape, J.scene, &J.states, J.cams, J.n_cams))
+            return fail(ctx, DGS_E_INVALID_ARG, "scene %d: not the scene batch the last dgs_render_scenes_batched rendered", k);
+        if (!grads_complete(J.scene, &grads[k])) return fail(ctx, DGS_E_INVALID_ARG, "scene %d: gradient array is null", k);
+        const Plan &p = kid->tape.plan;
+        const size_t words = (size_t)p.S_user * (size_t)((J.scene->n_clusters * J.scene->n_layers + 31) / 32);
+        uint32_t *flag = (uint32_t *)kid->total.p + 4;
+        CK(cudaMemsetAsync(flag, 0, 4, st));
+        launch_words_differ(J.states.masks, (const uint32_t *)kid->tapemask.p, words, flag, ctx->sms, st);
+        CK(cudaMemcpyAsync(kid->h_small + 12, flag, 4, cudaMemcpyDeviceToHost, st));
+        live.push_back(k);
+    }
+    if (live.empty()) return DGS_OK;
+    CK(cudaStreamSynchronize(st));
+    for (int k : live)
+        if (ctx->kids[k]->h_small[12])
+            return fail(ctx, DGS_E_STALE, "scene %d: the masks changed after the forward call", k);
+    std::vector<RasterBwdArgs> bargs;
+    std::vector<size_t> off(1, 0);
+    for (int k : live) {
+        const dgs_scene_job &J = jobs[k];
+        dgs_ctx *kid = ctx->kids[k];
+        const Lists &L = kid->tape.lists;
+        int r = ensure_zeroed(kid, kid->recgrad, sizeof(float4) * 3 * (size_t)L.nRec, st);
+        if (r != DGS_OK) return scene_job_fail(ctx, kid, k, r);
+        kid->recgrad.zeroed = false;
+        RasterBwdArgs b;
+        b.f = raster_args(kid, kid->tape.plan, J.scene->n_clusters, J.bg, L.evals);
+        b.dL_dimg = dL_dimages[k];
+        b.img_fwd = J.images;
+        b.rec_grad = (float4 *)kid->recgrad.p;
+        bargs.push_back(b);
+        off.push_back(off.back() + raster_bwd_items(b.f));
+    }
+    const int n = (int)bargs.size();
+    const size_t b_args = sizeof(RasterBwdArgs) * n, o_off = (b_args + 255) & ~(size_t)255;
+    const size_t total = o_off + sizeof(size_t) * (n + 1);
+    TRY(ensure(ctx, ctx->jobargs, total, st));
+    std::vector<char> host(total);
+    std::memcpy(host.data(), bargs.data(), b_args);
+    std::memcpy(host.data() + o_off, off.data(), sizeof(size_t) * (n + 1));
+    TRY(upload_jobs(ctx, host.data(), total, 0, st));
+    launch_raster_bwd_multi((const RasterBwdArgs *)ctx->jobargs.p,
+                            (const size_t *)((char *)ctx->jobargs.p + o_off), n, off.back(), st);
+    CK(cudaGetLastError());
+    for (int k : live) {
+        dgs_ctx *kid = ctx->kids[k];
+        const int r = project_backward(kid, jobs[k].scene, kid->tape.plan, kid->tape.lists, &grads[k], st);
+        if (r != DGS_OK) return scene_job_fail(ctx, kid, k, r);
+    }
+    return DGS_OK;
 }
 
 int dgs_state_utility(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *states, const dgs_camera *cams,

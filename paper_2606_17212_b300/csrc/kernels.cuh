@@ -85,6 +85,16 @@ struct RasterBwdArgs {
                                   // (S dx, S dy, S dx^2, S dx dy), (S dy^2, S 1, dL/dr, dL/dg), (dL/db, -, -, -)
 };
 void launch_raster_bwd(const RasterBwdArgs &a, cudaStream_t st);
+// Several scenes in one launch (device arrays of per-job arguments).  Forward:
+// queues[k] as launch_raster_fwd's, job k's items [item_off[k], item_off[k + 1])
+// of one shared zeroed counter, every job with images, no MSE, tile shift
+// tile_shift.  Adjoint: job k's items [item_off[k], item_off[k + 1]) with
+// item_off[k + 1] - item_off[k] = raster_bwd_items(jobs[k].f), forward images given.
+void launch_raster_fwd_multi(const RasterArgs *args, const WorkQueue *queues, const uint32_t *item_off, int n_jobs,
+                             uint32_t *counter, int tile_shift, int sms, cudaStream_t st);
+size_t raster_bwd_items(const RasterArgs &a);
+void launch_raster_bwd_multi(const RasterBwdArgs *jobs, const size_t *item_off, int n_jobs, size_t total_items,
+                             cudaStream_t st);
 
 void launch_mse_reduce(const double *partial, int S, int parts, double inv_count, double *mse, double *psnr,
                        cudaStream_t st);

@@ -492,6 +492,88 @@ __device__ __forceinline__ void load_depth(const RasterArgs &a, int s, WarpSmem 
 // writes the state's pixels and/or its FP64 squared-error partial; items come
 // costliest tile first from an atomic counter (or from an explicit work list).
 // Per pixel the arithmetic is fwd_pair(), exactly as for a single state.
+// One work item of the forward raster: (view-group tile, state) number `item`
+// of queue q.  Every lane of the warp calls it with the same item.
+template <bool WRITE, bool MSE, bool LIST, int SHIFT>
+__device__ __forceinline__ void fwd_item(const RasterArgs &a, const WorkQueue &q, uint32_t item, WarpSmem &sm,
+                                         int lane)
+{
+    uint32_t vt;
+    int s;
+    if (LIST) {
+        const uint32_t first = q.item_first[item];
+        vt = q.list_vt[first];
+        s = (int)q.list_state[first];
+    } else {
+        // largest j with item_offsets[j] <= item: a 32-way search, one
+        // probe per lane per step (item_offsets is non-decreasing)
+        uint32_t lo_ = 0, span = q.n_vt;
+        while (span > 1) {
+            const uint32_t stride = (span + 31) / 32;
+            const uint32_t j = lo_ + (uint32_t)lane * stride;
+            const bool le = j < lo_ + span && q.item_offsets[j] <= item;
+            const uint32_t bal = __ballot_sync(FULL, le);     // lanes 0 .. k-1 (lane 0 always)
+            const uint32_t k = 31 - __clz(bal);
+            lo_ += k * stride;
+            span = min(stride, span - k * stride);
+        }
+        vt = q.tile_order[lo_];
+        const int grp = q.vg_group_base[vt / a.tiles] + (int)(item - q.item_offsets[lo_]);
+        s = q.state_order[q.group_first[grp]];
+    }
+    const int tile = (int)(vt % a.tiles);
+    load_depth(a, s, sm);
+    const uint2 rg = a.ranges[vt];
+    const float *rbase = MSE ? a.refs + (size_t)a.ref_of_state[s] * a.H * a.W * 3 : nullptr;
+    // the tile's 16 x 16 regions in row-major order, each walked on its own
+    constexpr int rpx = 1 << (SHIFT - 4);
+    uint32_t stop = 0;
+    for (int reg = 0; reg < rpx * rpx; ++reg) {
+        const Lane<NPAIR> L = lane_of<NPAIR>(tile, (reg % rpx) * BLOCK, (reg / rpx) * BLOCK, a);
+        // a region of a 32 px tile can lie past the image edge (warp-uniform); 16 px tiles never do
+        if (SHIFT > 4 && (L.rx0 >= a.W || L.ry0 >= a.H)) continue;
+        FwdLane<NPAIR> f;
+        f.init(L);
+        const uint32_t e = walk(a, L, sm, rg.x, rg.y, f);
+        stop = max(stop, e - rg.x);
+        double se = 0.0;
+#pragma unroll
+        for (int j = 0; j < NPAIR; ++j) {
+            f2 o0, o1, o2;
+            f.out(j, a.bg0, a.bg1, a.bg2, o0, o1, o2);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = 2 * j + h;
+                if (!((L.inimg >> r) & 1u)) continue;
+                const float c0 = h ? hi(o0) : lo(o0), c1 = h ? hi(o1) : lo(o1), c2 = h ? hi(o2) : lo(o2);
+                const size_t pix = (size_t)(L.py0 + r) * a.W + L.px;
+                if (WRITE) {
+                    float *dst = a.images + ((size_t)(s - a.img_s0) * a.H * a.W + pix) * 3;
+                    dst[0] = c0; dst[1] = c1; dst[2] = c2;
+                }
+                if (MSE) {
+                    const float *rp = rbase + pix * 3;
+                    se += (double)pixel_sq_err(c0, c1, c2, rp[0], rp[1], rp[2]);
+                    if (a.dL) {   // the loss gradient, as the separate image-MSE pass forms it
+                        float *dst = a.dL + ((size_t)(s - a.img_s0) * a.H * a.W + pix) * 3;
+                        dst[0] = a.gscale * (c0 - rp[0]);
+                        dst[1] = a.gscale * (c1 - rp[1]);
+                        dst[2] = a.gscale * (c2 - rp[2]);
+                    }
+                }
+            }
+        }
+        if (MSE) {
+            // one partial per 16 x 16 pixel block: the same sum whatever the tile size
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) se += __shfl_xor_sync(FULL, se, off);
+            if (lane == 0)
+                a.partial[(size_t)s * a.blocks + (size_t)(L.ry0 / BLOCK) * a.blocks_x + L.rx0 / BLOCK] = se;
+        }
+    }
+    if (LIST && lane == 0) a.stop[(size_t)s * a.tiles + tile] = stop;
+}
+
 template <bool WRITE, bool MSE, bool LIST, int SHIFT>
 __global__ void __launch_bounds__(RT, FWD_MIN_BLOCKS) k_raster_fwd(RasterArgs a, WorkQueue q)
 {
@@ -504,80 +586,55 @@ __global__ void __launch_bounds__(RT, FWD_MIN_BLOCKS) k_raster_fwd(RasterArgs a,
         if (lane == 0) item = atomicAdd(q.counter, 1u);
         item = __shfl_sync(FULL, item, 0);
         if (item >= n_items) break;
-        uint32_t vt;
-        int s;
-        if (LIST) {
-            const uint32_t first = q.item_first[item];
-            vt = q.list_vt[first];
-            s = (int)q.list_state[first];
-        } else {
-            // largest j with item_offsets[j] <= item: a 32-way search, one
-            // probe per lane per step (item_offsets is non-decreasing)
-            uint32_t lo_ = 0, span = q.n_vt;
-            while (span > 1) {
-                const uint32_t stride = (span + 31) / 32;
-                const uint32_t j = lo_ + (uint32_t)lane * stride;
-                const bool le = j < lo_ + span && q.item_offsets[j] <= item;
-                const uint32_t bal = __ballot_sync(FULL, le);     // lanes 0 .. k-1 (lane 0 always)
-                const uint32_t k = 31 - __clz(bal);
-                lo_ += k * stride;
-                span = min(stride, span - k * stride);
-            }
-            vt = q.tile_order[lo_];
-            const int grp = q.vg_group_base[vt / a.tiles] + (int)(item - q.item_offsets[lo_]);
-            s = q.state_order[q.group_first[grp]];
+        fwd_item<WRITE, MSE, LIST, SHIFT>(a, q, item, sm, lane);
+        __syncwarp();
+    }
+}
+
+static_assert(sizeof(RasterArgs) % 4 == 0 && sizeof(WorkQueue) % 4 == 0 && sizeof(RasterBwdArgs) % 4 == 0,
+              "argument structs are copied word by word");
+// Copy a struct of `bytes` (a multiple of 4) word by word across the warp.
+__device__ __forceinline__ void copy_words(void *dst, const void *src, size_t bytes, int lane)
+{
+    uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+    for (int i = lane; i < (int)(bytes / 4); i += 32) d[i] = s[i];
+}
+
+// The forward raster of several scenes in one persistent launch: job k has
+// its own arguments and queue, its items are [item_off[k], item_off[k + 1])
+// of one shared counter, so warps move on to any scene's work as they finish.
+template <int SHIFT>
+__global__ void __launch_bounds__(RT, FWD_MIN_BLOCKS) k_raster_fwd_multi(const RasterArgs *__restrict__ args,
+                                                                          const WorkQueue *__restrict__ queues,
+                                                                          const uint32_t *__restrict__ item_off,
+                                                                          int n_jobs, uint32_t *counter)
+{
+    __shared__ WarpSmem smem[WARPS];
+    __shared__ RasterArgs jargs[WARPS];        // the warp's current job, copied from global memory
+    __shared__ __align__(16) unsigned char jqueue_raw[WARPS][sizeof(WorkQueue)];   // (WorkQueue has initialisers)
+    WorkQueue *jqueue = reinterpret_cast<WorkQueue *>(&jqueue_raw[0][0]);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmem &sm = smem[w];
+    const uint32_t n_items = item_off[n_jobs];
+    int job = -1;
+    for (;;) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1u);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= n_items) break;
+        int lo = 0, hi = n_jobs - 1;           // the last job whose first item is <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (item_off[mid] <= item) lo = mid; else hi = mid - 1;
         }
-        const int tile = (int)(vt % a.tiles);
-        load_depth(a, s, sm);
-        const uint2 rg = a.ranges[vt];
-        const float *rbase = MSE ? a.refs + (size_t)a.ref_of_state[s] * a.H * a.W * 3 : nullptr;
-        // the tile's 16 x 16 regions in row-major order, each walked on its own
-        constexpr int rpx = 1 << (SHIFT - 4);
-        uint32_t stop = 0;
-        for (int reg = 0; reg < rpx * rpx; ++reg) {
-            const Lane<NPAIR> L = lane_of<NPAIR>(tile, (reg % rpx) * BLOCK, (reg / rpx) * BLOCK, a);
-            // a region of a 32 px tile can lie past the image edge (warp-uniform); 16 px tiles never do
-            if (SHIFT > 4 && (L.rx0 >= a.W || L.ry0 >= a.H)) continue;
-            FwdLane<NPAIR> f;
-            f.init(L);
-            const uint32_t e = walk(a, L, sm, rg.x, rg.y, f);
-            stop = max(stop, e - rg.x);
-            double se = 0.0;
-#pragma unroll
-            for (int j = 0; j < NPAIR; ++j) {
-                f2 o0, o1, o2;
-                f.out(j, a.bg0, a.bg1, a.bg2, o0, o1, o2);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int r = 2 * j + h;
-                    if (!((L.inimg >> r) & 1u)) continue;
-                    const float c0 = h ? hi(o0) : lo(o0), c1 = h ? hi(o1) : lo(o1), c2 = h ? hi(o2) : lo(o2);
-                    const size_t pix = (size_t)(L.py0 + r) * a.W + L.px;
-                    if (WRITE) {
-                        float *dst = a.images + ((size_t)(s - a.img_s0) * a.H * a.W + pix) * 3;
-                        dst[0] = c0; dst[1] = c1; dst[2] = c2;
-                    }
-                    if (MSE) {
-                        const float *rp = rbase + pix * 3;
-                        se += (double)pixel_sq_err(c0, c1, c2, rp[0], rp[1], rp[2]);
-                        if (a.dL) {   // the loss gradient, as the separate image-MSE pass forms it
-                            float *dst = a.dL + ((size_t)(s - a.img_s0) * a.H * a.W + pix) * 3;
-                            dst[0] = a.gscale * (c0 - rp[0]);
-                            dst[1] = a.gscale * (c1 - rp[1]);
-                            dst[2] = a.gscale * (c2 - rp[2]);
-                        }
-                    }
-                }
-            }
-            if (MSE) {
-                // one partial per 16 x 16 pixel block: the same sum whatever the tile size
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) se += __shfl_xor_sync(FULL, se, off);
-                if (lane == 0)
-                    a.partial[(size_t)s * a.blocks + (size_t)(L.ry0 / BLOCK) * a.blocks_x + L.rx0 / BLOCK] = se;
-            }
+        if (lo != job) {
+            copy_words(&jargs[w], &args[lo], sizeof(RasterArgs), lane);
+            copy_words(&jqueue[w], &queues[lo], sizeof(WorkQueue), lane);
+            __syncwarp();
+            job = lo;
         }
-        if (LIST && lane == 0) a.stop[(size_t)s * a.tiles + tile] = stop;
+        fwd_item<true, false, false, SHIFT>(jargs[w], jqueue[w], item - item_off[lo], sm, lane);
         __syncwarp();
     }
 }
@@ -717,17 +774,21 @@ struct BwdLane {
 // final pixel value is read from the forward's image (IMG) or recomputed by a
 // first forward walk.  Per-Gaussian pixel moments: four pixels per lane, a
 // warp transpose reduction, one atomic add per moment.
+// Work items of the adjoint raster of one call: (tile, 16x8 region, state).
+__device__ __forceinline__ size_t bwd_items(const RasterArgs &a)
+{
+    const int RH = 4 * BWD_NP;
+    const int regs = (1 << (a.tile_shift - 4)) * ((1 << a.tile_shift) / RH);
+    return (size_t)a.tiles * regs * a.S;
+}
+
+// One adjoint work item (every lane of the warp calls it with the same item < bwd_items).
 template <bool IMG>
-__global__ void __launch_bounds__(RT, BWD_MIN_BLOCKS) k_raster_bwd(RasterBwdArgs b)
+__device__ __forceinline__ void bwd_item(const RasterBwdArgs &b, size_t item, WarpSmem &sm)
 {
     constexpr int NP = BWD_NP, RH = 4 * BWD_NP;     // pairs per lane, region height
     const RasterArgs &a = b.f;
-    __shared__ WarpSmem smem[WARPS];
-    const int w = threadIdx.x >> 5;
-    WarpSmem &sm = smem[w];
     const int rpx = 1 << (a.tile_shift - 4), rpy = (1 << a.tile_shift) / RH, regs = rpx * rpy;
-    const size_t item = (size_t)blockIdx.x * WARPS + w;
-    if (item >= (size_t)a.tiles * regs * a.S) return;
     const int s = (int)(item % (unsigned)a.S);
     const int tr = (int)(item / (unsigned)a.S), tile = tr / regs, reg = tr % regs;
     const Lane<NP> L = lane_of<NP>(tile, (reg % rpx) * BLOCK, (reg / rpx) * RH, a);
@@ -783,6 +844,37 @@ __global__ void __launch_bounds__(RT, BWD_MIN_BLOCKS) k_raster_bwd(RasterBwdArgs
         B.p[j].g2 = pk(g[0][2], g[1][2]);
     }
     walk(a, L, sm, rg.x, rg.y, B);
+}
+
+template <bool IMG>
+__global__ void __launch_bounds__(RT, BWD_MIN_BLOCKS) k_raster_bwd(RasterBwdArgs b)
+{
+    __shared__ WarpSmem smem[WARPS];
+    const int w = threadIdx.x >> 5;
+    const size_t item = (size_t)blockIdx.x * WARPS + w;
+    if (item >= bwd_items(b.f)) return;
+    bwd_item<IMG>(b, item, smem[w]);
+}
+
+// The adjoint raster of several scenes in one launch: warp g takes item
+// g - item_off[k] of job k, the last job with item_off[k] <= g.
+__global__ void __launch_bounds__(RT, BWD_MIN_BLOCKS) k_raster_bwd_multi(const RasterBwdArgs *__restrict__ jobs,
+                                                                         const size_t *__restrict__ item_off,
+                                                                         int n_jobs)
+{
+    __shared__ WarpSmem smem[WARPS];
+    __shared__ RasterBwdArgs jargs[WARPS];     // the warp's job, copied from global memory
+    const int w = threadIdx.x >> 5;
+    const size_t g = (size_t)blockIdx.x * WARPS + w;
+    if (g >= item_off[n_jobs]) return;
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (item_off[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    copy_words(&jargs[w], &jobs[lo], sizeof(RasterBwdArgs), threadIdx.x & 31);
+    __syncwarp();
+    bwd_item<true>(jargs[w], g - item_off[lo], smem[w]);
 }
 
 // Cost key of each (view group, tile), 16 bits: ascending key = descending
@@ -913,6 +1005,46 @@ static void launch_fwd_t(const RasterArgs &a, const WorkQueue &q, int sms, cudaS
         k_raster_fwd<WRITE, MSE, LIST, 4><<<sms * fwd_occupancy<WRITE, MSE, LIST, 4>(), RT, 0, st>>>(a, q);
 }
 
+template <int SHIFT>
+static int fwd_multi_occupancy()
+{
+    static int n = 0;
+    if (!n) {
+        int m = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k_raster_fwd_multi<SHIFT>, RT, 0);
+        n = m > 0 ? m : 1;
+    }
+    return n;
+}
+
+void launch_raster_fwd_multi(const RasterArgs *args, const WorkQueue *queues, const uint32_t *item_off, int n_jobs,
+                             uint32_t *counter, int tile_shift, int sms, cudaStream_t st)
+{
+    if (n_jobs <= 0) return;
+    ProfScope ps_("raster_fwd", st);
+    if (tile_shift == 5)
+        k_raster_fwd_multi<5><<<sms * fwd_multi_occupancy<5>(), RT, 0, st>>>(args, queues, item_off, n_jobs, counter);
+    else
+        k_raster_fwd_multi<4><<<sms * fwd_multi_occupancy<4>(), RT, 0, st>>>(args, queues, item_off, n_jobs, counter);
+    count_launch();
+}
+
+size_t raster_bwd_items(const RasterArgs &a)
+{
+    const int RH = 4 * BWD_NP;
+    const size_t regs = (size_t)(1 << (a.tile_shift - 4)) * (size_t)((1 << a.tile_shift) / RH);
+    return (size_t)a.tiles * regs * (size_t)a.S;
+}
+
+void launch_raster_bwd_multi(const RasterBwdArgs *jobs, const size_t *item_off, int n_jobs, size_t total_items,
+                             cudaStream_t st)
+{
+    if (n_jobs <= 0 || total_items == 0) return;
+    ProfScope ps_("raster_bwd", st);
+    k_raster_bwd_multi<<<(unsigned)((total_items + WARPS - 1) / WARPS), RT, 0, st>>>(jobs, item_off, n_jobs);
+    count_launch();
+}
+
 template <bool WRITE, bool MSE, bool LIST>
 static void query_t()
 {
@@ -942,6 +1074,8 @@ void raster_fwd_query_occupancy()
     query_t<true, false, false>();
     query_t<false, true, false>();
     query_t<false, true, true>();
+    fwd_multi_occupancy<4>();
+    fwd_multi_occupancy<5>();
     done = true;
 }
 

@@ -57,6 +57,11 @@ class States_t(ctypes.Structure):
                 ("n_states", ctypes.c_int32)]
 
 
+class SceneJob_t(ctypes.Structure):
+    _fields_ = [("scene", ctypes.POINTER(Scene_t)), ("states", States_t), ("cams", ctypes.POINTER(Camera_t)),
+                ("n_cams", ctypes.c_int32), ("bg", ctypes.c_float * 3), ("images", ctypes.c_void_p)]
+
+
 EXPORTS = ("dgs_create", "dgs_destroy", "dgs_last_error", "dgs_version", "dgs_render_state",
            "dgs_render_states_batched", "dgs_render_backward", "dgs_state_utility", "dgs_image_mse",
            "dgs_kernel_launches", "dgs_reset_kernel_launches", "dgs_profile_enable", "dgs_profile_read",
@@ -65,7 +70,8 @@ EXPORTS = ("dgs_create", "dgs_destroy", "dgs_last_error", "dgs_version", "dgs_re
            "dgs_plan_image_mse", "dgs_plan_status", "dgs_arena_create", "dgs_arena_destroy",
            "dgs_group_utility", "dgs_objective", "dgs_set_tile_reuse",
            "dgs_tile_reuse_stats", "dgs_set_tile_size", "dgs_set_memory_budget", "dgs_memory_stats",
-           "dgs_last_tile_size", "dgs_plan_tile_size", "dgs_plan_render_mse")
+           "dgs_last_tile_size", "dgs_plan_tile_size", "dgs_plan_render_mse",
+           "dgs_render_scenes_batched", "dgs_render_scenes_backward")
 OBJECTIVE_MAX_STATES = 16384
 UTILITY_MAX_CONTEXTS = 4096
 PLAN_RENDER, PLAN_UTILITY = 1, 2
@@ -90,6 +96,8 @@ def lib():
         L.dgs_render_state.argtypes = [P, ctypes.POINTER(Scene_t), P, F, ctypes.POINTER(Camera_t), P, P, P]
         L.dgs_render_states_batched.argtypes = [P, ctypes.POINTER(Scene_t), ctypes.POINTER(States_t),
                                                 P, I, P, P, P]
+        L.dgs_render_scenes_batched.argtypes = [P, ctypes.POINTER(SceneJob_t), I, P]
+        L.dgs_render_scenes_backward.argtypes = [P, ctypes.POINTER(SceneJob_t), I, P, P, P]
         L.dgs_render_backward.argtypes = [P, ctypes.POINTER(Scene_t), ctypes.POINTER(States_t), P, I, P, P, P,
                                           ctypes.POINTER(SceneGrad_t), P]
         L.dgs_state_utility.argtypes = [P, ctypes.POINTER(Scene_t), ctypes.POINTER(States_t), P, I, P, P, P, P]
@@ -351,6 +359,41 @@ class Renderer:
         self._check(self._lib.dgs_render_backward(self.h, ctypes.byref(sc), ctypes.byref(st), ca, len(cams), bgv,
                                                   _ptr(img), _ptr(dL_dimages.contiguous()), ctypes.byref(g),
                                                   _stream(stream)), "dgs_render_backward")
+        return grads
+
+    def _jobs(self, jobs):
+        """Marshal (scene, states, cams, bg, images) tuples; the keep list holds
+        every ctypes object the job array points into."""
+        arr = (SceneJob_t * len(jobs))()
+        keep = []
+        for k, (scene, states, cams, bg, images) in enumerate(jobs):
+            sc, ca = scene.struct(), camera_array(cams)
+            keep += [sc, ca]
+            arr[k].scene = ctypes.pointer(sc)
+            arr[k].states = states.struct()
+            arr[k].cams = ctypes.cast(ca, ctypes.POINTER(Camera_t))
+            arr[k].n_cams = len(cams)
+            for c in range(3):
+                arr[k].bg[c] = float(bg[c])
+            arr[k].images = _ptr(images)
+        return arr, keep
+
+    def render_scenes_batched(self, jobs, stream=None):
+        """dgs_render_scenes_batched: jobs = [(scene, states, cams, bg, images)];
+        every scene's states rendered into its images with one raster launch."""
+        arr, keep = self._jobs(jobs)
+        self._check(self._lib.dgs_render_scenes_batched(self.h, arr, len(jobs), _stream(stream)),
+                    "dgs_render_scenes_batched")
+        return [j[4] for j in jobs]
+
+    def render_scenes_backward(self, jobs, dL_dimages, grads, stream=None):
+        """dgs_render_scenes_backward: adjoint of the last render_scenes_batched of
+        these jobs; grads (one dict per job) accumulate."""
+        arr, keep = self._jobs(jobs)
+        dl = (ctypes.c_void_p * len(jobs))(*[_ptr(d.contiguous()) for d in dL_dimages])
+        gs = (SceneGrad_t * len(jobs))(*[_grad_struct(g) for g in grads])
+        self._check(self._lib.dgs_render_scenes_backward(self.h, arr, len(jobs), dl, gs, _stream(stream)),
+                    "dgs_render_scenes_backward")
         return grads
 
     def set_tile_reuse(self, enable: bool):

@@ -237,3 +237,41 @@ def test_arena_plans_of_several_scenes_in_one_graph(R, torch):
     for c in cases:
         c["plan"].close()
     arena.close()
+
+
+def test_scenes_batched_one_launch_equals_per_scene_calls(R, torch):
+    """dgs_render_scenes_batched over three serving-mix scenes of different sizes
+    and resolutions: every image equals dgs_render_states_batched of its scene,
+    bit for bit; dgs_render_scenes_backward gives the per-scene gradients up to
+    float atomic order; masks changed in place after the forward are refused."""
+    specs = synth.mix_specs(scale=0.02)
+    cases = []
+    for spec in (specs[0], specs[1], specs[2]):
+        w, sc, st, ridx, targets = _mix_case(torch, R, spec, 10)
+        S, H, W = st.n, w.cams[0].height, w.cams[0].width
+        cases.append(dict(w=w, sc=sc, st=st, images=torch.full((S, H, W, 3), 9.0, device="cuda")))
+    assert len({(c["w"].cams[0].width, c["w"].cams[0].height) for c in cases}) >= 2
+    jobs = [(c["sc"], c["st"], c["w"].cams, c["w"].bg, c["images"]) for c in cases]
+    R.set_tile_size(32)
+    try:
+        R.render_scenes_batched(jobs)
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(5)
+        dls = [torch.from_numpy(rng.normal(size=tuple(c["images"].shape)).astype(np.float32)).cuda() for c in cases]
+        grads = [c["sc"].zeros_like_grads() for c in cases]
+        R.render_scenes_backward(jobs, dls, grads)
+        torch.cuda.synchronize()
+        for c, dl, g in zip(cases, dls, grads):
+            ref = R.render_states_batched(c["sc"], c["st"], c["w"].cams, c["w"].bg)
+            assert torch.equal(c["images"], ref)
+            g_ref = R.render_backward(c["sc"], c["st"], c["w"].cams, c["w"].bg, dl, images=ref)
+            for k in dgs.SCENE_FIELDS:
+                if g_ref[k].numel():
+                    assert torch.allclose(g[k], g_ref[k], rtol=1e-4, atol=1e-5 * float(g_ref[k].abs().max()) + 1e-12), k
+        # a second call reuses the scene workspaces; masks edited in place after it are refused
+        R.render_scenes_batched(jobs)
+        cases[1]["st"].masks.copy_(_masks(torch, cases[1]["w"], 11))
+        with pytest.raises(RuntimeError, match="STALE"):
+            R.render_scenes_backward(jobs, dls, [c["sc"].zeros_like_grads() for c in cases])
+    finally:
+        R.set_tile_size(0)

@@ -1153,7 +1153,7 @@ int dgs_render_backward(dgs_ctx *ctx, const dgs_scene *scene, const dgs_states *
         b.dL_dimg = dL_s;
         b.img_fwd = img_s;
         b.rec_grad = (float4 *)ctx->recgrad.p;
-        launch_raster_bwd(b, st);
+        launch_raster_bwd(b, ctx->sms, st);
         return project_backward(ctx, scene, p, L, grads, st);
     };
     return chunked(ctx, states, (scene->n_clusters * scene->n_layers + 31) / 32, 0, st, pass);
@@ -2082,7 +2082,7 @@ int dgs_plan_backward(dgs_plan *P, const float *images, const float *dL_dimages,
     b.dL_dimg = dL_dimages;
     b.img_fwd = images;
     b.rec_grad = (float4 *)ctx->recgrad.p;
-    launch_raster_bwd(b, st);
+    launch_raster_bwd(b, ctx->sms, st);
     GradDev g;
     g.mu0 = grads->mu0; g.u = grads->u; g.ls = grads->log_scale; g.quat = grads->quat;
     g.logit = grads->opacity_logit; g.colour = grads->colour; g.res = grads->res;

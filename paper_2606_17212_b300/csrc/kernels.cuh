@@ -84,7 +84,7 @@ struct RasterBwdArgs {
     float4 *rec_grad;             // [nRec][3] pixel moments of dL/dpower (d = m - pixel centre) and colour:
                                   // (S dx, S dy, S dx^2, S dx dy), (S dy^2, S 1, dL/dr, dL/dg), (dL/db, -, -, -)
 };
-void launch_raster_bwd(const RasterBwdArgs &a, cudaStream_t st);
+void launch_raster_bwd(const RasterBwdArgs &a, int sms, cudaStream_t st);
 // Several scenes in one launch (device arrays of per-job arguments).  Forward:
 // queues[k] as launch_raster_fwd's, job k's items [item_off[k], item_off[k + 1])
 // of one shared zeroed counter, every job with images, no MSE, tile shift

@@ -1,12 +1,11 @@
 // Tile rasterization of delivery states: forward compositing with an optional
 // fused FP64 squared-error epilogue, and the adjoint compositing kernel.
 //
-// In the forward one warp renders one 16x16 tile of one state: lane l owns
-// column l & 15 of the tile and its rows 8 (l >> 4) .. 8 (l >> 4) + 7, held as
-// four vertical pixel pairs in packed FP32x2 registers, so every per-pixel
-// FP32 operation of a pair issues once.  The adjoint gives each warp one 16x8
-// half of a tile (two pairs per lane), which needs fewer registers and keeps
-// more warps resident.  A warp walks the tile's run of the batch-wide
+// One warp renders one 16x16 region of a sort tile for one state: lane l owns
+// column l & 15 of the region and its rows 8 (l >> 4) .. 8 (l >> 4) + 7, held
+// as four vertical pixel pairs in packed FP32x2 registers, so every per-pixel
+// FP32 operation of a pair issues once; the forward and the adjoint use the
+// same regions.  A warp walks the tile's run of the batch-wide
 // sorted entry list, which holds every depth variant any state of the view
 // group needs, in chunks of 32 entries: it keeps the variants this state
 // renders (variant depth == the state's delivered depth of the Gaussian's
@@ -36,13 +35,18 @@ constexpr int QCAP = 64;              // per-warp queue of staged entries (ring,
 constexpr int CHUNK = 32;             // run entries examined per staging step (one per lane)
 constexpr int NPAIR = 4;              // vertical pixel pairs per lane in the forward (8 rows: a warp per tile)
 // Resident blocks per SM.  Measured on the training workload (250k Gaussians,
-// 64 states, 512x512): the forward at 4 (121 registers, no spills) beats 5
-// (96 registers, spills); the adjoint is latency bound, and 16 x 8 regions at
-// 6 blocks (80 registers) beat 16 x 16 regions at 3 blocks (146 registers;
-// 4.52 vs 5.45 ms) and 16 x 4 regions at 8 blocks (5.73 ms).
+// 64 states, 512x512, 32 px tiles): the forward at 4 (117-124 registers) beats
+// 5 (96 registers); the adjoint's 16 x 16 regions (4 pixel pairs per lane) at
+// 4 blocks (128 registers, no spills) beat 16 x 8 regions (2 pairs) at 6
+// blocks (80 registers; 3.97 vs 4.08 ms), which beat 5, 7 or 8 blocks: the
+// per-entry warp reduction is shared by twice as many pixels.  A call with
+// too few (region, state) items to fill the GPU twice (a single state) takes
+// the 16 x 8 regions, which give twice the warps.
 constexpr int FWD_MIN_BLOCKS = 4;
-constexpr int BWD_MIN_BLOCKS = 6;
-constexpr int BWD_NP = 2;             // pixel pairs per lane in the adjoint (a warp per 16 x 4 NP region)
+template <int NP> struct BwdShape;    // pixel pairs per lane in the adjoint (a warp per 16 x 4 NP region)
+template <> struct BwdShape<4> { static constexpr int MIN_BLOCKS = 4; };
+template <> struct BwdShape<2> { static constexpr int MIN_BLOCKS = 6; };
+constexpr int BWD_NP_BATCH = 4, BWD_NP_FEW = 2;
 constexpr uint32_t FULL = 0xffffffffu;
 constexpr float T_STOP = 1e-4f;       // a pixel stops before the entry that would bring T below this
 constexpr float A_MAX = 0.99f;        // opacity clamp
@@ -766,27 +770,27 @@ struct BwdLane {
     }
 };
 
-// Adjoint compositing, one warp per (16x8 half tile, state).  Transmittance is never
+// Adjoint compositing, one warp per (16x16 region, state).  Transmittance is never
 // stored: the walk goes front to back recomputing it, and for each included k
 //   dC/drgb_k   = alpha_k T_k
 //   dC/dalpha_k = rgb_k T_k - (C_after_k + T_final bg) / (1 - alpha_k)
 // with C_after_k = C_final - (colour accumulated up to and including k).  The
 // final pixel value is read from the forward's image (IMG) or recomputed by a
-// first forward walk.  Per-Gaussian pixel moments: four pixels per lane, a
+// first forward walk.  Per-Gaussian pixel moments: eight pixels per lane, a
 // warp transpose reduction, one atomic add per moment.
-// Work items of the adjoint raster of one call: (tile, 16x8 region, state).
-__device__ __forceinline__ size_t bwd_items(const RasterArgs &a)
+// Work items of the adjoint raster of one call: (tile, 16x16 region, state).
+__host__ __device__ __forceinline__ size_t bwd_items(const RasterArgs &a, int np)
 {
-    const int RH = 4 * BWD_NP;
+    const int RH = 4 * np;
     const int regs = (1 << (a.tile_shift - 4)) * ((1 << a.tile_shift) / RH);
     return (size_t)a.tiles * regs * a.S;
 }
 
 // One adjoint work item (every lane of the warp calls it with the same item < bwd_items).
-template <bool IMG>
+template <bool IMG, int NP>
 __device__ __forceinline__ void bwd_item(const RasterBwdArgs &b, size_t item, WarpSmem &sm)
 {
-    constexpr int NP = BWD_NP, RH = 4 * BWD_NP;     // pairs per lane, region height
+    constexpr int RH = 4 * NP;     // region height (NP pixel pairs per lane)
     const RasterArgs &a = b.f;
     const int rpx = 1 << (a.tile_shift - 4), rpy = (1 << a.tile_shift) / RH, regs = rpx * rpy;
     const int s = (int)(item % (unsigned)a.S);
@@ -846,19 +850,19 @@ __device__ __forceinline__ void bwd_item(const RasterBwdArgs &b, size_t item, Wa
     walk(a, L, sm, rg.x, rg.y, B);
 }
 
-template <bool IMG>
-__global__ void __launch_bounds__(RT, BWD_MIN_BLOCKS) k_raster_bwd(RasterBwdArgs b)
+template <bool IMG, int NP>
+__global__ void __launch_bounds__(RT, BwdShape<NP>::MIN_BLOCKS) k_raster_bwd(RasterBwdArgs b)
 {
     __shared__ WarpSmem smem[WARPS];
     const int w = threadIdx.x >> 5;
     const size_t item = (size_t)blockIdx.x * WARPS + w;
-    if (item >= bwd_items(b.f)) return;
-    bwd_item<IMG>(b, item, smem[w]);
+    if (item >= bwd_items(b.f, NP)) return;
+    bwd_item<IMG, NP>(b, item, smem[w]);
 }
 
 // The adjoint raster of several scenes in one launch: warp g takes item
 // g - item_off[k] of job k, the last job with item_off[k] <= g.
-__global__ void __launch_bounds__(RT, BWD_MIN_BLOCKS) k_raster_bwd_multi(const RasterBwdArgs *__restrict__ jobs,
+__global__ void __launch_bounds__(RT, BwdShape<BWD_NP_BATCH>::MIN_BLOCKS) k_raster_bwd_multi(const RasterBwdArgs *__restrict__ jobs,
                                                                          const size_t *__restrict__ item_off,
                                                                          int n_jobs)
 {
@@ -874,7 +878,7 @@ __global__ void __launch_bounds__(RT, BWD_MIN_BLOCKS) k_raster_bwd_multi(const R
     }
     copy_words(&jargs[w], &jobs[lo], sizeof(RasterBwdArgs), threadIdx.x & 31);
     __syncwarp();
-    bwd_item<true>(jargs[w], g - item_off[lo], smem[w]);
+    bwd_item<true, BWD_NP_BATCH>(jargs[w], g - item_off[lo], smem[w]);
 }
 
 // Cost key of each (view group, tile), 16 bits: ascending key = descending
@@ -1031,7 +1035,7 @@ void launch_raster_fwd_multi(const RasterArgs *args, const WorkQueue *queues, co
 
 size_t raster_bwd_items(const RasterArgs &a)
 {
-    const int RH = 4 * BWD_NP;
+    const int RH = 4 * BWD_NP_BATCH;
     const size_t regs = (size_t)(1 << (a.tile_shift - 4)) * (size_t)((1 << a.tile_shift) / RH);
     return (size_t)a.tiles * regs * (size_t)a.S;
 }
@@ -1100,16 +1104,23 @@ void launch_item_counts(const uint32_t *tile_order, uint32_t n, uint32_t tiles, 
     count_launch();
 }
 
-// One warp per (tile, state), WARPS warps per block.
-void launch_raster_bwd(const RasterBwdArgs &b, cudaStream_t st)
+// One warp per (region, state), WARPS warps per block; the region height by
+// the item count (see BwdShape).
+void launch_raster_bwd(const RasterBwdArgs &b, int sms, cudaStream_t st)
 {
     if (b.f.S == 0 || b.f.tiles == 0) return;
-    const int regs = (1 << (b.f.tile_shift - 4)) * ((1 << b.f.tile_shift) / (4 * BWD_NP));
-    const size_t items = (size_t)b.f.tiles * regs * (size_t)b.f.S;
+    const size_t big = bwd_items(b.f, BWD_NP_BATCH);
+    const bool batch = big >= (size_t)2 * sms * BwdShape<BWD_NP_BATCH>::MIN_BLOCKS * WARPS;
+    const size_t items = batch ? big : bwd_items(b.f, BWD_NP_FEW);
     const unsigned grid = (unsigned)((items + WARPS - 1) / WARPS);
     ProfScope ps_(b.img_fwd ? "raster_bwd" : "raster_bwd_2pass", st);
-    if (b.img_fwd) k_raster_bwd<true><<<grid, RT, 0, st>>>(b);
-    else k_raster_bwd<false><<<grid, RT, 0, st>>>(b);
+    if (batch) {
+        if (b.img_fwd) k_raster_bwd<true, BWD_NP_BATCH><<<grid, RT, 0, st>>>(b);
+        else k_raster_bwd<false, BWD_NP_BATCH><<<grid, RT, 0, st>>>(b);
+    } else {
+        if (b.img_fwd) k_raster_bwd<true, BWD_NP_FEW><<<grid, RT, 0, st>>>(b);
+        else k_raster_bwd<false, BWD_NP_FEW><<<grid, RT, 0, st>>>(b);
+    }
     count_launch();
 }
 

@@ -45,8 +45,8 @@ MUFU_EX2_PER_SM_CLK = 32
 # kernel source it was taken on (sha1 of csrc/raster.cu), the workload at full size
 # and the sort tile side in pixels.
 MEASURED_TRAFFIC = {
-    ("raster_bwd", "c3_fwdbwd_250k", 32): (792_823_552 + 68_212_736, "e78495e7392f2ee621f361681e24618324a50084"),
-    ("raster_fwd", "c3_fwdbwd_250k", 32): (440_540_416 + 182_958_592, "e78495e7392f2ee621f361681e24618324a50084"),
+    ("raster_bwd", "c3_fwdbwd_250k", 32): (783_723_776 + 66_997_504, "acfc1cf6c25d61a7c8702e98da24e74a02c6c591"),
+    ("raster_fwd", "c3_fwdbwd_250k", 32): (441_528_064 + 182_790_400, "acfc1cf6c25d61a7c8702e98da24e74a02c6c591"),
 }
 
 
@@ -970,7 +970,8 @@ def run_others(args):
         try:
             line = run_mix(a2) if name == "c5_mix_48" else run_main(a2, synth.config(name))
             keep = ("value", "unit", "ms_per_step", "mpix_per_s", "plain_per_state", "batched_vs_plain",
-                    "tile_reuse", "gpu_launches", "clocks", "e2e", "eager_per_step", "graph_per_step")
+                    "tile_reuse", "gpu_launches", "clocks", "e2e", "eager_per_step", "graph_per_step",
+                    "scene_waves_per_step")
             summ = {k: line.get(k) for k in keep if line.get(k) is not None}
             summ["config"] = line["config"]
             summ["steps"], summ["warmup"] = a2.steps, a2.warmup

@@ -79,7 +79,19 @@ __global__ void __launch_bounds__(128, SH == 0 ? 4 : 1) k_project_bwd(SceneDev s
             Attr<SH> a;
             // view groups holding a record of (this Gaussian, depth d), in order; the
             // next record's gradient is loaded while the current one is processed
+            // with at most 64 view groups, the view groups holding depth d are read
+            // into a mask first (independent loads), then walked bit by bit
+            uint64_t vmask = 0;
+            if (V <= 64) {
+#pragma unroll 8
+                for (int v = 0; v < V; ++v)
+                    vmask |= (uint64_t)((__ldg(need + (size_t)v * s.C + c) >> d) & 1u) << v;
+            }
             auto next_vg = [&](int v) {
+                if (V <= 64) {
+                    const uint64_t rest = v >= 64 ? 0ull : vmask >> v;
+                    return rest ? v + __ffsll((long long)rest) - 1 : V;
+                }
                 while (v < V && !(((need[(size_t)v * s.C + c] & ~1u) >> d) & 1u)) ++v;
                 return v;
             };

@@ -279,7 +279,9 @@ void launch_tile_count(const Rec *recs, const uint32_t *order, uint32_t n, int t
 {
     if (n == 0) return;
     ProfScope ps_("tile_count", st);
-    k_tile_count<<<grid_for(n, 256, sms), 256, 0, st>>>(recs, order, n, n_dev, tiles_x, tiles, tile_shift, counts,
+    // four times the usual grid cap: more warps keep more of the dependent
+    // (slot, record) gathers in flight (0.152 -> 0.128 ms on the training step)
+    k_tile_count<<<grid_for(n, 256, sms * 4), 256, 0, st>>>(recs, order, n, n_dev, tiles_x, tiles, tile_shift, counts,
                                                         bins);
     count_launch();
 }

@@ -755,7 +755,7 @@ def run_main(args, w):
     # ---- graph path (training): a capture-safe plan, the whole step captured
     # once in a CUDA graph and replayed (masks live in a static device buffer)
     graph_ms = None
-    if training and args.loss == "mse":     # the Eq. 2 objective call is not capture-safe
+    if training:
         plan = dgs.Plan(R, scene, states, w.cams, w.bg, dgs.PLAN_RENDER, ref_index=ref_index,
                         n_refs=len(views), entry_headroom=args.entry_headroom)
         graph_tile = plan.tile_size()
@@ -763,11 +763,17 @@ def run_main(args, w):
         g_mse = torch.empty(S, dtype=torch.float64, device=dev)
         g_psnr = torch.empty_like(g_mse)
         g_dL = torch.empty_like(images)
+        if args.loss == "eq2":
+            plan.set_objective()
+            g_loss = torch.empty(1, dtype=torch.float64, device=dev)
 
         def plan_step():
             grad_flat.zero_()
             plan.render(g_masks, images)
-            plan.image_mse(images, targets, g_mse, g_psnr, g_dL, weight=loss_w)
+            if args.loss == "eq2":
+                plan.objective(images, targets, g_loss, g_mse, g_dL)
+            else:
+                plan.image_mse(images, targets, g_mse, g_psnr, g_dL, weight=loss_w)
             plan.backward(g_dL, grads, images=images)
 
         side = torch.cuda.Stream()

@@ -457,6 +457,22 @@ DGS_API int dgs_plan_image_mse(dgs_plan *plan, const float *images, const float 
 DGS_API int dgs_plan_tile_size(const dgs_plan *plan, int32_t *tile_px);
 DGS_API int dgs_plan_status(dgs_plan *plan, int64_t *n_records, int64_t *n_entries, dgs_stream stream);
 
+/* The Eq. 2 objective of dgs_objective for a plan made with ref_index, in
+ * two steps so that the per-step call can be captured in a CUDA graph.
+ * dgs_plan_set_objective (not during a capture) fixes the pair and anchor
+ * lists [host] (as dgs_objective's, states of the plan) and the weights
+ * (NULL: the paper's), validates them, allocates the plan's objective
+ * buffers and uploads the tables.  dgs_plan_objective then only launches
+ * kernels: images, refs [device] as dgs_objective's; loss [device] [1],
+ * D [device] [n_states] or NULL, dL_dimages [device] or NULL; the same bits
+ * as dgs_objective with the same arguments.  Returns DGS_E_INVALID_ARG when
+ * the objective was not set. */
+DGS_API int dgs_plan_set_objective(dgs_plan *plan, const int32_t *pairs_t, int n_pairs_t, const int32_t *pairs_m,
+                                   int n_pairs_m, const int32_t *anchors, int n_anchors,
+                                   const dgs_objective_params *params);
+DGS_API int dgs_plan_objective(dgs_plan *plan, const float *images, const float *refs, double *loss, double *D,
+                               float *dL_dimages, dgs_stream stream);
+
 /*
  * Test and inspection access to the projected records and tile lists of the
  * context's last dgs_render_states_batched / dgs_render_state call (or of a

@@ -792,6 +792,12 @@ struct dgs_plan {
     bool rendered = false;
     int n_refs = 0;
     int image_parts = 0;
+    // Eq. 2 objective fixed by dgs_plan_set_objective: pair, anchor and
+    // temporal-neighbour tables in ws.oints at these offsets (ints)
+    bool obj = false;
+    int obj_nt = 0, obj_nm = 0, obj_na = 0;
+    size_t obj_pt = 0, obj_pm = 0, obj_tl = 0, obj_an = 0, obj_to = 0;
+    dgs_objective_params obj_prm{};
 };
 
 namespace {
@@ -2133,6 +2139,103 @@ int dgs_plan_image_mse(dgs_plan *P, const float *images, const float *refs, floa
                      (double *)ctx->partial.p, P->image_parts, dL_dimages, st);
     launch_mse_reduce((const double *)ctx->partial.p, P->p.S_user, P->image_parts,
                       1.0 / (double)((size_t)P->p.W * P->p.H * 3), mse, psnr, st);
+    CK(cudaGetLastError());
+    return DGS_OK;
+}
+
+int dgs_plan_set_objective(dgs_plan *P, const int32_t *pairs_t, int n_pairs_t, const int32_t *pairs_m,
+                           int n_pairs_m, const int32_t *anchors, int n_anchors, const dgs_objective_params *params)
+{
+    if (!P) return DGS_E_INVALID_ARG;
+    if (P->n_refs < 1) return plan_fail(P, DGS_E_INVALID_ARG, "plan was made without ref_index");
+    const int S = P->p.S_user;
+    if (S < 1 || S > DGS_OBJECTIVE_MAX_STATES || n_pairs_t < 0 || n_pairs_m < 0 || n_anchors < 0)
+        return plan_fail(P, DGS_E_INVALID_ARG, "bad sizes");
+    if ((n_pairs_t && !pairs_t) || (n_pairs_m && !pairs_m) || (n_anchors && !anchors))
+        return plan_fail(P, DGS_E_INVALID_ARG, "null pair or anchor list");
+    for (int q = 0; q < 2 * n_pairs_t; ++q)
+        if (pairs_t[q] < 0 || pairs_t[q] >= S) return plan_fail(P, DGS_E_INVALID_ARG, "temporal pair out of range");
+    for (int q = 0; q < 2 * n_pairs_m; ++q)
+        if (pairs_m[q] < 0 || pairs_m[q] >= S) return plan_fail(P, DGS_E_INVALID_ARG, "prefix pair out of range");
+    for (int a = 0; a < n_anchors; ++a)
+        if (anchors[a] < 0 || anchors[a] >= S) return plan_fail(P, DGS_E_INVALID_ARG, "anchor out of range");
+    dgs_objective_params prm = {0.20, 0.30, 0.05, 0.10, 2.0, 0.50};
+    if (params) prm = *params;
+    if (!(prm.cvar_q >= 0.0 && prm.cvar_q <= 1.0)) return plan_fail(P, DGS_E_INVALID_ARG, "cvar_q outside [0, 1]");
+    dgs_ctx *ctx = &P->ws, *own = ctx;   // (CK reports through ctx)
+    CK(cudaSetDevice(own->device));
+    // temporal neighbour lists as dgs_objective builds them
+    std::vector<int32_t> toff(S + 1, 0), tl(4 * (size_t)n_pairs_t);
+    for (int q = 0; q < n_pairs_t; ++q) { ++toff[pairs_t[2 * q] + 1]; ++toff[pairs_t[2 * q + 1] + 1]; }
+    for (int s = 0; s < S; ++s) toff[s + 1] += toff[s];
+    {
+        std::vector<int32_t> fill(toff.begin(), toff.end() - 1);
+        for (int q = 0; q < n_pairs_t; ++q) {
+            const int i = pairs_t[2 * q], j = pairs_t[2 * q + 1];
+            tl[2 * fill[i]] = j; tl[2 * fill[i] + 1] = -1; ++fill[i];
+            tl[2 * fill[j]] = i; tl[2 * fill[j] + 1] = +1; ++fill[j];
+        }
+    }
+    const size_t o_pt = 0, o_pm = o_pt + 2 * (size_t)n_pairs_t, o_tl = o_pm + 2 * (size_t)n_pairs_m;
+    const size_t o_an = o_tl + tl.size(), o_to = o_an + n_anchors, n_ints = o_to + S + 1;
+    std::vector<int32_t> h(n_ints);
+    if (n_pairs_t) std::memcpy(h.data() + o_pt, pairs_t, 8 * (size_t)n_pairs_t);
+    if (n_pairs_m) std::memcpy(h.data() + o_pm, pairs_m, 8 * (size_t)n_pairs_m);
+    if (!tl.empty()) std::memcpy(h.data() + o_tl, tl.data(), 4 * tl.size());
+    if (n_anchors) std::memcpy(h.data() + o_an, anchors, 4 * (size_t)n_anchors);
+    std::memcpy(h.data() + o_to, toff.data(), 4 * (size_t)(S + 1));
+    const size_t npix = (size_t)P->p.H * P->p.W;
+    int tx;
+    const int nt = objective_tiles(P->p.H, P->p.W, &tx);
+    const int chunks = (int)((npix + 1023) / 1024);
+    int r;
+    if ((r = ensure(own, own->oints, 4 * n_ints + 16, 0)) != DGS_OK ||
+        (r = ensure(own, own->omaps, sizeof(float) * 3 * (size_t)S * 3 * npix, 0)) != DGS_OK ||
+        (r = ensure(own, own->opart, sizeof(double) * 2 * (size_t)S * nt, 0)) != DGS_OK ||
+        (r = ensure(own, own->otpart, sizeof(double) * (size_t)(n_pairs_t > 0 ? n_pairs_t : 1) * chunks, 0)) != DGS_OK ||
+        (r = ensure(own, own->oD, sizeof(double) * (size_t)S, 0)) != DGS_OK ||
+        (r = ensure(own, own->oweight, sizeof(double) * (size_t)S, 0)) != DGS_OK)
+        return plan_fail(P, r, own->err.c_str());
+    CK(cudaMemcpy(own->oints.p, h.data(), 4 * n_ints, cudaMemcpyHostToDevice));
+    if (objective_prepare() != 0) return plan_fail(P, DGS_E_CUDA, "objective kernel attribute");
+    P->obj = true;
+    P->obj_nt = n_pairs_t; P->obj_nm = n_pairs_m; P->obj_na = n_anchors;
+    P->obj_pt = o_pt; P->obj_pm = o_pm; P->obj_tl = o_tl; P->obj_an = o_an; P->obj_to = o_to;
+    P->obj_prm = prm;
+    return DGS_OK;
+}
+
+int dgs_plan_objective(dgs_plan *P, const float *images, const float *refs, double *loss, double *D,
+                       float *dL_dimages, dgs_stream stream)
+{
+    if (!P) return DGS_E_INVALID_ARG;
+    if (!P->obj) return plan_fail(P, DGS_E_INVALID_ARG, "dgs_plan_set_objective was not called");
+    if (!images || !refs || !loss) return plan_fail(P, DGS_E_INVALID_ARG, "null argument");
+    dgs_ctx *ctx = &P->ws, *own = ctx;   // (CK reports through ctx)
+    CK(cudaSetDevice(own->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int S = P->p.S_user, H = P->p.H, W = P->p.W;
+    const size_t npix = (size_t)H * W;
+    int tx;
+    const int nt = objective_tiles(H, W, &tx);
+    const int chunks = (int)((npix + 1023) / 1024);
+    const int32_t *d = (const int32_t *)own->oints.p;
+    const int32_t *ridx = (const int32_t *)own->refidx.p;
+    float *maps = (float *)own->omaps.p;
+    const size_t plane = (size_t)S * 3 * npix;
+    launch_ssim_fwd(images, refs, ridx, S, H, W, maps, maps + plane, maps + 2 * plane, (double *)own->opart.p, st);
+    launch_temporal(images, refs, ridx, (const int2 *)(d + P->obj_pt), P->obj_nt, H, W, (double *)own->otpart.p,
+                    chunks, st);
+    double *Dout = D ? D : (double *)own->oD.p;
+    if (launch_objective((const double *)own->opart.p, nt, (const double *)own->otpart.p, chunks, P->obj_nt,
+                         (const int2 *)(d + P->obj_pm), P->obj_nm, d + P->obj_an, P->obj_na, S,
+                         1.0 / (double)(npix * 3), P->obj_prm, Dout, (double *)own->oweight.p, loss, st) != 0)
+        return plan_fail(P, DGS_E_CUDA, "objective kernel attribute");
+    if (dL_dimages)
+        launch_objective_grad(images, refs, ridx, S, H, W, maps, maps + plane, maps + 2 * plane,
+                              (const double *)own->oweight.p, (float)P->obj_prm.ssim_weight,
+                              P->obj_nt ? (float)(P->obj_prm.lambda_t / (double)P->obj_nt) : 0.0f, d + P->obj_to,
+                              (const int2 *)(d + P->obj_tl), dL_dimages, st);
     CK(cudaGetLastError());
     return DGS_OK;
 }

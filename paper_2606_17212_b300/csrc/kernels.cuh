@@ -116,6 +116,7 @@ void launch_ssim_fwd(const float *images, const float *refs, const int32_t *ref_
                      float *d_mx, float *d_exx, float *d_exy, double *part, cudaStream_t st);
 void launch_temporal(const float *images, const float *refs, const int32_t *ref_index, const int2 *pairs,
                      int n_pairs, int H, int W, double *tpart, int chunks, cudaStream_t st);
+int objective_prepare();   // 0 on success
 int launch_objective(const double *part, int n_tiles, const double *tpart, int chunks, int n_t, const int2 *pm,
                      int n_m, const int32_t *anchors, int n_a, int S, double inv_vals, const ObjectiveParams &prm,
                      double *D, double *weight, double *loss, cudaStream_t st);

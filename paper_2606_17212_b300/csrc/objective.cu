@@ -378,11 +378,10 @@ size_t objective_smem(int S)
     return (size_t)P * (sizeof(double) + sizeof(int));
 }
 
-int launch_objective(const double *part, int n_tiles, const double *tpart, int chunks, int n_t, const int2 *pm,
-                     int n_m, const int32_t *anchors, int n_a, int S, double inv_vals, const ObjectiveParams &prm,
-                     double *D, double *weight, double *loss, cudaStream_t st)
+// The objective kernel's dynamic shared-memory limit, set once (before any
+// stream capture that launches it).
+int objective_prepare()
 {
-    const size_t smem = objective_smem(S);
     static bool attr = false;
     if (!attr) {
         if (cudaFuncSetAttribute(k_objective, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
@@ -390,6 +389,15 @@ int launch_objective(const double *part, int n_tiles, const double *tpart, int c
             return -1;
         attr = true;
     }
+    return 0;
+}
+
+int launch_objective(const double *part, int n_tiles, const double *tpart, int chunks, int n_t, const int2 *pm,
+                     int n_m, const int32_t *anchors, int n_a, int S, double inv_vals, const ObjectiveParams &prm,
+                     double *D, double *weight, double *loss, cudaStream_t st)
+{
+    const size_t smem = objective_smem(S);
+    if (objective_prepare() != 0) return -1;
     ProfScope ps_("objective", st);
     k_objective<<<1, 1024, smem, st>>>(part, n_tiles, tpart, chunks, n_t, pm, n_m, anchors, n_a, S, inv_vals, prm,
                                         D, weight, loss);

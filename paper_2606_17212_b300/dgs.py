@@ -71,7 +71,8 @@ EXPORTS = ("dgs_create", "dgs_destroy", "dgs_last_error", "dgs_version", "dgs_re
            "dgs_group_utility", "dgs_objective", "dgs_set_tile_reuse",
            "dgs_tile_reuse_stats", "dgs_set_tile_size", "dgs_set_memory_budget", "dgs_memory_stats",
            "dgs_last_tile_size", "dgs_plan_tile_size", "dgs_plan_render_mse",
-           "dgs_render_scenes_batched", "dgs_render_scenes_backward")
+           "dgs_render_scenes_batched", "dgs_render_scenes_backward", "dgs_plan_set_objective",
+           "dgs_plan_objective")
 OBJECTIVE_MAX_STATES = 16384
 UTILITY_MAX_CONTEXTS = 4096
 PLAN_RENDER, PLAN_UTILITY = 1, 2
@@ -140,6 +141,8 @@ def lib():
         L.dgs_plan_utility.argtypes = [P, P, P, P, P]
         L.dgs_plan_image_mse.argtypes = [P, P, P, F, P, P, P, P]
         L.dgs_plan_render_mse.argtypes = [P, P, P, P, F, P, P, P, P]
+        L.dgs_plan_set_objective.argtypes = [P, P, I, P, I, P, I, ctypes.POINTER(ObjectiveParams_t)]
+        L.dgs_plan_objective.argtypes = [P, P, P, P, P, P, P]
         L.dgs_plan_status.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), P]
         _lib = L
     return _lib
@@ -664,6 +667,28 @@ class Plan:
         self._check(self._lib.dgs_plan_image_mse(self.h, _ptr(images), _ptr(refs), float(weight), _ptr(mse),
                                                  _ptr(psnr), _ptr(dL), _stream(stream)), "dgs_plan_image_mse")
         return mse, psnr, dL
+
+    def set_objective(self, pairs_t=(), pairs_m=(), anchors=(), params=None):
+        """dgs_plan_set_objective: fix the Eq. 2 pair and anchor lists and weights
+        (as Renderer.objective's) for later capture-safe objective calls."""
+        pt = np.ascontiguousarray(np.asarray(pairs_t, np.int32).reshape(-1, 2))
+        pm = np.ascontiguousarray(np.asarray(pairs_m, np.int32).reshape(-1, 2))
+        an = np.ascontiguousarray(np.asarray(anchors, np.int32).reshape(-1))
+        prm = None
+        if params is not None:
+            v = dict(OBJECTIVE_DEFAULTS, **params)
+            prm = ObjectiveParams_t(*[float(v[k]) for k in OBJECTIVE_KEYS])
+        vp = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a.size else None
+        self._check(self._lib.dgs_plan_set_objective(self.h, vp(pt), pt.shape[0], vp(pm), pm.shape[0], vp(an),
+                                                     an.size, None if prm is None else ctypes.byref(prm)),
+                    "dgs_plan_set_objective")
+
+    def objective(self, images, refs, loss, D=None, dL=None, stream=None):
+        """dgs_plan_objective: Eq. 2 loss [1] f64, per-state D [S] f64 (or None)
+        and dL/dimages (or None) into the given device tensors; kernels only."""
+        self._check(self._lib.dgs_plan_objective(self.h, _ptr(images), _ptr(refs), _ptr(loss), _ptr(D), _ptr(dL),
+                                                 _stream(stream)), "dgs_plan_objective")
+        return loss, D, dL
 
     def tile_size(self) -> int:
         """dgs_plan_tile_size: sort tile side (px) fixed at creation."""

@@ -275,3 +275,69 @@ def test_scenes_batched_one_launch_equals_per_scene_calls(R, torch):
             R.render_scenes_backward(jobs, dls, [c["sc"].zeros_like_grads() for c in cases])
     finally:
         R.set_tile_size(0)
+
+
+def test_plan_objective_training_step_in_one_graph(R, torch):
+    """Render, the Eq. 2 objective (with its image gradient) and the adjoint,
+    all through one plan, captured in one CUDA graph: the loss, D and dL/dI
+    carry the bits of the context calls, and the replayed step with new masks
+    equals the context calls on those masks."""
+    w = synth.config("c3_fwdbwd_250k", scale=0.05, n_states=12)
+    sc = dgs.DeviceScene.from_host(w.scene)
+    st = dgs.DeviceStates.from_host(w.states)
+    S, H, W = st.n, w.cams[0].height, w.cams[0].width
+    tv = np.unique(w.states.t)
+    ridx = np.searchsorted(tv, w.states.t).astype(np.int32)
+    full = torch.full((len(tv), st.masks.shape[1]), -1, dtype=torch.int32, device="cuda")
+    refs = R.render_states_batched(sc, dgs.DeviceStates(full, tv, np.zeros(len(tv), np.int32)), w.cams, w.bg)
+    plan = dgs.Plan(R, sc, st, w.cams, w.bg, dgs.PLAN_RENDER, ref_index=ridx, n_refs=len(tv), entry_headroom=2.0)
+    kw = dict(pairs_t=[(0, 1), (2, 3), (5, 4)], pairs_m=[(0, 2), (6, 7)], anchors=[1, 11])
+    prm = dict(cvar_q=0.25, lambda_c=0.4)
+    with pytest.raises(RuntimeError):
+        plan.objective(refs, refs, torch.empty(1, dtype=torch.float64, device="cuda"))   # not set yet
+    with pytest.raises(RuntimeError):
+        plan.set_objective(pairs_t=[(0, S)])                                          # out of range
+    plan.set_objective(params=prm, **kw)
+    masks = st.masks.clone()
+    images = torch.empty((S, H, W, 3), device="cuda")
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    D = torch.empty(S, dtype=torch.float64, device="cuda")
+    dL = torch.empty_like(images)
+    grads = sc.zeros_like_grads()
+
+    def step():
+        for g in grads.values():
+            g.zero_()
+        plan.render(masks, images)
+        plan.objective(images, refs, loss, D, dL)
+        plan.backward(dL, grads, images=images)
+
+    def check(states):
+        img_ref = R.render_states_batched(sc, states, w.cams, w.bg)
+        assert torch.equal(images, img_ref)
+        l_ref, D_ref, dL_ref = R.objective(img_ref, refs, ridx, params=prm, **kw)
+        assert torch.equal(loss, l_ref) and torch.equal(D, D_ref) and torch.equal(dL, dL_ref)
+        g_ref = R.render_backward(sc, states, w.cams, w.bg, dL_ref, images=img_ref)
+        for k in dgs.SCENE_FIELDS:
+            if g_ref[k].numel():
+                assert torch.allclose(grads[k], g_ref[k], rtol=1e-4,
+                                      atol=1e-5 * float(g_ref[k].abs().max()) + 1e-12), k
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    check(st)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    for seed in (3, 4):
+        new = _masks(torch, w, seed)
+        masks.copy_(new)
+        graph.replay()
+        torch.cuda.synchronize()
+        plan.status()
+        check(dgs.DeviceStates(new, w.states.t, w.states.cam))
+    plan.close()

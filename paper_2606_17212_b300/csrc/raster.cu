@@ -43,9 +43,12 @@ constexpr int NPAIR = 4;              // vertical pixel pairs per lane in the fo
 // too few (region, state) items to fill the GPU twice (a single state) takes
 // the 16 x 8 regions, which give twice the warps.
 constexpr int FWD_MIN_BLOCKS = 4;
+// BATCH: the adjoint batches the per-lane sums of several entries before
+// one warp reduction (else each entry is reduced at once: 6 blocks of 16 x 8
+// regions leave no shared memory for a batch).
 template <int NP> struct BwdShape;    // pixel pairs per lane in the adjoint (a warp per 16 x 4 NP region)
-template <> struct BwdShape<4> { static constexpr int MIN_BLOCKS = 4; };
-template <> struct BwdShape<2> { static constexpr int MIN_BLOCKS = 6; };
+template <> struct BwdShape<4> { static constexpr int MIN_BLOCKS = 4; static constexpr bool BATCH = true; };
+template <> struct BwdShape<2> { static constexpr int MIN_BLOCKS = 6; static constexpr bool BATCH = false; };
 constexpr int BWD_NP_BATCH = 4, BWD_NP_FEW = 2;
 constexpr uint32_t FULL = 0xffffffffu;
 constexpr float T_STOP = 1e-4f;       // a pixel stops before the entry that would bring T below this
@@ -157,6 +160,19 @@ struct WarpSmem {
     Queue q;
     float4 pre[3][32];                // records of the next chunk, copied asynchronously (lane: its entry)
     uint8_t dep[MAX_CLUSTERS];        // the state's delivered depth per cluster
+};
+
+// The adjoint's batch of per-lane entry sums awaiting their warp reduction:
+// entry e of the batch, lane l: (S1, S4) at float2 index e RB_STRIDE / 2 + l,
+// (S5, Sr) at + 32 + l, (Sg, Sb) at + 64 + l.  RB_STRIDE = 200 words (= 8
+// mod 32) lets the reduction's lanes (4 per entry, source lanes q + 4 i)
+// read 64-bit words without bank conflicts.
+constexpr int RB = 8;                 // entries per batch
+constexpr int RB_STRIDE = 200;        // words per batch entry (3 x 64 used)
+struct RedBuf {
+    float2 v[RB * RB_STRIDE / 2];
+    uint32_t slot[RB];                // record slot of each batch entry
+    float mx[RB];                     // its mean x (the moments' dx = mx - pixel centre)
 };
 
 // Can Gaussian (mx, my, conic A B C, opacity o) reach alpha >= 1/255 at some
@@ -416,6 +432,7 @@ struct FwdLane {
         for (int j = 0; j < NP; ++j) any |= p[j].T;
         return __any_sync(FULL, any != 0ull);
     }
+    __device__ __forceinline__ void finish(const Lane<NP> &) {}
     // final colour of pair j: C + (T + Tk) bg
     __device__ __forceinline__ void out(int j, float bg0, float bg1, float bg2, f2 &o0, f2 &o1, f2 &o2) const
     {
@@ -481,6 +498,7 @@ __device__ __forceinline__ uint32_t walk(const RasterArgs &a, const Lane<NP> &L,
         if (!live || !pix.live()) break;
     }
     prefetch_wait();                  // no copy may land in the prefetch area after the walk
+    pix.finish(L);
     return min(e, end);
 }
 
@@ -720,6 +738,8 @@ struct BwdLane {
     static constexpr bool CLAMP_KINDS = true;
     BwdPair p[NP];
     float4 *rec_grad;
+    RedBuf *rb;                       // the warp's batch of entry sums
+    uint32_t nb;                      // entries in the batch
     __device__ __forceinline__ bool live() const
     {
         f2 any = 0ull;
@@ -744,15 +764,34 @@ struct BwdLane {
         const uint32_t nz = (__float_as_uint(s1) | __float_as_uint(s4) | __float_as_uint(s5) | __float_as_uint(sr) |
                              __float_as_uint(sg) | __float_as_uint(sb)) << 1;
         if (!__any_sync(FULL, nz != 0u)) return;
+        if (!BwdShape<NP>::BATCH) {
+            reduce_now(q, k, L, E.dx, s1, s4, s5, sr, sg, sb);
+            return;
+        }
+        // the lane's sums join the batch; the warp reduces a full batch at once
+        float2 *row = rb->v + nb * (RB_STRIDE / 2);
+        row[L.lane] = make_float2(s1, s4);
+        row[32 + L.lane] = make_float2(s5, sr);
+        row[64 + L.lane] = make_float2(sg, sb);
+        if (L.lane == 0) {
+            rb->slot[nb] = q.s4[k].w;
+            rb->mx[nb] = q.s3[k].x;
+        }
+        if (++nb == (uint32_t)RB) flush(L);
+    }
+    // One entry's warp reduction at once (no batch).
+    __device__ __forceinline__ void reduce_now(const Queue &q, int k, const Lane<NP> &L, float dx, float s1, float s4,
+                                               float s5, float sr, float sg, float sb)
+    {
         // the entry's pixel moments over the lane's pixels (dx is the lane's column
         // offset, the same for all its pixels); the projection adjoint turns their
         // sums into the conic, mean and opacity gradients
-        const float m0 = E.dx * s5;
+        const float m0 = dx * s5;
         float v[8];
         v[0] = m0;                 // sum dL/dpower dx
         v[1] = s1;                 // sum dL/dpower dy
-        v[2] = E.dx * m0;          // sum dL/dpower dx^2
-        v[3] = E.dx * s1;          // sum dL/dpower dx dy
+        v[2] = dx * m0;            // sum dL/dpower dx^2
+        v[3] = dx * s1;            // sum dL/dpower dx dy
         v[4] = s4;                 // sum dL/dpower dy^2
         v[5] = s5;                 // sum dL/dpower
         v[6] = sr;                 // sum dL/dC alpha T (per channel)
@@ -768,6 +807,71 @@ struct BwdLane {
             atomicAdd(dst + idx, L.lane == 1 ? xb : x);
         }
     }
+    // Reduce the batch: four lanes per entry, lane 4 e + q summing source
+    // lanes q, q + 4, ..., q + 28 of entry e, then a transpose over the four.
+    // The moments over the source lane's pixels (dx is its column offset,
+    // computed exactly as the entry's lanes compute it):
+    //   v0 = S dL/dpower dx, v1 = S dL/dpower dy, v2 = S dL/dpower dx^2,
+    //   v3 = S dL/dpower dx dy, v4 = S dL/dpower dy^2, v5 = S dL/dpower,
+    //   v6, v7, blue = S dL/dC alpha T per channel;
+    // the projection adjoint turns them into the conic, mean and opacity
+    // gradients.  One atomic add per moment goes to the record.
+    __device__ __forceinline__ void flush(const Lane<NP> &L)
+    {
+        __syncwarp();
+        const int e = L.lane >> 2, qd = L.lane & 3;
+        float v[8], blue = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = 0.0f;
+        if (e < (int)nb) {
+            const float2 *row = rb->v + e * (RB_STRIDE / 2);
+            const float mx = rb->mx[e];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int l = qd + 4 * i;
+                const float2 x = row[l], y = row[32 + l], z = row[64 + l];
+                const float dx = __fsub_rn(mx, (float)(L.rx0 + (l & 15)) + 0.5f);
+                const float m0 = __fmul_rn(dx, y.x);
+                v[0] += m0;
+                v[1] += x.x;
+                v[2] = fmaf(dx, m0, v[2]);
+                v[3] = fmaf(dx, x.x, v[3]);
+                v[4] += x.y;
+                v[5] += y.x;
+                v[6] += y.y;
+                v[7] += z.x;
+                blue += z.y;
+            }
+        }
+        // fold the entry's four lanes: lane 4 e + q ends with v[2 q], v[2 q + 1]
+        float u[4];
+        const bool b1 = qd & 2, b0 = qd & 1;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float send = b1 ? v[i] : v[i + 4], keep = b1 ? v[i + 4] : v[i];
+            u[i] = keep + __shfl_xor_sync(FULL, send, 2);
+        }
+        float w[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const float send = b0 ? u[i] : u[i + 2], keep = b0 ? u[i + 2] : u[i];
+            w[i] = keep + __shfl_xor_sync(FULL, send, 1);
+        }
+        blue += __shfl_xor_sync(FULL, blue, 1);
+        blue += __shfl_xor_sync(FULL, blue, 2);
+        if (e < (int)nb) {
+            float *dst = reinterpret_cast<float *>(rec_grad + (size_t)rb->slot[e] * 3);
+            atomicAdd(dst + 2 * qd, w[0]);
+            atomicAdd(dst + 2 * qd + 1, w[1]);
+            if (qd == 0) atomicAdd(dst + 8, blue);
+        }
+        __syncwarp();
+        nb = 0;
+    }
+    __device__ __forceinline__ void finish(const Lane<NP> &L)
+    {
+        if (BwdShape<NP>::BATCH && nb) flush(L);
+    }
 };
 
 // Adjoint compositing, one warp per (16x16 region, state).  Transmittance is never
@@ -776,8 +880,9 @@ struct BwdLane {
 //   dC/dalpha_k = rgb_k T_k - (C_after_k + T_final bg) / (1 - alpha_k)
 // with C_after_k = C_final - (colour accumulated up to and including k).  The
 // final pixel value is read from the forward's image (IMG) or recomputed by a
-// first forward walk.  Per-Gaussian pixel moments: eight pixels per lane, a
-// warp transpose reduction, one atomic add per moment.
+// first forward walk.  Per-Gaussian pixel moments: the lane's sums over its
+// pixels, reduced over the warp eight entries at a time (16 x 16 regions) or
+// entry by entry (16 x 8), one atomic add per moment.
 // Work items of the adjoint raster of one call: (tile, 16x16 region, state).
 __host__ __device__ __forceinline__ size_t bwd_items(const RasterArgs &a, int np)
 {
@@ -788,7 +893,7 @@ __host__ __device__ __forceinline__ size_t bwd_items(const RasterArgs &a, int np
 
 // One adjoint work item (every lane of the warp calls it with the same item < bwd_items).
 template <bool IMG, int NP>
-__device__ __forceinline__ void bwd_item(const RasterBwdArgs &b, size_t item, WarpSmem &sm)
+__device__ __forceinline__ void bwd_item(const RasterBwdArgs &b, size_t item, WarpSmem &sm, RedBuf *rb)
 {
     constexpr int RH = 4 * NP;     // region height (NP pixel pairs per lane)
     const RasterArgs &a = b.f;
@@ -827,6 +932,8 @@ __device__ __forceinline__ void bwd_item(const RasterBwdArgs &b, size_t item, Wa
     }
     BwdLane<NP> B;
     B.rec_grad = b.rec_grad;
+    B.rb = rb;
+    B.nb = 0;
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
         float g[2][3], T[2], Q[2];
@@ -850,14 +957,29 @@ __device__ __forceinline__ void bwd_item(const RasterBwdArgs &b, size_t item, Wa
     walk(a, L, sm, rg.x, rg.y, B);
 }
 
+// Dynamic shared memory of the adjoint kernels: WARPS WarpSmem, then (when
+// batching) WARPS RedBuf.
+template <int NP>
+constexpr size_t bwd_smem()
+{
+    return WARPS * (sizeof(WarpSmem) + (BwdShape<NP>::BATCH ? sizeof(RedBuf) : 0));
+}
+
+template <int NP>
+__device__ __forceinline__ RedBuf *red_buf(unsigned char *dsm, int w)
+{
+    return BwdShape<NP>::BATCH ? reinterpret_cast<RedBuf *>(dsm + WARPS * sizeof(WarpSmem)) + w : nullptr;
+}
+
 template <bool IMG, int NP>
 __global__ void __launch_bounds__(RT, BwdShape<NP>::MIN_BLOCKS) k_raster_bwd(RasterBwdArgs b)
 {
-    __shared__ WarpSmem smem[WARPS];
+    extern __shared__ __align__(16) unsigned char bwd_dsm[];
+    WarpSmem *smem = reinterpret_cast<WarpSmem *>(bwd_dsm);
     const int w = threadIdx.x >> 5;
     const size_t item = (size_t)blockIdx.x * WARPS + w;
     if (item >= bwd_items(b.f, NP)) return;
-    bwd_item<IMG, NP>(b, item, smem[w]);
+    bwd_item<IMG, NP>(b, item, smem[w], red_buf<NP>(bwd_dsm, w));
 }
 
 // The adjoint raster of several scenes in one launch: warp g takes item
@@ -866,7 +988,8 @@ __global__ void __launch_bounds__(RT, BwdShape<BWD_NP_BATCH>::MIN_BLOCKS) k_rast
                                                                          const size_t *__restrict__ item_off,
                                                                          int n_jobs)
 {
-    __shared__ WarpSmem smem[WARPS];
+    extern __shared__ __align__(16) unsigned char bwd_dsm[];
+    WarpSmem *smem = reinterpret_cast<WarpSmem *>(bwd_dsm);
     __shared__ RasterBwdArgs jargs[WARPS];     // the warp's job, copied from global memory
     const int w = threadIdx.x >> 5;
     const size_t g = (size_t)blockIdx.x * WARPS + w;
@@ -878,7 +1001,7 @@ __global__ void __launch_bounds__(RT, BwdShape<BWD_NP_BATCH>::MIN_BLOCKS) k_rast
     }
     copy_words(&jargs[w], &jobs[lo], sizeof(RasterBwdArgs), threadIdx.x & 31);
     __syncwarp();
-    bwd_item<true, BWD_NP_BATCH>(jargs[w], g - item_off[lo], smem[w]);
+    bwd_item<true, BWD_NP_BATCH>(jargs[w], g - item_off[lo], smem[w], red_buf<BWD_NP_BATCH>(bwd_dsm, w));
 }
 
 // Cost key of each (view group, tile), 16 bits: ascending key = descending
@@ -1045,7 +1168,7 @@ void launch_raster_bwd_multi(const RasterBwdArgs *jobs, const size_t *item_off, 
 {
     if (n_jobs <= 0 || total_items == 0) return;
     ProfScope ps_("raster_bwd", st);
-    k_raster_bwd_multi<<<(unsigned)((total_items + WARPS - 1) / WARPS), RT, 0, st>>>(jobs, item_off, n_jobs);
+    k_raster_bwd_multi<<<(unsigned)((total_items + WARPS - 1) / WARPS), RT, bwd_smem<BWD_NP_BATCH>(), st>>>(jobs, item_off, n_jobs);
     count_launch();
 }
 
@@ -1070,8 +1193,28 @@ void launch_raster_fwd(const RasterArgs &a, const WorkQueue &q, int G, int sms, 
     count_launch();
 }
 
+template <class K>
+static void bwd_attributes(K *kernel, size_t smem)
+{
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+}
+
+// Occupancy queries (once per process) and kernel attributes (once per
+// device), before any stream capture: a context's creation calls it.
 void raster_fwd_query_occupancy()
 {
+    static uint64_t attr_done = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !((attr_done >> dev) & 1u)) {
+        bwd_attributes(k_raster_bwd<true, BWD_NP_BATCH>, bwd_smem<BWD_NP_BATCH>());
+        bwd_attributes(k_raster_bwd<false, BWD_NP_BATCH>, bwd_smem<BWD_NP_BATCH>());
+        bwd_attributes(k_raster_bwd<true, BWD_NP_FEW>, bwd_smem<BWD_NP_FEW>());
+        bwd_attributes(k_raster_bwd<false, BWD_NP_FEW>, bwd_smem<BWD_NP_FEW>());
+        bwd_attributes(k_raster_bwd_multi, bwd_smem<BWD_NP_BATCH>());
+        attr_done |= 1ull << dev;
+    }
     static bool done = false;
     if (done) return;
     query_t<true, true, false>();
@@ -1115,11 +1258,11 @@ void launch_raster_bwd(const RasterBwdArgs &b, int sms, cudaStream_t st)
     const unsigned grid = (unsigned)((items + WARPS - 1) / WARPS);
     ProfScope ps_(b.img_fwd ? "raster_bwd" : "raster_bwd_2pass", st);
     if (batch) {
-        if (b.img_fwd) k_raster_bwd<true, BWD_NP_BATCH><<<grid, RT, 0, st>>>(b);
-        else k_raster_bwd<false, BWD_NP_BATCH><<<grid, RT, 0, st>>>(b);
+        if (b.img_fwd) k_raster_bwd<true, BWD_NP_BATCH><<<grid, RT, bwd_smem<BWD_NP_BATCH>(), st>>>(b);
+        else k_raster_bwd<false, BWD_NP_BATCH><<<grid, RT, bwd_smem<BWD_NP_BATCH>(), st>>>(b);
     } else {
-        if (b.img_fwd) k_raster_bwd<true, BWD_NP_FEW><<<grid, RT, 0, st>>>(b);
-        else k_raster_bwd<false, BWD_NP_FEW><<<grid, RT, 0, st>>>(b);
+        if (b.img_fwd) k_raster_bwd<true, BWD_NP_FEW><<<grid, RT, bwd_smem<BWD_NP_FEW>(), st>>>(b);
+        else k_raster_bwd<false, BWD_NP_FEW><<<grid, RT, bwd_smem<BWD_NP_FEW>(), st>>>(b);
     }
     count_launch();
 }

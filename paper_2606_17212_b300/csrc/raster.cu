@@ -129,20 +129,23 @@ __device__ __forceinline__ float ge1(float x, float y)
     return r;
 }
 
-// Threshold of the base-2 exponent: alpha = o 2^p2 >= 1/255 <=> p2 >= tau =
-// -log2(255 o), kept <= -0 (every staged record has o >= 1/255).  A p2 that
-// FP32 rounding leaves at +0 (Gaussian centre on the pixel centre, where the
-// exact power is 0) passes, as the exact arithmetic does.  For such tau the
-// float test p2 >= tau and the unsigned test bits(p2) <= bits(tau) agree
-// (negative floats order by magnitude; every p2 >= +0 passes both), so either
-// form may be used.  lg2.approx and ex2.approx err by ~2^-22 relative, so the
-// decision can differ from the exact alpha >= 1/255 only for alpha within
-// ~1e-6 relative of 1/255.
-__device__ __forceinline__ float tau_of(float o)
+// alpha = o 2^p2 = 2^(p2 + log2 o): each staged entry carries log2 o, which
+// a lane adds to its column's constant exponent term, so alpha is one ex2 and
+// alpha >= 1/255 is e = p2 + log2 o >= TAU0 = -log2 255 for every entry.  In
+// exact arithmetic e <= 0; an e that FP32 rounding leaves at or above +0
+// (Gaussian centre on the pixel centre, o near 1) passes, as the exact
+// arithmetic does.  For negative TAU0 the float test e >= TAU0 and the
+// unsigned test bits(e) <= bits(TAU0) agree (negative floats order by
+// magnitude; every e >= +0 passes both).  lg2.approx and ex2.approx err by
+// ~2^-22 relative, so the decision can differ from the exact alpha >= 1/255
+// only for alpha within ~1e-6 relative of 1/255.
+constexpr uint32_t TAU0_BITS = 0xc0ffd1beu;   // bits of the float nearest -log2 255 = -7.99435...
+
+__device__ __forceinline__ float lg2(float x)
 {
     float l;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(255.0f * o));
-    return -fmaxf(l, 0.0f);
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
+    return l;
 }
 
 // ------------------------------------------------------------ staging
@@ -150,9 +153,9 @@ __device__ __forceinline__ float tau_of(float o)
 // Fields are duplicated where the packed arithmetic wants a pair.
 struct Queue {
     float4 s0[QCAP];                  // my, my, c2, c2          (records hold the scaled conic)
-    float4 s1[QCAP];                  // o, o, r, r
+    float4 s1[QCAP];                  // log2 o, log2 o, r, r
     float4 s2[QCAP];                  // g, g, b, b
-    float4 s3[QCAP];                  // mx, a2, b2, tau
+    float4 s3[QCAP];                  // mx, a2, b2, -
     uint4 s4[QCAP];                   // box x, box y, kind (bit 0: boxed, bit 1: clamp), record slot
 };
 
@@ -292,9 +295,10 @@ __device__ __forceinline__ uint32_t stage_chunk(const uint8_t *dep, uint32_t slo
         const uint32_t k = (tail + __popc(bal & ((1u << lane) - 1u))) & (QCAP - 1);
         Queue &q = sm.q;
         q.s0[k] = make_float4(r0.y, r0.y, r1.x, r1.x);
-        q.s1[k] = make_float4(r1.y, r1.y, r1.z, r1.z);
+        const float lo2o = lg2(r1.y);
+        q.s1[k] = make_float4(lo2o, lo2o, r1.z, r1.z);
         q.s2[k] = make_float4(r1.w, r1.w, r2.x, r2.x);
-        q.s3[k] = make_float4(r0.x, r0.z, r0.w, tau_of(r1.y));
+        q.s3[k] = make_float4(r0.x, r0.z, r0.w, 0.0f);
         const uint32_t cd = __float_as_uint(r2.w);
         q.s4[k] = make_uint4(__float_as_uint(r2.y), __float_as_uint(r2.z),
                              (cd >> 31) | ((cd & REC_CLAMP) ? 2u : 0u), slot);
@@ -304,13 +308,11 @@ __device__ __forceinline__ uint32_t stage_chunk(const uint8_t *dep, uint32_t slo
 }
 
 // Per-entry, per-lane terms of one staged entry: the column's exponent terms
-// u = a2 dx^2, v = b2 dx (shared by the lane's pixels), the broadcast pairs,
-// and the rows of the lane that lie in the entry's pixel box (only where the
-// record's 3-sigma box clips its alpha box; else all rows).
+// u = a2 dx^2 + log2 o, v = b2 dx (shared by the lane's pixels), the
+// broadcast pairs, and the rows of the lane that lie in the entry's pixel box
+// (only where the record's 3-sigma box clips its alpha box; else all rows).
 struct Ent {
-    f2 my, c2, o, r, g, b, uu, vv;
-    float tau;                        // exponent threshold (as a float and as its bits)
-    uint32_t taub;
+    f2 my, c2, r, g, b, uu, vv;
     uint32_t rows;                    // bit r: row r passes the box test
     float dx;
 };
@@ -322,14 +324,11 @@ __device__ __forceinline__ Ent load_entry(const Queue &q, int k, const Lane<NP> 
     const float4 s0 = q.s0[k], s1 = q.s1[k], s2 = q.s2[k], s3 = q.s3[k];
     E.my = pk(s0.x, s0.y);
     E.c2 = pk(s0.z, s0.w);
-    E.o = pk(s1.x, s1.y);
     E.r = pk(s1.z, s1.w);
     E.g = pk(s2.x, s2.y);
     E.b = pk(s2.z, s2.w);
-    E.tau = s3.w;
-    E.taub = __float_as_uint(s3.w);
     E.dx = __fsub_rn(s3.x, L.pcx);
-    const float u = __fmul_rn(__fmul_rn(s3.y, E.dx), E.dx), v = __fmul_rn(s3.z, E.dx);
+    const float u = __fadd_rn(__fmul_rn(__fmul_rn(s3.y, E.dx), E.dx), s1.x), v = __fmul_rn(s3.z, E.dx);
     E.uu = pk(u, u);
     E.vv = pk(v, v);
     E.rows = 0xffu;
@@ -344,18 +343,18 @@ __device__ __forceinline__ Ent load_entry(const Queue &q, int k, const Lane<NP> 
     return E;
 }
 
-// Base-2 exponent p2 = a2 dx^2 + b2 dx dy + c2 dy^2 of a pixel pair and the
-// clamped opacity alpha of each pixel (0 where the entry is skipped: outside
-// the box or alpha < 1/255).  Returns the pair (alpha0, alpha1); `ar` gets the
-// unclamped o 2^p2 (for the clamp's derivative in the adjoint).
+// Base-2 exponent e = a2 dx^2 + b2 dx dy + c2 dy^2 + log2 o of a pixel pair
+// and the clamped opacity alpha of each pixel (0 where the entry is skipped:
+// outside the box or alpha < 1/255).  Returns the pair (alpha0, alpha1); `ar`
+// gets the unclamped o 2^p2 = 2^e (for the clamp's derivative in the adjoint).
 __device__ __forceinline__ f2 pair_alpha_clamped(const Ent &E, f2 pcy, int j, f2 &dy, f2 &ar)
 {
     dy = sub2(E.my, pcy);
     const f2 p2 = fma2(fma2(E.c2, dy, E.vv), dy, E.uu);
     const float q0 = lo(p2), q1 = hi(p2);
-    ar = mul2(E.o, pk(ex2(q0), ex2(q1)));
-    const bool h0 = __float_as_uint(q0) <= E.taub && ((E.rows >> (2 * j)) & 1u);
-    const bool h1 = __float_as_uint(q1) <= E.taub && ((E.rows >> (2 * j + 1)) & 1u);
+    ar = pk(ex2(q0), ex2(q1));
+    const bool h0 = __float_as_uint(q0) <= TAU0_BITS && ((E.rows >> (2 * j)) & 1u);
+    const bool h1 = __float_as_uint(q1) <= TAU0_BITS && ((E.rows >> (2 * j + 1)) & 1u);
     return pk(h0 ? fminf(A_MAX, lo(ar)) : 0.0f, h1 ? fminf(A_MAX, hi(ar)) : 0.0f);
 }
 
@@ -369,10 +368,10 @@ __device__ __forceinline__ f2 pair_alpha(const Ent &E, f2 pcy, int j, f2 &dy, f2
     dy = sub2(E.my, pcy);
     const f2 p2 = fma2(fma2(E.c2, dy, E.vv), dy, E.uu);
     const float q0 = lo(p2), q1 = hi(p2);
-    ar = mul2(E.o, pk(ex2(q0), ex2(q1)));
+    ar = pk(ex2(q0), ex2(q1));
     // (E.rows is all ones unless BOXED)
-    const bool h0 = __float_as_uint(q0) <= E.taub && ((E.rows >> (2 * j)) & 1u);
-    const bool h1 = __float_as_uint(q1) <= E.taub && ((E.rows >> (2 * j + 1)) & 1u);
+    const bool h0 = __float_as_uint(q0) <= TAU0_BITS && ((E.rows >> (2 * j)) & 1u);
+    const bool h1 = __float_as_uint(q1) <= TAU0_BITS && ((E.rows >> (2 * j + 1)) & 1u);
     if (CLAMP) return pk(h0 ? fminf(A_MAX, lo(ar)) : 0.0f, h1 ? fminf(A_MAX, hi(ar)) : 0.0f);
     return pk(h0 ? lo(ar) : 0.0f, h1 ? hi(ar) : 0.0f);
 }
@@ -382,6 +381,8 @@ __device__ __forceinline__ f2 pair_alpha(const Ent &E, f2 pcy, int j, f2 &dy, f2
 // would fall below 1e-4: the entry is not added) keeps T = 0 from then on, so
 // every later entry adds exactly zero, and its transmittance at the stop is
 // kept in Tk; the final transmittance is T + Tk (one of them is zero).
+// (Tracking T + Tk directly, as U - alpha T, is one operation less per pair
+// but measured 4% slower.)
 struct FwdPair {
     f2 T, Tk, cr, cg, cb;
 };
@@ -820,29 +821,31 @@ struct BwdLane {
     {
         __syncwarp();
         const int e = L.lane >> 2, qd = L.lane & 3;
-        float v[8], blue = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = 0.0f;
+        // the plain sums packed as (S1, S4), (S5, Sr), (Sg, Sb); the dx moments
+        // per column (source lanes c and c + 16 share it)
+        f2 a14 = 0ull, a5r = 0ull, agb = 0ull;
+        float v0 = 0.0f, v2 = 0.0f, v3 = 0.0f;
         if (e < (int)nb) {
-            const float2 *row = rb->v + e * (RB_STRIDE / 2);
+            const f2 *row = reinterpret_cast<const f2 *>(rb->v + e * (RB_STRIDE / 2));
             const float mx = rb->mx[e];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int l = qd + 4 * i;
-                const float2 x = row[l], y = row[32 + l], z = row[64 + l];
-                const float dx = __fsub_rn(mx, (float)(L.rx0 + (l & 15)) + 0.5f);
-                const float m0 = __fmul_rn(dx, y.x);
-                v[0] += m0;
-                v[1] += x.x;
-                v[2] = fmaf(dx, m0, v[2]);
-                v[3] = fmaf(dx, x.x, v[3]);
-                v[4] += x.y;
-                v[5] += y.x;
-                v[6] += y.y;
-                v[7] += z.x;
-                blue += z.y;
+            for (int c = 0; c < 4; ++c) {
+                const int l = qd + 4 * c;
+                const f2 x0 = row[l], y0 = row[32 + l], z0 = row[64 + l];
+                const f2 x1 = row[l + 16], y1 = row[48 + l], z1 = row[80 + l];
+                a14 = add2(a14, add2(x0, x1));
+                a5r = add2(a5r, add2(y0, y1));
+                agb = add2(agb, add2(z0, z1));
+                const float dx = __fsub_rn(mx, (float)(L.rx0 + l) + 0.5f);
+                const float s5 = lo(y0) + lo(y1), s1 = lo(x0) + lo(x1);
+                const float m0 = dx * s5;
+                v0 += m0;
+                v2 = fmaf(dx, m0, v2);
+                v3 = fmaf(dx, s1, v3);
             }
         }
+        float v[8] = {v0, lo(a14), v2, v3, hi(a14), lo(a5r), hi(a5r), lo(agb)};
+        float blue = hi(agb);
         // fold the entry's four lanes: lane 4 e + q ends with v[2 q], v[2 q + 1]
         float u[4];
         const bool b1 = qd & 2, b0 = qd & 1;

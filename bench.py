@@ -45,8 +45,8 @@ MUFU_EX2_PER_SM_CLK = 32
 # kernel source it was taken on (sha1 of csrc/raster.cu), the workload at full size
 # and the sort tile side in pixels.
 MEASURED_TRAFFIC = {
-    ("raster_bwd", "c3_fwdbwd_250k", 32): (783_723_776 + 66_997_504, "acfc1cf6c25d61a7c8702e98da24e74a02c6c591"),
-    ("raster_fwd", "c3_fwdbwd_250k", 32): (441_528_064 + 182_790_400, "acfc1cf6c25d61a7c8702e98da24e74a02c6c591"),
+    ("raster_bwd", "c3_fwdbwd_250k", 32): (783_110_144 + 66_551_296, "2af452a2fef0b5aff0dbedb090f628b7bcd5c238"),
+    ("raster_fwd", "c3_fwdbwd_250k", 32): (440_954_112 + 183_188_992, "2af452a2fef0b5aff0dbedb090f628b7bcd5c238"),
 }
 
 

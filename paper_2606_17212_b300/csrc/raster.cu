@@ -128,18 +128,25 @@ __device__ __forceinline__ float ge1(float x, float y)
     asm("set.ge.f32.f32 %0, %1, %2;" : "=f"(r) : "f"(x), "f"(y));
     return r;
 }
+// 1.0f when x < y, else 0.0f
+__device__ __forceinline__ float lt1(float x, float y)
+{
+    float r;
+    asm("set.lt.f32.f32 %0, %1, %2;" : "=f"(r) : "f"(x), "f"(y));
+    return r;
+}
 
 // alpha = o 2^p2 = 2^(p2 + log2 o): each staged entry carries log2 o, which
-// a lane adds to its column's constant exponent term, so alpha is one ex2 and
-// alpha >= 1/255 is e = p2 + log2 o >= TAU0 = -log2 255 for every entry.  In
-// exact arithmetic e <= 0; an e that FP32 rounding leaves at or above +0
-// (Gaussian centre on the pixel centre, o near 1) passes, as the exact
-// arithmetic does.  For negative TAU0 the float test e >= TAU0 and the
-// unsigned test bits(e) <= bits(TAU0) agree (negative floats order by
-// magnitude; every e >= +0 passes both).  lg2.approx and ex2.approx err by
-// ~2^-22 relative, so the decision can differ from the exact alpha >= 1/255
-// only for alpha within ~1e-6 relative of 1/255.
-constexpr uint32_t TAU0_BITS = 0xc0ffd1beu;   // bits of the float nearest -log2 255 = -7.99435...
+// a lane adds to its column's constant exponent term, so alpha is one ex2
+// and alpha >= 1/255 is e = p2 + log2 o >= TAU0 = -log2 255 for every entry
+// (the test does not wait for the ex2).  In exact arithmetic e <= 0; an e
+// that FP32 rounding leaves at or above +0 (Gaussian centre on the pixel
+// centre, o near 1) passes, as the exact arithmetic does.  The forward takes
+// the test as a compare and a select, the adjoint as a compare-and-set (1 or
+// 0) and one packed multiply per pixel pair: the same decision.  lg2.approx
+// and ex2.approx err by ~2^-22 relative, so the decision can differ from the
+// exact alpha >= 1/255 only for alpha within ~1e-6 relative of 1/255.
+constexpr float TAU0 = -7.99435343685886f;   // float nearest -log2 255
 
 __device__ __forceinline__ float lg2(float x)
 {
@@ -246,6 +253,7 @@ __device__ __forceinline__ Lane<NP> lane_of(int tile, int ox, int oy, const Rast
 // Start copying each lane's record (the lane's run entry of the next chunk,
 // record slot `slot`) into the warp's prefetch area; the copies land while
 // the warp composites the entries it has already staged.
+template <bool L1>
 __device__ __forceinline__ void prefetch_records(const Rec *__restrict__ recs, uint32_t slot, bool valid,
                                                  WarpSmem &sm)
 {
@@ -255,7 +263,10 @@ __device__ __forceinline__ void prefetch_records(const Rec *__restrict__ recs, u
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&sm.pre[k][lane]);
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src + 16 * k) : "memory");
+            if (L1)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src + 16 * k) : "memory");
+            else
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src + 16 * k) : "memory");
         }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -317,8 +328,9 @@ struct Ent {
     float dx;
 };
 
-template <int NP, bool BOXED>
-__device__ __forceinline__ Ent load_entry(const Queue &q, int k, const Lane<NP> &L)
+// s4: the entry's box and slot word as loaded by the dispatch (PRE), else read here.
+template <int NP, bool BOXED, bool PRE>
+__device__ __forceinline__ Ent load_entry(const Queue &q, int k, const uint4 &s4_, const Lane<NP> &L)
 {
     Ent E;
     const float4 s0 = q.s0[k], s1 = q.s1[k], s2 = q.s2[k], s3 = q.s3[k];
@@ -333,7 +345,7 @@ __device__ __forceinline__ Ent load_entry(const Queue &q, int k, const Lane<NP> 
     E.vv = pk(v, v);
     E.rows = 0xffu;
     if (BOXED) {
-        const uint4 s4 = q.s4[k];
+        const uint4 s4 = PRE ? s4_ : q.s4[k];
         const int xlo = (int)(s4.x & 0xffffu), xhi = (int)(s4.x >> 16);
         const int ylo = (int)(s4.y & 0xffffu), yhi = (int)(s4.y >> 16);
         const int rlo = max(ylo - L.py0, 0), rhi = min(yhi - L.py0, 2 * NP - 1);
@@ -351,10 +363,9 @@ __device__ __forceinline__ f2 pair_alpha_clamped(const Ent &E, f2 pcy, int j, f2
 {
     dy = sub2(E.my, pcy);
     const f2 p2 = fma2(fma2(E.c2, dy, E.vv), dy, E.uu);
-    const float q0 = lo(p2), q1 = hi(p2);
-    ar = pk(ex2(q0), ex2(q1));
-    const bool h0 = __float_as_uint(q0) <= TAU0_BITS && ((E.rows >> (2 * j)) & 1u);
-    const bool h1 = __float_as_uint(q1) <= TAU0_BITS && ((E.rows >> (2 * j + 1)) & 1u);
+    ar = pk(ex2(lo(p2)), ex2(hi(p2)));
+    const bool h0 = lo(p2) >= TAU0 && ((E.rows >> (2 * j)) & 1u);
+    const bool h1 = hi(p2) >= TAU0 && ((E.rows >> (2 * j + 1)) & 1u);
     return pk(h0 ? fminf(A_MAX, lo(ar)) : 0.0f, h1 ? fminf(A_MAX, hi(ar)) : 0.0f);
 }
 
@@ -367,13 +378,11 @@ __device__ __forceinline__ f2 pair_alpha(const Ent &E, f2 pcy, int j, f2 &dy, f2
 {
     dy = sub2(E.my, pcy);
     const f2 p2 = fma2(fma2(E.c2, dy, E.vv), dy, E.uu);
-    const float q0 = lo(p2), q1 = hi(p2);
-    ar = pk(ex2(q0), ex2(q1));
-    // (E.rows is all ones unless BOXED)
-    const bool h0 = __float_as_uint(q0) <= TAU0_BITS && ((E.rows >> (2 * j)) & 1u);
-    const bool h1 = __float_as_uint(q1) <= TAU0_BITS && ((E.rows >> (2 * j + 1)) & 1u);
-    if (CLAMP) return pk(h0 ? fminf(A_MAX, lo(ar)) : 0.0f, h1 ? fminf(A_MAX, hi(ar)) : 0.0f);
-    return pk(h0 ? lo(ar) : 0.0f, h1 ? hi(ar) : 0.0f);
+    ar = pk(ex2(lo(p2)), ex2(hi(p2)));
+    const f2 keep = pk(ge1(lo(p2), TAU0), ge1(hi(p2), TAU0));
+    const f2 a = mul2(CLAMP ? pk(fminf(A_MAX, lo(ar)), fminf(A_MAX, hi(ar))) : ar, keep);
+    if (!BOXED) return a;
+    return pk(((E.rows >> (2 * j)) & 1u) ? lo(a) : 0.0f, ((E.rows >> (2 * j + 1)) & 1u) ? hi(a) : 0.0f);
 }
 
 // ------------------------------------------------------------ forward
@@ -406,6 +415,7 @@ __device__ __forceinline__ void fwd_pair(FwdPair &P, const Ent &E, f2 al)
 template <int NP>
 struct FwdLane {
     static constexpr bool CLAMP_KINDS = false;
+    static constexpr bool RECS_L1 = true;     // record prefetch cached in L1 (cp.async.ca)
     FwdPair p[NP];
     __device__ __forceinline__ void init(const Lane<NP> &L)
     {
@@ -416,9 +426,9 @@ struct FwdLane {
         }
     }
     template <bool BOXED, bool CLAMP>
-    __device__ __forceinline__ void entry(const Queue &q, int k, const Lane<NP> &L)
+    __device__ __forceinline__ void entry(const Queue &q, int k, const uint4 &s4, const Lane<NP> &L)
     {
-        const Ent E = load_entry<NP, BOXED>(q, k, L);
+        const Ent E = load_entry<NP, BOXED, false>(q, k, s4, L);
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
             f2 dy, ar;
@@ -450,17 +460,19 @@ struct FwdLane {
 template <class PIX, int NP>
 __device__ __forceinline__ void dispatch_entry(PIX &pix, const Queue &q, int k, const Lane<NP> &L)
 {
-    const uint32_t kind = q.s4[k].z;
+    // the adjoint wants the whole word (its slot); the forward only the kind
+    const uint4 s4 = PIX::CLAMP_KINDS ? q.s4[k] : make_uint4(0u, 0u, q.s4[k].z, 0u);
+    const uint32_t kind = s4.z;
     if (!PIX::CLAMP_KINDS) {
-        if (kind & 1u) pix.template entry<true, true>(q, k, L);
-        else pix.template entry<false, true>(q, k, L);
+        if (kind & 1u) pix.template entry<true, true>(q, k, s4, L);
+        else pix.template entry<false, true>(q, k, s4, L);
         return;
     }
     switch (kind) {
-    case 1: pix.template entry<true, false>(q, k, L); break;
-    case 0: pix.template entry<false, false>(q, k, L); break;
-    case 3: pix.template entry<true, true>(q, k, L); break;
-    default: pix.template entry<false, true>(q, k, L); break;
+    case 1: pix.template entry<true, false>(q, k, s4, L); break;
+    case 0: pix.template entry<false, false>(q, k, s4, L); break;
+    case 3: pix.template entry<true, true>(q, k, s4, L); break;
+    default: pix.template entry<false, true>(q, k, s4, L); break;
     }
 }
 
@@ -476,7 +488,7 @@ __device__ __forceinline__ uint32_t walk(const RasterArgs &a, const Lane<NP> &L,
     if (!pix.live()) return e;
     // pipeline: the records of chunk e are in flight, the slots of chunk e + 32 loaded
     uint32_t slot = e + L.lane < end ? __ldg(a.evals + e + L.lane) : 0u;
-    prefetch_records(a.recs, slot, e + L.lane < end, sm);
+    prefetch_records<PIX::RECS_L1>(a.recs, slot, e + L.lane < end, sm);
     uint32_t slot_next = e + CHUNK + L.lane < end ? __ldg(a.evals + e + CHUNK + L.lane) : 0u;
     for (;;) {
         while (tail - head < (uint32_t)CHUNK && e < end) {
@@ -484,7 +496,7 @@ __device__ __forceinline__ uint32_t walk(const RasterArgs &a, const Lane<NP> &L,
             tail = stage_chunk(sm.dep, slot, e + L.lane < end, L.rx0, L.ry0, h, sm, tail);
             e += CHUNK;
             slot = slot_next;
-            if (e < end) prefetch_records(a.recs, slot, e + L.lane < end, sm);
+            if (e < end) prefetch_records<PIX::RECS_L1>(a.recs, slot, e + L.lane < end, sm);
             slot_next = e + CHUNK + L.lane < end ? __ldg(a.evals + e + CHUNK + L.lane) : 0u;
         }
         if (head == tail) break;
@@ -696,7 +708,7 @@ __device__ __forceinline__ void bwd_pair(BwdPair &P, BwdSums &S, const Ent &E, f
     const f2 da = fma2(P.Qn, pk(rcp(lo(om)), rcp(hi(om))), mul2(P.T, gr));
     // d alpha / d power = alpha on the linear range; 0 when skipped, stopped or clamped
     f2 alin = mul2(al, s);
-    if (CLAMP) alin = pk(lo(ar) < A_MAX ? lo(alin) : 0.0f, hi(ar) < A_MAX ? hi(alin) : 0.0f);
+    if (CLAMP) alin = mul2(alin, pk(lt1(lo(ar), A_MAX), lt1(hi(ar), A_MAX)));
     const f2 gpw = mul2(da, alin);
     const f2 t2 = mul2(gpw, dy);
     if (FIRST) {
@@ -737,6 +749,10 @@ __device__ __forceinline__ float reduce8_transpose(const float *v, int lane)
 template <int NP>
 struct BwdLane {
     static constexpr bool CLAMP_KINDS = true;
+    // the batch leaves little L1 beside shared memory: the record prefetch
+    // bypasses it (cp.async.cg; measured 0.5% faster than .ca here, 0.5%
+    // slower in the forward)
+    static constexpr bool RECS_L1 = false;
     BwdPair p[NP];
     float4 *rec_grad;
     RedBuf *rb;                       // the warp's batch of entry sums
@@ -749,9 +765,9 @@ struct BwdLane {
         return __any_sync(FULL, any != 0ull);
     }
     template <bool BOXED, bool CLAMP>
-    __device__ __forceinline__ void entry(const Queue &q, int k, const Lane<NP> &L)
+    __device__ __forceinline__ void entry(const Queue &q, int k, const uint4 &s4, const Lane<NP> &L)
     {
-        const Ent E = load_entry<NP, BOXED>(q, k, L);
+        const Ent E = load_entry<NP, BOXED, true>(q, k, s4, L);
         BwdSums S;
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
@@ -760,28 +776,30 @@ struct BwdLane {
             if (j == 0) bwd_pair<true, CLAMP>(p[j], S, E, al, ar, dy);
             else bwd_pair<false, CLAMP>(p[j], S, E, al, ar, dy);
         }
-        const float s1 = lo(S.S1) + hi(S.S1), s4 = lo(S.S4) + hi(S.S4), s5 = lo(S.S5) + hi(S.S5);
+        const float s1 = lo(S.S1) + hi(S.S1), s4v = lo(S.S4) + hi(S.S4), s5 = lo(S.S5) + hi(S.S5);
         const float sr = lo(S.Sr) + hi(S.Sr), sg = lo(S.Sg) + hi(S.Sg), sb = lo(S.Sb) + hi(S.Sb);
-        const uint32_t nz = (__float_as_uint(s1) | __float_as_uint(s4) | __float_as_uint(s5) | __float_as_uint(sr) |
-                             __float_as_uint(sg) | __float_as_uint(sb)) << 1;
-        if (!__any_sync(FULL, nz != 0u)) return;
         if (!BwdShape<NP>::BATCH) {
-            reduce_now(q, k, L, E.dx, s1, s4, s5, sr, sg, sb);
+            // entries that changed no lane's sums are skipped with one vote
+            const uint32_t nz = (__float_as_uint(s1) | __float_as_uint(s4v) | __float_as_uint(s5) |
+                                 __float_as_uint(sr) | __float_as_uint(sg) | __float_as_uint(sb)) << 1;
+            if (__any_sync(FULL, nz != 0u)) reduce_now(s4.w, L, E.dx, s1, s4v, s5, sr, sg, sb);
             return;
         }
+        // every entry joins the batch (zero sums add nothing; a vote to skip
+        // them cost more than the batch work it saved)
         // the lane's sums join the batch; the warp reduces a full batch at once
         float2 *row = rb->v + nb * (RB_STRIDE / 2);
-        row[L.lane] = make_float2(s1, s4);
+        row[L.lane] = make_float2(s1, s4v);
         row[32 + L.lane] = make_float2(s5, sr);
         row[64 + L.lane] = make_float2(sg, sb);
         if (L.lane == 0) {
-            rb->slot[nb] = q.s4[k].w;
+            rb->slot[nb] = s4.w;
             rb->mx[nb] = q.s3[k].x;
         }
         if (++nb == (uint32_t)RB) flush(L);
     }
     // One entry's warp reduction at once (no batch).
-    __device__ __forceinline__ void reduce_now(const Queue &q, int k, const Lane<NP> &L, float dx, float s1, float s4,
+    __device__ __forceinline__ void reduce_now(uint32_t slot, const Lane<NP> &L, float dx, float s1, float s4,
                                                float s5, float sr, float sg, float sb)
     {
         // the entry's pixel moments over the lane's pixels (dx is the lane's column
@@ -804,7 +822,7 @@ struct BwdLane {
         // lane 4 j holds the total of v[j], lane 1 the blue sum
         if ((L.lane & 3) == 0 || L.lane == 1) {
             const int idx = L.lane == 1 ? 8 : (L.lane >> 2);
-            float *dst = reinterpret_cast<float *>(rec_grad + (size_t)q.s4[k].w * 3);
+            float *dst = reinterpret_cast<float *>(rec_grad + (size_t)slot * 3);
             atomicAdd(dst + idx, L.lane == 1 ? xb : x);
         }
     }

@@ -45,8 +45,8 @@ MUFU_EX2_PER_SM_CLK = 32
 # kernel source it was taken on (sha1 of csrc/raster.cu), the workload at full size
 # and the sort tile side in pixels.
 MEASURED_TRAFFIC = {
-    ("raster_bwd", "c3_fwdbwd_250k", 32): (783_110_144 + 66_551_296, "2af452a2fef0b5aff0dbedb090f628b7bcd5c238"),
-    ("raster_fwd", "c3_fwdbwd_250k", 32): (440_954_112 + 183_188_992, "2af452a2fef0b5aff0dbedb090f628b7bcd5c238"),
+    ("raster_bwd", "c3_fwdbwd_250k", 32): (805_345_280 + 78_024_448, "743ee6f557420f32b4f7d1e189fac67d23338d5e"),
+    ("raster_fwd", "c3_fwdbwd_250k", 32): (441_935_360 + 183_101_184, "743ee6f557420f32b4f7d1e189fac67d23338d5e"),
 }
 
 

@@ -11,7 +11,8 @@
 // the SSIM value with respect to the three blurred moments it depends on
 // (mean of x, of x^2, of x y), and the gradient kernel blurs those back:
 //   dSSIM/dx = (G * d_mx + 2 x (G * d_exx) + y (G * d_exy)) / (3 H W).
-// Everything is FP32 except the sums over pixels, states and pairs (FP64).
+// Everything is FP32 except the sums over pixels, states and pairs (FP64;
+// the SSIM forward adds each thread's six values in FP32 first).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -28,6 +29,47 @@ constexpr int HR = 5;                        // window radius (11 taps)
 constexpr int RG_W = OT_W + 2 * HR, RG_H = OT_H + 2 * HR;   // 42 x 26 region
 constexpr int OT_THREADS = 256;
 constexpr float SSIM_C1 = 0.01f * 0.01f, SSIM_C2 = 0.03f * 0.03f;
+// The blurs keep each thread's inputs in registers: a horizontal-pass thread
+// makes HX consecutive outputs of one region row from 2 HR + HX inputs, a
+// vertical-pass thread VY consecutive output rows of one column.  Every
+// output is still the sum over the 11 taps in tap order (the same fmaf
+// chain), so the maps are the plain per-output filter's, bit for bit.
+constexpr int HX = 4, VY = 2;
+constexpr int HS = OT_W + 1;                 // padded row stride of the horizontal results
+
+// Two FP32 values in one 64-bit register pair, each lane rounded as the
+// scalar IEEE operation.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pk(float a, float b)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void unpk(f2 x, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
+}
+#pragma nv_diag_suppress 550
+__device__ __forceinline__ float lo(f2 x)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
+    return a;
+}
+#pragma nv_diag_default 550
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 
 // The normalised 11-tap Gaussian window (sigma 1.5), computed by every thread.
 __device__ __forceinline__ void window(float *g)
@@ -58,15 +100,17 @@ __device__ double block_sum_d(double v, double *red)
 // Forward: one block per (32x16 tile, state).  Writes the three per-pixel
 // derivative maps (channel-planar [S][3][H][W] each) and the tile's FP64 sums
 // of the SSIM values and of the squared errors (part[s][tile][0..1]).
-__global__ void __launch_bounds__(OT_THREADS) k_ssim_fwd(const float *__restrict__ images,
+__global__ void __launch_bounds__(OT_THREADS, 5) k_ssim_fwd(const float *__restrict__ images,
                                                          const float *__restrict__ refs,
                                                          const int32_t *__restrict__ ref_index, int H, int W,
                                                          int tiles_x, int n_tiles, float *__restrict__ d_mx,
                                                          float *__restrict__ d_exx, float *__restrict__ d_exy,
                                                          double *__restrict__ part)
 {
+    static_assert(RG_H * (OT_W / HX) <= OT_THREADS && OT_W * OT_H == OT_THREADS * VY, "blur thread layout");
     __shared__ float xs[RG_H][RG_W * 3], ys[RG_H][RG_W * 3];       // region, channel-interleaved rows
-    __shared__ float hx[RG_H][OT_W], hy[RG_H][OT_W], hxx[RG_H][OT_W], hyy[RG_H][OT_W], hxy[RG_H][OT_W];
+    __shared__ f2 hm[RG_H][HS], hq[RG_H][HS];     // row blurs of (x, y) and (x^2, y^2)
+    __shared__ float hc[RG_H][HS];                 // row blur of x y
     __shared__ double red[OT_THREADS / 32];
     const int tile = blockIdx.x % n_tiles, s = blockIdx.x / n_tiles;
     const int x0 = (tile % tiles_x) * OT_W, y0 = (tile / tiles_x) * OT_H;
@@ -75,46 +119,83 @@ __global__ void __launch_bounds__(OT_THREADS) k_ssim_fwd(const float *__restrict
     const float *ref = refs + (size_t)ref_index[s] * npix * 3;
     float g[2 * HR + 1];
     window(g);
-    for (int i = threadIdx.x; i < RG_H * RG_W * 3; i += OT_THREADS) {
-        const int r = i / (RG_W * 3), q = i % (RG_W * 3);
-        const int gy = y0 - HR + r, gx = x0 - HR + q / 3;
-        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-        const size_t o = ((size_t)gy * W + gx) * 3 + q % 3;
-        xs[r][q] = in ? img[o] : 0.0f;
-        ys[r][q] = in ? ref[o] : 0.0f;
+    f2 G[2 * HR + 1];
+#pragma unroll
+    for (int k = 0; k < 2 * HR + 1; ++k) G[k] = pk(g[k], g[k]);
+    // the region, warp by row and lane by float of the channel-interleaved row
+    // (float f of a row lies in the image iff 0 <= (x0 - HR) 3 + f < 3 W)
+    for (int r = threadIdx.x >> 5; r < RG_H; r += OT_THREADS / 32) {
+        const int gy = y0 - HR + r;
+        const long long f0 = (long long)(x0 - HR) * 3;
+        const bool row_in = gy >= 0 && gy < H;
+        for (int q = threadIdx.x & 31; q < RG_W * 3; q += 32) {
+            const long long f = f0 + q;
+            const bool in = row_in && f >= 0 && f < 3LL * W;
+            const size_t o = (size_t)gy * W * 3 + (size_t)f;
+            xs[r][q] = in ? img[o] : 0.0f;
+            ys[r][q] = in ? ref[o] : 0.0f;
+        }
     }
     __syncthreads();
-    double fsum = 0.0, esum = 0.0;
+    // each thread's six values (two rows, three channels) summed in FP32, then
+    // FP64 over the block: the FP64 pipe is slow, and six FP32 additions err
+    // by ~1e-7 relative
+    float fsum32 = 0.0f, esum32 = 0.0f;
     for (int c = 0; c < 3; ++c) {
-        // horizontal pass over the region rows, the tile's columns
-        for (int i = threadIdx.x; i < RG_H * OT_W; i += OT_THREADS) {
-            const int r = i / OT_W, col = i % OT_W;
-            float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
+        // horizontal pass over the region rows, the tile's columns: thread
+        // (row r, columns c0 .. c0 + HX - 1)
+        if (threadIdx.x < RG_H * (OT_W / HX)) {
+            const int r = threadIdx.x / (OT_W / HX), c0 = (threadIdx.x % (OT_W / HX)) * HX;
+            f2 m[HX], q[HX];
+            float xy[HX];
 #pragma unroll
-            for (int k = 0; k < 2 * HR + 1; ++k) {
-                const float xv = xs[r][(col + k) * 3 + c], yv = ys[r][(col + k) * 3 + c];
-                a = fmaf(g[k], xv, a);
-                b = fmaf(g[k], yv, b);
-                aa = fmaf(g[k], xv * xv, aa);
-                bb = fmaf(g[k], yv * yv, bb);
-                ab = fmaf(g[k], xv * yv, ab);
+            for (int j = 0; j < HX; ++j) { m[j] = q[j] = 0ull; xy[j] = 0.0f; }
+#pragma unroll
+            for (int i = 0; i < HX + 2 * HR; ++i) {
+                const float xv = xs[r][(c0 + i) * 3 + c], yv = ys[r][(c0 + i) * 3 + c];
+                const f2 v = pk(xv, yv), v2 = mul2(v, v);
+                const float vxy = xv * yv;
+#pragma unroll
+                for (int j = 0; j < HX; ++j) {
+                    const int k = i - j;
+                    if (k < 0 || k > 2 * HR) continue;
+                    m[j] = fma2(G[k], v, m[j]);
+                    q[j] = fma2(G[k], v2, q[j]);
+                    xy[j] = fmaf(lo(G[k]), vxy, xy[j]);
+                }
             }
-            hx[r][col] = a; hy[r][col] = b; hxx[r][col] = aa; hyy[r][col] = bb; hxy[r][col] = ab;
+#pragma unroll
+            for (int j = 0; j < HX; ++j) { hm[r][c0 + j] = m[j]; hq[r][c0 + j] = q[j]; hc[r][c0 + j] = xy[j]; }
         }
         __syncthreads();
-        // vertical pass and the per-pixel value and derivatives
-        for (int i = threadIdx.x; i < OT_H * OT_W; i += OT_THREADS) {
-            const int r = i / OT_W, col = i % OT_W;
-            const int gy = y0 + r, gx = x0 + col;
-            float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+        // vertical pass and the per-pixel value and derivatives: thread
+        // (column col, rows r0 .. r0 + VY - 1)
+        const int col = threadIdx.x % OT_W, r0 = (threadIdx.x / OT_W) * VY;
+        f2 mm[VY], qq[VY];
+        float cc[VY];
 #pragma unroll
-            for (int k = 0; k < 2 * HR + 1; ++k) {
-                mx = fmaf(g[k], hx[r + k][col], mx);
-                my = fmaf(g[k], hy[r + k][col], my);
-                exx = fmaf(g[k], hxx[r + k][col], exx);
-                eyy = fmaf(g[k], hyy[r + k][col], eyy);
-                exy = fmaf(g[k], hxy[r + k][col], exy);
+        for (int j = 0; j < VY; ++j) { mm[j] = qq[j] = 0ull; cc[j] = 0.0f; }
+#pragma unroll
+        for (int i = 0; i < VY + 2 * HR; ++i) {
+            const f2 a = hm[r0 + i][col], b = hq[r0 + i][col];
+            const float e = hc[r0 + i][col];
+#pragma unroll
+            for (int j = 0; j < VY; ++j) {
+                const int k = i - j;
+                if (k < 0 || k > 2 * HR) continue;
+                mm[j] = fma2(G[k], a, mm[j]);
+                qq[j] = fma2(G[k], b, qq[j]);
+                cc[j] = fmaf(lo(G[k]), e, cc[j]);
             }
+        }
+#pragma unroll
+        for (int j = 0; j < VY; ++j) {
+            const int r = r0 + j;
+            const int gy = y0 + r, gx = x0 + col;
+            float mx, my, exx, eyy;
+            unpk(mm[j], mx, my);
+            unpk(qq[j], exx, eyy);
+            const float exy = cc[j];
             if (gy < H && gx < W) {
                 const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
                 const float a1 = 2.f * mx * my + SSIM_C1, a2 = 2.f * sxy + SSIM_C2;
@@ -127,15 +208,15 @@ __global__ void __launch_bounds__(OT_THREADS) k_ssim_fwd(const float *__restrict
                 d_mx[o] = 2.f * f * (my * (ra1 - ra2) + mx * (rb2 - rb1));
                 d_exx[o] = -f * rb2;
                 d_exy[o] = 2.f * f * ra2;
-                fsum += (double)f;
+                fsum32 += f;
                 const float d = xs[r + HR][(col + HR) * 3 + c] - ys[r + HR][(col + HR) * 3 + c];
-                esum += (double)(d * d);
+                esum32 += d * d;
             }
         }
         __syncthreads();
     }
-    fsum = block_sum_d(fsum, red);
-    esum = block_sum_d(esum, red);
+    const double fsum = block_sum_d((double)fsum32, red);
+    const double esum = block_sum_d((double)esum32, red);
     if (threadIdx.x == 0) {
         part[((size_t)s * n_tiles + tile) * 2 + 0] = fsum;
         part[((size_t)s * n_tiles + tile) * 2 + 1] = esum;
@@ -277,7 +358,8 @@ __global__ void __launch_bounds__(OT_THREADS) k_objective_grad(
     const int32_t *__restrict__ toff, const int2 *__restrict__ tlist, float *__restrict__ dL)
 {
     __shared__ float pm_[RG_H][RG_W], pxx[RG_H][RG_W], pxy[RG_H][RG_W];
-    __shared__ float hm[RG_H][OT_W], hxx[RG_H][OT_W], hxy[RG_H][OT_W];
+    __shared__ f2 hmx[RG_H][HS];                   // row blurs of (d_mx, d_exx)
+    __shared__ float hxy[RG_H][HS];                // row blur of d_exy
     const int tile = blockIdx.x % n_tiles, s = blockIdx.x / n_tiles;
     const int x0 = (tile % tiles_x) * OT_W, y0 = (tile / tiles_x) * OT_H;
     const size_t npix = (size_t)H * W;
@@ -287,6 +369,9 @@ __global__ void __launch_bounds__(OT_THREADS) k_objective_grad(
     const float *ref = refs + (size_t)ref_index[s] * npix * 3;
     float g[2 * HR + 1];
     window(g);
+    f2 G[2 * HR + 1];
+#pragma unroll
+    for (int k = 0; k < 2 * HR + 1; ++k) G[k] = pk(g[k], g[k]);
     const int t0 = toff[s], t1 = toff[s + 1];
     for (int c = 0; c < 3; ++c) {
         const size_t plane = ((size_t)s * 3 + c) * npix;
@@ -300,42 +385,70 @@ __global__ void __launch_bounds__(OT_THREADS) k_objective_grad(
             pxy[r][q] = in ? d_exy[o] : 0.0f;
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < RG_H * OT_W; i += OT_THREADS) {
-            const int r = i / OT_W, col = i % OT_W;
-            float a = 0.f, b = 0.f, e = 0.f;
+        // horizontal pass: thread (row r, columns c0 .. c0 + HX - 1)
+        if (threadIdx.x < RG_H * (OT_W / HX)) {
+            const int r = threadIdx.x / (OT_W / HX), c0 = (threadIdx.x % (OT_W / HX)) * HX;
+            f2 ab[HX];
+            float e[HX];
 #pragma unroll
-            for (int k = 0; k < 2 * HR + 1; ++k) {
-                a = fmaf(g[k], pm_[r][col + k], a);
-                b = fmaf(g[k], pxx[r][col + k], b);
-                e = fmaf(g[k], pxy[r][col + k], e);
+            for (int j = 0; j < HX; ++j) { ab[j] = 0ull; e[j] = 0.0f; }
+#pragma unroll
+            for (int i = 0; i < HX + 2 * HR; ++i) {
+                const f2 v = pk(pm_[r][c0 + i], pxx[r][c0 + i]);
+                const float w = pxy[r][c0 + i];
+#pragma unroll
+                for (int j = 0; j < HX; ++j) {
+                    const int k = i - j;
+                    if (k < 0 || k > 2 * HR) continue;
+                    ab[j] = fma2(G[k], v, ab[j]);
+                    e[j] = fmaf(g[k], w, e[j]);
+                }
             }
-            hm[r][col] = a; hxx[r][col] = b; hxy[r][col] = e;
+#pragma unroll
+            for (int j = 0; j < HX; ++j) { hmx[r][c0 + j] = ab[j]; hxy[r][c0 + j] = e[j]; }
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < OT_H * OT_W; i += OT_THREADS) {
-            const int r = i / OT_W, col = i % OT_W;
-            const int gy = y0 + r, gx = x0 + col;
-            if (gy >= H || gx >= W) continue;
-            float bm = 0.f, bxx = 0.f, bxy = 0.f;
+        // vertical pass: thread (column col, rows r0 .. r0 + VY - 1)
+        const int col = threadIdx.x % OT_W, r0 = (threadIdx.x / OT_W) * VY;
+        f2 vb[VY];
+        float vc[VY];
 #pragma unroll
-            for (int k = 0; k < 2 * HR + 1; ++k) {
-                bm = fmaf(g[k], hm[r + k][col], bm);
-                bxx = fmaf(g[k], hxx[r + k][col], bxx);
-                bxy = fmaf(g[k], hxy[r + k][col], bxy);
+        for (int j = 0; j < VY; ++j) { vb[j] = 0ull; vc[j] = 0.0f; }
+#pragma unroll
+        for (int i = 0; i < VY + 2 * HR; ++i) {
+            const f2 a = hmx[r0 + i][col];
+            const float w = hxy[r0 + i][col];
+#pragma unroll
+            for (int j = 0; j < VY; ++j) {
+                const int k = i - j;
+                if (k < 0 || k > 2 * HR) continue;
+                vb[j] = fma2(G[k], a, vb[j]);
+                vc[j] = fmaf(g[k], w, vc[j]);
             }
-            const size_t o = ((size_t)gy * W + gx) * 3 + c;
-            const float xv = img[o], yv = ref[o];
-            const float dssim = (bm + 2.f * xv * bxx + yv * bxy) * inv_n;
-            float gval = ws * (2.f * (xv - yv) * inv_n - ssim_weight * dssim);
-            for (int t = t0; t < t1; ++t) {
-                const int2 e = tlist[t];               // partner, sign
-                const int j = e.x;
-                const float xj = images[(size_t)j * npix * 3 + o], yj = refs[(size_t)ref_index[j] * npix * 3 + o];
-                // e = (later - earlier) - (ref later - ref earlier); sign +1 when s is the later state
-                const float ev = (float)e.y * ((xv - xj) - (yv - yj));
-                gval += (float)e.y * tscale * 2.f * ev * inv_n;
+        }
+#pragma unroll
+        for (int j = 0; j < VY; ++j) {
+            const int r = r0 + j;
+            const int gy = y0 + r, gx = x0 + col;
+            if (gy < H && gx < W) {
+                float bm, bxx;
+                unpk(vb[j], bm, bxx);
+                const float bxy = vc[j];
+                const size_t o = ((size_t)gy * W + gx) * 3 + c;
+                const float xv = img[o], yv = ref[o];
+                const float dssim = (bm + 2.f * xv * bxx + yv * bxy) * inv_n;
+                float gval = ws * (2.f * (xv - yv) * inv_n - ssim_weight * dssim);
+                for (int t = t0; t < t1; ++t) {
+                    const int2 e = tlist[t];               // partner, sign
+                    const int sp = e.x;
+                    const float xj = images[(size_t)sp * npix * 3 + o];
+                    const float yj = refs[(size_t)ref_index[sp] * npix * 3 + o];
+                    // e = (later - earlier) - (ref later - ref earlier); sign +1 when s is the later state
+                    const float ev = (float)e.y * ((xv - xj) - (yv - yj));
+                    gval += (float)e.y * tscale * 2.f * ev * inv_n;
+                }
+                dL[(size_t)s * npix * 3 + o] = gval;
             }
-            dL[(size_t)s * npix * 3 + o] = gval;
         }
         __syncthreads();
     }

@@ -34,15 +34,20 @@ __device__ __forceinline__ int cluster_of_b(const int32_t *offs, int C, int i)
     return lo;
 }
 
-// Read a record's pixel moments and clear them, so the buffer is zero for
-// the next backward (each record is read by exactly one thread, once).
-__device__ __forceinline__ void take_record(float4 *p, float4 &a, float4 &b, float4 &c)
+// Read a record's pixel moments (issued one record ahead of their use).
+__device__ __forceinline__ void load_record(const float4 *p, float4 &a, float4 &b, float4 &c)
 {
     a = p[0]; b = p[1]; c = p[2];
+}
+
+// Clear a record whose moments were read and are not all zero, so the buffer
+// is zero for the next backward (each record is read by exactly one thread,
+// once).  Called when its values are in use, so the prefetch of the next
+// record does not wait for this test.
+__device__ __forceinline__ void clear_record(float4 *p)
+{
     const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (a.x != 0.0f || a.y != 0.0f || a.z != 0.0f || a.w != 0.0f || b.x != 0.0f || b.y != 0.0f || b.z != 0.0f ||
-        b.w != 0.0f || c.x != 0.0f)
-        p[0] = z, p[1] = z, p[2] = z;
+    p[0] = z; p[1] = z; p[2] = z;
 }
 
 // RK > 0: exactly RK temporal coefficients (the accumulators stay in registers);
@@ -104,7 +109,7 @@ __global__ void __launch_bounds__(128, SH == 0 ? 4 : 1) k_project_bwd(SceneDev s
             float4 n0 = make_float4(0, 0, 0, 0), n1 = n0, n2 = n0;
             if (vn < V) {
                 slot_n = slot_of(vn);
-                take_record(rec_grad + (size_t)slot_n * 3, n0, n1, n2);
+                load_record(rec_grad + (size_t)slot_n * 3, n0, n1, n2);
             }
             while (vn < V) {
                 const int v = vn;
@@ -113,11 +118,12 @@ __global__ void __launch_bounds__(128, SH == 0 ? 4 : 1) k_project_bwd(SceneDev s
                 vn = next_vg(v + 1);
                 if (vn < V) {
                     slot_n = slot_of(vn);
-                    take_record(rec_grad + (size_t)slot_n * 3, n0, n1, n2);
+                    load_record(rec_grad + (size_t)slot_n * 3, n0, n1, n2);
                 }
                 if (q0.x == 0.f && q0.y == 0.f && q0.z == 0.f && q0.w == 0.f && q1.x == 0.f && q1.y == 0.f &&
                     q1.z == 0.f && q1.w == 0.f && q2.x == 0.f)
                     continue;
+                clear_record(rec_grad + (size_t)slot * 3);
                 if (!decoded) {
                     load_base<SH>(s, i, a);
                     for (int l = 1; l < d; ++l) add_layer<SH>(s, i, l, a);

@@ -59,6 +59,17 @@ __device__ __forceinline__ int cluster_of(const int32_t *offs, int C, int i)
     return lo;
 }
 
+// The same over offsets staged in shared memory.
+__device__ __forceinline__ int cluster_of_shared(const int32_t *offs, int C, int i)
+{
+    int lo = 0, hi = C - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (offs[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // One thread per Gaussian: decode the base and the delivered refinement prefix
 // incrementally (Section 3), once per depth some state needs, and project that
 // decoded variant for every view group whose states render the Gaussian's
@@ -76,21 +87,24 @@ __global__ void __launch_bounds__(128, 4) k_project(SceneDev s, const ViewGroup 
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const ViewGroup *vgs = vgs_g;
     const uint32_t *need = need_g, *recBase = recBase_g;
+    const int32_t *offs = s.offs;
     if (SMEM) {
         ViewGroup *svg = reinterpret_cast<ViewGroup *>(sm_raw);
         uint32_t *sneed = reinterpret_cast<uint32_t *>(svg + V);
         uint32_t *sbase = sneed + (size_t)V * s.C;
+        int32_t *soffs = reinterpret_cast<int32_t *>(sbase + (size_t)V * s.C);
         const int nvg_words = (int)(sizeof(ViewGroup) / 4) * V;
         for (int k = threadIdx.x; k < nvg_words; k += blockDim.x)
             reinterpret_cast<uint32_t *>(svg)[k] = reinterpret_cast<const uint32_t *>(vgs_g)[k];
         for (int k = threadIdx.x; k < V * s.C; k += blockDim.x) { sneed[k] = need_g[k]; sbase[k] = recBase_g[k]; }
+        for (int k = threadIdx.x; k <= s.C; k += blockDim.x) soffs[k] = s.offs[k];
         __syncthreads();
-        vgs = svg; need = sneed; recBase = sbase;
+        vgs = svg; need = sneed; recBase = sbase; offs = soffs;
     }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += gridDim.x * blockDim.x) {
-        const int c = cluster_of(s.offs, s.C, i);
-        if (i < s.offs[c] || i >= s.offs[c + 1]) continue;   // offsets validated on the host; never taken
-        const uint32_t li = (uint32_t)(i - s.offs[c]);
+        const int c = SMEM ? cluster_of_shared(offs, s.C, i) : cluster_of(offs, s.C, i);
+        if (i < offs[c] || i >= offs[c + 1]) continue;   // offsets validated on the host; never taken
+        const uint32_t li = (uint32_t)(i - offs[c]);
         uint32_t any = 0;
         for (int v = 0; v < V; ++v) any |= need[(size_t)v * s.C + c];
         any &= ~1u;
@@ -261,7 +275,7 @@ void launch_project(const SceneDev &s, const ViewGroup *vgs, int V, const uint32
     unsigned g = (unsigned)((s.n + 127) / 128);
     if (g < 1) g = 1;
     if (g > (unsigned)sms * 4u) g = (unsigned)sms * 4u;
-    const size_t smem = sizeof(ViewGroup) * (size_t)V + 8 * (size_t)V * s.C;
+    const size_t smem = sizeof(ViewGroup) * (size_t)V + 8 * (size_t)V * s.C + 4 * (size_t)(s.C + 1);
     const bool use_smem = smem <= 40 * 1024;
     ProfScope ps_("project", st);
     if (use_smem) {
